@@ -1,0 +1,674 @@
+/*
+ * Oracle, part 3: classical algebraic multigrid (Sec. 3.2; solver settings of
+ * Sec. 4: one V-cycle, classical Ruge-Stueben interpolation, Gauss-Seidel
+ * smoothing). TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Readings and stated deviations (the same in the CUDA library):
+ *  - Strength: with s_i = -1 if a_ii < 0 else +1, j != i is strong for i iff
+ *    -s_i a_ij >= theta * max_{k != i} (-s_i a_ik) and that maximum is > 0.
+ *  - Coarsening: PMIS (De Sterck, Yang, Heys 2006) in place of the paper's
+ *    CLJP. Measure key_i = (|S^T_i| << 24) | (24 random bits); i beats j iff
+ *    key_i > key_j, or equal keys and i < j. Points no one depends on become
+ *    F. Each round, an undecided point that beats every undecided neighbour
+ *    in S u S^T becomes C; then every undecided point that strongly depends
+ *    on a new C point becomes F.
+ *  - Random bits: SplitMix64 (Steele, Lea, Flood 2014): the c-th output for
+ *    seed s is mix(s + (c + 1) * 0x9E3779B97F4A7C15). PMIS uses counter
+ *    c = ((2 l) << 32) + i, colouring c = ((2 l + 1) << 32) + i at level l.
+ *  - Interpolation: classical (direct plus distribution of strong F
+ *    neighbours through the common C points), with only the entries of row m
+ *    whose sign is opposite to a_mm distributed. Weak neighbours and strong F
+ *    neighbours that share no C point are added to the diagonal. An F point
+ *    with no strong C neighbour gets an empty row.
+ *  - Galerkin coarse operator A_c = P^T (A P), both products by ascending
+ *    inner index.
+ *  - Smoother: multicolour Gauss-Seidel (Jones-Plassmann colouring of the
+ *    symmetrised pattern, each point taking the lowest colour unused by its
+ *    already coloured neighbours), colours swept in ascending order for both
+ *    pre- and post-smoothing, in place of the paper's hybrid GS. l1-Jacobi
+ *    is the alternative.
+ *  - Coarsest level: dense LU with partial pivoting.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include "oracle.h"
+
+or_csr *or_csr_alloc(int32_t n, int32_t m, int32_t nnz);
+
+static void *xmalloc(size_t n) {
+  void *p = malloc(n ? n : 1);
+  if (!p) abort();
+  return p;
+}
+
+uint64_t or_splitmix64(uint64_t seed, uint64_t counter) {
+  uint64_t z = seed + (counter + 1u) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static double diag_of(const or_csr *A, int32_t i) {
+  for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
+    if (A->col[k] == i) return A->val[k];
+  return 0.0;
+}
+
+/* nfun > 1: unknown-based strength (hypre's "num_functions"): only entries
+ * coupling unknowns of the same kind (i mod nfun == j mod nfun) compete. */
+void or_strength_nf(const or_csr *A, double theta, int32_t nfun, uint8_t *strong) {
+  if (nfun < 1) nfun = 1;
+  for (int32_t i = 0; i < A->n; i++) {
+    double s = diag_of(A, i) < 0.0 ? -1.0 : 1.0;
+    double mx = 0.0;
+    for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
+      if (A->col[k] == i || A->col[k] % nfun != i % nfun) continue;
+      double v = -(s * A->val[k]);
+      if (v > mx) mx = v;
+    }
+    double thr = theta * mx;
+    for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
+      strong[k] = 0;
+      if (A->col[k] == i || A->col[k] % nfun != i % nfun || !(mx > 0.0)) continue;
+      double v = -(s * A->val[k]);
+      if (v >= thr) strong[k] = 1;
+    }
+  }
+}
+
+void or_strength(const or_csr *A, double theta, uint8_t *strong) { or_strength_nf(A, theta, 1, strong); }
+
+static int beats(uint64_t ki, int32_t i, uint64_t kj, int32_t j) {
+  return ki > kj || (ki == kj && i < j);
+}
+
+/* cf: 1 = C, -1 = F. */
+void or_pmis(const or_csr *A, const uint8_t *strong, uint64_t seed, int32_t level, int8_t *cf) {
+  int32_t n = A->n;
+  int32_t *lam = xmalloc(sizeof(int32_t) * (size_t)n);
+  uint64_t *key = xmalloc(sizeof(uint64_t) * (size_t)n);
+  int8_t *newc = xmalloc((size_t)n);
+  memset(lam, 0, sizeof(int32_t) * (size_t)n);
+  for (int32_t i = 0; i < n; i++)
+    for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
+      if (strong[k]) lam[A->col[k]]++;
+  /* S^T adjacency, so each point can see who depends on it */
+  int32_t *tp = xmalloc(sizeof(int32_t) * ((size_t)n + 1));
+  memset(tp, 0, sizeof(int32_t) * ((size_t)n + 1));
+  for (int32_t i = 0; i < n; i++)
+    for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
+      if (strong[k]) tp[A->col[k] + 1]++;
+  for (int32_t i = 0; i < n; i++) tp[i + 1] += tp[i];
+  int32_t *tc = xmalloc(sizeof(int32_t) * ((size_t)tp[n] + 1));
+  int32_t *fill = xmalloc(sizeof(int32_t) * ((size_t)n + 1));
+  memcpy(fill, tp, sizeof(int32_t) * (size_t)n);
+  for (int32_t i = 0; i < n; i++)
+    for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
+      if (strong[k]) tc[fill[A->col[k]]++] = i;
+  int32_t undecided = 0;
+  for (int32_t i = 0; i < n; i++) {
+    uint64_t r = or_splitmix64(seed, ((uint64_t)(2 * level) << 32) + (uint64_t)i);
+    key[i] = ((uint64_t)lam[i] << 24) | (r >> 40);
+    if (lam[i] == 0) cf[i] = -1;
+    else { cf[i] = 0; undecided++; }
+  }
+  while (undecided > 0) {
+    for (int32_t i = 0; i < n; i++) {
+      newc[i] = 0;
+      if (cf[i] != 0) continue;
+      int ok = 1;
+      for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1] && ok; k++) {
+        int32_t j = A->col[k];
+        if (strong[k] && cf[j] == 0 && !beats(key[i], i, key[j], j)) ok = 0;
+      }
+      for (int32_t q = tp[i]; q < tp[i + 1] && ok; q++) {
+        int32_t j = tc[q];
+        if (cf[j] == 0 && !beats(key[i], i, key[j], j)) ok = 0;
+      }
+      newc[i] = (int8_t)ok;
+    }
+    for (int32_t i = 0; i < n; i++)
+      if (newc[i]) { cf[i] = 1; undecided--; }
+    for (int32_t i = 0; i < n; i++) {
+      if (cf[i] != 0) continue;
+      for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
+        if (strong[k] && newc[A->col[k]]) { cf[i] = -1; undecided--; break; }
+    }
+  }
+  free(lam); free(key); free(newc); free(tp); free(tc); free(fill);
+}
+
+/* Classical interpolation; see the header comment for the reading. Row i of
+ * P for an F point, with C_i its strong C neighbours:
+ *   pass A over row i in ascending column order accumulates the diagonal
+ *     dacc from a_ii, weak a_ij, and strong F a_im whose row has no
+ *     distributable entry in C_i (denominator exactly 0); num_j = a_ij for
+ *     j in C_i;
+ *   pass B over the strong F neighbours m (ascending) with nonzero
+ *     denominator d_m = sum_{k in C_i} ahat_mk adds (a_im / d_m) * ahat_mj to
+ *     num_j for each j in C_i found in row m (ascending k);
+ *   w_ij = -(num_j / dacc); a zero dacc leaves the row empty. */
+or_csr *or_interp(const or_csr *A, const uint8_t *strong, const int8_t *cf) {
+  int32_t n = A->n;
+  int32_t *cidx = xmalloc(sizeof(int32_t) * (size_t)n);
+  int32_t nc = 0;
+  for (int32_t i = 0; i < n; i++) cidx[i] = cf[i] == 1 ? nc++ : -1;
+  /* row sizes */
+  int32_t *cnt = xmalloc(sizeof(int32_t) * (size_t)n);
+  int64_t tot = 0;
+  for (int32_t i = 0; i < n; i++) {
+    int32_t c = 0;
+    if (cf[i] == 1) c = 1;
+    else
+      for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++)
+        if (strong[k] && cf[A->col[k]] == 1) c++;
+    cnt[i] = c;
+    tot += c;
+  }
+  int32_t *mark = xmalloc(sizeof(int32_t) * (size_t)n);  /* position of j in C_i, or -1 */
+  double *num = xmalloc(sizeof(double) * (size_t)n);
+  for (int32_t j = 0; j < n; j++) mark[j] = -1;
+  or_csr *P = or_csr_alloc(n, nc, (int32_t)tot);
+  int32_t pos = 0;
+  P->rowptr[0] = 0;
+  for (int32_t i = 0; i < n; i++) {
+    if (cf[i] == 1) {
+      P->col[pos] = cidx[i];
+      P->val[pos] = 1.0;
+      pos++;
+      P->rowptr[i + 1] = pos;
+      continue;
+    }
+    if (cnt[i] == 0) { P->rowptr[i + 1] = pos; continue; }
+    int32_t base = pos;
+    for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
+      int32_t j = A->col[k];
+      if (strong[k] && cf[j] == 1) { mark[j] = pos - base; P->col[pos] = cidx[j]; pos++; }
+    }
+    /* pass A */
+    double dacc = 0.0;
+    int dinit = 0;
+    for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
+      int32_t j = A->col[k];
+      double a = A->val[k];
+      int add = 0;
+      if (j == i || !strong[k]) add = 1;
+      else if (cf[j] == 1) num[mark[j]] = a;
+      else {
+        double sm = diag_of(A, j) < 0.0 ? -1.0 : 1.0;
+        double d = 0.0;
+        int dset = 0;
+        for (int32_t q = A->rowptr[j]; q < A->rowptr[j + 1]; q++) {
+          int32_t kk = A->col[q];
+          if (kk == j || mark[kk] < 0) continue;
+          double av = A->val[q];
+          if (!(sm * av < 0.0)) continue;
+          if (!dset) { d = av; dset = 1; } else d = d + av;
+        }
+        if (d == 0.0) add = 1;
+      }
+      if (add) {
+        if (!dinit) { dacc = a; dinit = 1; } else dacc = dacc + a;
+      }
+    }
+    /* pass B */
+    for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
+      int32_t m = A->col[k];
+      if (m == i || !strong[k] || cf[m] == 1) continue;
+      double sm = diag_of(A, m) < 0.0 ? -1.0 : 1.0;
+      double d = 0.0;
+      int dset = 0;
+      for (int32_t q = A->rowptr[m]; q < A->rowptr[m + 1]; q++) {
+        int32_t kk = A->col[q];
+        if (kk == m || mark[kk] < 0) continue;
+        double av = A->val[q];
+        if (!(sm * av < 0.0)) continue;
+        if (!dset) { d = av; dset = 1; } else d = d + av;
+      }
+      if (d == 0.0) continue;
+      double t = A->val[k] / d;
+      for (int32_t q = A->rowptr[m]; q < A->rowptr[m + 1]; q++) {
+        int32_t kk = A->col[q];
+        if (kk == m || mark[kk] < 0) continue;
+        double av = A->val[q];
+        if (!(sm * av < 0.0)) continue;
+        num[mark[kk]] = num[mark[kk]] + t * av;
+      }
+    }
+    if (dacc == 0.0) {
+      for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) mark[A->col[k]] = -1;
+      pos = base;
+      P->rowptr[i + 1] = pos;
+      continue;
+    }
+    for (int32_t q = base; q < pos; q++) P->val[q] = -(num[q - base] / dacc);
+    for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) mark[A->col[k]] = -1;
+    P->rowptr[i + 1] = pos;
+  }
+  P->nnz = pos;
+  free(cidx); free(cnt); free(mark); free(num);
+  return P;
+}
+
+
+static int cmp_i32_amg(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return (x > y) - (x < y);
+}
+
+/* Distance-two "extended+i" interpolation (De Sterck, Falgout, Nolting, Yang
+ * 2008), the usual companion of PMIS. For an F point i with strong F
+ * neighbours F_i and strong C neighbours C_i, the interpolatory set is
+ * Chat_i = C_i united with the strong C neighbours of every k in F_i, and
+ *   w_ij = -(1/dtil) (a_ij + sum_{k in F_i} a_ik abar_kj / d_k),  j in Chat_i,
+ *   dtil = a_ii + sum_{weak n not in Chat_i} a_in + sum_{k in F_i} a_ik abar_ki / d_k,
+ *   d_k  = sum_{l in Chat_i + {i}} abar_kl,
+ * with abar_kl = a_kl when its sign is opposite to a_kk, else 0 (a_ij = 0
+ * when j is not a neighbour of i). A strong F neighbour with d_k = 0 is added
+ * to the diagonal. Arithmetic order: pass A runs over row i ascending
+ * (diagonal, weak lumps and d_k = 0 lumps into dtil; a_ij into num_j); pass B
+ * over the k of F_i ascending, t = a_ik / d_k, then over row k ascending adds
+ * t * abar_kl to num_l (l in Chat_i) or to dtil (l = i). Every sum starts from
+ * its first term. Entries whose num_j was never set are left out; a zero
+ * dtil or an empty Chat_i gives an empty row. */
+or_csr *or_interp_ext(const or_csr *A, const uint8_t *strong, const int8_t *cf) {
+  int32_t n = A->n;
+  int32_t *cidx = xmalloc(sizeof(int32_t) * (size_t)n);
+  int32_t nc = 0;
+  for (int32_t i = 0; i < n; i++) cidx[i] = cf[i] == 1 ? nc++ : -1;
+  int32_t *mark = xmalloc(sizeof(int32_t) * (size_t)n);
+  for (int32_t j = 0; j < n; j++) mark[j] = -1;
+  int32_t cap = 1024, rowcap = 4096;
+  int32_t *chat = xmalloc(sizeof(int32_t) * (size_t)rowcap);
+  double *num = xmalloc(sizeof(double) * (size_t)rowcap);
+  int8_t *nset = xmalloc((size_t)rowcap);
+  int32_t *pc = xmalloc(sizeof(int32_t) * (size_t)cap);
+  double *pv = xmalloc(sizeof(double) * (size_t)cap);
+  int32_t *rp = xmalloc(sizeof(int32_t) * ((size_t)n + 1));
+  int32_t pos = 0;
+  rp[0] = 0;
+  for (int32_t i = 0; i < n; i++) {
+    int32_t m = 0;
+    if (cf[i] == 1) {
+      if (pos + 1 > cap) { cap *= 2; pc = realloc(pc, sizeof(int32_t) * (size_t)cap); pv = realloc(pv, sizeof(double) * (size_t)cap); }
+      pc[pos] = cidx[i]; pv[pos] = 1.0; pos++;
+      rp[i + 1] = pos;
+      continue;
+    }
+    /* Chat_i */
+    for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+      int32_t j = A->col[q];
+      if (j == i || !strong[q]) continue;
+      if (cf[j] == 1) {
+        if (mark[j] < 0) { mark[j] = 0; chat[m++] = j; }
+      } else {
+        for (int32_t t = A->rowptr[j]; t < A->rowptr[j + 1]; t++) {
+          int32_t l = A->col[t];
+          if (l != j && strong[t] && cf[l] == 1 && mark[l] < 0) { mark[l] = 0; chat[m++] = l; }
+        }
+      }
+    }
+    if (m == 0) { rp[i + 1] = pos; continue; }
+    qsort(chat, (size_t)m, sizeof(int32_t), cmp_i32_amg);
+    for (int32_t q = 0; q < m; q++) { mark[chat[q]] = q; nset[q] = 0; num[q] = 0.0; }
+    double dacc = 0.0;
+    int dinit = 0;
+#define DADD(v) do { if (!dinit) { dacc = (v); dinit = 1; } else dacc = dacc + (v); } while (0)
+    /* pass A */
+    for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+      int32_t j = A->col[q];
+      double a = A->val[q];
+      if (j == i) { DADD(a); continue; }
+      if (mark[j] >= 0) { num[mark[j]] = a; nset[mark[j]] = 1; continue; }
+      if (strong[q] && cf[j] != 1) {
+        double sk = diag_of(A, j) < 0.0 ? -1.0 : 1.0, d = 0.0;
+        int ds = 0;
+        for (int32_t t = A->rowptr[j]; t < A->rowptr[j + 1]; t++) {
+          int32_t l = A->col[t];
+          if (l == j || !(l == i || mark[l] >= 0)) continue;
+          double av = A->val[t];
+          if (!(sk * av < 0.0)) continue;
+          if (!ds) { d = av; ds = 1; } else d = d + av;
+        }
+        if (d == 0.0) DADD(a);
+        continue;
+      }
+      DADD(a);
+    }
+    /* pass B */
+    for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+      int32_t k = A->col[q];
+      if (k == i || !strong[q] || cf[k] == 1 || mark[k] >= 0) continue;
+      double sk = diag_of(A, k) < 0.0 ? -1.0 : 1.0, d = 0.0;
+      int ds = 0;
+      for (int32_t t = A->rowptr[k]; t < A->rowptr[k + 1]; t++) {
+        int32_t l = A->col[t];
+        if (l == k || !(l == i || mark[l] >= 0)) continue;
+        double av = A->val[t];
+        if (!(sk * av < 0.0)) continue;
+        if (!ds) { d = av; ds = 1; } else d = d + av;
+      }
+      if (d == 0.0) continue;
+      double tq = A->val[q] / d;
+      for (int32_t t = A->rowptr[k]; t < A->rowptr[k + 1]; t++) {
+        int32_t l = A->col[t];
+        if (l == k || !(l == i || mark[l] >= 0)) continue;
+        double av = A->val[t];
+        if (!(sk * av < 0.0)) continue;
+        double pr = tq * av;
+        if (l == i) DADD(pr);
+        else if (!nset[mark[l]]) { num[mark[l]] = pr; nset[mark[l]] = 1; }
+        else num[mark[l]] = num[mark[l]] + pr;
+      }
+    }
+#undef DADD
+    if (dacc != 0.0) {
+      if (pos + m > cap) { while (pos + m > cap) cap *= 2; pc = realloc(pc, sizeof(int32_t) * (size_t)cap); pv = realloc(pv, sizeof(double) * (size_t)cap); }
+      for (int32_t q = 0; q < m; q++) {
+        if (!nset[q]) continue;
+        pc[pos] = cidx[chat[q]];
+        pv[pos] = -(num[q] / dacc);
+        pos++;
+      }
+    }
+    for (int32_t q = 0; q < m; q++) mark[chat[q]] = -1;
+    rp[i + 1] = pos;
+  }
+  or_csr *P = or_csr_alloc(n, nc, pos);
+  memcpy(P->rowptr, rp, sizeof(int32_t) * ((size_t)n + 1));
+  memcpy(P->col, pc, sizeof(int32_t) * (size_t)pos);
+  memcpy(P->val, pv, sizeof(double) * (size_t)pos);
+  free(cidx); free(mark); free(chat); free(num); free(nset); free(pc); free(pv); free(rp);
+  return P;
+}
+
+or_csr *or_spgemm(const or_csr *A, const or_csr *B);
+or_csr *or_transpose(const or_csr *A);
+void or_csr_free(or_csr *A);
+
+or_csr *or_galerkin(const or_csr *A, const or_csr *P) {
+  or_csr *AP = or_spgemm(A, P);
+  or_csr *R = or_transpose(P);
+  or_csr *Ac = or_spgemm(R, AP);
+  or_csr_free(AP);
+  or_csr_free(R);
+  return Ac;
+}
+
+/* Jones-Plassmann colouring of the symmetrised pattern of A (diagonal
+ * ignored). Returns the number of colours. */
+int32_t or_jp_colour(const or_csr *A, uint64_t seed, int32_t level, int32_t *colour) {
+  int32_t n = A->n;
+  uint64_t *key = xmalloc(sizeof(uint64_t) * (size_t)n);
+  int8_t *sel = xmalloc((size_t)n);
+  /* transpose adjacency */
+  int32_t *tp = xmalloc(sizeof(int32_t) * ((size_t)n + 1));
+  memset(tp, 0, sizeof(int32_t) * ((size_t)n + 1));
+  for (int32_t k = 0; k < A->nnz; k++) tp[A->col[k] + 1]++;
+  for (int32_t i = 0; i < n; i++) tp[i + 1] += tp[i];
+  int32_t *tc = xmalloc(sizeof(int32_t) * ((size_t)A->nnz + 1));
+  int32_t *fill = xmalloc(sizeof(int32_t) * ((size_t)n + 1));
+  memcpy(fill, tp, sizeof(int32_t) * (size_t)n);
+  for (int32_t i = 0; i < n; i++)
+    for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) tc[fill[A->col[k]]++] = i;
+  for (int32_t i = 0; i < n; i++) {
+    key[i] = or_splitmix64(seed, ((uint64_t)(2 * level + 1) << 32) + (uint64_t)i);
+    colour[i] = -1;
+  }
+  int32_t left = n, ncol = 0;
+  uint8_t *used = xmalloc(1024);
+  while (left > 0) {
+    for (int32_t i = 0; i < n; i++) {
+      sel[i] = 0;
+      if (colour[i] >= 0) continue;
+      int ok = 1;
+      for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1] && ok; k++) {
+        int32_t j = A->col[k];
+        if (j != i && colour[j] < 0 && !beats(key[i], i, key[j], j)) ok = 0;
+      }
+      for (int32_t q = tp[i]; q < tp[i + 1] && ok; q++) {
+        int32_t j = tc[q];
+        if (j != i && colour[j] < 0 && !beats(key[i], i, key[j], j)) ok = 0;
+      }
+      sel[i] = (int8_t)ok;
+    }
+    for (int32_t i = 0; i < n; i++) {
+      if (!sel[i]) continue;
+      memset(used, 0, 1024);
+      for (int32_t k = A->rowptr[i]; k < A->rowptr[i + 1]; k++) {
+        int32_t j = A->col[k];
+        if (j != i && colour[j] >= 0 && colour[j] < 1024) used[colour[j]] = 1;
+      }
+      for (int32_t q = tp[i]; q < tp[i + 1]; q++) {
+        int32_t j = tc[q];
+        if (j != i && colour[j] >= 0 && colour[j] < 1024) used[colour[j]] = 1;
+      }
+      int32_t c = 0;
+      while (c < 1024 && used[c]) c++;
+      colour[i] = c;
+    }
+    for (int32_t i = 0; i < n; i++)
+      if (sel[i]) { left--; if (colour[i] + 1 > ncol) ncol = colour[i] + 1; }
+  }
+  free(key); free(sel); free(tp); free(tc); free(fill); free(used);
+  return ncol;
+}
+
+/* ---------------- dense LU ---------------- */
+int32_t or_dense_lu(int32_t n, double *a, int32_t *piv) {
+  int32_t sing = 0;
+  for (int32_t k = 0; k < n; k++) {
+    int32_t p = k;
+    double mx = fabs(a[(size_t)k * n + k]);
+    for (int32_t i = k + 1; i < n; i++)
+      if (fabs(a[(size_t)i * n + k]) > mx) { mx = fabs(a[(size_t)i * n + k]); p = i; }
+    piv[k] = p;
+    if (p != k)
+      for (int32_t j = 0; j < n; j++) {
+        double t = a[(size_t)k * n + j];
+        a[(size_t)k * n + j] = a[(size_t)p * n + j];
+        a[(size_t)p * n + j] = t;
+      }
+    double d = a[(size_t)k * n + k];
+    if (d == 0.0) { sing = 1; continue; }
+    for (int32_t i = k + 1; i < n; i++) {
+      double l = a[(size_t)i * n + k] / d;
+      a[(size_t)i * n + k] = l;
+      for (int32_t j = k + 1; j < n; j++) a[(size_t)i * n + j] -= l * a[(size_t)k * n + j];
+    }
+  }
+  return sing;
+}
+
+void or_dense_lu_solve(int32_t n, const double *a, const int32_t *piv, const double *b, double *x) {
+  for (int32_t i = 0; i < n; i++) x[i] = b[i];
+  for (int32_t k = 0; k < n; k++)
+    if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+  for (int32_t i = 0; i < n; i++)
+    for (int32_t j = 0; j < i; j++) x[i] -= a[(size_t)i * n + j] * x[j];
+  for (int32_t i = n - 1; i >= 0; i--) {
+    for (int32_t j = i + 1; j < n; j++) x[i] -= a[(size_t)i * n + j] * x[j];
+    double d = a[(size_t)i * n + i];
+    x[i] = d != 0.0 ? x[i] / d : 0.0;
+  }
+}
+
+/* ---------------- hierarchy ---------------- */
+#define OR_MAXLEV 32
+struct or_amg {
+  or_amg_params prm;
+  int32_t nlev;
+  or_csr *A[OR_MAXLEV];
+  or_csr *P[OR_MAXLEV];
+  or_csr *R[OR_MAXLEV];
+  int8_t *cf[OR_MAXLEV];
+  int32_t *colour[OR_MAXLEV];
+  int32_t ncol[OR_MAXLEV];
+  double *l1[OR_MAXLEV];
+  double *lu;        /* coarsest dense LU */
+  int32_t *piv;
+  int32_t dense;     /* 1 if the coarsest level is solved by LU */
+};
+
+or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
+  or_amg *H = xmalloc(sizeof(or_amg));
+  memset(H, 0, sizeof(or_amg));
+  H->prm = *prm;
+  int32_t maxl = prm->max_levels < OR_MAXLEV ? prm->max_levels : OR_MAXLEV;
+  H->A[0] = or_csr_alloc(A0->n, A0->m, A0->nnz);
+  memcpy(H->A[0]->rowptr, A0->rowptr, sizeof(int32_t) * ((size_t)A0->n + 1));
+  memcpy(H->A[0]->col, A0->col, sizeof(int32_t) * (size_t)A0->nnz);
+  memcpy(H->A[0]->val, A0->val, sizeof(double) * (size_t)A0->nnz);
+  int32_t l = 0;
+  for (;;) {
+    or_csr *A = H->A[l];
+    int32_t n = A->n;
+    H->cf[l] = NULL;
+    if (n <= prm->coarse_n || l == maxl - 1) break;
+    uint8_t *st = xmalloc((size_t)A->nnz);
+    or_strength_nf(A, prm->theta, l == 0 ? prm->num_functions : 1, st);
+    int8_t *cf = xmalloc((size_t)n);
+    or_pmis(A, st, prm->seed, l, cf);
+    int32_t nc = 0;
+    for (int32_t i = 0; i < n; i++) nc += cf[i] == 1;
+    if (nc == 0 || (double)nc > 0.9 * (double)n) { free(st); free(cf); break; }
+    H->cf[l] = cf;
+    H->P[l] = prm->interp == 1 ? or_interp_ext(A, st, cf) : or_interp(A, st, cf);
+    H->R[l] = or_transpose(H->P[l]);
+    H->A[l + 1] = or_galerkin(A, H->P[l]);
+    free(st);
+    l++;
+  }
+  H->nlev = l + 1;
+  for (int32_t k = 0; k < H->nlev - 1; k++) {
+    or_csr *A = H->A[k];
+    H->colour[k] = xmalloc(sizeof(int32_t) * ((size_t)A->n + 1));
+    H->ncol[k] = or_jp_colour(A, prm->seed, k, H->colour[k]);
+    H->l1[k] = xmalloc(sizeof(double) * ((size_t)A->n + 1));
+    for (int32_t i = 0; i < A->n; i++) {
+      double d = 0.0, off = 0.0;
+      for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+        if (A->col[q] == i) d = A->val[q];
+        else off += fabs(A->val[q]);
+      }
+      H->l1[k][i] = d < 0.0 ? d - off : d + off;
+    }
+  }
+  or_csr *Ac = H->A[H->nlev - 1];
+  int32_t nc = Ac->n;
+  if (nc <= prm->max_dense) {
+    H->dense = 1;
+    H->lu = xmalloc(sizeof(double) * (size_t)nc * (size_t)nc + 1);
+    H->piv = xmalloc(sizeof(int32_t) * ((size_t)nc + 1));
+    memset(H->lu, 0, sizeof(double) * (size_t)nc * (size_t)nc);
+    for (int32_t i = 0; i < nc; i++)
+      for (int32_t q = Ac->rowptr[i]; q < Ac->rowptr[i + 1]; q++)
+        H->lu[(size_t)i * nc + Ac->col[q]] = Ac->val[q];
+    or_dense_lu(nc, H->lu, H->piv);
+  } else {
+    /* coarsest level too large for a dense factorisation: smooth it instead */
+    int32_t k = H->nlev - 1;
+    H->colour[k] = xmalloc(sizeof(int32_t) * ((size_t)nc + 1));
+    H->ncol[k] = or_jp_colour(Ac, prm->seed, k, H->colour[k]);
+    H->l1[k] = xmalloc(sizeof(double) * ((size_t)nc + 1));
+    for (int32_t i = 0; i < nc; i++) {
+      double d = 0.0, off = 0.0;
+      for (int32_t q = Ac->rowptr[i]; q < Ac->rowptr[i + 1]; q++) {
+        if (Ac->col[q] == i) d = Ac->val[q];
+        else off += fabs(Ac->val[q]);
+      }
+      H->l1[k][i] = d < 0.0 ? d - off : d + off;
+    }
+  }
+  return H;
+}
+
+void or_amg_free(or_amg *H) {
+  if (!H) return;
+  for (int32_t l = 0; l < H->nlev; l++) {
+    or_csr_free(H->A[l]);
+    or_csr_free(H->P[l]);
+    or_csr_free(H->R[l]);
+    free(H->cf[l]);
+    free(H->colour[l]);
+    free(H->l1[l]);
+  }
+  free(H->lu);
+  free(H->piv);
+  free(H);
+}
+
+int32_t or_amg_nlevels(const or_amg *H) { return H->nlev; }
+const or_csr *or_amg_A(const or_amg *H, int32_t l) { return H->A[l]; }
+const or_csr *or_amg_P(const or_amg *H, int32_t l) { return H->P[l]; }
+void or_amg_cf(const or_amg *H, int32_t l, int8_t *cf) {
+  if (H->cf[l]) memcpy(cf, H->cf[l], (size_t)H->A[l]->n);
+}
+int32_t or_amg_colours(const or_amg *H, int32_t l, int32_t *colour) {
+  if (!H->colour[l]) return 0;
+  memcpy(colour, H->colour[l], sizeof(int32_t) * (size_t)H->A[l]->n);
+  return H->ncol[l];
+}
+
+/* One smoothing sweep on level l (x updated in place). */
+void or_amg_smooth(const or_amg *H, int32_t l, const double *b, double *x) {
+  const or_csr *A = H->A[l];
+  if (H->prm.smoother == 1) {
+    double *r = xmalloc(sizeof(double) * ((size_t)A->n + 1));
+    for (int32_t i = 0; i < A->n; i++) {
+      double s = 0.0;
+      for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) s += A->val[q] * x[A->col[q]];
+      r[i] = b[i] - s;
+    }
+    for (int32_t i = 0; i < A->n; i++)
+      if (H->l1[l][i] != 0.0) x[i] += r[i] / H->l1[l][i];
+    free(r);
+    return;
+  }
+  for (int32_t c = 0; c < H->ncol[l]; c++) {
+    for (int32_t i = 0; i < A->n; i++) {
+      if (H->colour[l][i] != c) continue;
+      double s = 0.0, d = 0.0;
+      for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+        if (A->col[q] == i) d = A->val[q];
+        else s += A->val[q] * x[A->col[q]];
+      }
+      if (d != 0.0) x[i] = (b[i] - s) / d;
+    }
+  }
+}
+
+static void vcycle(const or_amg *H, int32_t l, const double *b, double *x) {
+  const or_csr *A = H->A[l];
+  int32_t n = A->n;
+  if (l == H->nlev - 1) {
+    if (H->dense) {
+      or_dense_lu_solve(n, H->lu, H->piv, b, x);
+    } else {
+      for (int32_t i = 0; i < n; i++) x[i] = 0.0;
+      for (int32_t s = 0; s < H->prm.nu1 + H->prm.nu2; s++) or_amg_smooth(H, l, b, x);
+    }
+    return;
+  }
+  for (int32_t i = 0; i < n; i++) x[i] = 0.0;
+  for (int32_t s = 0; s < H->prm.nu1; s++) or_amg_smooth(H, l, b, x);
+  double *r = xmalloc(sizeof(double) * ((size_t)n + 1));
+  for (int32_t i = 0; i < n; i++) {
+    double s = 0.0;
+    for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) s += A->val[q] * x[A->col[q]];
+    r[i] = b[i] - s;
+  }
+  int32_t nc = H->A[l + 1]->n;
+  double *bc = xmalloc(sizeof(double) * ((size_t)nc + 1));
+  double *xc = xmalloc(sizeof(double) * ((size_t)nc + 1));
+  or_csr_spmv(H->R[l], r, bc);
+  vcycle(H, l + 1, bc, xc);
+  const or_csr *P = H->P[l];
+  for (int32_t i = 0; i < n; i++)
+    for (int32_t q = P->rowptr[i]; q < P->rowptr[i + 1]; q++) x[i] += P->val[q] * xc[P->col[q]];
+  for (int32_t s = 0; s < H->prm.nu2; s++) or_amg_smooth(H, l, b, x);
+  free(r); free(bc); free(xc);
+}
+
+void or_amg_vcycle(const or_amg *H, const double *b, double *x) { vcycle(H, 0, b, x); }
