@@ -1,0 +1,240 @@
+/*
+ * rsflow: GB300 (sm_103a) solver for the Newton Jacobians of a fully implicit
+ * two-phase (water/oil) cell-centred finite-volume model, after Bui, Elman and
+ * Moulton, "Algebraic Multigrid Preconditioners for Multiphase Flow in Porous
+ * Media" (arXiv:1611.00127).
+ *
+ * Conventions for every call:
+ *  - Return value: 0 (RS_OK) on success; > 0 a non-fatal outcome
+ *    (RS_NOT_CONVERGED); < 0 an error (the call did nothing further). The
+ *    text of the last error of the calling thread is available from
+ *    rs_last_error().
+ *  - Array arguments are DEVICE pointers owned by the caller unless a field
+ *    says "host". They must stay valid and unmodified while a call that uses
+ *    them is in flight on the stream, and, for a preconditioner, for as long
+ *    as the preconditioner is applied (it keeps a reference to J).
+ *  - Every call takes a cudaStream_t and enqueues its GPU work there. Calls
+ *    marked (sync) wait for their own work before returning, to fill host
+ *    statistics; all others are asynchronous.
+ *  - Handles (rs_amg, rs_precond) own device memory allocated by the library;
+ *    free them with the matching *_destroy. A handle is not thread-safe.
+ *  - Unknowns are interleaved per cell: entry 2i is the water pressure P_w of
+ *    cell i [Pa], entry 2i+1 its oil saturation S_n (Sec. 2, u = (P_w, S_n)).
+ *  - Batches: a matrix may hold several independent systems stacked as a
+ *    block-diagonal matrix. seg_off (host array of nseg+1 block-row offsets)
+ *    marks them; all solver work (AMG hierarchies, orthogonalisation,
+ *    convergence tests) is then done per system, in one set of launches.
+ */
+#ifndef RSFLOW_H
+#define RSFLOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RS_OK 0
+#define RS_NOT_CONVERGED 1
+#define RS_EINVAL (-1)
+#define RS_ECUDA (-2)
+#define RS_ETIMEOUT (-3)
+#define RS_ENOMEM (-4)
+#define RS_ESETUP (-5)
+#define RS_EBREAKDOWN (-6)
+
+/* 2x2-block CSR matrix, FP64. Block k (columns col[k]) is stored row-major at
+ * val[4k..4k+3] = [dF_w/dP_w, dF_w/dS_n, dF_n/dP_w, dF_n/dS_n]; this is the
+ * grid-point ordering of Sec. 3.2, with the blocks A_pp, A_ps, A_sp, A_ss of
+ * eq. (jacobian) interleaved. Columns ascending in every block row, diagonal
+ * block present. nseg = 0 or seg_off = NULL means one system. */
+typedef struct rs_bsr2 {
+  int32_t nb;              /* block rows (cells) */
+  int32_t nnzb;            /* stored blocks */
+  const int32_t *row_ptr;  /* [nb+1] */
+  const int32_t *col;      /* [nnzb] */
+  double *val;             /* [4*nnzb] */
+  int32_t nseg;            /* number of stacked systems (0 or 1: one) */
+  const int32_t *seg_off;  /* host [nseg+1] block-row offsets, seg_off[0]=0, seg_off[nseg]=nb */
+} rs_bsr2;
+
+/* Scalar CSR matrix, FP64, square, columns ascending. */
+typedef struct rs_csr {
+  int32_t n, nnz;
+  const int32_t *row_ptr;  /* [n+1] */
+  const int32_t *col;      /* [nnz] */
+  const double *val;       /* [nnz] */
+  int32_t nseg;
+  const int32_t *seg_off;  /* host [nseg+1] row offsets, or NULL */
+} rs_csr;
+
+/* One Cartesian grid (Sec. 2): cells numbered x fastest,
+ * i = ix + nx (iy + ny iz); 2D grids have nz = 1 and unit thickness. */
+typedef struct rs_problem {
+  int32_t dim, nx, ny, nz;
+  double hx, hy, hz;                  /* cell sizes [m] */
+  const double *kx, *ky, *kz;         /* device [ncell] permeability [m^2] */
+  double phi, mu_w, mu_n, rho_w, rho_n, g;
+  int32_t pc_model;                   /* 0 none, 1 linear P_0 (1-Sb), 2 Brooks-Corey P_d Sb^(-1/lambda) */
+  double pc_p0, pc_pd, bc_lambda;     /* lambda also sets the Brooks-Corey relative permeabilities */
+  double s_wr, s_nr;                  /* residual saturations */
+  double u_in;                        /* water Darcy flux injected through the x = 0 face [m/s] */
+  double p_out, sn_out;               /* Dirichlet outlet on the x = L face */
+} rs_problem;
+
+#define RS_SMOOTH_MCGS 0
+#define RS_SMOOTH_L1JACOBI 1
+#define RS_INTERP_CLASSICAL 0
+#define RS_INTERP_EXTI 1
+#define RS_PREC_FP32 0   /* V-cycle values, vectors and sums in FP32 */
+#define RS_PREC_FP64 1
+
+typedef struct rs_amg_params {
+  double theta;            /* strength threshold (e.g. 0.25 in 2D, 0.5 in 3D) */
+  uint64_t seed;           /* PMIS and colouring random stream (SplitMix64) */
+  int32_t max_levels;      /* <= 25 */
+  int32_t coarse_n;        /* a system stops coarsening at or below this many rows */
+  int32_t max_dense;       /* largest coarsest level handled by the dense solve */
+  int32_t smoother;        /* RS_SMOOTH_* */
+  int32_t nu1, nu2;        /* pre- and post-smoothing sweeps */
+  int32_t interp;          /* RS_INTERP_* */
+  int32_t num_functions;   /* >1: unknown-based strength on the finest level */
+  int32_t precision;       /* RS_PREC_* of the V-cycle */
+} rs_amg_params;
+
+typedef struct rs_amg rs_amg;
+typedef struct rs_precond rs_precond;
+
+#define RS_PC_AMG_J 0   /* black-box AMG on the point-ordered J (Sec. 3.2) */
+#define RS_PC_CPR1 1    /* Algorithm 1, combinative two-stage CPR-AMG(1) */
+#define RS_PC_CPR2 2    /* Algorithm 2, additive two-stage CPR-AMG(2) */
+#define RS_PC_BF 3      /* Algorithm 3, block factorisation with SIMPLE Schur */
+
+#define RS_DECOUPLE_NONE 0
+#define RS_DECOUPLE_ABF 1     /* D^{-1} J, D = per-cell 2x2 diagonal block */
+#define RS_DECOUPLE_QIMPES 2  /* pressure row += -(a_ps,ii / a_ss,ii) oil row */
+
+typedef struct rs_precond_params {
+  int32_t kind;            /* RS_PC_* */
+  int32_t decouple;        /* CPR only: RS_DECOUPLE_* */
+  int32_t p1;              /* CPR only: 0 point-block Jacobi (the only GPU P1) */
+  rs_amg_params amg;
+} rs_precond_params;
+
+typedef struct rs_gmres_params {
+  int32_t m;               /* restart length */
+  int32_t maxit;           /* total Arnoldi steps per system */
+  double rtol;             /* stop when ||b - J x||_2 <= rtol ||b||_2 */
+} rs_gmres_params;
+
+typedef struct rs_gmres_stats {
+  int32_t iterations;      /* max over systems */
+  int32_t converged;       /* number of systems that reached rtol */
+  double relres;           /* max over systems of the true relative residual */
+  int32_t *its;            /* host [nseg] per-system iterations, or NULL */
+  double *relres_seg;      /* host [nseg] per-system true relative residual, or NULL */
+} rs_gmres_stats;
+
+typedef struct rs_newton_params {
+  int32_t max_newton;
+  double ftol;             /* on max_i |F_a,i| dt / (V phi rho_a) */
+  rs_gmres_params gmres;
+  rs_precond_params prec;
+} rs_newton_params;
+
+typedef struct rs_newton_stats {
+  int32_t newton_its;
+  int32_t linear_its;      /* summed over Newton iterations */
+  double fnorm;            /* final scaled residual */
+  double setup_ms, solve_ms, assemble_ms;
+} rs_newton_stats;
+
+/* Text of the last error on this thread (never NULL). */
+const char *rs_last_error(void);
+
+/* Library version and the CUDA architecture it was built for. */
+int rs_version(int *major, int *minor, int *arch);
+
+/* ---------------------------------------------------------------- grid --- */
+/* Number of stored blocks of the two-point-flux pattern of `nprob` grids
+ * stacked in order (host call, no GPU work). */
+int64_t rs_bsr2_nnzb(const rs_problem *probs, int32_t nprob);
+
+/* Block pattern (Sec. 2, TPFA neighbours plus the diagonal) of the stacked
+ * grids: row_ptr [ncell_total+1], col [nnzb] (device outputs). */
+int rs_bsr2_pattern(const rs_problem *probs, int32_t nprob, int32_t *row_ptr, int32_t *col,
+                    cudaStream_t stream);
+
+/* ------------------------------------------------------------ the calls --- */
+/* Residual F(u) and exact Jacobian J(u) of the backward-Euler TPFA system
+ * (eq. fully_discrete_system; Jacobian eq. linearize_fc / eq. jacobian), for
+ * `nprob` grids stacked in order. u, u_old: [2 N] interleaved (P_w, S_n).
+ * F: [2 N] output (mass-rate form, kg/s). J->val is overwritten on the
+ * pattern from rs_bsr2_pattern; J may be NULL to form F only. */
+int jacobian_assemble(const rs_problem *probs, int32_t nprob, const double *u, const double *u_old,
+                      double dt, rs_bsr2 *J, double *F, cudaStream_t stream);
+
+/* Classical AMG hierarchy for a scalar matrix (Sec. 3.2; solver settings of
+ * Sec. 4 with PMIS coarsening and the stated interpolation): strength graph,
+ * PMIS C/F splitting, interpolation, Galerkin A_c = P^T A P, colouring,
+ * coarsest dense inverse. A is read during the call only. (sync) */
+int amg_setup(const rs_csr *A, const rs_amg_params *params, rs_amg **H, cudaStream_t stream);
+int amg_destroy(rs_amg *H);
+
+/* x = one V(nu1,nu2)-cycle applied to b with zero initial guess (FP64 in and
+ * out; the cycle itself runs in params.precision). */
+int amg_apply(const rs_amg *H, const double *b, double *x, cudaStream_t stream);
+
+/* Preconditioner M for J (Sec. 3.2-3.4): builds the needed blocks, decoupling
+ * and AMG hierarchies. (sync) */
+int precond_create(const rs_bsr2 *J, const rs_precond_params *params, rs_precond **M,
+                   cudaStream_t stream);
+int precond_destroy(rs_precond *M);
+
+/* z = M^{-1} r (Algorithms 1-3 or the black-box V-cycle), FP64 [2N]. */
+int precond_apply(const rs_precond *M, const double *r, double *z, cudaStream_t stream);
+
+/* Right-preconditioned flexible GMRES(m) (Sec. 3, eq. precon-system) for
+ * J x = b, per system of the batch, with classical Gram-Schmidt applied twice
+ * and Givens rotations in FP64. x holds the initial guess on entry. M may be
+ * NULL (no preconditioner). Returns RS_OK when every system converged, else
+ * RS_NOT_CONVERGED. (sync) */
+int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *b, double *x,
+                const rs_gmres_params *params, rs_gmres_stats *stats, cudaStream_t stream);
+
+/* One backward-Euler step by Newton's method (Sec. 3): repeats
+ * assemble -> precond_create -> gmres_solve(J du = -F) -> u += du (S_n
+ * clamped to [0, 1 - S_wr - 1e-12]) until the scaled residual is <= ftol.
+ * u: [2N] in/out. (sync) */
+int newton_step(const rs_problem *probs, int32_t nprob, double *u, const double *u_old, double dt,
+                const rs_newton_params *params, rs_newton_stats *stats, cudaStream_t stream);
+
+/* ------------------------------------------------------- building blocks --- */
+/* y = J x (FP64). */
+int bsr2_spmv(const rs_bsr2 *J, const double *x, double *y, cudaStream_t stream);
+/* r = b - J x (FP64). */
+int bsr2_residual(const rs_bsr2 *J, const double *x, const double *b, double *r,
+                  cudaStream_t stream);
+
+/* ------------------------------------------------------ introspection --- */
+/* Number of levels of a hierarchy, and level l's size and stored entries
+ * (host outputs; sync). */
+int amg_levels(const rs_amg *H, int32_t *nlevels);
+int amg_level_info(const rs_amg *H, int32_t l, int32_t *n, int32_t *nnz, int32_t *nnz_p,
+                   int32_t *ncolours);
+/* Copies of level l (device outputs, any may be NULL): A_l in CSR, the C/F
+ * marks of level l (1 C, -1 F, int8 [n]), P_l in CSR (n x n_{l+1}),
+ * colours int32 [n]. */
+int amg_level_copy(const rs_amg *H, int32_t l, int32_t *a_row_ptr, int32_t *a_col, double *a_val,
+                   int8_t *cf, int32_t *p_row_ptr, int32_t *p_col, double *p_val, int32_t *colour,
+                   cudaStream_t stream);
+/* Hierarchy inside a preconditioner: which = 0 pressure / Schur / black-box,
+ * 1 saturation. NULL if absent. */
+const rs_amg *precond_amg(const rs_precond *M, int32_t which);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

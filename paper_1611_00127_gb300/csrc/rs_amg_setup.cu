@@ -1,0 +1,833 @@
+// On-device classical AMG setup (Sec. 3.2; solver settings of Sec. 4), FP64,
+// compiled without fused multiply-add so that every floating-point decision
+// (strength threshold, interpolation weights feeding the next level's
+// strength) matches the CPU check bit for bit.
+//
+//  strength   : with s_i = sign of a_ii (+1 for 0), j != i is strong for i iff
+//               -s_i a_ij >= theta * max_{k != i}(-s_i a_ik) and that max > 0;
+//               with num_functions > 1 on the finest level only couplings
+//               between unknowns of the same kind (i mod nf == j mod nf) count.
+//  coarsening : PMIS (De Sterck, Yang, Heys 2006) in place of the paper's
+//               CLJP. key_i = (|S^T_i| << 24) | (SplitMix64 bits >> 40); i
+//               beats j iff key_i > key_j or (equal and i < j). Points nobody
+//               depends on start as F. Each round an undecided point beating
+//               all undecided neighbours in S u S^T becomes C, then undecided
+//               points strongly depending on a C point become F.
+//  random bits: SplitMix64 (Steele, Lea, Flood 2014), c-th output for seed s =
+//               mix(s + (c+1) 0x9E3779B97F4A7C15); counter ((2l) << 32) + i
+//               for PMIS and ((2l+1) << 32) + i for colouring, i the row's
+//               index within its own system, so a batch member coarsens
+//               exactly as it would alone.
+//  interp.    : extended+i (De Sterck, Falgout, Nolting, Yang 2008) or classical
+//               Ruge-Stueben; see k_interp_ext / k_interp_classical.
+//  Galerkin   : A_c = P^T (A P) by the ordered sparse products.
+//  colouring  : Jones-Plassmann on the symmetrised pattern, lowest free colour.
+//  stopping   : per system: at or below coarse_n rows, at max_levels, or when
+//               a coarsening keeps more than 0.9 n (or no) points; that system
+//               is then solved there by a dense FP64 inverse.
+#include <algorithm>
+
+#include "rs_internal.cuh"
+
+namespace rs {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t counter) {
+  uint64_t z = seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ bool beats(uint64_t ki, int32_t i, uint64_t kj, int32_t j) {
+  return ki > kj || (ki == kj && i < j);
+}
+
+__global__ void k_diag(int32_t n, const int32_t *rp, const int32_t *col, const double *val, double *d) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = 0.0;
+  for (int32_t k = rp[i]; k < rp[i + 1]; k++)
+    if (col[k] == i) { v = val[k]; break; }
+  d[i] = v;
+}
+
+// rows of systems that do not coarsen at this level get no strong entries
+__global__ void k_strength(int32_t n, const int32_t *rp, const int32_t *col, const double *val, const double *diag,
+                           const int32_t *seg, const uint8_t *seg_act, double theta, int32_t nfun,
+                           uint8_t *strong) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t s = rp[i], e = rp[i + 1];
+  if (!seg_act[seg[i]]) {
+    for (int32_t k = s; k < e; k++) strong[k] = 0;
+    return;
+  }
+  const double sg = diag[i] < 0.0 ? -1.0 : 1.0;
+  double mx = 0.0;
+  for (int32_t k = s; k < e; k++) {
+    const int32_t j = col[k];
+    if (j == i || (j % nfun) != (i % nfun)) continue;
+    const double v = -(sg * val[k]);
+    if (v > mx) mx = v;
+  }
+  const double thr = theta * mx;
+  for (int32_t k = s; k < e; k++) {
+    const int32_t j = col[k];
+    uint8_t st = 0;
+    if (j != i && (j % nfun) == (i % nfun) && mx > 0.0) st = (-(sg * val[k]) >= thr) ? 1 : 0;
+    strong[k] = st;
+  }
+}
+
+__global__ void k_lambda(int32_t n, const int32_t *rp, const int32_t *col, const uint8_t *strong, int32_t *lam) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int32_t k = rp[i]; k < rp[i + 1]; k++)
+    if (strong[k]) atomicAdd(&lam[col[k]], 1);
+}
+
+// cf: 0 undecided, 1 C, -1 F
+__global__ void k_pmis_init(int32_t n, const int32_t *lam, const int32_t *seg, const int32_t *seg_off,
+                            const uint8_t *seg_act, uint64_t seed, int32_t level, uint64_t *key, int8_t *cf) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t sg = seg[i];
+  const uint64_t local = (uint64_t)(i - seg_off[sg]);
+  const uint64_t r = splitmix64(seed, ((uint64_t)(2 * level) << 32) + local);
+  key[i] = ((uint64_t)lam[i] << 24) | (r >> 40);
+  cf[i] = (seg_act[sg] && lam[i] > 0) ? 0 : -1;
+}
+
+// every strong edge between two undecided points marks its loser
+__global__ void k_pmis_losers(int32_t n, const int32_t *rp, const int32_t *col, const uint8_t *strong,
+                              const uint64_t *key, const int8_t *cf, uint8_t *notmax) {
+  int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || cf[j] != 0) return;
+  const uint64_t kj = key[j];
+  for (int32_t q = rp[j]; q < rp[j + 1]; q++) {
+    if (!strong[q]) continue;
+    const int32_t k = col[q];
+    if (cf[k] != 0) continue;
+    if (beats(kj, j, key[k], k)) notmax[k] = 1;
+    else notmax[j] = 1;
+  }
+}
+
+__global__ void k_pmis_select(int32_t n, const uint8_t *notmax, int8_t *cf) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && cf[i] == 0 && !notmax[i]) cf[i] = 1;
+}
+
+// undecided points strongly depending on a C point become F; count the rest
+__global__ void k_pmis_fmark(int32_t n, const int32_t *rp, const int32_t *col, const uint8_t *strong, int8_t *cf,
+                             int32_t *left) {
+  int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || cf[j] != 0) return;
+  for (int32_t q = rp[j]; q < rp[j + 1]; q++)
+    if (strong[q] && cf[col[q]] == 1) {
+      cf[j] = -1;
+      return;
+    }
+  atomicAdd(left, 1);
+}
+
+__global__ void k_seg_count_c(int32_t n, const int8_t *cf, const int32_t *seg, int32_t *cnt) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && cf[i] == 1) atomicAdd(&cnt[seg[i]], 1);
+}
+
+// systems that stop here lose their C points; C flags for the numbering
+__global__ void k_seg_revert(int32_t n, int8_t *cf, const int32_t *seg, const uint8_t *seg_act, int32_t *isc) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (!seg_act[seg[i]]) cf[i] = -1;
+  isc[i] = cf[i] == 1 ? 1 : 0;
+}
+
+__global__ void k_gather_offsets(int32_t m, const int32_t *at, const int32_t *v, int32_t *out) {
+  int32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < m) out[q] = v[at[q]];
+}
+
+// ------------------------------------------------------------------ interpolation
+constexpr int kMaxChat = 96;
+
+__device__ __forceinline__ int find_sorted(const int32_t *a, int m, int32_t v) {
+  int lo = 0, hi = m - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int32_t x = a[mid];
+    if (x == v) return mid;
+    if (x < v) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ bool insert_sorted(int32_t *a, int &m, int32_t v) {
+  int p = m;
+  while (p > 0 && a[p - 1] > v) p--;
+  if (p > 0 && a[p - 1] == v) return true;
+  if (m >= kMaxChat) return false;
+  for (int q = m; q > p; q--) a[q] = a[q - 1];
+  a[p] = v;
+  m++;
+  return true;
+}
+
+struct Acc {
+  double v;
+  bool set;
+  __device__ __forceinline__ void add(double x) {
+    if (!set) { v = x; set = true; } else v = v + x;
+  }
+};
+
+// Extended+i weights for F row i (see the CPU check for the same wording):
+//   Chat_i = strong C neighbours of i and of its strong F neighbours;
+//   pass A over row i (ascending): a_ii, weak a_ij outside Chat_i, and strong F
+//   a_ik with d_k = 0 go to dtil; a_ij with j in Chat_i start num_j;
+//   pass B over the strong F neighbours k (ascending) with d_k != 0:
+//   t = a_ik / d_k, then over row k (ascending, opposite sign to a_kk only)
+//   t * a_kl goes to num_l (l in Chat_i) or dtil (l = i);
+//   w_ij = -(num_j / dtil) for the num_j that were set; dtil = 0: empty row.
+// WRITE = false returns the row length only.
+template <bool WRITE>
+__global__ void k_interp_ext(int32_t n, const int32_t *rp, const int32_t *col, const double *val, const double *diag,
+                             const uint8_t *strong, const int8_t *cf, const int32_t *cidx, int32_t *prp,
+                             int32_t *pcol, double *pval, int32_t *err) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (cf[i] == 1) {
+    if (WRITE) { pcol[prp[i]] = cidx[i]; pval[prp[i]] = 1.0; }
+    else prp[i] = 1;
+    return;
+  }
+  int32_t chat[kMaxChat];
+  double num[kMaxChat];
+  bool nset[kMaxChat];
+  int m = 0;
+  bool ok = true;
+  const int32_t s = rp[i], e = rp[i + 1];
+  for (int32_t q = s; q < e && ok; q++) {
+    const int32_t j = col[q];
+    if (j == i || !strong[q]) continue;
+    if (cf[j] == 1) ok = insert_sorted(chat, m, j);
+    else
+      for (int32_t t = rp[j]; t < rp[j + 1] && ok; t++) {
+        const int32_t l = col[t];
+        if (l != j && strong[t] && cf[l] == 1) ok = insert_sorted(chat, m, l);
+      }
+  }
+  if (!ok) { atomicExch(err, 1); if (!WRITE) prp[i] = 0; return; }
+  if (m == 0) { if (!WRITE) prp[i] = 0; return; }
+  for (int q = 0; q < m; q++) { nset[q] = false; num[q] = 0.0; }
+  Acc dt{0.0, false};
+  // pass A
+  for (int32_t q = s; q < e; q++) {
+    const int32_t j = col[q];
+    const double a = val[q];
+    if (j == i) { dt.add(a); continue; }
+    const int mj = find_sorted(chat, m, j);
+    if (mj >= 0) { num[mj] = a; nset[mj] = true; continue; }
+    if (strong[q] && cf[j] != 1) {
+      const double sk = diag[j] < 0.0 ? -1.0 : 1.0;
+      Acc d{0.0, false};
+      for (int32_t t = rp[j]; t < rp[j + 1]; t++) {
+        const int32_t l = col[t];
+        if (l == j || !(l == i || find_sorted(chat, m, l) >= 0)) continue;
+        const double av = val[t];
+        if (!(sk * av < 0.0)) continue;
+        d.add(av);
+      }
+      if (d.v == 0.0) dt.add(a);
+      continue;
+    }
+    dt.add(a);
+  }
+  // pass B
+  for (int32_t q = s; q < e; q++) {
+    const int32_t k = col[q];
+    if (k == i || !strong[q] || cf[k] == 1) continue;
+    const double sk = diag[k] < 0.0 ? -1.0 : 1.0;
+    Acc d{0.0, false};
+    for (int32_t t = rp[k]; t < rp[k + 1]; t++) {
+      const int32_t l = col[t];
+      if (l == k || !(l == i || find_sorted(chat, m, l) >= 0)) continue;
+      const double av = val[t];
+      if (!(sk * av < 0.0)) continue;
+      d.add(av);
+    }
+    if (d.v == 0.0) continue;
+    const double tq = val[q] / d.v;
+    for (int32_t t = rp[k]; t < rp[k + 1]; t++) {
+      const int32_t l = col[t];
+      if (l == k) continue;
+      const int ml = l == i ? -2 : find_sorted(chat, m, l);
+      if (ml == -1) continue;
+      const double av = val[t];
+      if (!(sk * av < 0.0)) continue;
+      const double pr = tq * av;
+      if (ml == -2) dt.add(pr);
+      else if (!nset[ml]) { num[ml] = pr; nset[ml] = true; }
+      else num[ml] = num[ml] + pr;
+    }
+  }
+  int32_t cnt = 0;
+  const int32_t base = WRITE ? prp[i] : 0;
+  if (dt.v != 0.0) {
+    for (int q = 0; q < m; q++) {
+      if (!nset[q]) continue;
+      if (WRITE) { pcol[base + cnt] = cidx[chat[q]]; pval[base + cnt] = -(num[q] / dt.v); }
+      cnt++;
+    }
+  }
+  if (!WRITE) prp[i] = cnt;
+}
+
+// Classical Ruge-Stueben weights (C_i = strong C neighbours, distribution of
+// strong F neighbours m through C_i with entries of sign opposite to a_mm; a
+// strong F neighbour sharing no such entry, and weak neighbours, go to the
+// diagonal). Same accumulation order rules as above.
+template <bool WRITE>
+__global__ void k_interp_classical(int32_t n, const int32_t *rp, const int32_t *col, const double *val,
+                                   const double *diag, const uint8_t *strong, const int8_t *cf,
+                                   const int32_t *cidx, int32_t *prp, int32_t *pcol, double *pval, int32_t *err) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (cf[i] == 1) {
+    if (WRITE) { pcol[prp[i]] = cidx[i]; pval[prp[i]] = 1.0; }
+    else prp[i] = 1;
+    return;
+  }
+  int32_t ci[kMaxChat];
+  double num[kMaxChat];
+  int m = 0;
+  const int32_t s = rp[i], e = rp[i + 1];
+  for (int32_t q = s; q < e; q++)
+    if (strong[q] && col[q] != i && cf[col[q]] == 1) {
+      if (m >= kMaxChat) { atomicExch(err, 1); if (!WRITE) prp[i] = 0; return; }
+      ci[m++] = col[q];
+    }
+  if (m == 0) { if (!WRITE) prp[i] = 0; return; }
+  Acc dt{0.0, false};
+  for (int32_t q = s; q < e; q++) {
+    const int32_t j = col[q];
+    const double a = val[q];
+    if (j == i || !strong[q]) { dt.add(a); continue; }
+    if (cf[j] == 1) { num[find_sorted(ci, m, j)] = a; continue; }
+    const double sm = diag[j] < 0.0 ? -1.0 : 1.0;
+    Acc d{0.0, false};
+    for (int32_t t = rp[j]; t < rp[j + 1]; t++) {
+      const int32_t kk = col[t];
+      if (kk == j || find_sorted(ci, m, kk) < 0) continue;
+      const double av = val[t];
+      if (!(sm * av < 0.0)) continue;
+      d.add(av);
+    }
+    if (d.v == 0.0) dt.add(a);
+  }
+  for (int32_t q = s; q < e; q++) {
+    const int32_t mm = col[q];
+    if (mm == i || !strong[q] || cf[mm] == 1) continue;
+    const double sm = diag[mm] < 0.0 ? -1.0 : 1.0;
+    Acc d{0.0, false};
+    for (int32_t t = rp[mm]; t < rp[mm + 1]; t++) {
+      const int32_t kk = col[t];
+      if (kk == mm || find_sorted(ci, m, kk) < 0) continue;
+      const double av = val[t];
+      if (!(sm * av < 0.0)) continue;
+      d.add(av);
+    }
+    if (d.v == 0.0) continue;
+    const double tq = val[q] / d.v;
+    for (int32_t t = rp[mm]; t < rp[mm + 1]; t++) {
+      const int32_t kk = col[t];
+      if (kk == mm) continue;
+      const int mk = find_sorted(ci, m, kk);
+      if (mk < 0) continue;
+      const double av = val[t];
+      if (!(sm * av < 0.0)) continue;
+      num[mk] = num[mk] + tq * av;
+    }
+  }
+  if (dt.v == 0.0) { if (!WRITE) prp[i] = 0; return; }
+  if (WRITE)
+    for (int q = 0; q < m; q++) { pcol[prp[i] + q] = cidx[ci[q]]; pval[prp[i] + q] = -(num[q] / dt.v); }
+  else prp[i] = m;
+}
+
+// ------------------------------------------------------------------ colouring
+constexpr int kColourWords = 4;   // up to 256 colours
+
+__global__ void k_jp_init(int32_t n, const int32_t *seg, const int32_t *seg_off, const uint8_t *seg_smooth,
+                          uint64_t seed, int32_t level, uint64_t *key, int32_t *colour) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t sg = seg[i];
+  key[i] = splitmix64(seed, ((uint64_t)(2 * level + 1) << 32) + (uint64_t)(i - seg_off[sg]));
+  colour[i] = seg_smooth[sg] ? -1 : -2;     // -2: not coloured at this level
+}
+
+__global__ void k_jp_losers(int32_t n, const int32_t *rp, const int32_t *col, const uint64_t *key,
+                            const int32_t *colour, uint8_t *notmax) {
+  int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || colour[j] != -1) return;
+  const uint64_t kj = key[j];
+  for (int32_t q = rp[j]; q < rp[j + 1]; q++) {
+    const int32_t k = col[q];
+    if (k == j || colour[k] != -1) continue;
+    if (beats(kj, j, key[k], k)) notmax[k] = 1;
+    else notmax[j] = 1;
+  }
+}
+
+// forbidden colours of the selected points, from coloured neighbours in both directions
+__global__ void k_jp_forbid(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *colour,
+                            const uint8_t *notmax, unsigned long long *mask) {
+  int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int32_t cj = colour[j];
+  const bool sel_j = cj == -1 && !notmax[j];
+  for (int32_t q = rp[j]; q < rp[j + 1]; q++) {
+    const int32_t k = col[q];
+    if (k == j) continue;
+    const int32_t ck = colour[k];
+    if (sel_j && ck >= 0) atomicOr(&mask[(int64_t)j * kColourWords + (ck >> 6)], 1ull << (ck & 63));
+    if (cj >= 0 && ck == -1 && !notmax[k]) atomicOr(&mask[(int64_t)k * kColourWords + (cj >> 6)], 1ull << (cj & 63));
+  }
+}
+
+__global__ void k_jp_assign(int32_t n, const uint8_t *notmax, const unsigned long long *mask, int32_t *colour,
+                            int32_t *left, int32_t *maxc, int32_t *err) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || colour[i] != -1) return;
+  if (notmax[i]) { atomicAdd(left, 1); return; }
+  int c = -1;
+  for (int w = 0; w < kColourWords && c < 0; w++) {
+    const unsigned long long fm = ~mask[(int64_t)i * kColourWords + w];
+    if (fm) c = 64 * w + __ffsll((long long)fm) - 1;
+  }
+  if (c < 0) { atomicExch(err, 1); c = 0; }
+  colour[i] = c;
+  atomicMax(maxc, c + 1);
+}
+
+__global__ void k_colour_count(int32_t n, const int32_t *colour, int32_t *cnt) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && colour[i] >= 0) atomicAdd(&cnt[colour[i]], 1);
+}
+
+__global__ void k_colour_fill(int32_t n, const int32_t *colour, int32_t *fill, int32_t *rows) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && colour[i] >= 0) rows[atomicAdd(&fill[colour[i]], 1)] = i;
+}
+
+__global__ void k_sort_ints(int32_t nlists, const int32_t *off, int32_t *v) {
+  // one thread per colour list: the lists are sorted so that sweeps read rows in order
+  int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nlists) return;
+  // simple shell sort
+  const int32_t s = off[c], len = off[c + 1] - off[c];
+  int32_t *a = v + s;
+  for (int32_t gap = len / 2; gap > 0; gap /= 2)
+    for (int32_t i = gap; i < len; i++) {
+      const int32_t t = a[i];
+      int32_t j = i;
+      for (; j >= gap && a[j - gap] > t; j -= gap) a[j] = a[j - gap];
+      a[j] = t;
+    }
+}
+
+// inverse diagonal (GS) or inverse l1 row weight (Jacobi), FP64 and FP32
+__global__ void k_smoother_diag(int32_t n, const int32_t *rp, const int32_t *col, const double *val, int32_t l1,
+                                double *dinv, float *dinvf) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = 0.0, off = 0.0;
+  for (int32_t k = rp[i]; k < rp[i + 1]; k++) {
+    if (col[k] == i) d = val[k];
+    else off += fabs(val[k]);
+  }
+  if (l1) d = d < 0.0 ? d - off : d + off;
+  const double inv = d != 0.0 ? 1.0 / d : 0.0;
+  dinv[i] = inv;
+  dinvf[i] = (float)inv;
+}
+
+__global__ void k_to_f32(int64_t n, const double *a, float *b) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// ------------------------------------------------------------------ coarse inverse
+// Gauss-Jordan with partial pivoting (largest |a|, first on ties), one CTA per
+// system, dense FP64 in global scratch: [A | I] -> [I | A^{-1}].
+__global__ void k_coarse_dense(const int32_t *rp, const int32_t *col, const double *val, const int4 *info,
+                               const int64_t *inv_off, double *work, double *inv) {
+  const int4 in = info[blockIdx.x];
+  const int32_t r0 = in.x, n = in.y;
+  const int64_t off = inv_off[blockIdx.x];
+  double *a = work + 2 * off;   // n x n matrix followed by n x n identity, row-major each
+  double *b = a + (int64_t)n * n;
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) { a[t] = 0.0; b[t] = 0.0; }
+  __syncthreads();
+  for (int32_t r = threadIdx.x; r < n; r += blockDim.x) {
+    for (int32_t k = rp[r0 + r]; k < rp[r0 + r + 1]; k++) {
+      const int32_t c = col[k] - r0;
+      if (c >= 0 && c < n) a[(int64_t)r * n + c] = val[k];
+    }
+    b[(int64_t)r * n + r] = 1.0;
+  }
+  __syncthreads();
+  __shared__ int32_t piv;
+  __shared__ double red_v[256];
+  __shared__ int32_t red_i[256];
+  for (int32_t k = 0; k < n; k++) {
+    // pivot search
+    double best = -1.0;
+    int32_t bi = k;
+    for (int32_t r = k + threadIdx.x; r < n; r += blockDim.x) {
+      const double v = fabs(a[(int64_t)r * n + k]);
+      if (v > best) { best = v; bi = r; }
+    }
+    red_v[threadIdx.x] = best;
+    red_i[threadIdx.x] = bi;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bv = -1.0;
+      int32_t bix = k;
+      for (int t = 0; t < (int)blockDim.x; t++)
+        if (red_v[t] > bv || (red_v[t] == bv && red_i[t] < bix)) { bv = red_v[t]; bix = red_i[t]; }
+      piv = bix;
+    }
+    __syncthreads();
+    const int32_t p = piv;
+    if (p != k)
+      for (int32_t c = threadIdx.x; c < n; c += blockDim.x) {
+        double t = a[(int64_t)k * n + c]; a[(int64_t)k * n + c] = a[(int64_t)p * n + c]; a[(int64_t)p * n + c] = t;
+        t = b[(int64_t)k * n + c]; b[(int64_t)k * n + c] = b[(int64_t)p * n + c]; b[(int64_t)p * n + c] = t;
+      }
+    __syncthreads();
+    const double d = a[(int64_t)k * n + k];
+    const double dinv = d != 0.0 ? 1.0 / d : 0.0;
+    __syncthreads();
+    for (int32_t c = threadIdx.x; c < n; c += blockDim.x) {
+      a[(int64_t)k * n + c] *= dinv;
+      b[(int64_t)k * n + c] *= dinv;
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
+      const int32_t r = (int32_t)(t / n), c = (int32_t)(t % n);
+      if (r == k) continue;
+      const double f = a[(int64_t)r * n + k];
+      if (c != k) a[t] -= f * a[(int64_t)k * n + c];
+      b[t] -= f * b[(int64_t)k * n + c];
+    }
+    __syncthreads();
+    for (int32_t r = threadIdx.x; r < n; r += blockDim.x)
+      if (r != k) a[(int64_t)r * n + k] = 0.0;
+    __syncthreads();
+  }
+  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) inv[off + t] = b[t];
+}
+
+// ------------------------------------------------------------------ driver
+static int sync_copy(void *h, const void *d, size_t bytes, cudaStream_t s) {
+  RS_CHECK_CUDA(cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, s));
+  RS_CHECK_CUDA(cudaStreamSynchronize(s));
+  return 0;
+}
+
+template <typename T>
+static int upload(T **d, const std::vector<T> &h, cudaStream_t s) {
+  RS_TRY(dalloc_n(d, h.size() + 1, s));
+  if (!h.empty()) RS_CHECK_CUDA(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return 0;
+}
+
+static int colour_level(Level &L, const int32_t *seg, const int32_t *dseg_off, const std::vector<uint8_t> &smooth_seg,
+                        uint64_t seed, int32_t level, cudaStream_t s) {
+  const int32_t n = L.A.n;
+  const int32_t nseg = (int32_t)smooth_seg.size();
+  Scratch sc(s);
+  uint64_t *key = nullptr;
+  uint8_t *notmax = nullptr, *dsm = nullptr;
+  unsigned long long *mask = nullptr;
+  int32_t *cnt3 = nullptr;   // left, maxc, err
+  RS_TRY(sc.get(&key, (size_t)n));
+  RS_TRY(sc.get(&notmax, (size_t)n));
+  RS_TRY(sc.get(&mask, (size_t)n * kColourWords));
+  RS_TRY(sc.get(&cnt3, 3));
+  RS_TRY(dalloc_n(&L.colour, (size_t)n, s));
+  std::vector<uint8_t> sm(smooth_seg);
+  RS_TRY(sc.get(&dsm, (size_t)nseg));
+  RS_CHECK_CUDA(cudaMemcpyAsync(dsm, sm.data(), nseg, cudaMemcpyHostToDevice, s));
+  RS_CHECK_CUDA(cudaMemsetAsync(cnt3, 0, 3 * sizeof(int32_t), s));
+  k_jp_init<<<grid_for(n), kBlock, 0, s>>>(n, seg, dseg_off, dsm, seed, level, key, L.colour);
+  int32_t h3[3] = {1, 0, 0};
+  for (int round = 0; round < 100000 && h3[0] > 0; round++) {
+    RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)n, s));
+    RS_CHECK_CUDA(cudaMemsetAsync(mask, 0, sizeof(unsigned long long) * (size_t)n * kColourWords, s));
+    RS_CHECK_CUDA(cudaMemsetAsync(cnt3, 0, sizeof(int32_t), s));
+    k_jp_losers<<<grid_for(n), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, key, L.colour, notmax);
+    k_jp_forbid<<<grid_for(n), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.colour, notmax, mask);
+    k_jp_assign<<<grid_for(n), kBlock, 0, s>>>(n, notmax, mask, L.colour, cnt3, cnt3 + 1, cnt3 + 2);
+    RS_TRY(sync_copy(h3, cnt3, sizeof(h3), s));
+    if (h3[2]) return fail(RS_ESETUP, "more than 256 colours needed on level " + std::to_string(level));
+  }
+  const int32_t nc = h3[1];
+  L.ncolour = nc;
+  int32_t *ccnt = nullptr;
+  RS_TRY(sc.get(&ccnt, (size_t)nc + 1));
+  RS_CHECK_CUDA(cudaMemsetAsync(ccnt, 0, sizeof(int32_t) * ((size_t)nc + 1), s));
+  if (n > 0) k_colour_count<<<grid_for(n), kBlock, 0, s>>>(n, L.colour, ccnt);
+  RS_TRY(exclusive_scan(ccnt, ccnt, nc, s, &L.nsmooth));
+  L.colour_off.resize(nc + 1);
+  RS_TRY(sync_copy(L.colour_off.data(), ccnt, sizeof(int32_t) * (nc + 1), s));
+  RS_TRY(dalloc_n(&L.colour_rows, (size_t)L.nsmooth, s));
+  int32_t *fill = nullptr;
+  RS_TRY(sc.get(&fill, (size_t)nc + 1));
+  RS_CHECK_CUDA(cudaMemcpyAsync(fill, ccnt, sizeof(int32_t) * (nc + 1), cudaMemcpyDeviceToDevice, s));
+  if (n > 0) k_colour_fill<<<grid_for(n), kBlock, 0, s>>>(n, L.colour, fill, L.colour_rows);
+  if (nc > 0) k_sort_ints<<<grid_for(nc, 64), 64, 0, s>>>(nc, ccnt, L.colour_rows);
+  RS_CHECK_CUDA(cudaGetLastError());
+  return 0;
+}
+
+int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg_params &prm, Hier &H,
+              cudaStream_t s) {
+  H.prm = prm;
+  H.precision = prm.precision;
+  H.nseg = (int32_t)seg_off0.size() - 1;
+  H.L.clear();
+  H.L.reserve(33);
+  H.last_level.assign(H.nseg, -1);
+  const int32_t maxl = std::max(1, std::min(prm.max_levels, 32));
+  const int32_t nfun0 = std::max(1, prm.num_functions);
+  // level 0 owns a copy of A
+  H.L.emplace_back();
+  {
+    Level &L0 = H.L[0];
+    L0.A.n = L0.A.m = A0.n;
+    L0.A.nnz = A0.nnz;
+    RS_TRY(dalloc_n(&L0.A.rowptr, (size_t)A0.n + 1, s));
+    RS_TRY(dalloc_n(&L0.A.col, (size_t)A0.nnz, s));
+    RS_TRY(dalloc_n(&L0.A.val, (size_t)A0.nnz, s));
+    RS_CHECK_CUDA(cudaMemcpyAsync(L0.A.rowptr, A0.rowptr, sizeof(int32_t) * ((size_t)A0.n + 1), cudaMemcpyDeviceToDevice, s));
+    RS_CHECK_CUDA(cudaMemcpyAsync(L0.A.col, A0.col, sizeof(int32_t) * (size_t)A0.nnz, cudaMemcpyDeviceToDevice, s));
+    RS_CHECK_CUDA(cudaMemcpyAsync(L0.A.val, A0.val, sizeof(double) * (size_t)A0.nnz, cudaMemcpyDeviceToDevice, s));
+    L0.seg_off = seg_off0;
+  }
+  for (int32_t l = 0;; l++) {
+    Level &L = H.L[l];
+    const int32_t n = L.A.n, nseg = H.nseg;
+    Scratch sc(s);
+    int32_t *seg = nullptr, *dseg_off = nullptr;
+    RS_TRY(seg_ids(L.seg_off, n, &seg, s));
+    sc.ptrs.push_back(seg);
+    RS_TRY(upload(&dseg_off, L.seg_off, s));
+    sc.ptrs.push_back(dseg_off);
+    // which systems still coarsen
+    std::vector<uint8_t> act(nseg, 0);
+    int32_t nact = 0;
+    for (int32_t g = 0; g < nseg; g++) {
+      const int32_t ng = L.seg_off[g + 1] - L.seg_off[g];
+      if (H.last_level[g] >= 0) continue;
+      if (ng > prm.coarse_n && l < maxl - 1) { act[g] = 1; nact++; }
+      else H.last_level[g] = l;
+    }
+    std::vector<uint8_t> smooth_seg(act);   // systems smoothed (not solved) at this level
+    if (nact > 0) {
+      uint8_t *dact = nullptr, *strong = nullptr, *notmax = nullptr;
+      int32_t *lam = nullptr, *left = nullptr, *segc = nullptr, *isc = nullptr, *err = nullptr;
+      uint64_t *key = nullptr;
+      double *diag = nullptr;
+      RS_TRY(sc.get(&dact, (size_t)nseg));
+      RS_TRY(sc.get(&strong, (size_t)L.A.nnz));
+      RS_TRY(sc.get(&notmax, (size_t)n));
+      RS_TRY(sc.get(&lam, (size_t)n));
+      RS_TRY(sc.get(&left, 2));
+      RS_TRY(sc.get(&segc, (size_t)nseg));
+      RS_TRY(sc.get(&isc, (size_t)n + 1));
+      RS_TRY(sc.get(&key, (size_t)n));
+      RS_TRY(sc.get(&diag, (size_t)n));
+      RS_TRY(sc.get(&err, 1));
+      RS_CHECK_CUDA(cudaMemcpyAsync(dact, act.data(), nseg, cudaMemcpyHostToDevice, s));
+      RS_TRY(dalloc_n(&L.cf, (size_t)n, s));
+      const unsigned g = grid_for(n);
+      k_diag<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag);
+      k_strength<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, seg, dact, prm.theta,
+                                      l == 0 ? nfun0 : 1, strong);
+      RS_CHECK_CUDA(cudaMemsetAsync(lam, 0, sizeof(int32_t) * n, s));
+      k_lambda<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, lam);
+      k_pmis_init<<<g, kBlock, 0, s>>>(n, lam, seg, dseg_off, dact, prm.seed, l, key, L.cf);
+      int32_t hleft = 1, rounds = 0;
+      while (hleft > 0) {
+        if (++rounds > 100000) return fail(RS_ESETUP, "PMIS did not finish");
+        // a few rounds between host checks; a round with nothing undecided does nothing
+        for (int r = 0; r < 3; r++) {
+          RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)n, s));
+          RS_CHECK_CUDA(cudaMemsetAsync(left, 0, sizeof(int32_t), s));
+          k_pmis_losers<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, key, L.cf, notmax);
+          k_pmis_select<<<g, kBlock, 0, s>>>(n, notmax, L.cf);
+          k_pmis_fmark<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, L.cf, left);
+        }
+        RS_TRY(sync_copy(&hleft, left, sizeof(int32_t), s));
+      }
+      // per-system C counts; systems that coarsen too little stop here
+      RS_CHECK_CUDA(cudaMemsetAsync(segc, 0, sizeof(int32_t) * nseg, s));
+      k_seg_count_c<<<g, kBlock, 0, s>>>(n, L.cf, seg, segc);
+      std::vector<int32_t> hc(nseg);
+      RS_TRY(sync_copy(hc.data(), segc, sizeof(int32_t) * nseg, s));
+      nact = 0;
+      for (int32_t q = 0; q < nseg; q++) {
+        if (!act[q]) continue;
+        const int32_t ng = L.seg_off[q + 1] - L.seg_off[q];
+        if (hc[q] == 0 || (double)hc[q] > 0.9 * (double)ng) { act[q] = 0; smooth_seg[q] = 0; H.last_level[q] = l; }
+        else nact++;
+      }
+      RS_CHECK_CUDA(cudaMemcpyAsync(dact, act.data(), nseg, cudaMemcpyHostToDevice, s));
+      k_seg_revert<<<g, kBlock, 0, s>>>(n, L.cf, seg, dact, isc);
+      if (nact > 0) {
+        int32_t nc = 0;
+        RS_TRY(exclusive_scan(isc, isc, n, s, &nc));
+        std::vector<int32_t> off_next(nseg + 1);
+        int32_t *offd = nullptr;
+        RS_TRY(sc.get(&offd, (size_t)nseg + 1));
+        k_gather_offsets<<<grid_for(nseg + 1), kBlock, 0, s>>>(nseg + 1, dseg_off, isc, offd);
+        RS_TRY(sync_copy(off_next.data(), offd, sizeof(int32_t) * (nseg + 1), s));
+        // interpolation
+        DCsr &P = L.P;
+        P.n = n;
+        P.m = nc;
+        RS_TRY(dalloc_n(&P.rowptr, (size_t)n + 1, s));
+        RS_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+        if (prm.interp == RS_INTERP_CLASSICAL)
+          k_interp_classical<false><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
+                                                          P.rowptr, nullptr, nullptr, err);
+        else
+          k_interp_ext<false><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
+                                                    P.rowptr, nullptr, nullptr, err);
+        int32_t pnnz = 0;
+        RS_TRY(exclusive_scan(P.rowptr, P.rowptr, n, s, &pnnz));
+        int32_t herr = 0;
+        RS_TRY(sync_copy(&herr, err, sizeof(int32_t), s));
+        if (herr) return fail(RS_ESETUP, "interpolation set too large on level " + std::to_string(l));
+        P.nnz = pnnz;
+        RS_TRY(dalloc_n(&P.col, (size_t)pnnz, s));
+        RS_TRY(dalloc_n(&P.val, (size_t)pnnz, s));
+        if (prm.interp == RS_INTERP_CLASSICAL)
+          k_interp_classical<true><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
+                                                         P.rowptr, P.col, P.val, err);
+        else
+          k_interp_ext<true><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
+                                                   P.rowptr, P.col, P.val, err);
+        RS_CHECK_CUDA(cudaGetLastError());
+        RS_TRY(transpose(P, L.R, s));
+        DCsr AP;
+        RS_TRY(spgemm(L.A, P, AP, s));
+        Level next;
+        int r = spgemm(L.R, AP, next.A, s);
+        dcsr_free(AP, s);
+        if (r) return r;
+        next.seg_off = off_next;
+        H.L.push_back(next);
+      } else {
+        dfree(L.cf, s);
+        L.cf = nullptr;
+      }
+    }
+    Level &Lc = H.L[l];   // (reference may have moved after push_back)
+    // smoother data for the systems smoothed here
+    if (nact > 0 || std::any_of(smooth_seg.begin(), smooth_seg.end(), [](uint8_t v) { return v != 0; })) {
+      RS_TRY(colour_level(Lc, seg, dseg_off, smooth_seg, prm.seed, l, s));
+    }
+    RS_TRY(dalloc_n(&Lc.dinv, (size_t)n, s));
+    RS_TRY(dalloc_n(&Lc.dinvf, (size_t)n, s));
+    if (n > 0)
+      k_smoother_diag<<<grid_for(n), kBlock, 0, s>>>(n, Lc.A.rowptr, Lc.A.col, Lc.A.val,
+                                                     prm.smoother == RS_SMOOTH_L1JACOBI, Lc.dinv, Lc.dinvf);
+    // systems solved directly here
+    int64_t inv_tot = 0;
+    std::vector<int4> info;
+    std::vector<int64_t> ioff;
+    std::vector<int32_t> rows;
+    std::vector<int32_t> rowseg;
+    for (int32_t q = 0; q < nseg; q++) {
+      if (H.last_level[q] != l) continue;
+      const int32_t r0 = Lc.seg_off[q], ng = Lc.seg_off[q + 1] - Lc.seg_off[q];
+      if (ng == 0) continue;
+      if (ng > prm.max_dense)
+        return fail(RS_ESETUP, "coarsest level of system " + std::to_string(q) + " has " + std::to_string(ng) +
+                                   " rows (> max_dense)");
+      Lc.cseg.push_back(q);
+      info.push_back(make_int4(r0, ng, 0, 0));
+      ioff.push_back(inv_tot);
+      for (int32_t t = 0; t < ng; t++) { rows.push_back(r0 + t); rowseg.push_back((int32_t)info.size() - 1); }
+      inv_tot += (int64_t)ng * ng;
+    }
+    if (!info.empty()) {
+      Lc.ncoarse_rows = (int32_t)rows.size();
+      RS_TRY(upload(&Lc.cinfo, info, s));
+      RS_TRY(upload(&Lc.cinv_off, ioff, s));
+      RS_TRY(upload(&Lc.crows, rows, s));
+      RS_TRY(upload(&Lc.crow_seg, rowseg, s));
+      RS_TRY(dalloc_n(&Lc.cinv, (size_t)inv_tot, s));
+      double *work = nullptr;
+      RS_TRY(sc.get(&work, 2 * (size_t)inv_tot));
+      k_coarse_dense<<<(unsigned)info.size(), 256, 0, s>>>(Lc.A.rowptr, Lc.A.col, Lc.A.val, Lc.cinfo, Lc.cinv_off,
+                                                           work, Lc.cinv);
+      RS_CHECK_CUDA(cudaGetLastError());
+    }
+    // FP32 copies for the FP32 cycle
+    if (H.precision == RS_PREC_FP32) {
+      RS_TRY(dalloc_n(&Lc.A.valf, (size_t)Lc.A.nnz, s));
+      if (Lc.A.nnz) k_to_f32<<<grid_for(Lc.A.nnz), kBlock, 0, s>>>(Lc.A.nnz, Lc.A.val, Lc.A.valf);
+      if (Lc.P.rowptr) {
+        RS_TRY(dalloc_n(&Lc.P.valf, (size_t)Lc.P.nnz, s));
+        RS_TRY(dalloc_n(&Lc.R.valf, (size_t)Lc.R.nnz, s));
+        if (Lc.P.nnz) k_to_f32<<<grid_for(Lc.P.nnz), kBlock, 0, s>>>(Lc.P.nnz, Lc.P.val, Lc.P.valf);
+        if (Lc.R.nnz) k_to_f32<<<grid_for(Lc.R.nnz), kBlock, 0, s>>>(Lc.R.nnz, Lc.R.val, Lc.R.valf);
+      }
+    }
+    // work vectors
+    const size_t es = H.precision == RS_PREC_FP32 ? sizeof(float) : sizeof(double);
+    RS_TRY(dalloc(&Lc.x, es * ((size_t)n + 1), s));
+    RS_TRY(dalloc(&Lc.b, es * ((size_t)n + 1), s));
+    RS_TRY(dalloc(&Lc.r, es * ((size_t)n + 1), s));
+    RS_TRY(dalloc(&Lc.t, es * ((size_t)n + 1), s));
+    RS_CHECK_CUDA(cudaGetLastError());
+    if ((int32_t)H.L.size() == l + 1) break;   // no next level
+  }
+  H.nlev = (int32_t)H.L.size();
+  for (int32_t q = 0; q < H.nseg; q++)
+    if (H.last_level[q] < 0) H.last_level[q] = H.nlev - 1;
+  RS_CHECK_CUDA(cudaStreamSynchronize(s));
+  return 0;
+}
+
+void amg_free(Hier &H, cudaStream_t s) {
+  for (Level &L : H.L) {
+    dcsr_free(L.A, s);
+    dcsr_free(L.P, s);
+    dcsr_free(L.R, s);
+    dfree(L.cf, s);
+    dfree(L.colour, s);
+    dfree(L.colour_rows, s);
+    dfree(L.dinv, s);
+    dfree(L.dinvf, s);
+    dfree(L.cinfo, s);
+    dfree(L.cinv_off, s);
+    dfree(L.crows, s);
+    dfree(L.crow_seg, s);
+    dfree(L.cinv, s);
+    dfree(L.x, s);
+    dfree(L.b, s);
+    dfree(L.r, s);
+    dfree(L.t, s);
+  }
+  H.L.clear();
+  H.nlev = 0;
+}
+
+}  // namespace rs

@@ -1,0 +1,330 @@
+// Right-preconditioned flexible GMRES(m) (Sec. 3, eq. precon-system: solve
+// J M^{-1} c^ = q, c = M^{-1} c^; flexible because the AMG preconditioner
+// changes from one application to the next in FP32), FP64, per system of a
+// batch. Orthogonalisation is classical Gram-Schmidt applied twice (CGS2):
+// each pass is one multi-dot kernel (all j+1 inner products against the new
+// vector, which a block keeps in shared memory) plus one update kernel, in
+// place of the paper solver's modified Gram-Schmidt, whose j+1 dependent dot
+// products would each need a grid-wide reduction.
+//
+// Reductions are deterministic: each block reduces a fixed chunk of one
+// system's rows, then one thread per (system, vector) sums the chunk partials
+// in order. Givens rotations, the residual estimate and the convergence test
+// run on the device, one thread per system.
+#include <algorithm>
+#include <cmath>
+
+#include "rs_internal.cuh"
+
+namespace rs {
+int precond_apply_impl(const rs_precond *M, const double *r, double *z, cudaStream_t s);
+}
+using namespace rs;
+
+namespace {
+
+constexpr int kChunk = 2048;   // rows per reduction block
+constexpr int kRedThreads = 256;
+
+struct Chunk {
+  int32_t seg, beg, end;
+};
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kRedThreads / 32; k++) t += sh[k];
+  return t;
+}
+
+// part[c][i] = sum over chunk c of V_i . w, i < nvec  (V_i = V + i*ldv)
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const Chunk *__restrict__ chunks, const double *__restrict__ V,
+                                                          int64_t ldv, int nvec, const double *__restrict__ w,
+                                                          int stride, double *__restrict__ part) {
+  __shared__ double ws[kChunk];
+  __shared__ double sh[kRedThreads / 32];
+  const Chunk ch = chunks[blockIdx.x];
+  const int len = ch.end - ch.beg;
+  for (int t = threadIdx.x; t < len; t += kRedThreads) ws[t] = w[ch.beg + t];
+  __syncthreads();
+  for (int i = 0; i < nvec; i++) {
+    const double *vi = V + i * ldv + ch.beg;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < len; t += kRedThreads) acc = fma(vi[t], ws[t], acc);
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * stride + i] = tot;
+  }
+}
+
+// h[s][i] = sum of the partials of system s (in chunk order). mode 1: out = h
+// and H(i, col) = h; mode 2: out = h and H(i, col) += h; mode 3 (norm):
+// out[s] = sqrt(h). Inactive systems get h = 0.
+__global__ void k_reduce(int32_t nseg, const int32_t *__restrict__ seg_chunk, int nvec, int stride,
+                         const double *__restrict__ part, double *__restrict__ out, double *__restrict__ H,
+                         int ldh_seg, int col, int mode, const uint8_t *__restrict__ active) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nseg * nvec) return;
+  const int32_t s = (int32_t)(t / nvec);
+  const int i = (int)(t % nvec);
+  double acc = 0.0;
+  for (int32_t c = seg_chunk[s]; c < seg_chunk[s + 1]; c++) acc += part[(int64_t)c * stride + i];
+  if (active && !active[s]) acc = 0.0;
+  if (mode == 3) {
+    const double nrm = sqrt(acc);
+    out[s] = nrm;
+    return;
+  }
+  out[(int64_t)s * stride + i] = acc;
+  if (mode == 1) H[(int64_t)s * ldh_seg + (int64_t)i * 64 + col] = acc;
+  else if (mode == 2) H[(int64_t)s * ldh_seg + (int64_t)i * 64 + col] += acc;
+}
+
+// w -= sum_i V_i h[seg][i]
+__global__ void __launch_bounds__(kRedThreads) k_update(const Chunk *__restrict__ chunks, const double *__restrict__ V,
+                                                        int64_t ldv, int nvec, const double *__restrict__ h,
+                                                        int stride, double *__restrict__ w) {
+  const Chunk ch = chunks[blockIdx.x];
+  const double *hs = h + (int64_t)ch.seg * stride;
+  for (int t = ch.beg + threadIdx.x; t < ch.end; t += kRedThreads) {
+    double acc = w[t];
+    for (int i = 0; i < nvec; i++) acc = fma(-V[i * ldv + t], hs[i], acc);
+    w[t] = acc;
+  }
+}
+
+// y = x * f[seg] (0 where f is 0 or not finite)
+__global__ void __launch_bounds__(kRedThreads) k_scale(const Chunk *__restrict__ chunks, const double *__restrict__ nrm,
+                                                       const double *__restrict__ x, double *__restrict__ y) {
+  const Chunk ch = chunks[blockIdx.x];
+  const double d = nrm[ch.seg];
+  const double f = (d > 0.0 && isfinite(d)) ? 1.0 / d : 0.0;
+  for (int t = ch.beg + threadIdx.x; t < ch.end; t += kRedThreads) y[t] = x[t] * f;
+}
+
+// x += sum_{i < k[seg]} y[seg][i] Z_i
+__global__ void __launch_bounds__(kRedThreads) k_xupdate(const Chunk *__restrict__ chunks, const double *__restrict__ Z,
+                                                         int64_t ldz, const double *__restrict__ y, int m,
+                                                         const int32_t *__restrict__ kseg, double *__restrict__ x) {
+  const Chunk ch = chunks[blockIdx.x];
+  const int k = kseg[ch.seg];
+  const double *ys = y + (int64_t)ch.seg * m;
+  for (int t = ch.beg + threadIdx.x; t < ch.end; t += kRedThreads) {
+    double acc = x[t];
+    for (int i = 0; i < k; i++) acc = fma(ys[i], Z[i * ldz + t], acc);
+    x[t] = acc;
+  }
+}
+
+struct SegState {
+  double g[65];
+  double cs[64], sn[64];
+};
+
+// Givens update of column j for every active system; convergence test on the
+// residual estimate |g_{j+1}|.
+__global__ void k_givens(int32_t nseg, int j, int m, double *__restrict__ H, int ldh_seg, const double *__restrict__ hnext,
+                         SegState *__restrict__ st, uint8_t *__restrict__ active, int32_t *__restrict__ kseg,
+                         const double *__restrict__ tol, int32_t *__restrict__ its, int32_t maxit,
+                         int32_t *__restrict__ nactive, uint8_t *__restrict__ bad) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg || !active[s]) return;
+  double *Hs = H + (int64_t)s * ldh_seg;
+  SegState &S = st[s];
+  Hs[(int64_t)(j + 1) * 64 + j] = hnext[s];
+  for (int i = 0; i < j; i++) {
+    const double a = Hs[(int64_t)i * 64 + j], c = Hs[(int64_t)(i + 1) * 64 + j];
+    Hs[(int64_t)i * 64 + j] = S.cs[i] * a + S.sn[i] * c;
+    Hs[(int64_t)(i + 1) * 64 + j] = -S.sn[i] * a + S.cs[i] * c;
+  }
+  const double a = Hs[(int64_t)j * 64 + j], c = Hs[(int64_t)(j + 1) * 64 + j];
+  const double d = sqrt(a * a + c * c);
+  S.cs[j] = d != 0.0 ? a / d : 1.0;
+  S.sn[j] = d != 0.0 ? c / d : 0.0;
+  Hs[(int64_t)j * 64 + j] = d;
+  Hs[(int64_t)(j + 1) * 64 + j] = 0.0;
+  S.g[j + 1] = -S.sn[j] * S.g[j];
+  S.g[j] = S.cs[j] * S.g[j];
+  kseg[s] = j + 1;
+  its[s] += 1;
+  const double est = fabs(S.g[j + 1]);
+  if (!isfinite(est) || !isfinite(d)) {
+    bad[s] = 1;
+    active[s] = 0;
+    kseg[s] = j;   // drop the failed column
+    its[s] -= 1;
+    return;
+  }
+  if (est <= tol[s] || its[s] >= maxit || j + 1 >= m || hnext[s] == 0.0) active[s] = 0;
+  else atomicAdd(nactive, 1);
+}
+
+// back substitution y = R^{-1} g per system
+__global__ void k_backsolve(int32_t nseg, int m, const double *__restrict__ H, int ldh_seg,
+                            const SegState *__restrict__ st, const int32_t *__restrict__ kseg, double *__restrict__ y) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  const int k = kseg[s];
+  const double *Hs = H + (int64_t)s * ldh_seg;
+  double *ys = y + (int64_t)s * m;
+  for (int i = k - 1; i >= 0; i--) {
+    double acc = st[s].g[i];
+    for (int t = i + 1; t < k; t++) acc -= Hs[(int64_t)i * 64 + t] * ys[t];
+    const double d = Hs[(int64_t)i * 64 + i];
+    ys[i] = d != 0.0 ? acc / d : 0.0;
+  }
+}
+
+__global__ void k_cycle_start(int32_t nseg, const double *__restrict__ beta, const double *__restrict__ tol,
+                              const int32_t *__restrict__ its, int32_t maxit, const uint8_t *__restrict__ bad,
+                              uint8_t *__restrict__ active, int32_t *__restrict__ kseg, SegState *__restrict__ st) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nseg) return;
+  const bool go = !bad[s] && beta[s] > tol[s] && its[s] < maxit && isfinite(beta[s]);
+  active[s] = go ? 1 : 0;
+  kseg[s] = 0;
+  st[s].g[0] = go ? beta[s] : 0.0;
+}
+
+}  // namespace
+
+extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *b, double *x,
+                           const rs_gmres_params *params, rs_gmres_stats *stats, cudaStream_t s) {
+  if (!J || !b || !x || !params) return fail(RS_EINVAL, "null argument");
+  if (J->nb < 0 || (J->nb > 0 && (!J->row_ptr || !J->col || !J->val))) return fail(RS_EINVAL, "invalid matrix");
+  const int m = params->m;
+  if (m < 1 || m > 63) return fail(RS_EINVAL, "restart length must be in [1, 63]");
+  if (params->maxit < 0 || !(params->rtol >= 0.0)) return fail(RS_EINVAL, "bad tolerance or iteration limit");
+  const std::vector<int32_t> boff = seg_offsets(J->nb, J->nseg, J->seg_off);
+  if (boff.front() != 0 || boff.back() != J->nb) return fail(RS_EINVAL, "segment offsets must run from 0 to nb");
+  const int32_t nseg = (int32_t)boff.size() - 1;
+  const int64_t n = 2 * (int64_t)J->nb;
+  // chunk table
+  std::vector<Chunk> chunks;
+  std::vector<int32_t> seg_chunk(nseg + 1, 0);
+  for (int32_t q = 0; q < nseg; q++) {
+    seg_chunk[q] = (int32_t)chunks.size();
+    for (int64_t r0 = 2 * (int64_t)boff[q]; r0 < 2 * (int64_t)boff[q + 1]; r0 += kChunk)
+      chunks.push_back({q, (int32_t)r0, (int32_t)std::min<int64_t>(r0 + kChunk, 2 * (int64_t)boff[q + 1])});
+  }
+  seg_chunk[nseg] = (int32_t)chunks.size();
+  const int32_t nch = (int32_t)chunks.size();
+  const int stride = 64;
+  const int ldh = 65 * 64;
+  Scratch sc(s);
+  double *V = nullptr, *Z = nullptr, *H = nullptr, *part = nullptr, *hbuf = nullptr, *nrm = nullptr, *y = nullptr,
+         *tol = nullptr;
+  Chunk *dch = nullptr;
+  int32_t *dsegc = nullptr, *kseg = nullptr, *its = nullptr, *nact = nullptr;
+  uint8_t *active = nullptr, *bad = nullptr;
+  SegState *st = nullptr;
+  RS_TRY(sc.get(&V, (size_t)n * (m + 1) + 1));
+  RS_TRY(sc.get(&Z, (size_t)n * m + 1));
+  RS_TRY(sc.get(&H, (size_t)nseg * ldh));
+  RS_TRY(sc.get(&part, (size_t)std::max(nch, 1) * stride));
+  RS_TRY(sc.get(&hbuf, (size_t)nseg * stride));
+  RS_TRY(sc.get(&nrm, (size_t)nseg));
+  RS_TRY(sc.get(&y, (size_t)nseg * m));
+  RS_TRY(sc.get(&tol, (size_t)nseg));
+  RS_TRY(sc.get(&dch, (size_t)std::max(nch, 1)));
+  RS_TRY(sc.get(&dsegc, (size_t)nseg + 1));
+  RS_TRY(sc.get(&kseg, (size_t)nseg));
+  RS_TRY(sc.get(&its, (size_t)nseg));
+  RS_TRY(sc.get(&nact, 1));
+  RS_TRY(sc.get(&active, (size_t)nseg));
+  RS_TRY(sc.get(&bad, (size_t)nseg));
+  RS_TRY(sc.get(&st, (size_t)nseg));
+  if (nch > 0) RS_CHECK_CUDA(cudaMemcpyAsync(dch, chunks.data(), sizeof(Chunk) * nch, cudaMemcpyHostToDevice, s));
+  RS_CHECK_CUDA(cudaMemcpyAsync(dsegc, seg_chunk.data(), sizeof(int32_t) * (nseg + 1), cudaMemcpyHostToDevice, s));
+  RS_CHECK_CUDA(cudaMemsetAsync(its, 0, sizeof(int32_t) * nseg, s));
+  RS_CHECK_CUDA(cudaMemsetAsync(bad, 0, (size_t)nseg, s));
+  RS_CHECK_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * nseg * ldh, s));
+  const unsigned gseg = grid_for(nseg);
+  auto norms = [&](const double *vec, double *out) -> int {
+    if (nch > 0) k_multidot<<<nch, kRedThreads, 0, s>>>(dch, vec, 0, 1, vec, stride, part);
+    k_reduce<<<gseg, kBlock, 0, s>>>(nseg, dsegc, 1, stride, part, out, nullptr, 0, 0, 3, nullptr);
+    RS_CHECK_CUDA(cudaGetLastError());
+    return 0;
+  };
+  // tolerances from ||b||
+  RS_TRY(norms(b, nrm));
+  std::vector<double> hb(nseg), hbeta(nseg);
+  RS_CHECK_CUDA(cudaMemcpyAsync(hb.data(), nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, s));
+  RS_CHECK_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> htol(nseg);
+  for (int32_t q = 0; q < nseg; q++) htol[q] = params->rtol * (hb[q] > 0.0 ? hb[q] : 1.0);
+  RS_CHECK_CUDA(cudaMemcpyAsync(tol, htol.data(), sizeof(double) * nseg, cudaMemcpyHostToDevice, s));
+  int32_t *hnact = nullptr;
+  RS_CHECK_CUDA(cudaMallocHost(&hnact, sizeof(int32_t)));
+  std::vector<int32_t> hits(nseg, 0);
+  std::vector<uint8_t> hbad(nseg, 0);
+  int rc = RS_OK;
+  for (int cycle = 0;; cycle++) {
+    // true residual
+    rc = launch_bsr2_residual(*J, x, b, V, s);
+    if (rc) break;
+    rc = norms(V, nrm);
+    if (rc) break;
+    RS_CHECK_CUDA(cudaMemcpyAsync(hbeta.data(), nrm, sizeof(double) * nseg, cudaMemcpyDeviceToHost, s));
+    RS_CHECK_CUDA(cudaMemcpyAsync(hits.data(), its, sizeof(int32_t) * nseg, cudaMemcpyDeviceToHost, s));
+    RS_CHECK_CUDA(cudaMemcpyAsync(hbad.data(), bad, (size_t)nseg, cudaMemcpyDeviceToHost, s));
+    RS_CHECK_CUDA(cudaStreamSynchronize(s));
+    bool more = false;
+    for (int32_t q = 0; q < nseg; q++)
+      if (!hbad[q] && std::isfinite(hbeta[q]) && hbeta[q] > htol[q] && hits[q] < params->maxit) more = true;
+    if (!more) break;
+    k_cycle_start<<<gseg, kBlock, 0, s>>>(nseg, nrm, tol, its, params->maxit, bad, active, kseg, st);
+    if (nch > 0) k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, V, V);
+    for (int j = 0; j < m; j++) {
+      double *vj = V + (int64_t)j * n, *zj = Z + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
+      if (M) rc = precond_apply_impl(M, vj, zj, s);
+      else RS_CHECK_CUDA(cudaMemcpyAsync(zj, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      if (rc) break;
+      rc = launch_bsr2_spmv(*J, zj, w, s);
+      if (rc) break;
+      for (int pass = 0; pass < 2; pass++) {
+        if (nch > 0) k_multidot<<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, w, stride, part);
+        k_reduce<<<grid_for((int64_t)nseg * (j + 1)), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part, hbuf, H, ldh,
+                                                                     j, pass == 0 ? 1 : 2, active);
+        if (nch > 0) k_update<<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, hbuf, stride, w);
+      }
+      rc = norms(w, nrm);
+      if (rc) break;
+      if (nch > 0) k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, w, w);
+      RS_CHECK_CUDA(cudaMemsetAsync(nact, 0, sizeof(int32_t), s));
+      k_givens<<<gseg, kBlock, 0, s>>>(nseg, j, m, H, ldh, nrm, st, active, kseg, tol, its, params->maxit, nact, bad);
+      RS_CHECK_CUDA(cudaMemcpyAsync(hnact, nact, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      RS_CHECK_CUDA(cudaStreamSynchronize(s));
+      if (*hnact == 0) break;
+    }
+    if (rc) break;
+    k_backsolve<<<gseg, kBlock, 0, s>>>(nseg, m, H, ldh, st, kseg, y);
+    if (nch > 0) k_xupdate<<<nch, kRedThreads, 0, s>>>(dch, Z, n, y, m, kseg, x);
+    RS_CHECK_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * nseg * ldh, s));
+    RS_CHECK_CUDA(cudaGetLastError());
+  }
+  cudaFreeHost(hnact);
+  if (rc) return rc;
+  int32_t conv = 0, itmax = 0;
+  double rmax = 0.0;
+  for (int32_t q = 0; q < nseg; q++) {
+    const double bn = hb[q] > 0.0 ? hb[q] : 1.0;
+    const double rr = hbeta[q] / bn;
+    if (!hbad[q] && rr <= params->rtol) conv++;
+    if (!(rr <= rmax)) rmax = rr;
+    itmax = std::max(itmax, hits[q]);
+    if (stats && stats->its) stats->its[q] = hits[q];
+    if (stats && stats->relres_seg) stats->relres_seg[q] = rr;
+  }
+  if (stats) {
+    stats->iterations = itmax;
+    stats->converged = conv;
+    stats->relres = rmax;
+  }
+  return conv == nseg ? RS_OK : RS_NOT_CONVERGED;
+}

@@ -1,0 +1,141 @@
+// Internal declarations shared by the rsflow CUDA translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rsflow.h"
+
+namespace rs {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+#define RS_CHECK_CUDA(expr)                                                         \
+  do {                                                                              \
+    cudaError_t e__ = (expr);                                                       \
+    if (e__ != cudaSuccess)                                                         \
+      return ::rs::fail(RS_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e__)); \
+  } while (0)
+
+#define RS_TRY(expr)              \
+  do {                            \
+    int r__ = (expr);             \
+    if (r__ < 0) return r__;      \
+  } while (0)
+
+// ------------------------------------------------------------------ memory
+// Stream-ordered allocations from the device's default memory pool (kept
+// resident between calls), freed with dfree (stream-ordered) or dfree_sync.
+int dalloc(void **p, size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+template <typename T>
+inline int dalloc_n(T **p, size_t n, cudaStream_t s) {
+  return dalloc(reinterpret_cast<void **>(p), n * sizeof(T) + 16, s);
+}
+
+// Scratch list freed together at scope end (stream-ordered).
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void *> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  template <typename T>
+  int get(T **p, size_t n) {
+    int r = dalloc_n(p, n, s);
+    if (r == 0) ptrs.push_back(*p);
+    return r;
+  }
+  ~Scratch() {
+    for (void *p : ptrs) dfree(p, s);
+  }
+};
+
+// ------------------------------------------------------------------ launch
+constexpr int kBlock = 256;
+inline unsigned grid_for(int64_t n, int per_block = kBlock) {
+  int64_t g = (n + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > 0x7fffffff) g = 0x7fffffff;
+  return (unsigned)g;
+}
+int num_sms();
+
+// exclusive scan: out[i] = sum_{k<i} in[i], out[n] = total; in == out allowed.
+// `total` (host, optional) receives the total after a stream sync.
+int exclusive_scan(const int32_t *in, int32_t *out, int32_t n, cudaStream_t s, int32_t *total);
+
+// ------------------------------------------------------------------ matrices
+struct DCsr {
+  int32_t n = 0, m = 0, nnz = 0;
+  int32_t *rowptr = nullptr, *col = nullptr;
+  double *val = nullptr;  // FP64 values (setup and FP64 cycles)
+  float *valf = nullptr;  // FP32 copy (FP32 cycles)
+};
+void dcsr_free(DCsr &A, cudaStream_t s);
+
+// ------------------------------------------------------------------ kernels shared across files
+// y = J x, r = b - J x (bsr2, FP64)
+int launch_bsr2_spmv(const rs_bsr2 &J, const double *x, double *y, cudaStream_t s);
+int launch_bsr2_residual(const rs_bsr2 &J, const double *x, const double *b, double *r,
+                         cudaStream_t s);
+
+// Block extraction and derived matrices (setup; exact operation order).
+int bsr2_part(const rs_bsr2 &J, int r, int c, DCsr &out, cudaStream_t s);
+int bsr2_scalar(const rs_bsr2 &J, DCsr &out, cudaStream_t s);
+int simple_schur(const DCsr &App, const DCsr &Aps, const DCsr &Asp, const DCsr &Ass, DCsr &out,
+                 cudaStream_t s);
+int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s);
+int transpose(const DCsr &A, DCsr &T, cudaStream_t s);
+
+// ------------------------------------------------------------------ AMG
+struct Level {
+  DCsr A, P, R;
+  int8_t *cf = nullptr;          // C/F marks (1 C, -1 F) of this level (nullptr on the last)
+  int32_t *colour = nullptr;     // colour per row (-1: not smoothed here)
+  int32_t ncolour = 0;
+  std::vector<int32_t> colour_off;   // host [ncolour+1] into colour_rows
+  int32_t *colour_rows = nullptr;    // rows grouped by colour
+  int32_t nsmooth = 0;               // rows smoothed at this level
+  double *dinv = nullptr;            // 1 / a_ii (GS) or 1 / l1 row norm (Jacobi)
+  float *dinvf = nullptr;
+  std::vector<int32_t> seg_off;      // host [nseg+1]
+  // coarse solve of the systems whose last level is this one
+  std::vector<int32_t> cseg;         // systems solved here
+  int32_t ncoarse_rows = 0;
+  int32_t *crow_seg = nullptr;       // per coarse row: index into cinfo
+  int4 *cinfo = nullptr;             // per solved system: (row0, n, inverse offset (in doubles, low), hi)
+  int64_t *cinv_off = nullptr;
+  int32_t *crows = nullptr;          // the rows solved directly
+  double *cinv = nullptr;            // stacked dense inverses, row-major
+  // work vectors (FP32 or FP64 by the hierarchy's precision)
+  void *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+};
+
+struct Hier {
+  rs_amg_params prm;
+  int32_t nlev = 0;
+  int32_t nseg = 1;
+  std::vector<Level> L;
+  std::vector<int32_t> last_level;   // per system
+  int precision = RS_PREC_FP32;
+};
+
+int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off, const rs_amg_params &prm,
+              Hier &H, cudaStream_t s);
+void amg_free(Hier &H, cudaStream_t s);
+// x = V-cycle(b); FP64 in/out. `xin_zero` is always true here (zero guess).
+int amg_vcycle(const Hier &H, const double *b, double *x, cudaStream_t s);
+
+// ------------------------------------------------------------------ helpers
+std::vector<int32_t> seg_offsets(int32_t n, int32_t nseg, const int32_t *seg_off);
+int seg_ids(const std::vector<int32_t> &seg_off, int32_t n, int32_t **dseg, cudaStream_t s);
+
+}  // namespace rs
+
+struct rs_amg {
+  rs::Hier H;
+  cudaStream_t stream;
+};

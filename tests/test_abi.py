@@ -1,0 +1,56 @@
+"""The C-ABI library builds, loads and exports every function include/rsflow.h
+declares (no GPU work)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "rsflow.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", txt, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "sizeof")))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1611_00127_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert len(names) >= 18, names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_string_without_gpu():
+    from paper_1611_00127_gb300 import rsflow as R
+    L = R.lib()
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert L.rs_version(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == 0
+    assert c.value == 103
+    assert isinstance(L.rs_last_error(), bytes)
+
+
+def test_nnzb_host_count_matches_oracle_pattern(oracle, inputs):
+    """rs_bsr2_nnzb is pure host arithmetic: compare with the oracle pattern."""
+    from paper_1611_00127_gb300 import rsflow as R
+    for p in (inputs.config_small_2d(), inputs.homogeneous(5, 4, nz=3), inputs.homogeneous(1, 7)):
+        arr = (R.Problem * 1)()
+        arr[0] = R.Problem(p.dim, p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, 0, 0, 0, p.phi, p.mu_w, p.mu_n, p.rho_w,
+                           p.rho_n, p.g, p.pc_model, p.pc_p0, p.pc_pd, p.bc_lambda, p.s_wr, p.s_nr, p.u_in,
+                           p.p_out, p.sn_out)
+        rp, col = oracle.bsr2_pattern(p)
+        assert R.lib().rs_bsr2_nnzb(arr, 1) == col.size
+
+
+def test_invalid_arguments_rejected_on_host():
+    """Argument validation happens before any GPU work."""
+    from paper_1611_00127_gb300 import rsflow as R
+    L = R.lib()
+    h = ctypes.c_void_p()
+    assert L.precond_create(None, None, ctypes.byref(h), None) == -1
+    assert L.amg_setup(None, None, ctypes.byref(h), None) == -1
+    assert L.gmres_solve(None, None, None, None, None, None, None) == -1
+    assert b"invalid" in L.rs_last_error() or b"null" in L.rs_last_error()
