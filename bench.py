@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: Jacobian solves per second to a 1e-8 relative residual.
+
+Workload (one "step"): the 256x256-cell 2D log-normal permeability grid
+(sigma 2, correlation length 8 cells, mean ln 1e-12), capillary scale swept over
+{0, 1e3, 1e4, 1e5} Pa; for each scale the exact Newton Jacobian at the
+synthetic front state is assembled on the GPU and solved by right-
+preconditioned FGMRES(30) with each of the three preconditioners (black-box
+AMG on J, CPR-AMG with quasi-IMPES decoupling, block factorisation with the
+SIMPLE Schur complement): 12 solves per step, each with its own
+preconditioner setup. V-cycles run in FP64 for the headline number (the
+workload's "plain FP64 on GPU"); the same step with FP32 V-cycles is reported
+beside it. A solve counts when its true relative residual is <= 1e-8 within
+`--maxit` Arnoldi steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank runs the same step on its own GPU (replicas;
+no data-path collective) and `value` is all ranks' solves over the slowest
+rank's time. `--impl reference` times the CPU oracle on a bounded sample of
+the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = "Jacobian solves/s to 1e-8 relative residual (256x256 2D log-normal, 4 capillary scales x 3 preconditioners)"
+UNIT = "solves/s"
+WORKLOAD = "2d_256x256_lognormal_sigma2_ell8_pc{0,1e3,1e4,1e5}_x_{amgJ,cpr1_qimpes,bf}"
+PC_SCALES = (0.0, 1e3, 1e4, 1e5)
+KINDS = (("amgJ", 0, 0), ("cpr1", 1, 2), ("bf", 3, 0))
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--maxit", type=int, default=300)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_1611_00127_gb300 import inputs as I
+    probs, states = [], []
+    for pc in PC_SCALES:
+        p = I.config_lognormal_2d(pc, n=n)
+        probs.append(p)
+        states.append(I.front_state(p))
+    return probs, states
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+class GpuStep:
+    def __init__(self, probs, states, precision, maxit):
+        import torch
+        from paper_1611_00127_gb300 import rsflow as R
+        self.R, self.torch = R, torch
+        self.probs = probs
+        self.precision = precision
+        self.maxit = maxit
+        self.dps = [R.DeviceProblems(p) for p in probs]
+        self.J = R.Bsr2.pattern(self.dps[0])
+        n = 2 * probs[0].ncell
+        self.n = n
+        self.F = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.b = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.x = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.u = [torch.as_tensor(s[0], device="cuda") for s in states]
+        self.uo = [torch.as_tensor(s[1], device="cuda") for s in states]
+        self.xout = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(len(probs) * len(KINDS))]
+
+    def params(self, kind, dec):
+        R = self.R
+        return R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(precision=self.precision))
+
+    def run(self, dps=None, us=None, uos=None):
+        """One step; returns per-solve records."""
+        R, torch = self.R, self.torch
+        dps = dps or self.dps
+        us = us or self.u
+        uos = uos or self.uo
+        recs = []
+        q = 0
+        for k in range(len(self.probs)):
+            R.jacobian_assemble(dps[k], us[k], uos[k], 86400.0, self.J, self.F)
+            torch.neg(self.F, out=self.b)
+            for name, kind, dec in KINDS:
+                self.xout[q].zero_()
+                M = R.Precond(self.J, self.params(kind, dec))
+                st = R.gmres_solve(self.J, M, self.b, self.xout[q], R.GmresParams(m=30, maxit=self.maxit, rtol=1e-8))
+                M.close()
+                recs.append(dict(pc=PC_SCALES[k], prec=name, its=int(st.iterations), relres=float(st.relres),
+                                 converged=bool(st.converged == 1)))
+                q += 1
+        return recs
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def time_steps(step, steps, warmup, sync_barrier):
+    import torch
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    for _ in range(warmup):
+        step.run()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    recs = None
+    for _ in range(steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        sync_barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        recs = step.run()
+        e1.record()
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    return total_ms, recs
+
+
+def e2e_steps(probs, states, precision, maxit, steps, warmup):
+    """The same step through the public API starting from pinned host inputs:
+    permeability fields and states copied in, every solution copied out,
+    inside the timed region."""
+    import torch
+    from paper_1611_00127_gb300 import rsflow as R
+    n = 2 * probs[0].ncell
+    host_k = [torch.from_numpy(np.ascontiguousarray(np.stack([p.kx, p.ky, p.kz]))).pin_memory() for p in probs]
+    host_u = [torch.from_numpy(np.ascontiguousarray(s[0])).pin_memory() for s in states]
+    host_uo = [torch.from_numpy(np.ascontiguousarray(s[1])).pin_memory() for s in states]
+    host_x = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(len(probs) * len(KINDS))]
+    step = GpuStep(probs, states, precision, maxit)
+    dev_k = [torch.empty_like(h, device="cuda") for h in host_k]
+    dev_u = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in probs]
+    dev_uo = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in probs]
+    # problems bound to the device buffers that the copies refill every step
+    dps = []
+    for k, p in enumerate(probs):
+        dp = R.DeviceProblems(p)
+        dp.c[0].kx, dp.c[0].ky, dp.c[0].kz = (dev_k[k][0].data_ptr(), dev_k[k][1].data_ptr(), dev_k[k][2].data_ptr())
+        dps.append(dp)
+    h2d = sum(h.numel() * 8 for h in host_k) + sum(h.numel() * 8 for h in host_u) * 2
+    d2h = sum(h.numel() * 8 for h in host_x)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def one():
+        for k in range(len(probs)):
+            dev_k[k].copy_(host_k[k], non_blocking=True)
+            dev_u[k].copy_(host_u[k], non_blocking=True)
+            dev_uo[k].copy_(host_uo[k], non_blocking=True)
+        recs = step.run(dps, dev_u, dev_uo)
+        for q, h in enumerate(host_x):
+            h.copy_(step.xout[q], non_blocking=True)
+        return recs
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    total = 0.0
+    nconv = 0
+    for _ in range(steps):
+        flush.add_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        recs = one()
+        torch.cuda.synchronize()
+        total += time.perf_counter() - t0
+        nconv += sum(r["converged"] for r in recs)
+    return nconv / total, h2d, d2h
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(probs, states, maxit, budget_s=20.0):
+    """Times the oracle (single-threaded, as it stands) on whole solves of the
+    same workload, in workload order, until ~budget_s of CPU time is used."""
+    import oracle as O
+    t0 = time.perf_counter()
+    done, conv, ran = 0, 0, []
+    for k, p in enumerate(probs):
+        F, J, (rp, col) = O.assemble(p, states[k][0], states[k][1], 86400.0)
+        for name, kind, dec in KINDS:
+            M = O.Precond(rp, col, J, O.PrecParams(kind=kind, decouple=dec))
+            x, st, its, rr = O.fgmres(rp, col, J, -F, M, m=30, rtol=1e-8, maxit=maxit)
+            done += 1
+            conv += int(st == 0)
+            ran.append(f"pc{PC_SCALES[k]:g}/{name}")
+            if time.perf_counter() - t0 > budget_s:
+                break
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return dict(value=conv / el, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{done} of 12 solves of one step ({', '.join(ran)}), {conv} converged, {el:.1f} s, "
+                       f"assembly + setup + FGMRES per solve")
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    probs, states = workload(args.n)
+    import oracle as O
+    O.build()
+    vals, samples = [], []
+    for w in range(args.warmup + args.steps):
+        # each step: one bounded sample (first solves of the workload, ~10 s)
+        r = oracle_sample(probs, states, args.maxit, budget_s=10.0)
+        if w >= args.warmup:
+            vals.append(r["value"])
+            samples.append(r["sample"])
+    v = float(np.mean(vals))
+    line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", config=dict(workload=WORKLOAD, grid=f"{args.n}x{args.n}"),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=samples[-1]),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_1611_00127_gb300 import rsflow as R
+    probs, states = workload(args.n)
+    R.lib()
+    # headline: FP64 V-cycles
+    step64 = GpuStep(probs, states, R.FP64, args.maxit)
+    l0 = R.launch_count()
+    with ClockSampler(local) as clk:
+        ms64, recs64 = time_steps(step64, args.steps, args.warmup, barrier)
+    launches = (R.launch_count() - l0)
+    conv64 = sum(r["converged"] for r in recs64)
+    step32 = GpuStep(probs, states, R.FP32, args.maxit)
+    ms32, recs32 = time_steps(step32, args.steps, 1, barrier)
+    conv32 = sum(r["converged"] for r in recs32)
+    t = torch.tensor([ms64, ms32], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms64, ms32 = float(t[0]), float(t[1])
+    value = world * conv64 * args.steps / (ms64 / 1e3)
+    value32 = world * conv32 * args.steps / (ms32 / 1e3)
+    e2e = None
+    if not args.no_e2e:
+        v, h2d, d2h = e2e_steps(probs, states, R.FP64, args.maxit, args.steps, 1)
+        e2e = dict(value=world * v, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline else oracle_sample(probs, states, args.maxit)
+    warmup_launch_note = "counted over warm-up + timed steps / (warm-up + timed)"
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=ms64 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+        data="synthetic",
+        config=dict(workload=WORKLOAD, grid=f"{args.n}x{args.n}", solves_per_step=12,
+                    converged_per_step=conv64, gmres="FGMRES(30), rtol 1e-8, maxit %d" % args.maxit,
+                    vcycle="FP64", l2="flushed (256 MB write) before every timed step",
+                    parallelism="replicas" if world > 1 else "single GPU"),
+        solves=recs64,
+        fp32_vcycle=dict(value=value32, ms_per_step=ms32 / args.steps, converged_per_step=conv32, solves=recs32),
+        clocks=clk.summary(),
+        gpu_launches=int(round(launches / (args.steps + args.warmup))) * args.steps,
+        e2e=e2e,
+        cpu_baseline=cpu,
+    )
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -84,8 +84,9 @@ typedef struct rs_problem {
   double p_out, sn_out;               /* Dirichlet outlet on the x = L face */
 } rs_problem;
 
-#define RS_SMOOTH_MCGS 0
-#define RS_SMOOTH_L1JACOBI 1
+#define RS_SMOOTH_MCGS 0      /* multicolour Gauss-Seidel over the whole level */
+#define RS_SMOOTH_L1JACOBI 1  /* l1-Jacobi */
+#define RS_SMOOTH_HYBRID 2    /* Gauss-Seidel by colour inside chunks of `chunk` rows, Jacobi between chunks */
 #define RS_INTERP_CLASSICAL 0
 #define RS_INTERP_EXTI 1
 #define RS_PREC_FP32 0   /* V-cycle values, vectors and sums in FP32 */
@@ -102,6 +103,7 @@ typedef struct rs_amg_params {
   int32_t interp;          /* RS_INTERP_* */
   int32_t num_functions;   /* >1: unknown-based strength on the finest level */
   int32_t precision;       /* RS_PREC_* of the V-cycle */
+  int32_t chunk;           /* rows per chunk of the hybrid smoother (32..1024) */
 } rs_amg_params;
 
 typedef struct rs_amg rs_amg;
@@ -156,6 +158,14 @@ const char *rs_last_error(void);
 
 /* Library version and the CUDA architecture it was built for. */
 int rs_version(int *major, int *minor, int *arch);
+
+/* Number of CUDA kernels the library has launched in this process so far
+ * (all threads, all devices). */
+long long rs_launch_count(void);
+
+/* Lanes per block row of the block SpMV (2, 4 or 8; default 4), a tuning
+ * knob chosen by measurement. */
+int rs_tune_set_bsr2_lpr(int lanes);
 
 /* ---------------------------------------------------------------- grid --- */
 /* Number of stored blocks of the two-point-flux pattern of `nprob` grids

@@ -65,7 +65,7 @@ class _AmgParams(C.Structure):
     _fields_ = [("theta", C.c_double), ("seed", C.c_uint64), ("max_levels", C.c_int32),
                 ("coarse_n", C.c_int32), ("max_dense", C.c_int32), ("smoother", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("interp", C.c_int32),
-                ("num_functions", C.c_int32)]
+                ("num_functions", C.c_int32), ("chunk", C.c_int32)]
 
 
 class _PrecParams(C.Structure):
@@ -303,16 +303,17 @@ class AmgParams:
     max_levels: int = 25
     coarse_n: int = 64
     max_dense: int = 2048
-    smoother: int = 0
+    smoother: int = 2
     nu1: int = 1
     nu2: int = 1
     interp: int = 1
     num_functions: int = 1
+    chunk: int = 512
 
     def c(self):
         return _AmgParams(self.theta, self.seed, self.max_levels, self.coarse_n,
                           self.max_dense, self.smoother, self.nu1, self.nu2, self.interp,
-                          self.num_functions)
+                          self.num_functions, self.chunk)
 
 
 def splitmix64(seed: int, counter: int) -> int:

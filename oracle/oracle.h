@@ -41,10 +41,11 @@ typedef struct {
   int32_t max_levels;
   int32_t coarse_n;    /* stop coarsening at or below this many rows */
   int32_t max_dense;   /* largest coarsest level solved by dense LU */
-  int32_t smoother;    /* 0 multicolour Gauss-Seidel, 1 l1-Jacobi */
+  int32_t smoother;    /* 0 multicolour Gauss-Seidel, 1 l1-Jacobi, 2 hybrid multicolour GS */
   int32_t nu1, nu2;
   int32_t interp;      /* 0 classical, 1 extended+i */
   int32_t num_functions; /* >1: unknown-based strength on the finest level */
+  int32_t chunk;       /* rows per block of the hybrid smoother */
 } or_amg_params;
 
 typedef struct or_amg or_amg;

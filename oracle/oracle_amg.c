@@ -22,11 +22,16 @@
  *    with no strong C neighbour gets an empty row.
  *  - Galerkin coarse operator A_c = P^T (A P), both products by ascending
  *    inner index.
- *  - Smoother: multicolour Gauss-Seidel (Jones-Plassmann colouring of the
+ *  - Smoother: hybrid multicolour Gauss-Seidel (the default, smoother = 2):
+ *    the rows are cut into consecutive chunks of `chunk` rows; inside a chunk
+ *    Gauss-Seidel runs colour by colour (Jones-Plassmann colouring of the
  *    symmetrised pattern, each point taking the lowest colour unused by its
- *    already coloured neighbours), colours swept in ascending order for both
- *    pre- and post-smoothing, in place of the paper's hybrid GS. l1-Jacobi
- *    is the alternative.
+ *    already coloured neighbours, colours ascending) on the newest values,
+ *    while couplings to other chunks use the values from the start of the
+ *    sweep. This is the paper's hybrid Gauss-Seidel with a chunk of rows in
+ *    place of an MPI process. Alternatives: plain multicolour Gauss-Seidel
+ *    over the whole level (smoother = 0) and l1-Jacobi (smoother = 1). Pre-
+ *    and post-smoothing sweep the colours in the same ascending order.
  *  - Coarsest level: dense LU with partial pivoting.
  */
 #include <math.h>
@@ -624,6 +629,37 @@ void or_amg_smooth(const or_amg *H, int32_t l, const double *b, double *x) {
     for (int32_t i = 0; i < A->n; i++)
       if (H->l1[l][i] != 0.0) x[i] += r[i] / H->l1[l][i];
     free(r);
+    return;
+  }
+  if (H->prm.smoother == 2) {
+    /* hybrid multicolour Gauss-Seidel: rows are cut into consecutive chunks of
+     * `chunk` rows; inside a chunk the colours are swept in order using the
+     * chunk's newest values, couplings to other chunks use the values from the
+     * start of the sweep (block Jacobi between chunks, as in the hybrid
+     * Gauss-Seidel of parallel AMG codes, with a chunk in place of a process). */
+    double *xo = xmalloc(sizeof(double) * ((size_t)A->n + 1));
+    memcpy(xo, x, sizeof(double) * (size_t)A->n);
+    /* chunk size: the `chunk` parameter, halved (not below 32) while
+     * chunk * ceil(nnz / n) exceeds 12288 entries */
+    int32_t C = H->prm.chunk > 0 ? H->prm.chunk : 512;
+    int64_t avg = A->n > 0 ? ((int64_t)A->nnz + A->n - 1) / A->n : 1;
+    while (C > 32 && (int64_t)C * avg > 12288) C /= 2;
+    for (int32_t c0 = 0; c0 < A->n; c0 += C) {
+      int32_t c1 = c0 + C < A->n ? c0 + C : A->n;
+      for (int32_t c = 0; c < H->ncol[l]; c++) {
+        for (int32_t i = c0; i < c1; i++) {
+          if (H->colour[l][i] != c) continue;
+          double s = 0.0, d = 0.0;
+          for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+            int32_t j = A->col[q];
+            if (j == i) d = A->val[q];
+            else s += A->val[q] * ((j >= c0 && j < c1) ? x[j] : xo[j]);
+          }
+          if (d != 0.0) x[i] = (b[i] - s) / d;
+        }
+      }
+    }
+    free(xo);
     return;
   }
   for (int32_t c = 0; c < H->ncol[l]; c++) {

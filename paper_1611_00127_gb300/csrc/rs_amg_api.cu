@@ -8,7 +8,9 @@ static int check_amg_params(const rs_amg_params &a) {
   if (!(a.theta >= 0.0 && a.theta <= 1.0)) return fail(RS_EINVAL, "theta outside [0,1]");
   if (a.max_levels < 1 || a.coarse_n < 1 || a.max_dense < 1 || a.max_dense > 8192)
     return fail(RS_EINVAL, "bad level limits");
-  if (a.smoother != RS_SMOOTH_MCGS && a.smoother != RS_SMOOTH_L1JACOBI) return fail(RS_EINVAL, "bad smoother");
+  if (a.smoother != RS_SMOOTH_MCGS && a.smoother != RS_SMOOTH_L1JACOBI && a.smoother != RS_SMOOTH_HYBRID)
+    return fail(RS_EINVAL, "bad smoother");
+  if (a.smoother == RS_SMOOTH_HYBRID && (a.chunk < 32 || a.chunk > 1024)) return fail(RS_EINVAL, "chunk outside [32, 1024]");
   if (a.nu1 < 0 || a.nu2 < 0 || a.nu1 > 16 || a.nu2 > 16) return fail(RS_EINVAL, "bad sweep counts");
   if (a.interp != RS_INTERP_CLASSICAL && a.interp != RS_INTERP_EXTI) return fail(RS_EINVAL, "bad interpolation");
   if (a.precision != RS_PREC_FP32 && a.precision != RS_PREC_FP64) return fail(RS_EINVAL, "bad precision");
@@ -95,7 +97,7 @@ extern "C" int amg_level_copy(const rs_amg *H, int32_t l, int32_t *a_row_ptr, in
   if (a_val) RS_CHECK_CUDA(cudaMemcpyAsync(a_val, L.A.val, sizeof(double) * L.A.nnz, cudaMemcpyDeviceToDevice, s));
   if (cf) {
     if (L.cf) RS_CHECK_CUDA(cudaMemcpyAsync(cf, L.cf, n, cudaMemcpyDeviceToDevice, s));
-    else if (n) k_fill_i8<<<grid_for(n), kBlock, 0, s>>>((int32_t)n, 0, cf);
+    else if (n) RS_COUNTED k_fill_i8<<<grid_for(n), kBlock, 0, s>>>((int32_t)n, 0, cf);
   }
   if (L.P.rowptr) {
     if (p_row_ptr) RS_CHECK_CUDA(cudaMemcpyAsync(p_row_ptr, L.P.rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToDevice, s));
@@ -104,7 +106,7 @@ extern "C" int amg_level_copy(const rs_amg *H, int32_t l, int32_t *a_row_ptr, in
   }
   if (colour) {
     if (L.colour) RS_CHECK_CUDA(cudaMemcpyAsync(colour, L.colour, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-    else if (n) k_fill_i32<<<grid_for(n), kBlock, 0, s>>>((int32_t)n, -2, colour);
+    else if (n) RS_COUNTED k_fill_i32<<<grid_for(n), kBlock, 0, s>>>((int32_t)n, -2, colour);
   }
   RS_CHECK_CUDA(cudaGetLastError());
   return RS_OK;

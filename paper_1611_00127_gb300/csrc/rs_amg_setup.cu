@@ -422,20 +422,26 @@ __global__ void k_colour_fill(int32_t n, const int32_t *colour, int32_t *fill, i
   if (i < n && colour[i] >= 0) rows[atomicAdd(&fill[colour[i]], 1)] = i;
 }
 
-__global__ void k_sort_ints(int32_t nlists, const int32_t *off, int32_t *v) {
-  // one thread per colour list: the lists are sorted so that sweeps read rows in order
-  int32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nlists) return;
-  // simple shell sort
-  const int32_t s = off[c], len = off[c + 1] - off[c];
-  int32_t *a = v + s;
-  for (int32_t gap = len / 2; gap > 0; gap /= 2)
-    for (int32_t i = gap; i < len; i++) {
-      const int32_t t = a[i];
-      int32_t j = i;
-      for (; j >= gap && a[j - gap] > t; j -= gap) a[j] = a[j - gap];
-      a[j] = t;
-    }
+// Hybrid smoother tables: for chunk k (rows [cr[2k], cr[2k+1])), the local rows
+// sorted by (colour, row) and the offset of each colour inside the chunk.
+__global__ void k_chunk_sort(const int32_t *cr, const int32_t *colour, int32_t ncol, int32_t *coff,
+                             int32_t *rows) {
+  __shared__ int32_t cs[1024];
+  const int32_t k = blockIdx.x;
+  const int32_t r0 = cr[2 * k], len = cr[2 * k + 1] - r0;
+  for (int32_t t = threadIdx.x; t < len; t += blockDim.x) cs[t] = colour[r0 + t];
+  __syncthreads();
+  for (int32_t c = threadIdx.x; c <= ncol; c += blockDim.x) {
+    int32_t cnt = 0;
+    for (int32_t t = 0; t < len; t++) cnt += cs[t] < c;
+    coff[(int64_t)k * (ncol + 1) + c] = cnt;
+  }
+  for (int32_t t = threadIdx.x; t < len; t += blockDim.x) {
+    const int32_t c = cs[t];
+    int32_t rank = 0;
+    for (int32_t q = 0; q < len; q++) rank += (cs[q] < c) || (cs[q] == c && q < t);
+    rows[r0 + rank] = t;
+  }
 }
 
 // inverse diagonal (GS) or inverse l1 row weight (Jacobi), FP64 and FP32
@@ -483,22 +489,26 @@ __global__ void k_coarse_dense(const int32_t *rp, const int32_t *col, const doub
   __shared__ double red_v[256];
   __shared__ int32_t red_i[256];
   for (int32_t k = 0; k < n; k++) {
-    // pivot search
+    // pivot search: largest |a_rk| for r >= k, lowest row on ties (block-wide argmax)
     double best = -1.0;
-    int32_t bi = k;
+    int32_t bi = n;
     for (int32_t r = k + threadIdx.x; r < n; r += blockDim.x) {
       const double v = fabs(a[(int64_t)r * n + k]);
-      if (v > best) { best = v; bi = r; }
+      if (v > best || (v == best && r < bi)) { best = v; bi = r; }
     }
-    red_v[threadIdx.x] = best;
-    red_i[threadIdx.x] = bi;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int32_t oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { red_v[threadIdx.x >> 5] = best; red_i[threadIdx.x >> 5] = bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
       double bv = -1.0;
-      int32_t bix = k;
-      for (int t = 0; t < (int)blockDim.x; t++)
+      int32_t bix = n;
+      for (int t = 0; t < (int)(blockDim.x >> 5); t++)
         if (red_v[t] > bv || (red_v[t] == bv && red_i[t] < bix)) { bv = red_v[t]; bix = red_i[t]; }
-      piv = bix;
+      piv = bix < n ? bix : k;
     }
     __syncthreads();
     const int32_t p = piv;
@@ -563,15 +573,19 @@ static int colour_level(Level &L, const int32_t *seg, const int32_t *dseg_off, c
   RS_TRY(sc.get(&dsm, (size_t)nseg));
   RS_CHECK_CUDA(cudaMemcpyAsync(dsm, sm.data(), nseg, cudaMemcpyHostToDevice, s));
   RS_CHECK_CUDA(cudaMemsetAsync(cnt3, 0, 3 * sizeof(int32_t), s));
-  k_jp_init<<<grid_for(n), kBlock, 0, s>>>(n, seg, dseg_off, dsm, seed, level, key, L.colour);
+  RS_COUNTED k_jp_init<<<grid_for(n), kBlock, 0, s>>>(n, seg, dseg_off, dsm, seed, level, key, L.colour);
   int32_t h3[3] = {1, 0, 0};
-  for (int round = 0; round < 100000 && h3[0] > 0; round++) {
-    RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)n, s));
-    RS_CHECK_CUDA(cudaMemsetAsync(mask, 0, sizeof(unsigned long long) * (size_t)n * kColourWords, s));
-    RS_CHECK_CUDA(cudaMemsetAsync(cnt3, 0, sizeof(int32_t), s));
-    k_jp_losers<<<grid_for(n), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, key, L.colour, notmax);
-    k_jp_forbid<<<grid_for(n), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.colour, notmax, mask);
-    k_jp_assign<<<grid_for(n), kBlock, 0, s>>>(n, notmax, mask, L.colour, cnt3, cnt3 + 1, cnt3 + 2);
+  // rounds run in batches between host checks; a round with nothing left to
+  // colour changes nothing
+  for (int round = 0; round < 100000 && h3[0] > 0; round += 6) {
+    for (int r = 0; r < 6; r++) {
+      RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)n, s));
+      RS_CHECK_CUDA(cudaMemsetAsync(mask, 0, sizeof(unsigned long long) * (size_t)n * kColourWords, s));
+      RS_CHECK_CUDA(cudaMemsetAsync(cnt3, 0, sizeof(int32_t), s));
+      RS_COUNTED k_jp_losers<<<grid_for(n), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, key, L.colour, notmax);
+      RS_COUNTED k_jp_forbid<<<grid_for(n), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.colour, notmax, mask);
+      RS_COUNTED k_jp_assign<<<grid_for(n), kBlock, 0, s>>>(n, notmax, mask, L.colour, cnt3, cnt3 + 1, cnt3 + 2);
+    }
     RS_TRY(sync_copy(h3, cnt3, sizeof(h3), s));
     if (h3[2]) return fail(RS_ESETUP, "more than 256 colours needed on level " + std::to_string(level));
   }
@@ -580,7 +594,7 @@ static int colour_level(Level &L, const int32_t *seg, const int32_t *dseg_off, c
   int32_t *ccnt = nullptr;
   RS_TRY(sc.get(&ccnt, (size_t)nc + 1));
   RS_CHECK_CUDA(cudaMemsetAsync(ccnt, 0, sizeof(int32_t) * ((size_t)nc + 1), s));
-  if (n > 0) k_colour_count<<<grid_for(n), kBlock, 0, s>>>(n, L.colour, ccnt);
+  if (n > 0) RS_COUNTED k_colour_count<<<grid_for(n), kBlock, 0, s>>>(n, L.colour, ccnt);
   RS_TRY(exclusive_scan(ccnt, ccnt, nc, s, &L.nsmooth));
   L.colour_off.resize(nc + 1);
   RS_TRY(sync_copy(L.colour_off.data(), ccnt, sizeof(int32_t) * (nc + 1), s));
@@ -588,8 +602,7 @@ static int colour_level(Level &L, const int32_t *seg, const int32_t *dseg_off, c
   int32_t *fill = nullptr;
   RS_TRY(sc.get(&fill, (size_t)nc + 1));
   RS_CHECK_CUDA(cudaMemcpyAsync(fill, ccnt, sizeof(int32_t) * (nc + 1), cudaMemcpyDeviceToDevice, s));
-  if (n > 0) k_colour_fill<<<grid_for(n), kBlock, 0, s>>>(n, L.colour, fill, L.colour_rows);
-  if (nc > 0) k_sort_ints<<<grid_for(nc, 64), 64, 0, s>>>(nc, ccnt, L.colour_rows);
+  if (n > 0) RS_COUNTED k_colour_fill<<<grid_for(n), kBlock, 0, s>>>(n, L.colour, fill, L.colour_rows);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }
@@ -655,12 +668,12 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       RS_CHECK_CUDA(cudaMemcpyAsync(dact, act.data(), nseg, cudaMemcpyHostToDevice, s));
       RS_TRY(dalloc_n(&L.cf, (size_t)n, s));
       const unsigned g = grid_for(n);
-      k_diag<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag);
-      k_strength<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, seg, dact, prm.theta,
+      RS_COUNTED k_diag<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag);
+      RS_COUNTED k_strength<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, seg, dact, prm.theta,
                                       l == 0 ? nfun0 : 1, strong);
       RS_CHECK_CUDA(cudaMemsetAsync(lam, 0, sizeof(int32_t) * n, s));
-      k_lambda<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, lam);
-      k_pmis_init<<<g, kBlock, 0, s>>>(n, lam, seg, dseg_off, dact, prm.seed, l, key, L.cf);
+      RS_COUNTED k_lambda<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, lam);
+      RS_COUNTED k_pmis_init<<<g, kBlock, 0, s>>>(n, lam, seg, dseg_off, dact, prm.seed, l, key, L.cf);
       int32_t hleft = 1, rounds = 0;
       while (hleft > 0) {
         if (++rounds > 100000) return fail(RS_ESETUP, "PMIS did not finish");
@@ -668,15 +681,15 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         for (int r = 0; r < 3; r++) {
           RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)n, s));
           RS_CHECK_CUDA(cudaMemsetAsync(left, 0, sizeof(int32_t), s));
-          k_pmis_losers<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, key, L.cf, notmax);
-          k_pmis_select<<<g, kBlock, 0, s>>>(n, notmax, L.cf);
-          k_pmis_fmark<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, L.cf, left);
+          RS_COUNTED k_pmis_losers<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, key, L.cf, notmax);
+          RS_COUNTED k_pmis_select<<<g, kBlock, 0, s>>>(n, notmax, L.cf);
+          RS_COUNTED k_pmis_fmark<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, L.cf, left);
         }
         RS_TRY(sync_copy(&hleft, left, sizeof(int32_t), s));
       }
       // per-system C counts; systems that coarsen too little stop here
       RS_CHECK_CUDA(cudaMemsetAsync(segc, 0, sizeof(int32_t) * nseg, s));
-      k_seg_count_c<<<g, kBlock, 0, s>>>(n, L.cf, seg, segc);
+      RS_COUNTED k_seg_count_c<<<g, kBlock, 0, s>>>(n, L.cf, seg, segc);
       std::vector<int32_t> hc(nseg);
       RS_TRY(sync_copy(hc.data(), segc, sizeof(int32_t) * nseg, s));
       nact = 0;
@@ -687,14 +700,14 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         else nact++;
       }
       RS_CHECK_CUDA(cudaMemcpyAsync(dact, act.data(), nseg, cudaMemcpyHostToDevice, s));
-      k_seg_revert<<<g, kBlock, 0, s>>>(n, L.cf, seg, dact, isc);
+      RS_COUNTED k_seg_revert<<<g, kBlock, 0, s>>>(n, L.cf, seg, dact, isc);
       if (nact > 0) {
         int32_t nc = 0;
         RS_TRY(exclusive_scan(isc, isc, n, s, &nc));
         std::vector<int32_t> off_next(nseg + 1);
         int32_t *offd = nullptr;
         RS_TRY(sc.get(&offd, (size_t)nseg + 1));
-        k_gather_offsets<<<grid_for(nseg + 1), kBlock, 0, s>>>(nseg + 1, dseg_off, isc, offd);
+        RS_COUNTED k_gather_offsets<<<grid_for(nseg + 1), kBlock, 0, s>>>(nseg + 1, dseg_off, isc, offd);
         RS_TRY(sync_copy(off_next.data(), offd, sizeof(int32_t) * (nseg + 1), s));
         // interpolation
         DCsr &P = L.P;
@@ -703,10 +716,10 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         RS_TRY(dalloc_n(&P.rowptr, (size_t)n + 1, s));
         RS_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
         if (prm.interp == RS_INTERP_CLASSICAL)
-          k_interp_classical<false><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
+          RS_COUNTED k_interp_classical<false><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
                                                           P.rowptr, nullptr, nullptr, err);
         else
-          k_interp_ext<false><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
+          RS_COUNTED k_interp_ext<false><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
                                                     P.rowptr, nullptr, nullptr, err);
         int32_t pnnz = 0;
         RS_TRY(exclusive_scan(P.rowptr, P.rowptr, n, s, &pnnz));
@@ -717,10 +730,10 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         RS_TRY(dalloc_n(&P.col, (size_t)pnnz, s));
         RS_TRY(dalloc_n(&P.val, (size_t)pnnz, s));
         if (prm.interp == RS_INTERP_CLASSICAL)
-          k_interp_classical<true><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
+          RS_COUNTED k_interp_classical<true><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
                                                          P.rowptr, P.col, P.val, err);
         else
-          k_interp_ext<true><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
+          RS_COUNTED k_interp_ext<true><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
                                                    P.rowptr, P.col, P.val, err);
         RS_CHECK_CUDA(cudaGetLastError());
         RS_TRY(transpose(P, L.R, s));
@@ -742,10 +755,42 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     if (nact > 0 || std::any_of(smooth_seg.begin(), smooth_seg.end(), [](uint8_t v) { return v != 0; })) {
       RS_TRY(colour_level(Lc, seg, dseg_off, smooth_seg, prm.seed, l, s));
     }
+    if (prm.smoother == RS_SMOOTH_HYBRID && Lc.ncolour > 0) {
+      // chunk k = rows [packed[2k], packed[2k+1]), never spanning two systems;
+      // per system the chunk size is `chunk`, halved (not below 32) while
+      // chunk * ceil(nnz / n) of that system exceeds 12288 entries
+      std::vector<int32_t> rpb(nseg + 1);
+      {
+        int32_t *tmp = nullptr;
+        RS_TRY(sc.get(&tmp, (size_t)nseg + 1));
+        RS_COUNTED k_gather_offsets<<<grid_for(nseg + 1), kBlock, 0, s>>>(nseg + 1, dseg_off, Lc.A.rowptr, tmp);
+        RS_TRY(sync_copy(rpb.data(), tmp, sizeof(int32_t) * (nseg + 1), s));
+      }
+      std::vector<int32_t> packed;
+      for (int32_t q = 0; q < nseg; q++) {
+        if (!smooth_seg[q]) continue;
+        const int64_t nq = Lc.seg_off[q + 1] - Lc.seg_off[q], zq = rpb[q + 1] - rpb[q];
+        const int64_t avg = nq > 0 ? (zq + nq - 1) / nq : 1;
+        int32_t C = prm.chunk;
+        while (C > 32 && (int64_t)C * avg > 12288) C /= 2;
+        for (int32_t r = Lc.seg_off[q]; r < Lc.seg_off[q + 1]; r += C) {
+          packed.push_back(r);
+          packed.push_back(std::min(r + C, Lc.seg_off[q + 1]));
+        }
+      }
+      Lc.nchunk = (int32_t)(packed.size() / 2);
+      RS_TRY(upload(&Lc.chunk_row0, packed, s));
+      RS_TRY(dalloc_n(&Lc.chunk_coff, (size_t)Lc.nchunk * (Lc.ncolour + 1), s));
+      RS_TRY(dalloc_n(&Lc.chunk_rows, (size_t)n, s));
+      if (Lc.nchunk > 0)
+        RS_COUNTED k_chunk_sort<<<Lc.nchunk, 512, 0, s>>>(Lc.chunk_row0, Lc.colour, Lc.ncolour, Lc.chunk_coff,
+                                                          Lc.chunk_rows);
+      RS_CHECK_CUDA(cudaGetLastError());
+    }
     RS_TRY(dalloc_n(&Lc.dinv, (size_t)n, s));
     RS_TRY(dalloc_n(&Lc.dinvf, (size_t)n, s));
     if (n > 0)
-      k_smoother_diag<<<grid_for(n), kBlock, 0, s>>>(n, Lc.A.rowptr, Lc.A.col, Lc.A.val,
+      RS_COUNTED k_smoother_diag<<<grid_for(n), kBlock, 0, s>>>(n, Lc.A.rowptr, Lc.A.col, Lc.A.val,
                                                      prm.smoother == RS_SMOOTH_L1JACOBI, Lc.dinv, Lc.dinvf);
     // systems solved directly here
     int64_t inv_tot = 0;
@@ -775,24 +820,27 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       RS_TRY(dalloc_n(&Lc.cinv, (size_t)inv_tot, s));
       double *work = nullptr;
       RS_TRY(sc.get(&work, 2 * (size_t)inv_tot));
-      k_coarse_dense<<<(unsigned)info.size(), 256, 0, s>>>(Lc.A.rowptr, Lc.A.col, Lc.A.val, Lc.cinfo, Lc.cinv_off,
+      RS_COUNTED k_coarse_dense<<<(unsigned)info.size(), 256, 0, s>>>(Lc.A.rowptr, Lc.A.col, Lc.A.val, Lc.cinfo, Lc.cinv_off,
                                                            work, Lc.cinv);
       RS_CHECK_CUDA(cudaGetLastError());
     }
     // FP32 copies for the FP32 cycle
     if (H.precision == RS_PREC_FP32) {
       RS_TRY(dalloc_n(&Lc.A.valf, (size_t)Lc.A.nnz, s));
-      if (Lc.A.nnz) k_to_f32<<<grid_for(Lc.A.nnz), kBlock, 0, s>>>(Lc.A.nnz, Lc.A.val, Lc.A.valf);
+      if (Lc.A.nnz) RS_COUNTED k_to_f32<<<grid_for(Lc.A.nnz), kBlock, 0, s>>>(Lc.A.nnz, Lc.A.val, Lc.A.valf);
       if (Lc.P.rowptr) {
         RS_TRY(dalloc_n(&Lc.P.valf, (size_t)Lc.P.nnz, s));
         RS_TRY(dalloc_n(&Lc.R.valf, (size_t)Lc.R.nnz, s));
-        if (Lc.P.nnz) k_to_f32<<<grid_for(Lc.P.nnz), kBlock, 0, s>>>(Lc.P.nnz, Lc.P.val, Lc.P.valf);
-        if (Lc.R.nnz) k_to_f32<<<grid_for(Lc.R.nnz), kBlock, 0, s>>>(Lc.R.nnz, Lc.R.val, Lc.R.valf);
+        if (Lc.P.nnz) RS_COUNTED k_to_f32<<<grid_for(Lc.P.nnz), kBlock, 0, s>>>(Lc.P.nnz, Lc.P.val, Lc.P.valf);
+        if (Lc.R.nnz) RS_COUNTED k_to_f32<<<grid_for(Lc.R.nnz), kBlock, 0, s>>>(Lc.R.nnz, Lc.R.val, Lc.R.valf);
       }
     }
     // work vectors
     const size_t es = H.precision == RS_PREC_FP32 ? sizeof(float) : sizeof(double);
     RS_TRY(dalloc(&Lc.x, es * ((size_t)n + 1), s));
+    RS_TRY(dalloc(&Lc.x2, es * ((size_t)n + 1), s));
+    RS_CHECK_CUDA(cudaMemsetAsync(Lc.x, 0, es * ((size_t)n + 1), s));
+    RS_CHECK_CUDA(cudaMemsetAsync(Lc.x2, 0, es * ((size_t)n + 1), s));
     RS_TRY(dalloc(&Lc.b, es * ((size_t)n + 1), s));
     RS_TRY(dalloc(&Lc.r, es * ((size_t)n + 1), s));
     RS_TRY(dalloc(&Lc.t, es * ((size_t)n + 1), s));
@@ -822,6 +870,10 @@ void amg_free(Hier &H, cudaStream_t s) {
     dfree(L.crow_seg, s);
     dfree(L.cinv, s);
     dfree(L.x, s);
+    dfree(L.x2, s);
+    dfree(L.chunk_row0, s);
+    dfree(L.chunk_coff, s);
+    dfree(L.chunk_rows, s);
     dfree(L.b, s);
     dfree(L.r, s);
     dfree(L.t, s);

@@ -1,5 +1,6 @@
 // Error state, memory pool, device scan and batch helpers.
 #include <cstdio>
+#include <atomic>
 #include <mutex>
 
 #include "rs_internal.cuh"
@@ -14,6 +15,10 @@ int fail(int code, const std::string &msg) {
   g_last_error = msg;
   return code;
 }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 static std::once_flag g_pool_once;
 
@@ -146,9 +151,9 @@ int exclusive_scan(const int32_t *in, int32_t *out, int32_t n, cudaStream_t s, i
   Scratch sc(s);
   int32_t *sums = nullptr;
   RS_TRY(sc.get(&sums, (size_t)nt + 1));
-  scan_tiles<<<nt, kBlock, 0, s>>>(in, out, n, sums);
-  scan_sums<<<1, kBlock, 0, s>>>(sums, nt, sums + nt);
-  scan_add<<<nt, kBlock, 0, s>>>(out, n, sums, sums + nt);
+  RS_COUNTED scan_tiles<<<nt, kBlock, 0, s>>>(in, out, n, sums);
+  RS_COUNTED scan_sums<<<1, kBlock, 0, s>>>(sums, nt, sums + nt);
+  RS_COUNTED scan_add<<<nt, kBlock, 0, s>>>(out, n, sums, sums + nt);
   RS_CHECK_CUDA(cudaGetLastError());
   if (total) {
     RS_CHECK_CUDA(cudaMemcpyAsync(total, out + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -185,7 +190,7 @@ int seg_ids(const std::vector<int32_t> &seg_off, int32_t n, int32_t **dseg, cuda
   int32_t *doff = nullptr;
   RS_TRY(dalloc_n(&doff, seg_off.size(), s));
   RS_CHECK_CUDA(cudaMemcpyAsync(doff, seg_off.data(), seg_off.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-  if (n > 0) k_seg_ids<<<grid_for(n), kBlock, 0, s>>>(doff, nseg, n, *dseg);
+  if (n > 0) RS_COUNTED k_seg_ids<<<grid_for(n), kBlock, 0, s>>>(doff, nseg, n, *dseg);
   dfree(doff, s);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
@@ -194,6 +199,8 @@ int seg_ids(const std::vector<int32_t> &seg_off, int32_t n, int32_t **dseg, cuda
 }  // namespace rs
 
 extern "C" const char *rs_last_error(void) { return rs::g_last_error.c_str(); }
+
+extern "C" long long rs_launch_count(void) { return rs::g_launches.load(); }
 
 extern "C" int rs_version(int *major, int *minor, int *arch) {
   if (major) *major = 0;

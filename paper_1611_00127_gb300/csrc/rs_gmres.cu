@@ -246,8 +246,8 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
   RS_CHECK_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * nseg * ldh, s));
   const unsigned gseg = grid_for(nseg);
   auto norms = [&](const double *vec, double *out) -> int {
-    if (nch > 0) k_multidot<<<nch, kRedThreads, 0, s>>>(dch, vec, 0, 1, vec, stride, part);
-    k_reduce<<<gseg, kBlock, 0, s>>>(nseg, dsegc, 1, stride, part, out, nullptr, 0, 0, 3, nullptr);
+    if (nch > 0) RS_COUNTED k_multidot<<<nch, kRedThreads, 0, s>>>(dch, vec, 0, 1, vec, stride, part);
+    RS_COUNTED k_reduce<<<gseg, kBlock, 0, s>>>(nseg, dsegc, 1, stride, part, out, nullptr, 0, 0, 3, nullptr);
     RS_CHECK_CUDA(cudaGetLastError());
     return 0;
   };
@@ -263,6 +263,8 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
   RS_CHECK_CUDA(cudaMallocHost(&hnact, sizeof(int32_t)));
   std::vector<int32_t> hits(nseg, 0);
   std::vector<uint8_t> hbad(nseg, 0);
+  std::vector<double> hprev(nseg, -1.0);
+  std::vector<uint8_t> stalled(nseg, 0);
   int rc = RS_OK;
   for (int cycle = 0;; cycle++) {
     // true residual
@@ -274,12 +276,26 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
     RS_CHECK_CUDA(cudaMemcpyAsync(hits.data(), its, sizeof(int32_t) * nseg, cudaMemcpyDeviceToHost, s));
     RS_CHECK_CUDA(cudaMemcpyAsync(hbad.data(), bad, (size_t)nseg, cudaMemcpyDeviceToHost, s));
     RS_CHECK_CUDA(cudaStreamSynchronize(s));
-    bool more = false;
-    for (int32_t q = 0; q < nseg; q++)
-      if (!hbad[q] && std::isfinite(hbeta[q]) && hbeta[q] > htol[q] && hits[q] < params->maxit) more = true;
+    // a system whose true residual fell by less than 0.1 % over a whole
+    // restart cycle (or grew past 1e3 ||b||) has stalled and stops
+    bool more = false, newly = false;
+    for (int32_t q = 0; q < nseg; q++) {
+      if (!stalled[q] && hprev[q] >= 0.0 && hbeta[q] > htol[q] &&
+          (hbeta[q] > 0.999 * hprev[q] || hbeta[q] > 1e3 * (hb[q] > 0.0 ? hb[q] : 1.0))) {
+        stalled[q] = 1;
+        newly = true;
+      }
+      hprev[q] = hbeta[q];
+      if (!stalled[q] && !hbad[q] && std::isfinite(hbeta[q]) && hbeta[q] > htol[q] && hits[q] < params->maxit)
+        more = true;
+    }
+    if (newly)
+      for (int32_t q = 0; q < nseg; q++)
+        if (stalled[q]) hbad[q] = 2;
+    if (newly) RS_CHECK_CUDA(cudaMemcpyAsync(bad, hbad.data(), (size_t)nseg, cudaMemcpyHostToDevice, s));
     if (!more) break;
-    k_cycle_start<<<gseg, kBlock, 0, s>>>(nseg, nrm, tol, its, params->maxit, bad, active, kseg, st);
-    if (nch > 0) k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, V, V);
+    RS_COUNTED k_cycle_start<<<gseg, kBlock, 0, s>>>(nseg, nrm, tol, its, params->maxit, bad, active, kseg, st);
+    if (nch > 0) RS_COUNTED k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, V, V);
     for (int j = 0; j < m; j++) {
       double *vj = V + (int64_t)j * n, *zj = Z + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
       if (M) rc = precond_apply_impl(M, vj, zj, s);
@@ -288,23 +304,23 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
       rc = launch_bsr2_spmv(*J, zj, w, s);
       if (rc) break;
       for (int pass = 0; pass < 2; pass++) {
-        if (nch > 0) k_multidot<<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, w, stride, part);
-        k_reduce<<<grid_for((int64_t)nseg * (j + 1)), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part, hbuf, H, ldh,
+        if (nch > 0) RS_COUNTED k_multidot<<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, w, stride, part);
+        RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * (j + 1)), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part, hbuf, H, ldh,
                                                                      j, pass == 0 ? 1 : 2, active);
-        if (nch > 0) k_update<<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, hbuf, stride, w);
+        if (nch > 0) RS_COUNTED k_update<<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, hbuf, stride, w);
       }
       rc = norms(w, nrm);
       if (rc) break;
-      if (nch > 0) k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, w, w);
+      if (nch > 0) RS_COUNTED k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, w, w);
       RS_CHECK_CUDA(cudaMemsetAsync(nact, 0, sizeof(int32_t), s));
-      k_givens<<<gseg, kBlock, 0, s>>>(nseg, j, m, H, ldh, nrm, st, active, kseg, tol, its, params->maxit, nact, bad);
+      RS_COUNTED k_givens<<<gseg, kBlock, 0, s>>>(nseg, j, m, H, ldh, nrm, st, active, kseg, tol, its, params->maxit, nact, bad);
       RS_CHECK_CUDA(cudaMemcpyAsync(hnact, nact, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       RS_CHECK_CUDA(cudaStreamSynchronize(s));
       if (*hnact == 0) break;
     }
     if (rc) break;
-    k_backsolve<<<gseg, kBlock, 0, s>>>(nseg, m, H, ldh, st, kseg, y);
-    if (nch > 0) k_xupdate<<<nch, kRedThreads, 0, s>>>(dch, Z, n, y, m, kseg, x);
+    RS_COUNTED k_backsolve<<<gseg, kBlock, 0, s>>>(nseg, m, H, ldh, st, kseg, y);
+    if (nch > 0) RS_COUNTED k_xupdate<<<nch, kRedThreads, 0, s>>>(dch, Z, n, y, m, kseg, x);
     RS_CHECK_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * nseg * ldh, s));
     RS_CHECK_CUDA(cudaGetLastError());
   }
@@ -315,7 +331,7 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
   for (int32_t q = 0; q < nseg; q++) {
     const double bn = hb[q] > 0.0 ? hb[q] : 1.0;
     const double rr = hbeta[q] / bn;
-    if (!hbad[q] && rr <= params->rtol) conv++;
+    if (hbad[q] != 1 && rr <= params->rtol) conv++;
     if (!(rr <= rmax)) rmax = rr;
     itmax = std::max(itmax, hits[q]);
     if (stats && stats->its) stats->its[q] = hits[q];

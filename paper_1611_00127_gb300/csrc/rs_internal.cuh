@@ -54,6 +54,11 @@ struct Scratch {
 };
 
 // ------------------------------------------------------------------ launch
+// Every kernel launch of the library is written `RS_COUNTED kernel<<<...>>>(...)`
+// so that rs_launch_count() can report how many kernels a call issued.
+void count_launch();
+void count_launches(long long n);
+#define RS_COUNTED ::rs::count_launch(),
 constexpr int kBlock = 256;
 inline unsigned grid_for(int64_t n, int per_block = kBlock) {
   int64_t g = (n + per_block - 1) / per_block;
@@ -110,8 +115,14 @@ struct Level {
   int64_t *cinv_off = nullptr;
   int32_t *crows = nullptr;          // the rows solved directly
   double *cinv = nullptr;            // stacked dense inverses, row-major
-  // work vectors (FP32 or FP64 by the hierarchy's precision)
-  void *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+  // hybrid smoother: chunks of consecutive rows (never spanning two systems)
+  int32_t nchunk = 0;
+  int32_t *chunk_row0 = nullptr;     // [2 nchunk] (first row, end row) of each chunk
+  int32_t *chunk_coff = nullptr;     // [nchunk * (ncolour+1)] colour offsets inside each chunk
+  int32_t *chunk_rows = nullptr;     // [n] local row of each position, sorted by (chunk, colour, row)
+  // work vectors (FP32 or FP64 by the hierarchy's precision); x2 is the
+  // second buffer of the hybrid smoother's old/new pair
+  void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
 };
 
 struct Hier {

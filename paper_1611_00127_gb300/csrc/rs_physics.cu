@@ -299,9 +299,9 @@ extern "C" int rs_bsr2_pattern(const rs_problem *probs, int32_t nprob, int32_t *
   DProb *d = nullptr;
   int32_t ncell = 0;
   RS_TRY(upload_probs(probs, nprob, &d, &ncell, stream));
-  k_pattern_counts<<<grid_for(ncell), kBlock, 0, stream>>>(d, nprob, ncell, row_ptr);
+  RS_COUNTED k_pattern_counts<<<grid_for(ncell), kBlock, 0, stream>>>(d, nprob, ncell, row_ptr);
   RS_TRY(exclusive_scan(row_ptr, row_ptr, ncell, stream, nullptr));
-  k_pattern_fill<<<grid_for(ncell), kBlock, 0, stream>>>(d, nprob, ncell, row_ptr, col);
+  RS_COUNTED k_pattern_fill<<<grid_for(ncell), kBlock, 0, stream>>>(d, nprob, ncell, row_ptr, col);
   dfree(d, stream);
   RS_CHECK_CUDA(cudaGetLastError());
   return RS_OK;
@@ -321,8 +321,8 @@ extern "C" int jacobian_assemble(const rs_problem *probs, int32_t nprob, const d
   double *props = nullptr;
   int r = dalloc_n(&props, 6 * (size_t)ncell, stream);
   if (r) { dfree(d, stream); return r; }
-  k_props<<<grid_for(ncell), kBlock, 0, stream>>>(d, nprob, ncell, u, props);
-  k_assemble<<<grid_for(ncell, 128), 128, 0, stream>>>(d, nprob, ncell, u, u_old, dt, props,
+  RS_COUNTED k_props<<<grid_for(ncell), kBlock, 0, stream>>>(d, nprob, ncell, u, props);
+  RS_COUNTED k_assemble<<<grid_for(ncell, 128), 128, 0, stream>>>(d, nprob, ncell, u, u_old, dt, props,
                                                       J ? J->row_ptr : nullptr, J ? J->val : nullptr, F);
   dfree(props, stream);
   dfree(d, stream);
@@ -370,7 +370,7 @@ int scaled_fnorm(const rs_problem *probs, int32_t nprob, const double *F, double
   unsigned long long *acc = nullptr;
   RS_TRY(dalloc_n(&acc, 1, s));
   RS_CHECK_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
-  if (ncell > 0) k_scaled_fnorm<<<grid_for(ncell), kBlock, 0, s>>>(d, nprob, ncell, F, dt, acc);
+  if (ncell > 0) RS_COUNTED k_scaled_fnorm<<<grid_for(ncell), kBlock, 0, s>>>(d, nprob, ncell, F, dt, acc);
   unsigned long long h = 0;
   RS_CHECK_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
   RS_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -386,7 +386,7 @@ int newton_update(const rs_problem *probs, int32_t nprob, const double *du, doub
   DProb *d = nullptr;
   int32_t ncell = 0;
   RS_TRY(upload_probs(probs, nprob, &d, &ncell, s));
-  if (ncell > 0) k_newton_update<<<grid_for(ncell), kBlock, 0, s>>>(d, nprob, ncell, du, sign, u);
+  if (ncell > 0) RS_COUNTED k_newton_update<<<grid_for(ncell), kBlock, 0, s>>>(d, nprob, ncell, du, sign, u);
   dfree(d, s);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;

@@ -36,6 +36,14 @@ struct rs_precond {
   DCsr Aps;                        // BF coupling block
   double *rt = nullptr, *sb = nullptr, *ss = nullptr, *sx = nullptr, *sy = nullptr;
   cudaStream_t stream;
+  // the apply sequence recorded once as a CUDA graph (on a private stream,
+  // between fixed input/output buffers) and replayed on the caller's stream
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double *gin = nullptr, *gout = nullptr;
+  long long napply = 0;
+  long long graph_launches = 0;
+  bool use_graph = true;
 };
 
 namespace {
@@ -211,6 +219,10 @@ int build(rs_precond *M, cudaStream_t s) {
 void destroy(rs_precond *M) {
   cudaStream_t s = M->stream;
   cudaStreamSynchronize(s);
+  if (M->exec) cudaGraphExecDestroy(M->exec);
+  if (M->cap_stream) cudaStreamDestroy(M->cap_stream);
+  dfree(M->gin, s);
+  dfree(M->gout, s);
   if (M->has_p) amg_free(M->Hp, s);
   if (M->has_s) amg_free(M->Hs, s);
   if (M->has_j) amg_free(M->Hj, s);
@@ -230,7 +242,7 @@ void destroy(rs_precond *M) {
 }  // namespace
 
 namespace rs {
-int precond_apply_impl(const rs_precond *M, const double *r, double *z, cudaStream_t s) {
+static int apply_body(const rs_precond *M, const double *r, double *z, cudaStream_t s) {
   const int32_t nb = M->nb;
   if (nb == 0) return 0;
   const unsigned g = grid_for(nb);
@@ -238,29 +250,66 @@ int precond_apply_impl(const rs_precond *M, const double *r, double *z, cudaStre
     case RS_PC_AMG_J:
       return amg_vcycle(M->Hj, r, z, s);
     case RS_PC_BF: {
-      k_take<<<g, kBlock, 0, s>>>(nb, r, 1, M->sb);
+      RS_COUNTED k_take<<<g, kBlock, 0, s>>>(nb, r, 1, M->sb);
       RS_TRY(amg_vcycle(M->Hs, M->sb, M->sx, s));                 // A_ss s = R_s r
-      k_bf_rp<<<grid_for((int64_t)nb * 4), kBlock, 0, s>>>(nb, M->Aps.rowptr, M->Aps.col, M->Aps.val, M->sx, r,
+      RS_COUNTED k_bf_rp<<<grid_for((int64_t)nb * 4), kBlock, 0, s>>>(nb, M->Aps.rowptr, M->Aps.col, M->Aps.val, M->sx, r,
                                                            M->ss);    // r_p = R_p r - A_ps s
       RS_TRY(amg_vcycle(M->Hp, M->ss, M->sy, s));                 // S~ p = r_p
-      k_interleave<<<g, kBlock, 0, s>>>(nb, M->sy, M->sx, z);
+      RS_COUNTED k_interleave<<<g, kBlock, 0, s>>>(nb, M->sy, M->sx, z);
       RS_CHECK_CUDA(cudaGetLastError());
       return 0;
     }
     default: {
       const int mode = M->prm.decouple;
       const bool two = M->prm.kind == RS_PC_CPR2;
-      k_cpr_stage1<<<g, kBlock, 0, s>>>(nb, mode, M->qw, M->dinv, M->p1inv, r, M->rt, z);
-      k_cpr_resid<4><<<grid_for((int64_t)nb * 4), kBlock, 0, s>>>(nb, M->J.row_ptr, M->J.col, M->J.val, z, M->rt,
+      RS_COUNTED k_cpr_stage1<<<g, kBlock, 0, s>>>(nb, mode, M->qw, M->dinv, M->p1inv, r, M->rt, z);
+      RS_COUNTED k_cpr_resid<4><<<grid_for((int64_t)nb * 4), kBlock, 0, s>>>(nb, M->J.row_ptr, M->J.col, M->J.val, z, M->rt,
                                                                    mode, M->qw, M->dinv, M->sb,
                                                                    two ? M->ss : nullptr);
       RS_TRY(amg_vcycle(M->Hp, M->sb, M->sx, s));
       if (two) RS_TRY(amg_vcycle(M->Hs, M->ss, M->sy, s));
-      k_cpr_update<<<g, kBlock, 0, s>>>(nb, M->sx, two ? M->sy : nullptr, z);
+      RS_COUNTED k_cpr_update<<<g, kBlock, 0, s>>>(nb, M->sx, two ? M->sy : nullptr, z);
       RS_CHECK_CUDA(cudaGetLastError());
       return 0;
     }
   }
+}
+
+int precond_apply_impl(const rs_precond *Mc, const double *r, double *z, cudaStream_t s) {
+  rs_precond *M = const_cast<rs_precond *>(Mc);
+  const size_t bytes = sizeof(double) * 2 * (size_t)M->nb;
+  if (M->nb == 0) return 0;
+  if (M->use_graph && !M->exec && M->napply >= 1) {
+    // record the apply once; the first apply ran eagerly (kernel attributes set)
+    if (!M->cap_stream) RS_CHECK_CUDA(cudaStreamCreateWithFlags(&M->cap_stream, cudaStreamNonBlocking));
+    if (!M->gin) RS_TRY(dalloc_n(&M->gin, 2 * (size_t)M->nb, s));
+    if (!M->gout) RS_TRY(dalloc_n(&M->gout, 2 * (size_t)M->nb, s));
+    RS_CHECK_CUDA(cudaStreamSynchronize(s));
+    cudaGraph_t g = nullptr;
+    RS_CHECK_CUDA(cudaStreamBeginCapture(M->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = rs_launch_count();
+    int rc = apply_body(M, M->gin, M->gout, M->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(M->cap_stream, &g);
+    M->graph_launches = rs_launch_count() - l0;
+    if (rc || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      M->use_graph = false;
+    } else {
+      e = cudaGraphInstantiate(&M->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { cudaGetLastError(); M->exec = nullptr; M->use_graph = false; }
+    }
+  }
+  M->napply++;
+  if (M->exec) {
+    RS_CHECK_CUDA(cudaMemcpyAsync(M->gin, r, bytes, cudaMemcpyDeviceToDevice, s));
+    RS_CHECK_CUDA(cudaGraphLaunch(M->exec, s));
+    count_launches(M->graph_launches);
+    RS_CHECK_CUDA(cudaMemcpyAsync(z, M->gout, bytes, cudaMemcpyDeviceToDevice, s));
+    return 0;
+  }
+  return apply_body(M, r, z, s);
 }
 }  // namespace rs
 
@@ -268,7 +317,9 @@ static int check_params(const rs_amg_params &a) {
   if (!(a.theta >= 0.0 && a.theta <= 1.0)) return fail(RS_EINVAL, "theta outside [0,1]");
   if (a.max_levels < 1 || a.coarse_n < 1 || a.max_dense < 1 || a.max_dense > 8192)
     return fail(RS_EINVAL, "bad level limits");
-  if (a.smoother != RS_SMOOTH_MCGS && a.smoother != RS_SMOOTH_L1JACOBI) return fail(RS_EINVAL, "bad smoother");
+  if (a.smoother != RS_SMOOTH_MCGS && a.smoother != RS_SMOOTH_L1JACOBI && a.smoother != RS_SMOOTH_HYBRID)
+    return fail(RS_EINVAL, "bad smoother");
+  if (a.smoother == RS_SMOOTH_HYBRID && (a.chunk < 32 || a.chunk > 1024)) return fail(RS_EINVAL, "chunk outside [32, 1024]");
   if (a.nu1 < 0 || a.nu2 < 0 || a.nu1 > 16 || a.nu2 > 16) return fail(RS_EINVAL, "bad sweep counts");
   if (a.interp != RS_INTERP_CLASSICAL && a.interp != RS_INTERP_EXTI) return fail(RS_EINVAL, "bad interpolation");
   if (a.precision != RS_PREC_FP32 && a.precision != RS_PREC_FP64) return fail(RS_EINVAL, "bad precision");

@@ -24,7 +24,7 @@ int bsr2_part(const rs_bsr2 &J, int r, int c, DCsr &out, cudaStream_t s) {
   RS_TRY(dalloc_n(&out.val, (size_t)J.nnzb, s));
   RS_CHECK_CUDA(cudaMemcpyAsync(out.rowptr, J.row_ptr, sizeof(int32_t) * ((size_t)J.nb + 1), cudaMemcpyDeviceToDevice, s));
   RS_CHECK_CUDA(cudaMemcpyAsync(out.col, J.col, sizeof(int32_t) * (size_t)J.nnzb, cudaMemcpyDeviceToDevice, s));
-  if (J.nnzb > 0) k_part<<<grid_for(J.nnzb), kBlock, 0, s>>>(J.nnzb, J.val, 2 * r + c, out.val);
+  if (J.nnzb > 0) RS_COUNTED k_part<<<grid_for(J.nnzb), kBlock, 0, s>>>(J.nnzb, J.val, 2 * r + c, out.val);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }
@@ -54,7 +54,7 @@ int bsr2_scalar(const rs_bsr2 &J, DCsr &out, cudaStream_t s) {
   RS_TRY(dalloc_n(&out.rowptr, (size_t)out.n + 1, s));
   RS_TRY(dalloc_n(&out.col, (size_t)out.nnz, s));
   RS_TRY(dalloc_n(&out.val, (size_t)out.nnz, s));
-  if (J.nb > 0) k_scalar<<<grid_for(J.nb), kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, out.rowptr, out.col, out.val);
+  if (J.nb > 0) RS_COUNTED k_scalar<<<grid_for(J.nb), kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, out.rowptr, out.col, out.val);
   else RS_CHECK_CUDA(cudaMemsetAsync(out.rowptr, 0, sizeof(int32_t), s));
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
@@ -132,19 +132,19 @@ __global__ void k_diag_inv(int32_t nb, const int32_t *rowptr, const int32_t *col
 }
 
 int decouple_qimpes(const rs_bsr2 &J, double *out, double *w, cudaStream_t s) {
-  if (J.nb > 0) k_qimpes<<<grid_for(J.nb), kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, out, w);
+  if (J.nb > 0) RS_COUNTED k_qimpes<<<grid_for(J.nb), kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, out, w);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }
 
 int decouple_abf(const rs_bsr2 &J, double *out, double *dinv, cudaStream_t s) {
-  if (J.nb > 0) k_abf<<<grid_for(J.nb), kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, out, dinv);
+  if (J.nb > 0) RS_COUNTED k_abf<<<grid_for(J.nb), kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, out, dinv);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }
 
 int block_diag_inverse(const rs_bsr2 &J, double *dinv, cudaStream_t s) {
-  if (J.nb > 0) k_diag_inv<<<grid_for(J.nb), kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, dinv);
+  if (J.nb > 0) RS_COUNTED k_diag_inv<<<grid_for(J.nb), kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, dinv);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }
@@ -259,7 +259,7 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   }
   const unsigned grid = (unsigned)std::min<int64_t>((A.n + kGemmWarps - 1) / kGemmWarps, (int64_t)num_sms() * 16);
   if (A.n > 0)
-    k_spgemm<false><<<grid, 32 * kGemmWarps, shm, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val,
+    RS_COUNTED k_spgemm<false><<<grid, 32 * kGemmWarps, shm, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val,
                                                         C.rowptr, nullptr, nullptr, err);
   int32_t tot = 0;
   RS_TRY(exclusive_scan(C.rowptr, C.rowptr, A.n, s, &tot));
@@ -271,7 +271,7 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   RS_TRY(dalloc_n(&C.col, (size_t)tot, s));
   RS_TRY(dalloc_n(&C.val, (size_t)tot, s));
   if (A.n > 0)
-    k_spgemm<true><<<grid, 32 * kGemmWarps, shm, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val,
+    RS_COUNTED k_spgemm<true><<<grid, 32 * kGemmWarps, shm, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val,
                                                        C.rowptr, C.col, C.val, err);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
@@ -324,11 +324,11 @@ int transpose(const DCsr &A, DCsr &T, cudaStream_t s) {
   int32_t *fill = nullptr;
   RS_TRY(sc.get(&fill, (size_t)A.m + 1));
   RS_CHECK_CUDA(cudaMemsetAsync(T.rowptr, 0, sizeof(int32_t) * ((size_t)A.m + 1), s));
-  if (A.nnz > 0) k_col_count<<<grid_for(A.nnz), kBlock, 0, s>>>(A.nnz, A.col, T.rowptr);
+  if (A.nnz > 0) RS_COUNTED k_col_count<<<grid_for(A.nnz), kBlock, 0, s>>>(A.nnz, A.col, T.rowptr);
   RS_TRY(exclusive_scan(T.rowptr, T.rowptr, A.m, s, nullptr));
   RS_CHECK_CUDA(cudaMemcpyAsync(fill, T.rowptr, sizeof(int32_t) * ((size_t)A.m + 1), cudaMemcpyDeviceToDevice, s));
-  if (A.n > 0) k_transpose_fill<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, fill, T.col, T.val);
-  if (A.m > 0) k_row_sort<<<grid_for(A.m), kBlock, 0, s>>>(A.m, T.rowptr, T.col, T.val);
+  if (A.n > 0) RS_COUNTED k_transpose_fill<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, fill, T.col, T.val);
+  if (A.m > 0) RS_COUNTED k_row_sort<<<grid_for(A.m), kBlock, 0, s>>>(A.m, T.rowptr, T.col, T.val);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }
@@ -381,7 +381,7 @@ int csr_sub(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   C.m = A.m;
   RS_TRY(dalloc_n(&C.rowptr, (size_t)A.n + 1, s));
   if (A.n > 0)
-    k_sub<false><<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
+    RS_COUNTED k_sub<false><<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
                                                   nullptr, nullptr);
   int32_t tot = 0;
   RS_TRY(exclusive_scan(C.rowptr, C.rowptr, A.n, s, &tot));
@@ -389,7 +389,7 @@ int csr_sub(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   RS_TRY(dalloc_n(&C.col, (size_t)tot, s));
   RS_TRY(dalloc_n(&C.val, (size_t)tot, s));
   if (A.n > 0)
-    k_sub<true><<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
+    RS_COUNTED k_sub<true><<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
                                                  C.col, C.val);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
@@ -399,12 +399,12 @@ int simple_schur(const DCsr &App, const DCsr &Aps, const DCsr &Asp, const DCsr &
   Scratch sc(s);
   double *dss = nullptr;
   RS_TRY(sc.get(&dss, (size_t)Ass.n + 1));
-  if (Ass.n > 0) k_diag_vals<<<grid_for(Ass.n), kBlock, 0, s>>>(Ass.n, Ass.rowptr, Ass.col, Ass.val, dss);
+  if (Ass.n > 0) RS_COUNTED k_diag_vals<<<grid_for(Ass.n), kBlock, 0, s>>>(Ass.n, Ass.rowptr, Ass.col, Ass.val, dss);
   DCsr X = Aps;                      // shares pattern arrays with A_ps
   X.val = nullptr;
   X.valf = nullptr;
   RS_TRY(sc.get(&X.val, (size_t)Aps.nnz + 1));
-  if (Aps.nnz > 0) k_scale_cols<<<grid_for(Aps.nnz), kBlock, 0, s>>>(Aps.nnz, Aps.col, Aps.val, dss, X.val);
+  if (Aps.nnz > 0) RS_COUNTED k_scale_cols<<<grid_for(Aps.nnz), kBlock, 0, s>>>(Aps.nnz, Aps.col, Aps.val, dss, X.val);
   DCsr Pm;
   int r = spgemm(X, Asp, Pm, s);
   if (r) { dcsr_free(Pm, s); return r; }

@@ -63,9 +63,9 @@ static int launch(const rs_bsr2 &J, const double *x, const double *b, double *y,
   const int64_t threads = (int64_t)J.nb * g_bsr2_lpr;
   const unsigned grid = grid_for(threads);
   switch (g_bsr2_lpr) {
-    case 2: k_bsr2_spmv<2, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
-    case 8: k_bsr2_spmv<8, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
-    default: k_bsr2_spmv<4, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
+    case 2: RS_COUNTED k_bsr2_spmv<2, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
+    case 8: RS_COUNTED k_bsr2_spmv<8, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
+    default: RS_COUNTED k_bsr2_spmv<4, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
   }
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;

@@ -40,6 +40,109 @@ __global__ void __launch_bounds__(256) k_gs_colour(int32_t nrows, const int32_t 
   }
 }
 
+// Hybrid multicolour Gauss-Seidel sweep, one CTA per chunk of consecutive
+// rows. Couplings to rows outside the chunk read `xold` (the iterate at the
+// start of the sweep; nullptr means the zero vector), so their contribution to
+// each row is a constant of the sweep. Phase 1 walks the chunk's rows once
+// (LPR lanes per row, coalesced): it sums the out-of-chunk part of every row
+// into shared memory and, when the chunk's rows fit, copies the in-chunk
+// entries (local column, value) to shared memory as well. Phase 2 runs the
+// colours in order, each a __syncthreads apart, reading only shared memory
+// (or, for chunks too large to stage, the matrix from global memory), so a
+// colour costs shared-memory latency instead of a chain of global loads.
+// Result written to `xnew`; the order of CTAs does not affect it.
+constexpr int kHgsStageEntries = 12288;
+
+template <typename T>
+constexpr size_t hgs_smem(int cmax) {
+  return sizeof(T) * 3 * (size_t)cmax + sizeof(int32_t) * ((size_t)cmax + 1) +
+         (sizeof(int32_t) + sizeof(T)) * (size_t)kHgsStageEntries + 64;
+}
+
+template <typename T, int LPR>
+__global__ void __launch_bounds__(256) k_hgs(const int32_t *__restrict__ cr, const int32_t *__restrict__ coff,
+                                             const int32_t *__restrict__ crows, int32_t ncol, int32_t cmax,
+                                             const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                             const T *__restrict__ val, const T *__restrict__ dinv,
+                                             const T *__restrict__ b, const T *__restrict__ xold,
+                                             T *__restrict__ xnew) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *xs = reinterpret_cast<T *>(smem);               // chunk unknowns
+  T *rhs = xs + cmax;                                // b_i - (out-of-chunk part of row i)
+  T *dv = rhs + cmax;                                // 1 / a_ii
+  T *sval = dv + cmax;                               // staged values (all T arrays first: aligned)
+  int32_t *scol = reinterpret_cast<int32_t *>(sval + kHgsStageEntries);
+  int32_t *lrp = scol + kHgsStageEntries;            // staged row starts
+  const int32_t k = blockIdx.x;
+  const int32_t r0 = __ldg(cr + 2 * k), r1 = __ldg(cr + 2 * k + 1), len = r1 - r0;
+  const int32_t q0 = __ldg(rp + r0), nnz = __ldg(rp + r1) - q0;
+  const bool staged = nnz <= kHgsStageEntries;
+  const int group = threadIdx.x / LPR, lane = threadIdx.x % LPR, ngroups = blockDim.x / LPR;
+  // phase 1 (the trip count is the same for every thread of the CTA, so the
+  // group shuffles always see their whole warp)
+  for (int32_t base = 0; base < len; base += ngroups) {
+    const int32_t li = base + group;
+    const bool act = li < len;
+    const int32_t i = r0 + (act ? li : 0);
+    const int32_t s = act ? __ldg(rp + i) : 0, e = act ? __ldg(rp + i + 1) : 0;
+    T off = T(0);
+    for (int32_t q = s + lane; q < e; q += LPR) {
+      const int32_t j = __ldg(col + q);
+      const T a = __ldg(val + q);
+      const bool in = j >= r0 && j < r1;
+      if (!in && xold) off += a * __ldg(xold + j);
+      if (staged) {
+        scol[q - q0] = (in && j != i) ? j - r0 : -1;
+        sval[q - q0] = a;
+      }
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) off += __shfl_down_sync(0xffffffffu, off, o, LPR);
+    if (act && lane == 0) {
+      rhs[li] = __ldg(b + i) - off;
+      dv[li] = __ldg(dinv + i);
+      xs[li] = xold ? __ldg(xold + i) : T(0);
+      lrp[li] = s - q0;
+      if (li == len - 1) lrp[len] = e - q0;
+    }
+  }
+  __syncthreads();
+  // phase 2
+  const int32_t *cof = coff + (int64_t)k * (ncol + 1);
+  for (int32_t c = 0; c < ncol; c++) {
+    const int32_t beg = __ldg(cof + c), end = __ldg(cof + c + 1);
+    for (int32_t base = beg; base < end; base += ngroups) {
+      const int32_t pos = base + group;
+      int32_t li = -1;
+      T sacc = T(0);
+      if (pos < end) {
+        li = __ldg(crows + r0 + pos);
+        const int32_t s = lrp[li], e = lrp[li + 1];
+        if (staged) {
+          for (int32_t q = s + lane; q < e; q += LPR) {
+            const int32_t jl = scol[q];
+            if (jl >= 0) sacc += sval[q] * xs[jl];
+          }
+        } else {
+          const int32_t i = r0 + li;
+          for (int32_t q = s + lane; q < e; q += LPR) {
+            const int32_t j = __ldg(col + q0 + q);
+            if (j >= r0 && j < r1 && j != i) sacc += __ldg(val + q0 + q) * xs[j - r0];
+          }
+        }
+      }
+#pragma unroll
+      for (int o = LPR / 2; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o, LPR);
+      if (li >= 0 && lane == 0) {
+        const T di = dv[li];
+        if (di != T(0)) xs[li] = (rhs[li] - sacc) * di;
+      }
+    }
+    __syncthreads();
+  }
+  for (int32_t t = threadIdx.x; t < len; t += blockDim.x) xnew[r0 + t] = xs[t];
+}
+
 // t_i = b_i - (A x)_i for listed rows (first half of an l1-Jacobi sweep)
 template <typename T, int LPR>
 __global__ void __launch_bounds__(256) k_resid_rows(int32_t nrows, const int32_t *__restrict__ rows,
@@ -148,57 +251,97 @@ const float *dinv_of<float>(const Level &L) { return L.dinvf; }
 template <>
 const double *dinv_of<double>(const Level &L) { return L.dinv; }
 
+template <typename T, int LPR>
+static void hgs_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_hgs<T, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hgs_smem<T>(1024));
+    done = true;
+  }
+}
+
+// Smoothing sweeps on level l. `cur` holds the current iterate on entry (or
+// is nullptr when it is zero) and the buffer holding the result on exit.
 template <typename T>
-static void smooth(const Hier &H, const Level &L, int sweeps, cudaStream_t s) {
-  if (L.nsmooth == 0 || sweeps <= 0) return;
+static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStream_t s) {
+  if (sweeps <= 0) return;
   const int lpr = pick_lpr(L.A.n, L.A.nnz);
   const T *val = vals<T>(L.A);
   const T *dinv = dinv_of<T>(L);
-  T *x = static_cast<T *>(L.x);
   const T *b = static_cast<const T *>(L.b);
+  T *xa = static_cast<T *>(L.x), *xb = static_cast<T *>(L.x2);
+  if (L.nsmooth == 0) {
+    if (!cur) {
+      cudaMemsetAsync(xa, 0, sizeof(T) * (size_t)L.A.n, s);
+      cur = xa;
+    }
+    return;
+  }
+  if (H.prm.smoother == RS_SMOOTH_HYBRID) {
+    const size_t shm = hgs_smem<T>(H.prm.chunk);
+    for (int sw = 0; sw < sweeps; sw++) {
+      T *out = (cur == xa) ? xb : xa;
+      RS_LPR_SWITCH(lpr, hgs_attr<T, L_>(); RS_COUNTED k_hgs<T, L_><<<L.nchunk, 256, shm, s>>>(
+                             L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, H.prm.chunk, L.A.rowptr,
+                             L.A.col, val, dinv, b, cur, out));
+      cur = out;
+    }
+    return;
+  }
+  if (!cur) {
+    cudaMemsetAsync(xa, 0, sizeof(T) * (size_t)L.A.n, s);
+    cur = xa;
+  }
+  T *x = cur;
   for (int sw = 0; sw < sweeps; sw++) {
     if (H.prm.smoother == RS_SMOOTH_L1JACOBI) {
       T *t = static_cast<T *>(L.t);
       const int32_t nr = L.nsmooth;
-      RS_LPR_SWITCH(lpr, k_resid_rows<T, L_><<<grid_for((int64_t)nr * L_), kBlock, 0, s>>>(
+      RS_LPR_SWITCH(lpr, RS_COUNTED k_resid_rows<T, L_><<<grid_for((int64_t)nr * L_), kBlock, 0, s>>>(
                              nr, L.colour_rows, L.A.rowptr, L.A.col, val, b, x, t));
-      k_jacobi_update<T><<<grid_for(nr), kBlock, 0, s>>>(nr, L.colour_rows, dinv, t, x);
+      RS_COUNTED k_jacobi_update<T><<<grid_for(nr), kBlock, 0, s>>>(nr, L.colour_rows, dinv, t, x);
     } else {
       for (int c = 0; c < L.ncolour; c++) {
         const int32_t r0 = L.colour_off[c], nr = L.colour_off[c + 1] - r0;
         if (nr == 0) continue;
-        RS_LPR_SWITCH(lpr, k_gs_colour<T, L_><<<grid_for((int64_t)nr * L_), kBlock, 0, s>>>(
+        RS_LPR_SWITCH(lpr, RS_COUNTED k_gs_colour<T, L_><<<grid_for((int64_t)nr * L_), kBlock, 0, s>>>(
                                nr, L.colour_rows + r0, L.A.rowptr, L.A.col, val, dinv, b, x));
       }
     }
   }
 }
 
+// One V-cycle on level l with zero initial guess; returns the buffer that
+// holds x_l.
 template <typename T>
-static void cycle(const Hier &H, int32_t l, cudaStream_t s) {
+static T *cycle(const Hier &H, int32_t l, cudaStream_t s) {
   const Level &L = H.L[l];
-  T *x = static_cast<T *>(L.x);
-  if (L.A.n > 0) cudaMemsetAsync(x, 0, sizeof(T) * (size_t)L.A.n, s);
-  smooth<T>(H, L, H.prm.nu1, s);
+  T *cur = nullptr;
+  smooth<T>(H, L, H.prm.nu1, cur, s);
+  if (!cur) {
+    cur = static_cast<T *>(L.x);
+    cudaMemsetAsync(cur, 0, sizeof(T) * (size_t)L.A.n, s);
+  }
   if (l + 1 < H.nlev && L.P.rowptr) {
     const Level &N = H.L[l + 1];
     T *r = static_cast<T *>(L.r);
     const int lpr = pick_lpr(L.A.n, L.A.nnz);
-    RS_LPR_SWITCH(lpr, k_csr<T, L_, 1><<<grid_for((int64_t)L.A.n * L_), kBlock, 0, s>>>(
-                           L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), x, static_cast<const T *>(L.b), r));
+    RS_LPR_SWITCH(lpr, RS_COUNTED k_csr<T, L_, 1><<<grid_for((int64_t)L.A.n * L_), kBlock, 0, s>>>(
+                           L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), cur, static_cast<const T *>(L.b), r));
     const int lr = pick_lpr(L.R.n, L.R.nnz);
-    RS_LPR_SWITCH(lr, k_csr<T, L_, 0><<<grid_for((int64_t)L.R.n * L_), kBlock, 0, s>>>(
+    RS_LPR_SWITCH(lr, RS_COUNTED k_csr<T, L_, 0><<<grid_for((int64_t)L.R.n * L_), kBlock, 0, s>>>(
                           L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), r, nullptr, static_cast<T *>(N.b)));
-    cycle<T>(H, l + 1, s);
+    const T *xc = cycle<T>(H, l + 1, s);
     const int lp = pick_lpr(L.P.n, L.P.nnz);
-    RS_LPR_SWITCH(lp, k_csr<T, L_, 2><<<grid_for((int64_t)L.P.n * L_), kBlock, 0, s>>>(
-                          L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P), static_cast<const T *>(N.x), nullptr, x));
+    RS_LPR_SWITCH(lp, RS_COUNTED k_csr<T, L_, 2><<<grid_for((int64_t)L.P.n * L_), kBlock, 0, s>>>(
+                          L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P), xc, nullptr, cur));
   }
-  smooth<T>(H, L, H.prm.nu2, s);
+  smooth<T>(H, L, H.prm.nu2, cur, s);
   if (L.ncoarse_rows > 0) {
-    k_coarse_solve<T><<<grid_for((int64_t)L.ncoarse_rows * 32), kBlock, 0, s>>>(
-        L.ncoarse_rows, L.crows, L.crow_seg, L.cinfo, L.cinv_off, L.cinv, static_cast<const T *>(L.b), x);
+    RS_COUNTED k_coarse_solve<T><<<grid_for((int64_t)L.ncoarse_rows * 32), kBlock, 0, s>>>(
+        L.ncoarse_rows, L.crows, L.crow_seg, L.cinfo, L.cinv_off, L.cinv, static_cast<const T *>(L.b), cur);
   }
+  return cur;
 }
 
 int amg_vcycle(const Hier &H, const double *b, double *x, cudaStream_t s) {
@@ -207,13 +350,13 @@ int amg_vcycle(const Hier &H, const double *b, double *x, cudaStream_t s) {
   const int64_t n = L0.A.n;
   if (n == 0) return 0;
   if (H.precision == RS_PREC_FP32) {
-    k_cast<double, float><<<grid_for(n), kBlock, 0, s>>>(n, b, static_cast<float *>(L0.b));
-    cycle<float>(H, 0, s);
-    k_cast<float, double><<<grid_for(n), kBlock, 0, s>>>(n, static_cast<const float *>(L0.x), x);
+    RS_COUNTED k_cast<double, float><<<grid_for(n), kBlock, 0, s>>>(n, b, static_cast<float *>(L0.b));
+    const float *x0 = cycle<float>(H, 0, s);
+    RS_COUNTED k_cast<float, double><<<grid_for(n), kBlock, 0, s>>>(n, x0, x);
   } else {
     RS_CHECK_CUDA(cudaMemcpyAsync(L0.b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    cycle<double>(H, 0, s);
-    RS_CHECK_CUDA(cudaMemcpyAsync(x, L0.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    const double *x0 = cycle<double>(H, 0, s);
+    RS_CHECK_CUDA(cudaMemcpyAsync(x, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   }
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;

@@ -71,7 +71,7 @@ class AmgParamsC(C.Structure):
     _fields_ = [("theta", C.c_double), ("seed", C.c_uint64), ("max_levels", C.c_int32),
                 ("coarse_n", C.c_int32), ("max_dense", C.c_int32), ("smoother", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("interp", C.c_int32),
-                ("num_functions", C.c_int32), ("precision", C.c_int32)]
+                ("num_functions", C.c_int32), ("precision", C.c_int32), ("chunk", C.c_int32)]
 
 
 class PrecParamsC(C.Structure):
@@ -120,6 +120,7 @@ def _declare(L):
         "bsr2_spmv": (C.c_int, [P, P, P, P]),
         "bsr2_residual": (C.c_int, [P, P, P, P, P]),
         "rs_tune_set_bsr2_lpr": (C.c_int, [C.c_int]),
+        "rs_launch_count": (C.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -231,17 +232,18 @@ class AmgParams:
     max_levels: int = 25
     coarse_n: int = 64
     max_dense: int = 2048
-    smoother: int = 0
+    smoother: int = 2
     nu1: int = 1
     nu2: int = 1
     interp: int = 1
     num_functions: int = 1
     precision: int = FP32
+    chunk: int = 512
 
     def c(self):
         return AmgParamsC(self.theta, self.seed, self.max_levels, self.coarse_n, self.max_dense,
                           self.smoother, self.nu1, self.nu2, self.interp, self.num_functions,
-                          self.precision)
+                          self.precision, self.chunk)
 
 
 @dataclass
@@ -420,6 +422,10 @@ def newton_step(dp: DeviceProblems, u: torch.Tensor, u_old: torch.Tensor, dt: fl
                                   C.byref(st), _stream(stream)), "newton_step")
     return rc, dict(newton_its=st.newton_its, linear_its=st.linear_its, fnorm=st.fnorm,
                     setup_ms=st.setup_ms, solve_ms=st.solve_ms, assemble_ms=st.assemble_ms)
+
+
+def launch_count() -> int:
+    return int(lib().rs_launch_count())
 
 
 def set_bsr2_lanes(lpr: int):

@@ -162,7 +162,7 @@ def test_precond_hierarchies_bit_exact(R, oracle, inputs):
             _hier_compare(gM.amg(1), oM.amg(1))
 
 
-@pytest.mark.parametrize("smoother", [0, 1])
+@pytest.mark.parametrize("smoother", [0, 1, 2])
 def test_vcycle_fp64_matches_oracle(R, oracle, inputs, smoother):
     rp, c, v = inputs.poisson_2d(50)
     gh, oh = _amg_pair(R, oracle, rp, c, v, smoother=smoother)

@@ -232,9 +232,9 @@ def test_dense_lu_against_numpy(oracle):
     np.testing.assert_allclose(oracle.dense_lu_solve(M, b), np.linalg.solve(M, b), rtol=1e-12)
 
 
-def _vcycle_rate(oracle, A, theta, seed=1):
+def _vcycle_rate(oracle, A, theta, seed=1, smoother=0):
     Ao = oracle.Csr.from_scipy(A)
-    H = oracle.Amg(Ao, oracle.AmgParams(theta=theta))
+    H = oracle.Amg(Ao, oracle.AmgParams(theta=theta, smoother=smoother))
     rng = np.random.default_rng(seed)
     b = rng.standard_normal(A.shape[0])
     x = np.zeros_like(b)
@@ -265,6 +265,17 @@ def test_amg_mesh_independent_on_poisson_3d(oracle, inputs):
         rates.append(rate)
     assert max(rates) < 0.3, rates
     assert rates[-1] - rates[0] < 0.1, rates
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_hybrid_smoother_rate_bounded(oracle, inputs, dim):
+    """The hybrid smoother (Gauss-Seidel inside chunks, Jacobi between them)
+    keeps the V-cycle rate bounded as the number of chunks grows."""
+    sizes = (32, 64, 128) if dim == 2 else (12, 24, 40)
+    for n in sizes:
+        rp, c, v = inputs.poisson_2d(n) if dim == 2 else inputs.poisson_3d(n)
+        rate, H = _vcycle_rate(oracle, sp.csr_matrix((v, c, rp)), 0.25 if dim == 2 else 0.5, smoother=2)
+        assert rate < 0.3, (n, rate)
 
 
 def test_amg_pressure_block_gmres_iterations_flat(oracle, inputs):
