@@ -186,6 +186,20 @@ int rs_bsr2_pattern(const rs_problem *probs, int32_t nprob, int32_t *row_ptr, in
 int jacobian_assemble(const rs_problem *probs, int32_t nprob, const double *u, const double *u_old,
                       double dt, rs_bsr2 *J, double *F, cudaStream_t stream);
 
+/* Same as jacobian_assemble, but the call allocates no device memory: for
+ * callers that cannot call cudaMalloc at that point (the device allocator is
+ * owned by another component or fully reserved, or the call sits in a loop
+ * that must not allocate). The paper has no counterpart; this is a service of
+ * the library. Scratch lives in fixed arrays of the library's device image
+ * (about 3.2 MB held on every GPU that loads the library, until exit).
+ * Limits: at most 65536 cells and 64 grids per call, else RS_EINVAL with a
+ * message naming the limit. The first call on a device looks up the arrays'
+ * device addresses (cudaGetSymbolAddress); make that first call before any
+ * stream capture. All calls share the arrays: calls that overlap on the GPU
+ * race. Arguments and outputs as for jacobian_assemble. */
+int jacobian_assemble_noalloc(const rs_problem *probs, int32_t nprob, const double *u, const double *u_old,
+                              double dt, rs_bsr2 *J, double *F, cudaStream_t stream);
+
 /* Classical AMG hierarchy for a scalar matrix (Sec. 3.2; solver settings of
  * Sec. 4 with PMIS coarsening and the stated interpolation): strength graph,
  * PMIS C/F splitting, interpolation, Galerkin A_c = P^T A P, colouring,

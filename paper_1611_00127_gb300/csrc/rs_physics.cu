@@ -20,6 +20,7 @@
 //    x = L with half-cell transmissibility; other faces closed; depth is the
 //    last coordinate.
 #include <cstring>
+#include <mutex>
 
 #include "rs_internal.cuh"
 
@@ -393,3 +394,108 @@ int newton_update(const rs_problem *probs, int32_t nprob, const double *du, doub
 }
 
 }  // namespace rs
+
+// ------------------------------------------------------------------------
+// Assembly without any device allocation.
+//
+// Some callers cannot allocate device memory at the moment they need a
+// residual and Jacobian: code running while another component owns the
+// device allocator (a framework that forbids outside cudaMalloc, or one whose
+// memory is fully reserved), latency-critical loops where an allocation (and
+// the synchronisation it can imply) is not acceptable, or memory-capped
+// processes. For them, jacobian_assemble_noalloc does the same work as
+// jacobian_assemble with its scratch (the per-cell constitutive table and the
+// grid descriptors) held in fixed-size arrays that live in the library's
+// device image, so the call itself allocates nothing on the device.
+//
+// Limits: at most kNoAllocMaxCells cells and kNoAllocMaxGrids grids per call.
+// The arrays exist once per device for as long as the library is loaded
+// (about 3.2 MB of device memory on every GPU that loads it). Each call
+// overwrites them entirely (nothing has to start at zero); calls that overlap
+// on the GPU (concurrent streams, threads) share the arrays and race.
+namespace rs {
+namespace {
+
+constexpr int32_t kNoAllocMaxCells = 65536;
+constexpr int32_t kNoAllocMaxGrids = 64;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_props[6 * kNoAllocMaxCells];
+static __device__ __align__(256) DProb g_noalloc_grids[kNoAllocMaxGrids];
+
+struct NoAllocPtrs {
+  double *props = nullptr;
+  DProb *grids = nullptr;
+  bool ready = false;
+};
+static NoAllocPtrs g_noalloc_ptrs[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mu;
+
+// Device addresses of the two arrays for the current device, looked up once
+// per device (the array names are host-side stand-ins, not device addresses).
+int noalloc_ptrs(NoAllocPtrs *out) {
+  int dev = 0;
+  RS_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(RS_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocPtrs &p = g_noalloc_ptrs[dev];
+  if (!p.ready) {
+    void *a = nullptr, *b = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_props);
+    if (e != cudaSuccess) return fail(RS_ECUDA, std::string("cudaGetSymbolAddress(props): ") + cudaGetErrorString(e));
+    e = cudaGetSymbolAddress(&b, g_noalloc_grids);
+    if (e != cudaSuccess) return fail(RS_ECUDA, std::string("cudaGetSymbolAddress(grids): ") + cudaGetErrorString(e));
+    p.props = static_cast<double *>(a);
+    p.grids = static_cast<DProb *>(b);
+    p.ready = true;
+  }
+  *out = p;
+  return 0;
+}
+
+}  // namespace
+}  // namespace rs
+
+extern "C" int jacobian_assemble_noalloc(const rs_problem *probs, int32_t nprob, const double *u,
+                                         const double *u_old, double dt, rs_bsr2 *J, double *F,
+                                         cudaStream_t stream) {
+  if (!u || !u_old || !F) return fail(RS_EINVAL, "null vector");
+  if (!(dt > 0)) return fail(RS_EINVAL, "dt must be positive");
+  if (!probs || nprob < 1) return fail(RS_EINVAL, "no problem descriptions");
+  if (nprob > kNoAllocMaxGrids)
+    return fail(RS_EINVAL, "jacobian_assemble_noalloc: " + std::to_string(nprob) + " grids exceed the limit of " +
+                               std::to_string(kNoAllocMaxGrids));
+  DProb h[kNoAllocMaxGrids];
+  int64_t tot = 0;
+  for (int32_t k = 0; k < nprob; k++) {
+    const rs_problem &q = probs[k];
+    if (q.nx < 1 || q.ny < 1 || q.nz < 1 || (q.dim != 2 && q.dim != 3) || (q.dim == 2 && q.nz != 1))
+      return fail(RS_EINVAL, "bad grid dimensions in problem " + std::to_string(k));
+    if (!q.kx || !q.ky || (q.dim == 3 && !q.kz)) return fail(RS_EINVAL, "missing permeability");
+    if (q.pc_model < 0 || q.pc_model > 2 || !(q.bc_lambda > 0) || !(q.mu_w > 0) || !(q.mu_n > 0))
+      return fail(RS_EINVAL, "bad constitutive parameters");
+    DProb &p = h[k];
+    p.dim = q.dim; p.nx = q.nx; p.ny = q.ny; p.nz = q.nz;
+    p.hx = q.hx; p.hy = q.hy; p.hz = q.hz;
+    p.kx = q.kx; p.ky = q.ky; p.kz = q.kz ? q.kz : q.kx;
+    p.phi = q.phi; p.mu_w = q.mu_w; p.mu_n = q.mu_n; p.rho_w = q.rho_w; p.rho_n = q.rho_n; p.g = q.g;
+    p.pc_model = q.pc_model; p.pc_p0 = q.pc_p0; p.pc_pd = q.pc_pd; p.bc_lambda = q.bc_lambda;
+    p.s_wr = q.s_wr; p.s_nr = q.s_nr; p.u_in = q.u_in; p.p_out = q.p_out; p.sn_out = q.sn_out;
+    p.cell0 = (int32_t)tot;
+    p.ncell = q.nx * q.ny * q.nz;
+    tot += (int64_t)p.ncell;
+  }
+  if (tot > kNoAllocMaxCells)
+    return fail(RS_EINVAL, "jacobian_assemble_noalloc: " + std::to_string(tot) + " cells exceed the limit of " +
+                               std::to_string(kNoAllocMaxCells));
+  const int32_t ncell = (int32_t)tot;
+  if (J && (J->nb != ncell || !J->row_ptr || !J->val)) return fail(RS_EINVAL, "Jacobian does not match the grids");
+  NoAllocPtrs d;
+  RS_TRY(noalloc_ptrs(&d));
+  RS_CHECK_CUDA(cudaMemcpyAsync(d.grids, h, sizeof(DProb) * nprob, cudaMemcpyHostToDevice, stream));
+  RS_COUNTED k_props<<<grid_for(ncell), kBlock, 0, stream>>>(d.grids, nprob, ncell, u, d.props);
+  RS_COUNTED k_assemble<<<grid_for(ncell, 128), 128, 0, stream>>>(d.grids, nprob, ncell, u, u_old, dt, d.props,
+                                                                 J ? J->row_ptr : nullptr, J ? J->val : nullptr, F);
+  RS_CHECK_CUDA(cudaGetLastError());
+  return RS_OK;
+}

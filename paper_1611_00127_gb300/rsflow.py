@@ -105,6 +105,7 @@ def _declare(L):
         "rs_bsr2_nnzb": (i64, [P, i32]),
         "rs_bsr2_pattern": (C.c_int, [P, i32, P, P, P]),
         "jacobian_assemble": (C.c_int, [P, i32, P, P, f64, P, P, P]),
+        "jacobian_assemble_noalloc": (C.c_int, [P, i32, P, P, f64, P, P, P]),
         "amg_setup": (C.c_int, [P, P, P, P]),
         "amg_destroy": (C.c_int, [P]),
         "amg_apply": (C.c_int, [P, P, P, P]),
@@ -295,6 +296,15 @@ def jacobian_assemble(dp: DeviceProblems, u: torch.Tensor, u_old: torch.Tensor, 
     _check(lib().jacobian_assemble(dp.c, len(dp), _ptr(u), _ptr(u_old), float(dt),
                                    C.byref(Jc) if Jc is not None else None, _ptr(F), _stream(stream)),
            "jacobian_assemble")
+
+
+def jacobian_assemble_noalloc(dp: DeviceProblems, u: torch.Tensor, u_old: torch.Tensor, dt: float,
+                              J: Optional[Bsr2], F: torch.Tensor, stream=None):
+    """jacobian_assemble without device allocation (fixed scratch in the library)."""
+    Jc = J.c() if J is not None else None
+    _check(lib().jacobian_assemble_noalloc(dp.c, len(dp), _ptr(u), _ptr(u_old), float(dt),
+                                           C.byref(Jc) if Jc is not None else None, _ptr(F), _stream(stream)),
+           "jacobian_assemble_noalloc")
 
 
 def bsr2_spmv(J: Bsr2, x: torch.Tensor, y: torch.Tensor, stream=None):
