@@ -170,6 +170,28 @@ def flush_l2(buf):
     buf.add_(1.0)
 
 
+def hbm_peak():
+    """Measured STREAM-copy bandwidth of the GB300s, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_step(step):
+    """One more step with the library's event profiling on: per kernel class
+    device time and algorithmic bytes (preconditioner applies run without
+    graph replay so every launch is timed)."""
+    import torch
+    R = step.R
+    torch.cuda.synchronize()
+    R.profile_begin()
+    step.run()
+    torch.cuda.synchronize()
+    return R.profile_end()
+
+
 def time_steps(step, steps, warmup, sync_barrier):
     import torch
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -333,6 +355,17 @@ def main():
         e2e = dict(value=world * v, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
     if rank != 0:
         return
+    prof = profiled_step(step64)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    peak, peak_kind = hbm_peak()
+    achieved = dom[1][1] / (dom[1][0] * 1e-3) / 1e9 if dom[1][0] > 0 else 0.0
+    roofline = dict(bound="hbm", kernel=dom[0], achieved=achieved, peak=peak, unit="GB/s",
+                    frac=achieved / peak, traffic=None, peak_source=peak_kind,
+                    launches=dom[1][2], ms=dom[1][0],
+                    note="algorithmic bytes of the class over its CUDA-event device time in one profiled step "
+                         "(256x256 working set is L2-resident, so the fraction can exceed HBM)")
+    kernel_profile = {k: dict(ms=v[0], gbs=(v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else 0.0), launches=v[2])
+                      for k, v in prof.items() if v[2] > 0}
     cpu = None if args.no_cpu_baseline else oracle_sample(probs, states, args.maxit)
     warmup_launch_note = "counted over warm-up + timed steps / (warm-up + timed)"
     line = dict(
@@ -346,6 +379,8 @@ def main():
         solves=recs64,
         fp32_vcycle=dict(value=value32, ms_per_step=ms32 / args.steps, converged_per_step=conv32, solves=recs32),
         clocks=clk.summary(),
+        roofline=roofline,
+        kernel_profile=kernel_profile,
         gpu_launches=int(round(launches / (args.steps + args.warmup))) * args.steps,
         e2e=e2e,
         cpu_baseline=cpu,

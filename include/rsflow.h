@@ -103,7 +103,7 @@ typedef struct rs_amg_params {
   int32_t interp;          /* RS_INTERP_* */
   int32_t num_functions;   /* >1: unknown-based strength on the finest level */
   int32_t precision;       /* RS_PREC_* of the V-cycle */
-  int32_t chunk;           /* rows per chunk of the hybrid smoother (32..1024) */
+  int32_t chunk;           /* rows per chunk of the hybrid smoother (32..512) */
 } rs_amg_params;
 
 typedef struct rs_amg rs_amg;
@@ -162,6 +162,18 @@ int rs_version(int *major, int *minor, int *arch);
 /* Number of CUDA kernels the library has launched in this process so far
  * (all threads, all devices). */
 long long rs_launch_count(void);
+
+/* Kernel profiling for measurement: between rs_profile_begin and
+ * rs_profile_end the library brackets launches of its main kernel classes
+ * with CUDA events on their own stream (and runs preconditioner applies
+ * without graph replay). rs_profile_end fills, per class, the summed device
+ * time [ms], the summed algorithmic bytes and the launch count, and returns
+ * the number of classes: 0 hybrid GS sweep, 1 CSR residual/restriction/
+ * prolongation, 2 block SpMV (and CPR residual), 3 GMRES dot/update,
+ * 4 setup sparse products, 5 interpolation, 6 other. Not for use inside stream
+ * capture. */
+int rs_profile_begin(void);
+int rs_profile_end(double *ms, double *bytes, long long *launches, int nclasses);
 
 /* Lanes per block row of the block SpMV (2, 4 or 8; default 4), a tuning
  * knob chosen by measurement. */

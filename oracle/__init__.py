@@ -109,6 +109,8 @@ def lib():
             "or_interp_ext": (P, [P, P, P]),
             "or_galerkin": (P, [P, P]),
             "or_jp_colour": (i32, [P, u64, i32, P]),
+            "or_chunk_rows": (i32, [P, i32]),
+            "or_chunk_colour": (i32, [P, i32, P]),
             "or_amg_setup": (P, [P, P]),
             "or_amg_free": (None, [P]),
             "or_amg_nlevels": (i32, [P]),
@@ -353,6 +355,13 @@ def jp_colour(A: Csr, seed: int, level: int = 0):
     col = np.zeros(n, dtype=np.int32)
     nc = lib().or_jp_colour(A.h, seed, level, _p(col))
     return col, int(nc)
+
+
+def chunk_colour(A: Csr, chunk: int = 512):
+    n, m, nnz = A.info()
+    col = np.zeros(n, dtype=np.int32)
+    nc = lib().or_chunk_colour(A.h, chunk, _p(col))
+    return col, int(nc), int(lib().or_chunk_rows(A.h, chunk))
 
 
 class Amg:

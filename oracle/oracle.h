@@ -85,6 +85,8 @@ or_csr *or_interp(const or_csr *A, const uint8_t *strong, const int8_t *cf);
 or_csr *or_interp_ext(const or_csr *A, const uint8_t *strong, const int8_t *cf);
 or_csr *or_galerkin(const or_csr *A, const or_csr *P);
 int32_t or_jp_colour(const or_csr *A, uint64_t seed, int32_t level, int32_t *colour);
+int32_t or_chunk_rows(const or_csr *A, int32_t chunk);
+int32_t or_chunk_colour(const or_csr *A, int32_t chunk, int32_t *colour);
 
 or_amg *or_amg_setup(const or_csr *A, const or_amg_params *prm);
 void or_amg_free(or_amg *H);

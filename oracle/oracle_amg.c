@@ -460,6 +460,66 @@ int32_t or_jp_colour(const or_csr *A, uint64_t seed, int32_t level, int32_t *col
   return ncol;
 }
 
+/* Rows per chunk of the hybrid smoother on a matrix: `chunk`, halved (not
+ * below 32) while chunk * ceil(nnz / n) exceeds 12288 entries. */
+int32_t or_chunk_rows(const or_csr *A, int32_t chunk) {
+  int32_t C = chunk > 0 ? chunk : 512;
+  int64_t avg = A->n > 0 ? ((int64_t)A->nnz + A->n - 1) / A->n : 1;
+  while (C > 32 && (int64_t)C * avg > 12288) C /= 2;
+  return C;
+}
+
+/* Colouring used by the hybrid smoother: rows are cut into chunks of
+ * or_chunk_rows(A) consecutive rows; inside each chunk, rows are coloured
+ * first-fit in ascending order, each taking the lowest colour not used by an
+ * already coloured row of the same chunk that it is coupled to in either
+ * direction (a_ij or a_ji stored, i != j). Couplings across chunks are
+ * ignored: the smoother treats them with old values. Returns the number of
+ * colours (maximum over chunks). */
+int32_t or_chunk_colour(const or_csr *A, int32_t chunk, int32_t *colour) {
+  int32_t n = A->n, C = or_chunk_rows(A, chunk), ncol = 0;
+  int32_t *tp = xmalloc(sizeof(int32_t) * ((size_t)C + 1));
+  int32_t *tc = xmalloc(sizeof(int32_t) * ((size_t)A->nnz + 1));
+  int32_t *stamp = xmalloc(sizeof(int32_t) * ((size_t)n + 2));
+  for (int32_t c = 0; c <= n; c++) stamp[c] = -1;
+  for (int32_t c0 = 0; c0 < n; c0 += C) {
+    int32_t c1 = c0 + C < n ? c0 + C : n, len = c1 - c0;
+    /* in-chunk transpose adjacency: tc[tp[i]..tp[i+1]) = rows k of the chunk with a_ki stored */
+    for (int32_t t = 0; t <= len; t++) tp[t] = 0;
+    for (int32_t k = c0; k < c1; k++)
+      for (int32_t q = A->rowptr[k]; q < A->rowptr[k + 1]; q++) {
+        int32_t j = A->col[q];
+        if (j != k && j >= c0 && j < c1) tp[j - c0 + 1]++;
+      }
+    for (int32_t t = 0; t < len; t++) tp[t + 1] += tp[t];
+    int32_t *cnt = xmalloc(sizeof(int32_t) * ((size_t)len + 1));
+    for (int32_t t = 0; t < len; t++) cnt[t] = tp[t];
+    for (int32_t k = c0; k < c1; k++)
+      for (int32_t q = A->rowptr[k]; q < A->rowptr[k + 1]; q++) {
+        int32_t j = A->col[q];
+        if (j != k && j >= c0 && j < c1) tc[cnt[j - c0]++] = k;
+      }
+    free(cnt);
+    for (int32_t i = c0; i < c1; i++) {
+      /* mark colours of coloured in-chunk neighbours (rows < i) */
+      for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+        int32_t j = A->col[q];
+        if (j != i && j >= c0 && j < i) stamp[colour[j]] = i;
+      }
+      for (int32_t t = tp[i - c0]; t < tp[i - c0 + 1]; t++) {
+        int32_t k = tc[t];
+        if (k < i) stamp[colour[k]] = i;
+      }
+      int32_t c = 0;
+      while (stamp[c] == i) c++;
+      colour[i] = c;
+      if (c + 1 > ncol) ncol = c + 1;
+    }
+  }
+  free(tp); free(tc); free(stamp);
+  return ncol;
+}
+
 /* ---------------- dense LU ---------------- */
 int32_t or_dense_lu(int32_t n, double *a, int32_t *piv) {
   int32_t sing = 0;
@@ -549,7 +609,8 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
   for (int32_t k = 0; k < H->nlev - 1; k++) {
     or_csr *A = H->A[k];
     H->colour[k] = xmalloc(sizeof(int32_t) * ((size_t)A->n + 1));
-    H->ncol[k] = or_jp_colour(A, prm->seed, k, H->colour[k]);
+    if (prm->smoother == 2) H->ncol[k] = or_chunk_colour(A, prm->chunk, H->colour[k]);
+    else H->ncol[k] = or_jp_colour(A, prm->seed, k, H->colour[k]);
     H->l1[k] = xmalloc(sizeof(double) * ((size_t)A->n + 1));
     for (int32_t i = 0; i < A->n; i++) {
       double d = 0.0, off = 0.0;
@@ -575,7 +636,8 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
     /* coarsest level too large for a dense factorisation: smooth it instead */
     int32_t k = H->nlev - 1;
     H->colour[k] = xmalloc(sizeof(int32_t) * ((size_t)nc + 1));
-    H->ncol[k] = or_jp_colour(Ac, prm->seed, k, H->colour[k]);
+    if (prm->smoother == 2) H->ncol[k] = or_chunk_colour(Ac, prm->chunk, H->colour[k]);
+    else H->ncol[k] = or_jp_colour(Ac, prm->seed, k, H->colour[k]);
     H->l1[k] = xmalloc(sizeof(double) * ((size_t)nc + 1));
     for (int32_t i = 0; i < nc; i++) {
       double d = 0.0, off = 0.0;
@@ -641,9 +703,7 @@ void or_amg_smooth(const or_amg *H, int32_t l, const double *b, double *x) {
     memcpy(xo, x, sizeof(double) * (size_t)A->n);
     /* chunk size: the `chunk` parameter, halved (not below 32) while
      * chunk * ceil(nnz / n) exceeds 12288 entries */
-    int32_t C = H->prm.chunk > 0 ? H->prm.chunk : 512;
-    int64_t avg = A->n > 0 ? ((int64_t)A->nnz + A->n - 1) / A->n : 1;
-    while (C > 32 && (int64_t)C * avg > 12288) C /= 2;
+    int32_t C = or_chunk_rows(A, H->prm.chunk);
     for (int32_t c0 = 0; c0 < A->n; c0 += C) {
       int32_t c1 = c0 + C < A->n ? c0 + C : A->n;
       for (int32_t c = 0; c < H->ncol[l]; c++) {

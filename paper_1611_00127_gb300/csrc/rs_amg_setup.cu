@@ -113,9 +113,12 @@ __global__ void k_pmis_losers(int32_t n, const int32_t *rp, const int32_t *col, 
   }
 }
 
-__global__ void k_pmis_select(int32_t n, const uint8_t *notmax, int8_t *cf) {
+// (also clears the marks it read, so the next round starts clean)
+__global__ void k_pmis_select(int32_t n, uint8_t *notmax, int8_t *cf) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && cf[i] == 0 && !notmax[i]) cf[i] = 1;
+  if (i >= n || cf[i] != 0) return;
+  if (!notmax[i]) cf[i] = 1;
+  notmax[i] = 0;
 }
 
 // undecided points strongly depending on a C point become F; count the rest
@@ -284,6 +287,219 @@ __global__ void k_interp_ext(int32_t n, const int32_t *rp, const int32_t *col, c
   if (!WRITE) prp[i] = cnt;
 }
 
+// Warp-per-row form of the extended+i weights above (same sets, same sums in
+// the same order, so the same bits): the lanes share the work that has no
+// ordering constraint (gathering Chat_i, the denominators d_k, one lane per
+// k, and the numerators, one lane per target column j, each summing over k
+// ascending), while the single ordered accumulation of dtil is done by lane 0.
+constexpr int kIWarps = 4;
+constexpr int kICand = 512;
+constexpr int kICap = 128;
+constexpr int kIF = 64;
+
+struct IWarp {
+  int32_t cand[kICand];
+  uint8_t first[kICand];
+  int32_t chat[kICap];
+  double num[kICap];
+  int32_t nset[kICap];
+  int32_t fk[kIF];
+  double fa[kIF];
+  double fd[kIF];
+  int32_t ncand, m, nf;
+};
+
+__device__ __forceinline__ int find_row(const int32_t *col, int32_t s, int32_t e, int32_t v) {
+  int32_t lo = s, hi = e - 1;
+  while (lo <= hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    const int32_t x = col[mid];
+    if (x == v) return mid;
+    if (x < v) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(32 * kIWarps) k_interp_ext_w(int32_t n, const int32_t *__restrict__ rp,
+                                                                const int32_t *__restrict__ col,
+                                                                const double *__restrict__ val,
+                                                                const double *__restrict__ diag,
+                                                                const uint8_t *__restrict__ strong,
+                                                                const int8_t *__restrict__ cf,
+                                                                const int32_t *__restrict__ cidx, int32_t *prp,
+                                                                int32_t *__restrict__ pcol, double *__restrict__ pval,
+                                                                int32_t *err) {
+  __shared__ IWarp sw[kIWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  IWarp &W = sw[warp];
+  const unsigned lt = (1u << lane) - 1u;
+  for (int32_t i = blockIdx.x * kIWarps + warp; i < n; i += gridDim.x * kIWarps) {
+    if (cf[i] == 1) {
+      if (lane == 0) {
+        if (WRITE) { pcol[prp[i]] = cidx[i]; pval[prp[i]] = 1.0; }
+        else prp[i] = 1;
+      }
+      continue;
+    }
+    const int32_t s = rp[i], e = rp[i + 1];
+    if (lane == 0) { W.ncand = 0; W.nf = 0; }
+    __syncwarp();
+    // candidates for Chat_i, and the strong F neighbours in row order
+    bool ovf = false;
+    for (int32_t b0 = s; b0 < e; b0 += 32) {
+      const int32_t q = b0 + lane;
+      int32_t j = -1;
+      bool st = false;
+      if (q < e) { j = col[q]; st = j != i && strong[q]; }
+      const bool isC = st && cf[j] == 1;
+      const bool isF = st && cf[j] != 1;
+      if (isC) {
+        const int32_t p = atomicAdd(&W.ncand, 1);
+        if (p < kICand) W.cand[p] = j; else ovf = true;
+      }
+      if (isF) {
+        for (int32_t t = rp[j]; t < rp[j + 1]; t++) {
+          const int32_t l = col[t];
+          if (l != j && strong[t] && cf[l] == 1) {
+            const int32_t p = atomicAdd(&W.ncand, 1);
+            if (p < kICand) W.cand[p] = l; else ovf = true;
+          }
+        }
+      }
+      const unsigned fm = __ballot_sync(0xffffffffu, isF);
+      const int32_t nf0 = W.nf;
+      __syncwarp();
+      if (isF) {
+        const int32_t p = nf0 + __popc(fm & lt);
+        if (p < kIF) { W.fk[p] = j; W.fa[p] = val[q]; } else ovf = true;
+      }
+      __syncwarp();
+      if (lane == 0) W.nf = nf0 + __popc(fm);
+      __syncwarp();
+    }
+    const int32_t ncand = W.ncand, nf = W.nf;
+    ovf = __any_sync(0xffffffffu, ovf) || ncand > kICand || nf > kIF;
+    // sorted distinct candidates -> Chat_i: mark first occurrences, then rank
+    // each first occurrence among the others
+    int32_t mloc = 0;
+    if (!ovf) {
+      for (int32_t a = lane; a < ncand; a += 32) {
+        const int32_t v = W.cand[a];
+        uint8_t fst = 1;
+        for (int32_t b = 0; b < a; b++)
+          if (W.cand[b] == v) { fst = 0; break; }
+        W.first[a] = fst;
+      }
+      __syncwarp();
+      for (int32_t a = lane; a < ncand; a += 32) {
+        if (!W.first[a]) continue;
+        const int32_t v = W.cand[a];
+        int32_t rank = 0;
+        for (int32_t b = 0; b < ncand; b++) rank += (W.first[b] && W.cand[b] < v);
+        if (rank < kICap) W.chat[rank] = v; else ovf = true;
+        mloc++;
+      }
+    }
+    const int32_t m = __reduce_add_sync(0xffffffffu, mloc);
+    ovf = __any_sync(0xffffffffu, ovf) || m > kICap;
+    __syncwarp();
+    if (ovf) {
+      if (lane == 0) { atomicExch(err, 1); if (!WRITE) prp[i] = 0; }
+      continue;
+    }
+    if (m == 0) {
+      if (!WRITE && lane == 0) prp[i] = 0;
+      continue;
+    }
+    // denominators d_k = sum over row k (ascending) of entries in Chat_i + {i}
+    // whose sign is opposite to a_kk; one lane per k
+    for (int32_t f = lane; f < nf; f += 32) {
+      const int32_t k = W.fk[f];
+      const double sk = diag[k] < 0.0 ? -1.0 : 1.0;
+      Acc d{0.0, false};
+      for (int32_t t = rp[k]; t < rp[k + 1]; t++) {
+        const int32_t l = col[t];
+        if (l == k || !(l == i || find_sorted(W.chat, m, l) >= 0)) continue;
+        const double av = val[t];
+        if (!(sk * av < 0.0)) continue;
+        d.add(av);
+      }
+      W.fd[f] = d.v;
+    }
+    __syncwarp();
+    // numerators: one lane per target j; a_ij first, then t_k * abar_kj for k ascending
+    for (int32_t idx = lane; idx < m; idx += 32) {
+      const int32_t l = W.chat[idx];
+      const int32_t qi = find_row(col, s, e, l);
+      Acc nm{0.0, false};
+      if (qi >= 0) nm.add(val[qi]);
+      for (int32_t f = 0; f < nf; f++) {
+        const double d = W.fd[f];
+        if (d == 0.0) continue;
+        const int32_t k = W.fk[f];
+        const int32_t qk = find_row(col, rp[k], rp[k + 1], l);
+        if (qk < 0) continue;
+        const double sk = diag[k] < 0.0 ? -1.0 : 1.0;
+        const double av = val[qk];
+        if (!(sk * av < 0.0)) continue;
+        const double tq = W.fa[f] / d;
+        nm.add(tq * av);
+      }
+      W.num[idx] = nm.v;
+      W.nset[idx] = nm.set ? 1 : 0;
+    }
+    // dtil: pass A over row i, then the "+i" terms of the k (ascending), lane 0
+    double dt = 0.0;
+    if (lane == 0) {
+      Acc a{0.0, false};
+      int32_t f = 0;
+      for (int32_t q = s; q < e; q++) {
+        const int32_t j = col[q];
+        const double v = val[q];
+        if (j == i) { a.add(v); continue; }
+        if (find_sorted(W.chat, m, j) >= 0) continue;
+        if (strong[q] && cf[j] != 1) {
+          if (W.fd[f] == 0.0) a.add(v);
+          f++;
+          continue;
+        }
+        a.add(v);
+      }
+      for (int32_t g = 0; g < nf; g++) {
+        const double d = W.fd[g];
+        if (d == 0.0) continue;
+        const int32_t k = W.fk[g];
+        const int32_t qk = find_row(col, rp[k], rp[k + 1], i);
+        if (qk < 0) continue;
+        const double sk = diag[k] < 0.0 ? -1.0 : 1.0;
+        const double av = val[qk];
+        if (!(sk * av < 0.0)) continue;
+        const double tq = W.fa[g] / d;
+        a.add(tq * av);
+      }
+      dt = a.v;
+    }
+    dt = __shfl_sync(0xffffffffu, dt, 0);
+    __syncwarp();
+    // output the set entries in Chat order
+    int32_t base = 0;
+    for (int32_t b0 = 0; b0 < m; b0 += 32) {
+      const int32_t idx = b0 + lane;
+      const bool on = idx < m && W.nset[idx] && dt != 0.0;
+      const unsigned om = __ballot_sync(0xffffffffu, on);
+      if (WRITE && on) {
+        const int32_t p = prp[i] + base + __popc(om & lt);
+        pcol[p] = cidx[W.chat[idx]];
+        pval[p] = -(W.num[idx] / dt);
+      }
+      base += __popc(om);
+    }
+    if (!WRITE && lane == 0) prp[i] = base;
+    __syncwarp();
+  }
+}
+
 // Classical Ruge-Stueben weights (C_i = strong C neighbours, distribution of
 // strong F neighbours m through C_i with entries of sign opposite to a_mm; a
 // strong F neighbour sharing no such entry, and weak neighbours, go to the
@@ -397,15 +613,17 @@ __global__ void k_jp_forbid(int32_t n, const int32_t *rp, const int32_t *col, co
   }
 }
 
-__global__ void k_jp_assign(int32_t n, const uint8_t *notmax, const unsigned long long *mask, int32_t *colour,
+// (also clears the marks and masks it read, so the next round starts clean)
+__global__ void k_jp_assign(int32_t n, uint8_t *notmax, unsigned long long *mask, int32_t *colour,
                             int32_t *left, int32_t *maxc, int32_t *err) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || colour[i] != -1) return;
-  if (notmax[i]) { atomicAdd(left, 1); return; }
+  if (notmax[i]) { notmax[i] = 0; atomicAdd(left, 1); return; }
   int c = -1;
-  for (int w = 0; w < kColourWords && c < 0; w++) {
+  for (int w = 0; w < kColourWords; w++) {
     const unsigned long long fm = ~mask[(int64_t)i * kColourWords + w];
-    if (fm) c = 64 * w + __ffsll((long long)fm) - 1;
+    if (fm && c < 0) c = 64 * w + __ffsll((long long)fm) - 1;
+    mask[(int64_t)i * kColourWords + w] = 0ull;
   }
   if (c < 0) { atomicExch(err, 1); c = 0; }
   colour[i] = c;
@@ -420,6 +638,79 @@ __global__ void k_colour_count(int32_t n, const int32_t *colour, int32_t *cnt) {
 __global__ void k_colour_fill(int32_t n, const int32_t *colour, int32_t *fill, int32_t *rows) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n && colour[i] >= 0) rows[atomicAdd(&fill[colour[i]], 1)] = i;
+}
+
+// Colouring for the hybrid smoother, one CTA per chunk (rows [cr[2k],
+// cr[2k+1]), at most 512): rows are coloured first-fit in ascending order,
+// each taking the lowest colour (< 128) not used by an already coloured row
+// of the chunk coupled to it in either direction. The chunk's coupling graph
+// is built as a bit matrix in shared memory; warp 0 then walks the rows, the
+// lanes OR-ing the colours of the coloured neighbours found in their words.
+constexpr int kCCMax = 512;
+constexpr int kCCWords = kCCMax / 32;
+
+__global__ void __launch_bounds__(256) k_chunk_colour(const int32_t *cr, const int32_t *rp, const int32_t *col,
+                                                      int32_t *colour, int32_t *maxc, int32_t *err) {
+  __shared__ uint32_t adj[kCCMax * kCCWords];
+  __shared__ int32_t cs[kCCMax];
+  const int32_t k = blockIdx.x;
+  const int32_t r0 = cr[2 * k], len = cr[2 * k + 1] - r0;
+  if (len > kCCMax) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
+  for (int32_t t = threadIdx.x; t < len * kCCWords; t += blockDim.x) adj[t] = 0u;
+  __syncthreads();
+  for (int32_t li = threadIdx.x; li < len; li += blockDim.x) {
+    const int32_t i = r0 + li;
+    for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+      const int32_t lj = col[q] - r0;
+      if (lj == li || lj < 0 || lj >= len) continue;
+      atomicOr(&adj[li * kCCWords + (lj >> 5)], 1u << (lj & 31));
+      atomicOr(&adj[lj * kCCWords + (li >> 5)], 1u << (li & 31));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int32_t localmax = 0;
+    for (int32_t li = 0; li < len; li++) {
+      unsigned long long u0 = 0ull, u1 = 0ull;
+      const int32_t wl = li >> 5;
+      if (lane < kCCWords && lane <= wl) {
+        uint32_t w = adj[li * kCCWords + lane];
+        if (lane == wl) w &= (li & 31) ? ((1u << (li & 31)) - 1u) : 0u;
+        while (w) {
+          const int b = __ffs(w) - 1;
+          w &= w - 1u;
+          const int32_t c = cs[lane * 32 + b];
+          if (c < 64) u0 |= 1ull << c; else u1 |= 1ull << (c - 64);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        u0 |= __shfl_xor_sync(0xffffffffu, u0, o);
+        u1 |= __shfl_xor_sync(0xffffffffu, u1, o);
+      }
+      if (lane == 0) {
+        int32_t c;
+        if (~u0) c = __ffsll((long long)~u0) - 1;
+        else if (~u1) c = 64 + __ffsll((long long)~u1) - 1;
+        else { c = 0; atomicExch(err, 2); }
+        cs[li] = c;
+        if (c + 1 > localmax) localmax = c + 1;
+      }
+      __syncwarp();
+    }
+    if (lane == 0) atomicMax(maxc, localmax);
+  }
+  __syncthreads();
+  for (int32_t t = threadIdx.x; t < len; t += blockDim.x) colour[r0 + t] = cs[t];
+}
+
+__global__ void k_fill_colour(int32_t n, int32_t *c) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c[i] = -2;
 }
 
 // Hybrid smoother tables: for chunk k (rows [cr[2k], cr[2k+1])), the local rows
@@ -573,14 +864,14 @@ static int colour_level(Level &L, const int32_t *seg, const int32_t *dseg_off, c
   RS_TRY(sc.get(&dsm, (size_t)nseg));
   RS_CHECK_CUDA(cudaMemcpyAsync(dsm, sm.data(), nseg, cudaMemcpyHostToDevice, s));
   RS_CHECK_CUDA(cudaMemsetAsync(cnt3, 0, 3 * sizeof(int32_t), s));
+  RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)n, s));
+  RS_CHECK_CUDA(cudaMemsetAsync(mask, 0, sizeof(unsigned long long) * (size_t)n * kColourWords, s));
   RS_COUNTED k_jp_init<<<grid_for(n), kBlock, 0, s>>>(n, seg, dseg_off, dsm, seed, level, key, L.colour);
   int32_t h3[3] = {1, 0, 0};
   // rounds run in batches between host checks; a round with nothing left to
   // colour changes nothing
   for (int round = 0; round < 100000 && h3[0] > 0; round += 6) {
     for (int r = 0; r < 6; r++) {
-      RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)n, s));
-      RS_CHECK_CUDA(cudaMemsetAsync(mask, 0, sizeof(unsigned long long) * (size_t)n * kColourWords, s));
       RS_CHECK_CUDA(cudaMemsetAsync(cnt3, 0, sizeof(int32_t), s));
       RS_COUNTED k_jp_losers<<<grid_for(n), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, key, L.colour, notmax);
       RS_COUNTED k_jp_forbid<<<grid_for(n), kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.colour, notmax, mask);
@@ -674,12 +965,12 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       RS_CHECK_CUDA(cudaMemsetAsync(lam, 0, sizeof(int32_t) * n, s));
       RS_COUNTED k_lambda<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, lam);
       RS_COUNTED k_pmis_init<<<g, kBlock, 0, s>>>(n, lam, seg, dseg_off, dact, prm.seed, l, key, L.cf);
+      RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)n, s));
       int32_t hleft = 1, rounds = 0;
       while (hleft > 0) {
         if (++rounds > 100000) return fail(RS_ESETUP, "PMIS did not finish");
         // a few rounds between host checks; a round with nothing undecided does nothing
         for (int r = 0; r < 3; r++) {
-          RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)n, s));
           RS_CHECK_CUDA(cudaMemsetAsync(left, 0, sizeof(int32_t), s));
           RS_COUNTED k_pmis_losers<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, key, L.cf, notmax);
           RS_COUNTED k_pmis_select<<<g, kBlock, 0, s>>>(n, notmax, L.cf);
@@ -719,8 +1010,8 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           RS_COUNTED k_interp_classical<false><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
                                                           P.rowptr, nullptr, nullptr, err);
         else
-          RS_COUNTED k_interp_ext<false><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
-                                                    P.rowptr, nullptr, nullptr, err);
+          RS_COUNTED k_interp_ext_w<false><<<(unsigned)std::min<int64_t>((n + kIWarps - 1) / kIWarps, 65535), 32 * kIWarps, 0, s>>>(
+              n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc, P.rowptr, nullptr, nullptr, err);
         int32_t pnnz = 0;
         RS_TRY(exclusive_scan(P.rowptr, P.rowptr, n, s, &pnnz));
         int32_t herr = 0;
@@ -733,8 +1024,8 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           RS_COUNTED k_interp_classical<true><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
                                                          P.rowptr, P.col, P.val, err);
         else
-          RS_COUNTED k_interp_ext<true><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
-                                                   P.rowptr, P.col, P.val, err);
+          RS_COUNTED k_interp_ext_w<true><<<(unsigned)std::min<int64_t>((n + kIWarps - 1) / kIWarps, 65535), 32 * kIWarps, 0, s>>>(
+              n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc, P.rowptr, P.col, P.val, err);
         RS_CHECK_CUDA(cudaGetLastError());
         RS_TRY(transpose(P, L.R, s));
         DCsr AP;
@@ -752,10 +1043,8 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     }
     Level &Lc = H.L[l];   // (reference may have moved after push_back)
     // smoother data for the systems smoothed here
-    if (nact > 0 || std::any_of(smooth_seg.begin(), smooth_seg.end(), [](uint8_t v) { return v != 0; })) {
-      RS_TRY(colour_level(Lc, seg, dseg_off, smooth_seg, prm.seed, l, s));
-    }
-    if (prm.smoother == RS_SMOOTH_HYBRID && Lc.ncolour > 0) {
+    const bool any_smooth = std::any_of(smooth_seg.begin(), smooth_seg.end(), [](uint8_t v) { return v != 0; });
+    if (any_smooth && prm.smoother == RS_SMOOTH_HYBRID) {
       // chunk k = rows [packed[2k], packed[2k+1]), never spanning two systems;
       // per system the chunk size is `chunk`, halved (not below 32) while
       // chunk * ceil(nnz / n) of that system exceeds 12288 entries
@@ -767,6 +1056,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         RS_TRY(sync_copy(rpb.data(), tmp, sizeof(int32_t) * (nseg + 1), s));
       }
       std::vector<int32_t> packed;
+      int32_t nsm = 0;
       for (int32_t q = 0; q < nseg; q++) {
         if (!smooth_seg[q]) continue;
         const int64_t nq = Lc.seg_off[q + 1] - Lc.seg_off[q], zq = rpb[q + 1] - rpb[q];
@@ -777,15 +1067,30 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           packed.push_back(r);
           packed.push_back(std::min(r + C, Lc.seg_off[q + 1]));
         }
+        nsm += (int32_t)nq;
       }
       Lc.nchunk = (int32_t)(packed.size() / 2);
+      Lc.nsmooth = nsm;
       RS_TRY(upload(&Lc.chunk_row0, packed, s));
+      RS_TRY(dalloc_n(&Lc.colour, (size_t)n, s));
+      int32_t *cc = nullptr;   // max colour, error flag
+      RS_TRY(sc.get(&cc, 2));
+      RS_CHECK_CUDA(cudaMemsetAsync(cc, 0, 2 * sizeof(int32_t), s));
+      if (n > 0) RS_COUNTED k_fill_colour<<<grid_for(n), kBlock, 0, s>>>(n, Lc.colour);
+      if (Lc.nchunk > 0)
+        RS_COUNTED k_chunk_colour<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.colour, cc, cc + 1);
+      int32_t hcc[2] = {0, 0};
+      RS_TRY(sync_copy(hcc, cc, sizeof(hcc), s));
+      if (hcc[1]) return fail(RS_ESETUP, "chunk colouring failed on level " + std::to_string(l));
+      Lc.ncolour = hcc[0];
       RS_TRY(dalloc_n(&Lc.chunk_coff, (size_t)Lc.nchunk * (Lc.ncolour + 1), s));
       RS_TRY(dalloc_n(&Lc.chunk_rows, (size_t)n, s));
       if (Lc.nchunk > 0)
         RS_COUNTED k_chunk_sort<<<Lc.nchunk, 512, 0, s>>>(Lc.chunk_row0, Lc.colour, Lc.ncolour, Lc.chunk_coff,
                                                           Lc.chunk_rows);
       RS_CHECK_CUDA(cudaGetLastError());
+    } else if (any_smooth) {
+      RS_TRY(colour_level(Lc, seg, dseg_off, smooth_seg, prm.seed, l, s));
     }
     RS_TRY(dalloc_n(&Lc.dinv, (size_t)n, s));
     RS_TRY(dalloc_n(&Lc.dinvf, (size_t)n, s));

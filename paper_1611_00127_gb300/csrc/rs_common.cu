@@ -196,7 +196,71 @@ int seg_ids(const std::vector<int32_t> &seg_off, int32_t n, int32_t **dseg, cuda
   return 0;
 }
 
+// ------------------------------------------------------------------ profiling
+struct ProfPending {
+  int cls;
+  double bytes;
+  cudaEvent_t e0, e1;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfPending> g_prof_pending;
+static double g_prof_ms[kProfCount], g_prof_bytes[kProfCount];
+static long long g_prof_n[kProfCount];
+
+bool profiling() { return g_prof_on; }
+
+ProfScope::ProfScope(int c, double b, cudaStream_t st) : cls(c), bytes(b), s(st) {
+  if (!g_prof_on) return;
+  cudaEventCreate(&e0);
+  cudaEventRecord(e0, s);
+}
+
+ProfScope::~ProfScope() {
+  if (!e0) return;
+  cudaEvent_t e1;
+  cudaEventCreate(&e1);
+  cudaEventRecord(e1, s);
+  std::lock_guard<std::mutex> lock(g_prof_mu);
+  g_prof_pending.push_back({cls, bytes, e0, e1});
+}
+
+static void prof_resolve() {
+  for (auto &p : g_prof_pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(p.e1);
+    if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      g_prof_ms[p.cls] += ms;
+      g_prof_bytes[p.cls] += p.bytes;
+      g_prof_n[p.cls] += 1;
+    }
+    cudaEventDestroy(p.e0);
+    cudaEventDestroy(p.e1);
+  }
+  g_prof_pending.clear();
+}
+
 }  // namespace rs
+
+extern "C" int rs_profile_begin(void) {
+  std::lock_guard<std::mutex> lock(rs::g_prof_mu);
+  rs::prof_resolve();
+  for (int c = 0; c < rs::kProfCount; c++) { rs::g_prof_ms[c] = 0; rs::g_prof_bytes[c] = 0; rs::g_prof_n[c] = 0; }
+  rs::g_prof_on = true;
+  return RS_OK;
+}
+
+extern "C" int rs_profile_end(double *ms, double *bytes, long long *launches, int ncls) {
+  std::lock_guard<std::mutex> lock(rs::g_prof_mu);
+  rs::g_prof_on = false;
+  rs::prof_resolve();
+  for (int c = 0; c < ncls && c < rs::kProfCount; c++) {
+    if (ms) ms[c] = rs::g_prof_ms[c];
+    if (bytes) bytes[c] = rs::g_prof_bytes[c];
+    if (launches) launches[c] = rs::g_prof_n[c];
+  }
+  return rs::kProfCount;
+}
 
 extern "C" const char *rs_last_error(void) { return rs::g_last_error.c_str(); }
 

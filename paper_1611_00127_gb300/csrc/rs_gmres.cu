@@ -121,6 +121,71 @@ __global__ void __launch_bounds__(kRedThreads) k_xupdate(const Chunk *__restrict
   }
 }
 
+// Tiled multi-dot: part[c][i] = V_i . w over chunk c for i < nvec. Each thread
+// keeps TILE running sums in registers, so a block does one reduction per
+// tile of TILE vectors instead of one per vector; w is read from shared memory.
+constexpr int kTile = 8;
+
+__device__ __forceinline__ void block_sum_tile(double (&v)[kTile], double *sh, double *out, int nv) {
+  // sh: [kRedThreads/32][kTile]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < kTile; t++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[t] += __shfl_down_sync(0xffffffffu, v[t], o);
+  }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int t = 0; t < kTile; t++) sh[wid * kTile + t] = v[t];
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double acc = 0.0;
+    for (int w = 0; w < kRedThreads / 32; w++) acc += sh[w * kTile + threadIdx.x];
+    out[threadIdx.x] = acc;
+  }
+}
+
+// MODE 0: part = V_{0..nvec-1} . w
+// MODE 1: w -= sum_i V_i h[seg][i], then part = V_{0..nvec-1} . w (next CGS pass)
+// MODE 2: w -= sum_i V_i h[seg][i], then part[0] = w . w
+template <int MODE>
+__global__ void __launch_bounds__(kRedThreads) k_arnoldi(const Chunk *__restrict__ chunks, const double *__restrict__ V,
+                                                         int64_t ldv, int nvec, const double *__restrict__ h, int stride,
+                                                         double *__restrict__ w, double *__restrict__ part) {
+  __shared__ double ws[kChunk];
+  __shared__ double sh[(kRedThreads / 32) * kTile];
+  const Chunk ch = chunks[blockIdx.x];
+  const int len = ch.end - ch.beg;
+  const double *hs = h ? h + (int64_t)ch.seg * stride : nullptr;
+  for (int t = threadIdx.x; t < len; t += kRedThreads) {
+    double x = w[ch.beg + t];
+    if (MODE != 0) {
+      for (int i = 0; i < nvec; i++) x = fma(-V[i * ldv + ch.beg + t], hs[i], x);
+      w[ch.beg + t] = x;
+    }
+    ws[t] = x;
+  }
+  __syncthreads();
+  if (MODE == 2) {
+    double v[kTile] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < len; t += kRedThreads) v[0] = fma(ws[t], ws[t], v[0]);
+    block_sum_tile(v, sh, part + (int64_t)blockIdx.x * stride, 1);
+    return;
+  }
+  for (int i0 = 0; i0 < nvec; i0 += kTile) {
+    const int nv = min(kTile, nvec - i0);
+    double v[kTile] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < len; t += kRedThreads) {
+      const double x = ws[t];
+#pragma unroll
+      for (int q = 0; q < kTile; q++)
+        if (q < nv) v[q] = fma(V[(i0 + q) * ldv + ch.beg + t], x, v[q]);
+    }
+    block_sum_tile(v, sh, part + (int64_t)blockIdx.x * stride + i0, nv);
+  }
+}
+
 struct SegState {
   double g[65];
   double cs[64], sn[64];
@@ -303,14 +368,25 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
       if (rc) break;
       rc = launch_bsr2_spmv(*J, zj, w, s);
       if (rc) break;
-      for (int pass = 0; pass < 2; pass++) {
-        if (nch > 0) RS_COUNTED k_multidot<<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, w, stride, part);
-        RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * (j + 1)), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part, hbuf, H, ldh,
-                                                                     j, pass == 0 ? 1 : 2, active);
-        if (nch > 0) RS_COUNTED k_update<<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, hbuf, stride, w);
+      // CGS2: dots, reduce, (update + second dots), reduce, (update + norm)
+      const double nv = j + 1;
+      if (nch > 0) {
+        ProfScope ps(kProfArnoldi, (nv + 1) * 8.0 * n, s);
+        RS_COUNTED k_arnoldi<0><<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, nullptr, stride, w, part);
       }
-      rc = norms(w, nrm);
-      if (rc) break;
+      RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * (j + 1)), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part, hbuf,
+                                                                          H, ldh, j, 1, active);
+      if (nch > 0) {
+        ProfScope ps(kProfArnoldi, (2.0 * nv + 2) * 8.0 * n, s);
+        RS_COUNTED k_arnoldi<1><<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, hbuf, stride, w, part);
+      }
+      RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * (j + 1)), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part, hbuf,
+                                                                          H, ldh, j, 2, active);
+      if (nch > 0) {
+        ProfScope ps(kProfArnoldi, (nv + 2) * 8.0 * n, s);
+        RS_COUNTED k_arnoldi<2><<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, hbuf, stride, w, part);
+      }
+      RS_COUNTED k_reduce<<<gseg, kBlock, 0, s>>>(nseg, dsegc, 1, stride, part, nrm, nullptr, 0, 0, 3, nullptr);
       if (nch > 0) RS_COUNTED k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, w, w);
       RS_CHECK_CUDA(cudaMemsetAsync(nact, 0, sizeof(int32_t), s));
       RS_COUNTED k_givens<<<gseg, kBlock, 0, s>>>(nseg, j, m, H, ldh, nrm, st, active, kseg, tol, its, params->maxit, nact, bad);

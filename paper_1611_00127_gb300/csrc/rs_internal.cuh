@@ -60,6 +60,31 @@ void count_launch();
 void count_launches(long long n);
 #define RS_COUNTED ::rs::count_launch(),
 constexpr int kBlock = 256;
+
+// ------------------------------------------------------------------ profiling
+// When profiling is on (rs_profile_begin), launches of the main kernel classes
+// are bracketed by CUDA events on their stream and their algorithmic bytes are
+// accumulated; preconditioner applies then run eagerly (no graph replay) so
+// that every launch is seen.
+enum ProfClass {
+  kProfHgs = 0,       // hybrid Gauss-Seidel sweep
+  kProfCsr,           // residual / restriction / prolongation
+  kProfBsr2,          // block SpMV (and the CPR residual)
+  kProfArnoldi,       // CGS2 dot / update kernels
+  kProfSpgemm,        // sparse products of the setup
+  kProfInterp,        // interpolation
+  kProfOther,
+  kProfCount
+};
+bool profiling();
+struct ProfScope {
+  int cls;
+  double bytes;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(int c, double b, cudaStream_t st);
+  ~ProfScope();
+};
 inline unsigned grid_for(int64_t n, int per_block = kBlock) {
   int64_t g = (n + per_block - 1) / per_block;
   if (g < 1) g = 1;

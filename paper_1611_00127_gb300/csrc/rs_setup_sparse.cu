@@ -258,6 +258,7 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     attr = true;
   }
   const unsigned grid = (unsigned)std::min<int64_t>((A.n + kGemmWarps - 1) / kGemmWarps, (int64_t)num_sms() * 16);
+  ProfScope ps(kProfSpgemm, A.nnz * 12.0 + B.nnz * 12.0, s);
   if (A.n > 0)
     RS_COUNTED k_spgemm<false><<<grid, 32 * kGemmWarps, shm, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val,
                                                         C.rowptr, nullptr, nullptr, err);

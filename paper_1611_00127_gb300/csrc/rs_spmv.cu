@@ -62,6 +62,7 @@ static int launch(const rs_bsr2 &J, const double *x, const double *b, double *y,
   if (J.nb <= 0) return 0;
   const int64_t threads = (int64_t)J.nb * g_bsr2_lpr;
   const unsigned grid = grid_for(threads);
+  ProfScope ps(kProfBsr2, J.nnzb * 36.0 + (J.nb + 1) * 4.0 + J.nb * (RESID ? 48.0 : 32.0), s);
   switch (g_bsr2_lpr) {
     case 2: RS_COUNTED k_bsr2_spmv<2, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
     case 8: RS_COUNTED k_bsr2_spmv<8, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;

@@ -43,20 +43,23 @@ __global__ void __launch_bounds__(256) k_gs_colour(int32_t nrows, const int32_t 
 // Hybrid multicolour Gauss-Seidel sweep, one CTA per chunk of consecutive
 // rows. Couplings to rows outside the chunk read `xold` (the iterate at the
 // start of the sweep; nullptr means the zero vector), so their contribution to
-// each row is a constant of the sweep. Phase 1 walks the chunk's rows once
-// (LPR lanes per row, coalesced): it sums the out-of-chunk part of every row
-// into shared memory and, when the chunk's rows fit, copies the in-chunk
-// entries (local column, value) to shared memory as well. Phase 2 runs the
-// colours in order, each a __syncthreads apart, reading only shared memory
-// (or, for chunks too large to stage, the matrix from global memory), so a
-// colour costs shared-memory latency instead of a chain of global loads.
-// Result written to `xnew`; the order of CTAs does not affect it.
+// each row is a constant of the sweep. Everything the CTA needs is first
+// brought into shared memory by flat loops whose loads are all independent
+// (so they overlap instead of forming one latency chain per row): the chunk's
+// row pointers, right-hand side, inverse diagonal, colour offsets and rows by
+// colour, and its matrix entries, where an entry coupling to another chunk is
+// replaced by its product with xold. Then each row's out-of-chunk sum is
+// formed, and the colours are swept in order, a __syncthreads apart, on
+// shared memory only. Chunks whose rows exceed the staging area read the
+// matrix from global memory instead. Result in `xnew`; the order of CTAs does
+// not affect it.
 constexpr int kHgsStageEntries = 12288;
+constexpr int kHgsMaxColours = 128;
 
 template <typename T>
 constexpr size_t hgs_smem(int cmax) {
-  return sizeof(T) * 3 * (size_t)cmax + sizeof(int32_t) * ((size_t)cmax + 1) +
-         (sizeof(int32_t) + sizeof(T)) * (size_t)kHgsStageEntries + 64;
+  return sizeof(T) * 3 * (size_t)cmax + sizeof(T) * (size_t)kHgsStageEntries +
+         sizeof(int32_t) * ((size_t)kHgsStageEntries + 2 * (size_t)cmax + 1 + kHgsMaxColours + 1) + 64;
 }
 
 template <typename T, int LPR>
@@ -70,64 +73,78 @@ __global__ void __launch_bounds__(256) k_hgs(const int32_t *__restrict__ cr, con
   T *xs = reinterpret_cast<T *>(smem);               // chunk unknowns
   T *rhs = xs + cmax;                                // b_i - (out-of-chunk part of row i)
   T *dv = rhs + cmax;                                // 1 / a_ii
-  T *sval = dv + cmax;                               // staged values (all T arrays first: aligned)
-  int32_t *scol = reinterpret_cast<int32_t *>(sval + kHgsStageEntries);
-  int32_t *lrp = scol + kHgsStageEntries;            // staged row starts
+  T *sval = dv + cmax;                               // staged values / out-of-chunk products
+  int32_t *scol = reinterpret_cast<int32_t *>(sval + kHgsStageEntries);   // local column or -1
+  int32_t *lrp = scol + kHgsStageEntries;            // staged row starts [len+1]
+  int32_t *srows = lrp + cmax + 1;                   // rows by colour
+  int32_t *scof = srows + cmax;                      // colour offsets [ncol+1]
   const int32_t k = blockIdx.x;
   const int32_t r0 = __ldg(cr + 2 * k), r1 = __ldg(cr + 2 * k + 1), len = r1 - r0;
   const int32_t q0 = __ldg(rp + r0), nnz = __ldg(rp + r1) - q0;
   const bool staged = nnz <= kHgsStageEntries;
+  const int32_t *cof = coff + (int64_t)k * (ncol + 1);
+  // flat loads
+  for (int32_t t = threadIdx.x; t <= len; t += blockDim.x) {
+    lrp[t] = __ldg(rp + r0 + t) - q0;
+    if (t < len) {
+      rhs[t] = __ldg(b + r0 + t);
+      dv[t] = __ldg(dinv + r0 + t);
+      xs[t] = xold ? __ldg(xold + r0 + t) : T(0);
+      srows[t] = __ldg(crows + r0 + t);
+    }
+  }
+  for (int32_t c = threadIdx.x; c <= ncol; c += blockDim.x) scof[c] = __ldg(cof + c);
+  if (staged)
+    for (int32_t q = threadIdx.x; q < nnz; q += blockDim.x) {
+      const int32_t j = __ldg(col + q0 + q);
+      const T a = __ldg(val + q0 + q);
+      const bool in = j >= r0 && j < r1;
+      scol[q] = in ? j - r0 : -1;
+      sval[q] = in ? a : (xold ? a * __ldg(xold + j) : T(0));
+    }
+  __syncthreads();
   const int group = threadIdx.x / LPR, lane = threadIdx.x % LPR, ngroups = blockDim.x / LPR;
-  // phase 1 (the trip count is the same for every thread of the CTA, so the
-  // group shuffles always see their whole warp)
+  // out-of-chunk sums (uniform trip count: the group shuffles see whole warps)
   for (int32_t base = 0; base < len; base += ngroups) {
     const int32_t li = base + group;
     const bool act = li < len;
-    const int32_t i = r0 + (act ? li : 0);
-    const int32_t s = act ? __ldg(rp + i) : 0, e = act ? __ldg(rp + i + 1) : 0;
     T off = T(0);
-    for (int32_t q = s + lane; q < e; q += LPR) {
-      const int32_t j = __ldg(col + q);
-      const T a = __ldg(val + q);
-      const bool in = j >= r0 && j < r1;
-      if (!in && xold) off += a * __ldg(xold + j);
+    if (act) {
+      const int32_t s = lrp[li], e = lrp[li + 1];
       if (staged) {
-        scol[q - q0] = (in && j != i) ? j - r0 : -1;
-        sval[q - q0] = a;
+        for (int32_t q = s + lane; q < e; q += LPR)
+          if (scol[q] < 0) off += sval[q];
+      } else if (xold) {
+        for (int32_t q = s + lane; q < e; q += LPR) {
+          const int32_t j = __ldg(col + q0 + q);
+          if (j < r0 || j >= r1) off += __ldg(val + q0 + q) * __ldg(xold + j);
+        }
       }
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) off += __shfl_down_sync(0xffffffffu, off, o, LPR);
-    if (act && lane == 0) {
-      rhs[li] = __ldg(b + i) - off;
-      dv[li] = __ldg(dinv + i);
-      xs[li] = xold ? __ldg(xold + i) : T(0);
-      lrp[li] = s - q0;
-      if (li == len - 1) lrp[len] = e - q0;
-    }
+    if (act && lane == 0) rhs[li] -= off;
   }
   __syncthreads();
-  // phase 2
-  const int32_t *cof = coff + (int64_t)k * (ncol + 1);
+  // colour passes
   for (int32_t c = 0; c < ncol; c++) {
-    const int32_t beg = __ldg(cof + c), end = __ldg(cof + c + 1);
+    const int32_t beg = scof[c], end = scof[c + 1];
     for (int32_t base = beg; base < end; base += ngroups) {
       const int32_t pos = base + group;
       int32_t li = -1;
       T sacc = T(0);
       if (pos < end) {
-        li = __ldg(crows + r0 + pos);
+        li = srows[pos];
         const int32_t s = lrp[li], e = lrp[li + 1];
         if (staged) {
           for (int32_t q = s + lane; q < e; q += LPR) {
             const int32_t jl = scol[q];
-            if (jl >= 0) sacc += sval[q] * xs[jl];
+            if (jl >= 0 && jl != li) sacc += sval[q] * xs[jl];
           }
         } else {
-          const int32_t i = r0 + li;
           for (int32_t q = s + lane; q < e; q += LPR) {
             const int32_t j = __ldg(col + q0 + q);
-            if (j >= r0 && j < r1 && j != i) sacc += __ldg(val + q0 + q) * xs[j - r0];
+            if (j >= r0 && j < r1 && j != r0 + li) sacc += __ldg(val + q0 + q) * xs[j - r0];
           }
         }
       }
@@ -279,8 +296,11 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
   }
   if (H.prm.smoother == RS_SMOOTH_HYBRID) {
     const size_t shm = hgs_smem<T>(H.prm.chunk);
+    const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
     for (int sw = 0; sw < sweeps; sw++) {
       T *out = (cur == xa) ? xb : xa;
+      const double bytes = nz * (4.0 + sizeof(T)) + (ns + 1) * 4.0 + ns * 4.0 + ns * sizeof(T) * (cur ? 4.0 : 3.0);
+      ProfScope ps(kProfHgs, bytes, s);
       RS_LPR_SWITCH(lpr, hgs_attr<T, L_>(); RS_COUNTED k_hgs<T, L_><<<L.nchunk, 256, shm, s>>>(
                              L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, H.prm.chunk, L.A.rowptr,
                              L.A.col, val, dinv, b, cur, out));
@@ -325,16 +345,26 @@ static T *cycle(const Hier &H, int32_t l, cudaStream_t s) {
   if (l + 1 < H.nlev && L.P.rowptr) {
     const Level &N = H.L[l + 1];
     T *r = static_cast<T *>(L.r);
+    const double sz = sizeof(T);
     const int lpr = pick_lpr(L.A.n, L.A.nnz);
-    RS_LPR_SWITCH(lpr, RS_COUNTED k_csr<T, L_, 1><<<grid_for((int64_t)L.A.n * L_), kBlock, 0, s>>>(
-                           L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), cur, static_cast<const T *>(L.b), r));
+    {
+      ProfScope ps(kProfCsr, L.A.nnz * (4.0 + sz) + (L.A.n + 1) * 4.0 + 3.0 * L.A.n * sz, s);
+      RS_LPR_SWITCH(lpr, RS_COUNTED k_csr<T, L_, 1><<<grid_for((int64_t)L.A.n * L_), kBlock, 0, s>>>(
+                             L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), cur, static_cast<const T *>(L.b), r));
+    }
     const int lr = pick_lpr(L.R.n, L.R.nnz);
-    RS_LPR_SWITCH(lr, RS_COUNTED k_csr<T, L_, 0><<<grid_for((int64_t)L.R.n * L_), kBlock, 0, s>>>(
-                          L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), r, nullptr, static_cast<T *>(N.b)));
+    {
+      ProfScope ps(kProfCsr, L.R.nnz * (4.0 + sz) + (L.R.n + 1) * 4.0 + (L.R.n + L.A.n) * sz, s);
+      RS_LPR_SWITCH(lr, RS_COUNTED k_csr<T, L_, 0><<<grid_for((int64_t)L.R.n * L_), kBlock, 0, s>>>(
+                            L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), r, nullptr, static_cast<T *>(N.b)));
+    }
     const T *xc = cycle<T>(H, l + 1, s);
     const int lp = pick_lpr(L.P.n, L.P.nnz);
-    RS_LPR_SWITCH(lp, RS_COUNTED k_csr<T, L_, 2><<<grid_for((int64_t)L.P.n * L_), kBlock, 0, s>>>(
-                          L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P), xc, nullptr, cur));
+    {
+      ProfScope ps(kProfCsr, L.P.nnz * (4.0 + sz) + (L.P.n + 1) * 4.0 + (2.0 * L.P.n + L.R.n) * sz, s);
+      RS_LPR_SWITCH(lp, RS_COUNTED k_csr<T, L_, 2><<<grid_for((int64_t)L.P.n * L_), kBlock, 0, s>>>(
+                            L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P), xc, nullptr, cur));
+    }
   }
   smooth<T>(H, L, H.prm.nu2, cur, s);
   if (L.ncoarse_rows > 0) {

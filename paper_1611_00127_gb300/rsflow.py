@@ -122,6 +122,8 @@ def _declare(L):
         "bsr2_residual": (C.c_int, [P, P, P, P, P]),
         "rs_tune_set_bsr2_lpr": (C.c_int, [C.c_int]),
         "rs_launch_count": (C.c_longlong, []),
+        "rs_profile_begin": (C.c_int, []),
+        "rs_profile_end": (C.c_int, [P, P, P, C.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -432,6 +434,25 @@ def newton_step(dp: DeviceProblems, u: torch.Tensor, u_old: torch.Tensor, dt: fl
                                   C.byref(st), _stream(stream)), "newton_step")
     return rc, dict(newton_its=st.newton_its, linear_its=st.linear_its, fnorm=st.fnorm,
                     setup_ms=st.setup_ms, solve_ms=st.solve_ms, assemble_ms=st.assemble_ms)
+
+
+PROFILE_CLASSES = ("hybrid_gs_sweep", "csr_resid_restrict_prolong", "bsr2_spmv", "gmres_cgs2",
+                   "setup_spgemm", "setup_interp", "other")
+
+
+def profile_begin():
+    _check(lib().rs_profile_begin(), "rs_profile_begin")
+
+
+def profile_end():
+    """Per kernel class: (ms, algorithmic bytes, launches), timed with CUDA events."""
+    k = len(PROFILE_CLASSES)
+    ms = np.zeros(k)
+    by = np.zeros(k)
+    n = np.zeros(k, dtype=np.int64)
+    lib().rs_profile_end(ms.ctypes.data_as(C.c_void_p), by.ctypes.data_as(C.c_void_p),
+                         n.ctypes.data_as(C.c_void_p), k)
+    return {PROFILE_CLASSES[i]: (float(ms[i]), float(by[i]), int(n[i])) for i in range(k)}
 
 
 def launch_count() -> int:

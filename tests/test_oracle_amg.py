@@ -293,3 +293,35 @@ def test_amg_pressure_block_gmres_iterations_flat(oracle, inputs):
         assert st == 0
         its.append(it)
     assert max(its) - min(its) <= 3, its
+
+
+@pytest.mark.parametrize("which", ["poisson2d", "poisson3d", "random"])
+def test_chunk_colouring_valid_and_first_fit(oracle, inputs, which):
+    """Hybrid-smoother colouring: inside every chunk no two coupled rows share
+    a colour, and every row takes the lowest colour not used by the coupled,
+    earlier rows of its chunk (first fit); chunk sizes follow the stated rule."""
+    if which == "poisson2d":
+        rp, c, v = inputs.poisson_2d(37)
+        A = sp.csr_matrix((v, c, rp))
+    elif which == "poisson3d":
+        rp, c, v = inputs.poisson_3d(11)
+        A = sp.csr_matrix((v, c, rp))
+    else:
+        A = _random_graph_matrix(1500, 9, 7, symmetric=False)
+    col, nc, C = oracle.chunk_colour(oracle.Csr.from_scipy(A), 512)
+    avg = -(-A.nnz // A.shape[0])
+    exp_C = 512
+    while exp_C > 32 and exp_C * avg > 12288:
+        exp_C //= 2
+    assert C == exp_C
+    S = ((A + A.T) != 0).tocsr()
+    n = A.shape[0]
+    for c0 in range(0, n, C):
+        c1 = min(c0 + C, n)
+        for i in range(c0, c1):
+            nb = S.indices[S.indptr[i]:S.indptr[i + 1]]
+            nb = nb[(nb >= c0) & (nb < c1) & (nb != i)]
+            assert not np.any(col[nb] == col[i])
+            earlier = set(col[nb[nb < i]])
+            assert set(range(col[i])) <= earlier
+    assert nc == col.max() + 1
