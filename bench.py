@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     return ap.parse_args()
 
 
@@ -139,6 +140,9 @@ class GpuStep:
         self.u = [torch.as_tensor(s[0], device="cuda") for s in states]
         self.uo = [torch.as_tensor(s[1], device="cuda") for s in states]
         self.xout = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(len(probs) * len(KINDS))]
+        # pick the block SpMV's lanes per row for this matrix (autotuner)
+        R.jacobian_assemble(self.dps[0], self.u[0], self.uo[0], 86400.0, self.J, self.F)
+        self.lanes = R.autotune_bsr2(self.J, self.F, self.x)
 
     def params(self, kind, dec):
         R = self.R
@@ -166,6 +170,43 @@ class GpuStep:
         return recs
 
 
+class GpuBatchStep:
+    """The same 12 solves as a batch: the four Jacobians stacked block-diagonally
+    (one assembly call), one preconditioner setup and one FGMRES call per kind
+    for all four systems (segment-indexed kernels, per-system convergence)."""
+
+    def __init__(self, probs, states, precision, maxit):
+        import torch
+        from paper_1611_00127_gb300 import rsflow as R
+        self.R, self.torch = R, torch
+        self.probs = probs
+        self.precision = precision
+        self.maxit = maxit
+        self.dp = R.DeviceProblems(probs)
+        self.J = R.Bsr2.pattern(self.dp)
+        n = 2 * self.dp.ncell
+        self.F = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.b = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.u = torch.as_tensor(np.concatenate([s[0] for s in states]), device="cuda")
+        self.uo = torch.as_tensor(np.concatenate([s[1] for s in states]), device="cuda")
+        self.xout = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in KINDS]
+
+    def run(self):
+        R = self.R
+        R.jacobian_assemble(self.dp, self.u, self.uo, 86400.0, self.J, self.F)
+        self.torch.neg(self.F, out=self.b)
+        recs = []
+        for q, (name, kind, dec) in enumerate(KINDS):
+            self.xout[q].zero_()
+            M = R.Precond(self.J, R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(precision=self.precision)))
+            st = R.gmres_solve(self.J, M, self.b, self.xout[q], R.GmresParams(m=30, maxit=self.maxit, rtol=1e-8))
+            M.close()
+            for k in range(len(self.probs)):
+                recs.append(dict(pc=PC_SCALES[k], prec=name, its=int(st.its[k]), relres=float(st.relres_seg[k]),
+                                 converged=bool(st.relres_seg[k] <= 1e-8)))
+        return recs
+
+
 def flush_l2(buf):
     buf.add_(1.0)
 
@@ -177,6 +218,85 @@ def hbm_peak():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def sweep_roofline(probs, states, precision, reps=50):
+    """Average device duration of the dominant kernel (one hybrid Gauss-Seidel
+    sweep of level 0 of the largest hierarchy in the workload: the SIMPLE Schur
+    complement of the block-factorisation preconditioner), timed with CUDA
+    events on the launching stream over `reps` back-to-back launches, and the
+    block SpMV timed the same way."""
+    import torch
+    from paper_1611_00127_gb300 import rsflow as R
+    dp = R.DeviceProblems(probs[1])
+    J = R.Bsr2.pattern(dp)
+    F = torch.empty(2 * probs[1].ncell, dtype=torch.float64, device="cuda")
+    R.jacobian_assemble(dp, torch.as_tensor(states[1][0], device="cuda"),
+                        torch.as_tensor(states[1][1], device="cuda"), 86400.0, J, F)
+    M = R.Precond(J, R.PrecParams(kind=R.BF, amg=R.AmgParams(precision=precision)))
+    H = M.amg(0)
+    z = torch.empty_like(F)
+    M.apply(F, z)           # leaves a right-hand side on every level
+    H.level_smooth(0, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    by = H.level_smooth(0, reps)
+    e1.record()
+    torch.cuda.synchronize()
+    t_sweep = e0.elapsed_time(e1) / reps
+    y = torch.empty_like(F)
+    for _ in range(3):
+        R.bsr2_spmv(J, F, y)
+    e0.record()
+    for _ in range(reps):
+        R.bsr2_spmv(J, F, y)
+    e1.record()
+    torch.cuda.synchronize()
+    t_spmv = e0.elapsed_time(e1) / reps
+    spmv_bytes = J.nnzb * 36.0 + (J.nb + 1) * 4.0 + J.nb * 32.0
+    n0, nnz0 = H.level_info(0)[:2]
+    M.close()
+    return dict(sweep_ms=t_sweep, sweep_bytes=by, rows=n0, nnz=nnz0, spmv_ms=t_spmv, spmv_bytes=spmv_bytes,
+                nnzb=J.nnzb)
+
+
+def sweep_roofline_3d(precision, n=128, reps=20):
+    """The same sweep on an HBM-resident case: level 0 (A_pp, 2.1M rows) of the
+    CPR hierarchy of the 128^3 layered workload."""
+    import torch
+    from paper_1611_00127_gb300 import inputs as I, rsflow as R
+    p = I.config_layered_3d(n)
+    u, uo = I.front_state(p)
+    dp = R.DeviceProblems(p)
+    J = R.Bsr2.pattern(dp)
+    F = torch.empty(2 * p.ncell, dtype=torch.float64, device="cuda")
+    R.jacobian_assemble(dp, torch.as_tensor(u, device="cuda"), torch.as_tensor(uo, device="cuda"), 86400.0, J, F)
+    M = R.Precond(J, R.PrecParams(kind=R.CPR1, amg=R.AmgParams(theta=0.5, precision=precision)))
+    H = M.amg(0)
+    z = torch.empty_like(F)
+    M.apply(F, z)
+    H.level_smooth(0, 2)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    flush.add_(1.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    by = H.level_smooth(0, reps)
+    e1.record()
+    torch.cuda.synchronize()
+    n0, nnz0 = H.level_info(0)[:2]
+    t = e0.elapsed_time(e1) / reps
+    y = torch.empty_like(F)
+    e0.record()
+    for _ in range(reps):
+        R.bsr2_spmv(J, F, y)
+    e1.record()
+    torch.cuda.synchronize()
+    ts = e0.elapsed_time(e1) / reps
+    sb = J.nnzb * 36.0 + (J.nb + 1) * 4.0 + J.nb * 32.0
+    M.close()
+    return dict(sweep_ms=t, sweep_bytes=by, rows=n0, nnz=nnz0, spmv_ms=ts, spmv_bytes=sb, nnzb=J.nnzb)
 
 
 def profiled_step(step):
@@ -205,10 +325,12 @@ def time_steps(step, steps, warmup, sync_barrier):
         torch.cuda.synchronize()
         sync_barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("step")
         e0.record()
         recs = step.run()
         e1.record()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         total_ms += e0.elapsed_time(e1)
     return total_ms, recs
 
@@ -343,10 +465,14 @@ def main():
     step32 = GpuStep(probs, states, R.FP32, args.maxit)
     ms32, recs32 = time_steps(step32, args.steps, 1, barrier)
     conv32 = sum(r["converged"] for r in recs32)
-    t = torch.tensor([ms64, ms32], dtype=torch.float64, device="cuda")
+    stepb = GpuBatchStep(probs, states, R.FP32, args.maxit)
+    msb, recsb = time_steps(stepb, args.steps, 1, barrier)
+    convb = sum(r["converged"] for r in recsb)
+    t = torch.tensor([ms64, ms32, msb], dtype=torch.float64, device="cuda")
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms64, ms32 = float(t[0]), float(t[1])
+    ms64, ms32, msb = float(t[0]), float(t[1]), float(t[2])
+    valueb = world * convb * args.steps / (msb / 1e3)
     value = world * conv64 * args.steps / (ms64 / 1e3)
     value32 = world * conv32 * args.steps / (ms32 / 1e3)
     e2e = None
@@ -358,12 +484,27 @@ def main():
     prof = profiled_step(step64)
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     peak, peak_kind = hbm_peak()
-    achieved = dom[1][1] / (dom[1][0] * 1e-3) / 1e9 if dom[1][0] > 0 else 0.0
-    roofline = dict(bound="hbm", kernel=dom[0], achieved=achieved, peak=peak, unit="GB/s",
-                    frac=achieved / peak, traffic=None, peak_source=peak_kind,
-                    launches=dom[1][2], ms=dom[1][0],
-                    note="algorithmic bytes of the class over its CUDA-event device time in one profiled step "
-                         "(256x256 working set is L2-resident, so the fraction can exceed HBM)")
+    rl = sweep_roofline(probs, states, R.FP64)
+    achieved = rl["sweep_bytes"] / (rl["sweep_ms"] * 1e-3) / 1e9
+    roofline = dict(bound="hbm", kernel="k_hgs (hybrid multicolour Gauss-Seidel sweep, FP64)",
+                    achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=None,
+                    peak_source=peak_kind, launch_ms=rl["sweep_ms"], bytes_per_launch=rl["sweep_bytes"],
+                    units=f"level 0 of the Schur-complement hierarchy: {rl['rows']} rows, {rl['nnz']} entries",
+                    note="working set of this 256x256 workload is L2-resident (<129 MB); roofline_large repeats "
+                         "the measurement on an HBM-resident 128^3 level")
+    big = None if args.no_large else sweep_roofline_3d(R.FP64)
+    roofline_large = None
+    if big:
+        a2 = big["sweep_bytes"] / (big["sweep_ms"] * 1e-3) / 1e9
+        s2 = big["spmv_bytes"] / (big["spmv_ms"] * 1e-3) / 1e9
+        roofline_large = dict(bound="hbm", kernel="k_hgs FP64, level 0 (A_pp) of the 128^3 layered CPR hierarchy",
+                              achieved=a2, peak=peak, unit="GB/s", frac=a2 / peak, launch_ms=big["sweep_ms"],
+                              bytes_per_launch=big["sweep_bytes"], units=f"{big['rows']} rows, {big['nnz']} entries",
+                              bsr2_spmv=dict(achieved=s2, frac=s2 / peak, launch_ms=big["spmv_ms"],
+                                             bytes_per_launch=big["spmv_bytes"], nnzb=big["nnzb"]),
+                              l2="flushed before the timed launches; working set > L2")
+    spmv = dict(achieved=rl["spmv_bytes"] / (rl["spmv_ms"] * 1e-3) / 1e9, launch_ms=rl["spmv_ms"],
+                bytes_per_launch=rl["spmv_bytes"])
     kernel_profile = {k: dict(ms=v[0], gbs=(v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else 0.0), launches=v[2])
                       for k, v in prof.items() if v[2] > 0}
     cpu = None if args.no_cpu_baseline else oracle_sample(probs, states, args.maxit)
@@ -373,14 +514,22 @@ def main():
         ms_per_step=ms64 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
         data="synthetic",
         config=dict(workload=WORKLOAD, grid=f"{args.n}x{args.n}", solves_per_step=12,
+                    bsr2_lanes_per_row=step64.lanes,
                     converged_per_step=conv64, gmres="FGMRES(30), rtol 1e-8, maxit %d" % args.maxit,
                     vcycle="FP64", l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU"),
         solves=recs64,
         fp32_vcycle=dict(value=value32, ms_per_step=ms32 / args.steps, converged_per_step=conv32, solves=recs32),
+        batched_fp32=dict(value=valueb, ms_per_step=msb / args.steps, converged_per_step=convb,
+                          speedup_vs_fp64_single=valueb / value if value > 0 else None,
+                          how="4 Jacobians stacked as one batch; one setup + one FGMRES call per preconditioner kind",
+                          solves=recsb),
         clocks=clk.summary(),
         roofline=roofline,
-        kernel_profile=kernel_profile,
+        roofline_large=roofline_large,
+        bsr2_spmv=spmv,
+        kernel_profile=dict(note="one eager profiled step, CUDA events per launch (includes launch gaps)",
+                            classes=kernel_profile),
         gpu_launches=int(round(launches / (args.steps + args.warmup))) * args.steps,
         e2e=e2e,
         cpu_baseline=cpu,

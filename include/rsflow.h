@@ -175,9 +175,12 @@ long long rs_launch_count(void);
 int rs_profile_begin(void);
 int rs_profile_end(double *ms, double *bytes, long long *launches, int nclasses);
 
-/* Lanes per block row of the block SpMV (2, 4 or 8; default 4), a tuning
- * knob chosen by measurement. */
+/* Lanes per block row of the block SpMV (1, 2, 4 or 8; default 4), a tuning
+ * knob chosen by measurement; rs_autotune_bsr2 times every choice on J
+ * (CUDA events on `stream`, x and y as work vectors) and keeps the fastest,
+ * returning it in *best. */
 int rs_tune_set_bsr2_lpr(int lanes);
+int rs_autotune_bsr2(const rs_bsr2 *J, const double *x, double *y, int *best, cudaStream_t stream);
 
 /* ---------------------------------------------------------------- grid --- */
 /* Number of stored blocks of the two-point-flux pattern of `nprob` grids
@@ -266,6 +269,12 @@ int amg_level_info(const rs_amg *H, int32_t l, int32_t *n, int32_t *nnz, int32_t
 int amg_level_copy(const rs_amg *H, int32_t l, int32_t *a_row_ptr, int32_t *a_col, double *a_val,
                    int8_t *cf, int32_t *p_row_ptr, int32_t *p_col, double *p_val, int32_t *colour,
                    cudaStream_t stream);
+/* `sweeps` sweeps of level l's smoother on the hierarchy's own work vectors
+ * (right-hand side as left by the last cycle), for measuring the smoother in
+ * isolation; *bytes_per_sweep receives the algorithmic bytes one sweep moves
+ * (matrix entries, row pointers, and the vectors read and written once). */
+int amg_level_smooth(const rs_amg *H, int32_t l, int32_t sweeps, double *bytes_per_sweep, cudaStream_t stream);
+
 /* Hierarchy inside a preconditioner: which = 0 pressure / Schur / black-box,
  * 1 saturation. NULL if absent. */
 const rs_amg *precond_amg(const rs_precond *M, int32_t which);

@@ -111,3 +111,9 @@ extern "C" int amg_level_copy(const rs_amg *H, int32_t l, int32_t *a_row_ptr, in
   RS_CHECK_CUDA(cudaGetLastError());
   return RS_OK;
 }
+
+extern "C" int amg_level_smooth(const rs_amg *H, int32_t l, int32_t sweeps, double *bytes_per_sweep,
+                                cudaStream_t stream) {
+  if (!H || sweeps < 0) return fail(RS_EINVAL, "invalid arguments");
+  return amg_level_sweeps(H->H, l, sweeps, bytes_per_sweep, stream);
+}

@@ -292,10 +292,10 @@ __global__ void k_interp_ext(int32_t n, const int32_t *rp, const int32_t *col, c
 // ordering constraint (gathering Chat_i, the denominators d_k, one lane per
 // k, and the numerators, one lane per target column j, each summing over k
 // ascending), while the single ordered accumulation of dtil is done by lane 0.
-constexpr int kIWarps = 4;
-constexpr int kICand = 512;
-constexpr int kICap = 128;
-constexpr int kIF = 64;
+constexpr int kIWarps = 2;
+constexpr int kICand = 2048;
+constexpr int kICap = 256;
+constexpr int kIF = 256;
 
 struct IWarp {
   int32_t cand[kICand];
@@ -708,6 +708,11 @@ __global__ void __launch_bounds__(256) k_chunk_colour(const int32_t *cr, const i
   for (int32_t t = threadIdx.x; t < len; t += blockDim.x) colour[r0 + t] = cs[t];
 }
 
+__global__ void k_chunk_nnz_max(int32_t nchunk, const int32_t *cr, const int32_t *rp, int32_t *mx) {
+  int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nchunk) atomicMax(mx, rp[cr[2 * k + 1]] - rp[cr[2 * k]]);
+}
+
 __global__ void k_fill_colour(int32_t n, int32_t *c) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) c[i] = -2;
@@ -1073,16 +1078,19 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       Lc.nsmooth = nsm;
       RS_TRY(upload(&Lc.chunk_row0, packed, s));
       RS_TRY(dalloc_n(&Lc.colour, (size_t)n, s));
-      int32_t *cc = nullptr;   // max colour, error flag
-      RS_TRY(sc.get(&cc, 2));
-      RS_CHECK_CUDA(cudaMemsetAsync(cc, 0, 2 * sizeof(int32_t), s));
+      int32_t *cc = nullptr;   // max colour, error flag, largest chunk
+      RS_TRY(sc.get(&cc, 3));
+      RS_CHECK_CUDA(cudaMemsetAsync(cc, 0, 3 * sizeof(int32_t), s));
+      if (Lc.nchunk > 0)
+        RS_COUNTED k_chunk_nnz_max<<<grid_for(Lc.nchunk), kBlock, 0, s>>>(Lc.nchunk, Lc.chunk_row0, Lc.A.rowptr, cc + 2);
       if (n > 0) RS_COUNTED k_fill_colour<<<grid_for(n), kBlock, 0, s>>>(n, Lc.colour);
       if (Lc.nchunk > 0)
         RS_COUNTED k_chunk_colour<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.colour, cc, cc + 1);
-      int32_t hcc[2] = {0, 0};
+      int32_t hcc[3] = {0, 0, 0};
       RS_TRY(sync_copy(hcc, cc, sizeof(hcc), s));
       if (hcc[1]) return fail(RS_ESETUP, "chunk colouring failed on level " + std::to_string(l));
       Lc.ncolour = hcc[0];
+      Lc.chunk_max_nnz = hcc[2];
       RS_TRY(dalloc_n(&Lc.chunk_coff, (size_t)Lc.nchunk * (Lc.ncolour + 1), s));
       RS_TRY(dalloc_n(&Lc.chunk_rows, (size_t)n, s));
       if (Lc.nchunk > 0)

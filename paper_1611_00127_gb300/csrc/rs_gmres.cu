@@ -68,16 +68,21 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const Chunk *__restric
 __global__ void k_reduce(int32_t nseg, const int32_t *__restrict__ seg_chunk, int nvec, int stride,
                          const double *__restrict__ part, double *__restrict__ out, double *__restrict__ H,
                          int ldh_seg, int col, int mode, const uint8_t *__restrict__ active) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per (system, vector): lane l sums chunks l, l+32, ... in order,
+  // then a fixed shuffle tree adds the lanes (deterministic)
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (t >= (int64_t)nseg * nvec) return;
   const int32_t s = (int32_t)(t / nvec);
   const int i = (int)(t % nvec);
   double acc = 0.0;
-  for (int32_t c = seg_chunk[s]; c < seg_chunk[s + 1]; c++) acc += part[(int64_t)c * stride + i];
+  for (int32_t c = seg_chunk[s] + lane; c < seg_chunk[s + 1]; c += 32) acc += part[(int64_t)c * stride + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane != 0) return;
   if (active && !active[s]) acc = 0.0;
   if (mode == 3) {
-    const double nrm = sqrt(acc);
-    out[s] = nrm;
+    out[s] = sqrt(acc);
     return;
   }
   out[(int64_t)s * stride + i] = acc;
@@ -300,7 +305,7 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
   RS_TRY(sc.get(&dsegc, (size_t)nseg + 1));
   RS_TRY(sc.get(&kseg, (size_t)nseg));
   RS_TRY(sc.get(&its, (size_t)nseg));
-  RS_TRY(sc.get(&nact, 1));
+  RS_TRY(sc.get(&nact, 2));
   RS_TRY(sc.get(&active, (size_t)nseg));
   RS_TRY(sc.get(&bad, (size_t)nseg));
   RS_TRY(sc.get(&st, (size_t)nseg));
@@ -312,7 +317,8 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
   const unsigned gseg = grid_for(nseg);
   auto norms = [&](const double *vec, double *out) -> int {
     if (nch > 0) RS_COUNTED k_multidot<<<nch, kRedThreads, 0, s>>>(dch, vec, 0, 1, vec, stride, part);
-    RS_COUNTED k_reduce<<<gseg, kBlock, 0, s>>>(nseg, dsegc, 1, stride, part, out, nullptr, 0, 0, 3, nullptr);
+    RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * 32), kBlock, 0, s>>>(nseg, dsegc, 1, stride, part, out, nullptr, 0,
+                                                                        0, 3, nullptr);
     RS_CHECK_CUDA(cudaGetLastError());
     return 0;
   };
@@ -324,8 +330,15 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
   std::vector<double> htol(nseg);
   for (int32_t q = 0; q < nseg; q++) htol[q] = params->rtol * (hb[q] > 0.0 ? hb[q] : 1.0);
   RS_CHECK_CUDA(cudaMemcpyAsync(tol, htol.data(), sizeof(double) * nseg, cudaMemcpyHostToDevice, s));
-  int32_t *hnact = nullptr;
-  RS_CHECK_CUDA(cudaMallocHost(&hnact, sizeof(int32_t)));
+  // convergence flags come back through pinned memory one iteration late: the
+  // host waits for step j-1's count while step j is already queued, so the GPU
+  // does not idle between steps (a step queued after every system stopped
+  // changes nothing: stopped systems are frozen)
+  static thread_local int32_t *hnact = nullptr;   // pinned, kept for the thread's lifetime
+  if (!hnact) RS_CHECK_CUDA(cudaMallocHost(&hnact, 2 * sizeof(int32_t)));
+  cudaEvent_t evn[2];
+  RS_CHECK_CUDA(cudaEventCreateWithFlags(&evn[0], cudaEventDisableTiming));
+  RS_CHECK_CUDA(cudaEventCreateWithFlags(&evn[1], cudaEventDisableTiming));
   std::vector<int32_t> hits(nseg, 0);
   std::vector<uint8_t> hbad(nseg, 0);
   std::vector<double> hprev(nseg, -1.0);
@@ -374,25 +387,31 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
         ProfScope ps(kProfArnoldi, (nv + 1) * 8.0 * n, s);
         RS_COUNTED k_arnoldi<0><<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, nullptr, stride, w, part);
       }
-      RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * (j + 1)), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part, hbuf,
-                                                                          H, ldh, j, 1, active);
+      RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * (j + 1) * 32), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part,
+                                                                                hbuf, H, ldh, j, 1, active);
       if (nch > 0) {
         ProfScope ps(kProfArnoldi, (2.0 * nv + 2) * 8.0 * n, s);
         RS_COUNTED k_arnoldi<1><<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, hbuf, stride, w, part);
       }
-      RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * (j + 1)), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part, hbuf,
-                                                                          H, ldh, j, 2, active);
+      RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * (j + 1) * 32), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part,
+                                                                                hbuf, H, ldh, j, 2, active);
       if (nch > 0) {
         ProfScope ps(kProfArnoldi, (nv + 2) * 8.0 * n, s);
         RS_COUNTED k_arnoldi<2><<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, hbuf, stride, w, part);
       }
-      RS_COUNTED k_reduce<<<gseg, kBlock, 0, s>>>(nseg, dsegc, 1, stride, part, nrm, nullptr, 0, 0, 3, nullptr);
+      RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * 32), kBlock, 0, s>>>(nseg, dsegc, 1, stride, part, nrm, nullptr, 0,
+                                                                          0, 3, nullptr);
       if (nch > 0) RS_COUNTED k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, w, w);
-      RS_CHECK_CUDA(cudaMemsetAsync(nact, 0, sizeof(int32_t), s));
-      RS_COUNTED k_givens<<<gseg, kBlock, 0, s>>>(nseg, j, m, H, ldh, nrm, st, active, kseg, tol, its, params->maxit, nact, bad);
-      RS_CHECK_CUDA(cudaMemcpyAsync(hnact, nact, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      RS_CHECK_CUDA(cudaStreamSynchronize(s));
-      if (*hnact == 0) break;
+      const int slot = j & 1;
+      RS_CHECK_CUDA(cudaMemsetAsync(nact + slot, 0, sizeof(int32_t), s));
+      RS_COUNTED k_givens<<<gseg, kBlock, 0, s>>>(nseg, j, m, H, ldh, nrm, st, active, kseg, tol, its, params->maxit,
+                                                  nact + slot, bad);
+      RS_CHECK_CUDA(cudaMemcpyAsync(hnact + slot, nact + slot, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      RS_CHECK_CUDA(cudaEventRecord(evn[slot], s));
+      if (j >= 1) {
+        RS_CHECK_CUDA(cudaEventSynchronize(evn[slot ^ 1]));
+        if (hnact[slot ^ 1] == 0) break;
+      }
     }
     if (rc) break;
     RS_COUNTED k_backsolve<<<gseg, kBlock, 0, s>>>(nseg, m, H, ldh, st, kseg, y);
@@ -400,7 +419,8 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
     RS_CHECK_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * nseg * ldh, s));
     RS_CHECK_CUDA(cudaGetLastError());
   }
-  cudaFreeHost(hnact);
+  cudaEventDestroy(evn[0]);
+  cudaEventDestroy(evn[1]);
   if (rc) return rc;
   int32_t conv = 0, itmax = 0;
   double rmax = 0.0;

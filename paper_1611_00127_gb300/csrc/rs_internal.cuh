@@ -61,6 +61,34 @@ void count_launches(long long n);
 #define RS_COUNTED ::rs::count_launch(),
 constexpr int kBlock = 256;
 
+// Programmatic dependent launch: kernels launched with launch_pdl may be
+// scheduled while their predecessor in the stream is still running; every such
+// kernel starts with RS_PDL_ENTRY, which waits until the predecessor has
+// finished and its writes are visible (so data dependences are unchanged) and
+// then lets its own successor be scheduled, so each launch's latency overlaps
+// the previous kernel's execution with at most one kernel waiting ahead.
+#define RS_PDL_ENTRY()                                            \
+  do {                                                            \
+    asm volatile("griddepcontrol.wait;" ::: "memory");           \
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
+  } while (0)
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // ------------------------------------------------------------------ profiling
 // When profiling is on (rs_profile_begin), launches of the main kernel classes
 // are bracketed by CUDA events on their stream and their algorithmic bytes are
@@ -142,6 +170,7 @@ struct Level {
   double *cinv = nullptr;            // stacked dense inverses, row-major
   // hybrid smoother: chunks of consecutive rows (never spanning two systems)
   int32_t nchunk = 0;
+  int32_t chunk_max_nnz = 0;         // largest number of matrix entries in one chunk
   int32_t *chunk_row0 = nullptr;     // [2 nchunk] (first row, end row) of each chunk
   int32_t *chunk_coff = nullptr;     // [nchunk * (ncolour+1)] colour offsets inside each chunk
   int32_t *chunk_rows = nullptr;     // [n] local row of each position, sorted by (chunk, colour, row)
@@ -164,6 +193,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off, const rs_amg_
 void amg_free(Hier &H, cudaStream_t s);
 // x = V-cycle(b); FP64 in/out. `xin_zero` is always true here (zero guess).
 int amg_vcycle(const Hier &H, const double *b, double *x, cudaStream_t s);
+int amg_level_sweeps(const Hier &H, int32_t l, int sweeps, double *bytes_per_sweep, cudaStream_t s);
 
 // ------------------------------------------------------------------ helpers
 std::vector<int32_t> seg_offsets(int32_t n, int32_t nseg, const int32_t *seg_off);

@@ -158,8 +158,9 @@ int block_diag_inverse(const rs_bsr2 &J, double *dinv, cudaStream_t s) {
 constexpr int kHash = 2048;
 constexpr int kGemmWarps = 2;
 
-__device__ __forceinline__ int hslot(int32_t key) {
-  return (int)(((uint32_t)key * 2654435761u) >> (32 - 11));
+// table of `tsize` slots (a power of two, 32..kHash) sized per row
+__device__ __forceinline__ int hslot(int32_t key, int tbits) {
+  return (int)(((uint32_t)key * 2654435761u) >> (32 - tbits));
 }
 
 template <bool NUMERIC>
@@ -177,17 +178,27 @@ __global__ void __launch_bounds__(32 * kGemmWarps) k_spgemm(int32_t n, const int
   double *vals = reinterpret_cast<double *>(smem + sizeof(int32_t) * kHash * kGemmWarps) + warp * kHash;
   __shared__ int32_t cnt_s[kGemmWarps];
   for (int32_t row = blockIdx.x * kGemmWarps + warp; row < n; row += gridDim.x * kGemmWarps) {
-    for (int h = lane; h < kHash; h += 32) keys[h] = -1;
+    const int32_t as = arp[row], ae = arp[row + 1];
+    // upper bound of distinct columns: the number of products
+    int32_t np = 0;
+    for (int32_t ka = as + lane; ka < ae; ka += 32) {
+      const int32_t k = acol[ka];
+      np += brp[k + 1] - brp[k];
+    }
+    np = __reduce_add_sync(0xffffffffu, np);
+    int tbits = 5;
+    while (tbits < 11 && (1 << tbits) < 2 * np) tbits++;
+    const int tsize = 1 << tbits;
+    for (int h = lane; h < tsize; h += 32) keys[h] = -1;
     if (lane == 0) cnt_s[warp] = 0;
     __syncwarp();
-    const int32_t as = arp[row], ae = arp[row + 1];
     for (int32_t ka = as; ka < ae; ka++) {
       const int32_t k = acol[ka];
       const double a = aval[ka];
       const int32_t bs = brp[k], be = brp[k + 1];
       for (int32_t kb = bs + lane; kb < be; kb += 32) {
         const int32_t j = bcol[kb];
-        int h = hslot(j);
+        int h = hslot(j, tbits);
         int probes = 0;
         for (;;) {
           int32_t prev = atomicCAS(&keys[h], -1, j);
@@ -200,15 +211,15 @@ __global__ void __launch_bounds__(32 * kGemmWarps) k_spgemm(int32_t n, const int
             if (NUMERIC) vals[h] = vals[h] + a * bval[kb];
             break;
           }
-          h = (h + 1) & (kHash - 1);
-          if (++probes >= kHash / 2) { atomicExch(err, 1); break; }
+          h = (h + 1) & (tsize - 1);
+          if (++probes >= tsize) { atomicExch(err, 1); break; }
         }
       }
       __syncwarp();
     }
     __syncwarp();
     const int32_t cnt = cnt_s[warp];
-    if (cnt > kHash / 2 && lane == 0) atomicExch(err, 1);
+    if (cnt > tsize && lane == 0) atomicExch(err, 1);
     if (!NUMERIC) {
       if (lane == 0) crp[row] = cnt;
     } else {
@@ -216,7 +227,7 @@ __global__ void __launch_bounds__(32 * kGemmWarps) k_spgemm(int32_t n, const int
       // slot moves only to a lower index, after the whole warp has read its
       // chunk), then rank each entry by column and scatter to the output row
       int32_t base_c = 0;
-      for (int h0 = 0; h0 < kHash; h0 += 32) {
+      for (int h0 = 0; h0 < tsize; h0 += 32) {
         const int32_t j = keys[h0 + lane];
         const double v = NUMERIC ? vals[h0 + lane] : 0.0;
         const unsigned occ = __ballot_sync(0xffffffffu, j >= 0);

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_bsr2_spmv(int32_t nb, const int32_t *__
 static int g_bsr2_lpr = 4;   // lanes per block row; set by the tuner
 
 extern "C" int rs_tune_set_bsr2_lpr(int lpr) {
-  if (lpr != 2 && lpr != 4 && lpr != 8) return RS_EINVAL;
+  if (lpr != 1 && lpr != 2 && lpr != 4 && lpr != 8) return RS_EINVAL;
   g_bsr2_lpr = lpr;
   return RS_OK;
 }
@@ -64,6 +64,7 @@ static int launch(const rs_bsr2 &J, const double *x, const double *b, double *y,
   const unsigned grid = grid_for(threads);
   ProfScope ps(kProfBsr2, J.nnzb * 36.0 + (J.nb + 1) * 4.0 + J.nb * (RESID ? 48.0 : 32.0), s);
   switch (g_bsr2_lpr) {
+    case 1: RS_COUNTED k_bsr2_spmv<1, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
     case 2: RS_COUNTED k_bsr2_spmv<2, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
     case 8: RS_COUNTED k_bsr2_spmv<8, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
     default: RS_COUNTED k_bsr2_spmv<4, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
@@ -101,4 +102,33 @@ extern "C" int bsr2_residual(const rs_bsr2 *J, const double *x, const double *b,
   RS_TRY(check_bsr2(J));
   if (!x || !b || !r) return fail(RS_EINVAL, "null vector");
   return launch_bsr2_residual(*J, x, b, r, stream);
+}
+
+// Autotuner: times y = J x for each lanes-per-row choice (CUDA events on the
+// caller's stream, after a warm-up) and keeps the fastest.
+extern "C" int rs_autotune_bsr2(const rs_bsr2 *J, const double *x, double *y, int *best, cudaStream_t stream) {
+  RS_TRY(check_bsr2(J));
+  if (!x || !y) return fail(RS_EINVAL, "null vector");
+  const int cand[4] = {1, 2, 4, 8};
+  float bt = 1e30f;
+  int bl = g_bsr2_lpr;
+  cudaEvent_t e0, e1;
+  RS_CHECK_CUDA(cudaEventCreate(&e0));
+  RS_CHECK_CUDA(cudaEventCreate(&e1));
+  for (int c : cand) {
+    g_bsr2_lpr = c;
+    for (int w = 0; w < 3; w++) RS_TRY(launch_bsr2_spmv(*J, x, y, stream));
+    RS_CHECK_CUDA(cudaEventRecord(e0, stream));
+    for (int r = 0; r < 10; r++) RS_TRY(launch_bsr2_spmv(*J, x, y, stream));
+    RS_CHECK_CUDA(cudaEventRecord(e1, stream));
+    RS_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RS_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < bt) { bt = ms; bl = c; }
+  }
+  g_bsr2_lpr = bl;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best) *best = bl;
+  return RS_OK;
 }

@@ -10,6 +10,8 @@
 // colour coupled, so each sweep is an exact Gauss-Seidel update in colour
 // order), residual, restriction by R = P^T, recursion, prolongation with
 // correction, post-sweeps.
+#include <algorithm>
+
 #include "rs_internal.cuh"
 
 namespace rs {
@@ -57,31 +59,33 @@ constexpr int kHgsStageEntries = 12288;
 constexpr int kHgsMaxColours = 128;
 
 template <typename T>
-constexpr size_t hgs_smem(int cmax) {
-  return sizeof(T) * 3 * (size_t)cmax + sizeof(T) * (size_t)kHgsStageEntries +
-         sizeof(int32_t) * ((size_t)kHgsStageEntries + 2 * (size_t)cmax + 1 + kHgsMaxColours + 1) + 64;
+constexpr size_t hgs_smem(int cmax, int stage) {
+  return sizeof(T) * 3 * (size_t)cmax + sizeof(T) * (size_t)stage +
+         sizeof(int32_t) * ((size_t)stage + 2 * (size_t)cmax + 1 + kHgsMaxColours + 1) + 64;
 }
 
 template <typename T, int LPR>
 __global__ void __launch_bounds__(256) k_hgs(const int32_t *__restrict__ cr, const int32_t *__restrict__ coff,
                                              const int32_t *__restrict__ crows, int32_t ncol, int32_t cmax,
+                                             int32_t stage_cap,
                                              const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                              const T *__restrict__ val, const T *__restrict__ dinv,
                                              const T *__restrict__ b, const T *__restrict__ xold,
                                              T *__restrict__ xnew) {
+  RS_PDL_ENTRY();
   extern __shared__ __align__(16) unsigned char smem[];
   T *xs = reinterpret_cast<T *>(smem);               // chunk unknowns
   T *rhs = xs + cmax;                                // b_i - (out-of-chunk part of row i)
   T *dv = rhs + cmax;                                // 1 / a_ii
   T *sval = dv + cmax;                               // staged values / out-of-chunk products
-  int32_t *scol = reinterpret_cast<int32_t *>(sval + kHgsStageEntries);   // local column or -1
-  int32_t *lrp = scol + kHgsStageEntries;            // staged row starts [len+1]
+  int32_t *scol = reinterpret_cast<int32_t *>(sval + stage_cap);   // local column or -1
+  int32_t *lrp = scol + stage_cap;                   // staged row starts [len+1]
   int32_t *srows = lrp + cmax + 1;                   // rows by colour
   int32_t *scof = srows + cmax;                      // colour offsets [ncol+1]
   const int32_t k = blockIdx.x;
   const int32_t r0 = __ldg(cr + 2 * k), r1 = __ldg(cr + 2 * k + 1), len = r1 - r0;
   const int32_t q0 = __ldg(rp + r0), nnz = __ldg(rp + r1) - q0;
-  const bool staged = nnz <= kHgsStageEntries;
+  const bool staged = nnz <= stage_cap;
   const int32_t *cof = coff + (int64_t)k * (ncol + 1);
   // flat loads
   for (int32_t t = threadIdx.x; t <= len; t += blockDim.x) {
@@ -94,14 +98,35 @@ __global__ void __launch_bounds__(256) k_hgs(const int32_t *__restrict__ cr, con
     }
   }
   for (int32_t c = threadIdx.x; c <= ncol; c += blockDim.x) scof[c] = __ldg(cof + c);
-  if (staged)
-    for (int32_t q = threadIdx.x; q < nnz; q += blockDim.x) {
-      const int32_t j = __ldg(col + q0 + q);
-      const T a = __ldg(val + q0 + q);
-      const bool in = j >= r0 && j < r1;
-      scol[q] = in ? j - r0 : -1;
-      sval[q] = in ? a : (xold ? a * __ldg(xold + j) : T(0));
+  if (staged) {
+    // four entries per thread in flight: columns and values, then the gathers
+    const int32_t bd = blockDim.x;
+    for (int32_t qb = threadIdx.x; qb < nnz; qb += 4 * bd) {
+      int32_t jj[4];
+      T aa[4], xx[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int32_t q = qb + u * bd;
+        jj[u] = q < nnz ? __ldg(col + q0 + q) : r0;
+        aa[u] = q < nnz ? __ldg(val + q0 + q) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const bool in = jj[u] >= r0 && jj[u] < r1;
+        xx[u] = (!in && xold) ? __ldg(xold + jj[u]) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int32_t q = qb + u * bd;
+        if (q < nnz) {
+          const bool in = jj[u] >= r0 && jj[u] < r1;
+          scol[q] = in ? jj[u] - r0 : -1;
+          if (in) sval[q] = aa[u];
+          else sval[q] = aa[u] * xx[u];
+        }
+      }
     }
+  }
   __syncthreads();
   const int group = threadIdx.x / LPR, lane = threadIdx.x % LPR, ngroups = blockDim.x / LPR;
   // out-of-chunk sums (uniform trip count: the group shuffles see whole warps)
@@ -195,6 +220,7 @@ template <typename T, int LPR, int MODE>
 __global__ void __launch_bounds__(256) k_csr(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                              const T *__restrict__ val, const T *__restrict__ x,
                                              const T *__restrict__ b, T *__restrict__ y) {
+  RS_PDL_ENTRY();
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = tid / LPR;
   const int lane = threadIdx.x % LPR;
@@ -217,6 +243,7 @@ template <typename T>
 __global__ void k_coarse_solve(int32_t nrows, const int32_t *__restrict__ crows, const int32_t *__restrict__ crow_seg,
                                const int4 *__restrict__ info, const int64_t *__restrict__ inv_off,
                                const double *__restrict__ inv, const T *__restrict__ b, T *__restrict__ x) {
+  RS_PDL_ENTRY();
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= nrows) return;
@@ -234,12 +261,24 @@ __global__ void k_coarse_solve(int32_t nrows, const int32_t *__restrict__ crows,
 
 template <typename A, typename B>
 __global__ void k_cast(int64_t n, const A *__restrict__ a, B *__restrict__ b) {
+  RS_PDL_ENTRY();
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (B)a[i];
 }
 
+// Lanes per row. FP32: enough lanes to cover a row in one or two steps.
+// FP64: GB300's FP64 pipe issues about 2 lanes per clock per SM, so every
+// warp-wide FP64 instruction is costly even with idle lanes; FP64 kernels use
+// one lane per row (two or four for long rows), which needs no FP64
+// shuffle-reduction additions.
+template <typename T>
 static int pick_lpr(int32_t n, int32_t nnz) {
   const double avg = n > 0 ? (double)nnz / n : 1.0;
+  if (sizeof(T) == 8) {
+    if (avg <= 32.0) return 1;
+    if (avg <= 128.0) return 2;
+    return 4;
+  }
   if (avg <= 6.0) return 4;
   if (avg <= 14.0) return 8;
   if (avg <= 40.0) return 16;
@@ -248,6 +287,8 @@ static int pick_lpr(int32_t n, int32_t nnz) {
 
 #define RS_LPR_SWITCH(lpr, ...)                  \
   switch (lpr) {                                 \
+    case 1: { constexpr int L_ = 1; __VA_ARGS__; } break;   \
+    case 2: { constexpr int L_ = 2; __VA_ARGS__; } break;   \
     case 4: { constexpr int L_ = 4; __VA_ARGS__; } break;   \
     case 8: { constexpr int L_ = 8; __VA_ARGS__; } break;   \
     case 16: { constexpr int L_ = 16; __VA_ARGS__; } break; \
@@ -272,7 +313,8 @@ template <typename T, int LPR>
 static void hgs_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_hgs<T, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hgs_smem<T>(1024));
+    cudaFuncSetAttribute(k_hgs<T, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)hgs_smem<T>(512, kHgsStageEntries));
     done = true;
   }
 }
@@ -282,7 +324,7 @@ static void hgs_attr() {
 template <typename T>
 static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStream_t s) {
   if (sweeps <= 0) return;
-  const int lpr = pick_lpr(L.A.n, L.A.nnz);
+  const int lpr = pick_lpr<T>(L.A.n, L.A.nnz);
   const T *val = vals<T>(L.A);
   const T *dinv = dinv_of<T>(L);
   const T *b = static_cast<const T *>(L.b);
@@ -295,15 +337,16 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
     return;
   }
   if (H.prm.smoother == RS_SMOOTH_HYBRID) {
-    const size_t shm = hgs_smem<T>(H.prm.chunk);
+    const int32_t stage = std::min(L.chunk_max_nnz, kHgsStageEntries);
+    const size_t shm = hgs_smem<T>(H.prm.chunk, stage);
     const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
     for (int sw = 0; sw < sweeps; sw++) {
       T *out = (cur == xa) ? xb : xa;
       const double bytes = nz * (4.0 + sizeof(T)) + (ns + 1) * 4.0 + ns * 4.0 + ns * sizeof(T) * (cur ? 4.0 : 3.0);
       ProfScope ps(kProfHgs, bytes, s);
-      RS_LPR_SWITCH(lpr, hgs_attr<T, L_>(); RS_COUNTED k_hgs<T, L_><<<L.nchunk, 256, shm, s>>>(
-                             L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, H.prm.chunk, L.A.rowptr,
-                             L.A.col, val, dinv, b, cur, out));
+      RS_LPR_SWITCH(lpr, hgs_attr<T, L_>(); RS_COUNTED launch_pdl(k_hgs<T, L_>, dim3(L.nchunk), dim3(256), shm, s,
+                             L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, H.prm.chunk, stage, L.A.rowptr,
+                             L.A.col, val, dinv, b, (const T *)cur, out));
       cur = out;
     }
     return;
@@ -346,32 +389,53 @@ static T *cycle(const Hier &H, int32_t l, cudaStream_t s) {
     const Level &N = H.L[l + 1];
     T *r = static_cast<T *>(L.r);
     const double sz = sizeof(T);
-    const int lpr = pick_lpr(L.A.n, L.A.nnz);
+    const int lpr = pick_lpr<T>(L.A.n, L.A.nnz);
     {
       ProfScope ps(kProfCsr, L.A.nnz * (4.0 + sz) + (L.A.n + 1) * 4.0 + 3.0 * L.A.n * sz, s);
-      RS_LPR_SWITCH(lpr, RS_COUNTED k_csr<T, L_, 1><<<grid_for((int64_t)L.A.n * L_), kBlock, 0, s>>>(
-                             L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), cur, static_cast<const T *>(L.b), r));
+      RS_LPR_SWITCH(lpr, RS_COUNTED launch_pdl(k_csr<T, L_, 1>, dim3(grid_for((int64_t)L.A.n * L_)), dim3(kBlock), 0, s,
+                             L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), (const T *)cur, static_cast<const T *>(L.b), r));
     }
-    const int lr = pick_lpr(L.R.n, L.R.nnz);
+    const int lr = pick_lpr<T>(L.R.n, L.R.nnz);
     {
       ProfScope ps(kProfCsr, L.R.nnz * (4.0 + sz) + (L.R.n + 1) * 4.0 + (L.R.n + L.A.n) * sz, s);
-      RS_LPR_SWITCH(lr, RS_COUNTED k_csr<T, L_, 0><<<grid_for((int64_t)L.R.n * L_), kBlock, 0, s>>>(
-                            L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), r, nullptr, static_cast<T *>(N.b)));
+      RS_LPR_SWITCH(lr, RS_COUNTED launch_pdl(k_csr<T, L_, 0>, dim3(grid_for((int64_t)L.R.n * L_)), dim3(kBlock), 0, s,
+                            L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), (const T *)r, (const T *)nullptr, static_cast<T *>(N.b)));
     }
     const T *xc = cycle<T>(H, l + 1, s);
-    const int lp = pick_lpr(L.P.n, L.P.nnz);
+    const int lp = pick_lpr<T>(L.P.n, L.P.nnz);
     {
       ProfScope ps(kProfCsr, L.P.nnz * (4.0 + sz) + (L.P.n + 1) * 4.0 + (2.0 * L.P.n + L.R.n) * sz, s);
-      RS_LPR_SWITCH(lp, RS_COUNTED k_csr<T, L_, 2><<<grid_for((int64_t)L.P.n * L_), kBlock, 0, s>>>(
-                            L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P), xc, nullptr, cur));
+      RS_LPR_SWITCH(lp, RS_COUNTED launch_pdl(k_csr<T, L_, 2>, dim3(grid_for((int64_t)L.P.n * L_)), dim3(kBlock), 0, s,
+                            L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P), xc, (const T *)nullptr, cur));
     }
   }
   smooth<T>(H, L, H.prm.nu2, cur, s);
   if (L.ncoarse_rows > 0) {
-    RS_COUNTED k_coarse_solve<T><<<grid_for((int64_t)L.ncoarse_rows * 32), kBlock, 0, s>>>(
-        L.ncoarse_rows, L.crows, L.crow_seg, L.cinfo, L.cinv_off, L.cinv, static_cast<const T *>(L.b), cur);
+    RS_COUNTED launch_pdl(k_coarse_solve<T>, dim3(grid_for((int64_t)L.ncoarse_rows * 32)), dim3(kBlock), 0, s,
+        L.ncoarse_rows, (const int32_t *)L.crows, (const int32_t *)L.crow_seg, (const int4 *)L.cinfo,
+        (const int64_t *)L.cinv_off, (const double *)L.cinv, static_cast<const T *>(L.b), cur);
   }
   return cur;
+}
+
+// Sweeps of level l's smoother on the hierarchy's own vectors (right-hand
+// side b_l as left by the last cycle, iterate x_l), for measurement.
+template <typename T>
+static double level_sweeps(const Hier &H, int32_t l, int sweeps, cudaStream_t s) {
+  const Level &L = H.L[l];
+  T *cur = static_cast<T *>(L.x);
+  smooth<T>(H, L, sweeps, cur, s);
+  const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
+  return nz * (4.0 + sizeof(T)) + (ns + 1) * 4.0 + ns * 4.0 + ns * sizeof(T) * 4.0;
+}
+
+int amg_level_sweeps(const Hier &H, int32_t l, int sweeps, double *bytes_per_sweep, cudaStream_t s) {
+  if (l < 0 || l >= H.nlev) return fail(RS_EINVAL, "level out of range");
+  const double by = H.precision == RS_PREC_FP32 ? level_sweeps<float>(H, l, sweeps, s)
+                                                : level_sweeps<double>(H, l, sweeps, s);
+  if (bytes_per_sweep) *bytes_per_sweep = by;
+  RS_CHECK_CUDA(cudaGetLastError());
+  return 0;
 }
 
 int amg_vcycle(const Hier &H, const double *b, double *x, cudaStream_t s) {
@@ -380,9 +444,9 @@ int amg_vcycle(const Hier &H, const double *b, double *x, cudaStream_t s) {
   const int64_t n = L0.A.n;
   if (n == 0) return 0;
   if (H.precision == RS_PREC_FP32) {
-    RS_COUNTED k_cast<double, float><<<grid_for(n), kBlock, 0, s>>>(n, b, static_cast<float *>(L0.b));
+    RS_COUNTED launch_pdl(k_cast<double, float>, dim3(grid_for(n)), dim3(kBlock), 0, s, n, b, static_cast<float *>(L0.b));
     const float *x0 = cycle<float>(H, 0, s);
-    RS_COUNTED k_cast<float, double><<<grid_for(n), kBlock, 0, s>>>(n, x0, x);
+    RS_COUNTED launch_pdl(k_cast<float, double>, dim3(grid_for(n)), dim3(kBlock), 0, s, n, x0, x);
   } else {
     RS_CHECK_CUDA(cudaMemcpyAsync(L0.b, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     const double *x0 = cycle<double>(H, 0, s);

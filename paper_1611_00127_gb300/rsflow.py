@@ -112,6 +112,7 @@ def _declare(L):
         "amg_levels": (C.c_int, [P, P]),
         "amg_level_info": (C.c_int, [P, i32, P, P, P, P]),
         "amg_level_copy": (C.c_int, [P, i32, P, P, P, P, P, P, P, P, P]),
+        "amg_level_smooth": (C.c_int, [P, i32, i32, P, P]),
         "precond_create": (C.c_int, [P, P, P, P]),
         "precond_destroy": (C.c_int, [P]),
         "precond_apply": (C.c_int, [P, P, P, P]),
@@ -121,6 +122,7 @@ def _declare(L):
         "bsr2_spmv": (C.c_int, [P, P, P, P]),
         "bsr2_residual": (C.c_int, [P, P, P, P, P]),
         "rs_tune_set_bsr2_lpr": (C.c_int, [C.c_int]),
+        "rs_autotune_bsr2": (C.c_int, [P, P, P, P, P]),
         "rs_launch_count": (C.c_longlong, []),
         "rs_profile_begin": (C.c_int, []),
         "rs_profile_end": (C.c_int, [P, P, P, C.c_int]),
@@ -361,6 +363,12 @@ class Amg:
                "amg_level_info")
         return n.value, nnz.value, nnzp.value, nc.value
 
+    def level_smooth(self, l: int, sweeps: int, stream=None) -> float:
+        """Run smoother sweeps on level l's own vectors; returns bytes per sweep."""
+        by = C.c_double()
+        _check(lib().amg_level_smooth(self.h, l, sweeps, C.byref(by), _stream(stream)), "amg_level_smooth")
+        return by.value
+
     def sizes(self) -> List[int]:
         return [self.level_info(l)[0] for l in range(self.nlevels)]
 
@@ -457,6 +465,14 @@ def profile_end():
 
 def launch_count() -> int:
     return int(lib().rs_launch_count())
+
+
+def autotune_bsr2(J: Bsr2, x: torch.Tensor, y: torch.Tensor, stream=None) -> int:
+    """Pick the fastest lanes-per-row for y = J x on this matrix; returns it."""
+    best = C.c_int()
+    Jc = J.c()
+    _check(lib().rs_autotune_bsr2(C.byref(Jc), _ptr(x), _ptr(y), C.byref(best), _stream(stream)), "rs_autotune_bsr2")
+    return best.value
 
 
 def set_bsr2_lanes(lpr: int):

@@ -78,7 +78,7 @@ def test_bsr2_spmv_and_residual(R, oracle, inputs):
         x = inputs.rhs_vector(2 * p.ncell, 1)
         b = inputs.rhs_vector(2 * p.ncell, 2)
         y = torch.empty(2 * p.ncell, dtype=torch.float64, device="cuda")
-        for lanes in (2, 4, 8):
+        for lanes in (1, 2, 4, 8):
             R.set_bsr2_lanes(lanes)
             R.bsr2_spmv(J, _dev(x), y)
             yo = oracle.bsr2_spmv(rp, col, Jo, x)
@@ -296,3 +296,38 @@ def test_newton_step_matches_oracle(R, oracle, inputs):
     assert oracle.scaled_fnorm(p, F, inputs.DAY) <= 1e-6
     np.testing.assert_allclose(ug[0::2], uo[0::2], rtol=1e-7)
     np.testing.assert_allclose(ug[1::2], uo[1::2], atol=1e-7)
+
+
+def test_precond_hierarchies_bit_exact_3d(R, oracle, inputs):
+    """3D layered field (7-point J, dense coarse rows): the CPR and BF
+    hierarchies built on the device match the oracle's bit for bit."""
+    p = inputs.config_layered_3d(n=16, layers=4)
+    u, uo = inputs.front_state(p)
+    Fo, Jo, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
+    J = R.Bsr2.from_host(rp, col, Jo)
+    for kind, dec in ((1, 2), (3, 0)):
+        gM = R.Precond(J, R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(theta=0.5, precision=R.FP64)))
+        oM = oracle.Precond(rp, col, Jo, oracle.PrecParams(kind=kind, decouple=dec, amg=oracle.AmgParams(theta=0.5)))
+        _hier_compare(gM.amg(0), oM.amg(0))
+        if kind == 3:
+            _hier_compare(gM.amg(1), oM.amg(1))
+
+
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_gmres_3d_matches_oracle(R, oracle, inputs, prec):
+    p = inputs.config_layered_3d(n=16, layers=4)
+    u, uo = inputs.front_state(p)
+    Fo, Jo, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
+    J = R.Bsr2.from_host(rp, col, Jo)
+    b = -Fo
+    x = torch.zeros(2 * p.ncell, dtype=torch.float64, device="cuda")
+    M = R.Precond(J, R.PrecParams(kind=R.CPR1, amg=R.AmgParams(theta=0.5, precision=getattr(R, prec))))
+    st = R.gmres_solve(J, M, _dev(b), x, R.GmresParams(rtol=1e-8, maxit=500))
+    assert st.status == R.RS_OK, st
+    xg = x.cpu().numpy()
+    res = b - oracle.bsr2_spmv(rp, col, Jo, xg)
+    assert np.linalg.norm(res) <= 1.0001e-8 * np.linalg.norm(b)
+    xo, sto, _, _ = oracle.fgmres(rp, col, Jo, b, oracle.Precond(rp, col, Jo, oracle.PrecParams(
+        kind=1, decouple=2, amg=oracle.AmgParams(theta=0.5))), maxit=500)
+    assert sto == 0
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-6
