@@ -160,10 +160,12 @@ class GpuStep:
             R.jacobian_assemble(dps[k], us[k], uos[k], 86400.0, self.J, self.F)
             torch.neg(self.F, out=self.b)
             for name, kind, dec in KINDS:
+                torch.cuda.nvtx.range_push(f"pc{PC_SCALES[k]:g}_{name}")
                 self.xout[q].zero_()
                 M = R.Precond(self.J, self.params(kind, dec))
                 st = R.gmres_solve(self.J, M, self.b, self.xout[q], R.GmresParams(m=30, maxit=self.maxit, rtol=1e-8))
                 M.close()
+                torch.cuda.nvtx.range_pop()
                 recs.append(dict(pc=PC_SCALES[k], prec=name, its=int(st.iterations), relres=float(st.relres),
                                  converged=bool(st.converged == 1)))
                 q += 1
@@ -263,40 +265,10 @@ def sweep_roofline(probs, states, precision, reps=50):
 
 def sweep_roofline_3d(precision, n=128, reps=20):
     """The same sweep on an HBM-resident case: level 0 (A_pp, 2.1M rows) of the
-    CPR hierarchy of the 128^3 layered workload."""
-    import torch
-    from paper_1611_00127_gb300 import inputs as I, rsflow as R
-    p = I.config_layered_3d(n)
-    u, uo = I.front_state(p)
-    dp = R.DeviceProblems(p)
-    J = R.Bsr2.pattern(dp)
-    F = torch.empty(2 * p.ncell, dtype=torch.float64, device="cuda")
-    R.jacobian_assemble(dp, torch.as_tensor(u, device="cuda"), torch.as_tensor(uo, device="cuda"), 86400.0, J, F)
-    M = R.Precond(J, R.PrecParams(kind=R.CPR1, amg=R.AmgParams(theta=0.5, precision=precision)))
-    H = M.amg(0)
-    z = torch.empty_like(F)
-    M.apply(F, z)
-    H.level_smooth(0, 2)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    flush.add_(1.0)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    by = H.level_smooth(0, reps)
-    e1.record()
-    torch.cuda.synchronize()
-    n0, nnz0 = H.level_info(0)[:2]
-    t = e0.elapsed_time(e1) / reps
-    y = torch.empty_like(F)
-    e0.record()
-    for _ in range(reps):
-        R.bsr2_spmv(J, F, y)
-    e1.record()
-    torch.cuda.synchronize()
-    ts = e0.elapsed_time(e1) / reps
-    sb = J.nnzb * 36.0 + (J.nb + 1) * 4.0 + J.nb * 32.0
-    M.close()
-    return dict(sweep_ms=t, sweep_bytes=by, rows=n0, nnz=nnz0, spmv_ms=ts, spmv_bytes=sb, nnzb=J.nnzb)
+    CPR hierarchy of the 128^3 layered workload, L2 flushed before the loop."""
+    from paper_1611_00127_gb300 import kernel_bench
+    from paper_1611_00127_gb300 import rsflow as R
+    return kernel_bench.layered(n, precision, R.CPR1, reps)
 
 
 def profiled_step(step):
@@ -492,17 +464,20 @@ def main():
                     units=f"level 0 of the Schur-complement hierarchy: {rl['rows']} rows, {rl['nnz']} entries",
                     note="working set of this 256x256 workload is L2-resident (<129 MB); roofline_large repeats "
                          "the measurement on an HBM-resident 128^3 level")
-    big = None if args.no_large else sweep_roofline_3d(R.FP64)
     roofline_large = None
-    if big:
-        a2 = big["sweep_bytes"] / (big["sweep_ms"] * 1e-3) / 1e9
-        s2 = big["spmv_bytes"] / (big["spmv_ms"] * 1e-3) / 1e9
-        roofline_large = dict(bound="hbm", kernel="k_hgs FP64, level 0 (A_pp) of the 128^3 layered CPR hierarchy",
-                              achieved=a2, peak=peak, unit="GB/s", frac=a2 / peak, launch_ms=big["sweep_ms"],
-                              bytes_per_launch=big["sweep_bytes"], units=f"{big['rows']} rows, {big['nnz']} entries",
-                              bsr2_spmv=dict(achieved=s2, frac=s2 / peak, launch_ms=big["spmv_ms"],
-                                             bytes_per_launch=big["spmv_bytes"], nnzb=big["nnzb"]),
-                              l2="flushed before the timed launches; working set > L2")
+    if not args.no_large:
+        roofline_large = {}
+        for pname, prec in (("fp64", R.FP64), ("fp32", R.FP32)):
+            big = sweep_roofline_3d(prec)
+            a2 = big["sweep_bytes"] / (big["sweep_ms"] * 1e-3) / 1e9
+            s2 = big["spmv_bytes"] / (big["spmv_ms"] * 1e-3) / 1e9
+            roofline_large[pname] = dict(
+                bound="hbm", kernel=f"k_hgs {pname.upper()}, level 0 (A_pp) of the 128^3 layered CPR hierarchy",
+                achieved=a2, peak=peak, unit="GB/s", frac=a2 / peak, launch_ms=big["sweep_ms"],
+                bytes_per_launch=big["sweep_bytes"], units=f"{big['rows']} rows, {big['nnz']} entries",
+                bsr2_spmv=dict(achieved=s2, frac=s2 / peak, launch_ms=big["spmv_ms"],
+                               bytes_per_launch=big["spmv_bytes"], nnzb=big["nnzb"]),
+                l2="flushed before the timed launches; working set > L2")
     spmv = dict(achieved=rl["spmv_bytes"] / (rl["spmv_ms"] * 1e-3) / 1e9, launch_ms=rl["spmv_ms"],
                 bytes_per_launch=rl["spmv_bytes"])
     kernel_profile = {k: dict(ms=v[0], gbs=(v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else 0.0), launches=v[2])

@@ -1,0 +1,122 @@
+"""Kernel microbenchmark: the hybrid Gauss-Seidel sweep of AMG level 0 and the
+block SpMV on a 3D layered workload, timed back to back with CUDA events on
+the launching stream.
+
+    python -m paper_1611_00127_gb300.kernel_bench [--n 128] [--prec fp64|fp32]
+        [--reps 20] [--kind cpr1|bf]
+
+The case is the exact Newton Jacobian of the n^3 layered log-normal grid at
+its synthetic front state (the 7-point two-point-flux stencil of Sec. 2 in
+3D); level 0 is the pressure block A_pp of the quasi-IMPES-decoupled Jacobian
+(CPR, Alg. 1) or the SIMPLE Schur complement (block factorisation, Alg. 3).
+The L2 cache is flushed before each timed loop. Each loop sits in an NVTX
+range ("sweep", "spmv"), so a profiler can select exactly those launches.
+Prints one JSON object: per-launch time and algorithmic bytes of each kernel.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import inputs as I
+from . import rsflow as R
+
+
+def bsr2_spmv_bytes(J: R.Bsr2) -> float:
+    """Algorithmic bytes of one y = J x: every block (32 B) and column index
+    (4 B) once, the row pointers, x and y once each (16 B per cell)."""
+    return J.nnzb * 36.0 + (J.nb + 1) * 4.0 + J.nb * 32.0
+
+
+class Level0Case:
+    """Assembled Jacobian, preconditioner and level-0 hierarchy of one grid."""
+
+    def __init__(self, p, state, precision: int, kind: int = R.CPR1, theta: float = 0.5):
+        self.p = p
+        u, uo = state
+        self.dp = R.DeviceProblems(p)
+        self.J = R.Bsr2.pattern(self.dp)
+        self.F = torch.empty(2 * p.ncell, dtype=torch.float64, device="cuda")
+        R.jacobian_assemble(self.dp, torch.as_tensor(u, device="cuda"), torch.as_tensor(uo, device="cuda"),
+                            I.DAY, self.J, self.F)
+        self.M = R.Precond(self.J, R.PrecParams(kind=kind, amg=R.AmgParams(theta=theta, precision=precision)))
+        self.H = self.M.amg(0)
+        z = torch.empty_like(self.F)
+        self.M.apply(self.F, z)          # leaves a right-hand side on every level
+        self.y = torch.empty_like(self.F)
+        self.lanes = R.autotune_bsr2(self.J, self.F, self.y)     # lanes per block row of the SpMV
+
+    def time_sweeps(self, reps: int, flush: torch.Tensor | None = None):
+        """(ms per sweep, algorithmic bytes per sweep) over `reps` back-to-back
+        level-0 sweeps."""
+        self.H.level_smooth(0, 3)
+        if flush is not None:
+            flush.add_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("sweep")
+        e0.record()
+        by = self.H.level_smooth(0, reps)
+        e1.record()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        return e0.elapsed_time(e1) / reps, by
+
+    def time_spmv(self, reps: int, flush: torch.Tensor | None = None):
+        """(ms per launch, algorithmic bytes per launch) of y = J x."""
+        for _ in range(3):
+            R.bsr2_spmv(self.J, self.F, self.y)
+        if flush is not None:
+            flush.add_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("spmv")
+        e0.record()
+        for _ in range(reps):
+            R.bsr2_spmv(self.J, self.F, self.y)
+        e1.record()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        return e0.elapsed_time(e1) / reps, bsr2_spmv_bytes(self.J)
+
+    def level0(self):
+        n0, nnz0 = self.H.level_info(0)[:2]
+        return n0, nnz0
+
+    def close(self):
+        self.M.close()
+
+
+def layered(n: int, precision: int, kind: int = R.CPR1, reps: int = 20) -> dict:
+    """Sweep and SpMV timings on the n^3 layered workload, L2 flushed."""
+    p = I.config_layered_3d(n)
+    case = Level0Case(p, I.front_state(p), precision, kind)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    ts, bs = case.time_sweeps(reps, flush)
+    tm, bm = case.time_spmv(reps, flush)
+    n0, nnz0 = case.level0()
+    nnzb = case.J.nnzb
+    case.close()
+    return dict(sweep_ms=ts, sweep_bytes=bs, rows=n0, nnz=nnz0, spmv_ms=tm, spmv_bytes=bm, nnzb=nnzb,
+                spmv_lanes=case.lanes)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--kind", choices=["cpr1", "bf"], default="cpr1")
+    ap.add_argument("--reps", type=int, default=20)
+    a = ap.parse_args()
+    r = layered(a.n, R.FP64 if a.prec == "fp64" else R.FP32, R.CPR1 if a.kind == "cpr1" else R.BF, a.reps)
+    r.update(n=a.n, prec=a.prec, kind=a.kind,
+             sweep_gbs=r["sweep_bytes"] / (r["sweep_ms"] * 1e-3) / 1e9,
+             spmv_gbs=r["spmv_bytes"] / (r["spmv_ms"] * 1e-3) / 1e9,
+             device_used_gb=(lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info()))
+    print(json.dumps(r))
+
+
+if __name__ == "__main__":
+    main()
