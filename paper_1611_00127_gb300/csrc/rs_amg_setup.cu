@@ -761,6 +761,46 @@ __global__ void k_to_f32(int64_t n, const double *a, float *b) {
   if (i < n) b[i] = (float)a[i];
 }
 
+// Hybrid smoother operator. For every row of a chunk: its off-diagonal
+// entries coupling to rows of the same chunk (column stored as the position
+// inside the chunk), then those coupling to other rows (global column), each
+// part in ascending column order; the diagonal is left out (the smoother
+// uses its inverse). hs_mid[i] is where row i's second part begins.
+__global__ void k_hs_count(const int32_t *cr, const int32_t *rp, const int32_t *col, int32_t *cnt) {
+  const int32_t k = blockIdx.x;
+  const int32_t r0 = cr[2 * k], r1 = cr[2 * k + 1];
+  for (int32_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    int32_t c = 0;
+    for (int32_t q = rp[i]; q < rp[i + 1]; q++) c += col[q] != i;
+    cnt[i] = c;
+  }
+}
+
+template <typename T>
+__global__ void k_hs_fill(const int32_t *cr, const int32_t *rp, const int32_t *col, const double *val,
+                          const int32_t *hrp, int32_t *hmid, int32_t *hcol, T *hval) {
+  const int32_t k = blockIdx.x;
+  const int32_t r0 = cr[2 * k], r1 = cr[2 * k + 1];
+  for (int32_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    int32_t pos = hrp[i];
+    for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+      const int32_t j = col[q];
+      if (j != i && j >= r0 && j < r1) {
+        hcol[pos] = j - r0;
+        hval[pos++] = (T)val[q];
+      }
+    }
+    hmid[i] = pos;
+    for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+      const int32_t j = col[q];
+      if (j < r0 || j >= r1) {
+        hcol[pos] = j;
+        hval[pos++] = (T)val[q];
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ coarse inverse
 // Gauss-Jordan with partial pivoting (largest |a|, first on ties), one CTA per
 // system, dense FP64 in global scratch: [A | I] -> [I | A^{-1}].
@@ -1148,6 +1188,27 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         if (Lc.R.nnz) RS_COUNTED k_to_f32<<<grid_for(Lc.R.nnz), kBlock, 0, s>>>(Lc.R.nnz, Lc.R.val, Lc.R.valf);
       }
     }
+    // packed operator of the hybrid smoother, in the cycle's precision
+    if (prm.smoother == RS_SMOOTH_HYBRID && Lc.nchunk > 0) {
+      RS_TRY(dalloc_n(&Lc.hs_rp, (size_t)n + 1, s));
+      RS_TRY(dalloc_n(&Lc.hs_mid, (size_t)n, s));
+      RS_CHECK_CUDA(cudaMemsetAsync(Lc.hs_rp, 0, sizeof(int32_t) * ((size_t)n + 1), s));
+      RS_COUNTED k_hs_count<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.hs_rp);
+      int32_t tot = 0;
+      RS_TRY(exclusive_scan(Lc.hs_rp, Lc.hs_rp, n, s, &tot));
+      Lc.hs_nnz = tot;
+      RS_TRY(dalloc_n(&Lc.hs_col, (size_t)tot + 1, s));
+      if (H.precision == RS_PREC_FP32) {
+        RS_TRY(dalloc_n(&Lc.hs_valf, (size_t)tot + 1, s));
+        RS_COUNTED k_hs_fill<float><<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.A.val,
+                                                              Lc.hs_rp, Lc.hs_mid, Lc.hs_col, Lc.hs_valf);
+      } else {
+        RS_TRY(dalloc_n(&Lc.hs_val, (size_t)tot + 1, s));
+        RS_COUNTED k_hs_fill<double><<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.A.val,
+                                                               Lc.hs_rp, Lc.hs_mid, Lc.hs_col, Lc.hs_val);
+      }
+      RS_CHECK_CUDA(cudaGetLastError());
+    }
     // work vectors
     const size_t es = H.precision == RS_PREC_FP32 ? sizeof(float) : sizeof(double);
     RS_TRY(dalloc(&Lc.x, es * ((size_t)n + 1), s));
@@ -1187,6 +1248,11 @@ void amg_free(Hier &H, cudaStream_t s) {
     dfree(L.chunk_row0, s);
     dfree(L.chunk_coff, s);
     dfree(L.chunk_rows, s);
+    dfree(L.hs_rp, s);
+    dfree(L.hs_mid, s);
+    dfree(L.hs_col, s);
+    dfree(L.hs_val, s);
+    dfree(L.hs_valf, s);
     dfree(L.b, s);
     dfree(L.r, s);
     dfree(L.t, s);

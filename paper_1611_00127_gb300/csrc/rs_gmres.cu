@@ -422,6 +422,8 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
   cudaEventDestroy(evn[0]);
   cudaEventDestroy(evn[1]);
   if (rc) return rc;
+  rc = vcycle_wait_status(s);
+  if (rc) return rc;
   int32_t conv = 0, itmax = 0;
   double rmax = 0.0;
   for (int32_t q = 0; q < nseg; q++) {

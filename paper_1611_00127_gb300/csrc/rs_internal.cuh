@@ -174,6 +174,14 @@ struct Level {
   int32_t *chunk_row0 = nullptr;     // [2 nchunk] (first row, end row) of each chunk
   int32_t *chunk_coff = nullptr;     // [nchunk * (ncolour+1)] colour offsets inside each chunk
   int32_t *chunk_rows = nullptr;     // [n] local row of each position, sorted by (chunk, colour, row)
+  // packed operator of the hybrid smoother: per chunk row, off-diagonal
+  // entries inside the chunk (chunk-local column) in [hs_rp[i], hs_mid[i]),
+  // then those coupling to other rows (global column) up to hs_rp[i+1];
+  // values in the cycle's precision (hs_val FP64 or hs_valf FP32)
+  int32_t hs_nnz = 0;
+  int32_t *hs_rp = nullptr, *hs_mid = nullptr, *hs_col = nullptr;
+  double *hs_val = nullptr;
+  float *hs_valf = nullptr;
   // work vectors (FP32 or FP64 by the hierarchy's precision); x2 is the
   // second buffer of the hybrid smoother's old/new pair
   void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
@@ -194,6 +202,9 @@ void amg_free(Hier &H, cudaStream_t s);
 // x = V-cycle(b); FP64 in/out. `xin_zero` is always true here (zero guess).
 int amg_vcycle(const Hier &H, const double *b, double *x, cudaStream_t s);
 int amg_level_sweeps(const Hier &H, int32_t l, int sweeps, double *bytes_per_sweep, cudaStream_t s);
+// RS_ETIMEOUT (and clears the flag) if a smoother CTA gave up waiting for its
+// staging copies since the last call; synchronises the stream.
+int vcycle_wait_status(cudaStream_t s);
 
 // ------------------------------------------------------------------ helpers
 std::vector<int32_t> seg_offsets(int32_t n, int32_t nseg, const int32_t *seg_off);

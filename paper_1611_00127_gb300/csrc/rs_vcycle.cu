@@ -43,141 +43,223 @@ __global__ void __launch_bounds__(256) k_gs_colour(int32_t nrows, const int32_t 
 }
 
 // Hybrid multicolour Gauss-Seidel sweep, one CTA per chunk of consecutive
-// rows. Couplings to rows outside the chunk read `xold` (the iterate at the
+// rows, on the level's packed smoother operator (per row: the off-diagonal
+// entries inside the chunk with chunk-local columns, then the entries
+// coupling to other chunks with global columns; the diagonal enters through
+// its inverse). Couplings to other chunks read `xold` (the iterate at the
 // start of the sweep; nullptr means the zero vector), so their contribution to
-// each row is a constant of the sweep. Everything the CTA needs is first
-// brought into shared memory by flat loops whose loads are all independent
-// (so they overlap instead of forming one latency chain per row): the chunk's
-// row pointers, right-hand side, inverse diagonal, colour offsets and rows by
-// colour, and its matrix entries, where an entry coupling to another chunk is
-// replaced by its product with xold. Then each row's out-of-chunk sum is
-// formed, and the colours are swept in order, a __syncthreads apart, on
-// shared memory only. Chunks whose rows exceed the staging area read the
-// matrix from global memory instead. Result in `xnew`; the order of CTAs does
-// not affect it.
+// each row is a constant of the sweep.
+//
+// Staging. Everything the CTA reads from HBM, apart from the xold values of
+// other chunks, is a contiguous range: the chunk's packed row starts and
+// split points, right-hand side, inverse diagonal, start iterate, rows by
+// colour, and its packed columns and values. One thread issues a bulk
+// asynchronous copy (cp.async.bulk, the TMA engine's 1D form) for the
+// 16-byte-aligned interior of each range, all tracked by one mbarrier, so the
+// whole chunk is in flight at once; the few elements before the first and
+// after the last 16-byte boundary are loaded by plain loads. Each range lands
+// in its shared-memory segment shifted by its global address mod 16, which
+// keeps both sides of every bulk copy 16-byte aligned. Then each row's sum
+// over other chunks is formed (gathers of xold, mostly from L2) and the
+// colours are swept in order, a __syncthreads apart, on shared memory only.
+// Chunks with more entries than the staging area read their entries from
+// global memory instead. Result in `xnew`; the order of CTAs does not affect
+// it.
 constexpr int kHgsStageEntries = 12288;
 constexpr int kHgsMaxColours = 128;
+constexpr int kHgsSpin = 1 << 20;     // bound on the mbarrier wait (iterations)
+
+// Set when a smoother CTA gave up waiting for its staging copies; read and
+// cleared by vcycle_wait_status().
+__device__ int g_hgs_wait_timeout;
+
+__host__ __device__ constexpr size_t hgs_seg(size_t bytes) { return ((bytes + 15) & ~size_t(15)) + 16; }
 
 template <typename T>
 constexpr size_t hgs_smem(int cmax, int stage) {
-  return sizeof(T) * 3 * (size_t)cmax + sizeof(T) * (size_t)stage +
-         sizeof(int32_t) * ((size_t)stage + 2 * (size_t)cmax + 1 + kHgsMaxColours + 1) + 64;
+  return 3 * hgs_seg(sizeof(T) * (size_t)cmax) + hgs_seg(sizeof(T) * (size_t)stage) +
+         hgs_seg(sizeof(int32_t) * (size_t)stage) + hgs_seg(sizeof(int32_t) * ((size_t)cmax + 1)) +
+         2 * hgs_seg(sizeof(int32_t) * (size_t)cmax) + sizeof(int32_t) * (kHgsMaxColours + 1);
 }
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Where the elements [off, off + cnt) of global array g go in a segment: the
+// shifted base (same address mod 16 as g + off), the number of leading
+// elements before the first 16-byte boundary, and the aligned interior bytes.
+template <typename E>
+struct BulkRange {
+  E *dst;
+  const E *src;
+  int32_t cnt, head;
+  uint32_t bytes;
+  __device__ BulkRange(unsigned char *seg, const E *g, int64_t off, int32_t n) {
+    src = g + off;
+    const uint32_t shift = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src) & 15u);
+    dst = reinterpret_cast<E *>(seg + shift);
+    cnt = n;
+    head = min(n, static_cast<int32_t>(((16u - shift) & 15u) / sizeof(E)));
+    bytes = static_cast<uint32_t>(((int64_t)(n - head) * (int64_t)sizeof(E)) & ~int64_t(15));
+  }
+  __device__ int32_t tail_begin() const { return head + static_cast<int32_t>(bytes / sizeof(E)); }
+  // thread 0: bulk copy of the interior
+  __device__ void issue(uint32_t bar) const {
+    if (bytes == 0) return;
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(smem_addr(dst + head)), "l"(src + head), "r"(bytes), "r"(bar) : "memory");
+  }
+  // every thread: its share of the head and tail elements
+  __device__ void edges(int t, int nt) const {
+    for (int32_t e = t; e < head; e += nt) dst[e] = __ldg(src + e);
+    for (int32_t e = tail_begin() + t; e < cnt; e += nt) dst[e] = __ldg(src + e);
+  }
+};
 
 template <typename T, int LPR>
 __global__ void __launch_bounds__(256) k_hgs(const int32_t *__restrict__ cr, const int32_t *__restrict__ coff,
                                              const int32_t *__restrict__ crows, int32_t ncol, int32_t cmax,
-                                             int32_t stage_cap,
-                                             const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                             const T *__restrict__ val, const T *__restrict__ dinv,
+                                             int32_t stage_cap, const int32_t *__restrict__ hrp,
+                                             const int32_t *__restrict__ hmid, const int32_t *__restrict__ hcol,
+                                             const T *__restrict__ hval, const T *__restrict__ dinv,
                                              const T *__restrict__ b, const T *__restrict__ xold,
                                              T *__restrict__ xnew) {
   RS_PDL_ENTRY();
   extern __shared__ __align__(16) unsigned char smem[];
-  T *xs = reinterpret_cast<T *>(smem);               // chunk unknowns
-  T *rhs = xs + cmax;                                // b_i - (out-of-chunk part of row i)
-  T *dv = rhs + cmax;                                // 1 / a_ii
-  T *sval = dv + cmax;                               // staged values / out-of-chunk products
-  int32_t *scol = reinterpret_cast<int32_t *>(sval + stage_cap);   // local column or -1
-  int32_t *lrp = scol + stage_cap;                   // staged row starts [len+1]
-  int32_t *srows = lrp + cmax + 1;                   // rows by colour
-  int32_t *scof = srows + cmax;                      // colour offsets [ncol+1]
+  __shared__ __align__(8) uint64_t bar;
+  unsigned char *seg = smem;
+  unsigned char *seg_x = seg;    seg += hgs_seg(sizeof(T) * cmax);
+  unsigned char *seg_b = seg;    seg += hgs_seg(sizeof(T) * cmax);
+  unsigned char *seg_d = seg;    seg += hgs_seg(sizeof(T) * cmax);
+  unsigned char *seg_v = seg;    seg += hgs_seg(sizeof(T) * stage_cap);
+  unsigned char *seg_c = seg;    seg += hgs_seg(sizeof(int32_t) * stage_cap);
+  unsigned char *seg_rp = seg;   seg += hgs_seg(sizeof(int32_t) * (cmax + 1));
+  unsigned char *seg_md = seg;   seg += hgs_seg(sizeof(int32_t) * cmax);
+  unsigned char *seg_rw = seg;   seg += hgs_seg(sizeof(int32_t) * cmax);
+  int32_t *scof = reinterpret_cast<int32_t *>(seg);            // colour offsets [ncol+1]
+
   const int32_t k = blockIdx.x;
   const int32_t r0 = __ldg(cr + 2 * k), r1 = __ldg(cr + 2 * k + 1), len = r1 - r0;
-  const int32_t q0 = __ldg(rp + r0), nnz = __ldg(rp + r1) - q0;
-  const bool staged = nnz <= stage_cap;
+  const int32_t p0 = __ldg(hrp + r0), np = __ldg(hrp + r1) - p0;
+  const bool staged = np <= stage_cap;
   const int32_t *cof = coff + (int64_t)k * (ncol + 1);
-  // flat loads
-  for (int32_t t = threadIdx.x; t <= len; t += blockDim.x) {
-    lrp[t] = __ldg(rp + r0 + t) - q0;
-    if (t < len) {
-      rhs[t] = __ldg(b + r0 + t);
-      dv[t] = __ldg(dinv + r0 + t);
-      xs[t] = xold ? __ldg(xold + r0 + t) : T(0);
-      srows[t] = __ldg(crows + r0 + t);
-    }
+
+  const BulkRange<int32_t> g_rp(seg_rp, hrp, r0, len + 1);
+  const BulkRange<int32_t> g_md(seg_md, hmid, r0, len);
+  const BulkRange<T> g_b(seg_b, b, r0, len);
+  const BulkRange<T> g_d(seg_d, dinv, r0, len);
+  const BulkRange<int32_t> g_rw(seg_rw, crows, r0, len);
+  const BulkRange<T> g_x(seg_x, xold ? xold : b, r0, xold ? len : 0);
+  const BulkRange<int32_t> g_c(seg_c, hcol, p0, staged ? np : 0);
+  const BulkRange<T> g_v(seg_v, hval, p0, staged ? np : 0);
+  const uint32_t ubar = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(ubar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t tx = g_rp.bytes + g_md.bytes + g_b.bytes + g_d.bytes + g_rw.bytes + g_x.bytes + g_c.bytes +
+                        g_v.bytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(ubar), "r"(tx) : "memory");
+    g_c.issue(ubar);
+    g_v.issue(ubar);
+    g_rp.issue(ubar);
+    g_md.issue(ubar);
+    g_rw.issue(ubar);
+    g_b.issue(ubar);
+    g_d.issue(ubar);
+    g_x.issue(ubar);
+  } else {
+    const int t = threadIdx.x - 1, nt = blockDim.x - 1;
+    g_rp.edges(t, nt);
+    g_md.edges(t, nt);
+    g_b.edges(t, nt);
+    g_d.edges(t, nt);
+    g_rw.edges(t, nt);
+    g_x.edges(t, nt);
+    g_c.edges(t, nt);
+    g_v.edges(t, nt);
   }
   for (int32_t c = threadIdx.x; c <= ncol; c += blockDim.x) scof[c] = __ldg(cof + c);
-  if (staged) {
-    // four entries per thread in flight: columns and values, then the gathers
-    const int32_t bd = blockDim.x;
-    for (int32_t qb = threadIdx.x; qb < nnz; qb += 4 * bd) {
-      int32_t jj[4];
-      T aa[4], xx[4];
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int32_t q = qb + u * bd;
-        jj[u] = q < nnz ? __ldg(col + q0 + q) : r0;
-        aa[u] = q < nnz ? __ldg(val + q0 + q) : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const bool in = jj[u] >= r0 && jj[u] < r1;
-        xx[u] = (!in && xold) ? __ldg(xold + jj[u]) : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const int32_t q = qb + u * bd;
-        if (q < nnz) {
-          const bool in = jj[u] >= r0 && jj[u] < r1;
-          scol[q] = in ? jj[u] - r0 : -1;
-          if (in) sval[q] = aa[u];
-          else sval[q] = aa[u] * xx[u];
-        }
-      }
+  T *xs = g_x.dst;
+  if (!xold)
+    for (int32_t t = threadIdx.x; t < len; t += blockDim.x) xs[t] = T(0);
+  // bounded wait for the bulk copies (phase 0 of the barrier)
+  {
+    uint32_t done = 0;
+    for (int it = 0; it < kHgsSpin && !done; it++)
+      asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                   : "=r"(done) : "r"(ubar) : "memory");
+    if (!done) {
+      atomicOr(&g_hgs_wait_timeout, 1);
+      for (int it = 0; it < kHgsSpin && !done; it++)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(ubar) : "memory");
     }
   }
   __syncthreads();
+  const int32_t *lrp = g_rp.dst;       // packed row starts of rows r0..r1
+  const int32_t *lmd = g_md.dst;       // packed split points
+  T *rhs = g_b.dst;
+  const T *dv = g_d.dst;
+  const int32_t *srows = g_rw.dst;
+  const int32_t *pcol = staged ? g_c.dst : hcol + p0;
+  const T *pval = staged ? g_v.dst : hval + p0;
   const int group = threadIdx.x / LPR, lane = threadIdx.x % LPR, ngroups = blockDim.x / LPR;
-  // out-of-chunk sums (uniform trip count: the group shuffles see whole warps)
-  for (int32_t base = 0; base < len; base += ngroups) {
-    const int32_t li = base + group;
-    const bool act = li < len;
-    T off = T(0);
-    if (act) {
-      const int32_t s = lrp[li], e = lrp[li + 1];
-      if (staged) {
-        for (int32_t q = s + lane; q < e; q += LPR)
-          if (scol[q] < 0) off += sval[q];
-      } else if (xold) {
-        for (int32_t q = s + lane; q < e; q += LPR) {
-          const int32_t j = __ldg(col + q0 + q);
-          if (j < r0 || j >= r1) off += __ldg(val + q0 + q) * __ldg(xold + j);
+  // rhs_i = b_i - sum_j a_ij xold_j over other chunks (uniform trip count:
+  // the group shuffles see whole warps); four gathers in flight per lane
+  if (xold) {
+    for (int32_t base = 0; base < len; base += ngroups) {
+      const int32_t li = base + group;
+      const bool act = li < len;
+      T off = T(0);
+      if (act) {
+        if (lane == 0) off = rhs[li];
+        const int32_t m = lmd[li] - p0, e = lrp[li + 1] - p0;
+        for (int32_t q = m + lane; q < e; q += 4 * LPR) {
+          int32_t jj[4];
+          T aa[4], xx[4];
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const int32_t qq = q + u * LPR;
+            jj[u] = qq < e ? pcol[qq] : -1;
+            aa[u] = qq < e ? pval[qq] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; u++) xx[u] = jj[u] >= 0 ? __ldg(xold + jj[u]) : T(0);
+#pragma unroll
+          for (int u = 0; u < 4; u++)
+            if (jj[u] >= 0) off -= aa[u] * xx[u];
         }
       }
-    }
 #pragma unroll
-    for (int o = LPR / 2; o > 0; o >>= 1) off += __shfl_down_sync(0xffffffffu, off, o, LPR);
-    if (act && lane == 0) rhs[li] -= off;
+      for (int o = LPR / 2; o > 0; o >>= 1) off += __shfl_down_sync(0xffffffffu, off, o, LPR);
+      if (act && lane == 0) rhs[li] = off;
+    }
   }
   __syncthreads();
-  // colour passes
+  // colour passes over the entries inside the chunk
   for (int32_t c = 0; c < ncol; c++) {
     const int32_t beg = scof[c], end = scof[c + 1];
     for (int32_t base = beg; base < end; base += ngroups) {
       const int32_t pos = base + group;
       int32_t li = -1;
-      T sacc = T(0);
+      T acc = T(0);
       if (pos < end) {
         li = srows[pos];
-        const int32_t s = lrp[li], e = lrp[li + 1];
-        if (staged) {
-          for (int32_t q = s + lane; q < e; q += LPR) {
-            const int32_t jl = scol[q];
-            if (jl >= 0 && jl != li) sacc += sval[q] * xs[jl];
-          }
-        } else {
-          for (int32_t q = s + lane; q < e; q += LPR) {
-            const int32_t j = __ldg(col + q0 + q);
-            if (j >= r0 && j < r1 && j != r0 + li) sacc += __ldg(val + q0 + q) * xs[j - r0];
-          }
-        }
+        if (lane == 0) acc = rhs[li];
+        const int32_t s0 = lrp[li] - p0, m = lmd[li] - p0;
+        for (int32_t q = s0 + lane; q < m; q += LPR) acc -= pval[q] * xs[pcol[q]];
       }
 #pragma unroll
-      for (int o = LPR / 2; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o, LPR);
+      for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LPR);
       if (li >= 0 && lane == 0) {
         const T di = dv[li];
-        if (di != T(0)) xs[li] = (rhs[li] - sacc) * di;
+        if (di != T(0)) xs[li] = acc * di;
       }
     }
     __syncthreads();
@@ -309,6 +391,30 @@ const float *dinv_of<float>(const Level &L) { return L.dinvf; }
 template <>
 const double *dinv_of<double>(const Level &L) { return L.dinv; }
 
+template <typename T>
+static const T *hs_vals(const Level &L);
+template <>
+const float *hs_vals<float>(const Level &L) { return L.hs_valf; }
+template <>
+const double *hs_vals<double>(const Level &L) { return L.hs_val; }
+
+// Lanes per row of the hybrid sweep: its inner loops run over a row's packed
+// entries in shared memory (about half the row on each side of the chunk
+// boundary), so one lane per row unless rows are long.
+static int hgs_lpr(int32_t n, int32_t nnz) {
+  const double avg = n > 0 ? (double)nnz / n : 1.0;
+  if (avg <= 16.0) return 1;
+  if (avg <= 64.0) return 4;
+  return 8;
+}
+
+// Algorithmic bytes of one hybrid sweep over ns rows holding nz entries: the
+// matrix entries and row pointers once, b once, the iterate written once and
+// (unless it starts at zero) read once.
+static double hgs_bytes(double ns, double nz, size_t es, bool xin) {
+  return nz * (4.0 + es) + (ns + 1) * 4.0 + ns * es * (xin ? 3.0 : 2.0);
+}
+
 template <typename T, int LPR>
 static void hgs_attr() {
   static bool done = false;
@@ -340,13 +446,13 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
     const int32_t stage = std::min(L.chunk_max_nnz, kHgsStageEntries);
     const size_t shm = hgs_smem<T>(H.prm.chunk, stage);
     const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
+    const int hl = hgs_lpr(L.A.n, L.A.nnz);
     for (int sw = 0; sw < sweeps; sw++) {
       T *out = (cur == xa) ? xb : xa;
-      const double bytes = nz * (4.0 + sizeof(T)) + (ns + 1) * 4.0 + ns * 4.0 + ns * sizeof(T) * (cur ? 4.0 : 3.0);
-      ProfScope ps(kProfHgs, bytes, s);
-      RS_LPR_SWITCH(lpr, hgs_attr<T, L_>(); RS_COUNTED launch_pdl(k_hgs<T, L_>, dim3(L.nchunk), dim3(256), shm, s,
-                             L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, H.prm.chunk, stage, L.A.rowptr,
-                             L.A.col, val, dinv, b, (const T *)cur, out));
+      ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);
+      RS_LPR_SWITCH(hl, hgs_attr<T, L_>(); RS_COUNTED launch_pdl(k_hgs<T, L_>, dim3(L.nchunk), dim3(256), shm, s,
+                            L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, H.prm.chunk, stage, L.hs_rp,
+                            L.hs_mid, L.hs_col, hs_vals<T>(L), dinv, b, (const T *)cur, out));
       cur = out;
     }
     return;
@@ -426,7 +532,18 @@ static double level_sweeps(const Hier &H, int32_t l, int sweeps, cudaStream_t s)
   T *cur = static_cast<T *>(L.x);
   smooth<T>(H, L, sweeps, cur, s);
   const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
-  return nz * (4.0 + sizeof(T)) + (ns + 1) * 4.0 + ns * 4.0 + ns * sizeof(T) * 4.0;
+  return hgs_bytes(ns, nz, sizeof(T), true);
+}
+
+int vcycle_wait_status(cudaStream_t s) {
+  int h = 0;
+  RS_CHECK_CUDA(cudaMemcpyFromSymbolAsync(&h, g_hgs_wait_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  RS_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (h == 0) return 0;
+  const int z = 0;
+  RS_CHECK_CUDA(cudaMemcpyToSymbolAsync(g_hgs_wait_timeout, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+  RS_CHECK_CUDA(cudaStreamSynchronize(s));
+  return fail(RS_ETIMEOUT, "smoother: a staging copy did not complete within the wait limit");
 }
 
 int amg_level_sweeps(const Hier &H, int32_t l, int sweeps, double *bytes_per_sweep, cudaStream_t s) {
