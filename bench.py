@@ -40,6 +40,14 @@ UNIT = "solves/s"
 WORKLOAD = "2d_256x256_lognormal_sigma2_ell8_pc{0,1e3,1e4,1e5}_x_{amgJ,cpr1_qimpes,bf}"
 PC_SCALES = (0.0, 1e3, 1e4, 1e5)
 KINDS = (("amgJ", 0, 0), ("cpr1", 1, 2), ("bf", 3, 0))
+# DRAM bytes (read + write) per launch of the roofline kernels, from one ncu
+# capture of the current kernel version (summaries and commands in profiles/);
+# None where no capture of the current version exists.
+NCU_TRAFFIC = {
+    ("k_hgs", "fp64", "layered128"): (225.416704e6 + 12.058624e6, "profiles/k_hgs_fp64_layered128_level0.md"),
+    ("k_hgs", "fp32", "layered128"): (150.325760e6 + 6.161408e6, "profiles/k_hgs_fp32_layered128_level0.md"),
+    ("k_bsr2_spmv", "f64", "layered128"): (608.675840e6 + 30.454272e6, "profiles/k_bsr2_spmv_layered128.md"),
+}
 
 
 def parse():
@@ -148,8 +156,10 @@ class GpuStep:
         R = self.R
         return R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(precision=self.precision))
 
-    def run(self, dps=None, us=None, uos=None):
-        """One step; returns per-solve records."""
+    def run(self, dps=None, us=None, uos=None, per_solve_profile=None):
+        """One step; returns per-solve records. With `per_solve_profile` (a
+        dict), each solve runs between profile_begin/profile_end and its
+        kernel-class times are stored under the solve's name."""
         R, torch = self.R, self.torch
         dps = dps or self.dps
         us = us or self.u
@@ -160,11 +170,18 @@ class GpuStep:
             R.jacobian_assemble(dps[k], us[k], uos[k], 86400.0, self.J, self.F)
             torch.neg(self.F, out=self.b)
             for name, kind, dec in KINDS:
-                torch.cuda.nvtx.range_push(f"pc{PC_SCALES[k]:g}_{name}")
+                tag = f"pc{PC_SCALES[k]:g}_{name}"
+                torch.cuda.nvtx.range_push(tag)
+                if per_solve_profile is not None:
+                    torch.cuda.synchronize()
+                    R.profile_begin()
                 self.xout[q].zero_()
                 M = R.Precond(self.J, self.params(kind, dec))
                 st = R.gmres_solve(self.J, M, self.b, self.xout[q], R.GmresParams(m=30, maxit=self.maxit, rtol=1e-8))
                 M.close()
+                if per_solve_profile is not None:
+                    torch.cuda.synchronize()
+                    per_solve_profile[tag] = R.profile_end()
                 torch.cuda.nvtx.range_pop()
                 recs.append(dict(pc=PC_SCALES[k], prec=name, its=int(st.iterations), relres=float(st.relres),
                                  converged=bool(st.converged == 1)))
@@ -225,42 +242,12 @@ def hbm_peak():
 def sweep_roofline(probs, states, precision, reps=50):
     """Average device duration of the dominant kernel (one hybrid Gauss-Seidel
     sweep of level 0 of the largest hierarchy in the workload: the SIMPLE Schur
-    complement of the block-factorisation preconditioner), timed with CUDA
-    events on the launching stream over `reps` back-to-back launches, and the
-    block SpMV timed the same way."""
-    import torch
+    complement of the block-factorisation preconditioner at capillary scale
+    1e3), timed with CUDA events on the launching stream over `reps`
+    back-to-back launches, and the block SpMV timed the same way."""
+    from paper_1611_00127_gb300 import kernel_bench
     from paper_1611_00127_gb300 import rsflow as R
-    dp = R.DeviceProblems(probs[1])
-    J = R.Bsr2.pattern(dp)
-    F = torch.empty(2 * probs[1].ncell, dtype=torch.float64, device="cuda")
-    R.jacobian_assemble(dp, torch.as_tensor(states[1][0], device="cuda"),
-                        torch.as_tensor(states[1][1], device="cuda"), 86400.0, J, F)
-    M = R.Precond(J, R.PrecParams(kind=R.BF, amg=R.AmgParams(precision=precision)))
-    H = M.amg(0)
-    z = torch.empty_like(F)
-    M.apply(F, z)           # leaves a right-hand side on every level
-    H.level_smooth(0, 3)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    by = H.level_smooth(0, reps)
-    e1.record()
-    torch.cuda.synchronize()
-    t_sweep = e0.elapsed_time(e1) / reps
-    y = torch.empty_like(F)
-    for _ in range(3):
-        R.bsr2_spmv(J, F, y)
-    e0.record()
-    for _ in range(reps):
-        R.bsr2_spmv(J, F, y)
-    e1.record()
-    torch.cuda.synchronize()
-    t_spmv = e0.elapsed_time(e1) / reps
-    spmv_bytes = J.nnzb * 36.0 + (J.nb + 1) * 4.0 + J.nb * 32.0
-    n0, nnz0 = H.level_info(0)[:2]
-    M.close()
-    return dict(sweep_ms=t_sweep, sweep_bytes=by, rows=n0, nnz=nnz0, spmv_ms=t_spmv, spmv_bytes=spmv_bytes,
-                nnzb=J.nnzb)
+    return kernel_bench.lognormal(probs[1].nx, PC_SCALES[1], precision, R.BF, reps)
 
 
 def sweep_roofline_3d(precision, n=128, reps=20):
@@ -271,17 +258,26 @@ def sweep_roofline_3d(precision, n=128, reps=20):
     return kernel_bench.layered(n, precision, R.CPR1, reps)
 
 
+def shares(prof):
+    tot = sum(v[0] for v in prof.values()) or 1.0
+    return {k: round(v[0] / tot, 4) for k, v in prof.items() if v[2] > 0}
+
+
 def profiled_step(step):
-    """One more step with the library's event profiling on: per kernel class
-    device time and algorithmic bytes (preconditioner applies run without
-    graph replay so every launch is timed)."""
+    """One more step with the library's event profiling on, solve by solve:
+    per kernel class device time, algorithmic bytes and launches (the
+    preconditioner applies run without graph replay so every launch is
+    timed). Returns (whole-step totals, per-solve classes)."""
     import torch
-    R = step.R
+    per = {}
     torch.cuda.synchronize()
-    R.profile_begin()
-    step.run()
-    torch.cuda.synchronize()
-    return R.profile_end()
+    step.run(per_solve_profile=per)
+    tot = {}
+    for prof in per.values():
+        for k, (ms, by, n) in prof.items():
+            a = tot.get(k, (0.0, 0.0, 0))
+            tot[k] = (a[0] + ms, a[1] + by, a[2] + n)
+    return tot, per
 
 
 def time_steps(step, steps, warmup, sync_barrier):
@@ -453,8 +449,7 @@ def main():
         e2e = dict(value=world * v, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
     if rank != 0:
         return
-    prof = profiled_step(step64)
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    prof, per_solve = profiled_step(step64)
     peak, peak_kind = hbm_peak()
     rl = sweep_roofline(probs, states, R.FP64)
     achieved = rl["sweep_bytes"] / (rl["sweep_ms"] * 1e-3) / 1e9
@@ -471,12 +466,15 @@ def main():
             big = sweep_roofline_3d(prec)
             a2 = big["sweep_bytes"] / (big["sweep_ms"] * 1e-3) / 1e9
             s2 = big["spmv_bytes"] / (big["spmv_ms"] * 1e-3) / 1e9
+            tr, src = NCU_TRAFFIC.get(("k_hgs", pname, "layered128"), (None, None))
+            trs, srcs = NCU_TRAFFIC.get(("k_bsr2_spmv", "f64", "layered128"), (None, None))
             roofline_large[pname] = dict(
                 bound="hbm", kernel=f"k_hgs {pname.upper()}, level 0 (A_pp) of the 128^3 layered CPR hierarchy",
-                achieved=a2, peak=peak, unit="GB/s", frac=a2 / peak, launch_ms=big["sweep_ms"],
-                bytes_per_launch=big["sweep_bytes"], units=f"{big['rows']} rows, {big['nnz']} entries",
-                bsr2_spmv=dict(achieved=s2, frac=s2 / peak, launch_ms=big["spmv_ms"],
-                               bytes_per_launch=big["spmv_bytes"], nnzb=big["nnzb"]),
+                achieved=a2, peak=peak, unit="GB/s", frac=a2 / peak, traffic=tr, traffic_source=src,
+                launch_ms=big["sweep_ms"], bytes_per_launch=big["sweep_bytes"],
+                units=f"{big['rows']} rows, {big['nnz']} entries",
+                bsr2_spmv=dict(achieved=s2, frac=s2 / peak, launch_ms=big["spmv_ms"], traffic=trs,
+                               traffic_source=srcs, bytes_per_launch=big["spmv_bytes"], nnzb=big["nnzb"]),
                 l2="flushed before the timed launches; working set > L2")
     spmv = dict(achieved=rl["spmv_bytes"] / (rl["spmv_ms"] * 1e-3) / 1e9, launch_ms=rl["spmv_ms"],
                 bytes_per_launch=rl["spmv_bytes"])
@@ -504,7 +502,8 @@ def main():
         roofline_large=roofline_large,
         bsr2_spmv=spmv,
         kernel_profile=dict(note="one eager profiled step, CUDA events per launch (includes launch gaps)",
-                            classes=kernel_profile),
+                            classes=kernel_profile,
+                            shares_pc10000_cpr1=shares(per_solve.get("pc10000_cpr1", {}))),
         gpu_launches=int(round(launches / (args.steps + args.warmup))) * args.steps,
         e2e=e2e,
         cpu_baseline=cpu,

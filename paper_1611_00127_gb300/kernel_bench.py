@@ -1,15 +1,16 @@
 """Kernel microbenchmark: the hybrid Gauss-Seidel sweep of AMG level 0 and the
-block SpMV on a 3D layered workload, timed back to back with CUDA events on
-the launching stream.
+block SpMV, timed back to back with CUDA events on the launching stream.
 
-    python -m paper_1611_00127_gb300.kernel_bench [--n 128] [--prec fp64|fp32]
-        [--reps 20] [--kind cpr1|bf]
+    python -m paper_1611_00127_gb300.kernel_bench [--grid layered3d|lognormal2d]
+        [--n N] [--pc PC] [--prec fp64|fp32] [--reps 20] [--kind cpr1|bf]
 
-The case is the exact Newton Jacobian of the n^3 layered log-normal grid at
-its synthetic front state (the 7-point two-point-flux stencil of Sec. 2 in
-3D); level 0 is the pressure block A_pp of the quasi-IMPES-decoupled Jacobian
-(CPR, Alg. 1) or the SIMPLE Schur complement (block factorisation, Alg. 3).
-The L2 cache is flushed before each timed loop. Each loop sits in an NVTX
+The case is the exact Newton Jacobian at the synthetic front state of the
+n^3 layered log-normal grid (7-point two-point-flux stencil of Sec. 2 in 3D;
+L2 flushed before each timed loop, the working set exceeds L2) or of the
+n x n log-normal grid with capillary scale PC (operands L2-resident, as in
+a solve of that size). Level 0 is the pressure block A_pp of the
+quasi-IMPES-decoupled Jacobian (CPR, Alg. 1) or the SIMPLE Schur complement
+(block factorisation, Alg. 3). Each loop sits in an NVTX
 range ("sweep", "spmv"), so a profiler can select exactly those launches.
 Prints one JSON object: per-launch time and algorithmic bytes of each kernel.
 """
@@ -103,15 +104,40 @@ def layered(n: int, precision: int, kind: int = R.CPR1, reps: int = 20) -> dict:
                 spmv_lanes=case.lanes)
 
 
+def lognormal(n: int, pc: float, precision: int, kind: int = R.BF, reps: int = 50, flush_l2: bool = False) -> dict:
+    """Sweep and SpMV timings on the n x n log-normal grid with capillary scale
+    `pc` (2D strength threshold 0.25). Without `flush_l2` the operands stay
+    in L2 between launches, as they do inside a solve of this size."""
+    p = I.config_lognormal_2d(pc, n=n)
+    case = Level0Case(p, I.front_state(p), precision, kind, theta=0.25)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda") if flush_l2 else None
+    ts, bs = case.time_sweeps(reps, flush)
+    tm, bm = case.time_spmv(reps, flush)
+    n0, nnz0 = case.level0()
+    nnzb = case.J.nnzb
+    case.close()
+    return dict(sweep_ms=ts, sweep_bytes=bs, rows=n0, nnz=nnz0, spmv_ms=tm, spmv_bytes=bm, nnzb=nnzb,
+                spmv_lanes=case.lanes)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--grid", choices=["layered3d", "lognormal2d"], default="layered3d")
+    ap.add_argument("--n", type=int, default=None, help="cells per side (128 for 3D, 256 for 2D)")
+    ap.add_argument("--pc", type=float, default=1e3, help="capillary scale of the 2D grid")
     ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--kind", choices=["cpr1", "bf"], default="cpr1")
     ap.add_argument("--reps", type=int, default=20)
     a = ap.parse_args()
-    r = layered(a.n, R.FP64 if a.prec == "fp64" else R.FP32, R.CPR1 if a.kind == "cpr1" else R.BF, a.reps)
-    r.update(n=a.n, prec=a.prec, kind=a.kind,
+    prec = R.FP64 if a.prec == "fp64" else R.FP32
+    kind = R.CPR1 if a.kind == "cpr1" else R.BF
+    if a.grid == "layered3d":
+        a.n = a.n or 128
+        r = layered(a.n, prec, kind, a.reps)
+    else:
+        a.n = a.n or 256
+        r = lognormal(a.n, a.pc, prec, kind, a.reps)
+    r.update(grid=a.grid, n=a.n, prec=a.prec, kind=a.kind,
              sweep_gbs=r["sweep_bytes"] / (r["sweep_ms"] * 1e-3) / 1e9,
              spmv_gbs=r["spmv_bytes"] / (r["spmv_ms"] * 1e-3) / 1e9,
              device_used_gb=(lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info()))
