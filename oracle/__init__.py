@@ -23,7 +23,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _SRCS = ["oracle_physics.c", "oracle_sparse.c", "oracle_amg.c", "oracle_solve.c"]
 
-AMG_J, CPR1, CPR2, BF = 0, 1, 2, 3
+AMG_J, CPR1, CPR2, BF, AMG_J_SCALAR = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
@@ -111,6 +111,8 @@ def lib():
             "or_jp_colour": (i32, [P, u64, i32, P]),
             "or_chunk_rows": (i32, [P, i32]),
             "or_chunk_colour": (i32, [P, i32, P]),
+            "or_chunk_colour_pt": (i32, [P, i32, i32, P]),
+            "or_func_part": (P, [P, i32, i32]),
             "or_amg_setup": (P, [P, P]),
             "or_amg_free": (None, [P]),
             "or_amg_nlevels": (i32, [P]),
@@ -362,6 +364,19 @@ def chunk_colour(A: Csr, chunk: int = 512):
     col = np.zeros(n, dtype=np.int32)
     nc = lib().or_chunk_colour(A.h, chunk, _p(col))
     return col, int(nc), int(lib().or_chunk_rows(A.h, chunk))
+
+
+def chunk_colour_pt(A: Csr, chunk: int = 512, b: int = 2):
+    """Point colouring of the point-block hybrid smoother (colour per row)."""
+    n, m, nnz = A.info()
+    col = np.zeros(n, dtype=np.int32)
+    nc = lib().or_chunk_colour_pt(A.h, chunk, b, _p(col))
+    return col, int(nc)
+
+
+def func_part(A: Csr, b: int, f: int) -> Csr:
+    """Rows b*i + f and columns b*j + f of A."""
+    return Csr(lib().or_func_part(A.h, b, f))
 
 
 class Amg:

@@ -44,7 +44,7 @@ typedef struct {
   int32_t smoother;    /* 0 multicolour Gauss-Seidel, 1 l1-Jacobi, 2 hybrid multicolour GS */
   int32_t nu1, nu2;
   int32_t interp;      /* 0 classical, 1 extended+i */
-  int32_t num_functions; /* >1: unknown-based strength on the finest level */
+  int32_t num_functions; /* 2: systems (point) AMG, 2 interleaved unknowns per point; else scalar */
   int32_t chunk;       /* rows per block of the hybrid smoother */
 } or_amg_params;
 
@@ -87,6 +87,8 @@ or_csr *or_galerkin(const or_csr *A, const or_csr *P);
 int32_t or_jp_colour(const or_csr *A, uint64_t seed, int32_t level, int32_t *colour);
 int32_t or_chunk_rows(const or_csr *A, int32_t chunk);
 int32_t or_chunk_colour(const or_csr *A, int32_t chunk, int32_t *colour);
+int32_t or_chunk_colour_pt(const or_csr *A, int32_t chunk, int32_t b, int32_t *colour);
+or_csr *or_func_part(const or_csr *A, int32_t b, int32_t f);
 
 or_amg *or_amg_setup(const or_csr *A, const or_amg_params *prm);
 void or_amg_free(or_amg *H);
@@ -103,7 +105,7 @@ int32_t or_dense_lu(int32_t n, double *a, int32_t *piv);
 void or_dense_lu_solve(int32_t n, const double *a, const int32_t *piv, const double *b, double *x);
 
 /* ---- preconditioners (Sec. 3.2-3.4) ---- */
-enum { OR_AMG_J = 0, OR_CPR1 = 1, OR_CPR2 = 2, OR_BF = 3 };
+enum { OR_AMG_J = 0, OR_CPR1 = 1, OR_CPR2 = 2, OR_BF = 3, OR_AMG_J_SCALAR = 4 };
 typedef struct {
   int32_t kind;
   int32_t decouple;   /* CPR only: 0 none, 1 per-cell inverse of the 2x2 diagonal block,

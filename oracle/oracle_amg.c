@@ -33,6 +33,18 @@
  *    over the whole level (smoother = 0) and l1-Jacobi (smoother = 1). Pre-
  *    and post-smoothing sweep the colours in the same ascending order.
  *  - Coarsest level: dense LU with partial pivoting.
+ *  - Systems ("point") AMG, num_functions = b = 2 (Sec. 3.2: BoomerAMG on the
+ *    Jacobian ordered by grid points, the point method of Stueben et al.):
+ *    the unknowns are interleaved, b per point (row b*i + f is function f of
+ *    point i). Each level coarsens the points by strength and PMIS on the
+ *    function-0 (pressure) part A_00, the primary unknown; every unknown of a
+ *    C point is a C unknown. Each function f is interpolated only from the
+ *    same function at C points, with the weights of the interpolation of
+ *    A_ff under the point splitting; couplings between functions enter only
+ *    through the Galerkin product with the whole matrix. The smoother is the
+ *    point-block hybrid Gauss-Seidel: chunks of consecutive points, points
+ *    coloured first-fit inside the chunk, each point's b x b diagonal block
+ *    solved with its inverse (no update where that block is singular).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -520,6 +532,109 @@ int32_t or_chunk_colour(const or_csr *A, int32_t chunk, int32_t *colour) {
   return ncol;
 }
 
+/* Function f of b interleaved unknowns per point: rows b*i + f, columns
+ * b*j + f of A, as an N x N matrix (N = n / b). */
+or_csr *or_func_part(const or_csr *A, int32_t b, int32_t f) {
+  int32_t N = A->n / b, nnz = 0;
+  for (int32_t i = 0; i < N; i++)
+    for (int32_t q = A->rowptr[b * i + f]; q < A->rowptr[b * i + f + 1]; q++) nnz += A->col[q] % b == f;
+  or_csr *B = or_csr_alloc(N, A->m / b, nnz);
+  int32_t pos = 0;
+  B->rowptr[0] = 0;
+  for (int32_t i = 0; i < N; i++) {
+    for (int32_t q = A->rowptr[b * i + f]; q < A->rowptr[b * i + f + 1]; q++)
+      if (A->col[q] % b == f) {
+        B->col[pos] = A->col[q] / b;
+        B->val[pos++] = A->val[q];
+      }
+    B->rowptr[i + 1] = pos;
+  }
+  return B;
+}
+
+/* Interleaved interpolation: row b*i + f of P is row i of Pf[f] with column
+ * c mapped to b*c + f. */
+static or_csr *interleave_P(or_csr **Pf, int32_t b) {
+  int32_t N = Pf[0]->n, nc = Pf[0]->m, nnz = 0;
+  for (int32_t f = 0; f < b; f++) nnz += Pf[f]->nnz;
+  or_csr *P = or_csr_alloc(b * N, b * nc, nnz);
+  int32_t pos = 0;
+  P->rowptr[0] = 0;
+  for (int32_t i = 0; i < N; i++)
+    for (int32_t f = 0; f < b; f++) {
+      const or_csr *Q = Pf[f];
+      for (int32_t q = Q->rowptr[i]; q < Q->rowptr[i + 1]; q++) {
+        P->col[pos] = b * Q->col[q] + f;
+        P->val[pos++] = Q->val[q];
+      }
+      P->rowptr[b * i + f + 1] = pos;
+    }
+  return P;
+}
+
+/* Point colouring of the point-block hybrid smoother: chunks of
+ * or_chunk_rows(A) consecutive rows (a whole number of points); inside a
+ * chunk the points are coloured first-fit in ascending order, each taking the
+ * lowest colour not used by an already coloured point of the chunk that it
+ * is coupled to in either direction (some a_rc or a_cr stored with r in
+ * point i and c in point k != i). Every unknown of a point gets the point's
+ * colour. Returns the number of colours. */
+int32_t or_chunk_colour_pt(const or_csr *A, int32_t chunk, int32_t b, int32_t *colour) {
+  int32_t n = A->n, C = or_chunk_rows(A, chunk), ncol = 0;
+  int32_t N = n / b;
+  int32_t *pc = xmalloc(sizeof(int32_t) * ((size_t)N + 1));
+  int32_t *stamp = xmalloc(sizeof(int32_t) * ((size_t)n + 2));
+  for (int32_t c = 0; c <= n; c++) stamp[c] = -1;
+  for (int32_t c0 = 0; c0 < n; c0 += C) {
+    int32_t c1 = c0 + C < n ? c0 + C : n;
+    int32_t p0 = c0 / b, p1 = c1 / b;
+    for (int32_t i = p0; i < p1; i++) {
+      /* in-chunk neighbours through the rows of point i */
+      for (int32_t f = 0; f < b; f++)
+        for (int32_t q = A->rowptr[b * i + f]; q < A->rowptr[b * i + f + 1]; q++) {
+          int32_t k = A->col[q] / b;
+          if (k != i && k >= p0 && k < i) stamp[pc[k]] = i;
+        }
+      /* and through the rows of earlier points of the chunk */
+      for (int32_t k = p0; k < i; k++)
+        for (int32_t f = 0; f < b; f++)
+          for (int32_t q = A->rowptr[b * k + f]; q < A->rowptr[b * k + f + 1]; q++)
+            if (A->col[q] / b == i) stamp[pc[k]] = i;
+      int32_t c = 0;
+      while (stamp[c] == i) c++;
+      pc[i] = c;
+      if (c + 1 > ncol) ncol = c + 1;
+    }
+  }
+  for (int32_t i = 0; i < N; i++)
+    for (int32_t f = 0; f < b; f++) colour[b * i + f] = pc[i];
+  free(pc); free(stamp);
+  return ncol;
+}
+
+/* Inverses of the 2 x 2 diagonal blocks of the points, row-major; a singular
+ * block gets four zeros (the smoother then leaves that point unchanged). */
+static double *block_inverses2(const or_csr *A) {
+  int32_t N = A->n / 2;
+  double *inv = xmalloc(sizeof(double) * 4 * ((size_t)N + 1));
+  for (int32_t i = 0; i < N; i++) {
+    double d[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int32_t f = 0; f < 2; f++)
+      for (int32_t q = A->rowptr[2 * i + f]; q < A->rowptr[2 * i + f + 1]; q++)
+        if (A->col[q] / 2 == i) d[2 * f + A->col[q] % 2] = A->val[q];
+    double det = d[0] * d[3] - d[1] * d[2];
+    if (det != 0.0) {
+      inv[4 * i + 0] = d[3] / det;
+      inv[4 * i + 1] = -d[1] / det;
+      inv[4 * i + 2] = -d[2] / det;
+      inv[4 * i + 3] = d[0] / det;
+    } else {
+      inv[4 * i + 0] = inv[4 * i + 1] = inv[4 * i + 2] = inv[4 * i + 3] = 0.0;
+    }
+  }
+  return inv;
+}
+
 /* ---------------- dense LU ---------------- */
 int32_t or_dense_lu(int32_t n, double *a, int32_t *piv) {
   int32_t sing = 0;
@@ -571,6 +686,8 @@ struct or_amg {
   int32_t *colour[OR_MAXLEV];
   int32_t ncol[OR_MAXLEV];
   double *l1[OR_MAXLEV];
+  double *binv[OR_MAXLEV];  /* point mode: inverses of the 2 x 2 diagonal blocks */
+  int32_t b;                /* unknowns per point (1: scalar AMG) */
   double *lu;        /* coarsest dense LU */
   int32_t *piv;
   int32_t dense;     /* 1 if the coarsest level is solved by LU */
@@ -580,6 +697,8 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
   or_amg *H = xmalloc(sizeof(or_amg));
   memset(H, 0, sizeof(or_amg));
   H->prm = *prm;
+  H->b = prm->num_functions == 2 ? 2 : 1;
+  if (H->b > 1) H->prm.smoother = 2;   /* point mode uses the point-block hybrid smoother */
   int32_t maxl = prm->max_levels < OR_MAXLEV ? prm->max_levels : OR_MAXLEV;
   H->A[0] = or_csr_alloc(A0->n, A0->m, A0->nnz);
   memcpy(H->A[0]->rowptr, A0->rowptr, sizeof(int32_t) * ((size_t)A0->n + 1));
@@ -591,25 +710,59 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
     int32_t n = A->n;
     H->cf[l] = NULL;
     if (n <= prm->coarse_n || l == maxl - 1) break;
-    uint8_t *st = xmalloc((size_t)A->nnz);
-    or_strength_nf(A, prm->theta, l == 0 ? prm->num_functions : 1, st);
-    int8_t *cf = xmalloc((size_t)n);
-    or_pmis(A, st, prm->seed, l, cf);
-    int32_t nc = 0;
-    for (int32_t i = 0; i < n; i++) nc += cf[i] == 1;
-    if (nc == 0 || (double)nc > 0.9 * (double)n) { free(st); free(cf); break; }
-    H->cf[l] = cf;
-    H->P[l] = prm->interp == 1 ? or_interp_ext(A, st, cf) : or_interp(A, st, cf);
+    if (H->b > 1) {
+      /* point mode: coarsen the points on the pressure part */
+      int32_t b = H->b, N = n / b;
+      or_csr *Ap = or_func_part(A, b, 0);
+      uint8_t *st = xmalloc((size_t)Ap->nnz + 1);
+      or_strength_nf(Ap, prm->theta, 1, st);
+      int8_t *cfp = xmalloc((size_t)N + 1);
+      or_pmis(Ap, st, prm->seed, l, cfp);
+      free(st);
+      or_csr_free(Ap);
+      int32_t nc = 0;
+      for (int32_t i = 0; i < N; i++) nc += cfp[i] == 1;
+      if (nc == 0 || (double)nc > 0.9 * (double)N) { free(cfp); break; }
+      or_csr *Pf[2];
+      for (int32_t f = 0; f < b; f++) {
+        or_csr *Af = or_func_part(A, b, f);
+        uint8_t *sf = xmalloc((size_t)Af->nnz + 1);
+        or_strength_nf(Af, prm->theta, 1, sf);
+        Pf[f] = prm->interp == 1 ? or_interp_ext(Af, sf, cfp) : or_interp(Af, sf, cfp);
+        free(sf);
+        or_csr_free(Af);
+      }
+      H->P[l] = interleave_P(Pf, b);
+      for (int32_t f = 0; f < b; f++) or_csr_free(Pf[f]);
+      int8_t *cf = xmalloc((size_t)n);
+      for (int32_t i = 0; i < N; i++)
+        for (int32_t f = 0; f < b; f++) cf[b * i + f] = cfp[i];
+      free(cfp);
+      H->cf[l] = cf;
+    } else {
+      uint8_t *st = xmalloc((size_t)A->nnz);
+      or_strength_nf(A, prm->theta, 1, st);
+      int8_t *cf = xmalloc((size_t)n);
+      or_pmis(A, st, prm->seed, l, cf);
+      int32_t nc = 0;
+      for (int32_t i = 0; i < n; i++) nc += cf[i] == 1;
+      if (nc == 0 || (double)nc > 0.9 * (double)n) { free(st); free(cf); break; }
+      H->cf[l] = cf;
+      H->P[l] = prm->interp == 1 ? or_interp_ext(A, st, cf) : or_interp(A, st, cf);
+      free(st);
+    }
     H->R[l] = or_transpose(H->P[l]);
     H->A[l + 1] = or_galerkin(A, H->P[l]);
-    free(st);
     l++;
   }
   H->nlev = l + 1;
   for (int32_t k = 0; k < H->nlev - 1; k++) {
     or_csr *A = H->A[k];
     H->colour[k] = xmalloc(sizeof(int32_t) * ((size_t)A->n + 1));
-    if (prm->smoother == 2) H->ncol[k] = or_chunk_colour(A, prm->chunk, H->colour[k]);
+    if (H->b > 1) {
+      H->ncol[k] = or_chunk_colour_pt(A, prm->chunk, H->b, H->colour[k]);
+      H->binv[k] = block_inverses2(A);
+    } else if (prm->smoother == 2) H->ncol[k] = or_chunk_colour(A, prm->chunk, H->colour[k]);
     else H->ncol[k] = or_jp_colour(A, prm->seed, k, H->colour[k]);
     H->l1[k] = xmalloc(sizeof(double) * ((size_t)A->n + 1));
     for (int32_t i = 0; i < A->n; i++) {
@@ -636,7 +789,10 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
     /* coarsest level too large for a dense factorisation: smooth it instead */
     int32_t k = H->nlev - 1;
     H->colour[k] = xmalloc(sizeof(int32_t) * ((size_t)nc + 1));
-    if (prm->smoother == 2) H->ncol[k] = or_chunk_colour(Ac, prm->chunk, H->colour[k]);
+    if (H->b > 1) {
+      H->ncol[k] = or_chunk_colour_pt(Ac, prm->chunk, H->b, H->colour[k]);
+      H->binv[k] = block_inverses2(Ac);
+    } else if (prm->smoother == 2) H->ncol[k] = or_chunk_colour(Ac, prm->chunk, H->colour[k]);
     else H->ncol[k] = or_jp_colour(Ac, prm->seed, k, H->colour[k]);
     H->l1[k] = xmalloc(sizeof(double) * ((size_t)nc + 1));
     for (int32_t i = 0; i < nc; i++) {
@@ -660,6 +816,7 @@ void or_amg_free(or_amg *H) {
     free(H->cf[l]);
     free(H->colour[l]);
     free(H->l1[l]);
+    free(H->binv[l]);
   }
   free(H->lu);
   free(H->piv);
@@ -691,6 +848,40 @@ void or_amg_smooth(const or_amg *H, int32_t l, const double *b, double *x) {
     for (int32_t i = 0; i < A->n; i++)
       if (H->l1[l][i] != 0.0) x[i] += r[i] / H->l1[l][i];
     free(r);
+    return;
+  }
+  if (H->b == 2) {
+    /* point-block hybrid Gauss-Seidel: as below with points in place of rows;
+     * for a point of the current colour, each of its rows takes b minus the
+     * couplings outside the point (newest values inside the chunk, start
+     * values outside it), then the point's two unknowns are set to the
+     * inverse diagonal block times those two numbers */
+    double *xo = xmalloc(sizeof(double) * ((size_t)A->n + 1));
+    memcpy(xo, x, sizeof(double) * (size_t)A->n);
+    int32_t C = or_chunk_rows(A, H->prm.chunk);
+    for (int32_t c0 = 0; c0 < A->n; c0 += C) {
+      int32_t c1 = c0 + C < A->n ? c0 + C : A->n;
+      for (int32_t c = 0; c < H->ncol[l]; c++) {
+        for (int32_t i = c0 / 2; i < c1 / 2; i++) {
+          if (H->colour[l][2 * i] != c) continue;
+          double r[2];
+          for (int32_t f = 0; f < 2; f++) {
+            double t = b[2 * i + f];
+            for (int32_t q = A->rowptr[2 * i + f]; q < A->rowptr[2 * i + f + 1]; q++) {
+              int32_t j = A->col[q];
+              if (j / 2 == i) continue;
+              t -= A->val[q] * ((j >= c0 && j < c1) ? x[j] : xo[j]);
+            }
+            r[f] = t;
+          }
+          const double *m = H->binv[l] + 4 * (size_t)i;
+          if (m[0] == 0.0 && m[1] == 0.0 && m[2] == 0.0 && m[3] == 0.0) continue;
+          x[2 * i] = m[0] * r[0] + m[1] * r[1];
+          x[2 * i + 1] = m[2] * r[0] + m[3] * r[1];
+        }
+      }
+    }
+    free(xo);
     return;
   }
   if (H->prm.smoother == 2) {

@@ -128,9 +128,13 @@ or_precond *or_precond_create(int32_t nb, const int32_t *rowptr, const int32_t *
   } else {
     memcpy(M->Jt, val, sizeof(double) * 4 * (size_t)nnzb);
   }
-  if (prm->kind == OR_AMG_J) {
+  if (prm->kind == OR_AMG_J || prm->kind == OR_AMG_J_SCALAR) {
+    /* black-box AMG on the point-ordered J (Sec. 3.2): the point method with
+     * (p_w, S_n) per cell, or unknown-agnostic scalar AMG */
     or_csr *A = or_scalar_from_bsr2(nb, rowptr, col, val);
-    M->Hj = or_amg_setup(A, &prm->amg);
+    or_amg_params ap = prm->amg;
+    ap.num_functions = prm->kind == OR_AMG_J ? 2 : 1;
+    M->Hj = or_amg_setup(A, &ap);
     or_csr_free(A);
   } else if (cpr) {
     if (prm->p1 == 1) {
@@ -186,7 +190,7 @@ static void apply2(const double *m, const double *x, double *y) {
 
 void or_precond_apply(const or_precond *M, const double *r, double *z) {
   int32_t nb = M->nb, n = 2 * nb;
-  if (M->prm.kind == OR_AMG_J) {
+  if (M->prm.kind == OR_AMG_J || M->prm.kind == OR_AMG_J_SCALAR) {
     or_amg_vcycle(M->Hj, r, z);
     return;
   }
