@@ -101,7 +101,10 @@ typedef struct rs_amg_params {
   int32_t smoother;        /* RS_SMOOTH_* */
   int32_t nu1, nu2;        /* pre- and post-smoothing sweeps */
   int32_t interp;          /* RS_INTERP_* */
-  int32_t num_functions;   /* >1: unknown-based strength on the finest level */
+  int32_t num_functions;   /* 2: systems (point) AMG with 2 interleaved unknowns per point
+                              (row 2i + f is unknown f of point i): points coarsened on the
+                              unknown-0 part, each unknown interpolated from the same unknown,
+                              point-block hybrid Gauss-Seidel smoother; 1: scalar AMG */
   int32_t precision;       /* RS_PREC_* of the V-cycle */
   int32_t chunk;           /* rows per chunk of the hybrid smoother (32..512) */
 } rs_amg_params;
@@ -109,10 +112,11 @@ typedef struct rs_amg_params {
 typedef struct rs_amg rs_amg;
 typedef struct rs_precond rs_precond;
 
-#define RS_PC_AMG_J 0   /* black-box AMG on the point-ordered J (Sec. 3.2) */
+#define RS_PC_AMG_J 0   /* black-box AMG on the point-ordered J (Sec. 3.2), the point method */
 #define RS_PC_CPR1 1    /* Algorithm 1, combinative two-stage CPR-AMG(1) */
 #define RS_PC_CPR2 2    /* Algorithm 2, additive two-stage CPR-AMG(2) */
 #define RS_PC_BF 3      /* Algorithm 3, block factorisation with SIMPLE Schur */
+#define RS_PC_AMG_J_SCALAR 4  /* scalar AMG on the interleaved J (no point structure) */
 
 #define RS_DECOUPLE_NONE 0
 #define RS_DECOUPLE_ABF 1     /* D^{-1} J, D = per-cell 2x2 diagonal block */

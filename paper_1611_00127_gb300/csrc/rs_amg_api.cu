@@ -11,6 +11,7 @@ static int check_amg_params(const rs_amg_params &a) {
   if (a.smoother != RS_SMOOTH_MCGS && a.smoother != RS_SMOOTH_L1JACOBI && a.smoother != RS_SMOOTH_HYBRID)
     return fail(RS_EINVAL, "bad smoother");
   if (a.smoother == RS_SMOOTH_HYBRID && (a.chunk < 32 || a.chunk > 512)) return fail(RS_EINVAL, "chunk outside [32, 512]");
+  if (a.num_functions < 0 || a.num_functions > 2) return fail(RS_EINVAL, "num_functions must be 1 or 2");
   if (a.nu1 < 0 || a.nu2 < 0 || a.nu1 > 16 || a.nu2 > 16) return fail(RS_EINVAL, "bad sweep counts");
   if (a.interp != RS_INTERP_CLASSICAL && a.interp != RS_INTERP_EXTI) return fail(RS_EINVAL, "bad interpolation");
   if (a.precision != RS_PREC_FP32 && a.precision != RS_PREC_FP64) return fail(RS_EINVAL, "bad precision");

@@ -649,23 +649,29 @@ __global__ void k_colour_fill(int32_t n, const int32_t *colour, int32_t *fill, i
 constexpr int kCCMax = 512;
 constexpr int kCCWords = kCCMax / 32;
 
+// B unknowns per point (B = 1: rows are the points): the graph and the
+// colours are those of the chunk's points, and every unknown of a point gets
+// the point's colour.
+template <int B>
 __global__ void __launch_bounds__(256) k_chunk_colour(const int32_t *cr, const int32_t *rp, const int32_t *col,
                                                       int32_t *colour, int32_t *maxc, int32_t *err) {
   __shared__ uint32_t adj[kCCMax * kCCWords];
   __shared__ int32_t cs[kCCMax];
   const int32_t k = blockIdx.x;
-  const int32_t r0 = cr[2 * k], len = cr[2 * k + 1] - r0;
+  const int32_t r0 = cr[2 * k], nrow = cr[2 * k + 1] - r0, len = nrow / B;
   if (len > kCCMax) {
     if (threadIdx.x == 0) atomicExch(err, 1);
     return;
   }
   for (int32_t t = threadIdx.x; t < len * kCCWords; t += blockDim.x) adj[t] = 0u;
   __syncthreads();
-  for (int32_t li = threadIdx.x; li < len; li += blockDim.x) {
-    const int32_t i = r0 + li;
+  for (int32_t lr = threadIdx.x; lr < nrow; lr += blockDim.x) {
+    const int32_t i = r0 + lr, li = lr / B;
     for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
-      const int32_t lj = col[q] - r0;
-      if (lj == li || lj < 0 || lj >= len) continue;
+      const int32_t lc = col[q] - r0;
+      if (lc < 0 || lc >= nrow) continue;
+      const int32_t lj = lc / B;
+      if (lj == li) continue;
       atomicOr(&adj[li * kCCWords + (lj >> 5)], 1u << (lj & 31));
       atomicOr(&adj[lj * kCCWords + (li >> 5)], 1u << (li & 31));
     }
@@ -705,7 +711,7 @@ __global__ void __launch_bounds__(256) k_chunk_colour(const int32_t *cr, const i
     if (lane == 0) atomicMax(maxc, localmax);
   }
   __syncthreads();
-  for (int32_t t = threadIdx.x; t < len; t += blockDim.x) colour[r0 + t] = cs[t];
+  for (int32_t t = threadIdx.x; t < nrow; t += blockDim.x) colour[r0 + t] = cs[t / B];
 }
 
 __global__ void k_chunk_nnz_max(int32_t nchunk, const int32_t *cr, const int32_t *rp, int32_t *mx) {
@@ -720,12 +726,15 @@ __global__ void k_fill_colour(int32_t n, int32_t *c) {
 
 // Hybrid smoother tables: for chunk k (rows [cr[2k], cr[2k+1])), the local rows
 // sorted by (colour, row) and the offset of each colour inside the chunk.
+// With B unknowns per point the entries are the chunk's local points, stored
+// from position r0 / B.
+template <int B>
 __global__ void k_chunk_sort(const int32_t *cr, const int32_t *colour, int32_t ncol, int32_t *coff,
                              int32_t *rows) {
   __shared__ int32_t cs[1024];
   const int32_t k = blockIdx.x;
-  const int32_t r0 = cr[2 * k], len = cr[2 * k + 1] - r0;
-  for (int32_t t = threadIdx.x; t < len; t += blockDim.x) cs[t] = colour[r0 + t];
+  const int32_t r0 = cr[2 * k], len = (cr[2 * k + 1] - r0) / B;
+  for (int32_t t = threadIdx.x; t < len; t += blockDim.x) cs[t] = colour[r0 + B * t];
   __syncthreads();
   for (int32_t c = threadIdx.x; c <= ncol; c += blockDim.x) {
     int32_t cnt = 0;
@@ -736,7 +745,7 @@ __global__ void k_chunk_sort(const int32_t *cr, const int32_t *colour, int32_t n
     const int32_t c = cs[t];
     int32_t rank = 0;
     for (int32_t q = 0; q < len; q++) rank += (cs[q] < c) || (cs[q] == c && q < t);
-    rows[r0 + rank] = t;
+    rows[r0 / B + rank] = t;
   }
 }
 
@@ -756,6 +765,95 @@ __global__ void k_smoother_diag(int32_t n, const int32_t *rp, const int32_t *col
   dinvf[i] = (float)inv;
 }
 
+// ---- systems (point) AMG: B interleaved unknowns per point, row B*i + f
+// function f of point i (Sec. 3.2, the point method)
+// rows B*i + f and columns B*j + f of A as an N x N matrix
+__global__ void k_func_count(int32_t N, int32_t B, int32_t f, const int32_t *rp, const int32_t *col,
+                             int32_t *cnt) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int32_t c = 0;
+  for (int32_t q = rp[B * i + f]; q < rp[B * i + f + 1]; q++) c += col[q] % B == f;
+  cnt[i] = c;
+}
+
+__global__ void k_func_fill(int32_t N, int32_t B, int32_t f, const int32_t *rp, const int32_t *col,
+                            const double *val, const int32_t *orp, int32_t *ocol, double *oval) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int32_t pos = orp[i];
+  for (int32_t q = rp[B * i + f]; q < rp[B * i + f + 1]; q++)
+    if (col[q] % B == f) {
+      ocol[pos] = col[q] / B;
+      oval[pos++] = val[q];
+    }
+}
+
+// interleaved interpolation: row B*i + f is row i of Pf with column c -> B*c + f
+__global__ void k_ileave_count(int32_t N, int32_t B, int32_t f, const int32_t *prp, int32_t *cnt) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) cnt[B * i + f] = prp[i + 1] - prp[i];
+}
+
+__global__ void k_ileave_fill(int32_t N, int32_t B, int32_t f, const int32_t *prp, const int32_t *pcol,
+                              const double *pval, const int32_t *orp, int32_t *ocol, double *oval) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int32_t pos = orp[B * i + f];
+  for (int32_t q = prp[i]; q < prp[i + 1]; q++) {
+    ocol[pos] = B * pcol[q] + f;
+    oval[pos++] = pval[q];
+  }
+}
+
+__global__ void k_cf_expand(int32_t N, int32_t B, const int8_t *cfp, int8_t *cf) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N)
+    for (int32_t f = 0; f < B; f++) cf[B * i + f] = cfp[i];
+}
+
+// inverses of the 2 x 2 diagonal blocks of the points (row-major, FP64 and an
+// FP32 copy); a singular block gets zeros (that point is left unchanged)
+__global__ void k_block_inv2(int32_t N, const int32_t *rp, const int32_t *col, const double *val, double *inv,
+                             float *invf) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double d[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int32_t f = 0; f < 2; f++)
+    for (int32_t q = rp[2 * i + f]; q < rp[2 * i + f + 1]; q++)
+      if (col[q] / 2 == i) d[2 * f + col[q] % 2] = val[q];
+  const double det = d[0] * d[3] - d[1] * d[2];
+  double m[4] = {0.0, 0.0, 0.0, 0.0};
+  if (det != 0.0) {
+    m[0] = d[3] / det;
+    m[1] = -d[1] / det;
+    m[2] = -d[2] / det;
+    m[3] = d[0] / det;
+  }
+  for (int q = 0; q < 4; q++) {
+    inv[4 * (int64_t)i + q] = m[q];
+    invf[4 * (int64_t)i + q] = (float)m[q];
+  }
+}
+
+static int func_part(const DCsr &A, int32_t B, int32_t f, DCsr &out, cudaStream_t s) {
+  const int32_t N = A.n / B;
+  out.n = N;
+  out.m = A.m / B;
+  RS_TRY(dalloc_n(&out.rowptr, (size_t)N + 1, s));
+  if (N > 0) RS_COUNTED k_func_count<<<grid_for(N), kBlock, 0, s>>>(N, B, f, A.rowptr, A.col, out.rowptr);
+  int32_t nnz = 0;
+  RS_TRY(exclusive_scan(out.rowptr, out.rowptr, N, s, &nnz));
+  out.nnz = nnz;
+  RS_TRY(dalloc_n(&out.col, (size_t)nnz + 1, s));
+  RS_TRY(dalloc_n(&out.val, (size_t)nnz + 1, s));
+  if (N > 0)
+    RS_COUNTED k_func_fill<<<grid_for(N), kBlock, 0, s>>>(N, B, f, A.rowptr, A.col, A.val, out.rowptr, out.col,
+                                                          out.val);
+  RS_CHECK_CUDA(cudaGetLastError());
+  return 0;
+}
+
 __global__ void k_to_f32(int64_t n, const double *a, float *b) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -766,17 +864,20 @@ __global__ void k_to_f32(int64_t n, const double *a, float *b) {
 // inside the chunk), then those coupling to other rows (global column), each
 // part in ascending column order; the diagonal is left out (the smoother
 // uses its inverse). hs_mid[i] is where row i's second part begins.
+// With B unknowns per point the whole diagonal block of the row's point is
+// left out (the point-block smoother uses its inverse).
+template <int B>
 __global__ void k_hs_count(const int32_t *cr, const int32_t *rp, const int32_t *col, int32_t *cnt) {
   const int32_t k = blockIdx.x;
   const int32_t r0 = cr[2 * k], r1 = cr[2 * k + 1];
   for (int32_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     int32_t c = 0;
-    for (int32_t q = rp[i]; q < rp[i + 1]; q++) c += col[q] != i;
+    for (int32_t q = rp[i]; q < rp[i + 1]; q++) c += col[q] / B != i / B;
     cnt[i] = c;
   }
 }
 
-template <typename T>
+template <typename T, int B>
 __global__ void k_hs_fill(const int32_t *cr, const int32_t *rp, const int32_t *col, const double *val,
                           const int32_t *hrp, int32_t *hmid, int32_t *hcol, T *hval) {
   const int32_t k = blockIdx.x;
@@ -785,7 +886,7 @@ __global__ void k_hs_fill(const int32_t *cr, const int32_t *rp, const int32_t *c
     int32_t pos = hrp[i];
     for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
       const int32_t j = col[q];
-      if (j != i && j >= r0 && j < r1) {
+      if (j / B != i / B && j >= r0 && j < r1) {
         hcol[pos] = j - r0;
         hval[pos++] = (T)val[q];
       }
@@ -946,6 +1047,12 @@ static int colour_level(Level &L, const int32_t *seg, const int32_t *dseg_off, c
 int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg_params &prm, Hier &H,
               cudaStream_t s) {
   H.prm = prm;
+  if (prm.num_functions == 2) {
+    H.prm.smoother = RS_SMOOTH_HYBRID;   // point-block hybrid smoother
+    if (prm.chunk < 32 || prm.chunk > 512) return fail(RS_EINVAL, "chunk outside [32, 512]");
+    for (size_t q = 0; q < seg_off0.size(); q++)
+      if (seg_off0[q] % 2) return fail(RS_EINVAL, "systems AMG needs whole points (even row counts per system)");
+  }
   H.precision = prm.precision;
   H.nseg = (int32_t)seg_off0.size() - 1;
   H.L.clear();
@@ -967,9 +1074,13 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     RS_CHECK_CUDA(cudaMemcpyAsync(L0.A.val, A0.val, sizeof(double) * (size_t)A0.nnz, cudaMemcpyDeviceToDevice, s));
     L0.seg_off = seg_off0;
   }
+  // systems (point) AMG: B unknowns per point; points are coarsened on the
+  // function-0 part and each function is interpolated on its own part
+  const int32_t B = prm.num_functions == 2 ? 2 : 1;
   for (int32_t l = 0;; l++) {
     Level &L = H.L[l];
     const int32_t n = L.A.n, nseg = H.nseg;
+    L.nfun = B;
     Scratch sc(s);
     int32_t *seg = nullptr, *dseg_off = nullptr;
     RS_TRY(seg_ids(L.seg_off, n, &seg, s));
@@ -987,91 +1098,150 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     }
     std::vector<uint8_t> smooth_seg(act);   // systems smoothed (not solved) at this level
     if (nact > 0) {
+      // the matrix whose points are coarsened: A itself, or its function-0 part
+      DCsr Ap;
+      const DCsr &M = B > 1 ? Ap : L.A;
+      const int32_t np = n / B;
+      std::vector<int32_t> pseg_off(nseg + 1);
+      for (int32_t q = 0; q <= nseg; q++) pseg_off[q] = L.seg_off[q] / B;
+      int32_t *pseg = seg, *dpseg_off = dseg_off;
+      if (B > 1) {
+        RS_TRY(func_part(L.A, B, 0, Ap, s));
+        RS_TRY(seg_ids(pseg_off, np, &pseg, s));
+        sc.ptrs.push_back(pseg);
+        RS_TRY(upload(&dpseg_off, pseg_off, s));
+        sc.ptrs.push_back(dpseg_off);
+      }
       uint8_t *dact = nullptr, *strong = nullptr, *notmax = nullptr;
       int32_t *lam = nullptr, *left = nullptr, *segc = nullptr, *isc = nullptr, *err = nullptr;
       uint64_t *key = nullptr;
       double *diag = nullptr;
+      int8_t *cfp = nullptr;
       RS_TRY(sc.get(&dact, (size_t)nseg));
-      RS_TRY(sc.get(&strong, (size_t)L.A.nnz));
-      RS_TRY(sc.get(&notmax, (size_t)n));
-      RS_TRY(sc.get(&lam, (size_t)n));
+      RS_TRY(sc.get(&strong, (size_t)std::max(M.nnz, L.A.nnz) + 1));
+      RS_TRY(sc.get(&notmax, (size_t)np + 1));
+      RS_TRY(sc.get(&lam, (size_t)np + 1));
       RS_TRY(sc.get(&left, 2));
       RS_TRY(sc.get(&segc, (size_t)nseg));
-      RS_TRY(sc.get(&isc, (size_t)n + 1));
-      RS_TRY(sc.get(&key, (size_t)n));
-      RS_TRY(sc.get(&diag, (size_t)n));
+      RS_TRY(sc.get(&isc, (size_t)np + 1));
+      RS_TRY(sc.get(&key, (size_t)np + 1));
+      RS_TRY(sc.get(&diag, (size_t)np + 1));
       RS_TRY(sc.get(&err, 1));
       RS_CHECK_CUDA(cudaMemcpyAsync(dact, act.data(), nseg, cudaMemcpyHostToDevice, s));
       RS_TRY(dalloc_n(&L.cf, (size_t)n, s));
-      const unsigned g = grid_for(n);
-      RS_COUNTED k_diag<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag);
-      RS_COUNTED k_strength<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, seg, dact, prm.theta,
-                                      l == 0 ? nfun0 : 1, strong);
-      RS_CHECK_CUDA(cudaMemsetAsync(lam, 0, sizeof(int32_t) * n, s));
-      RS_COUNTED k_lambda<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, lam);
-      RS_COUNTED k_pmis_init<<<g, kBlock, 0, s>>>(n, lam, seg, dseg_off, dact, prm.seed, l, key, L.cf);
-      RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)n, s));
+      if (B > 1) RS_TRY(sc.get(&cfp, (size_t)np + 1));
+      else cfp = L.cf;
+      const unsigned g = grid_for(np);
+      RS_COUNTED k_diag<<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, M.val, diag);
+      RS_COUNTED k_strength<<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, M.val, diag, pseg, dact, prm.theta, 1,
+                                                 strong);
+      RS_CHECK_CUDA(cudaMemsetAsync(lam, 0, sizeof(int32_t) * np, s));
+      RS_COUNTED k_lambda<<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, lam);
+      RS_COUNTED k_pmis_init<<<g, kBlock, 0, s>>>(np, lam, pseg, dpseg_off, dact, prm.seed, l, key, cfp);
+      RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)np, s));
       int32_t hleft = 1, rounds = 0;
       while (hleft > 0) {
         if (++rounds > 100000) return fail(RS_ESETUP, "PMIS did not finish");
         // a few rounds between host checks; a round with nothing undecided does nothing
         for (int r = 0; r < 3; r++) {
           RS_CHECK_CUDA(cudaMemsetAsync(left, 0, sizeof(int32_t), s));
-          RS_COUNTED k_pmis_losers<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, key, L.cf, notmax);
-          RS_COUNTED k_pmis_select<<<g, kBlock, 0, s>>>(n, notmax, L.cf);
-          RS_COUNTED k_pmis_fmark<<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, strong, L.cf, left);
+          RS_COUNTED k_pmis_losers<<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, key, cfp, notmax);
+          RS_COUNTED k_pmis_select<<<g, kBlock, 0, s>>>(np, notmax, cfp);
+          RS_COUNTED k_pmis_fmark<<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, cfp, left);
         }
         RS_TRY(sync_copy(&hleft, left, sizeof(int32_t), s));
       }
       // per-system C counts; systems that coarsen too little stop here
       RS_CHECK_CUDA(cudaMemsetAsync(segc, 0, sizeof(int32_t) * nseg, s));
-      RS_COUNTED k_seg_count_c<<<g, kBlock, 0, s>>>(n, L.cf, seg, segc);
+      RS_COUNTED k_seg_count_c<<<g, kBlock, 0, s>>>(np, cfp, pseg, segc);
       std::vector<int32_t> hc(nseg);
       RS_TRY(sync_copy(hc.data(), segc, sizeof(int32_t) * nseg, s));
       nact = 0;
       for (int32_t q = 0; q < nseg; q++) {
         if (!act[q]) continue;
-        const int32_t ng = L.seg_off[q + 1] - L.seg_off[q];
+        const int32_t ng = pseg_off[q + 1] - pseg_off[q];
         if (hc[q] == 0 || (double)hc[q] > 0.9 * (double)ng) { act[q] = 0; smooth_seg[q] = 0; H.last_level[q] = l; }
         else nact++;
       }
       RS_CHECK_CUDA(cudaMemcpyAsync(dact, act.data(), nseg, cudaMemcpyHostToDevice, s));
-      RS_COUNTED k_seg_revert<<<g, kBlock, 0, s>>>(n, L.cf, seg, dact, isc);
+      RS_COUNTED k_seg_revert<<<g, kBlock, 0, s>>>(np, cfp, pseg, dact, isc);
+      if (B > 1 && np > 0) RS_COUNTED k_cf_expand<<<g, kBlock, 0, s>>>(np, B, cfp, L.cf);
+      if (B > 1) dcsr_free(Ap, s);
       if (nact > 0) {
         int32_t nc = 0;
-        RS_TRY(exclusive_scan(isc, isc, n, s, &nc));
+        RS_TRY(exclusive_scan(isc, isc, np, s, &nc));
         std::vector<int32_t> off_next(nseg + 1);
         int32_t *offd = nullptr;
         RS_TRY(sc.get(&offd, (size_t)nseg + 1));
-        RS_COUNTED k_gather_offsets<<<grid_for(nseg + 1), kBlock, 0, s>>>(nseg + 1, dseg_off, isc, offd);
+        RS_COUNTED k_gather_offsets<<<grid_for(nseg + 1), kBlock, 0, s>>>(nseg + 1, dpseg_off, isc, offd);
         RS_TRY(sync_copy(off_next.data(), offd, sizeof(int32_t) * (nseg + 1), s));
-        // interpolation
+        for (int32_t q = 0; q <= nseg; q++) off_next[q] *= B;
+        // interpolation of one function part F (np rows) under the point splitting
+        auto interpolate = [&](const DCsr &F, const int8_t *cfu, DCsr &Pf) -> int {
+          const unsigned gf = grid_for(F.n);
+          RS_COUNTED k_diag<<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag);
+          RS_COUNTED k_strength<<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, pseg, dact, prm.theta, 1,
+                                                      strong);
+          Pf.n = F.n;
+          Pf.m = nc;
+          RS_TRY(dalloc_n(&Pf.rowptr, (size_t)F.n + 1, s));
+          RS_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+          const unsigned gw = (unsigned)std::min<int64_t>((F.n + kIWarps - 1) / kIWarps, 65535);
+          if (prm.interp == RS_INTERP_CLASSICAL)
+            RS_COUNTED k_interp_classical<false><<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong, cfu,
+                                                                       isc, Pf.rowptr, nullptr, nullptr, err);
+          else
+            RS_COUNTED k_interp_ext_w<false><<<gw, 32 * kIWarps, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong,
+                                                                         cfu, isc, Pf.rowptr, nullptr, nullptr, err);
+          int32_t pnnz = 0;
+          RS_TRY(exclusive_scan(Pf.rowptr, Pf.rowptr, F.n, s, &pnnz));
+          int32_t herr = 0;
+          RS_TRY(sync_copy(&herr, err, sizeof(int32_t), s));
+          if (herr) return fail(RS_ESETUP, "interpolation set too large on level " + std::to_string(l));
+          Pf.nnz = pnnz;
+          RS_TRY(dalloc_n(&Pf.col, (size_t)pnnz + 1, s));
+          RS_TRY(dalloc_n(&Pf.val, (size_t)pnnz + 1, s));
+          if (prm.interp == RS_INTERP_CLASSICAL)
+            RS_COUNTED k_interp_classical<true><<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong, cfu,
+                                                                      isc, Pf.rowptr, Pf.col, Pf.val, err);
+          else
+            RS_COUNTED k_interp_ext_w<true><<<gw, 32 * kIWarps, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong,
+                                                                        cfu, isc, Pf.rowptr, Pf.col, Pf.val, err);
+          RS_CHECK_CUDA(cudaGetLastError());
+          return 0;
+        };
         DCsr &P = L.P;
-        P.n = n;
-        P.m = nc;
-        RS_TRY(dalloc_n(&P.rowptr, (size_t)n + 1, s));
-        RS_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
-        if (prm.interp == RS_INTERP_CLASSICAL)
-          RS_COUNTED k_interp_classical<false><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
-                                                          P.rowptr, nullptr, nullptr, err);
-        else
-          RS_COUNTED k_interp_ext_w<false><<<(unsigned)std::min<int64_t>((n + kIWarps - 1) / kIWarps, 65535), 32 * kIWarps, 0, s>>>(
-              n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc, P.rowptr, nullptr, nullptr, err);
-        int32_t pnnz = 0;
-        RS_TRY(exclusive_scan(P.rowptr, P.rowptr, n, s, &pnnz));
-        int32_t herr = 0;
-        RS_TRY(sync_copy(&herr, err, sizeof(int32_t), s));
-        if (herr) return fail(RS_ESETUP, "interpolation set too large on level " + std::to_string(l));
-        P.nnz = pnnz;
-        RS_TRY(dalloc_n(&P.col, (size_t)pnnz, s));
-        RS_TRY(dalloc_n(&P.val, (size_t)pnnz, s));
-        if (prm.interp == RS_INTERP_CLASSICAL)
-          RS_COUNTED k_interp_classical<true><<<g, kBlock, 0, s>>>(n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc,
-                                                         P.rowptr, P.col, P.val, err);
-        else
-          RS_COUNTED k_interp_ext_w<true><<<(unsigned)std::min<int64_t>((n + kIWarps - 1) / kIWarps, 65535), 32 * kIWarps, 0, s>>>(
-              n, L.A.rowptr, L.A.col, L.A.val, diag, strong, L.cf, isc, P.rowptr, P.col, P.val, err);
-        RS_CHECK_CUDA(cudaGetLastError());
+        if (B == 1) {
+          RS_TRY(interpolate(L.A, L.cf, P));
+        } else {
+          P.n = n;
+          P.m = B * nc;
+          RS_TRY(dalloc_n(&P.rowptr, (size_t)n + 1, s));
+          DCsr Pf[2];
+          for (int32_t f = 0; f < B; f++) {
+            DCsr Af;
+            RS_TRY(func_part(L.A, B, f, Af, s));
+            const int r = interpolate(Af, cfp, Pf[f]);
+            dcsr_free(Af, s);
+            if (r) {
+              for (int32_t q = 0; q <= f; q++) dcsr_free(Pf[q], s);
+              return r;
+            }
+            if (np > 0) RS_COUNTED k_ileave_count<<<g, kBlock, 0, s>>>(np, B, f, Pf[f].rowptr, P.rowptr);
+          }
+          int32_t pnnz = 0;
+          RS_TRY(exclusive_scan(P.rowptr, P.rowptr, n, s, &pnnz));
+          P.nnz = pnnz;
+          RS_TRY(dalloc_n(&P.col, (size_t)pnnz + 1, s));
+          RS_TRY(dalloc_n(&P.val, (size_t)pnnz + 1, s));
+          for (int32_t f = 0; f < B; f++) {
+            if (np > 0)
+              RS_COUNTED k_ileave_fill<<<g, kBlock, 0, s>>>(np, B, f, Pf[f].rowptr, Pf[f].col, Pf[f].val, P.rowptr,
+                                                            P.col, P.val);
+            dcsr_free(Pf[f], s);
+          }
+          RS_CHECK_CUDA(cudaGetLastError());
+        }
         RS_TRY(transpose(P, L.R, s));
         DCsr AP;
         RS_TRY(spgemm(L.A, P, AP, s));
@@ -1089,7 +1259,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     Level &Lc = H.L[l];   // (reference may have moved after push_back)
     // smoother data for the systems smoothed here
     const bool any_smooth = std::any_of(smooth_seg.begin(), smooth_seg.end(), [](uint8_t v) { return v != 0; });
-    if (any_smooth && prm.smoother == RS_SMOOTH_HYBRID) {
+    if (any_smooth && H.prm.smoother == RS_SMOOTH_HYBRID) {
       // chunk k = rows [packed[2k], packed[2k+1]), never spanning two systems;
       // per system the chunk size is `chunk`, halved (not below 32) while
       // chunk * ceil(nnz / n) of that system exceeds 12288 entries
@@ -1125,7 +1295,8 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         RS_COUNTED k_chunk_nnz_max<<<grid_for(Lc.nchunk), kBlock, 0, s>>>(Lc.nchunk, Lc.chunk_row0, Lc.A.rowptr, cc + 2);
       if (n > 0) RS_COUNTED k_fill_colour<<<grid_for(n), kBlock, 0, s>>>(n, Lc.colour);
       if (Lc.nchunk > 0)
-        RS_COUNTED k_chunk_colour<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.colour, cc, cc + 1);
+        RS_COUNTED (B == 1 ? k_chunk_colour<1> : k_chunk_colour<2>)<<<Lc.nchunk, 256, 0, s>>>(
+            Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.colour, cc, cc + 1);
       int32_t hcc[3] = {0, 0, 0};
       RS_TRY(sync_copy(hcc, cc, sizeof(hcc), s));
       if (hcc[1]) return fail(RS_ESETUP, "chunk colouring failed on level " + std::to_string(l));
@@ -1134,7 +1305,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       RS_TRY(dalloc_n(&Lc.chunk_coff, (size_t)Lc.nchunk * (Lc.ncolour + 1), s));
       RS_TRY(dalloc_n(&Lc.chunk_rows, (size_t)n, s));
       if (Lc.nchunk > 0)
-        RS_COUNTED k_chunk_sort<<<Lc.nchunk, 512, 0, s>>>(Lc.chunk_row0, Lc.colour, Lc.ncolour, Lc.chunk_coff,
+        RS_COUNTED (B == 1 ? k_chunk_sort<1> : k_chunk_sort<2>)<<<Lc.nchunk, 512, 0, s>>>(Lc.chunk_row0, Lc.colour, Lc.ncolour, Lc.chunk_coff,
                                                           Lc.chunk_rows);
       RS_CHECK_CUDA(cudaGetLastError());
     } else if (any_smooth) {
@@ -1144,7 +1315,15 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     RS_TRY(dalloc_n(&Lc.dinvf, (size_t)n, s));
     if (n > 0)
       RS_COUNTED k_smoother_diag<<<grid_for(n), kBlock, 0, s>>>(n, Lc.A.rowptr, Lc.A.col, Lc.A.val,
-                                                     prm.smoother == RS_SMOOTH_L1JACOBI, Lc.dinv, Lc.dinvf);
+                                                     H.prm.smoother == RS_SMOOTH_L1JACOBI, Lc.dinv, Lc.dinvf);
+    if (B == 2) {
+      const int32_t np = n / 2;
+      RS_TRY(dalloc_n(&Lc.binv, 4 * (size_t)np + 4, s));
+      RS_TRY(dalloc_n(&Lc.binvf, 4 * (size_t)np + 4, s));
+      if (np > 0)
+        RS_COUNTED k_block_inv2<<<grid_for(np), kBlock, 0, s>>>(np, Lc.A.rowptr, Lc.A.col, Lc.A.val, Lc.binv,
+                                                                Lc.binvf);
+    }
     // systems solved directly here
     int64_t inv_tot = 0;
     std::vector<int4> info;
@@ -1189,22 +1368,23 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       }
     }
     // packed operator of the hybrid smoother, in the cycle's precision
-    if (prm.smoother == RS_SMOOTH_HYBRID && Lc.nchunk > 0) {
+    if (H.prm.smoother == RS_SMOOTH_HYBRID && Lc.nchunk > 0) {
       RS_TRY(dalloc_n(&Lc.hs_rp, (size_t)n + 1, s));
       RS_TRY(dalloc_n(&Lc.hs_mid, (size_t)n, s));
       RS_CHECK_CUDA(cudaMemsetAsync(Lc.hs_rp, 0, sizeof(int32_t) * ((size_t)n + 1), s));
-      RS_COUNTED k_hs_count<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.hs_rp);
+      RS_COUNTED (B == 1 ? k_hs_count<1> : k_hs_count<2>)<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr,
+                                                                                   Lc.A.col, Lc.hs_rp);
       int32_t tot = 0;
       RS_TRY(exclusive_scan(Lc.hs_rp, Lc.hs_rp, n, s, &tot));
       Lc.hs_nnz = tot;
       RS_TRY(dalloc_n(&Lc.hs_col, (size_t)tot + 1, s));
       if (H.precision == RS_PREC_FP32) {
         RS_TRY(dalloc_n(&Lc.hs_valf, (size_t)tot + 1, s));
-        RS_COUNTED k_hs_fill<float><<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.A.val,
+        RS_COUNTED (B == 1 ? k_hs_fill<float, 1> : k_hs_fill<float, 2>)<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.A.val,
                                                               Lc.hs_rp, Lc.hs_mid, Lc.hs_col, Lc.hs_valf);
       } else {
         RS_TRY(dalloc_n(&Lc.hs_val, (size_t)tot + 1, s));
-        RS_COUNTED k_hs_fill<double><<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.A.val,
+        RS_COUNTED (B == 1 ? k_hs_fill<double, 1> : k_hs_fill<double, 2>)<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.A.val,
                                                                Lc.hs_rp, Lc.hs_mid, Lc.hs_col, Lc.hs_val);
       }
       RS_CHECK_CUDA(cudaGetLastError());
@@ -1253,6 +1433,8 @@ void amg_free(Hier &H, cudaStream_t s) {
     dfree(L.hs_col, s);
     dfree(L.hs_val, s);
     dfree(L.hs_valf, s);
+    dfree(L.binv, s);
+    dfree(L.binvf, s);
     dfree(L.b, s);
     dfree(L.r, s);
     dfree(L.t, s);

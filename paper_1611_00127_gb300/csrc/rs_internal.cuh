@@ -178,6 +178,11 @@ struct Level {
   // entries inside the chunk (chunk-local column) in [hs_rp[i], hs_mid[i]),
   // then those coupling to other rows (global column) up to hs_rp[i+1];
   // values in the cycle's precision (hs_val FP64 or hs_valf FP32)
+  // systems (point) AMG: unknowns per point, and the inverses of the 2 x 2
+  // diagonal blocks of the points (row-major, FP64 and FP32)
+  int32_t nfun = 1;
+  double *binv = nullptr;
+  float *binvf = nullptr;
   int32_t hs_nnz = 0;
   int32_t *hs_rp = nullptr, *hs_mid = nullptr, *hs_col = nullptr;
   double *hs_val = nullptr;

@@ -156,10 +156,14 @@ int build(rs_precond *M, cudaStream_t s) {
   RS_TRY(dalloc_n(&M->ss, (size_t)nb, s));
   RS_TRY(dalloc_n(&M->sx, (size_t)nb, s));
   RS_TRY(dalloc_n(&M->sy, (size_t)nb, s));
-  if (kind == RS_PC_AMG_J) {
+  if (kind == RS_PC_AMG_J || kind == RS_PC_AMG_J_SCALAR) {
+    // black-box AMG on the point-ordered J (Sec. 3.2): the point method with
+    // (p_w, S_n) per cell, or unknown-agnostic scalar AMG
     DCsr A;
     RS_TRY(bsr2_scalar(J, A, s));
-    int r = amg_build(A, dof_offsets(M->seg_off), p.amg, M->Hj, s);
+    rs_amg_params ap = p.amg;
+    ap.num_functions = kind == RS_PC_AMG_J ? 2 : 1;
+    int r = amg_build(A, dof_offsets(M->seg_off), ap, M->Hj, s);
     dcsr_free(A, s);
     if (r) return r;
     M->has_j = true;
@@ -248,6 +252,7 @@ static int apply_body(const rs_precond *M, const double *r, double *z, cudaStrea
   const unsigned g = grid_for(nb);
   switch (M->prm.kind) {
     case RS_PC_AMG_J:
+    case RS_PC_AMG_J_SCALAR:
       return amg_vcycle(M->Hj, r, z, s);
     case RS_PC_BF: {
       RS_COUNTED k_take<<<g, kBlock, 0, s>>>(nb, r, 1, M->sb);
@@ -263,10 +268,11 @@ static int apply_body(const rs_precond *M, const double *r, double *z, cudaStrea
       const int mode = M->prm.decouple;
       const bool two = M->prm.kind == RS_PC_CPR2;
       RS_COUNTED k_cpr_stage1<<<g, kBlock, 0, s>>>(nb, mode, M->qw, M->dinv, M->p1inv, r, M->rt, z);
-      ProfScope ps(kProfBsr2, M->J.nnzb * 36.0 + (nb + 1) * 4.0 + nb * (16.0 + 16.0 + 16.0), s);
-      RS_COUNTED k_cpr_resid<4><<<grid_for((int64_t)nb * 4), kBlock, 0, s>>>(nb, M->J.row_ptr, M->J.col, M->J.val, z, M->rt,
-                                                                   mode, M->qw, M->dinv, M->sb,
-                                                                   two ? M->ss : nullptr);
+      {
+        ProfScope ps(kProfBsr2, M->J.nnzb * 36.0 + (nb + 1) * 4.0 + nb * (16.0 + 16.0 + 16.0), s);
+        RS_COUNTED k_cpr_resid<4><<<grid_for((int64_t)nb * 4), kBlock, 0, s>>>(
+            nb, M->J.row_ptr, M->J.col, M->J.val, z, M->rt, mode, M->qw, M->dinv, M->sb, two ? M->ss : nullptr);
+      }
       RS_TRY(amg_vcycle(M->Hp, M->sb, M->sx, s));
       if (two) RS_TRY(amg_vcycle(M->Hs, M->ss, M->sy, s));
       RS_COUNTED k_cpr_update<<<g, kBlock, 0, s>>>(nb, M->sx, two ? M->sy : nullptr, z);
@@ -325,6 +331,7 @@ static int check_params(const rs_amg_params &a) {
   if (a.smoother != RS_SMOOTH_MCGS && a.smoother != RS_SMOOTH_L1JACOBI && a.smoother != RS_SMOOTH_HYBRID)
     return fail(RS_EINVAL, "bad smoother");
   if (a.smoother == RS_SMOOTH_HYBRID && (a.chunk < 32 || a.chunk > 512)) return fail(RS_EINVAL, "chunk outside [32, 512]");
+  if (a.num_functions < 0 || a.num_functions > 2) return fail(RS_EINVAL, "num_functions must be 1 or 2");
   if (a.nu1 < 0 || a.nu2 < 0 || a.nu1 > 16 || a.nu2 > 16) return fail(RS_EINVAL, "bad sweep counts");
   if (a.interp != RS_INTERP_CLASSICAL && a.interp != RS_INTERP_EXTI) return fail(RS_EINVAL, "bad interpolation");
   if (a.precision != RS_PREC_FP32 && a.precision != RS_PREC_FP64) return fail(RS_EINVAL, "bad precision");
@@ -337,7 +344,8 @@ extern "C" int precond_create(const rs_bsr2 *J, const rs_precond_params *params,
   *out = nullptr;
   if (!J || !params || J->nb < 0 || J->nnzb < 0 || (J->nb > 0 && (!J->row_ptr || !J->col || !J->val)))
     return fail(RS_EINVAL, "invalid arguments");
-  if (params->kind < RS_PC_AMG_J || params->kind > RS_PC_BF) return fail(RS_EINVAL, "unknown preconditioner kind");
+  if (params->kind < RS_PC_AMG_J || params->kind > RS_PC_AMG_J_SCALAR)
+    return fail(RS_EINVAL, "unknown preconditioner kind");
   if (params->decouple < RS_DECOUPLE_NONE || params->decouple > RS_DECOUPLE_QIMPES)
     return fail(RS_EINVAL, "unknown decoupling");
   if (params->p1 != 0) return fail(RS_EINVAL, "only the point-block Jacobi P1 is available on the GPU");

@@ -267,6 +267,158 @@ __global__ void __launch_bounds__(256) k_hgs(const int32_t *__restrict__ cr, con
   for (int32_t t = threadIdx.x; t < len; t += blockDim.x) xnew[r0 + t] = xs[t];
 }
 
+// Point-block hybrid Gauss-Seidel sweep of systems AMG (two interleaved
+// unknowns per point, rows 2i and 2i+1 of point i): the same chunking,
+// staging and packed operator as k_hgs (the packed rows leave out the whole
+// 2 x 2 diagonal block of their point), points coloured inside the chunk,
+// and each point of the current colour set to the inverse of its diagonal
+// block times its two right-hand sides less their couplings (a point whose
+// block is singular keeps its values). One thread per point.
+template <typename T>
+constexpr size_t hgs2_smem(int cmax, int stage) {
+  return 2 * hgs_seg(sizeof(T) * (size_t)cmax) + hgs_seg(sizeof(T) * 2 * (size_t)cmax) +
+         hgs_seg(sizeof(T) * (size_t)stage) + hgs_seg(sizeof(int32_t) * (size_t)stage) +
+         hgs_seg(sizeof(int32_t) * ((size_t)cmax + 1)) + 2 * hgs_seg(sizeof(int32_t) * (size_t)cmax) +
+         sizeof(int32_t) * (kHgsMaxColours + 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_hgs2(const int32_t *__restrict__ cr, const int32_t *__restrict__ coff,
+                                              const int32_t *__restrict__ crows, int32_t ncol, int32_t cmax,
+                                              int32_t stage_cap, const int32_t *__restrict__ hrp,
+                                              const int32_t *__restrict__ hmid, const int32_t *__restrict__ hcol,
+                                              const T *__restrict__ hval, const T *__restrict__ binv,
+                                              const T *__restrict__ b, const T *__restrict__ xold,
+                                              T *__restrict__ xnew) {
+  RS_PDL_ENTRY();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  unsigned char *seg = smem;
+  unsigned char *seg_x = seg;    seg += hgs_seg(sizeof(T) * cmax);
+  unsigned char *seg_b = seg;    seg += hgs_seg(sizeof(T) * cmax);
+  unsigned char *seg_d = seg;    seg += hgs_seg(sizeof(T) * 2 * cmax);
+  unsigned char *seg_v = seg;    seg += hgs_seg(sizeof(T) * stage_cap);
+  unsigned char *seg_c = seg;    seg += hgs_seg(sizeof(int32_t) * stage_cap);
+  unsigned char *seg_rp = seg;   seg += hgs_seg(sizeof(int32_t) * (cmax + 1));
+  unsigned char *seg_md = seg;   seg += hgs_seg(sizeof(int32_t) * cmax);
+  unsigned char *seg_rw = seg;   seg += hgs_seg(sizeof(int32_t) * cmax);
+  int32_t *scof = reinterpret_cast<int32_t *>(seg);            // colour offsets [ncol+1], in points
+
+  const int32_t k = blockIdx.x;
+  const int32_t r0 = __ldg(cr + 2 * k), r1 = __ldg(cr + 2 * k + 1), len = r1 - r0, npt = len / 2;
+  const int32_t p0 = __ldg(hrp + r0), np = __ldg(hrp + r1) - p0;
+  const bool staged = np <= stage_cap;
+  const int32_t *cof = coff + (int64_t)k * (ncol + 1);
+
+  const BulkRange<int32_t> g_rp(seg_rp, hrp, r0, len + 1);
+  const BulkRange<int32_t> g_md(seg_md, hmid, r0, len);
+  const BulkRange<T> g_b(seg_b, b, r0, len);
+  const BulkRange<T> g_d(seg_d, binv, 2 * (int64_t)r0, 2 * len);
+  const BulkRange<int32_t> g_rw(seg_rw, crows, r0 / 2, npt);
+  const BulkRange<T> g_x(seg_x, xold ? xold : b, r0, xold ? len : 0);
+  const BulkRange<int32_t> g_c(seg_c, hcol, p0, staged ? np : 0);
+  const BulkRange<T> g_v(seg_v, hval, p0, staged ? np : 0);
+  const uint32_t ubar = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(ubar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t tx = g_rp.bytes + g_md.bytes + g_b.bytes + g_d.bytes + g_rw.bytes + g_x.bytes + g_c.bytes +
+                        g_v.bytes;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(ubar), "r"(tx) : "memory");
+    g_c.issue(ubar);
+    g_v.issue(ubar);
+    g_rp.issue(ubar);
+    g_md.issue(ubar);
+    g_rw.issue(ubar);
+    g_b.issue(ubar);
+    g_d.issue(ubar);
+    g_x.issue(ubar);
+  } else {
+    const int t = threadIdx.x - 1, nt = blockDim.x - 1;
+    g_rp.edges(t, nt);
+    g_md.edges(t, nt);
+    g_b.edges(t, nt);
+    g_d.edges(t, nt);
+    g_rw.edges(t, nt);
+    g_x.edges(t, nt);
+    g_c.edges(t, nt);
+    g_v.edges(t, nt);
+  }
+  for (int32_t c = threadIdx.x; c <= ncol; c += blockDim.x) scof[c] = __ldg(cof + c);
+  T *xs = g_x.dst;
+  if (!xold)
+    for (int32_t t = threadIdx.x; t < len; t += blockDim.x) xs[t] = T(0);
+  {
+    uint32_t done = 0;
+    for (int it = 0; it < kHgsSpin && !done; it++)
+      asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                   : "=r"(done) : "r"(ubar) : "memory");
+    if (!done) {
+      atomicOr(&g_hgs_wait_timeout, 1);
+      for (int it = 0; it < kHgsSpin && !done; it++)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(ubar) : "memory");
+    }
+  }
+  __syncthreads();
+  const int32_t *lrp = g_rp.dst;
+  const int32_t *lmd = g_md.dst;
+  T *rhs = g_b.dst;
+  const T *dv = g_d.dst;
+  const int32_t *srows = g_rw.dst;
+  const int32_t *pcol = staged ? g_c.dst : hcol + p0;
+  const T *pval = staged ? g_v.dst : hval + p0;
+  // right-hand sides less the couplings to other chunks
+  if (xold) {
+    for (int32_t lr = threadIdx.x; lr < len; lr += blockDim.x) {
+      T acc = rhs[lr];
+      const int32_t m = lmd[lr] - p0, e = lrp[lr + 1] - p0;
+      for (int32_t q = m; q < e; q += 4) {
+        int32_t jj[4];
+        T aa[4], xx[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          jj[u] = q + u < e ? pcol[q + u] : -1;
+          aa[u] = q + u < e ? pval[q + u] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) xx[u] = jj[u] >= 0 ? __ldg(xold + jj[u]) : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          if (jj[u] >= 0) acc -= aa[u] * xx[u];
+      }
+      rhs[lr] = acc;
+    }
+  }
+  __syncthreads();
+  for (int32_t c = 0; c < ncol; c++) {
+    const int32_t beg = scof[c], end = scof[c + 1];
+    for (int32_t pos = beg + threadIdx.x; pos < end; pos += blockDim.x) {
+      const int32_t li = srows[pos];
+      T acc[2];
+#pragma unroll
+      for (int f = 0; f < 2; f++) {
+        const int32_t lr = 2 * li + f;
+        T a = rhs[lr];
+        const int32_t s0 = lrp[lr] - p0, m = lmd[lr] - p0;
+        for (int32_t q = s0; q < m; q++) a -= pval[q] * xs[pcol[q]];
+        acc[f] = a;
+      }
+      const T *mi = dv + 4 * li;
+      if (mi[0] != T(0) || mi[1] != T(0) || mi[2] != T(0) || mi[3] != T(0)) {
+        xs[2 * li] = mi[0] * acc[0] + mi[1] * acc[1];
+        xs[2 * li + 1] = mi[2] * acc[0] + mi[3] * acc[1];
+      }
+    }
+    __syncthreads();
+  }
+  for (int32_t t = threadIdx.x; t < len; t += blockDim.x) xnew[r0 + t] = xs[t];
+}
+
 // t_i = b_i - (A x)_i for listed rows (first half of an l1-Jacobi sweep)
 template <typename T, int LPR>
 __global__ void __launch_bounds__(256) k_resid_rows(int32_t nrows, const int32_t *__restrict__ rows,
@@ -415,6 +567,23 @@ static double hgs_bytes(double ns, double nz, size_t es, bool xin) {
   return nz * (4.0 + es) + (ns + 1) * 4.0 + ns * es * (xin ? 3.0 : 2.0);
 }
 
+template <typename T>
+static const T *binv_of(const Level &L);
+template <>
+const float *binv_of<float>(const Level &L) { return L.binvf; }
+template <>
+const double *binv_of<double>(const Level &L) { return L.binv; }
+
+template <typename T>
+static void hgs2_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_hgs2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)hgs2_smem<T>(512, kHgsStageEntries));
+    done = true;
+  }
+}
+
 template <typename T, int LPR>
 static void hgs_attr() {
   static bool done = false;
@@ -447,6 +616,19 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
     const size_t shm = hgs_smem<T>(H.prm.chunk, stage);
     const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
     const int hl = hgs_lpr(L.A.n, L.A.nnz);
+    if (L.nfun == 2) {
+      const size_t shm2 = hgs2_smem<T>(H.prm.chunk, stage);
+      hgs2_attr<T>();
+      for (int sw = 0; sw < sweeps; sw++) {
+        T *out = (cur == xa) ? xb : xa;
+        ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);
+        RS_COUNTED launch_pdl(k_hgs2<T>, dim3(L.nchunk), dim3(256), shm2, s, L.chunk_row0, L.chunk_coff,
+                              L.chunk_rows, L.ncolour, H.prm.chunk, stage, L.hs_rp, L.hs_mid, L.hs_col,
+                              hs_vals<T>(L), binv_of<T>(L), b, (const T *)cur, out);
+        cur = out;
+      }
+      return;
+    }
     for (int sw = 0; sw < sweeps; sw++) {
       T *out = (cur == xa) ? xb : xa;
       ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);

@@ -18,7 +18,7 @@ import torch
 from . import build as _build
 
 RS_OK, RS_NOT_CONVERGED = 0, 1
-AMG_J, CPR1, CPR2, BF = 0, 1, 2, 3
+AMG_J, CPR1, CPR2, BF, AMG_J_SCALAR = 0, 1, 2, 3, 4
 DECOUPLE_NONE, DECOUPLE_ABF, DECOUPLE_QIMPES = 0, 1, 2
 FP32, FP64 = 0, 1
 

@@ -1,8 +1,8 @@
 """Full-size workloads on the GPU, checked by the oracle.
 
-* 256x256 log-normal (the benchmark workload): every CPR solve and the BF
-  solves that converge, FP32 and FP64 V-cycles, against the oracle's
-  solution (1e-6) and the oracle's residual (1e-8).
+* 256x256 log-normal (the benchmark workload): every black-box AMG (point
+  method) and CPR solve and the BF solves that converge, FP32 and FP64
+  V-cycles, against the oracle's solution (1e-6) and residual (1e-8).
 * 128^3 layered grid: the first Jacobian solved with FP32 and FP64
   hierarchies (true residual by the oracle, FP32-vs-FP64 difference), and ten
   backward-Euler time steps whose every result the oracle's residual accepts.
@@ -40,7 +40,7 @@ def test_lognormal_256_solves_match_oracle(R, oracle, inputs, pc):
     Fo, Jo, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
     b = -Fo
     J = R.Bsr2.from_host(rp, col, Jo)
-    kinds = [(1, 2)] + ([(3, 0)] if pc <= 1e3 else [])
+    kinds = [(0, 0), (1, 2)] + ([(3, 0)] if pc <= 1e3 else [])
     for kind, dec in kinds:
         xo, sto, ito, _ = oracle.fgmres(rp, col, Jo, b, oracle.Precond(rp, col, Jo, oracle.PrecParams(kind=kind, decouple=dec)),
                                         maxit=400)

@@ -154,7 +154,7 @@ def test_precond_hierarchies_bit_exact(R, oracle, inputs):
     u, uo = inputs.front_state(p)
     Fo, Jo, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
     J = R.Bsr2.from_host(rp, col, Jo)
-    for kind, dec in ((1, 2), (1, 1), (2, 2), (3, 0), (0, 0)):
+    for kind, dec in ((1, 2), (1, 1), (2, 2), (3, 0), (0, 0), (4, 0)):
         gM = R.Precond(J, R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(precision=R.FP64)))
         oM = oracle.Precond(rp, col, Jo, oracle.PrecParams(kind=kind, decouple=dec))
         _hier_compare(gM.amg(0), oM.amg(0))
@@ -171,6 +171,31 @@ def test_vcycle_fp64_matches_oracle(R, oracle, inputs, smoother):
     gh.apply(_dev(b), x)
     xo = oh.vcycle(b)
     np.testing.assert_allclose(x.cpu().numpy(), xo, rtol=1e-10, atol=1e-11 * np.abs(xo).max())
+
+
+@pytest.mark.parametrize("prec", ["FP32", "FP64"])
+def test_point_vcycle_matches_oracle(R, oracle, inputs, prec):
+    """Systems (point) AMG on the scalar two-phase J: point coarsening,
+    interleaved interpolation and the point-block hybrid smoother give the
+    oracle's V-cycle (FP64 to 1e-10, FP32 to 1e-5)."""
+    p = inputs.config_lognormal_2d(1e4, n=40)
+    u, uo = inputs.front_state(p)
+    Fo, Jo, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
+    arp, ac, av = oracle.scalar_from_bsr2(rp, col, Jo).arrays()
+    oh = oracle.Amg(oracle.Csr.from_arrays(arp, ac, av), oracle.AmgParams(num_functions=2))
+    gh = R.Amg.setup(R.Csr(arp, ac, av), R.AmgParams(num_functions=2, precision=getattr(R, prec)))
+    _hier_compare(gh, oh)
+    b = -Fo
+    x = torch.empty(b.size, dtype=torch.float64, device="cuda")
+    gh.apply(_dev(b), x)
+    xo = oh.vcycle(b)
+    xg = x.cpu().numpy()
+    for comp in (0, 1):
+        a, e = xg[comp::2], xo[comp::2]
+        if prec == "FP64":
+            np.testing.assert_allclose(a, e, rtol=1e-10, atol=1e-11 * np.abs(e).max())
+        else:
+            assert np.linalg.norm(a - e) / np.linalg.norm(e) < 1e-5
 
 
 def test_vcycle_fp32_close_to_oracle(R, oracle, inputs):
@@ -215,7 +240,7 @@ def _solve_pair(R, oracle, inputs, p, kind, dec, prec, rtol=1e-8, maxit=600):
 
 
 @pytest.mark.parametrize("prec", ["FP32", "FP64"])
-@pytest.mark.parametrize("kind,dec", [(1, 2), (1, 1), (1, 0), (2, 2), (3, 0)])
+@pytest.mark.parametrize("kind,dec", [(0, 0), (1, 2), (1, 1), (1, 0), (2, 2), (3, 0)])
 def test_gmres_solution_matches_oracle(R, oracle, inputs, prec, kind, dec):
     p = inputs.config_small_2d()
     st, xg, (rp, col, Jo, b) = _solve_pair(R, oracle, inputs, p, kind, dec, getattr(R, prec))
@@ -243,7 +268,8 @@ def test_gmres_unpreconditioned_and_zero_rhs(R, oracle, inputs):
     assert st.status == R.RS_OK and st.iterations == 0 and float(x0.abs().max()) == 0.0
 
 
-def test_batch_equals_single_systems(R, oracle, inputs):
+@pytest.mark.parametrize("kind", ["BF", "AMG_J"])
+def test_batch_equals_single_systems(R, oracle, inputs, kind):
     """Three systems of different sizes solved in one batch: each member's
     hierarchy equals its single-system hierarchy, each solution meets the
     tolerance and matches the single solve."""
@@ -256,7 +282,7 @@ def test_batch_equals_single_systems(R, oracle, inputs):
     R.jacobian_assemble(dp, _dev(np.concatenate(us)), _dev(np.concatenate(uos)), inputs.DAY, J, F)
     b = -F
     x = torch.zeros_like(b)
-    prm = R.PrecParams(kind=R.BF, amg=R.AmgParams(precision=R.FP32))
+    prm = R.PrecParams(kind=getattr(R, kind), decouple=0, amg=R.AmgParams(precision=R.FP32))
     M = R.Precond(J, prm)
     st = R.gmres_solve(J, M, b, x, R.GmresParams())
     assert st.status == R.RS_OK and st.converged == 3
@@ -305,7 +331,7 @@ def test_precond_hierarchies_bit_exact_3d(R, oracle, inputs):
     u, uo = inputs.front_state(p)
     Fo, Jo, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
     J = R.Bsr2.from_host(rp, col, Jo)
-    for kind, dec in ((1, 2), (3, 0)):
+    for kind, dec in ((1, 2), (3, 0), (0, 0)):
         gM = R.Precond(J, R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(theta=0.5, precision=R.FP64)))
         oM = oracle.Precond(rp, col, Jo, oracle.PrecParams(kind=kind, decouple=dec, amg=oracle.AmgParams(theta=0.5)))
         _hier_compare(gM.amg(0), oM.amg(0))
