@@ -176,15 +176,21 @@ class GpuStep:
                     torch.cuda.synchronize()
                     R.profile_begin()
                 self.xout[q].zero_()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                ev[0].record()
                 M = R.Precond(self.J, self.params(kind, dec))
+                ev[1].record()
                 st = R.gmres_solve(self.J, M, self.b, self.xout[q], R.GmresParams(m=30, maxit=self.maxit, rtol=1e-8))
+                ev[2].record()
                 M.close()
                 if per_solve_profile is not None:
                     torch.cuda.synchronize()
                     per_solve_profile[tag] = R.profile_end()
                 torch.cuda.nvtx.range_pop()
+                ev[2].synchronize()
                 recs.append(dict(pc=PC_SCALES[k], prec=name, its=int(st.iterations), relres=float(st.relres),
-                                 converged=bool(st.converged == 1)))
+                                 converged=bool(st.converged == 1), setup_ms=round(ev[0].elapsed_time(ev[1]), 3),
+                                 solve_ms=round(ev[1].elapsed_time(ev[2]), 3)))
                 q += 1
         return recs
 
@@ -475,6 +481,8 @@ def main():
                 units=f"{big['rows']} rows, {big['nnz']} entries",
                 bsr2_spmv=dict(achieved=s2, frac=s2 / peak, launch_ms=big["spmv_ms"], traffic=trs,
                                traffic_source=srcs, bytes_per_launch=big["spmv_bytes"], nnzb=big["nnzb"]),
+                transfer={k: dict(achieved=v["gbs"], frac=v["gbs"] / peak, launch_ms=v["ms"],
+                              bytes_per_launch=v["bytes"]) for k, v in big["transfer"].items()},
                 l2="flushed before the timed launches; working set > L2")
     spmv = dict(achieved=rl["spmv_bytes"] / (rl["spmv_ms"] * 1e-3) / 1e9, launch_ms=rl["spmv_ms"],
                 bytes_per_launch=rl["spmv_bytes"])

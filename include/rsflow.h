@@ -278,6 +278,15 @@ int amg_level_copy(const rs_amg *H, int32_t l, int32_t *a_row_ptr, int32_t *a_co
  * isolation; *bytes_per_sweep receives the algorithmic bytes one sweep moves
  * (matrix entries, row pointers, and the vectors read and written once). */
 int amg_level_smooth(const rs_amg *H, int32_t l, int32_t sweeps, double *bytes_per_sweep, cudaStream_t stream);
+/* `reps` back-to-back launches of one transfer kernel of the V-cycle on
+ * level l (l below the coarsest), on the hierarchy's own work vectors, for
+ * measuring it in isolation: which = 0 residual r_l = b_l - A_l x_l,
+ * 1 restriction b_{l+1} = R_l r_l, 2 prolongation with correction
+ * x_l += P_l x_{l+1}. *bytes_per_launch receives the algorithmic bytes of one
+ * launch (matrix entries and row pointers, vectors read and written once).
+ * RS_EINVAL for a level without a coarser one or an unknown `which`. */
+int amg_level_transfer(const rs_amg *H, int32_t l, int32_t which, int32_t reps, double *bytes_per_launch,
+                       cudaStream_t stream);
 
 /* Hierarchy inside a preconditioner: which = 0 pressure / Schur / black-box,
  * 1 saturation. NULL if absent. */

@@ -118,3 +118,9 @@ extern "C" int amg_level_smooth(const rs_amg *H, int32_t l, int32_t sweeps, doub
   if (!H || sweeps < 0) return fail(RS_EINVAL, "invalid arguments");
   return amg_level_sweeps(H->H, l, sweeps, bytes_per_sweep, stream);
 }
+
+extern "C" int amg_level_transfer(const rs_amg *H, int32_t l, int32_t which, int32_t reps, double *bytes_per_launch,
+                                  cudaStream_t stream) {
+  if (!H || reps < 0) return fail(RS_EINVAL, "invalid arguments");
+  return rs::amg_level_xfer(H->H, l, which, reps, bytes_per_launch, stream);
+}

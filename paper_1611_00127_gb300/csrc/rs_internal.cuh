@@ -207,6 +207,7 @@ void amg_free(Hier &H, cudaStream_t s);
 // x = V-cycle(b); FP64 in/out. `xin_zero` is always true here (zero guess).
 int amg_vcycle(const Hier &H, const double *b, double *x, cudaStream_t s);
 int amg_level_sweeps(const Hier &H, int32_t l, int sweeps, double *bytes_per_sweep, cudaStream_t s);
+int amg_level_xfer(const Hier &H, int32_t l, int which, int reps, double *bytes_per_launch, cudaStream_t s);
 // RS_ETIMEOUT (and clears the flag) if a smoother CTA gave up waiting for its
 // staging copies since the last call; synchronises the stream.
 int vcycle_wait_status(cudaStream_t s);

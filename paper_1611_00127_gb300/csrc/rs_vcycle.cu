@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(256) k_gs_colour(int32_t nrows, const int32_t 
 constexpr int kHgsStageEntries = 12288;
 constexpr int kHgsMaxColours = 128;
 constexpr int kHgsSpin = 1 << 20;     // bound on the mbarrier wait (iterations)
+constexpr int kHgsThreads = 256;      // threads per chunk CTA
 
 // Set when a smoother CTA gave up waiting for its staging copies; read and
 // cleared by vcycle_wait_status().
@@ -119,7 +120,7 @@ struct BulkRange {
 };
 
 template <typename T, int LPR>
-__global__ void __launch_bounds__(256) k_hgs(const int32_t *__restrict__ cr, const int32_t *__restrict__ coff,
+__global__ void __launch_bounds__(kHgsThreads) k_hgs(const int32_t *__restrict__ cr, const int32_t *__restrict__ coff,
                                              const int32_t *__restrict__ crows, int32_t ncol, int32_t cmax,
                                              int32_t stage_cap, const int32_t *__restrict__ hrp,
                                              const int32_t *__restrict__ hmid, const int32_t *__restrict__ hcol,
@@ -283,7 +284,7 @@ constexpr size_t hgs2_smem(int cmax, int stage) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_hgs2(const int32_t *__restrict__ cr, const int32_t *__restrict__ coff,
+__global__ void __launch_bounds__(kHgsThreads) k_hgs2(const int32_t *__restrict__ cr, const int32_t *__restrict__ coff,
                                               const int32_t *__restrict__ crows, int32_t ncol, int32_t cmax,
                                               int32_t stage_cap, const int32_t *__restrict__ hrp,
                                               const int32_t *__restrict__ hmid, const int32_t *__restrict__ hcol,
@@ -449,27 +450,39 @@ __global__ void k_jacobi_update(int32_t nrows, const int32_t *__restrict__ rows,
   x[i] += t[i] * inv[i];
 }
 
-// y = b - A x over all rows (b == nullptr: y = A x); `accum`: y += A x
+// y = b - A x over all rows (b == nullptr: y = A x); `accum`: y += A x.
+// Groups of LPR lanes take rows in a grid-stride loop (the grid is capped at
+// a few CTAs per SM, so large levels do not pay for tens of thousands of
+// short-lived CTAs); the trip count is uniform across each warp.
 template <typename T, int LPR, int MODE>
 __global__ void __launch_bounds__(256) k_csr(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                              const T *__restrict__ val, const T *__restrict__ x,
                                              const T *__restrict__ b, T *__restrict__ y) {
   RS_PDL_ENTRY();
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = tid / LPR;
+  const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / LPR;
   const int lane = threadIdx.x % LPR;
-  T s = T(0);
-  if (i < n) {
-    const int32_t e = __ldg(rp + i + 1);
-    for (int32_t k = __ldg(rp + i) + lane; k < e; k += LPR) s += __ldg(val + k) * __ldg(x + __ldg(col + k));
-  }
+  for (int64_t base = 0; base < n; base += groups) {
+    const int64_t i = base + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
+    T s = T(0);
+    if (i < n) {
+      const int32_t e = __ldg(rp + i + 1);
+      for (int32_t k = __ldg(rp + i) + lane; k < e; k += LPR) s += __ldg(val + k) * __ldg(x + __ldg(col + k));
+    }
 #pragma unroll
-  for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, LPR);
-  if (i < n && lane == 0) {
-    if (MODE == 0) y[i] = s;                 // y = A x
-    else if (MODE == 1) y[i] = b[i] - s;     // y = b - A x
-    else y[i] += s;                          // y += A x
+    for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, LPR);
+    if (i < n && lane == 0) {
+      if (MODE == 0) y[i] = s;                 // y = A x
+      else if (MODE == 1) y[i] = b[i] - s;     // y = b - A x
+      else y[i] += s;                          // y += A x
+    }
   }
+}
+
+// grid of a k_csr launch over n rows with LPR lanes each
+static unsigned csr_grid(int64_t n, int lpr) {
+  const int64_t need = (n * lpr + kBlock - 1) / kBlock;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  return (unsigned)std::max<int64_t>(1, std::min(need, cap));
 }
 
 // x[row] = A_c^{-1} b over the systems solved directly at this level, FP64
@@ -500,7 +513,8 @@ __global__ void k_cast(int64_t n, const A *__restrict__ a, B *__restrict__ b) {
   if (i < n) b[i] = (B)a[i];
 }
 
-// Lanes per row. FP32: enough lanes to cover a row in one or two steps.
+// Lanes per row. FP32: one lane for short rows (the row's entries share
+// cache lines, and no reduction is needed), more for long coarse-level rows.
 // FP64: GB300's FP64 pipe issues about 2 lanes per clock per SM, so every
 // warp-wide FP64 instruction is costly even with idle lanes; FP64 kernels use
 // one lane per row (two or four for long rows), which needs no FP64
@@ -513,10 +527,10 @@ static int pick_lpr(int32_t n, int32_t nnz) {
     if (avg <= 128.0) return 2;
     return 4;
   }
-  if (avg <= 6.0) return 4;
-  if (avg <= 14.0) return 8;
-  if (avg <= 40.0) return 16;
-  return 32;
+  if (avg <= 16.0) return 1;
+  if (avg <= 40.0) return 4;
+  if (avg <= 96.0) return 8;
+  return 16;
 }
 
 #define RS_LPR_SWITCH(lpr, ...)                  \
@@ -622,7 +636,7 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
       for (int sw = 0; sw < sweeps; sw++) {
         T *out = (cur == xa) ? xb : xa;
         ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);
-        RS_COUNTED launch_pdl(k_hgs2<T>, dim3(L.nchunk), dim3(256), shm2, s, L.chunk_row0, L.chunk_coff,
+        RS_COUNTED launch_pdl(k_hgs2<T>, dim3(L.nchunk), dim3(kHgsThreads), shm2, s, L.chunk_row0, L.chunk_coff,
                               L.chunk_rows, L.ncolour, H.prm.chunk, stage, L.hs_rp, L.hs_mid, L.hs_col,
                               hs_vals<T>(L), binv_of<T>(L), b, (const T *)cur, out);
         cur = out;
@@ -632,7 +646,7 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
     for (int sw = 0; sw < sweeps; sw++) {
       T *out = (cur == xa) ? xb : xa;
       ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);
-      RS_LPR_SWITCH(hl, hgs_attr<T, L_>(); RS_COUNTED launch_pdl(k_hgs<T, L_>, dim3(L.nchunk), dim3(256), shm, s,
+      RS_LPR_SWITCH(hl, hgs_attr<T, L_>(); RS_COUNTED launch_pdl(k_hgs<T, L_>, dim3(L.nchunk), dim3(kHgsThreads), shm, s,
                             L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, H.prm.chunk, stage, L.hs_rp,
                             L.hs_mid, L.hs_col, hs_vals<T>(L), dinv, b, (const T *)cur, out));
       cur = out;
@@ -680,20 +694,20 @@ static T *cycle(const Hier &H, int32_t l, cudaStream_t s) {
     const int lpr = pick_lpr<T>(L.A.n, L.A.nnz);
     {
       ProfScope ps(kProfCsr, L.A.nnz * (4.0 + sz) + (L.A.n + 1) * 4.0 + 3.0 * L.A.n * sz, s);
-      RS_LPR_SWITCH(lpr, RS_COUNTED launch_pdl(k_csr<T, L_, 1>, dim3(grid_for((int64_t)L.A.n * L_)), dim3(kBlock), 0, s,
+      RS_LPR_SWITCH(lpr, RS_COUNTED launch_pdl(k_csr<T, L_, 1>, dim3(csr_grid(L.A.n, L_)), dim3(kBlock), 0, s,
                              L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), (const T *)cur, static_cast<const T *>(L.b), r));
     }
     const int lr = pick_lpr<T>(L.R.n, L.R.nnz);
     {
       ProfScope ps(kProfCsr, L.R.nnz * (4.0 + sz) + (L.R.n + 1) * 4.0 + (L.R.n + L.A.n) * sz, s);
-      RS_LPR_SWITCH(lr, RS_COUNTED launch_pdl(k_csr<T, L_, 0>, dim3(grid_for((int64_t)L.R.n * L_)), dim3(kBlock), 0, s,
+      RS_LPR_SWITCH(lr, RS_COUNTED launch_pdl(k_csr<T, L_, 0>, dim3(csr_grid(L.R.n, L_)), dim3(kBlock), 0, s,
                             L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), (const T *)r, (const T *)nullptr, static_cast<T *>(N.b)));
     }
     const T *xc = cycle<T>(H, l + 1, s);
     const int lp = pick_lpr<T>(L.P.n, L.P.nnz);
     {
       ProfScope ps(kProfCsr, L.P.nnz * (4.0 + sz) + (L.P.n + 1) * 4.0 + (2.0 * L.P.n + L.R.n) * sz, s);
-      RS_LPR_SWITCH(lp, RS_COUNTED launch_pdl(k_csr<T, L_, 2>, dim3(grid_for((int64_t)L.P.n * L_)), dim3(kBlock), 0, s,
+      RS_LPR_SWITCH(lp, RS_COUNTED launch_pdl(k_csr<T, L_, 2>, dim3(csr_grid(L.P.n, L_)), dim3(kBlock), 0, s,
                             L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P), xc, (const T *)nullptr, cur));
     }
   }
@@ -715,6 +729,47 @@ static double level_sweeps(const Hier &H, int32_t l, int sweeps, cudaStream_t s)
   smooth<T>(H, L, sweeps, cur, s);
   const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
   return hgs_bytes(ns, nz, sizeof(T), true);
+}
+
+// Transfer kernels of level l, as the V-cycle launches them (same lanes per
+// row), on the level's own vectors.
+template <typename T>
+static double level_xfer(const Hier &H, int32_t l, int which, int reps, cudaStream_t s) {
+  const Level &L = H.L[l];
+  const Level &N = H.L[l + 1];
+  const double sz = sizeof(T);
+  T *x = static_cast<T *>(L.x), *r = static_cast<T *>(L.r);
+  for (int k = 0; k < reps; k++) {
+    if (which == 0) {
+      const int lpr = pick_lpr<T>(L.A.n, L.A.nnz);
+      RS_LPR_SWITCH(lpr, RS_COUNTED launch_pdl(k_csr<T, L_, 1>, dim3(csr_grid(L.A.n, L_)), dim3(kBlock), 0,
+                                               s, L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), (const T *)x,
+                                               static_cast<const T *>(L.b), r));
+    } else if (which == 1) {
+      const int lr = pick_lpr<T>(L.R.n, L.R.nnz);
+      RS_LPR_SWITCH(lr, RS_COUNTED launch_pdl(k_csr<T, L_, 0>, dim3(csr_grid(L.R.n, L_)), dim3(kBlock), 0,
+                                              s, L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), (const T *)r,
+                                              (const T *)nullptr, static_cast<T *>(N.b)));
+    } else {
+      const int lp = pick_lpr<T>(L.P.n, L.P.nnz);
+      RS_LPR_SWITCH(lp, RS_COUNTED launch_pdl(k_csr<T, L_, 2>, dim3(csr_grid(L.P.n, L_)), dim3(kBlock), 0,
+                                              s, L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P),
+                                              (const T *)static_cast<T *>(N.x), (const T *)nullptr, x));
+    }
+  }
+  if (which == 0) return L.A.nnz * (4.0 + sz) + (L.A.n + 1) * 4.0 + 3.0 * L.A.n * sz;
+  if (which == 1) return L.R.nnz * (4.0 + sz) + (L.R.n + 1) * 4.0 + (L.R.n + L.A.n) * sz;
+  return L.P.nnz * (4.0 + sz) + (L.P.n + 1) * 4.0 + (2.0 * L.P.n + L.R.n) * sz;
+}
+
+int amg_level_xfer(const Hier &H, int32_t l, int which, int reps, double *bytes_per_launch, cudaStream_t s) {
+  if (l < 0 || l + 1 >= H.nlev || !H.L[l].P.rowptr) return fail(RS_EINVAL, "level has no coarser level");
+  if (which < 0 || which > 2) return fail(RS_EINVAL, "unknown transfer kernel");
+  const double by = H.precision == RS_PREC_FP32 ? level_xfer<float>(H, l, which, reps, s)
+                                                : level_xfer<double>(H, l, which, reps, s);
+  if (bytes_per_launch) *bytes_per_launch = by;
+  RS_CHECK_CUDA(cudaGetLastError());
+  return 0;
 }
 
 int vcycle_wait_status(cudaStream_t s) {

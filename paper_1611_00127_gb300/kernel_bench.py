@@ -82,6 +82,22 @@ class Level0Case:
         torch.cuda.nvtx.range_pop()
         return e0.elapsed_time(e1) / reps, bsr2_spmv_bytes(self.J)
 
+    def time_transfer(self, which: int, reps: int, flush: torch.Tensor | None = None):
+        """(ms per launch, algorithmic bytes per launch) of one level-0
+        transfer kernel: 0 residual, 1 restriction, 2 prolongation."""
+        self.H.level_transfer(0, which, 3)
+        if flush is not None:
+            flush.add_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(("residual", "restrict", "prolong")[which])
+        e0.record()
+        by = self.H.level_transfer(0, which, reps)
+        e1.record()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        return e0.elapsed_time(e1) / reps, by
+
     def level0(self):
         n0, nnz0 = self.H.level_info(0)[:2]
         return n0, nnz0
@@ -97,11 +113,15 @@ def layered(n: int, precision: int, kind: int = R.CPR1, reps: int = 20) -> dict:
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     ts, bs = case.time_sweeps(reps, flush)
     tm, bm = case.time_spmv(reps, flush)
+    xfer = {}
+    for which, name in enumerate(("residual", "restrict", "prolong")):
+        t, by = case.time_transfer(which, reps, flush)
+        xfer[name] = dict(ms=t, bytes=by, gbs=by / (t * 1e-3) / 1e9)
     n0, nnz0 = case.level0()
     nnzb = case.J.nnzb
     case.close()
     return dict(sweep_ms=ts, sweep_bytes=bs, rows=n0, nnz=nnz0, spmv_ms=tm, spmv_bytes=bm, nnzb=nnzb,
-                spmv_lanes=case.lanes)
+                spmv_lanes=case.lanes, transfer=xfer)
 
 
 def lognormal(n: int, pc: float, precision: int, kind: int = R.BF, reps: int = 50, flush_l2: bool = False) -> dict:

@@ -113,6 +113,7 @@ def _declare(L):
         "amg_level_info": (C.c_int, [P, i32, P, P, P, P]),
         "amg_level_copy": (C.c_int, [P, i32, P, P, P, P, P, P, P, P, P]),
         "amg_level_smooth": (C.c_int, [P, i32, i32, P, P]),
+        "amg_level_transfer": (C.c_int, [P, i32, i32, i32, P, P]),
         "precond_create": (C.c_int, [P, P, P, P]),
         "precond_destroy": (C.c_int, [P]),
         "precond_apply": (C.c_int, [P, P, P, P]),
@@ -367,6 +368,13 @@ class Amg:
         """Run smoother sweeps on level l's own vectors; returns bytes per sweep."""
         by = C.c_double()
         _check(lib().amg_level_smooth(self.h, l, sweeps, C.byref(by), _stream(stream)), "amg_level_smooth")
+        return by.value
+
+    def level_transfer(self, l: int, which: int, reps: int, stream=None) -> float:
+        """Launch a transfer kernel of level l `reps` times (0 residual, 1
+        restriction, 2 prolongation); returns bytes per launch."""
+        by = C.c_double()
+        _check(lib().amg_level_transfer(self.h, l, which, reps, C.byref(by), _stream(stream)), "amg_level_transfer")
         return by.value
 
     def sizes(self) -> List[int]:
