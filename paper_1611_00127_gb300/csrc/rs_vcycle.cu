@@ -283,7 +283,7 @@ constexpr size_t hgs2_smem(int cmax, int stage) {
          sizeof(int32_t) * (kHgsMaxColours + 1);
 }
 
-template <typename T>
+template <typename T, int LPR>
 __global__ void __launch_bounds__(kHgsThreads) k_hgs2(const int32_t *__restrict__ cr, const int32_t *__restrict__ coff,
                                               const int32_t *__restrict__ crows, int32_t ncol, int32_t cmax,
                                               int32_t stage_cap, const int32_t *__restrict__ hrp,
@@ -373,46 +373,69 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs2(const int32_t *__restrict_
   const int32_t *srows = g_rw.dst;
   const int32_t *pcol = staged ? g_c.dst : hcol + p0;
   const T *pval = staged ? g_v.dst : hval + p0;
-  // right-hand sides less the couplings to other chunks
+  const int group = threadIdx.x / LPR, lane = threadIdx.x % LPR, ngroups = blockDim.x / LPR;
+  // right-hand sides less the couplings to other chunks, a group of LPR
+  // lanes per row (uniform trip count: the group shuffles see whole warps)
   if (xold) {
-    for (int32_t lr = threadIdx.x; lr < len; lr += blockDim.x) {
-      T acc = rhs[lr];
-      const int32_t m = lmd[lr] - p0, e = lrp[lr + 1] - p0;
-      for (int32_t q = m; q < e; q += 4) {
-        int32_t jj[4];
-        T aa[4], xx[4];
+    for (int32_t base = 0; base < len; base += ngroups) {
+      const int32_t lr = base + group;
+      const bool act = lr < len;
+      T acc = T(0);
+      if (act) {
+        if (lane == 0) acc = rhs[lr];
+        const int32_t m = lmd[lr] - p0, e = lrp[lr + 1] - p0;
+        for (int32_t q = m + lane; q < e; q += 4 * LPR) {
+          int32_t jj[4];
+          T aa[4], xx[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          jj[u] = q + u < e ? pcol[q + u] : -1;
-          aa[u] = q + u < e ? pval[q + u] : T(0);
+          for (int u = 0; u < 4; u++) {
+            const int32_t qq = q + u * LPR;
+            jj[u] = qq < e ? pcol[qq] : -1;
+            aa[u] = qq < e ? pval[qq] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; u++) xx[u] = jj[u] >= 0 ? __ldg(xold + jj[u]) : T(0);
+#pragma unroll
+          for (int u = 0; u < 4; u++)
+            if (jj[u] >= 0) acc -= aa[u] * xx[u];
         }
-#pragma unroll
-        for (int u = 0; u < 4; u++) xx[u] = jj[u] >= 0 ? __ldg(xold + jj[u]) : T(0);
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-          if (jj[u] >= 0) acc -= aa[u] * xx[u];
       }
-      rhs[lr] = acc;
+#pragma unroll
+      for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, LPR);
+      if (act && lane == 0) rhs[lr] = acc;
     }
   }
   __syncthreads();
+  // colour passes: a group per point, its two rows' in-chunk sums, then the
+  // 2 x 2 block solve
   for (int32_t c = 0; c < ncol; c++) {
     const int32_t beg = scof[c], end = scof[c + 1];
-    for (int32_t pos = beg + threadIdx.x; pos < end; pos += blockDim.x) {
-      const int32_t li = srows[pos];
-      T acc[2];
+    for (int32_t base = beg; base < end; base += ngroups) {
+      const int32_t pos = base + group;
+      int32_t li = -1;
+      T acc[2] = {T(0), T(0)};
+      if (pos < end) {
+        li = srows[pos];
 #pragma unroll
-      for (int f = 0; f < 2; f++) {
-        const int32_t lr = 2 * li + f;
-        T a = rhs[lr];
-        const int32_t s0 = lrp[lr] - p0, m = lmd[lr] - p0;
-        for (int32_t q = s0; q < m; q++) a -= pval[q] * xs[pcol[q]];
-        acc[f] = a;
+        for (int f = 0; f < 2; f++) {
+          const int32_t lr = 2 * li + f;
+          T a = lane == 0 ? rhs[lr] : T(0);
+          const int32_t s0 = lrp[lr] - p0, m = lmd[lr] - p0;
+          for (int32_t q = s0 + lane; q < m; q += LPR) a -= pval[q] * xs[pcol[q]];
+          acc[f] = a;
+        }
       }
-      const T *mi = dv + 4 * li;
-      if (mi[0] != T(0) || mi[1] != T(0) || mi[2] != T(0) || mi[3] != T(0)) {
-        xs[2 * li] = mi[0] * acc[0] + mi[1] * acc[1];
-        xs[2 * li + 1] = mi[2] * acc[0] + mi[3] * acc[1];
+#pragma unroll
+      for (int o = LPR / 2; o > 0; o >>= 1) {
+        acc[0] += __shfl_down_sync(0xffffffffu, acc[0], o, LPR);
+        acc[1] += __shfl_down_sync(0xffffffffu, acc[1], o, LPR);
+      }
+      if (li >= 0 && lane == 0) {
+        const T *mi = dv + 4 * li;
+        if (mi[0] != T(0) || mi[1] != T(0) || mi[2] != T(0) || mi[3] != T(0)) {
+          xs[2 * li] = mi[0] * acc[0] + mi[1] * acc[1];
+          xs[2 * li + 1] = mi[2] * acc[0] + mi[3] * acc[1];
+        }
       }
     }
     __syncthreads();
@@ -564,14 +587,32 @@ const float *hs_vals<float>(const Level &L) { return L.hs_valf; }
 template <>
 const double *hs_vals<double>(const Level &L) { return L.hs_val; }
 
-// Lanes per row of the hybrid sweep: its inner loops run over a row's packed
-// entries in shared memory (about half the row on each side of the chunk
-// boundary), so one lane per row unless rows are long.
-static int hgs_lpr(int32_t n, int32_t nnz) {
+// Lanes per row of the hybrid sweep. Its inner loops run over a row's packed
+// entries in shared memory. With at least half as many chunks as SMs the
+// sweep is bandwidth-bound: one lane per row unless rows are long, which also
+// keeps FP64 free of shuffle additions. With fewer chunks, a few CTAs walk
+// the rows colour by colour, and the chains of dependent shared-memory loads
+// and FMAs per row set the time, so more lanes shorten each chain; with very
+// few chunks (under 16) even short rows are split.
+static int hgs_lpr(int32_t n, int32_t nnz, int32_t nchunk) {
   const double avg = n > 0 ? (double)nnz / n : 1.0;
-  if (avg <= 16.0) return 1;
-  if (avg <= 64.0) return 4;
-  return 8;
+  if (2 * nchunk >= num_sms()) {
+    if (avg <= 16.0) return 1;
+    if (avg <= 64.0) return 4;
+    return 8;
+  }
+  if (nchunk >= 16) {
+    if (avg <= 6.0) return 1;
+    if (avg <= 16.0) return 2;
+    if (avg <= 32.0) return 4;
+    if (avg <= 64.0) return 8;
+    return 16;
+  }
+  if (avg <= 6.0) return 1;
+  if (avg <= 12.0) return 2;
+  if (avg <= 24.0) return 4;
+  if (avg <= 48.0) return 8;
+  return 16;
 }
 
 // Algorithmic bytes of one hybrid sweep over ns rows holding nz entries: the
@@ -588,11 +629,11 @@ const float *binv_of<float>(const Level &L) { return L.binvf; }
 template <>
 const double *binv_of<double>(const Level &L) { return L.binv; }
 
-template <typename T>
+template <typename T, int LPR>
 static void hgs2_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_hgs2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_hgs2<T, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)hgs2_smem<T>(512, kHgsStageEntries));
     done = true;
   }
@@ -629,16 +670,15 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
     const int32_t stage = std::min(L.chunk_max_nnz, kHgsStageEntries);
     const size_t shm = hgs_smem<T>(H.prm.chunk, stage);
     const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
-    const int hl = hgs_lpr(L.A.n, L.A.nnz);
+    const int hl = hgs_lpr(L.A.n, L.A.nnz, L.nchunk);
     if (L.nfun == 2) {
       const size_t shm2 = hgs2_smem<T>(H.prm.chunk, stage);
-      hgs2_attr<T>();
       for (int sw = 0; sw < sweeps; sw++) {
         T *out = (cur == xa) ? xb : xa;
         ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);
-        RS_COUNTED launch_pdl(k_hgs2<T>, dim3(L.nchunk), dim3(kHgsThreads), shm2, s, L.chunk_row0, L.chunk_coff,
-                              L.chunk_rows, L.ncolour, H.prm.chunk, stage, L.hs_rp, L.hs_mid, L.hs_col,
-                              hs_vals<T>(L), binv_of<T>(L), b, (const T *)cur, out);
+        RS_LPR_SWITCH(hl, hgs2_attr<T, L_>(); RS_COUNTED launch_pdl(k_hgs2<T, L_>, dim3(L.nchunk), dim3(kHgsThreads),
+                              shm2, s, L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, H.prm.chunk, stage,
+                              L.hs_rp, L.hs_mid, L.hs_col, hs_vals<T>(L), binv_of<T>(L), b, (const T *)cur, out));
         cur = out;
       }
       return;
