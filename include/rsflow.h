@@ -45,6 +45,10 @@ extern "C" {
 #define RS_ESETUP (-5)
 #define RS_EBREAKDOWN (-6)
 
+/* Empty systems (nb = 0, n = 0) are valid everywhere: vector arguments may
+ * then be NULL, set-up builds nothing, applies and solves return RS_OK at once
+ * (a solve reports 0 iterations, converged). */
+
 /* 2x2-block CSR matrix, FP64. Block k (columns col[k]) is stored row-major at
  * val[4k..4k+3] = [dF_w/dP_w, dF_w/dS_n, dF_n/dP_w, dF_n/dS_n]; this is the
  * grid-point ordering of Sec. 3.2, with the blocks A_pp, A_ps, A_sp, A_ss of

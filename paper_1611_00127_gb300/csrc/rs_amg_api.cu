@@ -57,7 +57,8 @@ extern "C" int amg_destroy(rs_amg *H) {
 }
 
 extern "C" int amg_apply(const rs_amg *H, const double *b, double *x, cudaStream_t stream) {
-  if (!H || !b || !x) return fail(RS_EINVAL, "null argument");
+  if (!H) return fail(RS_EINVAL, "null argument");
+  if ((!b || !x) && H->H.nlev > 0 && H->H.L[0].A.n > 0) return fail(RS_EINVAL, "null argument");
   return amg_vcycle(H->H, b, x, stream);
 }
 

@@ -1059,6 +1059,13 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
   H.L.reserve(33);
   H.last_level.assign(H.nseg, -1);
   const int32_t maxl = std::max(1, std::min(prm.max_levels, 32));
+  if (A0.n == 0) {   // empty system: one empty level, nothing to coarsen or solve
+    H.L.emplace_back();
+    H.L[0].seg_off = seg_off0;
+    H.nlev = 1;
+    H.last_level.assign(H.nseg, 0);
+    return 0;
+  }
   const int32_t nfun0 = std::max(1, prm.num_functions);
   // level 0 owns a copy of A
   H.L.emplace_back();

@@ -265,7 +265,7 @@ __global__ void k_cycle_start(int32_t nseg, const double *__restrict__ beta, con
 
 extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *b, double *x,
                            const rs_gmres_params *params, rs_gmres_stats *stats, cudaStream_t s) {
-  if (!J || !b || !x || !params) return fail(RS_EINVAL, "null argument");
+  if (!J || !params || ((!b || !x) && J->nb > 0)) return fail(RS_EINVAL, "null argument");
   if (J->nb < 0 || (J->nb > 0 && (!J->row_ptr || !J->col || !J->val))) return fail(RS_EINVAL, "invalid matrix");
   const int m = params->m;
   if (m < 1 || m > 63) return fail(RS_EINVAL, "restart length must be in [1, 63]");
@@ -274,6 +274,18 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
   if (boff.front() != 0 || boff.back() != J->nb) return fail(RS_EINVAL, "segment offsets must run from 0 to nb");
   const int32_t nseg = (int32_t)boff.size() - 1;
   const int64_t n = 2 * (int64_t)J->nb;
+  if (n == 0) {   // empty system(s): converged with no iterations
+    if (stats) {
+      stats->iterations = 0;
+      stats->converged = nseg;
+      stats->relres = 0.0;
+      for (int32_t q = 0; q < nseg; q++) {
+        if (stats->its) stats->its[q] = 0;
+        if (stats->relres_seg) stats->relres_seg[q] = 0.0;
+      }
+    }
+    return RS_OK;
+  }
   // chunk table
   std::vector<Chunk> chunks;
   std::vector<int32_t> seg_chunk(nseg + 1, 0);

@@ -151,6 +151,7 @@ int build(rs_precond *M, cudaStream_t s) {
   const int32_t nb = J.nb;
   const rs_precond_params &p = M->prm;
   const int kind = p.kind;
+  if (nb == 0) return 0;   // empty system: applying M is a no-op
   RS_TRY(dalloc_n(&M->rt, 2 * (size_t)nb, s));
   RS_TRY(dalloc_n(&M->sb, (size_t)nb, s));
   RS_TRY(dalloc_n(&M->ss, (size_t)nb, s));
@@ -376,7 +377,7 @@ extern "C" int precond_destroy(rs_precond *M) {
 }
 
 extern "C" int precond_apply(const rs_precond *M, const double *r, double *z, cudaStream_t stream) {
-  if (!M || !r || !z) return fail(RS_EINVAL, "null argument");
+  if (!M || ((!r || !z) && M->nb > 0)) return fail(RS_EINVAL, "null argument");
   return precond_apply_impl(M, r, z, stream);
 }
 

@@ -93,14 +93,14 @@ static int check_bsr2(const rs_bsr2 *J) {
 
 extern "C" int bsr2_spmv(const rs_bsr2 *J, const double *x, double *y, cudaStream_t stream) {
   RS_TRY(check_bsr2(J));
-  if (!x || !y) return fail(RS_EINVAL, "null vector");
+  if ((!x || !y) && J->nb > 0) return fail(RS_EINVAL, "null vector");
   return launch_bsr2_spmv(*J, x, y, stream);
 }
 
 extern "C" int bsr2_residual(const rs_bsr2 *J, const double *x, const double *b, double *r,
                              cudaStream_t stream) {
   RS_TRY(check_bsr2(J));
-  if (!x || !b || !r) return fail(RS_EINVAL, "null vector");
+  if ((!x || !b || !r) && J->nb > 0) return fail(RS_EINVAL, "null vector");
   return launch_bsr2_residual(*J, x, b, r, stream);
 }
 
@@ -108,7 +108,7 @@ extern "C" int bsr2_residual(const rs_bsr2 *J, const double *x, const double *b,
 // caller's stream, after a warm-up) and keeps the fastest.
 extern "C" int rs_autotune_bsr2(const rs_bsr2 *J, const double *x, double *y, int *best, cudaStream_t stream) {
   RS_TRY(check_bsr2(J));
-  if (!x || !y) return fail(RS_EINVAL, "null vector");
+  if ((!x || !y) && J->nb > 0) return fail(RS_EINVAL, "null vector");
   const int cand[4] = {1, 2, 4, 8};
   float bt = 1e30f;
   int bl = g_bsr2_lpr;

@@ -128,6 +128,11 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs(const int32_t *__restrict__
                                              const T *__restrict__ b, const T *__restrict__ xold,
                                              T *__restrict__ xnew) {
   RS_PDL_ENTRY();
+  // entries of the out-of-chunk pass in flight per lane: four for FP32; two
+  // for FP64, where every issued FMA costs FP64-pipe time even for lanes
+  // past their row's end (rows of 7-point levels have two or three such
+  // entries)
+  constexpr int kOffU = sizeof(T) == 8 ? 2 : 4;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   unsigned char *seg = smem;
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs(const int32_t *__restrict__
   const T *pval = staged ? g_v.dst : hval + p0;
   const int group = threadIdx.x / LPR, lane = threadIdx.x % LPR, ngroups = blockDim.x / LPR;
   // rhs_i = b_i - sum_j a_ij xold_j over other chunks (uniform trip count:
-  // the group shuffles see whole warps); four gathers in flight per lane
+  // the group shuffles see whole warps); kOffU gathers in flight per lane
   if (xold) {
     for (int32_t base = 0; base < len; base += ngroups) {
       const int32_t li = base + group;
@@ -221,19 +226,19 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs(const int32_t *__restrict__
       if (act) {
         if (lane == 0) off = rhs[li];
         const int32_t m = lmd[li] - p0, e = lrp[li + 1] - p0;
-        for (int32_t q = m + lane; q < e; q += 4 * LPR) {
-          int32_t jj[4];
-          T aa[4], xx[4];
+        for (int32_t q = m + lane; q < e; q += kOffU * LPR) {
+          int32_t jj[kOffU];
+          T aa[kOffU], xx[kOffU];
 #pragma unroll
-          for (int u = 0; u < 4; u++) {
+          for (int u = 0; u < kOffU; u++) {
             const int32_t qq = q + u * LPR;
             jj[u] = qq < e ? pcol[qq] : -1;
             aa[u] = qq < e ? pval[qq] : T(0);
           }
 #pragma unroll
-          for (int u = 0; u < 4; u++) xx[u] = jj[u] >= 0 ? __ldg(xold + jj[u]) : T(0);
+          for (int u = 0; u < kOffU; u++) xx[u] = jj[u] >= 0 ? __ldg(xold + jj[u]) : T(0);
 #pragma unroll
-          for (int u = 0; u < 4; u++)
+          for (int u = 0; u < kOffU; u++)
             if (jj[u] >= 0) off -= aa[u] * xx[u];
         }
       }
@@ -292,6 +297,11 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs2(const int32_t *__restrict_
                                               const T *__restrict__ b, const T *__restrict__ xold,
                                               T *__restrict__ xnew) {
   RS_PDL_ENTRY();
+  // entries of the out-of-chunk pass in flight per lane: four for FP32; two
+  // for FP64, where every issued FMA costs FP64-pipe time even for lanes
+  // past their row's end (rows of 7-point levels have two or three such
+  // entries)
+  constexpr int kOffU = sizeof(T) == 8 ? 2 : 4;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar;
   unsigned char *seg = smem;
@@ -384,19 +394,19 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs2(const int32_t *__restrict_
       if (act) {
         if (lane == 0) acc = rhs[lr];
         const int32_t m = lmd[lr] - p0, e = lrp[lr + 1] - p0;
-        for (int32_t q = m + lane; q < e; q += 4 * LPR) {
-          int32_t jj[4];
-          T aa[4], xx[4];
+        for (int32_t q = m + lane; q < e; q += kOffU * LPR) {
+          int32_t jj[kOffU];
+          T aa[kOffU], xx[kOffU];
 #pragma unroll
-          for (int u = 0; u < 4; u++) {
+          for (int u = 0; u < kOffU; u++) {
             const int32_t qq = q + u * LPR;
             jj[u] = qq < e ? pcol[qq] : -1;
             aa[u] = qq < e ? pval[qq] : T(0);
           }
 #pragma unroll
-          for (int u = 0; u < 4; u++) xx[u] = jj[u] >= 0 ? __ldg(xold + jj[u]) : T(0);
+          for (int u = 0; u < kOffU; u++) xx[u] = jj[u] >= 0 ? __ldg(xold + jj[u]) : T(0);
 #pragma unroll
-          for (int u = 0; u < 4; u++)
+          for (int u = 0; u < kOffU; u++)
             if (jj[u] >= 0) acc -= aa[u] * xx[u];
         }
       }

@@ -1,0 +1,107 @@
+"""Edge cases of the GPU path through the C-ABI, against the oracle or exact
+solves: an empty system, a single cell, a one-row strip (1D flow), a ragged
+batch with a single-cell member, and a one-level hierarchy (the V-cycle is
+then the dense coarse solve, so FGMRES converges in one iteration)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1611_00127_gb300 import rsflow
+    rsflow.lib()
+    return rsflow
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def test_empty_system(R):
+    J = R.Bsr2.from_host(np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    x = torch.zeros(0, dtype=torch.float64, device="cuda")
+    y = torch.zeros(0, dtype=torch.float64, device="cuda")
+    R.bsr2_spmv(J, x, y)
+    for kind in (R.AMG_J, R.CPR1, R.CPR2, R.BF):
+        M = R.Precond(J, R.PrecParams(kind=kind, decouple=0))
+        M.apply(x, y)
+        st = R.gmres_solve(J, M, x, y, R.GmresParams())
+        assert st.status == R.RS_OK and st.iterations == 0 and st.converged == 1
+        M.close()
+    H = R.Amg.setup(R.Csr(np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0)), R.AmgParams())
+    assert H.nlevels == 1 and H.level_info(0)[0] == 0
+    H.apply(x, y)
+    torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (300, 1), (1, 150)])
+@pytest.mark.parametrize("kind,dec", [(0, 0), (1, 2), (3, 0)])
+def test_tiny_and_strip_grids_match_dense_solve(R, oracle, inputs, shape, kind, dec):
+    p = inputs.homogeneous(*shape).with_(pc_model=2, pc_pd=5e3)
+    u, uo = inputs.front_state(p)
+    dp = R.DeviceProblems(p)
+    J = R.Bsr2.pattern(dp)
+    F = torch.empty(2 * p.ncell, dtype=torch.float64, device="cuda")
+    R.jacobian_assemble(dp, _dev(u), _dev(uo), inputs.DAY, J, F)
+    Fo, Jo, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
+    np.testing.assert_allclose(F.cpu().numpy(), Fo, rtol=1e-10, atol=1e-12 * np.abs(Fo).max())
+    x = torch.zeros_like(F)
+    for prec in (R.FP32, R.FP64):
+        x.zero_()
+        M = R.Precond(J, R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(precision=prec)))
+        st = R.gmres_solve(J, M, -F, x, R.GmresParams(maxit=200))
+        assert st.status == R.RS_OK, (shape, kind, prec, st)
+        A = oracle.bsr2_to_scipy(rp, col, Jo).toarray()
+        xe = np.linalg.solve(A, -Fo)
+        np.testing.assert_allclose(x.cpu().numpy(), xe, rtol=1e-6, atol=1e-6 * np.abs(xe).max())
+        M.close()
+
+
+def test_ragged_batch_with_single_cell_member(R, oracle, inputs):
+    probs = [inputs.homogeneous(1, 1).with_(pc_model=2, pc_pd=5e3), inputs.config_lognormal_2d(1e4, n=40, member=3),
+             inputs.homogeneous(7, 1).with_(pc_model=2, pc_pd=5e3), inputs.homogeneous(3, 5).with_(pc_model=2, pc_pd=5e3)]
+    states = [inputs.front_state(p) for p in probs]
+    dp = R.DeviceProblems(probs)
+    J = R.Bsr2.pattern(dp)
+    F = torch.empty(2 * dp.ncell, dtype=torch.float64, device="cuda")
+    R.jacobian_assemble(dp, _dev(np.concatenate([s[0] for s in states])),
+                        _dev(np.concatenate([s[1] for s in states])), inputs.DAY, J, F)
+    for kind, dec in ((0, 0), (1, 2), (3, 0)):
+        x = torch.zeros_like(F)
+        M = R.Precond(J, R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(precision=R.FP32)))
+        st = R.gmres_solve(J, M, -F, x, R.GmresParams(maxit=300))
+        assert st.status == R.RS_OK and st.converged == len(probs), (kind, st)
+        xg = x.cpu().numpy()
+        off = dp.cell_off
+        for k, p in enumerate(probs):
+            Fo, Jo, (rp, col) = oracle.assemble(p, states[k][0], states[k][1], inputs.DAY)
+            res = -Fo - oracle.bsr2_spmv(rp, col, Jo, xg[2 * off[k]:2 * off[k + 1]])
+            assert np.linalg.norm(res) <= 1.0001e-8 * np.linalg.norm(Fo), (kind, k)
+        M.close()
+
+
+def test_one_level_hierarchy_is_exact(R, oracle, inputs):
+    """coarse_n above the system size: no coarsening, the V-cycle is the dense
+    FP64 coarse solve, and FGMRES preconditioned by it converges at once."""
+    p = inputs.config_lognormal_2d(1e3, n=12)
+    u, uo = inputs.front_state(p)
+    Fo, Jo, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
+    App = oracle.bsr2_part(rp, col, Jo, 0, 0)
+    arp, ac, av = App.arrays()
+    H = R.Amg.setup(R.Csr(arp, ac, av), R.AmgParams(coarse_n=10 ** 6, precision=R.FP64))
+    assert H.nlevels == 1
+    b = inputs.rhs_vector(p.ncell, 4)
+    x = torch.empty(p.ncell, dtype=torch.float64, device="cuda")
+    H.apply(_dev(b), x)
+    xe = np.linalg.solve(App.scipy().toarray(), b)
+    np.testing.assert_allclose(x.cpu().numpy(), xe, rtol=1e-10, atol=1e-12 * np.abs(xe).max())
+    J = R.Bsr2.from_host(rp, col, Jo)
+    M = R.Precond(J, R.PrecParams(kind=R.AMG_J, amg=R.AmgParams(coarse_n=10 ** 6, precision=R.FP64)))
+    xj = torch.zeros(2 * p.ncell, dtype=torch.float64, device="cuda")
+    st = R.gmres_solve(J, M, _dev(-Fo), xj, R.GmresParams())
+    assert st.status == R.RS_OK and st.iterations == 1
