@@ -44,7 +44,10 @@ KINDS = (("amgJ", 0, 0), ("cpr1", 1, 2), ("bf", 3, 0))
 # capture of the current kernel version (summaries and commands in profiles/);
 # None where no capture of the current version exists.
 NCU_TRAFFIC = {
-    ("k_hgs", "fp64", "layered128"): (225.416704e6 + 12.058624e6, "profiles/k_hgs_fp64_layered128_level0.md"),
+    ("k_hgs", "fp64", "lognormal256bf"): (11.759872e6 + 0.0, "profiles/k_hgs_fp64_lognormal256_bf_level0.md"),
+    ("k_hgs", "fp64", "layered128"): (225.427968e6 + 12.004352e6, "profiles/k_hgs_fp64_layered128_level0.md"),
+    ("k_csr_residual", "fp32", "layered128"): (141.960448e6 + 6.054144e6,
+                                             "profiles/k_csr_residual_fp32_layered128_level0.md"),
     ("k_hgs", "fp32", "layered128"): (150.325760e6 + 6.161408e6, "profiles/k_hgs_fp32_layered128_level0.md"),
     ("k_bsr2_spmv", "f64", "layered128"): (608.675840e6 + 30.454272e6, "profiles/k_bsr2_spmv_layered128.md"),
 }
@@ -460,7 +463,9 @@ def main():
     rl = sweep_roofline(probs, states, R.FP64)
     achieved = rl["sweep_bytes"] / (rl["sweep_ms"] * 1e-3) / 1e9
     roofline = dict(bound="hbm", kernel="k_hgs (hybrid multicolour Gauss-Seidel sweep, FP64)",
-                    achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=None,
+                    achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                    traffic=NCU_TRAFFIC[("k_hgs", "fp64", "lognormal256bf")][0],
+                    traffic_source=NCU_TRAFFIC[("k_hgs", "fp64", "lognormal256bf")][1] + " (caches flushed by ncu)",
                     peak_source=peak_kind, launch_ms=rl["sweep_ms"], bytes_per_launch=rl["sweep_bytes"],
                     units=f"level 0 of the Schur-complement hierarchy: {rl['rows']} rows, {rl['nnz']} entries",
                     note="working set of this 256x256 workload is L2-resident (<129 MB); roofline_large repeats "
@@ -482,7 +487,9 @@ def main():
                 bsr2_spmv=dict(achieved=s2, frac=s2 / peak, launch_ms=big["spmv_ms"], traffic=trs,
                                traffic_source=srcs, bytes_per_launch=big["spmv_bytes"], nnzb=big["nnzb"]),
                 transfer={k: dict(achieved=v["gbs"], frac=v["gbs"] / peak, launch_ms=v["ms"],
-                              bytes_per_launch=v["bytes"]) for k, v in big["transfer"].items()},
+                              bytes_per_launch=v["bytes"],
+                              traffic=NCU_TRAFFIC.get(("k_csr_" + k, pname, "layered128"), (None,))[0])
+                          for k, v in big["transfer"].items()},
                 l2="flushed before the timed launches; working set > L2")
     spmv = dict(achieved=rl["spmv_bytes"] / (rl["spmv_ms"] * 1e-3) / 1e9, launch_ms=rl["spmv_ms"],
                 bytes_per_launch=rl["spmv_bytes"])

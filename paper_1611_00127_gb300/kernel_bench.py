@@ -34,7 +34,7 @@ def bsr2_spmv_bytes(J: R.Bsr2) -> float:
 class Level0Case:
     """Assembled Jacobian, preconditioner and level-0 hierarchy of one grid."""
 
-    def __init__(self, p, state, precision: int, kind: int = R.CPR1, theta: float = 0.5):
+    def __init__(self, p, state, precision: int, kind: int = R.CPR1, theta: float = 0.5, chunk: int = 512):
         self.p = p
         u, uo = state
         self.dp = R.DeviceProblems(p)
@@ -42,7 +42,8 @@ class Level0Case:
         self.F = torch.empty(2 * p.ncell, dtype=torch.float64, device="cuda")
         R.jacobian_assemble(self.dp, torch.as_tensor(u, device="cuda"), torch.as_tensor(uo, device="cuda"),
                             I.DAY, self.J, self.F)
-        self.M = R.Precond(self.J, R.PrecParams(kind=kind, amg=R.AmgParams(theta=theta, precision=precision)))
+        self.M = R.Precond(self.J, R.PrecParams(kind=kind, amg=R.AmgParams(theta=theta, precision=precision,
+                                                                           chunk=chunk)))
         self.H = self.M.amg(0)
         z = torch.empty_like(self.F)
         self.M.apply(self.F, z)          # leaves a right-hand side on every level
@@ -106,10 +107,10 @@ class Level0Case:
         self.M.close()
 
 
-def layered(n: int, precision: int, kind: int = R.CPR1, reps: int = 20) -> dict:
+def layered(n: int, precision: int, kind: int = R.CPR1, reps: int = 20, chunk: int = 512) -> dict:
     """Sweep and SpMV timings on the n^3 layered workload, L2 flushed."""
     p = I.config_layered_3d(n)
-    case = Level0Case(p, I.front_state(p), precision, kind)
+    case = Level0Case(p, I.front_state(p), precision, kind, chunk=chunk)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     ts, bs = case.time_sweeps(reps, flush)
     tm, bm = case.time_spmv(reps, flush)
@@ -124,12 +125,13 @@ def layered(n: int, precision: int, kind: int = R.CPR1, reps: int = 20) -> dict:
                 spmv_lanes=case.lanes, transfer=xfer)
 
 
-def lognormal(n: int, pc: float, precision: int, kind: int = R.BF, reps: int = 50, flush_l2: bool = False) -> dict:
+def lognormal(n: int, pc: float, precision: int, kind: int = R.BF, reps: int = 50, flush_l2: bool = False,
+              chunk: int = 512) -> dict:
     """Sweep and SpMV timings on the n x n log-normal grid with capillary scale
     `pc` (2D strength threshold 0.25). Without `flush_l2` the operands stay
     in L2 between launches, as they do inside a solve of this size."""
     p = I.config_lognormal_2d(pc, n=n)
-    case = Level0Case(p, I.front_state(p), precision, kind, theta=0.25)
+    case = Level0Case(p, I.front_state(p), precision, kind, theta=0.25, chunk=chunk)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda") if flush_l2 else None
     ts, bs = case.time_sweeps(reps, flush)
     tm, bm = case.time_spmv(reps, flush)
@@ -148,16 +150,17 @@ def main():
     ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--kind", choices=["cpr1", "bf"], default="cpr1")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--chunk", type=int, default=512, help="rows per chunk of the hybrid smoother")
     a = ap.parse_args()
     prec = R.FP64 if a.prec == "fp64" else R.FP32
     kind = R.CPR1 if a.kind == "cpr1" else R.BF
     if a.grid == "layered3d":
         a.n = a.n or 128
-        r = layered(a.n, prec, kind, a.reps)
+        r = layered(a.n, prec, kind, a.reps, a.chunk)
     else:
         a.n = a.n or 256
-        r = lognormal(a.n, a.pc, prec, kind, a.reps)
-    r.update(grid=a.grid, n=a.n, prec=a.prec, kind=a.kind,
+        r = lognormal(a.n, a.pc, prec, kind, a.reps, chunk=a.chunk)
+    r.update(grid=a.grid, n=a.n, prec=a.prec, kind=a.kind, chunk=a.chunk,
              sweep_gbs=r["sweep_bytes"] / (r["sweep_ms"] * 1e-3) / 1e9,
              spmv_gbs=r["spmv_bytes"] / (r["spmv_ms"] * 1e-3) / 1e9,
              device_used_gb=(lambda fr: (fr[1] - fr[0]) / 1e9)(torch.cuda.mem_get_info()))
