@@ -23,7 +23,7 @@ using namespace rs;
 
 namespace {
 
-constexpr int kChunk = 2048;   // rows per reduction block
+constexpr int kChunk = 512;    // rows per reduction block (FP64 work spread over every SM)
 constexpr int kRedThreads = 256;
 
 struct Chunk {
