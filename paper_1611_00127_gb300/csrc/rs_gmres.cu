@@ -23,7 +23,15 @@ using namespace rs;
 
 namespace {
 
-constexpr int kChunk = 512;    // rows per reduction block (FP64 work spread over every SM)
+// Rows per reduction block: the CGS2 passes are FP64-FMA work, so a solve
+// uses about four blocks per SM (at least 512 rows each, at most kChunk).
+constexpr int kChunk = 4096;   // largest block (shared-memory copy of w)
+static int64_t chunk_rows(int64_t n) {
+  const int64_t want = (n + 4 * (int64_t)num_sms() - 1) / (4 * (int64_t)num_sms());
+  int64_t c = 512;
+  while (c < want && c < kChunk) c *= 2;
+  return c;
+}
 constexpr int kRedThreads = 256;
 
 struct Chunk {
@@ -287,12 +295,13 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
     return RS_OK;
   }
   // chunk table
+  const int64_t crows = chunk_rows(n);
   std::vector<Chunk> chunks;
   std::vector<int32_t> seg_chunk(nseg + 1, 0);
   for (int32_t q = 0; q < nseg; q++) {
     seg_chunk[q] = (int32_t)chunks.size();
-    for (int64_t r0 = 2 * (int64_t)boff[q]; r0 < 2 * (int64_t)boff[q + 1]; r0 += kChunk)
-      chunks.push_back({q, (int32_t)r0, (int32_t)std::min<int64_t>(r0 + kChunk, 2 * (int64_t)boff[q + 1])});
+    for (int64_t r0 = 2 * (int64_t)boff[q]; r0 < 2 * (int64_t)boff[q + 1]; r0 += crows)
+      chunks.push_back({q, (int32_t)r0, (int32_t)std::min<int64_t>(r0 + crows, 2 * (int64_t)boff[q + 1])});
   }
   seg_chunk[nseg] = (int32_t)chunks.size();
   const int32_t nch = (int32_t)chunks.size();

@@ -122,17 +122,15 @@ __global__ void k_take(int32_t nb, const double *r, int comp, double *out) {
 }
 
 // rp_i = r_{2i} - (A_ps s)_i
+// one thread per row (rows of A_ps hold a handful of entries; no FP64
+// shuffle additions)
 __global__ void k_bf_rp(int32_t nb, const int32_t *rp, const int32_t *col, const double *val, const double *s,
                         const double *r, double *out) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = tid >> 2;
-  const int lane = threadIdx.x & 3;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb) return;
   double acc = 0.0;
-  if (i < nb)
-    for (int32_t k = rp[i] + lane; k < rp[i + 1]; k += 4) acc = fma(val[k], s[col[k]], acc);
-  acc += __shfl_down_sync(0xffffffffu, acc, 2, 4);
-  acc += __shfl_down_sync(0xffffffffu, acc, 1, 4);
-  if (i < nb && lane == 0) out[i] = r[2 * i] - acc;
+  for (int32_t k = rp[i]; k < rp[i + 1]; k++) acc = fma(val[k], s[col[k]], acc);
+  out[i] = r[2 * i] - acc;
 }
 
 __global__ void k_interleave(int32_t nb, const double *p, const double *s, double *z) {
@@ -258,7 +256,7 @@ static int apply_body(const rs_precond *M, const double *r, double *z, cudaStrea
     case RS_PC_BF: {
       RS_COUNTED k_take<<<g, kBlock, 0, s>>>(nb, r, 1, M->sb);
       RS_TRY(amg_vcycle(M->Hs, M->sb, M->sx, s));                 // A_ss s = R_s r
-      RS_COUNTED k_bf_rp<<<grid_for((int64_t)nb * 4), kBlock, 0, s>>>(nb, M->Aps.rowptr, M->Aps.col, M->Aps.val, M->sx, r,
+      RS_COUNTED k_bf_rp<<<grid_for((int64_t)nb), kBlock, 0, s>>>(nb, M->Aps.rowptr, M->Aps.col, M->Aps.val, M->sx, r,
                                                            M->ss);    // r_p = R_p r - A_ps s
       RS_TRY(amg_vcycle(M->Hp, M->ss, M->sy, s));                 // S~ p = r_p
       RS_COUNTED k_interleave<<<g, kBlock, 0, s>>>(nb, M->sy, M->sx, z);
@@ -271,7 +269,9 @@ static int apply_body(const rs_precond *M, const double *r, double *z, cudaStrea
       RS_COUNTED k_cpr_stage1<<<g, kBlock, 0, s>>>(nb, mode, M->qw, M->dinv, M->p1inv, r, M->rt, z);
       {
         ProfScope ps(kProfBsr2, M->J.nnzb * 36.0 + (nb + 1) * 4.0 + nb * (16.0 + 16.0 + 16.0), s);
-        RS_COUNTED k_cpr_resid<4><<<grid_for((int64_t)nb * 4), kBlock, 0, s>>>(
+        // one lane per block row: on GB300 every FP64 shuffle addition costs
+        // FP64-pipe time, and a row's blocks share cache lines
+        RS_COUNTED k_cpr_resid<1><<<grid_for((int64_t)nb), kBlock, 0, s>>>(
             nb, M->J.row_ptr, M->J.col, M->J.val, z, M->rt, mode, M->qw, M->dinv, M->sb, two ? M->ss : nullptr);
       }
       RS_TRY(amg_vcycle(M->Hp, M->sb, M->sx, s));
