@@ -657,6 +657,7 @@ __global__ void __launch_bounds__(256) k_chunk_colour(const int32_t *cr, const i
                                                       int32_t *colour, int32_t *maxc, int32_t *err) {
   __shared__ uint32_t adj[kCCMax * kCCWords];
   __shared__ int32_t cs[kCCMax];
+  __shared__ unsigned long long um[2];   // colours used by the current point's coloured neighbours
   const int32_t k = blockIdx.x;
   const int32_t r0 = cr[2 * k], nrow = cr[2 * k + 1] - r0, len = nrow / B;
   if (len > kCCMax) {
@@ -681,6 +682,8 @@ __global__ void __launch_bounds__(256) k_chunk_colour(const int32_t *cr, const i
     const int lane = threadIdx.x;
     int32_t localmax = 0;
     for (int32_t li = 0; li < len; li++) {
+      if (lane == 0) { um[0] = 0ull; um[1] = 0ull; }
+      __syncwarp();
       unsigned long long u0 = 0ull, u1 = 0ull;
       const int32_t wl = li >> 5;
       if (lane < kCCWords && lane <= wl) {
@@ -693,15 +696,15 @@ __global__ void __launch_bounds__(256) k_chunk_colour(const int32_t *cr, const i
           if (c < 64) u0 |= 1ull << c; else u1 |= 1ull << (c - 64);
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        u0 |= __shfl_xor_sync(0xffffffffu, u0, o);
-        u1 |= __shfl_xor_sync(0xffffffffu, u1, o);
-      }
+      // only the lanes whose words hold coloured neighbours contribute
+      if (u0) atomicOr(&um[0], u0);
+      if (u1) atomicOr(&um[1], u1);
+      __syncwarp();
       if (lane == 0) {
+        const unsigned long long m0 = um[0], m1 = um[1];
         int32_t c;
-        if (~u0) c = __ffsll((long long)~u0) - 1;
-        else if (~u1) c = 64 + __ffsll((long long)~u1) - 1;
+        if (~m0) c = __ffsll((long long)~m0) - 1;
+        else if (~m1) c = 64 + __ffsll((long long)~m1) - 1;
         else { c = 0; atomicExch(err, 2); }
         cs[li] = c;
         if (c + 1 > localmax) localmax = c + 1;
@@ -751,7 +754,7 @@ __global__ void k_chunk_sort(const int32_t *cr, const int32_t *colour, int32_t n
 
 // inverse diagonal (GS) or inverse l1 row weight (Jacobi), FP64 and FP32
 __global__ void k_smoother_diag(int32_t n, const int32_t *rp, const int32_t *col, const double *val, int32_t l1,
-                                double *dinv, float *dinvf) {
+                                double *dinv, float *dinvf, int32_t *range_err) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double d = 0.0, off = 0.0;
@@ -763,6 +766,7 @@ __global__ void k_smoother_diag(int32_t n, const int32_t *rp, const int32_t *col
   const double inv = d != 0.0 ? 1.0 / d : 0.0;
   dinv[i] = inv;
   dinvf[i] = (float)inv;
+  if (range_err && isinf(dinvf[i]) && isfinite(inv)) atomicOr(range_err, 1);
 }
 
 // ---- systems (point) AMG: B interleaved unknowns per point, row B*i + f
@@ -815,7 +819,7 @@ __global__ void k_cf_expand(int32_t N, int32_t B, const int8_t *cfp, int8_t *cf)
 // inverses of the 2 x 2 diagonal blocks of the points (row-major, FP64 and an
 // FP32 copy); a singular block gets zeros (that point is left unchanged)
 __global__ void k_block_inv2(int32_t N, const int32_t *rp, const int32_t *col, const double *val, double *inv,
-                             float *invf) {
+                             float *invf, int32_t *range_err) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double d[4] = {0.0, 0.0, 0.0, 0.0};
@@ -833,6 +837,7 @@ __global__ void k_block_inv2(int32_t N, const int32_t *rp, const int32_t *col, c
   for (int q = 0; q < 4; q++) {
     inv[4 * (int64_t)i + q] = m[q];
     invf[4 * (int64_t)i + q] = (float)m[q];
+    if (range_err && isinf((float)m[q]) && isfinite(m[q])) atomicOr(range_err, 1);
   }
 }
 
@@ -854,9 +859,13 @@ static int func_part(const DCsr &A, int32_t B, int32_t f, DCsr &out, cudaStream_
   return 0;
 }
 
-__global__ void k_to_f32(int64_t n, const double *a, float *b) {
+// FP32 copy; a finite value beyond the FP32 range sets *range_err
+__global__ void k_to_f32(int64_t n, const double *a, float *b, int32_t *range_err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (float)a[i];
+  if (i >= n) return;
+  const float f = (float)a[i];
+  b[i] = f;
+  if (isinf(f) && isfinite(a[i])) atomicOr(range_err, 1);
 }
 
 // Hybrid smoother operator. For every row of a chunk: its off-diagonal
@@ -1066,6 +1075,11 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     H.last_level.assign(H.nseg, 0);
     return 0;
   }
+  // set by the FP32 copies when a finite FP64 value lies beyond the FP32 range
+  Scratch scb(s);
+  int32_t *f32err = nullptr;
+  RS_TRY(scb.get(&f32err, 1));
+  RS_CHECK_CUDA(cudaMemsetAsync(f32err, 0, sizeof(int32_t), s));
   const int32_t nfun0 = std::max(1, prm.num_functions);
   // level 0 owns a copy of A
   H.L.emplace_back();
@@ -1322,14 +1336,16 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     RS_TRY(dalloc_n(&Lc.dinvf, (size_t)n, s));
     if (n > 0)
       RS_COUNTED k_smoother_diag<<<grid_for(n), kBlock, 0, s>>>(n, Lc.A.rowptr, Lc.A.col, Lc.A.val,
-                                                     H.prm.smoother == RS_SMOOTH_L1JACOBI, Lc.dinv, Lc.dinvf);
+                                                     H.prm.smoother == RS_SMOOTH_L1JACOBI, Lc.dinv, Lc.dinvf,
+                                                     H.precision == RS_PREC_FP32 ? f32err : nullptr);
     if (B == 2) {
       const int32_t np = n / 2;
       RS_TRY(dalloc_n(&Lc.binv, 4 * (size_t)np + 4, s));
       RS_TRY(dalloc_n(&Lc.binvf, 4 * (size_t)np + 4, s));
       if (np > 0)
         RS_COUNTED k_block_inv2<<<grid_for(np), kBlock, 0, s>>>(np, Lc.A.rowptr, Lc.A.col, Lc.A.val, Lc.binv,
-                                                                Lc.binvf);
+                                                                Lc.binvf,
+                                                                H.precision == RS_PREC_FP32 ? f32err : nullptr);
     }
     // systems solved directly here
     int64_t inv_tot = 0;
@@ -1366,12 +1382,12 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     // FP32 copies for the FP32 cycle
     if (H.precision == RS_PREC_FP32) {
       RS_TRY(dalloc_n(&Lc.A.valf, (size_t)Lc.A.nnz, s));
-      if (Lc.A.nnz) RS_COUNTED k_to_f32<<<grid_for(Lc.A.nnz), kBlock, 0, s>>>(Lc.A.nnz, Lc.A.val, Lc.A.valf);
+      if (Lc.A.nnz) RS_COUNTED k_to_f32<<<grid_for(Lc.A.nnz), kBlock, 0, s>>>(Lc.A.nnz, Lc.A.val, Lc.A.valf, f32err);
       if (Lc.P.rowptr) {
         RS_TRY(dalloc_n(&Lc.P.valf, (size_t)Lc.P.nnz, s));
         RS_TRY(dalloc_n(&Lc.R.valf, (size_t)Lc.R.nnz, s));
-        if (Lc.P.nnz) RS_COUNTED k_to_f32<<<grid_for(Lc.P.nnz), kBlock, 0, s>>>(Lc.P.nnz, Lc.P.val, Lc.P.valf);
-        if (Lc.R.nnz) RS_COUNTED k_to_f32<<<grid_for(Lc.R.nnz), kBlock, 0, s>>>(Lc.R.nnz, Lc.R.val, Lc.R.valf);
+        if (Lc.P.nnz) RS_COUNTED k_to_f32<<<grid_for(Lc.P.nnz), kBlock, 0, s>>>(Lc.P.nnz, Lc.P.val, Lc.P.valf, f32err);
+        if (Lc.R.nnz) RS_COUNTED k_to_f32<<<grid_for(Lc.R.nnz), kBlock, 0, s>>>(Lc.R.nnz, Lc.R.val, Lc.R.valf, f32err);
       }
     }
     // packed operator of the hybrid smoother, in the cycle's precision
@@ -1411,7 +1427,10 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
   H.nlev = (int32_t)H.L.size();
   for (int32_t q = 0; q < H.nseg; q++)
     if (H.last_level[q] < 0) H.last_level[q] = H.nlev - 1;
-  RS_CHECK_CUDA(cudaStreamSynchronize(s));
+  int32_t hrange = 0;
+  RS_TRY(sync_copy(&hrange, f32err, sizeof(int32_t), s));
+  if (hrange)
+    return fail(RS_ESETUP, "hierarchy values lie beyond the FP32 range; use an FP64 hierarchy (RS_PREC_FP64)");
   return 0;
 }
 

@@ -155,29 +155,49 @@ int block_diag_inverse(const rs_bsr2 &J, double *dinv, cudaStream_t s) {
 // take the (distinct) entries of B's row k, so every C(i,j) receives its
 // terms in ascending k. Pass 1 counts distinct columns, pass 2 accumulates,
 // sorts the row by column and writes it.
-constexpr int kHash = 2048;
-constexpr int kGemmWarps = 2;
+constexpr int kHash = 2048;       // largest per-row table (slots)
+constexpr int kGemmThreads = 256;
 
-// table of `tsize` slots (a power of two, 32..kHash) sized per row
+// table slot of a column key (Fibonacci hashing into 2^tbits slots)
 __device__ __forceinline__ int hslot(int32_t key, int tbits) {
   return (int)(((uint32_t)key * 2654435761u) >> (32 - tbits));
 }
 
+// largest number of products of one row of A with B (an upper bound of the
+// row's distinct output columns)
+__global__ void k_spgemm_maxprod(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                                 const int32_t *__restrict__ brp, int32_t *mx) {
+  const int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  int32_t np = 0;
+  for (int32_t ka = arp[row]; ka < arp[row + 1]; ka++) {
+    const int32_t k = acol[ka];
+    np += brp[k + 1] - brp[k];
+  }
+  atomicMax(mx, np);
+}
+
+// One warp per row, with a hash table of `tcap` slots per warp in shared
+// memory (tcap sized from the level's largest row, so small rows leave room
+// for many warps per SM); each row uses the smallest power of two >= 2x its
+// product count. Products are accumulated in ascending inner index (the ka
+// loop is sequential, a B row holds each column once), so sums are
+// reproducible.
 template <bool NUMERIC>
-__global__ void __launch_bounds__(32 * kGemmWarps) k_spgemm(int32_t n, const int32_t *__restrict__ arp,
-                                                            const int32_t *__restrict__ acol,
-                                                            const double *__restrict__ aval,
-                                                            const int32_t *__restrict__ brp,
-                                                            const int32_t *__restrict__ bcol,
-                                                            const double *__restrict__ bval,
-                                                            int32_t *__restrict__ crp, int32_t *__restrict__ ccol,
-                                                            double *__restrict__ cval, int32_t *err) {
+__global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t n, int32_t tcap, const int32_t *__restrict__ arp,
+                                                         const int32_t *__restrict__ acol,
+                                                         const double *__restrict__ aval,
+                                                         const int32_t *__restrict__ brp,
+                                                         const int32_t *__restrict__ bcol,
+                                                         const double *__restrict__ bval,
+                                                         int32_t *__restrict__ crp, int32_t *__restrict__ ccol,
+                                                         double *__restrict__ cval, int32_t *err) {
   extern __shared__ unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int32_t *keys = reinterpret_cast<int32_t *>(smem) + warp * kHash;
-  double *vals = reinterpret_cast<double *>(smem + sizeof(int32_t) * kHash * kGemmWarps) + warp * kHash;
-  __shared__ int32_t cnt_s[kGemmWarps];
-  for (int32_t row = blockIdx.x * kGemmWarps + warp; row < n; row += gridDim.x * kGemmWarps) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  double *vals = reinterpret_cast<double *>(smem) + (int64_t)warp * tcap;
+  int32_t *keys = reinterpret_cast<int32_t *>(smem + sizeof(double) * (size_t)tcap * nwarps) + (int64_t)warp * tcap;
+  __shared__ int32_t cnt_s[kGemmThreads / 32];
+  for (int32_t row = blockIdx.x * nwarps + warp; row < n; row += gridDim.x * nwarps) {
     const int32_t as = arp[row], ae = arp[row + 1];
     // upper bound of distinct columns: the number of products
     int32_t np = 0;
@@ -187,7 +207,7 @@ __global__ void __launch_bounds__(32 * kGemmWarps) k_spgemm(int32_t n, const int
     }
     np = __reduce_add_sync(0xffffffffu, np);
     int tbits = 5;
-    while (tbits < 11 && (1 << tbits) < 2 * np) tbits++;
+    while ((1 << tbits) < tcap && (1 << tbits) < 2 * np) tbits++;
     const int tsize = 1 << tbits;
     for (int h = lane; h < tsize; h += 32) keys[h] = -1;
     if (lane == 0) cnt_s[warp] = 0;
@@ -229,7 +249,7 @@ __global__ void __launch_bounds__(32 * kGemmWarps) k_spgemm(int32_t n, const int
       int32_t base_c = 0;
       for (int h0 = 0; h0 < tsize; h0 += 32) {
         const int32_t j = keys[h0 + lane];
-        const double v = NUMERIC ? vals[h0 + lane] : 0.0;
+        const double v = vals[h0 + lane];
         const unsigned occ = __ballot_sync(0xffffffffu, j >= 0);
         __syncwarp();
         if (j >= 0) {
@@ -259,20 +279,33 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   RS_TRY(dalloc_n(&C.rowptr, (size_t)A.n + 1, s));
   Scratch sc(s);
   int32_t *err = nullptr;
-  RS_TRY(sc.get(&err, 1));
-  RS_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
-  const size_t shm = (sizeof(int32_t) + sizeof(double)) * kHash * kGemmWarps;
+  RS_TRY(sc.get(&err, 2));
+  RS_CHECK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), s));
   static bool attr = false;
   if (!attr) {
-    RS_CHECK_CUDA(cudaFuncSetAttribute(k_spgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    RS_CHECK_CUDA(cudaFuncSetAttribute(k_spgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    const int mx = (int)(sizeof(double) + sizeof(int32_t)) * kHash * (kGemmThreads / 32);
+    RS_CHECK_CUDA(cudaFuncSetAttribute(k_spgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    RS_CHECK_CUDA(cudaFuncSetAttribute(k_spgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     attr = true;
   }
-  const unsigned grid = (unsigned)std::min<int64_t>((A.n + kGemmWarps - 1) / kGemmWarps, (int64_t)num_sms() * 16);
+  // per-warp table: twice the largest row's product count, as a power of two
+  // (32..kHash); rows with more products than kHash / 2 are an error
+  int32_t maxprod = 0;
+  if (A.n > 0) {
+    RS_COUNTED k_spgemm_maxprod<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, B.rowptr, err + 1);
+    RS_CHECK_CUDA(cudaMemcpyAsync(&maxprod, err + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RS_CHECK_CUDA(cudaStreamSynchronize(s));
+  }
+  int32_t tcap = 32;
+  while (tcap < kHash && tcap < 2 * maxprod) tcap *= 2;
+  // as many warps per CTA as keep a CTA's tables within 48 KB (1..8)
+  int warps = (int)std::min<int64_t>(kGemmThreads / 32, std::max<int64_t>(1, (48 * 1024) / (12 * (int64_t)tcap)));
+  const size_t shm = (sizeof(double) + sizeof(int32_t)) * (size_t)tcap * warps;
+  const unsigned grid = (unsigned)std::min<int64_t>((A.n + warps - 1) / warps, (int64_t)num_sms() * 32);
   ProfScope ps(kProfSpgemm, A.nnz * 12.0 + B.nnz * 12.0, s);
   if (A.n > 0)
-    RS_COUNTED k_spgemm<false><<<grid, 32 * kGemmWarps, shm, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val,
-                                                        C.rowptr, nullptr, nullptr, err);
+    RS_COUNTED k_spgemm<false><<<grid, 32 * warps, shm, s>>>(A.n, tcap, A.rowptr, A.col, A.val, B.rowptr, B.col,
+                                                             B.val, C.rowptr, nullptr, nullptr, err);
   int32_t tot = 0;
   RS_TRY(exclusive_scan(C.rowptr, C.rowptr, A.n, s, &tot));
   int32_t herr = 0;
@@ -283,8 +316,8 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   RS_TRY(dalloc_n(&C.col, (size_t)tot, s));
   RS_TRY(dalloc_n(&C.val, (size_t)tot, s));
   if (A.n > 0)
-    RS_COUNTED k_spgemm<true><<<grid, 32 * kGemmWarps, shm, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val,
-                                                       C.rowptr, C.col, C.val, err);
+    RS_COUNTED k_spgemm<true><<<grid, 32 * warps, shm, s>>>(A.n, tcap, A.rowptr, A.col, A.val, B.rowptr, B.col,
+                                                            B.val, C.rowptr, C.col, C.val, err);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }

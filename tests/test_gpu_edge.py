@@ -105,3 +105,17 @@ def test_one_level_hierarchy_is_exact(R, oracle, inputs):
     xj = torch.zeros(2 * p.ncell, dtype=torch.float64, device="cuda")
     st = R.gmres_solve(J, M, _dev(-Fo), xj, R.GmresParams())
     assert st.status == R.RS_OK and st.iterations == 1
+
+
+def test_fp32_hierarchy_beyond_range_is_rejected(R, oracle, inputs):
+    """The unknown-agnostic scalar AMG on the 256^2 Jacobian builds coarse
+    values beyond the FP32 range (the oracle pins that); an FP32 hierarchy is
+    refused at set-up with a clear error, the FP64 one is built."""
+    p = inputs.config_lognormal_2d(0.0, n=256)
+    u, uo = inputs.front_state(p)
+    Fo, Jo, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
+    J = R.Bsr2.from_host(rp, col, Jo)
+    with pytest.raises(R.RsError, match="FP32 range"):
+        R.Precond(J, R.PrecParams(kind=R.AMG_J_SCALAR, amg=R.AmgParams(precision=R.FP32)))
+    M = R.Precond(J, R.PrecParams(kind=R.AMG_J_SCALAR, amg=R.AmgParams(precision=R.FP64)))
+    M.close()
