@@ -292,22 +292,52 @@ __global__ void k_interp_ext(int32_t n, const int32_t *rp, const int32_t *col, c
 // ordering constraint (gathering Chat_i, the denominators d_k, one lane per
 // k, and the numerators, one lane per target column j, each summing over k
 // ascending), while the single ordered accumulation of dtil is done by lane 0.
-constexpr int kIWarps = 2;
 constexpr int kICand = 2048;
 constexpr int kICap = 256;
 constexpr int kIF = 256;
 
+// Per-warp work arrays of the interpolation kernels, carved from dynamic
+// shared memory with capacities sized for the level (ccap candidates, hcap
+// interpolation points, fcap strong F neighbours; at most kICand, kICap,
+// kIF): small capacities on the fine levels let many warps share an SM.
 struct IWarp {
-  int32_t cand[kICand];
-  uint8_t first[kICand];
-  int32_t chat[kICap];
-  double num[kICap];
-  int32_t nset[kICap];
-  int32_t fk[kIF];
-  double fa[kIF];
-  double fd[kIF];
-  int32_t ncand, m, nf;
+  double *num, *fa, *fd;
+  int32_t *cand, *chat, *nset, *fk, *cnt;   // cnt: ncand, m, nf
+  uint8_t *first;
 };
+
+__host__ __device__ inline size_t iwarp_bytes(int ccap, int hcap, int fcap) {
+  return 8 * (size_t)(hcap + 2 * fcap) + 4 * (size_t)(ccap + 2 * hcap + fcap + 4) + (((size_t)ccap + 7) & ~size_t(7));
+}
+
+__device__ inline IWarp iwarp_at(unsigned char *base, int ccap, int hcap, int fcap) {
+  IWarp W;
+  W.num = reinterpret_cast<double *>(base);
+  W.fa = W.num + hcap;
+  W.fd = W.fa + fcap;
+  W.cand = reinterpret_cast<int32_t *>(W.fd + fcap);
+  W.chat = W.cand + ccap;
+  W.nset = W.chat + hcap;
+  W.fk = W.nset + hcap;
+  W.cnt = W.fk + fcap;
+  W.first = reinterpret_cast<uint8_t *>(W.cnt + 4);
+  return W;
+}
+
+// bounds of a level for the interpolation capacities: the largest number of
+// entries of a row plus its neighbours' rows (bounds the candidate count),
+// and the largest row
+__global__ void k_interp_bounds(int32_t n, const int32_t *rp, const int32_t *col, int32_t *mx) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t c = rp[i + 1] - rp[i];
+  for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+    const int32_t j = col[q];
+    c += rp[j + 1] - rp[j];
+  }
+  atomicMax(mx, c);
+  atomicMax(mx + 1, rp[i + 1] - rp[i]);
+}
 
 __device__ __forceinline__ int find_row(const int32_t *col, int32_t s, int32_t e, int32_t v) {
   int32_t lo = s, hi = e - 1;
@@ -321,7 +351,8 @@ __device__ __forceinline__ int find_row(const int32_t *col, int32_t s, int32_t e
 }
 
 template <bool WRITE>
-__global__ void __launch_bounds__(32 * kIWarps) k_interp_ext_w(int32_t n, const int32_t *__restrict__ rp,
+__global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int hcap, int fcap,
+                                                     const int32_t *__restrict__ rp,
                                                                 const int32_t *__restrict__ col,
                                                                 const double *__restrict__ val,
                                                                 const double *__restrict__ diag,
@@ -330,11 +361,11 @@ __global__ void __launch_bounds__(32 * kIWarps) k_interp_ext_w(int32_t n, const 
                                                                 const int32_t *__restrict__ cidx, int32_t *prp,
                                                                 int32_t *__restrict__ pcol, double *__restrict__ pval,
                                                                 int32_t *err) {
-  __shared__ IWarp sw[kIWarps];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  IWarp &W = sw[warp];
+  extern __shared__ __align__(16) unsigned char iwsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const IWarp W = iwarp_at(iwsm + (size_t)warp * iwarp_bytes(ccap, hcap, fcap), ccap, hcap, fcap);
   const unsigned lt = (1u << lane) - 1u;
-  for (int32_t i = blockIdx.x * kIWarps + warp; i < n; i += gridDim.x * kIWarps) {
+  for (int32_t i = blockIdx.x * nwarps + warp; i < n; i += gridDim.x * nwarps) {
     if (cf[i] == 1) {
       if (lane == 0) {
         if (WRITE) { pcol[prp[i]] = cidx[i]; pval[prp[i]] = 1.0; }
@@ -343,7 +374,7 @@ __global__ void __launch_bounds__(32 * kIWarps) k_interp_ext_w(int32_t n, const 
       continue;
     }
     const int32_t s = rp[i], e = rp[i + 1];
-    if (lane == 0) { W.ncand = 0; W.nf = 0; }
+    if (lane == 0) { W.cnt[0] = 0; W.cnt[2] = 0; }
     __syncwarp();
     // candidates for Chat_i, and the strong F neighbours in row order
     bool ovf = false;
@@ -355,31 +386,31 @@ __global__ void __launch_bounds__(32 * kIWarps) k_interp_ext_w(int32_t n, const 
       const bool isC = st && cf[j] == 1;
       const bool isF = st && cf[j] != 1;
       if (isC) {
-        const int32_t p = atomicAdd(&W.ncand, 1);
-        if (p < kICand) W.cand[p] = j; else ovf = true;
+        const int32_t p = atomicAdd(&W.cnt[0], 1);
+        if (p < ccap) W.cand[p] = j; else ovf = true;
       }
       if (isF) {
         for (int32_t t = rp[j]; t < rp[j + 1]; t++) {
           const int32_t l = col[t];
           if (l != j && strong[t] && cf[l] == 1) {
-            const int32_t p = atomicAdd(&W.ncand, 1);
-            if (p < kICand) W.cand[p] = l; else ovf = true;
+            const int32_t p = atomicAdd(&W.cnt[0], 1);
+            if (p < ccap) W.cand[p] = l; else ovf = true;
           }
         }
       }
       const unsigned fm = __ballot_sync(0xffffffffu, isF);
-      const int32_t nf0 = W.nf;
+      const int32_t nf0 = W.cnt[2];
       __syncwarp();
       if (isF) {
         const int32_t p = nf0 + __popc(fm & lt);
-        if (p < kIF) { W.fk[p] = j; W.fa[p] = val[q]; } else ovf = true;
+        if (p < fcap) { W.fk[p] = j; W.fa[p] = val[q]; } else ovf = true;
       }
       __syncwarp();
-      if (lane == 0) W.nf = nf0 + __popc(fm);
+      if (lane == 0) W.cnt[2] = nf0 + __popc(fm);
       __syncwarp();
     }
-    const int32_t ncand = W.ncand, nf = W.nf;
-    ovf = __any_sync(0xffffffffu, ovf) || ncand > kICand || nf > kIF;
+    const int32_t ncand = W.cnt[0], nf = W.cnt[2];
+    ovf = __any_sync(0xffffffffu, ovf) || ncand > ccap || nf > fcap;
     // sorted distinct candidates -> Chat_i: mark first occurrences, then rank
     // each first occurrence among the others
     int32_t mloc = 0;
@@ -397,12 +428,12 @@ __global__ void __launch_bounds__(32 * kIWarps) k_interp_ext_w(int32_t n, const 
         const int32_t v = W.cand[a];
         int32_t rank = 0;
         for (int32_t b = 0; b < ncand; b++) rank += (W.first[b] && W.cand[b] < v);
-        if (rank < kICap) W.chat[rank] = v; else ovf = true;
+        if (rank < hcap) W.chat[rank] = v; else ovf = true;
         mloc++;
       }
     }
     const int32_t m = __reduce_add_sync(0xffffffffu, mloc);
-    ovf = __any_sync(0xffffffffu, ovf) || m > kICap;
+    ovf = __any_sync(0xffffffffu, ovf) || m > hcap;
     __syncwarp();
     if (ovf) {
       if (lane == 0) { atomicExch(err, 1); if (!WRITE) prp[i] = 0; }
@@ -1207,13 +1238,33 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           Pf.m = nc;
           RS_TRY(dalloc_n(&Pf.rowptr, (size_t)F.n + 1, s));
           RS_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
-          const unsigned gw = (unsigned)std::min<int64_t>((F.n + kIWarps - 1) / kIWarps, 65535);
+          // ext+i work arrays sized for this level (see IWarp)
+          int ccap = kICand, hcap = kICap, fcap = kIF, iw = 2;
+          size_t ishm = 0;
+          if (prm.interp != RS_INTERP_CLASSICAL && F.n > 0) {
+            int32_t *bd = nullptr;
+            RS_TRY(sc.get(&bd, 2));
+            RS_CHECK_CUDA(cudaMemsetAsync(bd, 0, 2 * sizeof(int32_t), s));
+            RS_COUNTED k_interp_bounds<<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, bd);
+            int32_t hb[2] = {0, 0};
+            RS_TRY(sync_copy(hb, bd, sizeof(hb), s));
+            ccap = 32;
+            while (ccap < kICand && ccap < hb[0]) ccap *= 2;
+            hcap = std::min(ccap, kICap);
+            fcap = 8;
+            while (fcap < kIF && fcap < hb[1]) fcap *= 2;
+            const size_t wb = iwarp_bytes(ccap, hcap, fcap);
+            iw = (int)std::min<size_t>(8, std::max<size_t>(1, (48 * 1024) / wb));
+            ishm = wb * iw;
+          }
+          const unsigned gw = (unsigned)std::min<int64_t>((F.n + iw - 1) / iw, (int64_t)num_sms() * 64);
           if (prm.interp == RS_INTERP_CLASSICAL)
             RS_COUNTED k_interp_classical<false><<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong, cfu,
                                                                        isc, Pf.rowptr, nullptr, nullptr, err);
           else
-            RS_COUNTED k_interp_ext_w<false><<<gw, 32 * kIWarps, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong,
-                                                                         cfu, isc, Pf.rowptr, nullptr, nullptr, err);
+            RS_COUNTED k_interp_ext_w<false><<<gw, 32 * iw, ishm, s>>>(F.n, ccap, hcap, fcap, F.rowptr, F.col, F.val,
+                                                                       diag, strong, cfu, isc, Pf.rowptr, nullptr,
+                                                                       nullptr, err);
           int32_t pnnz = 0;
           RS_TRY(exclusive_scan(Pf.rowptr, Pf.rowptr, F.n, s, &pnnz));
           int32_t herr = 0;
@@ -1226,8 +1277,9 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
             RS_COUNTED k_interp_classical<true><<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong, cfu,
                                                                       isc, Pf.rowptr, Pf.col, Pf.val, err);
           else
-            RS_COUNTED k_interp_ext_w<true><<<gw, 32 * kIWarps, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong,
-                                                                        cfu, isc, Pf.rowptr, Pf.col, Pf.val, err);
+            RS_COUNTED k_interp_ext_w<true><<<gw, 32 * iw, ishm, s>>>(F.n, ccap, hcap, fcap, F.rowptr, F.col, F.val,
+                                                                      diag, strong, cfu, isc, Pf.rowptr, Pf.col,
+                                                                      Pf.val, err);
           RS_CHECK_CUDA(cudaGetLastError());
           return 0;
         };
