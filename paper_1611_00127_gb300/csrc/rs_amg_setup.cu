@@ -945,14 +945,19 @@ __global__ void k_hs_fill(const int32_t *cr, const int32_t *rp, const int32_t *c
 // ------------------------------------------------------------------ coarse inverse
 // Gauss-Jordan with partial pivoting (largest |a|, first on ties), one CTA per
 // system, dense FP64 in global scratch: [A | I] -> [I | A^{-1}].
+template <bool SMEM>
 __global__ void k_coarse_dense(const int32_t *rp, const int32_t *col, const double *val, const int4 *info,
                                const int64_t *inv_off, double *work, double *inv) {
+  extern __shared__ __align__(16) unsigned char cdsm[];
   const int4 in = info[blockIdx.x];
   const int32_t r0 = in.x, n = in.y;
   const int64_t off = inv_off[blockIdx.x];
-  double *a = work + 2 * off;   // n x n matrix followed by n x n identity, row-major each
+  // n x n matrix followed by the n x n identity, row-major each, in shared
+  // memory when they fit, else in the global work area
+  double *a = SMEM ? reinterpret_cast<double *>(cdsm) : work + 2 * off;
   double *b = a + (int64_t)n * n;
-  for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) { a[t] = 0.0; b[t] = 0.0; }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int64_t t = threadIdx.x; t < 2 * (int64_t)n * n; t += blockDim.x) a[t] = 0.0;
   __syncthreads();
   for (int32_t r = threadIdx.x; r < n; r += blockDim.x) {
     for (int32_t k = rp[r0 + r]; k < rp[r0 + r + 1]; k++) {
@@ -963,8 +968,8 @@ __global__ void k_coarse_dense(const int32_t *rp, const int32_t *col, const doub
   }
   __syncthreads();
   __shared__ int32_t piv;
-  __shared__ double red_v[256];
-  __shared__ int32_t red_i[256];
+  __shared__ double red_v[32];
+  __shared__ int32_t red_i[32];
   for (int32_t k = 0; k < n; k++) {
     // pivot search: largest |a_rk| for r >= k, lowest row on ties (block-wide argmax)
     double best = -1.0;
@@ -978,12 +983,12 @@ __global__ void k_coarse_dense(const int32_t *rp, const int32_t *col, const doub
       const int32_t oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
-    if ((threadIdx.x & 31) == 0) { red_v[threadIdx.x >> 5] = best; red_i[threadIdx.x >> 5] = bi; }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
       double bv = -1.0;
       int32_t bix = n;
-      for (int t = 0; t < (int)(blockDim.x >> 5); t++)
+      for (int t = 0; t < nwarps; t++)
         if (red_v[t] > bv || (red_v[t] == bv && red_i[t] < bix)) { bv = red_v[t]; bix = red_i[t]; }
       piv = bix < n ? bix : k;
     }
@@ -1003,12 +1008,15 @@ __global__ void k_coarse_dense(const int32_t *rp, const int32_t *col, const doub
       b[(int64_t)k * n + c] *= dinv;
     }
     __syncthreads();
-    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
-      const int32_t r = (int32_t)(t / n), c = (int32_t)(t % n);
+    // eliminate column k from every other row: a warp per row, lanes over columns
+    for (int32_t r = warp; r < n; r += nwarps) {
       if (r == k) continue;
       const double f = a[(int64_t)r * n + k];
-      if (c != k) a[t] -= f * a[(int64_t)k * n + c];
-      b[t] -= f * b[(int64_t)k * n + c];
+      if (f == 0.0) continue;
+      for (int32_t c = lane; c < n; c += 32) {
+        if (c != k) a[(int64_t)r * n + c] -= f * a[(int64_t)k * n + c];
+        b[(int64_t)r * n + c] -= f * b[(int64_t)k * n + c];
+      }
     }
     __syncthreads();
     for (int32_t r = threadIdx.x; r < n; r += blockDim.x)
@@ -1017,6 +1025,9 @@ __global__ void k_coarse_dense(const int32_t *rp, const int32_t *col, const doub
   }
   for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) inv[off + t] = b[t];
 }
+
+// largest coarse system staged in shared memory (2 n^2 doubles <= 96 KB)
+constexpr int kCoarseSmemN = 78;
 
 // ------------------------------------------------------------------ driver
 static int sync_copy(void *h, const void *d, size_t bytes, cudaStream_t s) {
@@ -1425,10 +1436,24 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       RS_TRY(upload(&Lc.crows, rows, s));
       RS_TRY(upload(&Lc.crow_seg, rowseg, s));
       RS_TRY(dalloc_n(&Lc.cinv, (size_t)inv_tot, s));
-      double *work = nullptr;
-      RS_TRY(sc.get(&work, 2 * (size_t)inv_tot));
-      RS_COUNTED k_coarse_dense<<<(unsigned)info.size(), 256, 0, s>>>(Lc.A.rowptr, Lc.A.col, Lc.A.val, Lc.cinfo, Lc.cinv_off,
-                                                           work, Lc.cinv);
+      int32_t maxng = 0;
+      for (const int4 &in : info) maxng = std::max(maxng, in.y);
+      if (maxng <= kCoarseSmemN) {
+        const size_t shm = 2 * sizeof(double) * (size_t)maxng * maxng;
+        static bool attr = false;
+        if (!attr) {
+          RS_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_dense<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(2 * sizeof(double) * kCoarseSmemN * kCoarseSmemN)));
+          attr = true;
+        }
+        RS_COUNTED k_coarse_dense<true><<<(unsigned)info.size(), 256, shm, s>>>(
+            Lc.A.rowptr, Lc.A.col, Lc.A.val, Lc.cinfo, Lc.cinv_off, nullptr, Lc.cinv);
+      } else {
+        double *work = nullptr;
+        RS_TRY(sc.get(&work, 2 * (size_t)inv_tot));
+        RS_COUNTED k_coarse_dense<false><<<(unsigned)info.size(), 256, 0, s>>>(
+            Lc.A.rowptr, Lc.A.col, Lc.A.val, Lc.cinfo, Lc.cinv_off, work, Lc.cinv);
+      }
       RS_CHECK_CUDA(cudaGetLastError());
     }
     // FP32 copies for the FP32 cycle
