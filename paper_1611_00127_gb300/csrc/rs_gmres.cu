@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const Chunk *__restric
 __global__ void k_reduce(int32_t nseg, const int32_t *__restrict__ seg_chunk, int nvec, int stride,
                          const double *__restrict__ part, double *__restrict__ out, double *__restrict__ H,
                          int ldh_seg, int col, int mode, const uint8_t *__restrict__ active) {
+  RS_PDL_ENTRY();
   // one warp per (system, vector): lane l sums chunks l, l+32, ... in order,
   // then a fixed shuffle tree adds the lanes (deterministic)
   const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(kRedThreads) k_update(const Chunk *__restrict_
 // y = x * f[seg] (0 where f is 0 or not finite)
 __global__ void __launch_bounds__(kRedThreads) k_scale(const Chunk *__restrict__ chunks, const double *__restrict__ nrm,
                                                        const double *__restrict__ x, double *__restrict__ y) {
+  RS_PDL_ENTRY();
   const Chunk ch = chunks[blockIdx.x];
   const double d = nrm[ch.seg];
   const double f = (d > 0.0 && isfinite(d)) ? 1.0 / d : 0.0;
@@ -166,6 +168,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kRedThreads) k_arnoldi(const Chunk *__restrict__ chunks, const double *__restrict__ V,
                                                          int64_t ldv, int nvec, const double *__restrict__ h, int stride,
                                                          double *__restrict__ w, double *__restrict__ part) {
+  RS_PDL_ENTRY();
   __shared__ double ws[kChunk];
   __shared__ double sh[(kRedThreads / 32) * kTile];
   const Chunk ch = chunks[blockIdx.x];
@@ -210,6 +213,7 @@ __global__ void k_givens(int32_t nseg, int j, int m, double *__restrict__ H, int
                          SegState *__restrict__ st, uint8_t *__restrict__ active, int32_t *__restrict__ kseg,
                          const double *__restrict__ tol, int32_t *__restrict__ its, int32_t maxit,
                          int32_t *__restrict__ nactive, uint8_t *__restrict__ bad) {
+  RS_PDL_ENTRY();
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg || !active[s]) return;
   double *Hs = H + (int64_t)s * ldh_seg;
@@ -406,23 +410,31 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
       const double nv = j + 1;
       if (nch > 0) {
         ProfScope ps(kProfArnoldi, (nv + 1) * 8.0 * n, s);
-        RS_COUNTED k_arnoldi<0><<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, nullptr, stride, w, part);
+        RS_COUNTED launch_pdl(k_arnoldi<0>, dim3(nch), dim3(kRedThreads), 0, s, (const Chunk *)dch, (const double *)V,
+                              (int64_t)n, j + 1, (const double *)nullptr, stride, w, part);
       }
-      RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * (j + 1) * 32), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part,
-                                                                                hbuf, H, ldh, j, 1, active);
+      RS_COUNTED launch_pdl(k_reduce, dim3(grid_for((int64_t)nseg * (j + 1) * 32)), dim3(kBlock), 0, s, nseg,
+                            (const int32_t *)dsegc, j + 1, stride, (const double *)part, hbuf, H, ldh, j, 1,
+                            (const uint8_t *)active);
       if (nch > 0) {
         ProfScope ps(kProfArnoldi, (2.0 * nv + 2) * 8.0 * n, s);
-        RS_COUNTED k_arnoldi<1><<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, hbuf, stride, w, part);
+        RS_COUNTED launch_pdl(k_arnoldi<1>, dim3(nch), dim3(kRedThreads), 0, s, (const Chunk *)dch, (const double *)V,
+                              (int64_t)n, j + 1, (const double *)hbuf, stride, w, part);
       }
-      RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * (j + 1) * 32), kBlock, 0, s>>>(nseg, dsegc, j + 1, stride, part,
-                                                                                hbuf, H, ldh, j, 2, active);
+      RS_COUNTED launch_pdl(k_reduce, dim3(grid_for((int64_t)nseg * (j + 1) * 32)), dim3(kBlock), 0, s, nseg,
+                            (const int32_t *)dsegc, j + 1, stride, (const double *)part, hbuf, H, ldh, j, 2,
+                            (const uint8_t *)active);
       if (nch > 0) {
         ProfScope ps(kProfArnoldi, (nv + 2) * 8.0 * n, s);
-        RS_COUNTED k_arnoldi<2><<<nch, kRedThreads, 0, s>>>(dch, V, n, j + 1, hbuf, stride, w, part);
+        RS_COUNTED launch_pdl(k_arnoldi<2>, dim3(nch), dim3(kRedThreads), 0, s, (const Chunk *)dch, (const double *)V,
+                              (int64_t)n, j + 1, (const double *)hbuf, stride, w, part);
       }
-      RS_COUNTED k_reduce<<<grid_for((int64_t)nseg * 32), kBlock, 0, s>>>(nseg, dsegc, 1, stride, part, nrm, nullptr, 0,
-                                                                          0, 3, nullptr);
-      if (nch > 0) RS_COUNTED k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, w, w);
+      RS_COUNTED launch_pdl(k_reduce, dim3(grid_for((int64_t)nseg * 32)), dim3(kBlock), 0, s, nseg,
+                            (const int32_t *)dsegc, 1, stride, (const double *)part, nrm, (double *)nullptr, 0, 0, 3,
+                            (const uint8_t *)nullptr);
+      if (nch > 0)
+        RS_COUNTED launch_pdl(k_scale, dim3(nch), dim3(kRedThreads), 0, s, (const Chunk *)dch, (const double *)nrm,
+                              (const double *)w, w);
       const int slot = j & 1;
       RS_CHECK_CUDA(cudaMemsetAsync(nact + slot, 0, sizeof(int32_t), s));
       RS_COUNTED k_givens<<<gseg, kBlock, 0, s>>>(nseg, j, m, H, ldh, nrm, st, active, kseg, tol, its, params->maxit,
