@@ -113,9 +113,13 @@ __global__ void __launch_bounds__(kRedThreads) k_update(const Chunk *__restrict_
 }
 
 // y = x * f[seg] (0 where f is 0 or not finite)
+// y = x / nrm per system; also clears *zero (the next Givens step's counter
+// of still-active systems) when given
 __global__ void __launch_bounds__(kRedThreads) k_scale(const Chunk *__restrict__ chunks, const double *__restrict__ nrm,
-                                                       const double *__restrict__ x, double *__restrict__ y) {
+                                                       const double *__restrict__ x, double *__restrict__ y,
+                                                       int32_t *zero) {
   RS_PDL_ENTRY();
+  if (zero && blockIdx.x == 0 && threadIdx.x == 0) *zero = 0;
   const Chunk ch = chunks[blockIdx.x];
   const double d = nrm[ch.seg];
   const double f = (d > 0.0 && isfinite(d)) ? 1.0 / d : 0.0;
@@ -398,7 +402,7 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
     if (newly) RS_CHECK_CUDA(cudaMemcpyAsync(bad, hbad.data(), (size_t)nseg, cudaMemcpyHostToDevice, s));
     if (!more) break;
     RS_COUNTED k_cycle_start<<<gseg, kBlock, 0, s>>>(nseg, nrm, tol, its, params->maxit, bad, active, kseg, st);
-    if (nch > 0) RS_COUNTED k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, V, V);
+    if (nch > 0) RS_COUNTED k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, V, V, nullptr);
     for (int j = 0; j < m; j++) {
       double *vj = V + (int64_t)j * n, *zj = Z + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
       if (M) rc = precond_apply_impl(M, vj, zj, s);
@@ -432,13 +436,11 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
       RS_COUNTED launch_pdl(k_reduce, dim3(grid_for((int64_t)nseg * 32)), dim3(kBlock), 0, s, nseg,
                             (const int32_t *)dsegc, 1, stride, (const double *)part, nrm, (double *)nullptr, 0, 0, 3,
                             (const uint8_t *)nullptr);
-      if (nch > 0)
-        RS_COUNTED launch_pdl(k_scale, dim3(nch), dim3(kRedThreads), 0, s, (const Chunk *)dch, (const double *)nrm,
-                              (const double *)w, w);
       const int slot = j & 1;
-      RS_CHECK_CUDA(cudaMemsetAsync(nact + slot, 0, sizeof(int32_t), s));
-      RS_COUNTED k_givens<<<gseg, kBlock, 0, s>>>(nseg, j, m, H, ldh, nrm, st, active, kseg, tol, its, params->maxit,
-                                                  nact + slot, bad);
+      RS_COUNTED launch_pdl(k_scale, dim3(nch), dim3(kRedThreads), 0, s, (const Chunk *)dch, (const double *)nrm,
+                            (const double *)w, w, nact + slot);
+      RS_COUNTED launch_pdl(k_givens, dim3(gseg), dim3(kBlock), 0, s, nseg, j, m, H, ldh, (const double *)nrm, st,
+                            active, kseg, (const double *)tol, its, params->maxit, nact + slot, bad);
       RS_CHECK_CUDA(cudaMemcpyAsync(hnact + slot, nact + slot, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       RS_CHECK_CUDA(cudaEventRecord(evn[slot], s));
       if (j >= 1) {
