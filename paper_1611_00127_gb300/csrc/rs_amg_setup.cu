@@ -1508,7 +1508,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
   RS_TRY(sync_copy(&hrange, f32err, sizeof(int32_t), s));
   if (hrange)
     return fail(RS_ESETUP, "hierarchy values lie beyond the FP32 range; use an FP64 hierarchy (RS_PREC_FP64)");
-  return 0;
+  return amg_tune_smoother(H, s);
 }
 
 void amg_free(Hier &H, cudaStream_t s) {

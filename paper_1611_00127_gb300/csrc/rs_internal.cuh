@@ -181,6 +181,7 @@ struct Level {
   // systems (point) AMG: unknowns per point, and the inverses of the 2 x 2
   // diagonal blocks of the points (row-major, FP64 and FP32)
   int32_t nfun = 1;
+  int32_t hgs_lpr = 0;               // lanes per row of the hybrid sweep (0: by rule)
   double *binv = nullptr;
   float *binvf = nullptr;
   int32_t hs_nnz = 0;
@@ -208,6 +209,10 @@ void amg_free(Hier &H, cudaStream_t s);
 int amg_vcycle(const Hier &H, const double *b, double *x, cudaStream_t s);
 int amg_level_sweeps(const Hier &H, int32_t l, int sweeps, double *bytes_per_sweep, cudaStream_t s);
 int amg_level_xfer(const Hier &H, int32_t l, int which, int reps, double *bytes_per_launch, cudaStream_t s);
+// Autotuner of the hybrid sweep's lanes per row: times the candidates on each
+// smoothed level's own vectors and stores the fastest in Level::hgs_lpr
+// (decisions cached per level shape). Not inside stream capture.
+int amg_tune_smoother(Hier &H, cudaStream_t s);
 // RS_ETIMEOUT (and clears the flag) if a smoother CTA gave up waiting for its
 // staging copies since the last call; synchronises the stream.
 int vcycle_wait_status(cudaStream_t s);

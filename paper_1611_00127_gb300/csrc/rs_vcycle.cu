@@ -11,6 +11,9 @@
 // order), residual, restriction by R = P^T, recursion, prolongation with
 // correction, post-sweeps.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "rs_internal.cuh"
 
@@ -680,7 +683,7 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
     const int32_t stage = std::min(L.chunk_max_nnz, kHgsStageEntries);
     const size_t shm = hgs_smem<T>(H.prm.chunk, stage);
     const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
-    const int hl = hgs_lpr(L.A.n, L.A.nnz, L.nchunk);
+    const int hl = L.hgs_lpr > 0 ? L.hgs_lpr : hgs_lpr(L.A.n, L.A.nnz, L.nchunk);
     if (L.nfun == 2) {
       const size_t shm2 = hgs2_smem<T>(H.prm.chunk, stage);
       for (int sw = 0; sw < sweeps; sw++) {
@@ -818,6 +821,68 @@ int amg_level_xfer(const Hier &H, int32_t l, int which, int reps, double *bytes_
   const double by = H.precision == RS_PREC_FP32 ? level_xfer<float>(H, l, which, reps, s)
                                                 : level_xfer<double>(H, l, which, reps, s);
   if (bytes_per_launch) *bytes_per_launch = by;
+  RS_CHECK_CUDA(cudaGetLastError());
+  return 0;
+}
+
+// ------------------------------------------------------------------ smoother autotuner
+// Key of a level shape: precision, unknowns per point, and log2 buckets of
+// the chunk count and of the mean row length (x4); levels of one key get the
+// same lanes per row.
+static std::mutex g_hgs_tune_mu;
+static std::map<std::tuple<int, int, int, int>, int> g_hgs_tune;
+
+static int ilog2(double v) {
+  int k = 0;
+  while (v >= 2.0 && k < 40) { v *= 0.5; k++; }
+  return k;
+}
+
+template <typename T>
+static int tune_level(const Hier &H, Level &L, cudaStream_t s) {
+  static const int cand[] = {1, 2, 4, 8, 16};
+  cudaEvent_t e0, e1;
+  RS_CHECK_CUDA(cudaEventCreate(&e0));
+  RS_CHECK_CUDA(cudaEventCreate(&e1));
+  float best = 0.f;
+  int bestl = 0;
+  for (int c : cand) {
+    L.hgs_lpr = c;
+    T *cur = static_cast<T *>(L.x);
+    smooth<T>(H, L, 1, cur, s);          // warm-up (kernel attributes, caches)
+    RS_CHECK_CUDA(cudaEventRecord(e0, s));
+    smooth<T>(H, L, 4, cur, s);
+    RS_CHECK_CUDA(cudaEventRecord(e1, s));
+    RS_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RS_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (bestl == 0 || ms < best) { best = ms; bestl = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.hgs_lpr = bestl;
+  return 0;
+}
+
+int amg_tune_smoother(Hier &H, cudaStream_t s) {
+  if (H.prm.smoother != RS_SMOOTH_HYBRID) return 0;
+  for (int32_t l = 0; l < H.nlev; l++) {
+    Level &L = H.L[l];
+    if (L.nsmooth == 0 || L.nchunk == 0 || L.A.n == 0) continue;
+    const auto key = std::make_tuple(H.precision, (int)L.nfun, ilog2((double)L.nchunk),
+                                     ilog2(4.0 * (double)L.A.nnz / (double)L.A.n));
+    {
+      std::lock_guard<std::mutex> lock(g_hgs_tune_mu);
+      auto it = g_hgs_tune.find(key);
+      if (it != g_hgs_tune.end()) {
+        L.hgs_lpr = it->second;
+        continue;
+      }
+    }
+    RS_TRY(H.precision == RS_PREC_FP32 ? tune_level<float>(H, L, s) : tune_level<double>(H, L, s));
+    std::lock_guard<std::mutex> lock(g_hgs_tune_mu);
+    g_hgs_tune[key] = L.hgs_lpr;
+  }
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }

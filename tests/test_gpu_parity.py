@@ -270,9 +270,12 @@ def test_gmres_unpreconditioned_and_zero_rhs(R, oracle, inputs):
 
 @pytest.mark.parametrize("kind", ["BF", "AMG_J"])
 def test_batch_equals_single_systems(R, oracle, inputs, kind):
-    """Three systems of different sizes solved in one batch: each member's
-    hierarchy equals its single-system hierarchy, each solution meets the
-    tolerance and matches the single solve."""
+    """Three systems of different sizes solved in one batch: each solution
+    meets the tolerance (by the oracle's residual) and matches the single
+    solve to the parity bar. The smoother's lanes per row are tuned per level
+    shape, and a stacked level may get another choice than a single system's,
+    so the FP32 V-cycle's summation order can differ: iteration counts agree
+    within one."""
     probs = [inputs.config_lognormal_2d(1e4, n=24, member=1), inputs.config_small_2d(),
              inputs.config_lognormal_2d(1e3, n=40, member=2)]
     dp = R.DeviceProblems(probs)
@@ -297,9 +300,9 @@ def test_batch_equals_single_systems(R, oracle, inputs, kind):
         Mk = R.Precond(Jk, prm)
         xk = torch.zeros_like(Fk)
         stk = R.gmres_solve(Jk, Mk, -Fk, xk, R.GmresParams())
-        assert st.its[k] == stk.iterations
-        np.testing.assert_allclose(xb[2 * off[k]:2 * off[k + 1]], xk.cpu().numpy(), rtol=1e-9,
-                                   atol=1e-12 * float(xk.abs().max()))
+        assert abs(int(st.its[k]) - stk.iterations) <= 1
+        xs = xk.cpu().numpy()
+        assert np.linalg.norm(xb[2 * off[k]:2 * off[k + 1]] - xs) <= 1e-6 * np.linalg.norm(xs)
         Fo, Jo, (rp, col) = oracle.assemble(p, us[k], uos[k], inputs.DAY)
         res = -Fo - oracle.bsr2_spmv(rp, col, Jo, xb[2 * off[k]:2 * off[k + 1]])
         assert np.linalg.norm(res) <= 1e-8 * np.linalg.norm(Fo) * 1.01
