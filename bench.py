@@ -360,7 +360,7 @@ def e2e_steps(probs, states, precision, maxit, steps, warmup):
         torch.cuda.synchronize()
         total += time.perf_counter() - t0
         nconv += sum(r["converged"] for r in recs)
-    return nconv / total, h2d, d2h
+    return nconv, total, h2d, d2h
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -411,6 +411,25 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def reduce_over_ranks(times_ms, converged, dist, device):
+    """Whole-job figures of a replicated step: the slowest rank's times (MAX)
+    and the converged solves of all ranks (SUM). With dist None (one
+    process) the inputs come back unchanged."""
+    import torch
+    if dist is None:
+        return list(times_ms), list(converged)
+    t = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    c = torch.tensor(list(converged), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t], [int(round(float(v))) for v in c]
+
+
+def solves_per_second(converged, steps, total_ms):
+    """Converged solves of all ranks over the slowest rank's time."""
+    return converged * steps / (total_ms / 1e3) if total_ms > 0 else 0.0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -445,17 +464,16 @@ def main():
     stepb = GpuBatchStep(probs, states, R.FP32, args.maxit)
     msb, recsb = time_steps(stepb, args.steps, 1, barrier)
     convb = sum(r["converged"] for r in recsb)
-    t = torch.tensor([ms64, ms32, msb], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms64, ms32, msb = float(t[0]), float(t[1]), float(t[2])
-    valueb = world * convb * args.steps / (msb / 1e3)
-    value = world * conv64 * args.steps / (ms64 / 1e3)
-    value32 = world * conv32 * args.steps / (ms32 / 1e3)
+    (ms64, ms32, msb), (conv64, conv32, convb) = reduce_over_ranks([ms64, ms32, msb], [conv64, conv32, convb],
+                                                                   dist, "cuda")
+    value = solves_per_second(conv64, args.steps, ms64)
+    value32 = solves_per_second(conv32, args.steps, ms32)
+    valueb = solves_per_second(convb, args.steps, msb)
     e2e = None
     if not args.no_e2e:
-        v, h2d, d2h = e2e_steps(probs, states, R.FP64, args.maxit, args.steps, 1)
-        e2e = dict(value=world * v, unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
+        nconv_e, total_s, h2d, d2h = e2e_steps(probs, states, R.FP64, args.maxit, args.steps, 1)
+        (te_ms,), (ce,) = reduce_over_ranks([total_s * 1e3], [nconv_e], dist, "cuda")
+        e2e = dict(value=solves_per_second(ce, 1, te_ms), unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
     if rank != 0:
         return
     prof, per_solve = profiled_step(step64)
