@@ -1477,6 +1477,13 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       int32_t tot = 0;
       RS_TRY(exclusive_scan(Lc.hs_rp, Lc.hs_rp, n, s, &tot));
       Lc.hs_nnz = tot;
+      {
+        int32_t *mx = nullptr;
+        RS_TRY(sc.get(&mx, 1));
+        RS_CHECK_CUDA(cudaMemsetAsync(mx, 0, sizeof(int32_t), s));
+        RS_COUNTED k_chunk_nnz_max<<<grid_for(Lc.nchunk), kBlock, 0, s>>>(Lc.nchunk, Lc.chunk_row0, Lc.hs_rp, mx);
+        RS_TRY(sync_copy(&Lc.hs_chunk_max, mx, sizeof(int32_t), s));
+      }
       RS_TRY(dalloc_n(&Lc.hs_col, (size_t)tot + 1, s));
       if (H.precision == RS_PREC_FP32) {
         RS_TRY(dalloc_n(&Lc.hs_valf, (size_t)tot + 1, s));

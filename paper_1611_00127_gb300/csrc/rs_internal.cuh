@@ -171,6 +171,7 @@ struct Level {
   // hybrid smoother: chunks of consecutive rows (never spanning two systems)
   int32_t nchunk = 0;
   int32_t chunk_max_nnz = 0;         // largest number of matrix entries in one chunk
+  int32_t hs_chunk_max = 0;          // largest number of packed smoother entries in one chunk
   int32_t *chunk_row0 = nullptr;     // [2 nchunk] (first row, end row) of each chunk
   int32_t *chunk_coff = nullptr;     // [nchunk * (ncolour+1)] colour offsets inside each chunk
   int32_t *chunk_rows = nullptr;     // [n] local row of each position, sorted by (chunk, colour, row)

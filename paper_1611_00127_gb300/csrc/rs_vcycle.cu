@@ -79,11 +79,14 @@ __device__ int g_hgs_wait_timeout;
 
 __host__ __device__ constexpr size_t hgs_seg(size_t bytes) { return ((bytes + 15) & ~size_t(15)) + 16; }
 
+// Dynamic shared memory of a sweep CTA: chunks of up to cmax rows, up to
+// `stage` packed entries staged, ncol colours (the colour offsets come last,
+// so a smaller ncol only trims the end).
 template <typename T>
-constexpr size_t hgs_smem(int cmax, int stage) {
+constexpr size_t hgs_smem(int cmax, int stage, int ncol = kHgsMaxColours) {
   return 3 * hgs_seg(sizeof(T) * (size_t)cmax) + hgs_seg(sizeof(T) * (size_t)stage) +
          hgs_seg(sizeof(int32_t) * (size_t)stage) + hgs_seg(sizeof(int32_t) * ((size_t)cmax + 1)) +
-         2 * hgs_seg(sizeof(int32_t) * (size_t)cmax) + sizeof(int32_t) * (kHgsMaxColours + 1);
+         2 * hgs_seg(sizeof(int32_t) * (size_t)cmax) + sizeof(int32_t) * ((size_t)ncol + 1);
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -284,11 +287,11 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs(const int32_t *__restrict__
 // block times its two right-hand sides less their couplings (a point whose
 // block is singular keeps its values). One thread per point.
 template <typename T>
-constexpr size_t hgs2_smem(int cmax, int stage) {
+constexpr size_t hgs2_smem(int cmax, int stage, int ncol = kHgsMaxColours) {
   return 2 * hgs_seg(sizeof(T) * (size_t)cmax) + hgs_seg(sizeof(T) * 2 * (size_t)cmax) +
          hgs_seg(sizeof(T) * (size_t)stage) + hgs_seg(sizeof(int32_t) * (size_t)stage) +
          hgs_seg(sizeof(int32_t) * ((size_t)cmax + 1)) + 2 * hgs_seg(sizeof(int32_t) * (size_t)cmax) +
-         sizeof(int32_t) * (kHgsMaxColours + 1);
+         sizeof(int32_t) * ((size_t)ncol + 1);
 }
 
 template <typename T, int LPR>
@@ -680,12 +683,14 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
     return;
   }
   if (H.prm.smoother == RS_SMOOTH_HYBRID) {
-    const int32_t stage = std::min(L.chunk_max_nnz, kHgsStageEntries);
-    const size_t shm = hgs_smem<T>(H.prm.chunk, stage);
+    // staging area: the level's largest chunk of packed entries (the diagonal
+    // is not among them)
+    const int32_t stage = std::min(L.hs_chunk_max, kHgsStageEntries);
+    const size_t shm = hgs_smem<T>(H.prm.chunk, stage, L.ncolour);
     const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
     const int hl = L.hgs_lpr > 0 ? L.hgs_lpr : hgs_lpr(L.A.n, L.A.nnz, L.nchunk);
     if (L.nfun == 2) {
-      const size_t shm2 = hgs2_smem<T>(H.prm.chunk, stage);
+      const size_t shm2 = hgs2_smem<T>(H.prm.chunk, stage, L.ncolour);
       for (int sw = 0; sw < sweeps; sw++) {
         T *out = (cur == xa) ? xb : xa;
         ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);
