@@ -86,6 +86,12 @@ typedef struct rs_problem {
   double s_wr, s_nr;                  /* residual saturations */
   double u_in;                        /* water Darcy flux injected through the x = 0 face [m/s] */
   double p_out, sn_out;               /* Dirichlet outlet on the x = L face */
+  /* point wells (the corner wells of the paper's examples, Sec. 4):
+   * well_in >= 0: water enters only as a source of q_in [m^3/s] in that cell
+   * (u_in unused); well_out >= 0: only that cell's x = L face (ix = nx-1) is
+   * the outlet. -1: the face conditions above. */
+  double q_in;
+  int32_t well_in, well_out;
 } rs_problem;
 
 #define RS_SMOOTH_MCGS 0      /* multicolour Gauss-Seidel over the whole level */

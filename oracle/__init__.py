@@ -53,7 +53,8 @@ class _Problem(C.Structure):
                 ("rho_w", C.c_double), ("rho_n", C.c_double), ("g", C.c_double),
                 ("pc_model", C.c_int32), ("pc_p0", C.c_double), ("pc_pd", C.c_double),
                 ("bc_lambda", C.c_double), ("s_wr", C.c_double), ("s_nr", C.c_double),
-                ("u_in", C.c_double), ("p_out", C.c_double), ("sn_out", C.c_double)]
+                ("u_in", C.c_double), ("p_out", C.c_double), ("sn_out", C.c_double),
+                ("q_in", C.c_double), ("well_in", C.c_int32), ("well_out", C.c_int32)]
 
 
 class _Csr(C.Structure):
@@ -163,7 +164,7 @@ def _problem(prob) -> tuple:
                  keep.kx.ctypes.data, keep.ky.ctypes.data, keep.kz.ctypes.data,
                  prob.phi, prob.mu_w, prob.mu_n, prob.rho_w, prob.rho_n, prob.g,
                  prob.pc_model, prob.pc_p0, prob.pc_pd, prob.bc_lambda, prob.s_wr,
-                 prob.s_nr, prob.u_in, prob.p_out, prob.sn_out)
+                 prob.s_nr, prob.u_in, prob.p_out, prob.sn_out, prob.q_in, prob.well_in, prob.well_out)
     return s, keep
 
 

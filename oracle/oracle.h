@@ -26,6 +26,8 @@ typedef struct {
   double pc_p0, pc_pd, bc_lambda;
   double s_wr, s_nr;
   double u_in, p_out, sn_out;
+  double q_in;                         /* point wells, see or_assemble */
+  int32_t well_in, well_out;
 } or_problem;
 
 /* Scalar CSR, n rows by m columns, columns ascending in each row. */

@@ -26,7 +26,10 @@
  *  - Boundaries: water enters through the x = 0 face at Darcy flux u_in
  *    (mass source rho_w u_in A on those cells); the x = L face is a Dirichlet
  *    face at P_w = p_out with inflowing oil saturation sn_out, using the half
- *    transmissibility A K_i / (h/2); all other faces are closed.
+ *    transmissibility A K_i / (h/2); all other faces are closed. Point wells
+ *    (the corner wells of the examples of Sec. 4): with well_in >= 0 the
+ *    water enters only as a mass source rho_w q_in in that cell; with
+ *    well_out >= 0 only that cell's x = L face is the outlet.
  *  - Depth D is the last coordinate (y in 2D, z in 3D), cell centres.
  */
 #include <math.h>
@@ -218,8 +221,8 @@ void or_assemble(const or_problem *p, const double *u, const double *u_old, doub
       }
     }
     int32_t ix = i % p->nx;
-    /* Dirichlet outlet face at x = L */
-    if (ix == p->nx - 1) {
+    /* Dirichlet outlet face at x = L (the whole face, or one cell's) */
+    if (ix == p->nx - 1 && (p->well_out < 0 || i == p->well_out)) {
       double T = face_area(p, 0) * p->kx[i] / (0.5 * p->hx);
       double mob_b[6];
       or_constitutive(p, p->sn_out, mob_b);
@@ -239,8 +242,12 @@ void or_assemble(const or_problem *p, const double *u, const double *u_old, doub
         }
       }
     }
-    /* injection through x = 0 */
-    if (ix == 0) Fw -= p->rho_w * p->u_in * face_area(p, 0);
+    /* injection through x = 0, or at the injection well */
+    if (p->well_in < 0) {
+      if (ix == 0) Fw -= p->rho_w * p->u_in * face_area(p, 0);
+    } else if (i == p->well_in) {
+      Fw -= p->rho_w * p->q_in;
+    }
     F[2 * i] = Fw;
     F[2 * i + 1] = Fn;
   }

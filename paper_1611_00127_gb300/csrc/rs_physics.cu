@@ -18,7 +18,9 @@
 //    linearly below Sb = 1e-4.
 //  - Water injected through x = 0 at Darcy flux u_in; Dirichlet outlet on
 //    x = L with half-cell transmissibility; other faces closed; depth is the
-//    last coordinate.
+//    last coordinate. Point wells (the corner wells of the examples of
+//    Sec. 4): a water source rho_w q_in in cell well_in instead of the x = 0
+//    flux, and the outlet restricted to the x = L face of cell well_out.
 #include <cstring>
 #include <mutex>
 
@@ -33,6 +35,8 @@ struct DProb {
   double phi, mu_w, mu_n, rho_w, rho_n, g;
   int32_t pc_model;
   double pc_p0, pc_pd, bc_lambda, s_wr, s_nr, u_in, p_out, sn_out;
+  double q_in;
+  int32_t well_in, well_out;   // point wells (-1: face conditions)
   int32_t cell0;   // first global cell of this grid
   int32_t ncell;
 };
@@ -217,7 +221,7 @@ __global__ void k_assemble(const DProb *probs, int32_t nprob, int32_t ncell, con
     }
   }
   const int32_t ix = i % p.nx;
-  if (ix == p.nx - 1) {
+  if (ix == p.nx - 1 && (p.well_out < 0 || i == p.well_out)) {
     const double T = face_area(p, 0) * p.kx[i] / (0.5 * p.hx);
     double mb[6];
     constitutive(p, p.sn_out, mb);
@@ -236,7 +240,11 @@ __global__ void k_assemble(const DProb *probs, int32_t nprob, int32_t ncell, con
       if (up_i) blk[kd][2 * a + 1] += cc * mi[2 + a] * dphi;
     }
   }
-  if (ix == 0) Fw -= p.rho_w * p.u_in * face_area(p, 0);
+  if (p.well_in < 0) {
+    if (ix == 0) Fw -= p.rho_w * p.u_in * face_area(p, 0);
+  } else if (i == p.well_in) {
+    Fw -= p.rho_w * p.q_in;
+  }
   F[2 * (int64_t)g] = Fw;
   F[2 * (int64_t)g + 1] = Fn;
   if (Jval) {
@@ -259,6 +267,9 @@ static int upload_probs(const rs_problem *probs, int32_t nprob, DProb **d, int32
     if (!q.kx || !q.ky || (q.dim == 3 && !q.kz)) return fail(RS_EINVAL, "missing permeability");
     if (q.pc_model < 0 || q.pc_model > 2 || !(q.bc_lambda > 0) || !(q.mu_w > 0) || !(q.mu_n > 0))
       return fail(RS_EINVAL, "bad constitutive parameters");
+    if (q.well_in < -1 || q.well_in >= q.nx * q.ny * q.nz || q.well_out < -1 ||
+        q.well_out >= q.nx * q.ny * q.nz || (q.well_out >= 0 && q.well_out % q.nx != q.nx - 1))
+      return fail(RS_EINVAL, "bad well cells in problem " + std::to_string(k));
     DProb &p = h[k];
     p.dim = q.dim; p.nx = q.nx; p.ny = q.ny; p.nz = q.nz;
     p.hx = q.hx; p.hy = q.hy; p.hz = q.hz;
@@ -266,6 +277,7 @@ static int upload_probs(const rs_problem *probs, int32_t nprob, DProb **d, int32
     p.phi = q.phi; p.mu_w = q.mu_w; p.mu_n = q.mu_n; p.rho_w = q.rho_w; p.rho_n = q.rho_n; p.g = q.g;
     p.pc_model = q.pc_model; p.pc_p0 = q.pc_p0; p.pc_pd = q.pc_pd; p.bc_lambda = q.bc_lambda;
     p.s_wr = q.s_wr; p.s_nr = q.s_nr; p.u_in = q.u_in; p.p_out = q.p_out; p.sn_out = q.sn_out;
+    p.q_in = q.q_in; p.well_in = q.well_in; p.well_out = q.well_out;
     p.cell0 = (int32_t)tot;
     p.ncell = q.nx * q.ny * q.nz;
     tot += (int64_t)p.ncell;
@@ -474,6 +486,9 @@ extern "C" int jacobian_assemble_noalloc(const rs_problem *probs, int32_t nprob,
     if (!q.kx || !q.ky || (q.dim == 3 && !q.kz)) return fail(RS_EINVAL, "missing permeability");
     if (q.pc_model < 0 || q.pc_model > 2 || !(q.bc_lambda > 0) || !(q.mu_w > 0) || !(q.mu_n > 0))
       return fail(RS_EINVAL, "bad constitutive parameters");
+    if (q.well_in < -1 || q.well_in >= q.nx * q.ny * q.nz || q.well_out < -1 ||
+        q.well_out >= q.nx * q.ny * q.nz || (q.well_out >= 0 && q.well_out % q.nx != q.nx - 1))
+      return fail(RS_EINVAL, "bad well cells in problem " + std::to_string(k));
     DProb &p = h[k];
     p.dim = q.dim; p.nx = q.nx; p.ny = q.ny; p.nz = q.nz;
     p.hx = q.hx; p.hy = q.hy; p.hz = q.hz;
@@ -481,6 +496,7 @@ extern "C" int jacobian_assemble_noalloc(const rs_problem *probs, int32_t nprob,
     p.phi = q.phi; p.mu_w = q.mu_w; p.mu_n = q.mu_n; p.rho_w = q.rho_w; p.rho_n = q.rho_n; p.g = q.g;
     p.pc_model = q.pc_model; p.pc_p0 = q.pc_p0; p.pc_pd = q.pc_pd; p.bc_lambda = q.bc_lambda;
     p.s_wr = q.s_wr; p.s_nr = q.s_nr; p.u_in = q.u_in; p.p_out = q.p_out; p.sn_out = q.sn_out;
+    p.q_in = q.q_in; p.well_in = q.well_in; p.well_out = q.well_out;
     p.cell0 = (int32_t)tot;
     p.ncell = q.nx * q.ny * q.nz;
     tot += (int64_t)p.ncell;

@@ -77,6 +77,9 @@ class Problem:
     u_in: float = 1e-6       # injected water Darcy flux through the x = 0 face [m/s]
     p_out: float = 1e5       # Dirichlet water pressure on the x = L face [Pa]
     sn_out: float = 0.1      # oil saturation of fluid entering through x = L
+    q_in: float = 0.0        # point-well water rate into cell `well_in` [m^3/s]
+    well_in: int = -1        # injection cell (-1: through the x = 0 face at u_in)
+    well_out: int = -1       # outlet cell on x = L (-1: the whole x = L face)
     name: str = ""
 
     @property

@@ -54,7 +54,8 @@ class Problem(C.Structure):
                 ("rho_w", C.c_double), ("rho_n", C.c_double), ("g", C.c_double),
                 ("pc_model", C.c_int32), ("pc_p0", C.c_double), ("pc_pd", C.c_double),
                 ("bc_lambda", C.c_double), ("s_wr", C.c_double), ("s_nr", C.c_double),
-                ("u_in", C.c_double), ("p_out", C.c_double), ("sn_out", C.c_double)]
+                ("u_in", C.c_double), ("p_out", C.c_double), ("sn_out", C.c_double),
+                ("q_in", C.c_double), ("well_in", C.c_int32), ("well_out", C.c_int32)]
 
 
 class Bsr2C(C.Structure):
@@ -170,7 +171,8 @@ class DeviceProblems:
             self._keep += [kx, ky, kz]
             arr[k] = Problem(p.dim, p.nx, p.ny, p.nz, p.hx, p.hy, p.hz, kx.data_ptr(), ky.data_ptr(),
                              kz.data_ptr(), p.phi, p.mu_w, p.mu_n, p.rho_w, p.rho_n, p.g, p.pc_model,
-                             p.pc_p0, p.pc_pd, p.bc_lambda, p.s_wr, p.s_nr, p.u_in, p.p_out, p.sn_out)
+                             p.pc_p0, p.pc_pd, p.bc_lambda, p.s_wr, p.s_nr, p.u_in, p.p_out, p.sn_out,
+                             p.q_in, p.well_in, p.well_out)
         self.c = arr
         self.ncell = sum(p.ncell for p in self.probs)
         self.cell_off = np.cumsum([0] + [p.ncell for p in self.probs]).astype(np.int32)

@@ -119,3 +119,19 @@ def test_fp32_hierarchy_beyond_range_is_rejected(R, oracle, inputs):
         R.Precond(J, R.PrecParams(kind=R.AMG_J_SCALAR, amg=R.AmgParams(precision=R.FP32)))
     M = R.Precond(J, R.PrecParams(kind=R.AMG_J_SCALAR, amg=R.AmgParams(precision=R.FP64)))
     M.close()
+
+
+@pytest.mark.parametrize("wells", [dict(well_in=-2), dict(well_in=10 ** 6), dict(well_out=0),
+                                   dict(well_out=10 ** 6)])
+def test_bad_well_cells_are_rejected(R, inputs, wells):
+    """A well cell outside the grid, or an outlet cell that is not on the
+    x = L face, is refused before any launch."""
+    good = inputs.homogeneous(6, 4).with_(pc_model=2, pc_pd=5e3)
+    u, uo = inputs.front_state(good)
+    J = R.Bsr2.pattern(R.DeviceProblems(good))
+    F = torch.empty(2 * good.ncell, dtype=torch.float64, device="cuda")
+    dp = R.DeviceProblems(good.with_(**wells))
+    with pytest.raises(R.RsError, match="well"):
+        R.Bsr2.pattern(dp)
+    with pytest.raises(R.RsError, match="well"):
+        R.jacobian_assemble(dp, _dev(u), _dev(uo), inputs.DAY, J, F)

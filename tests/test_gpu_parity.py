@@ -32,12 +32,16 @@ def _small_cases(I):
     rng = np.random.default_rng(5)
     k = np.exp(rng.normal(np.log(1e-12), 1.0, 7 * 5 * 4))
     p3 = I.Problem(dim=3, nx=7, ny=5, nz=4, kx=k, ky=k * 0.5, kz=k * 0.1, pc_model=2, pc_pd=5e3, g=9.81)
+    # point wells (corner injection cell, single-cell outlet) with gravity
+    pw = I.config_small_2d().with_(pc_model=2, pc_pd=2e4, g=9.81, q_in=5.0 / 86400.0, well_in=0)
+    pw = pw.with_(well_out=pw.nx - 1)
+    p3w = p3.with_(q_in=1e-5, well_in=3 * 7 * 5 + 2 * 7, well_out=6)
     return [I.config_small_2d(), I.config_lognormal_2d(1e4, n=48), p3,
             I.config_small_2d().with_(pc_model=1, pc_p0=1e5, nx=13, ny=11, kx=np.full(143, 2e-12),
-                                      ky=np.full(143, 1e-12), kz=np.full(143, 1e-12))]
+                                      ky=np.full(143, 1e-12), kz=np.full(143, 1e-12)), pw, p3w]
 
 
-@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("case", range(6))
 def test_assembly_matches_oracle(R, oracle, inputs, case):
     p = _small_cases(inputs)[case]
     u, uo = inputs.front_state(p)

@@ -158,3 +158,57 @@ def test_jacobian_block_structure(oracle, inputs):
     assert np.all(d > 0)
     assert np.all(off <= 0)
     assert np.all(d + off.sum(axis=1) >= -1e-12 * d)
+
+
+def _wells(p):
+    """Corner wells of the examples of Sec. 4 on grid p: injection in cell 0
+    (top-left: depth grows with iy), outlet on the x = L face of the top-right
+    cell."""
+    return p.with_(well_in=0, well_out=p.nx - 1, q_in=5.0 / 86400.0)
+
+
+@pytest.mark.parametrize("case", [
+    dict(dim=2, nx=6, ny=5, nz=1, pc_model=2, g=9.81),
+    dict(dim=3, nx=4, ny=3, nz=3, pc_model=1, g=9.81),
+])
+def test_jacobian_with_point_wells_matches_finite_differences(oracle, inputs, case):
+    p, u, uo = _small(inputs, **case)
+    p = _wells(p)
+    F0, J, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
+    A = oracle.bsr2_to_scipy(rp, col, J).toarray()
+    n = u.size
+    Jfd = np.zeros((n, n))
+    for k in range(n):
+        h = 1e-3 if k % 2 == 0 else 1e-8
+        up, um = u.copy(), u.copy()
+        up[k] += h
+        um[k] -= h
+        Fp = oracle.assemble(p, up, uo, inputs.DAY, pattern=(rp, col), jacobian=False)[0]
+        Fm = oracle.assemble(p, um, uo, inputs.DAY, pattern=(rp, col), jacobian=False)[0]
+        Jfd[:, k] = (Fp - Fm) / (2 * h)
+    scale = np.abs(A).max(axis=0, keepdims=True)
+    assert (np.abs(A - Jfd) / scale).max() < 1e-6
+
+
+def test_point_wells_mass_balance(oracle, inputs):
+    """Summed over cells, with the outlet cell at outlet conditions and g = 0:
+    sum F_w = storage - rho_w q_in, sum F_n = storage; and only the well cells
+    differ from the face-condition residual apart from the old face cells."""
+    p, u, uo = _small(inputs, nx=7, ny=6, pc_model=2)
+    p = _wells(p).with_(sn_out=0.3)
+    u[2 * p.well_out] = p.p_out
+    u[2 * p.well_out + 1] = p.sn_out
+    F, _, _ = oracle.assemble(p, u, uo, inputs.DAY, jacobian=False)
+    V = p.hx * p.hy * 1.0
+    stor_w = V * p.phi * p.rho_w * ((1 - u[1::2]) - (1 - uo[1::2])).sum() / inputs.DAY
+    stor_n = V * p.phi * p.rho_n * (u[1::2] - uo[1::2]).sum() / inputs.DAY
+    flux_scale = np.abs(F).max()
+    np.testing.assert_allclose(F[0::2].sum(), stor_w - p.rho_w * p.q_in, atol=1e-11 * flux_scale * p.ncell)
+    np.testing.assert_allclose(F[1::2].sum(), stor_n, atol=1e-11 * flux_scale * p.ncell)
+    # the face-condition problem differs from the well problem only in the
+    # x = 0 cells (injection) and the x = L cells (outlet)
+    Ff, _, _ = oracle.assemble(p.with_(well_in=-1, well_out=-1), u, uo, inputs.DAY, jacobian=False)
+    ix = np.arange(p.ncell) % p.nx
+    same = (ix != 0) & (ix != p.nx - 1)
+    np.testing.assert_array_equal(F[0::2][same], Ff[0::2][same])
+    np.testing.assert_array_equal(F[1::2][same], Ff[1::2][same])
