@@ -158,6 +158,8 @@ typedef struct rs_newton_params {
   double ftol;             /* on max_i |F_a,i| dt / (V phi rho_a) */
   rs_gmres_params gmres;
   rs_precond_params prec;
+  double max_ds;           /* > 0: each cell's S_n change per iteration is cut to
+                              [-max_ds, max_ds] (Appleyard chop); <= 0: full steps */
 } rs_newton_params;
 
 typedef struct rs_newton_stats {
@@ -259,7 +261,10 @@ int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *b, double *
 
 /* One backward-Euler step by Newton's method (Sec. 3): repeats
  * assemble -> precond_create -> gmres_solve(J du = -F) -> u += du (S_n
- * clamped to [0, 1 - S_wr - 1e-12]) until the scaled residual is <= ftol.
+ * change cut to +-max_ds when max_ds > 0, S_n clamped to
+ * [0, 1 - S_wr - 1e-12]) until the scaled residual is <= ftol. Returns
+ * RS_NOT_CONVERGED after max_newton iterations, when FGMRES does not converge,
+ * or when the residual is not finite; u then holds the last iterate.
  * u: [2N] in/out. (sync) */
 int newton_step(const rs_problem *probs, int32_t nprob, double *u, const double *u_old, double dt,
                 const rs_newton_params *params, rs_newton_stats *stats, cudaStream_t stream);

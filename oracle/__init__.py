@@ -76,7 +76,8 @@ class _PrecParams(C.Structure):
 
 class _NewtonParams(C.Structure):
     _fields_ = [("max_newton", C.c_int32), ("ftol", C.c_double), ("gmres_m", C.c_int32),
-                ("gmres_maxit", C.c_int32), ("gmres_rtol", C.c_double), ("prec", _PrecParams)]
+                ("gmres_maxit", C.c_int32), ("gmres_rtol", C.c_double), ("prec", _PrecParams),
+                ("max_ds", C.c_double)]
 
 
 def lib():
@@ -496,10 +497,11 @@ class NewtonParams:
     gmres_maxit: int = 1000
     gmres_rtol: float = 1e-8
     prec: PrecParams = None
+    max_ds: float = 0.0
 
     def c(self):
         return _NewtonParams(self.max_newton, self.ftol, self.gmres_m, self.gmres_maxit,
-                             self.gmres_rtol, (self.prec or PrecParams()).c())
+                             self.gmres_rtol, (self.prec or PrecParams()).c(), self.max_ds)
 
 
 def newton(prob, u, u_old, dt, params: NewtonParams = None):

@@ -133,6 +133,7 @@ typedef struct {
   int32_t gmres_m, gmres_maxit;
   double gmres_rtol;
   or_precond_params prec;
+  double max_ds;        /* > 0: cut each cell's S_n change to [-max_ds, max_ds] */
 } or_newton_params;
 int32_t or_newton(const or_problem *p, double *u, const double *u_old, double dt,
                   const or_newton_params *prm, int32_t *newton_its, int32_t *linear_its,

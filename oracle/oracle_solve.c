@@ -327,9 +327,12 @@ int32_t or_fgmres(int32_t nb, const int32_t *rowptr, const int32_t *col, const d
 }
 
 /* Newton's method for one backward-Euler step: J(u_k) du = -F(u_k),
- * u_{k+1} = u_k + du, then S_n clamped to [0, 1 - S_wr - 1e-12]. Converged
- * when the scaled residual (or_scaled_fnorm) is <= ftol. Returns 0 on
- * convergence, 1 if max_newton is reached, 2 if a linear solve failed. */
+ * u_{k+1} = u_k + du, each cell's S_n change first cut to [-max_ds, max_ds]
+ * when max_ds > 0 (Appleyard chop; the paper does not state its damping),
+ * then S_n clamped to [0, 1 - S_wr - 1e-12]. Converged when the scaled
+ * residual (or_scaled_fnorm) is <= ftol. Returns 0 on convergence, 1 if
+ * max_newton is reached, 2 if a linear solve failed, 3 if the residual is not
+ * finite. */
 int32_t or_newton(const or_problem *p, double *u, const double *u_old, double dt,
                   const or_newton_params *prm, int32_t *newton_its, int32_t *linear_its,
                   double *fnorm_hist) {
@@ -348,6 +351,7 @@ int32_t or_newton(const or_problem *p, double *u, const double *u_old, double dt
     if (fnorm_hist) fnorm_hist[k] = fn;
     if (fn <= prm->ftol) { status = 0; break; }
     if (k == prm->max_newton) break;
+    if (!isfinite(fn)) { status = 3; break; }
     for (int32_t i = 0; i < n; i++) { F[i] = -F[i]; du[i] = 0.0; }
     or_precond *M = or_precond_create(nb, rowptr, col, J, &prm->prec);
     int32_t its = 0;
@@ -359,7 +363,9 @@ int32_t or_newton(const or_problem *p, double *u, const double *u_old, double dt
     double smax = 1.0 - p->s_wr - 1e-12;
     for (int32_t i = 0; i < nb; i++) {
       u[2 * i] += du[2 * i];
-      double s = u[2 * i + 1] + du[2 * i + 1];
+      double ds = du[2 * i + 1];
+      if (prm->max_ds > 0.0 && fabs(ds) > prm->max_ds) ds = ds > 0.0 ? prm->max_ds : -prm->max_ds;
+      double s = u[2 * i + 1] + ds;
       u[2 * i + 1] = s < 0.0 ? 0.0 : (s > smax ? smax : s);
     }
   }

@@ -1,15 +1,18 @@
 // One backward-Euler step by Newton's method (Sec. 3): J(u_k) du = -F(u_k),
-// u_{k+1} = u_k + du with S_n clamped to [0, 1 - S_wr - 1e-12], until the
+// u_{k+1} = u_k + du with S_n clamped to [0, 1 - S_wr - 1e-12] (and, when
+// asked, each cell's S_n change cut to +-max_ds: an Appleyard chop), until the
 // scaled residual max |F_a,i| dt / (V phi rho_a) is at most ftol. Each
 // iteration re-assembles F and the exact J, rebuilds the preconditioner and
 // solves with FGMRES; several grids may be stepped together as one batch.
 #include <chrono>
+#include <cmath>
 
 #include "rs_internal.cuh"
 
 namespace rs {
 int scaled_fnorm(const rs_problem *probs, int32_t nprob, const double *F, double dt, double *out, cudaStream_t s);
-int newton_update(const rs_problem *probs, int32_t nprob, const double *du, double sign, double *u, cudaStream_t s);
+int newton_update(const rs_problem *probs, int32_t nprob, const double *du, double sign, double max_ds, double *u,
+                  cudaStream_t s);
 }  // namespace rs
 using namespace rs;
 
@@ -48,6 +51,7 @@ extern "C" int newton_step(const rs_problem *probs, int32_t nprob, double *u, co
     st.fnorm = fn;
     if (fn <= params->ftol) { status = RS_OK; break; }
     if (k >= params->max_newton) break;
+    if (!std::isfinite(fn)) { st.newton_its = k; k = -1; break; }
     RS_CHECK_CUDA(cudaMemsetAsync(du, 0, sizeof(double) * 2 * (size_t)nb, s));
     t0 = std::chrono::steady_clock::now();
     rs_precond *M = nullptr;
@@ -64,9 +68,9 @@ extern "C" int newton_step(const rs_problem *probs, int32_t nprob, double *u, co
     if (r < 0) return r;
     if (r == RS_NOT_CONVERGED) { status = RS_NOT_CONVERGED; st.newton_its = k + 1; break; }
     // u -= du (du solves J du = F)
-    RS_TRY(newton_update(probs, nprob, du, -1.0, u, s));
+    RS_TRY(newton_update(probs, nprob, du, -1.0, params->max_ds, u, s));
   }
-  if (status == RS_OK || k >= params->max_newton) st.newton_its = k;
+  if (k >= 0 && (status == RS_OK || k >= params->max_newton)) st.newton_its = k;
   if (stats) *stats = st;
   RS_CHECK_CUDA(cudaStreamSynchronize(s));
   return status;

@@ -362,15 +362,18 @@ __global__ void k_scaled_fnorm(const DProb *probs, int32_t nprob, int32_t ncell,
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
 }
 
-// u += sign * du; S_n clamped to [0, 1 - S_wr - 1e-12]
+// u += sign * du, the S_n change cut to [-max_ds, max_ds] when max_ds > 0;
+// S_n clamped to [0, 1 - S_wr - 1e-12]
 __global__ void k_newton_update(const DProb *probs, int32_t nprob, int32_t ncell, const double *du, double sign,
-                                double *u) {
+                                double max_ds, double *u) {
   int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ncell) return;
   const DProb &p = probs[find_prob(probs, nprob, g)];
   const double smax = 1.0 - p.s_wr - 1e-12;
   u[2 * (int64_t)g] += sign * du[2 * (int64_t)g];
-  double sn = u[2 * (int64_t)g + 1] + sign * du[2 * (int64_t)g + 1];
+  double ds = sign * du[2 * (int64_t)g + 1];
+  if (max_ds > 0.0) ds = ds < -max_ds ? -max_ds : (ds > max_ds ? max_ds : ds);
+  double sn = u[2 * (int64_t)g + 1] + ds;
   sn = sn < 0.0 ? 0.0 : (sn > smax ? smax : sn);
   u[2 * (int64_t)g + 1] = sn;
 }
@@ -395,11 +398,12 @@ int scaled_fnorm(const rs_problem *probs, int32_t nprob, const double *F, double
   return 0;
 }
 
-int newton_update(const rs_problem *probs, int32_t nprob, const double *du, double sign, double *u, cudaStream_t s) {
+int newton_update(const rs_problem *probs, int32_t nprob, const double *du, double sign, double max_ds, double *u,
+                  cudaStream_t s) {
   DProb *d = nullptr;
   int32_t ncell = 0;
   RS_TRY(upload_probs(probs, nprob, &d, &ncell, s));
-  if (ncell > 0) RS_COUNTED k_newton_update<<<grid_for(ncell), kBlock, 0, s>>>(d, nprob, ncell, du, sign, u);
+  if (ncell > 0) RS_COUNTED k_newton_update<<<grid_for(ncell), kBlock, 0, s>>>(d, nprob, ncell, du, sign, max_ds, u);
   dfree(d, s);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;

@@ -202,6 +202,47 @@ def config_channel_3d(n: int = 256, pc_scale: float = 1e4) -> Problem:
                    name=f"3d_{n}^3_channel")
 
 
+MILLIDARCY = 9.869233e-16   # m^2
+
+# Capillary-pressure parameter sets "Ex 1".."Ex 4" of Sec. 4 (Table of P_c
+# parameters): (linear entry pressure P0, Brooks-Corey entry pressure Pd,
+# Brooks-Corey lambda). Ex 1 is diffusion-dominated, Ex 2 advection-dominated,
+# Ex 3 strongly advection-dominated.
+PC_EXAMPLES = {1: (1e5, 1e6, 2.5), 2: (1e4, 1e5, 0.8), 3: (1e3, 2e4, 2.5), 4: (1e6, 1e6, 0.8)}
+
+# time step [days] and number of steps of the gravity study per example
+# (final times 20, 8 and 2 days)
+GRAVITY_DT_DAYS = {1: 10.0, 2: 4.0, 3: 1.0}
+GRAVITY_STEPS = 2
+
+
+def config_gravity_2d(n: int, example: int = 1, pc_model: int = PC_BROOKS_COREY) -> Problem:
+    """The gravity example of Sec. 4.2: a vertical 20 m x 20 m box (unit
+    thickness, depth = y, so row iy = 0 is the top) on an n x n mesh,
+    homogeneous 100 mD, water injected at 5 m^3/day into the top-left cell,
+    outlet on the x = L face of the top-right cell. Fluids, porosity and the
+    outlet state are those of the two-dimensional oil-water example (1000 /
+    700 kg/m^3, 1 / 10 cP, phi 0.2, S_wr 0, outlet p_w = 0 and S_w = 0.2);
+    the capillary model takes parameter set `example`."""
+    k = np.full(n * n, 100.0 * MILLIDARCY)
+    p0, pd, lam = PC_EXAMPLES[example]
+    h = 20.0 / n
+    return Problem(dim=2, nx=n, ny=n, nz=1, kx=k, ky=k.copy(), kz=k.copy(), hx=h, hy=h, hz=1.0,
+                   phi=0.2, mu_w=1e-3, mu_n=1e-2, rho_w=1000.0, rho_n=700.0, g=9.81,
+                   pc_model=pc_model, pc_p0=p0, pc_pd=pd, bc_lambda=lam, s_wr=0.0, s_nr=0.0,
+                   u_in=0.0, p_out=0.0, sn_out=0.8, q_in=5.0 / DAY, well_in=0, well_out=n - 1,
+                   name=f"2d_gravity_{n}x{n}_ex{example}_{'bc' if pc_model == PC_BROOKS_COREY else 'lin'}")
+
+
+def uniform_state(p: Problem, p_w: float = 1e5, s_n: float = 0.8) -> np.ndarray:
+    """Uniform initial state (the oil-water examples of Sec. 4: p_w = 1e5 Pa,
+    S_n = 0.8)."""
+    u = np.empty(2 * p.ncell)
+    u[0::2] = p_w
+    u[1::2] = s_n
+    return u
+
+
 def cell_x(p: Problem) -> np.ndarray:
     """x coordinate of each cell centre, in cell order."""
     ix = np.arange(p.ncell) % p.nx

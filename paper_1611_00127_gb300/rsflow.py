@@ -90,7 +90,7 @@ class GmresStatsC(C.Structure):
 
 class NewtonParamsC(C.Structure):
     _fields_ = [("max_newton", C.c_int32), ("ftol", C.c_double), ("gmres", GmresParamsC),
-                ("prec", PrecParamsC)]
+                ("prec", PrecParamsC), ("max_ds", C.c_double)]
 
 
 class NewtonStatsC(C.Structure):
@@ -291,9 +291,10 @@ class NewtonParams:
     ftol: float = 1e-6
     gmres: GmresParams = field(default_factory=GmresParams)
     prec: PrecParams = field(default_factory=PrecParams)
+    max_ds: float = 0.0      # > 0: Appleyard chop of each cell's S_n change per iteration
 
     def c(self):
-        return NewtonParamsC(self.max_newton, self.ftol, self.gmres.c(), self.prec.c())
+        return NewtonParamsC(self.max_newton, self.ftol, self.gmres.c(), self.prec.c(), self.max_ds)
 
 
 # ------------------------------------------------------------------ calls

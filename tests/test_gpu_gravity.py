@@ -1,0 +1,86 @@
+"""The gravity-driven two-dimensional study (Sec. 4.2) on the GPU.
+
+* 20^2 and 40^2, Ex 1..3, every preconditioner that converges there: the GPU
+  time stepping (Newton with the Appleyard chop, FGMRES, FP64 V-cycles)
+  takes the oracle's Newton iteration counts (within one per step), linear
+  counts within 10 % per step, and ends at the oracle's state within the
+  Newton tolerance.
+* 20^2 .. 160^2 in Ex 1 and Ex 3: every step of the point AMG, CPR-AMG(2)
+  and block factorisation converges, the oracle's residual accepts the final
+  state, and in the diffusion-dominated Ex 1 LI/NI of the point AMG and of
+  block factorisation at 160^2 stays within twice its 20^2 value (the
+  oracle: 9.9 -> 14.5 and 21.2 -> 29.0). In Ex 2 FGMRES(30) stops at its
+  1000-iteration limit from 80^2 on for several preconditioners, in the
+  oracle as on the GPU, so Ex 2 is checked at 20^2 and 40^2 only.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1611_00127_gb300 import rsflow
+    rsflow.lib()
+    return rsflow
+
+
+@pytest.fixture(scope="module")
+def G(R):
+    from paper_1611_00127_gb300 import gravity_study
+    return gravity_study
+
+
+ORACLE_KIND = {"AMG": (0, 0), "CPR1": (1, 2), "CPR2": (2, 2), "BF": (3, 0)}
+
+
+def _oracle_run(oracle, inputs, n, ex, kind):
+    p = inputs.config_gravity_2d(n, ex)
+    dt = inputs.GRAVITY_DT_DAYS[ex] * inputs.DAY
+    k, dec = ORACLE_KIND[kind]
+    u = inputs.uniform_state(p)
+    steps = []
+    for _ in range(inputs.GRAVITY_STEPS):
+        u, st, ni, li, _ = oracle.newton(p, u, u, dt, oracle.NewtonParams(
+            max_newton=40, max_ds=0.2, prec=oracle.PrecParams(kind=k, decouple=dec)))
+        assert st == 0
+        steps.append((ni, li, u.copy()))
+    return steps
+
+
+@pytest.mark.parametrize("n,kinds", [(20, ("AMG", "CPR1", "CPR2", "BF")), (40, ("AMG", "CPR2", "BF"))])
+@pytest.mark.parametrize("ex", [1, 2, 3])
+def test_gravity_time_steps_match_oracle(R, G, oracle, inputs, n, kinds, ex):
+    for kind in kinds:
+        ref = _oracle_run(oracle, inputs, n, ex, kind)
+        r = G.run_case(n, ex, kind, precision=R.FP64, keep_states=True)
+        assert r["converged"], (n, ex, kind, r["steps"])
+        for s, (ni, li, uo) in enumerate(ref):
+            g = r["steps"][s]
+            assert abs(g["ni"] - ni) <= 1, (n, ex, kind, s, g, ni)
+            assert abs(g["li"] - li) <= max(2, 0.1 * li), (n, ex, kind, s, g, li)
+            ug = r["states"][s]
+            np.testing.assert_allclose(ug[1::2], uo[1::2], atol=1e-5)
+            np.testing.assert_allclose(ug[0::2], uo[0::2], rtol=1e-5, atol=1e-5 * np.abs(uo[0::2]).max())
+
+
+@pytest.mark.parametrize("ex,bounded", [(1, ("AMG", "BF")), (3, ())])
+def test_gravity_mesh_sweep(R, G, oracle, inputs, ex, bounded):
+    dt = inputs.GRAVITY_DT_DAYS[ex] * inputs.DAY
+    ratio = {}
+    for kind in ("AMG", "CPR2", "BF"):
+        for n in G.MESHES:
+            r = G.run_case(n, ex, kind, precision=R.FP64, keep_states=(n == G.MESHES[-1]))
+            assert r["converged"], (ex, kind, n, r["steps"])
+            ratio[kind, n] = r["LI_per_NI"]
+            if n == G.MESHES[-1]:
+                p = inputs.config_gravity_2d(n, ex)
+                prev = r["states"][-2]
+                F, _, _ = oracle.assemble(p, r["states"][-1], prev, dt, jacobian=False)
+                assert oracle.scaled_fnorm(p, F, dt) <= 1e-6
+    for kind in bounded:
+        assert ratio[kind, G.MESHES[-1]] <= 2.0 * ratio[kind, G.MESHES[0]], (ex, kind, ratio)
