@@ -121,6 +121,10 @@ typedef struct rs_amg_params {
 
 typedef struct rs_amg rs_amg;
 typedef struct rs_precond rs_precond;
+typedef struct rs_ilu0 rs_ilu0;
+
+#define RS_P1_BLOCK_JACOBI 0  /* inverse of each cell's 2x2 diagonal block */
+#define RS_P1_ILU0 1          /* ILU(0) of the point-ordered matrix (Sec. 3.3) */
 
 #define RS_PC_AMG_J 0   /* black-box AMG on the point-ordered J (Sec. 3.2), the point method */
 #define RS_PC_CPR1 1    /* Algorithm 1, combinative two-stage CPR-AMG(1) */
@@ -135,7 +139,7 @@ typedef struct rs_precond rs_precond;
 typedef struct rs_precond_params {
   int32_t kind;            /* RS_PC_* */
   int32_t decouple;        /* CPR only: RS_DECOUPLE_* */
-  int32_t p1;              /* CPR only: 0 point-block Jacobi (the only GPU P1) */
+  int32_t p1;              /* CPR only: RS_P1_* first-stage preconditioner */
   rs_amg_params amg;
 } rs_precond_params;
 
@@ -275,6 +279,27 @@ int bsr2_spmv(const rs_bsr2 *J, const double *x, double *y, cudaStream_t stream)
 /* r = b - J x (FP64). */
 int bsr2_residual(const rs_bsr2 *J, const double *x, const double *b, double *r,
                   cudaStream_t stream);
+
+/* ILU(0) (Sec. 3.3: the first stage P1 of CPR, Algorithms 1 and 2) of the
+ * point-ordered scalar matrix of J: rows 2i, 2i+1 per cell, the pattern of
+ * J's blocks with their structural zeros, no fill. Factored in IKJ order
+ * (a zero pivot skips the elimination; the solve then divides by one) and
+ * applied as the forward and backward triangular solves, both level-scheduled
+ * over the cells: each phase is one launch of a single thread-block cluster
+ * (1..8 CTAs) walking the levels with a cluster barrier. J's block pattern
+ * must be structurally symmetric with every diagonal block present
+ * (RS_EINVAL otherwise). The handle keeps a reference to J's row_ptr and col
+ * and its own copy of the factors; J.val may change afterwards. (sync) */
+int ilu0_create(const rs_bsr2 *J, rs_ilu0 **out, cudaStream_t stream);
+/* x = (L U)^{-1} b; b, x [2 nb], not aliased. */
+int ilu0_apply(const rs_ilu0 *F, const double *b, double *x, cudaStream_t stream);
+/* Level count, widest level and CTAs per cluster of the schedule. */
+int ilu0_info(const rs_ilu0 *F, int32_t *nlevels, int32_t *max_width, int32_t *cluster_ctas);
+/* Copy of the factors into lu (device [4 nnzb], J's block layout:
+ * lu[4k + 2r + c] is the entry of scalar row 2i+r, column 2 col[k] + c;
+ * L strictly lower with unit diagonal, U upper). */
+int ilu0_factors(const rs_ilu0 *F, double *lu, cudaStream_t stream);
+int ilu0_destroy(rs_ilu0 *F);
 
 /* ------------------------------------------------------ introspection --- */
 /* Number of levels of a hierarchy, and level l's size and stored entries

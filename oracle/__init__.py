@@ -100,6 +100,8 @@ def lib():
             "or_scalar_from_bsr2": (P, [i32, P, P, P]),
             "or_bsr2_part": (P, [i32, P, P, P, i32, i32]),
             "or_decouple_abf": (None, [i32, P, P, P, P]),
+            "or_ilu0_bsr2": (None, [i32, P, P, P, P]),
+            "or_ilu0_solve_bsr2": (None, [i32, P, P, P, P, P]),
             "or_simple_schur": (P, [P, P, P, P]),
             "or_transpose": (P, [P]),
             "or_spgemm": (P, [P, P]),
@@ -287,6 +289,21 @@ def decouple_abf(rowptr, col, val):
     out = np.zeros_like(val)
     lib().or_decouple_abf(rowptr.size - 1, _p(_i32(rowptr)), _p(_i32(col)), _p(val), _p(out))
     return out
+
+
+def ilu0(rowptr, col, val):
+    """ILU(0) factors of the point-ordered scalar matrix, in the block layout."""
+    val = _f64(val)
+    lu = np.zeros_like(val)
+    lib().or_ilu0_bsr2(rowptr.size - 1, _p(_i32(rowptr)), _p(_i32(col)), _p(val), _p(lu))
+    return lu
+
+
+def ilu0_solve(rowptr, col, lu, b):
+    b = _f64(b)
+    x = np.zeros_like(b)
+    lib().or_ilu0_solve_bsr2(rowptr.size - 1, _p(_i32(rowptr)), _p(_i32(col)), _p(_f64(lu)), _p(b), _p(x))
+    return x
 
 
 def simple_schur(App: Csr, Aps: Csr, Asp: Csr, Ass: Csr) -> Csr:

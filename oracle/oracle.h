@@ -126,6 +126,13 @@ int32_t or_fgmres(int32_t nb, const int32_t *rowptr, const int32_t *col, const d
                   const or_precond *M, const double *b, double *x, int32_t m, double rtol,
                   int32_t maxit, int32_t *its, double *relres);
 
+/* ILU(0) of the point-ordered scalar matrix (P1 of CPR, Sec. 3.3): factors in
+ * the block layout (lu[4k + 2r + c]: scalar row 2i+r, column 2 col[k] + c),
+ * and the forward/backward solve with them. */
+void or_ilu0_bsr2(int32_t nb, const int32_t *rowptr, const int32_t *col, const double *val, double *lu);
+void or_ilu0_solve_bsr2(int32_t nb, const int32_t *rowptr, const int32_t *col, const double *lu, const double *b,
+                        double *x);
+
 /* ---- Newton (Sec. 3) ---- */
 typedef struct {
   int32_t max_newton;

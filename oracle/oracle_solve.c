@@ -105,6 +105,39 @@ static void ilu0_solve(const or_csr *A, const int32_t *dpos, const double *b, do
   }
 }
 
+/* ILU(0) of the point-ordered scalar matrix of a 2x2-block matrix (the
+ * paper's P1, Sec. 3.3), its factors returned in the block layout:
+ * lu[4k + 2r + cc] is the factor entry of scalar row 2i+r, column
+ * 2 col[k] + cc (L strictly lower with unit diagonal, U upper). */
+void or_ilu0_bsr2(int32_t nb, const int32_t *rowptr, const int32_t *col, const double *val, double *lu) {
+  or_csr *A = or_scalar_from_bsr2(nb, rowptr, col, val);
+  int32_t *dpos = xmalloc(sizeof(int32_t) * (size_t)(2 * nb + 1));
+  ilu0(A, dpos);
+  for (int32_t i = 0; i < nb; i++)
+    for (int r = 0; r < 2; r++) {
+      int32_t q = A->rowptr[2 * i + r];
+      for (int32_t k = rowptr[i]; k < rowptr[i + 1]; k++)
+        for (int c = 0; c < 2; c++) lu[4 * (size_t)k + 2 * r + c] = A->val[q++];
+    }
+  free(dpos);
+  or_csr_free(A);
+}
+
+/* x = (L U)^{-1} b with the factors of or_ilu0_bsr2. */
+void or_ilu0_solve_bsr2(int32_t nb, const int32_t *rowptr, const int32_t *col, const double *lu, const double *b,
+                        double *x) {
+  or_csr *A = or_scalar_from_bsr2(nb, rowptr, col, lu);
+  int32_t *dpos = xmalloc(sizeof(int32_t) * (size_t)(2 * nb + 1));
+  for (int32_t i = 0; i < 2 * nb; i++) {
+    dpos[i] = -1;
+    for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++)
+      if (A->col[q] == i) dpos[i] = q;
+  }
+  ilu0_solve(A, dpos, b, x);
+  free(dpos);
+  or_csr_free(A);
+}
+
 or_precond *or_precond_create(int32_t nb, const int32_t *rowptr, const int32_t *col, const double *val,
                               const or_precond_params *prm) {
   or_precond *M = xmalloc(sizeof(or_precond));

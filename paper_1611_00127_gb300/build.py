@@ -2,9 +2,10 @@
 
 Each translation unit is compiled by nvcc in parallel and linked into
 ``_build/librsflow.so``. The setup translation units (AMG hierarchy, block
-splitting, Schur complement, sparse products) are compiled with
-``--fmad=false`` so that their FP64 sums round exactly as written; the
-solve-phase kernels use fused multiply-add.
+splitting, Schur complement, sparse products) and the ILU(0) factorisation
+and triangular solves are compiled with ``--fmad=false`` so that their FP64
+sums round exactly as written; the other solve-phase kernels use fused
+multiply-add.
 """
 from __future__ import annotations
 
@@ -21,7 +22,7 @@ LIB = os.path.join(BUILD, "librsflow.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-EXACT_FP = {"rs_setup_sparse.cu", "rs_amg_setup.cu"}
+EXACT_FP = {"rs_setup_sparse.cu", "rs_amg_setup.cu", "rs_ilu.cu"}
 
 
 def nvcc() -> str:

@@ -1,0 +1,402 @@
+// ILU(0) of the point-ordered scalar matrix of a 2x2-block BSR matrix: the
+// first stage P1 of CPR (Sec. 3.3, Algorithms 1 and 2), factored and applied
+// on the GPU in level-scheduled form.
+//
+// The scalar matrix has rows 2c and 2c+1 for cell c; row 2c+r holds the
+// entries (2 col[k] + cc), cc = 0, 1, of every block k of block row c -- the
+// block pattern with its structural zeros. ILU(0) keeps exactly that pattern.
+// In IKJ order row i eliminates its lower entries in ascending column order:
+// for lower entry j, l = a_ij / u_jj (skipped when u_jj = 0), then every
+// entry of row j right of its diagonal updates the entry of row i in the same
+// column, when row i has one. The factors overwrite a copy of the values in
+// the BSR layout: L strictly lower with a unit diagonal, U upper. The solve
+// is L y = b forward, then U x = y backward (a zero pivot divides by one).
+//
+// Dependencies: row 2c+1 needs row 2c, and both need the rows of the
+// lower-numbered neighbour cells. Cells are grouped into levels (Kahn's
+// layering of that dependency DAG: level 0 has no lower neighbour, a cell
+// sits one level above its highest lower neighbour); cells of one level are
+// independent. Each phase -- layering, factorisation, forward + backward
+// solve -- is one launch of a single thread-block cluster (1..8 CTAs of up to
+// 1024 threads, sized to the widest level) that walks the levels with a
+// cluster barrier between them (hardware barrier; no spin loop). One thread
+// handles both rows of a cell in the sequential algorithm's operation order,
+// and this file is compiled without FMA contraction, so factors and solves
+// round exactly as the sequential algorithm does. Values that other threads
+// wrote earlier in the same launch are read with ld.global.cg (L2), so no
+// stale L1 line is ever used.
+//
+// The block pattern must be structurally symmetric (TPFA Jacobians are): the
+// layering releases a cell's upper neighbours from its own row and the
+// backward solve walks the levels in reverse. Set-up checks the symmetry and
+// that the layering placed every cell once.
+#include <cooperative_groups.h>
+
+#include "rs_internal.cuh"
+
+namespace cg = cooperative_groups;
+using namespace rs;
+
+struct rs_ilu0 {
+  int32_t nb = 0, nnzb = 0;
+  const int32_t *row_ptr = nullptr, *col = nullptr;   // caller's pattern (kept by reference)
+  double *lu = nullptr;            // factors, BSR layout [4 nnzb]
+  int32_t *dblk = nullptr;         // diagonal block of each block row [nb]
+  int32_t *lvl_cells = nullptr;    // cells ordered by level [nb]
+  int32_t *lvl_ptr = nullptr;      // level offsets [nb + 1]
+  int32_t *nlev_d = nullptr;       // level count on the device [1]
+  int32_t nlev = 0, maxw = 0;
+  int cluster = 1, threads = 32;
+  cudaStream_t stream = nullptr;
+};
+
+namespace {
+
+constexpr int kIluThreads = 1024;
+constexpr int kIluMaxCluster = 8;
+
+struct ClusterIdx {
+  int64_t tid, nthreads;
+};
+
+__device__ __forceinline__ ClusterIdx cluster_idx() {
+  cg::cluster_group cl = cg::this_cluster();
+  return {(int64_t)cl.block_rank() * blockDim.x + threadIdx.x, (int64_t)cl.num_blocks() * blockDim.x};
+}
+
+// diagonal block of every block row, and the structural symmetry of the
+// pattern: err |= 1 (no diagonal block), 2 (block (c,d) without (d,c)).
+__global__ void k_ilu_check(int32_t nb, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                            int32_t *__restrict__ dblk, int32_t *__restrict__ err) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nb) return;
+  int32_t kd = -1;
+  for (int32_t k = rowptr[c]; k < rowptr[c + 1]; k++) {
+    const int32_t d = col[k];
+    if (d == c) kd = k;
+    if (d < 0 || d >= nb) { atomicOr(err, 2); continue; }
+    int32_t lo = rowptr[d], hi = rowptr[d + 1];
+    while (lo < hi) {
+      const int32_t m = (lo + hi) >> 1;
+      if (col[m] < c) lo = m + 1; else hi = m;
+    }
+    if (lo == rowptr[d + 1] || col[lo] != c) atomicOr(err, 2);
+  }
+  dblk[c] = kd;
+  if (kd < 0) atomicOr(err, 1);
+}
+
+// Kahn's layering. cnt[t] counts the cells of level t (zeroed before the
+// launch): level t's cells are lvl_cells[b, e); a cell released while level
+// t is processed lands at e + atomicAdd(&cnt[t + 1], 1). Every thread keeps
+// b, e and t itself; all read cnt[t + 1] only after the barrier that ends
+// level t, and nothing writes it afterwards, so the loop is uniform over the
+// cluster. lvl_ptr[0..nlev] receives the level offsets. ctrl: [0] level
+// count, [1] widest level, [2] cells placed, [3] error (a cell released more
+// often than it has lower neighbours).
+__global__ void __launch_bounds__(kIluThreads, 1)
+    k_ilu_levels(int32_t nb, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                 int32_t *__restrict__ indeg, int32_t *__restrict__ cnt, int32_t *__restrict__ lvl_cells,
+                 int32_t *__restrict__ lvl_ptr, int32_t *__restrict__ nlev_d, int32_t *__restrict__ ctrl) {
+  cg::cluster_group cl = cg::this_cluster();
+  const ClusterIdx ix = cluster_idx();
+  for (int64_t c = ix.tid; c < nb; c += ix.nthreads) {
+    int32_t d = 0;
+    for (int32_t k = rowptr[c]; k < rowptr[c + 1]; k++) d += col[k] < c;
+    indeg[c] = d;
+    if (d == 0) lvl_cells[atomicAdd(&cnt[0], 1)] = (int32_t)c;
+  }
+  cl.sync();
+  int32_t b = 0, e = __ldcg(&cnt[0]), t = 0, maxw = e;
+  if (ix.tid == 0) lvl_ptr[0] = 0;
+  while (e > b && t < nb) {
+    for (int64_t q = b + ix.tid; q < e; q += ix.nthreads) {
+      const int32_t c = __ldcg(&lvl_cells[q]);
+      for (int32_t k = rowptr[c]; k < rowptr[c + 1]; k++) {
+        const int32_t d = col[k];
+        if (d <= c) continue;
+        const int32_t old = atomicSub(&indeg[d], 1);
+        if (old == 1) lvl_cells[e + atomicAdd(&cnt[t + 1], 1)] = d;
+        else if (old <= 0) atomicOr(&ctrl[3], 1);
+      }
+    }
+    cl.sync();
+    t++;
+    b = e;
+    e += __ldcg(&cnt[t]);
+    maxw = max(maxw, e - b);
+    if (ix.tid == 0) lvl_ptr[t] = b;
+  }
+  // here lvl_ptr[t] = b = e: the level offsets end with the cell count
+  if (ix.tid == 0) {
+    *nlev_d = t;
+    ctrl[0] = t;
+    ctrl[1] = maxw;
+    ctrl[2] = e;
+  }
+}
+
+// row 2c+r of cell c: position of column (2 cb + cc) in it, or -1
+__device__ __forceinline__ int32_t find_block(const int32_t *__restrict__ col, int32_t kb, int32_t ke, int32_t cb) {
+  for (int32_t k = kb; k < ke; k++) {
+    const int32_t v = col[k];
+    if (v == cb) return k;
+    if (v > cb) break;
+  }
+  return -1;
+}
+
+// Eliminate lower entry (block k, column part cc) of row 2c+r: pivot row
+// j = 2 col[k] + cc.
+__device__ __forceinline__ void ilu_eliminate(int32_t c, int r, int32_t k, int cc, const int32_t *__restrict__ rowptr,
+                                              const int32_t *__restrict__ col, const int32_t *__restrict__ dblk,
+                                              double *lu) {
+  const int32_t cp = col[k];
+  const int32_t kdp = dblk[cp];
+  const double dk = __ldcg(&lu[4 * (int64_t)kdp + 3 * cc]);
+  if (dk == 0.0) return;
+  double *q = &lu[4 * (int64_t)k + 2 * r + cc];
+  const double l = *q / dk;
+  *q = l;
+  const int32_t kb = rowptr[c], ke = rowptr[c + 1];
+  // row j right of its diagonal: the rest of its diagonal block, then the
+  // blocks after it
+  if (cc == 0) {
+    const int32_t kt = find_block(col, kb, ke, cp);
+    if (kt >= 0) lu[4 * (int64_t)kt + 2 * r + 1] -= l * __ldcg(&lu[4 * (int64_t)kdp + 1]);
+  }
+  const int32_t pe = rowptr[cp + 1];
+  int32_t kt = kb;
+  for (int32_t k2 = kdp + 1; k2 < pe; k2++) {
+    const int32_t cj = col[k2];
+    while (kt < ke && col[kt] < cj) kt++;
+    if (kt == ke) break;
+    if (col[kt] != cj) continue;
+    lu[4 * (int64_t)kt + 2 * r] -= l * __ldcg(&lu[4 * (int64_t)k2 + 2 * cc]);
+    lu[4 * (int64_t)kt + 2 * r + 1] -= l * __ldcg(&lu[4 * (int64_t)k2 + 2 * cc + 1]);
+  }
+}
+
+__global__ void __launch_bounds__(kIluThreads, 1)
+    k_ilu_factor(const int32_t *__restrict__ nlev_d, const int32_t *__restrict__ lvl_ptr,
+                 const int32_t *__restrict__ lvl_cells, const int32_t *__restrict__ rowptr,
+                 const int32_t *__restrict__ col, const int32_t *__restrict__ dblk, double *lu) {
+  cg::cluster_group cl = cg::this_cluster();
+  const ClusterIdx ix = cluster_idx();
+  const int32_t nlev = *nlev_d;
+  for (int32_t t = 0; t < nlev; t++) {
+    const int32_t b = lvl_ptr[t], e = lvl_ptr[t + 1];
+    for (int64_t q = b + ix.tid; q < e; q += ix.nthreads) {
+      const int32_t c = lvl_cells[q];
+      const int32_t kb = rowptr[c], kd = dblk[c];
+      for (int r = 0; r < 2; r++) {
+        for (int32_t k = kb; k < kd; k++) {
+          ilu_eliminate(c, r, k, 0, rowptr, col, dblk, lu);
+          ilu_eliminate(c, r, k, 1, rowptr, col, dblk, lu);
+        }
+        if (r == 1) ilu_eliminate(c, 1, kd, 0, rowptr, col, dblk, lu);
+      }
+    }
+    cl.sync();
+  }
+}
+
+// x = U^{-1} L^{-1} b: the forward sweep over the levels, then the backward
+// sweep over them in reverse.
+__global__ void __launch_bounds__(kIluThreads, 1)
+    k_ilu_solve(const int32_t *__restrict__ nlev_d, const int32_t *__restrict__ lvl_ptr,
+                const int32_t *__restrict__ lvl_cells, const int32_t *__restrict__ rowptr,
+                const int32_t *__restrict__ col, const int32_t *__restrict__ dblk, const double *__restrict__ lu,
+                const double *__restrict__ b, double *x) {
+  cg::cluster_group cl = cg::this_cluster();
+  const ClusterIdx ix = cluster_idx();
+  const int32_t nlev = *nlev_d;
+  for (int32_t t = 0; t < nlev; t++) {
+    const int32_t lb = lvl_ptr[t], le = lvl_ptr[t + 1];
+    for (int64_t q = lb + ix.tid; q < le; q += ix.nthreads) {
+      const int32_t c = lvl_cells[q];
+      const int32_t kb = rowptr[c], kd = dblk[c];
+      double s0 = b[2 * (int64_t)c];
+      for (int32_t k = kb; k < kd; k++) {
+        const int64_t j = 2 * (int64_t)col[k];
+        s0 -= lu[4 * (int64_t)k] * __ldcg(&x[j]);
+        s0 -= lu[4 * (int64_t)k + 1] * __ldcg(&x[j + 1]);
+      }
+      x[2 * (int64_t)c] = s0;
+      double s1 = b[2 * (int64_t)c + 1];
+      for (int32_t k = kb; k < kd; k++) {
+        const int64_t j = 2 * (int64_t)col[k];
+        s1 -= lu[4 * (int64_t)k + 2] * __ldcg(&x[j]);
+        s1 -= lu[4 * (int64_t)k + 3] * __ldcg(&x[j + 1]);
+      }
+      s1 -= lu[4 * (int64_t)kd + 2] * s0;
+      x[2 * (int64_t)c + 1] = s1;
+    }
+    cl.sync();
+  }
+  for (int32_t t = nlev - 1; t >= 0; t--) {
+    const int32_t lb = lvl_ptr[t], le = lvl_ptr[t + 1];
+    for (int64_t q = lb + ix.tid; q < le; q += ix.nthreads) {
+      const int32_t c = lvl_cells[q];
+      const int32_t kd = dblk[c], ke = rowptr[c + 1];
+      double s1 = __ldcg(&x[2 * (int64_t)c + 1]);
+      for (int32_t k = kd + 1; k < ke; k++) {
+        const int64_t j = 2 * (int64_t)col[k];
+        s1 -= lu[4 * (int64_t)k + 2] * __ldcg(&x[j]);
+        s1 -= lu[4 * (int64_t)k + 3] * __ldcg(&x[j + 1]);
+      }
+      const double d1 = lu[4 * (int64_t)kd + 3];
+      s1 = d1 != 0.0 ? s1 / d1 : s1;
+      x[2 * (int64_t)c + 1] = s1;
+      double s0 = __ldcg(&x[2 * (int64_t)c]);
+      s0 -= lu[4 * (int64_t)kd + 1] * s1;
+      for (int32_t k = kd + 1; k < ke; k++) {
+        const int64_t j = 2 * (int64_t)col[k];
+        s0 -= lu[4 * (int64_t)k] * __ldcg(&x[j]);
+        s0 -= lu[4 * (int64_t)k + 1] * __ldcg(&x[j + 1]);
+      }
+      const double d0 = lu[4 * (int64_t)kd];
+      x[2 * (int64_t)c] = d0 != 0.0 ? s0 / d0 : s0;
+    }
+    cl.sync();
+  }
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cluster(void (*kern)(KArgs...), int cluster, int threads, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+void ilu_free(rs_ilu0 *F) {
+  cudaStream_t s = F->stream;
+  dfree(F->lu, s);
+  dfree(F->dblk, s);
+  dfree(F->lvl_cells, s);
+  dfree(F->lvl_ptr, s);
+  dfree(F->nlev_d, s);
+  delete F;
+}
+
+}  // namespace
+
+namespace rs {
+
+int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s) {
+  *out = nullptr;
+  rs_ilu0 *F = new rs_ilu0();
+  F->nb = J.nb;
+  F->nnzb = J.nnzb;
+  F->row_ptr = J.row_ptr;
+  F->col = J.col;
+  F->stream = s;
+  const int32_t nb = J.nb;
+  if (nb == 0) { *out = F; return 0; }
+  int rc = 0;
+  Scratch sc(s);
+  int32_t *indeg = nullptr, *cnt = nullptr, *ctrl = nullptr;
+  auto attempt = [&]() -> int {
+    RS_TRY(dalloc_n(&F->lu, 4 * (size_t)J.nnzb, s));
+    RS_TRY(dalloc_n(&F->dblk, (size_t)nb, s));
+    RS_TRY(dalloc_n(&F->lvl_cells, (size_t)nb, s));
+    RS_TRY(dalloc_n(&F->lvl_ptr, (size_t)nb + 1, s));
+    RS_TRY(dalloc_n(&F->nlev_d, 1, s));
+    RS_TRY(sc.get(&indeg, (size_t)nb));
+    RS_TRY(sc.get(&cnt, (size_t)nb + 1));
+    RS_TRY(sc.get(&ctrl, 5));
+    RS_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ((size_t)nb + 1), s));
+    RS_CHECK_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(int32_t) * 5, s));
+    RS_COUNTED k_ilu_check<<<grid_for(nb), kBlock, 0, s>>>(nb, J.row_ptr, J.col, F->dblk, ctrl + 4);
+    RS_CHECK_CUDA(cudaGetLastError());
+    // the layering runs with the largest cluster: its widest level is not
+    // known yet
+    RS_CHECK_CUDA(launch_cluster(k_ilu_levels, kIluMaxCluster, kIluThreads, s, nb, J.row_ptr, J.col, indeg, cnt,
+                                 F->lvl_cells, F->lvl_ptr, F->nlev_d, ctrl));
+    int32_t h[5];
+    RS_CHECK_CUDA(cudaMemcpyAsync(h, ctrl, sizeof(h), cudaMemcpyDeviceToHost, s));
+    RS_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (h[4] & 1) return fail(RS_EINVAL, "ILU(0): a block row has no diagonal block");
+    if (h[4] & 2) return fail(RS_EINVAL, "ILU(0): the block pattern is not structurally symmetric");
+    if (h[3] || h[2] != nb) return fail(RS_ESETUP, "ILU(0): level scheduling did not place every cell once");
+    F->nlev = h[0];
+    F->maxw = h[1];
+    const int64_t per = (F->maxw + 31) / 32 * 32;
+    F->cluster = 1;
+    while (F->cluster < kIluMaxCluster && per > (int64_t)F->cluster * kIluThreads) F->cluster *= 2;
+    F->threads = (int)std::min<int64_t>(kIluThreads, std::max<int64_t>(32, per));
+    RS_CHECK_CUDA(cudaMemcpyAsync(F->lu, J.val, sizeof(double) * 4 * (size_t)J.nnzb, cudaMemcpyDeviceToDevice, s));
+    RS_CHECK_CUDA(launch_cluster(k_ilu_factor, F->cluster, F->threads, s, F->nlev_d, F->lvl_ptr, F->lvl_cells,
+                                 J.row_ptr, J.col, F->dblk, F->lu));
+    RS_CHECK_CUDA(cudaStreamSynchronize(s));
+    return 0;
+  };
+  rc = attempt();
+  if (rc) {
+    ilu_free(F);
+    return rc;
+  }
+  *out = F;
+  return 0;
+}
+
+int ilu0_solve(const rs_ilu0 *F, const double *b, double *x, cudaStream_t s) {
+  if (F->nb == 0) return 0;
+  RS_CHECK_CUDA(launch_cluster(k_ilu_solve, F->cluster, F->threads, s, F->nlev_d, F->lvl_ptr, F->lvl_cells,
+                               F->row_ptr, F->col, F->dblk, F->lu, b, x));
+  return 0;
+}
+
+void ilu0_free(rs_ilu0 *F) {
+  if (F) ilu_free(F);
+}
+
+}  // namespace rs
+
+extern "C" int ilu0_create(const rs_bsr2 *J, rs_ilu0 **out, cudaStream_t stream) {
+  if (!out) return fail(RS_EINVAL, "null output handle");
+  *out = nullptr;
+  if (!J || J->nb < 0 || J->nnzb < 0 || (J->nb > 0 && (!J->row_ptr || !J->col || !J->val)))
+    return fail(RS_EINVAL, "invalid arguments");
+  return ilu0_build(*J, out, stream);
+}
+
+extern "C" int ilu0_apply(const rs_ilu0 *F, const double *b, double *x, cudaStream_t stream) {
+  if (!F || ((!b || !x) && F->nb > 0)) return fail(RS_EINVAL, "null argument");
+  if (b == x && F->nb > 0) return fail(RS_EINVAL, "b and x must not alias");
+  return ilu0_solve(F, b, x, stream);
+}
+
+extern "C" int ilu0_info(const rs_ilu0 *F, int32_t *nlevels, int32_t *max_width, int32_t *cluster_ctas) {
+  if (!F) return fail(RS_EINVAL, "null handle");
+  if (nlevels) *nlevels = F->nlev;
+  if (max_width) *max_width = F->maxw;
+  if (cluster_ctas) *cluster_ctas = F->nb ? F->cluster : 0;
+  return RS_OK;
+}
+
+extern "C" int ilu0_factors(const rs_ilu0 *F, double *lu, cudaStream_t stream) {
+  if (!F || (!lu && F->nnzb > 0)) return fail(RS_EINVAL, "null argument");
+  if (F->nnzb > 0)
+    RS_CHECK_CUDA(cudaMemcpyAsync(lu, F->lu, sizeof(double) * 4 * (size_t)F->nnzb, cudaMemcpyDeviceToDevice, stream));
+  return RS_OK;
+}
+
+extern "C" int ilu0_destroy(rs_ilu0 *F) {
+  if (F) {
+    cudaStreamSynchronize(F->stream);
+    ilu_free(F);
+  }
+  return RS_OK;
+}

@@ -217,6 +217,11 @@ int amg_tune_smoother(Hier &H, cudaStream_t s);
 // RS_ETIMEOUT (and clears the flag) if a smoother CTA gave up waiting for its
 // staging copies since the last call; synchronises the stream.
 int vcycle_wait_status(cudaStream_t s);
+// ILU(0) of the point-ordered scalar matrix of J (rs_ilu.cu); the factors
+// keep a reference to J's pattern
+int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s);
+int ilu0_solve(const rs_ilu0 *F, const double *b, double *x, cudaStream_t s);
+void ilu0_free(rs_ilu0 *F);
 
 // ------------------------------------------------------------------ helpers
 std::vector<int32_t> seg_offsets(int32_t n, int32_t nseg, const int32_t *seg_off);

@@ -8,8 +8,9 @@
 //           (eq. SIMPLE-Schur read with A_sp).
 // CPR with decoupling W (per-cell 2x2: ABF D^{-1}, or quasi-IMPES
 // [1, -a_ps,ii/a_ss,ii; 0, 1]) runs Algorithm 1/2 on W J and W r. P1 is the
-// point-block Jacobi inverse of W J's diagonal blocks (the paper's ILU(0) is
-// sequential; this is the parallel stand-in).
+// point-block Jacobi inverse of W J's diagonal blocks (p1 = 0, the parallel
+// stand-in) or the paper's ILU(0) of the point-ordered W J (p1 = 1,
+// level-scheduled factorisation and triangular solves).
 //
 // Glue kernels work in FP64 on interleaved (P_w, S_n) vectors; the V-cycles
 // take FP64 in and out and run in the hierarchy's precision.
@@ -30,7 +31,8 @@ struct rs_precond {
   int32_t nb = 0;
   double *qw = nullptr;            // quasi-IMPES weights [nb]
   double *dinv = nullptr;          // ABF D^{-1} blocks [4 nb]
-  double *p1inv = nullptr;         // P1^{-1} blocks [4 nb]
+  double *p1inv = nullptr;         // P1^{-1} blocks [4 nb] (point-block Jacobi)
+  rs_ilu0 *ilu = nullptr;          // P1 = ILU(0) of W J
   Hier Hp, Hs, Hj;
   bool has_p = false, has_s = false, has_j = false;
   DCsr Aps;                        // BF coupling block
@@ -48,7 +50,7 @@ struct rs_precond {
 
 namespace {
 
-// rt = W r; z = P1^{-1} rt
+// rt = W r; z = P1^{-1} rt when P1 is point-block Jacobi (p1inv != NULL)
 __global__ void k_cpr_stage1(int32_t nb, int mode, const double *qw, const double *dinv, const double *p1inv,
                              const double *r, double *rt, double *z) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,6 +65,7 @@ __global__ void k_cpr_stage1(int32_t nb, int mode, const double *qw, const doubl
     t.y = d[2] * rv.x + d[3] * rv.y;
   }
   reinterpret_cast<double2 *>(rt)[i] = t;
+  if (!p1inv) return;
   const double *p = p1inv + 4 * (int64_t)i;
   reinterpret_cast<double2 *>(z)[i] = make_double2(p[0] * t.x + p[1] * t.y, p[2] * t.x + p[3] * t.y);
 }
@@ -183,8 +186,12 @@ int build(rs_precond *M, cudaStream_t s) {
       RS_TRY(decouple_abf(J, jt, M->dinv, s));
       Jt.val = jt;
     }
-    RS_TRY(dalloc_n(&M->p1inv, 4 * (size_t)nb, s));
-    RS_TRY(block_diag_inverse(Jt, M->p1inv, s));
+    if (p.p1 == RS_P1_ILU0) {
+      RS_TRY(ilu0_build(Jt, &M->ilu, s));
+    } else {
+      RS_TRY(dalloc_n(&M->p1inv, 4 * (size_t)nb, s));
+      RS_TRY(block_diag_inverse(Jt, M->p1inv, s));
+    }
     DCsr App;
     RS_TRY(bsr2_part(Jt, 0, 0, App, s));
     int r = amg_build(App, M->seg_off, p.amg, M->Hp, s);
@@ -233,6 +240,7 @@ void destroy(rs_precond *M) {
   dfree(M->qw, s);
   dfree(M->dinv, s);
   dfree(M->p1inv, s);
+  ilu0_free(M->ilu);
   dfree(M->rt, s);
   dfree(M->sb, s);
   dfree(M->ss, s);
@@ -267,6 +275,7 @@ static int apply_body(const rs_precond *M, const double *r, double *z, cudaStrea
       const int mode = M->prm.decouple;
       const bool two = M->prm.kind == RS_PC_CPR2;
       RS_COUNTED k_cpr_stage1<<<g, kBlock, 0, s>>>(nb, mode, M->qw, M->dinv, M->p1inv, r, M->rt, z);
+      if (M->ilu) RS_TRY(ilu0_solve(M->ilu, M->rt, z, s));
       {
         ProfScope ps(kProfBsr2, M->J.nnzb * 36.0 + (nb + 1) * 4.0 + nb * (16.0 + 16.0 + 16.0), s);
         // one lane per block row: on GB300 every FP64 shuffle addition costs
@@ -349,7 +358,7 @@ extern "C" int precond_create(const rs_bsr2 *J, const rs_precond_params *params,
     return fail(RS_EINVAL, "unknown preconditioner kind");
   if (params->decouple < RS_DECOUPLE_NONE || params->decouple > RS_DECOUPLE_QIMPES)
     return fail(RS_EINVAL, "unknown decoupling");
-  if (params->p1 != 0) return fail(RS_EINVAL, "only the point-block Jacobi P1 is available on the GPU");
+  if (params->p1 != RS_P1_BLOCK_JACOBI && params->p1 != RS_P1_ILU0) return fail(RS_EINVAL, "unknown P1");
   RS_TRY(check_params(params->amg));
   rs_precond *M = new rs_precond();
   M->prm = *params;

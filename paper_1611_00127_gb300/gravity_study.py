@@ -32,14 +32,17 @@ import torch
 from . import inputs as I
 from . import rsflow as R
 
-# preconditioner name -> (kind, decoupling); CPR uses the quasi-IMPES
-# decoupling, AMG is the systems (point) AMG on the whole Jacobian
+# preconditioner name -> (kind, decoupling, P1); CPR uses the quasi-IMPES
+# decoupling with P1 = ILU(0) (the paper's choice) or point-block Jacobi,
+# AMG is the systems (point) AMG on the whole Jacobian
 KINDS = {
-    "AMG": (R.AMG_J, R.DECOUPLE_NONE),
-    "CPR1": (R.CPR1, R.DECOUPLE_QIMPES),
-    "CPR2": (R.CPR2, R.DECOUPLE_QIMPES),
-    "BF": (R.BF, R.DECOUPLE_NONE),
-    "AMG_SCALAR": (R.AMG_J_SCALAR, R.DECOUPLE_NONE),
+    "AMG": (R.AMG_J, R.DECOUPLE_NONE, R.P1_BLOCK_JACOBI),
+    "CPR1": (R.CPR1, R.DECOUPLE_QIMPES, R.P1_ILU0),
+    "CPR2": (R.CPR2, R.DECOUPLE_QIMPES, R.P1_ILU0),
+    "BF": (R.BF, R.DECOUPLE_NONE, R.P1_BLOCK_JACOBI),
+    "CPR1_BJ": (R.CPR1, R.DECOUPLE_QIMPES, R.P1_BLOCK_JACOBI),
+    "CPR2_BJ": (R.CPR2, R.DECOUPLE_QIMPES, R.P1_BLOCK_JACOBI),
+    "AMG_SCALAR": (R.AMG_J_SCALAR, R.DECOUPLE_NONE, R.P1_BLOCK_JACOBI),
 }
 MESHES = (20, 40, 80, 160)
 MAX_DS = 0.2
@@ -47,10 +50,10 @@ MAX_DS = 0.2
 
 def newton_params(kind: str, precision: int = R.FP64, rtol: float = 1e-8, max_newton: int = 40,
                   max_ds: float = MAX_DS) -> R.NewtonParams:
-    k, dec = KINDS[kind]
+    k, dec, p1 = KINDS[kind]
     return R.NewtonParams(max_newton=max_newton, ftol=1e-6, max_ds=max_ds,
                           gmres=R.GmresParams(m=30, maxit=1000, rtol=rtol),
-                          prec=R.PrecParams(kind=k, decouple=dec, amg=R.AmgParams(precision=precision)))
+                          prec=R.PrecParams(kind=k, decouple=dec, p1=p1, amg=R.AmgParams(precision=precision)))
 
 
 def run_case(n: int, example: int, kind: str, pc_model: int = I.PC_BROOKS_COREY, precision: int = R.FP64,

@@ -20,6 +20,7 @@ from . import build as _build
 RS_OK, RS_NOT_CONVERGED = 0, 1
 AMG_J, CPR1, CPR2, BF, AMG_J_SCALAR = 0, 1, 2, 3, 4
 DECOUPLE_NONE, DECOUPLE_ABF, DECOUPLE_QIMPES = 0, 1, 2
+P1_BLOCK_JACOBI, P1_ILU0 = 0, 1
 FP32, FP64 = 0, 1
 
 _lib = None
@@ -115,6 +116,11 @@ def _declare(L):
         "amg_level_copy": (C.c_int, [P, i32, P, P, P, P, P, P, P, P, P]),
         "amg_level_smooth": (C.c_int, [P, i32, i32, P, P]),
         "amg_level_transfer": (C.c_int, [P, i32, i32, i32, P, P]),
+        "ilu0_create": (C.c_int, [P, P, P]),
+        "ilu0_apply": (C.c_int, [P, P, P, P]),
+        "ilu0_info": (C.c_int, [P, P, P, P]),
+        "ilu0_factors": (C.c_int, [P, P, P]),
+        "ilu0_destroy": (C.c_int, [P]),
         "precond_create": (C.c_int, [P, P, P, P]),
         "precond_destroy": (C.c_int, [P]),
         "precond_apply": (C.c_int, [P, P, P, P]),
@@ -431,6 +437,41 @@ class Precond:
     def amg(self, which: int) -> Optional[Amg]:
         h = lib().precond_amg(self.h, which)
         return Amg(C.c_void_p(h), owner=self, own=False) if h else None
+
+
+class Ilu0:
+    """ILU(0) of the point-ordered scalar matrix of J (P1 of CPR)."""
+
+    def __init__(self, J: Bsr2, stream=None):
+        self.J = J
+        self._Jc = J.c()
+        self.h = C.c_void_p()
+        _check(lib().ilu0_create(C.byref(self._Jc), C.byref(self.h), _stream(stream)), "ilu0_create")
+
+    def apply(self, b: torch.Tensor, x: torch.Tensor, stream=None):
+        _check(lib().ilu0_apply(self.h, _ptr(b), _ptr(x), _stream(stream)), "ilu0_apply")
+
+    def info(self):
+        """(levels, widest level, CTAs per cluster)"""
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().ilu0_info(self.h, C.byref(a), C.byref(b), C.byref(c)), "ilu0_info")
+        return a.value, b.value, c.value
+
+    def factors(self, stream=None) -> torch.Tensor:
+        lu = torch.empty_like(self.J.val)
+        _check(lib().ilu0_factors(self.h, _ptr(lu), _stream(stream)), "ilu0_factors")
+        return lu
+
+    def close(self):
+        if self.h:
+            lib().ilu0_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gmres_solve(J: Bsr2, M: Optional[Precond], b: torch.Tensor, x: torch.Tensor,

@@ -1,6 +1,7 @@
 """The gravity-driven two-dimensional study (Sec. 4.2) on the GPU.
 
-* 20^2 and 40^2, Ex 1..3, every preconditioner that converges there: the GPU
+* 20^2 and 40^2, Ex 1..3, every preconditioner that converges there (CPR
+  with the paper's ILU(0) first stage and with point-block Jacobi): the GPU
   time stepping (Newton with the Appleyard chop, FGMRES, FP64 V-cycles)
   takes the oracle's Newton iteration counts (within one per step), linear
   counts within 10 % per step, and ends at the oracle's state within the
@@ -35,24 +36,27 @@ def G(R):
     return gravity_study
 
 
-ORACLE_KIND = {"AMG": (0, 0), "CPR1": (1, 2), "CPR2": (2, 2), "BF": (3, 0)}
+# study name -> oracle (kind, decoupling, P1)
+ORACLE_KIND = {"AMG": (0, 0, 0), "CPR1": (1, 2, 1), "CPR2": (2, 2, 1), "BF": (3, 0, 0),
+               "CPR1_BJ": (1, 2, 0), "CPR2_BJ": (2, 2, 0)}
 
 
 def _oracle_run(oracle, inputs, n, ex, kind):
     p = inputs.config_gravity_2d(n, ex)
     dt = inputs.GRAVITY_DT_DAYS[ex] * inputs.DAY
-    k, dec = ORACLE_KIND[kind]
+    k, dec, p1 = ORACLE_KIND[kind]
     u = inputs.uniform_state(p)
     steps = []
     for _ in range(inputs.GRAVITY_STEPS):
         u, st, ni, li, _ = oracle.newton(p, u, u, dt, oracle.NewtonParams(
-            max_newton=40, max_ds=0.2, prec=oracle.PrecParams(kind=k, decouple=dec)))
+            max_newton=40, max_ds=0.2, prec=oracle.PrecParams(kind=k, decouple=dec, p1=p1)))
         assert st == 0
         steps.append((ni, li, u.copy()))
     return steps
 
 
-@pytest.mark.parametrize("n,kinds", [(20, ("AMG", "CPR1", "CPR2", "BF")), (40, ("AMG", "CPR2", "BF"))])
+@pytest.mark.parametrize("n,kinds", [(20, ("AMG", "CPR1", "CPR2", "BF", "CPR1_BJ", "CPR2_BJ")),
+                                     (40, ("AMG", "CPR1", "CPR2", "BF", "CPR2_BJ"))])
 @pytest.mark.parametrize("ex", [1, 2, 3])
 def test_gravity_time_steps_match_oracle(R, G, oracle, inputs, n, kinds, ex):
     for kind in kinds:

@@ -176,3 +176,56 @@ def test_newton_converges_quadratically_on_small_grid(oracle, inputs):
     assert any(r > 1.6 for r in ratios), hist
     F, _, _ = oracle.assemble(p, u, u0, inputs.DAY, jacobian=False)
     assert oracle.scaled_fnorm(p, F, inputs.DAY) <= 1e-6
+
+
+def _lu_parts(oracle, rp, col, lu):
+    M = sp.csr_matrix(oracle.bsr2_to_scipy(rp, col, lu))
+    L = sp.tril(M, -1, format="csr") + sp.eye(M.shape[0], format="csr")
+    U = sp.triu(M, 0, format="csr")
+    return L, U
+
+
+@pytest.mark.parametrize("decouple", [0, 2])
+def test_ilu0_factors_match_matrix_on_its_pattern(oracle, inputs, decouple):
+    """The defining property of ILU(0) (Saad, Iterative Methods, Sec. 10.3):
+    L unit lower and U upper on the pattern of A, with (L U)_ij = a_ij for
+    every (i, j) in the pattern. On a 2D gravity Jacobian (raw and
+    quasi-IMPES decoupled) fill outside the pattern is dropped, so L U
+    differs from A there."""
+    p = inputs.config_gravity_2d(10, 2)
+    u = inputs.uniform_state(p)
+    u = inputs.jitter(u, 4, dp=1e4, ds=0.05)
+    F, J, (rp, col) = oracle.assemble(p, u, inputs.uniform_state(p), 4 * inputs.DAY)
+    if decouple == 2:
+        # quasi-IMPES: pressure row += w * oil row, w = -a_ps,ii / a_ss,ii
+        d = J[np.flatnonzero(col == np.repeat(np.arange(rp.size - 1), np.diff(rp)))]
+        w = -d[:, 0, 1] / d[:, 1, 1]
+        Jt = J.copy()
+        Jt[:, 0, :] += np.repeat(w, np.diff(rp))[:, None] * J[:, 1, :]
+        J = Jt
+    A = sp.csr_matrix(oracle.bsr2_to_scipy(rp, col, J))
+    lu = oracle.ilu0(rp, col, J)
+    L, U = _lu_parts(oracle, rp, col, lu)
+    P = (abs(sp.csr_matrix(oracle.bsr2_to_scipy(rp, col, np.ones_like(J)))) > 0).toarray()
+    LU = (L @ U).toarray()
+    Ad = A.toarray()
+    scale = np.abs(Ad).max(axis=1, keepdims=True)
+    assert np.abs((LU - Ad) * P / scale).max() < 1e-12
+    assert np.abs((LU - Ad) * ~P / scale).max() > 1e-6      # dropped fill
+    b = inputs.rhs_vector(A.shape[0], 8)
+    x = oracle.ilu0_solve(rp, col, lu, b)
+    xe = sp.linalg.spsolve_triangular(U, sp.linalg.spsolve_triangular(L, b, lower=True), lower=False)
+    np.testing.assert_allclose(x, xe, rtol=1e-10, atol=1e-12 * np.abs(xe).max())
+
+
+def test_ilu0_is_exact_lu_on_a_strip(oracle, inputs):
+    """A one-row strip has a block-tridiagonal Jacobian: its LU makes no fill
+    outside the pattern, so ILU(0) is the exact LU and the solve is A^{-1}."""
+    p = inputs.homogeneous(40, 1).with_(pc_model=2, pc_pd=5e3)
+    u, uo = inputs.front_state(p)
+    F, J, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
+    lu = oracle.ilu0(rp, col, J)
+    A = oracle.bsr2_to_scipy(rp, col, J).toarray()
+    b = inputs.rhs_vector(A.shape[0], 9)
+    np.testing.assert_allclose(oracle.ilu0_solve(rp, col, lu, b), np.linalg.solve(A, b), rtol=1e-9,
+                               atol=1e-12 * np.abs(np.linalg.solve(A, b)).max())
