@@ -234,6 +234,35 @@ def config_gravity_2d(n: int, example: int = 1, pc_model: int = PC_BROOKS_COREY)
                    name=f"2d_gravity_{n}x{n}_ex{example}_{'bc' if pc_model == PC_BROOKS_COREY else 'lin'}")
 
 
+def config_oil_water_2d(example: int = 1, pc_model: int = PC_LINEAR, nx: int = 100, nz: int = 20,
+                        sigma: float = 2.0, ell=(2.0, 16.0)) -> Problem:
+    """The two-dimensional oil-water example of Sec. 4.1: a 762 m x 15.24 m
+    vertical section (depth = the second coordinate) on a 100 x 20 mesh, the
+    geometry of the SPE10 model-1 section, whose single cell layer across is
+    7.62 m thick; the model's unit thickness carries the 50 m^3/day injected
+    into the lower-left cell as 50 / 7.62 m^3/day per metre of thickness,
+    outlet (p_w = 0, S_w = 0.2) on the x = L face of the top-right cell, no
+    gravity, fluids and porosity of the table of input data, capillary
+    parameter set `example`. The SPE10 permeability is not available; a
+    seeded log-normal stand-in with sample std `sigma` of ln k, correlation
+    lengths `ell` = (vertical, horizontal) in cells (layered, like the SPE10
+    sections) and geometric mean 100 mD takes its place."""
+    rng = _rng(6, nx, nz)
+    lnk = lognormal_field((nz, nx), sigma, ell, np.log(100.0 * MILLIDARCY), rng)
+    k = np.exp(lnk).reshape(-1)
+    p0, pd, lam = PC_EXAMPLES[example]
+    return Problem(dim=2, nx=nx, ny=nz, nz=1, kx=k, ky=k.copy(), kz=k.copy(), hx=762.0 / nx, hy=15.24 / nz,
+                   hz=1.0, phi=0.2, mu_w=1e-3, mu_n=1e-2, rho_w=1000.0, rho_n=700.0, g=0.0,
+                   pc_model=pc_model, pc_p0=p0, pc_pd=pd, bc_lambda=lam, s_wr=0.0, s_nr=0.0,
+                   u_in=0.0, p_out=0.0, sn_out=0.8, q_in=50.0 / 7.62 / DAY, well_in=(nz - 1) * nx, well_out=nx - 1,
+                   name=f"2d_oil_water_{nx}x{nz}_ex{example}_{'bc' if pc_model == PC_BROOKS_COREY else 'lin'}")
+
+
+# the oil-water example runs 200 days in steps of 20 days
+OIL_WATER_DT_DAYS = 20.0
+OIL_WATER_STEPS = 10
+
+
 def uniform_state(p: Problem, p_w: float = 1e5, s_n: float = 0.8) -> np.ndarray:
     """Uniform initial state (the oil-water examples of Sec. 4: p_w = 1e5 Pa,
     S_n = 0.8)."""

@@ -32,8 +32,8 @@ def R():
 
 @pytest.fixture(scope="module")
 def G(R):
-    from paper_1611_00127_gb300 import gravity_study
-    return gravity_study
+    from paper_1611_00127_gb300 import studies
+    return studies
 
 
 # study name -> oracle (kind, decoupling, P1)

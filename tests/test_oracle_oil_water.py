@@ -1,0 +1,59 @@
+"""Pins of the oil-water study (Sec. 4.1, Tables performance_q5_1..q5_3) on
+the oracle: the configuration the section states, the properties of the
+seeded stand-in for its SPE10 permeability, and a converged 200-day run."""
+import numpy as np
+import pytest
+
+
+def test_oil_water_configuration(inputs):
+    for ex, (p0, pd, lam) in ((1, (1e5, 1e6, 2.5)), (2, (1e4, 1e5, 0.8)), (3, (1e3, 2e4, 2.5)), (4, (1e6, 1e6, 0.8))):
+        for model in (inputs.PC_LINEAR, inputs.PC_BROOKS_COREY):
+            p = inputs.config_oil_water_2d(ex, model)
+            assert (p.nx, p.ny, p.nz, p.dim) == (100, 20, 1, 2)
+            assert p.nx * p.hx == pytest.approx(762.0) and p.ny * p.hy == pytest.approx(15.24)
+            assert p.pc_model == model and (p.pc_p0, p.pc_pd, p.bc_lambda) == (p0, pd, lam)
+            # 50 m^3/day over the 7.62 m thickness of the section, per metre
+            assert p.q_in * inputs.DAY * 7.62 == pytest.approx(50.0)
+            assert p.well_in == 19 * 100 and p.well_out == 99        # lower left, top right
+            assert (p.p_out, p.sn_out) == (0.0, 0.8)                 # P_w = 0, S_w = 0.2 at the outlet
+            assert (p.rho_w, p.rho_n, p.mu_w, p.mu_n, p.phi, p.s_wr, p.g) == (1000.0, 700.0, 1e-3, 1e-2, 0.2, 0.0, 0.0)
+    assert inputs.OIL_WATER_DT_DAYS * inputs.OIL_WATER_STEPS == 200.0 and inputs.OIL_WATER_DT_DAYS == 20.0
+
+
+def test_permeability_stand_in(inputs):
+    """Seeded and deterministic; ln k has sample std 2 and the geometric
+    mean of 100 mD; layered: neighbours along x are far more alike than
+    neighbours along the depth."""
+    a = inputs.config_oil_water_2d(1).kx
+    b = inputs.config_oil_water_2d(3, inputs.PC_BROOKS_COREY).kx
+    np.testing.assert_array_equal(a, b)
+    lnk = np.log(a).reshape(20, 100)
+    assert np.std(lnk) == pytest.approx(2.0, rel=1e-12)
+    assert np.exp(lnk.mean()) == pytest.approx(100 * 9.869233e-16, rel=1e-12)
+    z = lnk - lnk.mean()
+    cx = (z[:, 1:] * z[:, :-1]).mean() / z.var()
+    cz = (z[1:, :] * z[:-1, :]).mean() / z.var()
+    assert cx > 0.95 and cx > cz
+
+
+def test_oil_water_run_converges_and_moves_water(oracle, inputs):
+    """CPR-AMG(1) with ILU(0) on the linear Ex 3 case: every one of the ten
+    20-day steps converges; the injector cell is swept, and the water gained
+    in place is positive and at most the volume injected (the rest left
+    through the outlet; both phases are incompressible)."""
+    p = inputs.config_oil_water_2d(3, inputs.PC_LINEAR)
+    u = inputs.uniform_state(p)
+    dt = inputs.OIL_WATER_DT_DAYS * inputs.DAY
+    NI = 0
+    for _ in range(inputs.OIL_WATER_STEPS):
+        u, st, ni, li, _ = oracle.newton(p, u, u, dt, oracle.NewtonParams(
+            max_newton=40, max_ds=0.2, prec=oracle.PrecParams(kind=1, decouple=2, p1=1)))
+        assert st == 0
+        NI += ni
+    assert NI <= 60
+    sn = u[1::2]
+    assert sn[p.well_in] < 0.3
+    V = p.hx * p.hy * 1.0
+    gained = (p.phi * V * (0.8 - sn)).sum()
+    injected = p.q_in * dt * inputs.OIL_WATER_STEPS
+    assert 0.3 * injected < gained <= injected * (1 + 1e-6)
