@@ -18,8 +18,9 @@
 // sits one level above its highest lower neighbour); cells of one level are
 // independent. Each phase -- layering, factorisation, forward + backward
 // solve -- is one launch of a single thread-block cluster (1..8 CTAs of up to
-// 1024 threads, sized to the widest level) that walks the levels with a
-// cluster barrier between them (hardware barrier; no spin loop). One thread
+// 1024 threads for the set-up and 512 for the solve, sized to the widest
+// level) that walks the levels with a cluster barrier between them (hardware
+// barrier; no spin loop). One thread
 // handles both rows of a cell in the sequential algorithm's operation order,
 // and this file is compiled without FMA contraction, so factors and solves
 // round exactly as the sequential algorithm does. Values that other threads
@@ -45,14 +46,17 @@ struct rs_ilu0 {
   int32_t *lvl_cells = nullptr;    // cells ordered by level [nb]
   int32_t *lvl_ptr = nullptr;      // level offsets [nb + 1]
   int32_t *nlev_d = nullptr;       // level count on the device [1]
+  int4 *rec = nullptr;             // level-ordered solve records [3 nb]
   int32_t nlev = 0, maxw = 0;
-  int cluster = 1, threads = 32;
+  int cluster = 1, threads = 32;   // factorisation launch
+  int cluster_s = 1, threads_s = 32;   // solve launch
   cudaStream_t stream = nullptr;
 };
 
 namespace {
 
-constexpr int kIluThreads = 1024;
+constexpr int kIluThreads = 1024;       // layering and factorisation
+constexpr int kIluSolveThreads = 512;   // triangular solves (room for the prefetched records)
 constexpr int kIluMaxCluster = 8;
 
 struct ClusterIdx {
@@ -201,62 +205,192 @@ __global__ void __launch_bounds__(kIluThreads, 1)
   }
 }
 
+// Level-ordered record of the cell at position q: {c, first block, diagonal
+// block, end of row} and the columns of its first four lower and first four
+// upper neighbour blocks (-1 past them). A solve thread reads one record
+// (three int4) per cell, prefetched before the barrier that precedes the
+// cell's level, so that after the barrier only the neighbours' x values
+// (and the factor entries) are on the critical path.
+__global__ void k_ilu_records(int32_t nb, const int32_t *__restrict__ lvl_cells, const int32_t *__restrict__ rowptr,
+                              const int32_t *__restrict__ col, const int32_t *__restrict__ dblk,
+                              int4 *__restrict__ rec) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nb) return;
+  const int32_t c = lvl_cells[q], kb = rowptr[c], kd = dblk[c], ke = rowptr[c + 1];
+  int32_t lo[4], up[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    lo[i] = kb + i < kd ? col[kb + i] : -1;
+    up[i] = kd + 1 + i < ke ? col[kd + 1 + i] : -1;
+  }
+  rec[3 * q] = make_int4(c, kb, kd, ke);
+  rec[3 * q + 1] = make_int4(lo[0], lo[1], lo[2], lo[3]);
+  rec[3 * q + 2] = make_int4(up[0], up[1], up[2], up[3]);
+}
+
+__device__ __forceinline__ int32_t pick(const int4 v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// forward rows 2c, 2c+1 of one cell (L y = b, unit diagonal); b0, b1 = b
+__device__ __forceinline__ void ilu_forward_cell(const int4 a, const int4 lo, double b0, double b1,
+                                                 const int32_t *__restrict__ col, const double *__restrict__ lu,
+                                                 double *x) {
+  const int32_t c = a.x, kb = a.y, kd = a.z;
+  const int32_t nl = kd - kb;
+  double xa[4], xb[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    if (i < nl) {
+      const int64_t j = 2 * (int64_t)pick(lo, i);
+      xa[i] = __ldcg(&x[j]);
+      xb[i] = __ldcg(&x[j + 1]);
+    }
+  }
+  double s0 = b0;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    if (i < nl) {
+      const int64_t k = kb + i;
+      s0 -= lu[4 * k] * xa[i];
+      s0 -= lu[4 * k + 1] * xb[i];
+    }
+  }
+  for (int32_t k = kb + 4; k < kd; k++) {
+    const int64_t j = 2 * (int64_t)col[k];
+    s0 -= lu[4 * (int64_t)k] * __ldcg(&x[j]);
+    s0 -= lu[4 * (int64_t)k + 1] * __ldcg(&x[j + 1]);
+  }
+  x[2 * (int64_t)c] = s0;
+  double s1 = b1;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    if (i < nl) {
+      const int64_t k = kb + i;
+      s1 -= lu[4 * k + 2] * xa[i];
+      s1 -= lu[4 * k + 3] * xb[i];
+    }
+  }
+  for (int32_t k = kb + 4; k < kd; k++) {
+    const int64_t j = 2 * (int64_t)col[k];
+    s1 -= lu[4 * (int64_t)k + 2] * __ldcg(&x[j]);
+    s1 -= lu[4 * (int64_t)k + 3] * __ldcg(&x[j + 1]);
+  }
+  s1 -= lu[4 * (int64_t)kd + 2] * s0;
+  x[2 * (int64_t)c + 1] = s1;
+}
+
+// backward rows 2c+1, then 2c of one cell (U x = y); y0, y1 = the cell's y
+__device__ __forceinline__ void ilu_backward_cell(const int4 a, const int4 up, double y0, double y1,
+                                                  const int32_t *__restrict__ col, const double *__restrict__ lu,
+                                                  double *x) {
+  const int32_t c = a.x, kd = a.z, ke = a.w;
+  const int32_t nu = ke - kd - 1;
+  double xa[4], xb[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    if (i < nu) {
+      const int64_t j = 2 * (int64_t)pick(up, i);
+      xa[i] = __ldcg(&x[j]);
+      xb[i] = __ldcg(&x[j + 1]);
+    }
+  }
+  double s1 = y1;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    if (i < nu) {
+      const int64_t k = kd + 1 + i;
+      s1 -= lu[4 * k + 2] * xa[i];
+      s1 -= lu[4 * k + 3] * xb[i];
+    }
+  }
+  for (int32_t k = kd + 5; k < ke; k++) {
+    const int64_t j = 2 * (int64_t)col[k];
+    s1 -= lu[4 * (int64_t)k + 2] * __ldcg(&x[j]);
+    s1 -= lu[4 * (int64_t)k + 3] * __ldcg(&x[j + 1]);
+  }
+  const double d1 = lu[4 * (int64_t)kd + 3];
+  s1 = d1 != 0.0 ? s1 / d1 : s1;
+  x[2 * (int64_t)c + 1] = s1;
+  double s0 = y0;
+  s0 -= lu[4 * (int64_t)kd + 1] * s1;
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    if (i < nu) {
+      const int64_t k = kd + 1 + i;
+      s0 -= lu[4 * k] * xa[i];
+      s0 -= lu[4 * k + 1] * xb[i];
+    }
+  }
+  for (int32_t k = kd + 5; k < ke; k++) {
+    const int64_t j = 2 * (int64_t)col[k];
+    s0 -= lu[4 * (int64_t)k] * __ldcg(&x[j]);
+    s0 -= lu[4 * (int64_t)k + 1] * __ldcg(&x[j + 1]);
+  }
+  const double d0 = lu[4 * (int64_t)kd];
+  x[2 * (int64_t)c] = d0 != 0.0 ? s0 / d0 : s0;
+}
+
 // x = U^{-1} L^{-1} b: the forward sweep over the levels, then the backward
-// sweep over them in reverse.
-__global__ void __launch_bounds__(kIluThreads, 1)
+// sweep over them in reverse. Position q of level t goes to thread
+// q - lvl_ptr[t] (then + nthreads, ...), in both sweeps.
+__global__ void __launch_bounds__(kIluSolveThreads, 1)
     k_ilu_solve(const int32_t *__restrict__ nlev_d, const int32_t *__restrict__ lvl_ptr,
-                const int32_t *__restrict__ lvl_cells, const int32_t *__restrict__ rowptr,
-                const int32_t *__restrict__ col, const int32_t *__restrict__ dblk, const double *__restrict__ lu,
+                const int4 *__restrict__ rec, const int32_t *__restrict__ col, const double *__restrict__ lu,
                 const double *__restrict__ b, double *x) {
   cg::cluster_group cl = cg::this_cluster();
   const ClusterIdx ix = cluster_idx();
   const int32_t nlev = *nlev_d;
+  int4 ra = make_int4(0, 0, 0, 0), rl = ra, ru = ra;
+  double p0 = 0.0, p1 = 0.0;
+  auto fetch = [&](int64_t q) {
+    ra = rec[3 * q];
+    rl = rec[3 * q + 1];
+    ru = rec[3 * q + 2];
+  };
+  if (nlev > 0 && lvl_ptr[0] + ix.tid < lvl_ptr[1]) {
+    fetch(lvl_ptr[0] + ix.tid);
+    p0 = b[2 * (int64_t)ra.x];
+    p1 = b[2 * (int64_t)ra.x + 1];
+  }
   for (int32_t t = 0; t < nlev; t++) {
     const int32_t lb = lvl_ptr[t], le = lvl_ptr[t + 1];
     for (int64_t q = lb + ix.tid; q < le; q += ix.nthreads) {
-      const int32_t c = lvl_cells[q];
-      const int32_t kb = rowptr[c], kd = dblk[c];
-      double s0 = b[2 * (int64_t)c];
-      for (int32_t k = kb; k < kd; k++) {
-        const int64_t j = 2 * (int64_t)col[k];
-        s0 -= lu[4 * (int64_t)k] * __ldcg(&x[j]);
-        s0 -= lu[4 * (int64_t)k + 1] * __ldcg(&x[j + 1]);
+      if (q != lb + ix.tid) {
+        fetch(q);
+        p0 = b[2 * (int64_t)ra.x];
+        p1 = b[2 * (int64_t)ra.x + 1];
       }
-      x[2 * (int64_t)c] = s0;
-      double s1 = b[2 * (int64_t)c + 1];
-      for (int32_t k = kb; k < kd; k++) {
-        const int64_t j = 2 * (int64_t)col[k];
-        s1 -= lu[4 * (int64_t)k + 2] * __ldcg(&x[j]);
-        s1 -= lu[4 * (int64_t)k + 3] * __ldcg(&x[j + 1]);
-      }
-      s1 -= lu[4 * (int64_t)kd + 2] * s0;
-      x[2 * (int64_t)c + 1] = s1;
+      ilu_forward_cell(ra, rl, p0, p1, col, lu, x);
+    }
+    if (t + 1 < nlev && le + ix.tid < lvl_ptr[t + 2]) {    // next level's first cell
+      fetch(le + ix.tid);
+      p0 = b[2 * (int64_t)ra.x];
+      p1 = b[2 * (int64_t)ra.x + 1];
     }
     cl.sync();
+  }
+  if (nlev > 0 && lvl_ptr[nlev - 1] + ix.tid < lvl_ptr[nlev]) {
+    fetch(lvl_ptr[nlev - 1] + ix.tid);
+    p0 = __ldcg(&x[2 * (int64_t)ra.x]);
+    p1 = __ldcg(&x[2 * (int64_t)ra.x + 1]);
   }
   for (int32_t t = nlev - 1; t >= 0; t--) {
     const int32_t lb = lvl_ptr[t], le = lvl_ptr[t + 1];
     for (int64_t q = lb + ix.tid; q < le; q += ix.nthreads) {
-      const int32_t c = lvl_cells[q];
-      const int32_t kd = dblk[c], ke = rowptr[c + 1];
-      double s1 = __ldcg(&x[2 * (int64_t)c + 1]);
-      for (int32_t k = kd + 1; k < ke; k++) {
-        const int64_t j = 2 * (int64_t)col[k];
-        s1 -= lu[4 * (int64_t)k + 2] * __ldcg(&x[j]);
-        s1 -= lu[4 * (int64_t)k + 3] * __ldcg(&x[j + 1]);
+      if (q != lb + ix.tid) {
+        fetch(q);
+        p0 = __ldcg(&x[2 * (int64_t)ra.x]);
+        p1 = __ldcg(&x[2 * (int64_t)ra.x + 1]);
       }
-      const double d1 = lu[4 * (int64_t)kd + 3];
-      s1 = d1 != 0.0 ? s1 / d1 : s1;
-      x[2 * (int64_t)c + 1] = s1;
-      double s0 = __ldcg(&x[2 * (int64_t)c]);
-      s0 -= lu[4 * (int64_t)kd + 1] * s1;
-      for (int32_t k = kd + 1; k < ke; k++) {
-        const int64_t j = 2 * (int64_t)col[k];
-        s0 -= lu[4 * (int64_t)k] * __ldcg(&x[j]);
-        s0 -= lu[4 * (int64_t)k + 1] * __ldcg(&x[j + 1]);
-      }
-      const double d0 = lu[4 * (int64_t)kd];
-      x[2 * (int64_t)c] = d0 != 0.0 ? s0 / d0 : s0;
+      ilu_backward_cell(ra, ru, p0, p1, col, lu, x);
+    }
+    // the previous level's first cell: its y values are final since the
+    // forward sweep, and no thread writes them before its own turn
+    if (t > 0 && lvl_ptr[t - 1] + ix.tid < lb) {
+      fetch(lvl_ptr[t - 1] + ix.tid);
+      p0 = __ldcg(&x[2 * (int64_t)ra.x]);
+      p1 = __ldcg(&x[2 * (int64_t)ra.x + 1]);
     }
     cl.sync();
   }
@@ -287,6 +421,7 @@ void ilu_free(rs_ilu0 *F) {
   dfree(F->lvl_cells, s);
   dfree(F->lvl_ptr, s);
   dfree(F->nlev_d, s);
+  dfree(F->rec, s);
   delete F;
 }
 
@@ -313,6 +448,7 @@ int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s) {
     RS_TRY(dalloc_n(&F->lvl_cells, (size_t)nb, s));
     RS_TRY(dalloc_n(&F->lvl_ptr, (size_t)nb + 1, s));
     RS_TRY(dalloc_n(&F->nlev_d, 1, s));
+    RS_TRY(dalloc_n(&F->rec, 3 * (size_t)nb, s));
     RS_TRY(sc.get(&indeg, (size_t)nb));
     RS_TRY(sc.get(&cnt, (size_t)nb + 1));
     RS_TRY(sc.get(&ctrl, 5));
@@ -336,6 +472,11 @@ int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s) {
     F->cluster = 1;
     while (F->cluster < kIluMaxCluster && per > (int64_t)F->cluster * kIluThreads) F->cluster *= 2;
     F->threads = (int)std::min<int64_t>(kIluThreads, std::max<int64_t>(32, per));
+    F->cluster_s = 1;
+    while (F->cluster_s < kIluMaxCluster && per > (int64_t)F->cluster_s * kIluSolveThreads) F->cluster_s *= 2;
+    F->threads_s = (int)std::min<int64_t>(kIluSolveThreads, std::max<int64_t>(32, per));
+    RS_COUNTED k_ilu_records<<<grid_for(nb), kBlock, 0, s>>>(nb, F->lvl_cells, J.row_ptr, J.col, F->dblk, F->rec);
+    RS_CHECK_CUDA(cudaGetLastError());
     RS_CHECK_CUDA(cudaMemcpyAsync(F->lu, J.val, sizeof(double) * 4 * (size_t)J.nnzb, cudaMemcpyDeviceToDevice, s));
     RS_CHECK_CUDA(launch_cluster(k_ilu_factor, F->cluster, F->threads, s, F->nlev_d, F->lvl_ptr, F->lvl_cells,
                                  J.row_ptr, J.col, F->dblk, F->lu));
@@ -353,8 +494,8 @@ int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s) {
 
 int ilu0_solve(const rs_ilu0 *F, const double *b, double *x, cudaStream_t s) {
   if (F->nb == 0) return 0;
-  RS_CHECK_CUDA(launch_cluster(k_ilu_solve, F->cluster, F->threads, s, F->nlev_d, F->lvl_ptr, F->lvl_cells,
-                               F->row_ptr, F->col, F->dblk, F->lu, b, x));
+  RS_CHECK_CUDA(launch_cluster(k_ilu_solve, F->cluster_s, F->threads_s, s, F->nlev_d, F->lvl_ptr, F->rec, F->col,
+                               F->lu, b, x));
   return 0;
 }
 
