@@ -24,8 +24,10 @@
 // handles both rows of a cell in the sequential algorithm's operation order,
 // and this file is compiled without FMA contraction, so factors and solves
 // round exactly as the sequential algorithm does. Values that other threads
-// wrote earlier in the same launch are read with ld.global.cg (L2), so no
-// stale L1 line is ever used.
+// wrote earlier in the same launch are read with ld.global.cg (L2) when the
+// cluster has several CTAs, so no stale L1 line is ever used; a single-CTA
+// solve separates its levels by __syncthreads, which makes them visible to
+// plain loads.
 //
 // The block pattern must be structurally symmetric (TPFA Jacobians are): the
 // layering releases a cell's upper neighbours from its own row and the
@@ -232,7 +234,23 @@ __device__ __forceinline__ int32_t pick(const int4 v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
+// a value another thread of the launch wrote before the last barrier: within
+// one CTA the barrier makes it visible to a plain (L1) load; across the CTAs
+// of a cluster it is read from L2
+template <bool ONE>
+__device__ __forceinline__ double ld_shared_state(const double *p) {
+  if constexpr (ONE) return *p;
+  else return __ldcg(p);
+}
+
+template <bool ONE>
+__device__ __forceinline__ void level_barrier() {
+  if constexpr (ONE) __syncthreads();
+  else cg::this_cluster().sync();
+}
+
 // forward rows 2c, 2c+1 of one cell (L y = b, unit diagonal); b0, b1 = b
+template <bool ONE>
 __device__ __forceinline__ void ilu_forward_cell(const int4 a, const int4 lo, double b0, double b1,
                                                  const int32_t *__restrict__ col, const double *__restrict__ lu,
                                                  double *x) {
@@ -243,8 +261,8 @@ __device__ __forceinline__ void ilu_forward_cell(const int4 a, const int4 lo, do
   for (int i = 0; i < 4; i++) {
     if (i < nl) {
       const int64_t j = 2 * (int64_t)pick(lo, i);
-      xa[i] = __ldcg(&x[j]);
-      xb[i] = __ldcg(&x[j + 1]);
+      xa[i] = ld_shared_state<ONE>(&x[j]);
+      xb[i] = ld_shared_state<ONE>(&x[j + 1]);
     }
   }
   double s0 = b0;
@@ -258,8 +276,8 @@ __device__ __forceinline__ void ilu_forward_cell(const int4 a, const int4 lo, do
   }
   for (int32_t k = kb + 4; k < kd; k++) {
     const int64_t j = 2 * (int64_t)col[k];
-    s0 -= lu[4 * (int64_t)k] * __ldcg(&x[j]);
-    s0 -= lu[4 * (int64_t)k + 1] * __ldcg(&x[j + 1]);
+    s0 -= lu[4 * (int64_t)k] * ld_shared_state<ONE>(&x[j]);
+    s0 -= lu[4 * (int64_t)k + 1] * ld_shared_state<ONE>(&x[j + 1]);
   }
   x[2 * (int64_t)c] = s0;
   double s1 = b1;
@@ -273,14 +291,15 @@ __device__ __forceinline__ void ilu_forward_cell(const int4 a, const int4 lo, do
   }
   for (int32_t k = kb + 4; k < kd; k++) {
     const int64_t j = 2 * (int64_t)col[k];
-    s1 -= lu[4 * (int64_t)k + 2] * __ldcg(&x[j]);
-    s1 -= lu[4 * (int64_t)k + 3] * __ldcg(&x[j + 1]);
+    s1 -= lu[4 * (int64_t)k + 2] * ld_shared_state<ONE>(&x[j]);
+    s1 -= lu[4 * (int64_t)k + 3] * ld_shared_state<ONE>(&x[j + 1]);
   }
   s1 -= lu[4 * (int64_t)kd + 2] * s0;
   x[2 * (int64_t)c + 1] = s1;
 }
 
 // backward rows 2c+1, then 2c of one cell (U x = y); y0, y1 = the cell's y
+template <bool ONE>
 __device__ __forceinline__ void ilu_backward_cell(const int4 a, const int4 up, double y0, double y1,
                                                   const int32_t *__restrict__ col, const double *__restrict__ lu,
                                                   double *x) {
@@ -291,8 +310,8 @@ __device__ __forceinline__ void ilu_backward_cell(const int4 a, const int4 up, d
   for (int i = 0; i < 4; i++) {
     if (i < nu) {
       const int64_t j = 2 * (int64_t)pick(up, i);
-      xa[i] = __ldcg(&x[j]);
-      xb[i] = __ldcg(&x[j + 1]);
+      xa[i] = ld_shared_state<ONE>(&x[j]);
+      xb[i] = ld_shared_state<ONE>(&x[j + 1]);
     }
   }
   double s1 = y1;
@@ -306,8 +325,8 @@ __device__ __forceinline__ void ilu_backward_cell(const int4 a, const int4 up, d
   }
   for (int32_t k = kd + 5; k < ke; k++) {
     const int64_t j = 2 * (int64_t)col[k];
-    s1 -= lu[4 * (int64_t)k + 2] * __ldcg(&x[j]);
-    s1 -= lu[4 * (int64_t)k + 3] * __ldcg(&x[j + 1]);
+    s1 -= lu[4 * (int64_t)k + 2] * ld_shared_state<ONE>(&x[j]);
+    s1 -= lu[4 * (int64_t)k + 3] * ld_shared_state<ONE>(&x[j + 1]);
   }
   const double d1 = lu[4 * (int64_t)kd + 3];
   s1 = d1 != 0.0 ? s1 / d1 : s1;
@@ -324,8 +343,8 @@ __device__ __forceinline__ void ilu_backward_cell(const int4 a, const int4 up, d
   }
   for (int32_t k = kd + 5; k < ke; k++) {
     const int64_t j = 2 * (int64_t)col[k];
-    s0 -= lu[4 * (int64_t)k] * __ldcg(&x[j]);
-    s0 -= lu[4 * (int64_t)k + 1] * __ldcg(&x[j + 1]);
+    s0 -= lu[4 * (int64_t)k] * ld_shared_state<ONE>(&x[j]);
+    s0 -= lu[4 * (int64_t)k + 1] * ld_shared_state<ONE>(&x[j + 1]);
   }
   const double d0 = lu[4 * (int64_t)kd];
   x[2 * (int64_t)c] = d0 != 0.0 ? s0 / d0 : s0;
@@ -334,11 +353,11 @@ __device__ __forceinline__ void ilu_backward_cell(const int4 a, const int4 up, d
 // x = U^{-1} L^{-1} b: the forward sweep over the levels, then the backward
 // sweep over them in reverse. Position q of level t goes to thread
 // q - lvl_ptr[t] (then + nthreads, ...), in both sweeps.
+template <bool ONE>
 __global__ void __launch_bounds__(kIluSolveThreads, 1)
     k_ilu_solve(const int32_t *__restrict__ nlev_d, const int32_t *__restrict__ lvl_ptr,
                 const int4 *__restrict__ rec, const int32_t *__restrict__ col, const double *__restrict__ lu,
                 const double *__restrict__ b, double *x) {
-  cg::cluster_group cl = cg::this_cluster();
   const ClusterIdx ix = cluster_idx();
   const int32_t nlev = *nlev_d;
   int4 ra = make_int4(0, 0, 0, 0), rl = ra, ru = ra;
@@ -361,38 +380,38 @@ __global__ void __launch_bounds__(kIluSolveThreads, 1)
         p0 = b[2 * (int64_t)ra.x];
         p1 = b[2 * (int64_t)ra.x + 1];
       }
-      ilu_forward_cell(ra, rl, p0, p1, col, lu, x);
+      ilu_forward_cell<ONE>(ra, rl, p0, p1, col, lu, x);
     }
     if (t + 1 < nlev && le + ix.tid < lvl_ptr[t + 2]) {    // next level's first cell
       fetch(le + ix.tid);
       p0 = b[2 * (int64_t)ra.x];
       p1 = b[2 * (int64_t)ra.x + 1];
     }
-    cl.sync();
+    level_barrier<ONE>();
   }
   if (nlev > 0 && lvl_ptr[nlev - 1] + ix.tid < lvl_ptr[nlev]) {
     fetch(lvl_ptr[nlev - 1] + ix.tid);
-    p0 = __ldcg(&x[2 * (int64_t)ra.x]);
-    p1 = __ldcg(&x[2 * (int64_t)ra.x + 1]);
+    p0 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x]);
+    p1 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x + 1]);
   }
   for (int32_t t = nlev - 1; t >= 0; t--) {
     const int32_t lb = lvl_ptr[t], le = lvl_ptr[t + 1];
     for (int64_t q = lb + ix.tid; q < le; q += ix.nthreads) {
       if (q != lb + ix.tid) {
         fetch(q);
-        p0 = __ldcg(&x[2 * (int64_t)ra.x]);
-        p1 = __ldcg(&x[2 * (int64_t)ra.x + 1]);
+        p0 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x]);
+        p1 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x + 1]);
       }
-      ilu_backward_cell(ra, ru, p0, p1, col, lu, x);
+      ilu_backward_cell<ONE>(ra, ru, p0, p1, col, lu, x);
     }
     // the previous level's first cell: its y values are final since the
     // forward sweep, and no thread writes them before its own turn
     if (t > 0 && lvl_ptr[t - 1] + ix.tid < lb) {
       fetch(lvl_ptr[t - 1] + ix.tid);
-      p0 = __ldcg(&x[2 * (int64_t)ra.x]);
-      p1 = __ldcg(&x[2 * (int64_t)ra.x + 1]);
+      p0 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x]);
+      p1 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x + 1]);
     }
-    cl.sync();
+    level_barrier<ONE>();
   }
 }
 
@@ -494,8 +513,12 @@ int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s) {
 
 int ilu0_solve(const rs_ilu0 *F, const double *b, double *x, cudaStream_t s) {
   if (F->nb == 0) return 0;
-  RS_CHECK_CUDA(launch_cluster(k_ilu_solve, F->cluster_s, F->threads_s, s, F->nlev_d, F->lvl_ptr, F->rec, F->col,
-                               F->lu, b, x));
+  if (F->cluster_s == 1)
+    RS_CHECK_CUDA(launch_cluster(k_ilu_solve<true>, 1, F->threads_s, s, F->nlev_d, F->lvl_ptr, F->rec, F->col, F->lu,
+                                 b, x));
+  else
+    RS_CHECK_CUDA(launch_cluster(k_ilu_solve<false>, F->cluster_s, F->threads_s, s, F->nlev_d, F->lvl_ptr, F->rec,
+                                 F->col, F->lu, b, x));
   return 0;
 }
 

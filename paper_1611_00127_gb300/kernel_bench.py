@@ -2,7 +2,7 @@
 block SpMV, timed back to back with CUDA events on the launching stream.
 
     python -m paper_1611_00127_gb300.kernel_bench [--grid layered3d|lognormal2d]
-        [--n N] [--pc PC] [--prec fp64|fp32] [--reps 20] [--kind cpr1|bf]
+        [--n N] [--pc PC] [--prec fp64|fp32] [--reps 20] [--kind cpr1|bf] [--ilu]
 
 The case is the exact Newton Jacobian at the synthetic front state of the
 n^3 layered log-normal grid (7-point two-point-flux stencil of Sec. 2 in 3D;
@@ -99,6 +99,26 @@ class Level0Case:
         torch.cuda.nvtx.range_pop()
         return e0.elapsed_time(e1) / reps, by
 
+    def time_ilu(self, reps: int):
+        """(ms per apply, levels, widest level, CTAs per cluster) of the ILU(0)
+        triangular solves on J (the first stage of CPR with P1 = ILU(0))."""
+        f = R.Ilu0(self.J)
+        y = torch.empty_like(self.F)
+        for _ in range(3):
+            f.apply(self.F, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("ilu")
+        e0.record()
+        for _ in range(reps):
+            f.apply(self.F, y)
+        e1.record()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        nlev, maxw, _ = f.info()
+        f.close()
+        return e0.elapsed_time(e1) / reps, nlev, maxw
+
     def level0(self):
         n0, nnz0 = self.H.level_info(0)[:2]
         return n0, nnz0
@@ -151,9 +171,19 @@ def main():
     ap.add_argument("--kind", choices=["cpr1", "bf"], default="cpr1")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--chunk", type=int, default=512, help="rows per chunk of the hybrid smoother")
+    ap.add_argument("--ilu", action="store_true", help="time the ILU(0) solves on J instead")
     a = ap.parse_args()
     prec = R.FP64 if a.prec == "fp64" else R.FP32
     kind = R.CPR1 if a.kind == "cpr1" else R.BF
+    if a.ilu:
+        a.n = a.n or (128 if a.grid == "layered3d" else 256)
+        p = I.config_layered_3d(a.n) if a.grid == "layered3d" else I.config_lognormal_2d(a.pc, n=a.n)
+        case = Level0Case(p, I.front_state(p), prec, kind)
+        ms, nlev, maxw = case.time_ilu(a.reps)
+        case.close()
+        print(json.dumps(dict(grid=a.grid, n=a.n, ilu_ms=ms, levels=nlev, widest=maxw,
+                              us_per_level_step=1e3 * ms / (2 * nlev))))
+        return
     if a.grid == "layered3d":
         a.n = a.n or 128
         r = layered(a.n, prec, kind, a.reps, a.chunk)
