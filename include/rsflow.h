@@ -288,9 +288,13 @@ int bsr2_residual(const rs_bsr2 *J, const double *x, const double *b, double *r,
  * over the cells: each phase is one launch of a single thread-block cluster
  * (1..8 CTAs) walking the levels with a cluster barrier. J's block pattern
  * must be structurally symmetric with every diagonal block present
- * (RS_EINVAL otherwise). The handle keeps a reference to J's row_ptr and col
- * and its own copy of the factors; J.val may change afterwards. (sync) */
-int ilu0_create(const rs_bsr2 *J, rs_ilu0 **out, cudaStream_t stream);
+ * (RS_EINVAL otherwise). The factors are computed in FP64; precision
+ * (RS_PREC_*) is the arithmetic of the solves (FP32: the factors rounded
+ * once, RS_ESETUP if one leaves the FP32 range; vectors stay FP64). Inside
+ * CPR the solves take the V-cycle precision. The handle keeps a reference to
+ * J's row_ptr and col and its own copy of the factors; J.val may change
+ * afterwards. (sync) */
+int ilu0_create(const rs_bsr2 *J, int32_t precision, rs_ilu0 **out, cudaStream_t stream);
 /* x = (L U)^{-1} b; b, x [2 nb], not aliased. */
 int ilu0_apply(const rs_ilu0 *F, const double *b, double *x, cudaStream_t stream);
 /* Level count, widest level and CTAs per cluster of the schedule. */

@@ -23,7 +23,11 @@
 // barrier; no spin loop). One thread
 // handles both rows of a cell in the sequential algorithm's operation order,
 // and this file is compiled without FMA contraction, so factors and solves
-// round exactly as the sequential algorithm does. Values that other threads
+// round exactly as the sequential algorithm does. With FP32 solves (the
+// mixed-precision preconditioner) the FP64 factors are rounded to FP32 once
+// and both sweeps compute in FP32 -- GB300 issues FP32 at 64 times its FP64
+// rate, and a level's arithmetic sits on the critical path; vectors stay FP64
+// in memory. Values that other threads
 // wrote earlier in the same launch are read with ld.global.cg (L2) when the
 // cluster has several CTAs, so no stale L1 line is ever used; a single-CTA
 // solve separates its levels by __syncthreads, which makes them visible to
@@ -44,6 +48,8 @@ struct rs_ilu0 {
   int32_t nb = 0, nnzb = 0;
   const int32_t *row_ptr = nullptr, *col = nullptr;   // caller's pattern (kept by reference)
   double *lu = nullptr;            // factors, BSR layout [4 nnzb]
+  float *luf = nullptr;            // FP32 copy of the factors (FP32 solves) [4 nnzb]
+  int precision = RS_PREC_FP64;    // arithmetic of the solves
   int32_t *dblk = nullptr;         // diagonal block of each block row [nb]
   int32_t *lvl_cells = nullptr;    // cells ordered by level [nb]
   int32_t *lvl_ptr = nullptr;      // level offsets [nb + 1]
@@ -250,22 +256,22 @@ __device__ __forceinline__ void level_barrier() {
 }
 
 // forward rows 2c, 2c+1 of one cell (L y = b, unit diagonal); b0, b1 = b
-template <bool ONE>
-__device__ __forceinline__ void ilu_forward_cell(const int4 a, const int4 lo, double b0, double b1,
-                                                 const int32_t *__restrict__ col, const double *__restrict__ lu,
+template <bool ONE, typename T>
+__device__ __forceinline__ void ilu_forward_cell(const int4 a, const int4 lo, T b0, T b1,
+                                                 const int32_t *__restrict__ col, const T *__restrict__ lu,
                                                  double *x) {
   const int32_t c = a.x, kb = a.y, kd = a.z;
   const int32_t nl = kd - kb;
-  double xa[4], xb[4];
+  T xa[4], xb[4];
 #pragma unroll
   for (int i = 0; i < 4; i++) {
     if (i < nl) {
       const int64_t j = 2 * (int64_t)pick(lo, i);
-      xa[i] = ld_shared_state<ONE>(&x[j]);
-      xb[i] = ld_shared_state<ONE>(&x[j + 1]);
+      xa[i] = (T)ld_shared_state<ONE>(&x[j]);
+      xb[i] = (T)ld_shared_state<ONE>(&x[j + 1]);
     }
   }
-  double s0 = b0;
+  T s0 = b0;
 #pragma unroll
   for (int i = 0; i < 4; i++) {
     if (i < nl) {
@@ -276,11 +282,11 @@ __device__ __forceinline__ void ilu_forward_cell(const int4 a, const int4 lo, do
   }
   for (int32_t k = kb + 4; k < kd; k++) {
     const int64_t j = 2 * (int64_t)col[k];
-    s0 -= lu[4 * (int64_t)k] * ld_shared_state<ONE>(&x[j]);
-    s0 -= lu[4 * (int64_t)k + 1] * ld_shared_state<ONE>(&x[j + 1]);
+    s0 -= lu[4 * (int64_t)k] * (T)ld_shared_state<ONE>(&x[j]);
+    s0 -= lu[4 * (int64_t)k + 1] * (T)ld_shared_state<ONE>(&x[j + 1]);
   }
-  x[2 * (int64_t)c] = s0;
-  double s1 = b1;
+  x[2 * (int64_t)c] = (double)s0;
+  T s1 = b1;
 #pragma unroll
   for (int i = 0; i < 4; i++) {
     if (i < nl) {
@@ -291,30 +297,30 @@ __device__ __forceinline__ void ilu_forward_cell(const int4 a, const int4 lo, do
   }
   for (int32_t k = kb + 4; k < kd; k++) {
     const int64_t j = 2 * (int64_t)col[k];
-    s1 -= lu[4 * (int64_t)k + 2] * ld_shared_state<ONE>(&x[j]);
-    s1 -= lu[4 * (int64_t)k + 3] * ld_shared_state<ONE>(&x[j + 1]);
+    s1 -= lu[4 * (int64_t)k + 2] * (T)ld_shared_state<ONE>(&x[j]);
+    s1 -= lu[4 * (int64_t)k + 3] * (T)ld_shared_state<ONE>(&x[j + 1]);
   }
   s1 -= lu[4 * (int64_t)kd + 2] * s0;
-  x[2 * (int64_t)c + 1] = s1;
+  x[2 * (int64_t)c + 1] = (double)s1;
 }
 
 // backward rows 2c+1, then 2c of one cell (U x = y); y0, y1 = the cell's y
-template <bool ONE>
-__device__ __forceinline__ void ilu_backward_cell(const int4 a, const int4 up, double y0, double y1,
-                                                  const int32_t *__restrict__ col, const double *__restrict__ lu,
+template <bool ONE, typename T>
+__device__ __forceinline__ void ilu_backward_cell(const int4 a, const int4 up, T y0, T y1,
+                                                  const int32_t *__restrict__ col, const T *__restrict__ lu,
                                                   double *x) {
   const int32_t c = a.x, kd = a.z, ke = a.w;
   const int32_t nu = ke - kd - 1;
-  double xa[4], xb[4];
+  T xa[4], xb[4];
 #pragma unroll
   for (int i = 0; i < 4; i++) {
     if (i < nu) {
       const int64_t j = 2 * (int64_t)pick(up, i);
-      xa[i] = ld_shared_state<ONE>(&x[j]);
-      xb[i] = ld_shared_state<ONE>(&x[j + 1]);
+      xa[i] = (T)ld_shared_state<ONE>(&x[j]);
+      xb[i] = (T)ld_shared_state<ONE>(&x[j + 1]);
     }
   }
-  double s1 = y1;
+  T s1 = y1;
 #pragma unroll
   for (int i = 0; i < 4; i++) {
     if (i < nu) {
@@ -325,13 +331,13 @@ __device__ __forceinline__ void ilu_backward_cell(const int4 a, const int4 up, d
   }
   for (int32_t k = kd + 5; k < ke; k++) {
     const int64_t j = 2 * (int64_t)col[k];
-    s1 -= lu[4 * (int64_t)k + 2] * ld_shared_state<ONE>(&x[j]);
-    s1 -= lu[4 * (int64_t)k + 3] * ld_shared_state<ONE>(&x[j + 1]);
+    s1 -= lu[4 * (int64_t)k + 2] * (T)ld_shared_state<ONE>(&x[j]);
+    s1 -= lu[4 * (int64_t)k + 3] * (T)ld_shared_state<ONE>(&x[j + 1]);
   }
-  const double d1 = lu[4 * (int64_t)kd + 3];
-  s1 = d1 != 0.0 ? s1 / d1 : s1;
-  x[2 * (int64_t)c + 1] = s1;
-  double s0 = y0;
+  const T d1 = lu[4 * (int64_t)kd + 3];
+  s1 = d1 != T(0) ? s1 / d1 : s1;
+  x[2 * (int64_t)c + 1] = (double)s1;
+  T s0 = y0;
   s0 -= lu[4 * (int64_t)kd + 1] * s1;
 #pragma unroll
   for (int i = 0; i < 4; i++) {
@@ -343,25 +349,25 @@ __device__ __forceinline__ void ilu_backward_cell(const int4 a, const int4 up, d
   }
   for (int32_t k = kd + 5; k < ke; k++) {
     const int64_t j = 2 * (int64_t)col[k];
-    s0 -= lu[4 * (int64_t)k] * ld_shared_state<ONE>(&x[j]);
-    s0 -= lu[4 * (int64_t)k + 1] * ld_shared_state<ONE>(&x[j + 1]);
+    s0 -= lu[4 * (int64_t)k] * (T)ld_shared_state<ONE>(&x[j]);
+    s0 -= lu[4 * (int64_t)k + 1] * (T)ld_shared_state<ONE>(&x[j + 1]);
   }
-  const double d0 = lu[4 * (int64_t)kd];
-  x[2 * (int64_t)c] = d0 != 0.0 ? s0 / d0 : s0;
+  const T d0 = lu[4 * (int64_t)kd];
+  x[2 * (int64_t)c] = (double)(d0 != T(0) ? s0 / d0 : s0);
 }
 
 // x = U^{-1} L^{-1} b: the forward sweep over the levels, then the backward
 // sweep over them in reverse. Position q of level t goes to thread
 // q - lvl_ptr[t] (then + nthreads, ...), in both sweeps.
-template <bool ONE>
+template <bool ONE, typename T>
 __global__ void __launch_bounds__(kIluSolveThreads, 1)
     k_ilu_solve(const int32_t *__restrict__ nlev_d, const int32_t *__restrict__ lvl_ptr,
-                const int4 *__restrict__ rec, const int32_t *__restrict__ col, const double *__restrict__ lu,
+                const int4 *__restrict__ rec, const int32_t *__restrict__ col, const T *__restrict__ lu,
                 const double *__restrict__ b, double *x) {
   const ClusterIdx ix = cluster_idx();
   const int32_t nlev = *nlev_d;
   int4 ra = make_int4(0, 0, 0, 0), rl = ra, ru = ra;
-  double p0 = 0.0, p1 = 0.0;
+  T p0 = T(0), p1 = T(0);
   auto fetch = [&](int64_t q) {
     ra = rec[3 * q];
     rl = rec[3 * q + 1];
@@ -369,50 +375,59 @@ __global__ void __launch_bounds__(kIluSolveThreads, 1)
   };
   if (nlev > 0 && lvl_ptr[0] + ix.tid < lvl_ptr[1]) {
     fetch(lvl_ptr[0] + ix.tid);
-    p0 = b[2 * (int64_t)ra.x];
-    p1 = b[2 * (int64_t)ra.x + 1];
+    p0 = (T)b[2 * (int64_t)ra.x];
+    p1 = (T)b[2 * (int64_t)ra.x + 1];
   }
   for (int32_t t = 0; t < nlev; t++) {
     const int32_t lb = lvl_ptr[t], le = lvl_ptr[t + 1];
     for (int64_t q = lb + ix.tid; q < le; q += ix.nthreads) {
       if (q != lb + ix.tid) {
         fetch(q);
-        p0 = b[2 * (int64_t)ra.x];
-        p1 = b[2 * (int64_t)ra.x + 1];
+        p0 = (T)b[2 * (int64_t)ra.x];
+        p1 = (T)b[2 * (int64_t)ra.x + 1];
       }
-      ilu_forward_cell<ONE>(ra, rl, p0, p1, col, lu, x);
+      ilu_forward_cell<ONE, T>(ra, rl, p0, p1, col, lu, x);
     }
     if (t + 1 < nlev && le + ix.tid < lvl_ptr[t + 2]) {    // next level's first cell
       fetch(le + ix.tid);
-      p0 = b[2 * (int64_t)ra.x];
-      p1 = b[2 * (int64_t)ra.x + 1];
+      p0 = (T)b[2 * (int64_t)ra.x];
+      p1 = (T)b[2 * (int64_t)ra.x + 1];
     }
     level_barrier<ONE>();
   }
   if (nlev > 0 && lvl_ptr[nlev - 1] + ix.tid < lvl_ptr[nlev]) {
     fetch(lvl_ptr[nlev - 1] + ix.tid);
-    p0 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x]);
-    p1 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x + 1]);
+    p0 = (T)ld_shared_state<ONE>(&x[2 * (int64_t)ra.x]);
+    p1 = (T)ld_shared_state<ONE>(&x[2 * (int64_t)ra.x + 1]);
   }
   for (int32_t t = nlev - 1; t >= 0; t--) {
     const int32_t lb = lvl_ptr[t], le = lvl_ptr[t + 1];
     for (int64_t q = lb + ix.tid; q < le; q += ix.nthreads) {
       if (q != lb + ix.tid) {
         fetch(q);
-        p0 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x]);
-        p1 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x + 1]);
+        p0 = (T)ld_shared_state<ONE>(&x[2 * (int64_t)ra.x]);
+        p1 = (T)ld_shared_state<ONE>(&x[2 * (int64_t)ra.x + 1]);
       }
-      ilu_backward_cell<ONE>(ra, ru, p0, p1, col, lu, x);
+      ilu_backward_cell<ONE, T>(ra, ru, p0, p1, col, lu, x);
     }
     // the previous level's first cell: its y values are final since the
     // forward sweep, and no thread writes them before its own turn
     if (t > 0 && lvl_ptr[t - 1] + ix.tid < lb) {
       fetch(lvl_ptr[t - 1] + ix.tid);
-      p0 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x]);
-      p1 = ld_shared_state<ONE>(&x[2 * (int64_t)ra.x + 1]);
+      p0 = (T)ld_shared_state<ONE>(&x[2 * (int64_t)ra.x]);
+      p1 = (T)ld_shared_state<ONE>(&x[2 * (int64_t)ra.x + 1]);
     }
     level_barrier<ONE>();
   }
+}
+
+// FP32 copy of the factors; err |= 1 where a value is not finite in FP32
+__global__ void k_ilu_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ f, int32_t *err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = (float)a[i];
+  if (!isfinite(v)) atomicOr(err, 1);
+  f[i] = v;
 }
 
 template <typename... KArgs, typename... Args>
@@ -441,6 +456,7 @@ void ilu_free(rs_ilu0 *F) {
   dfree(F->lvl_ptr, s);
   dfree(F->nlev_d, s);
   dfree(F->rec, s);
+  dfree(F->luf, s);
   delete F;
 }
 
@@ -448,7 +464,7 @@ void ilu_free(rs_ilu0 *F) {
 
 namespace rs {
 
-int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s) {
+int ilu0_build(const rs_bsr2 &J, int precision, rs_ilu0 **out, cudaStream_t s) {
   *out = nullptr;
   rs_ilu0 *F = new rs_ilu0();
   F->nb = J.nb;
@@ -456,6 +472,7 @@ int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s) {
   F->row_ptr = J.row_ptr;
   F->col = J.col;
   F->stream = s;
+  F->precision = precision;
   const int32_t nb = J.nb;
   if (nb == 0) { *out = F; return 0; }
   int rc = 0;
@@ -499,6 +516,16 @@ int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s) {
     RS_CHECK_CUDA(cudaMemcpyAsync(F->lu, J.val, sizeof(double) * 4 * (size_t)J.nnzb, cudaMemcpyDeviceToDevice, s));
     RS_CHECK_CUDA(launch_cluster(k_ilu_factor, F->cluster, F->threads, s, F->nlev_d, F->lvl_ptr, F->lvl_cells,
                                  J.row_ptr, J.col, F->dblk, F->lu));
+    if (precision == RS_PREC_FP32) {
+      RS_TRY(dalloc_n(&F->luf, 4 * (size_t)J.nnzb, s));
+      RS_CHECK_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(int32_t), s));
+      RS_COUNTED k_ilu_to_f32<<<grid_for(4 * (int64_t)J.nnzb), kBlock, 0, s>>>(4 * (int64_t)J.nnzb, F->lu, F->luf, ctrl);
+      RS_CHECK_CUDA(cudaGetLastError());
+      int32_t e = 0;
+      RS_CHECK_CUDA(cudaMemcpyAsync(&e, ctrl, sizeof(e), cudaMemcpyDeviceToHost, s));
+      RS_CHECK_CUDA(cudaStreamSynchronize(s));
+      if (e) return fail(RS_ESETUP, "ILU(0): factors beyond the FP32 range");
+    }
     RS_CHECK_CUDA(cudaStreamSynchronize(s));
     return 0;
   };
@@ -513,12 +540,22 @@ int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s) {
 
 int ilu0_solve(const rs_ilu0 *F, const double *b, double *x, cudaStream_t s) {
   if (F->nb == 0) return 0;
-  if (F->cluster_s == 1)
-    RS_CHECK_CUDA(launch_cluster(k_ilu_solve<true>, 1, F->threads_s, s, F->nlev_d, F->lvl_ptr, F->rec, F->col, F->lu,
-                                 b, x));
-  else
-    RS_CHECK_CUDA(launch_cluster(k_ilu_solve<false>, F->cluster_s, F->threads_s, s, F->nlev_d, F->lvl_ptr, F->rec,
-                                 F->col, F->lu, b, x));
+  const bool one = F->cluster_s == 1;
+  if (F->precision == RS_PREC_FP32) {
+    if (one)
+      RS_CHECK_CUDA(launch_cluster(k_ilu_solve<true, float>, 1, F->threads_s, s, F->nlev_d, F->lvl_ptr, F->rec, F->col,
+                                   F->luf, b, x));
+    else
+      RS_CHECK_CUDA(launch_cluster(k_ilu_solve<false, float>, F->cluster_s, F->threads_s, s, F->nlev_d, F->lvl_ptr,
+                                   F->rec, F->col, F->luf, b, x));
+  } else {
+    if (one)
+      RS_CHECK_CUDA(launch_cluster(k_ilu_solve<true, double>, 1, F->threads_s, s, F->nlev_d, F->lvl_ptr, F->rec,
+                                   F->col, F->lu, b, x));
+    else
+      RS_CHECK_CUDA(launch_cluster(k_ilu_solve<false, double>, F->cluster_s, F->threads_s, s, F->nlev_d, F->lvl_ptr,
+                                   F->rec, F->col, F->lu, b, x));
+  }
   return 0;
 }
 
@@ -528,12 +565,13 @@ void ilu0_free(rs_ilu0 *F) {
 
 }  // namespace rs
 
-extern "C" int ilu0_create(const rs_bsr2 *J, rs_ilu0 **out, cudaStream_t stream) {
+extern "C" int ilu0_create(const rs_bsr2 *J, int32_t precision, rs_ilu0 **out, cudaStream_t stream) {
   if (!out) return fail(RS_EINVAL, "null output handle");
   *out = nullptr;
   if (!J || J->nb < 0 || J->nnzb < 0 || (J->nb > 0 && (!J->row_ptr || !J->col || !J->val)))
     return fail(RS_EINVAL, "invalid arguments");
-  return ilu0_build(*J, out, stream);
+  if (precision != RS_PREC_FP32 && precision != RS_PREC_FP64) return fail(RS_EINVAL, "bad precision");
+  return ilu0_build(*J, precision, out, stream);
 }
 
 extern "C" int ilu0_apply(const rs_ilu0 *F, const double *b, double *x, cudaStream_t stream) {

@@ -219,7 +219,7 @@ int amg_tune_smoother(Hier &H, cudaStream_t s);
 int vcycle_wait_status(cudaStream_t s);
 // ILU(0) of the point-ordered scalar matrix of J (rs_ilu.cu); the factors
 // keep a reference to J's pattern
-int ilu0_build(const rs_bsr2 &J, rs_ilu0 **out, cudaStream_t s);
+int ilu0_build(const rs_bsr2 &J, int precision, rs_ilu0 **out, cudaStream_t s);
 int ilu0_solve(const rs_ilu0 *F, const double *b, double *x, cudaStream_t s);
 void ilu0_free(rs_ilu0 *F);
 

@@ -187,7 +187,7 @@ int build(rs_precond *M, cudaStream_t s) {
       Jt.val = jt;
     }
     if (p.p1 == RS_P1_ILU0) {
-      RS_TRY(ilu0_build(Jt, &M->ilu, s));
+      RS_TRY(ilu0_build(Jt, p.amg.precision, &M->ilu, s));   // solves in the V-cycle precision
     } else {
       RS_TRY(dalloc_n(&M->p1inv, 4 * (size_t)nb, s));
       RS_TRY(block_diag_inverse(Jt, M->p1inv, s));

@@ -36,6 +36,7 @@ class Level0Case:
 
     def __init__(self, p, state, precision: int, kind: int = R.CPR1, theta: float = 0.5, chunk: int = 512):
         self.p = p
+        self.precision = precision
         u, uo = state
         self.dp = R.DeviceProblems(p)
         self.J = R.Bsr2.pattern(self.dp)
@@ -100,9 +101,10 @@ class Level0Case:
         return e0.elapsed_time(e1) / reps, by
 
     def time_ilu(self, reps: int):
-        """(ms per apply, levels, widest level, CTAs per cluster) of the ILU(0)
-        triangular solves on J (the first stage of CPR with P1 = ILU(0))."""
-        f = R.Ilu0(self.J)
+        """(ms per apply, levels, widest level) of the ILU(0) triangular solves
+        on J (the first stage of CPR with P1 = ILU(0)) in the case's
+        precision."""
+        f = R.Ilu0(self.J, self.precision)
         y = torch.empty_like(self.F)
         for _ in range(3):
             f.apply(self.F, y)
@@ -181,7 +183,7 @@ def main():
         case = Level0Case(p, I.front_state(p), prec, kind)
         ms, nlev, maxw = case.time_ilu(a.reps)
         case.close()
-        print(json.dumps(dict(grid=a.grid, n=a.n, ilu_ms=ms, levels=nlev, widest=maxw,
+        print(json.dumps(dict(grid=a.grid, n=a.n, prec=a.prec, ilu_ms=ms, levels=nlev, widest=maxw,
                               us_per_level_step=1e3 * ms / (2 * nlev))))
         return
     if a.grid == "layered3d":

@@ -116,7 +116,7 @@ def _declare(L):
         "amg_level_copy": (C.c_int, [P, i32, P, P, P, P, P, P, P, P, P]),
         "amg_level_smooth": (C.c_int, [P, i32, i32, P, P]),
         "amg_level_transfer": (C.c_int, [P, i32, i32, i32, P, P]),
-        "ilu0_create": (C.c_int, [P, P, P]),
+        "ilu0_create": (C.c_int, [P, i32, P, P]),
         "ilu0_apply": (C.c_int, [P, P, P, P]),
         "ilu0_info": (C.c_int, [P, P, P, P]),
         "ilu0_factors": (C.c_int, [P, P, P]),
@@ -442,11 +442,11 @@ class Precond:
 class Ilu0:
     """ILU(0) of the point-ordered scalar matrix of J (P1 of CPR)."""
 
-    def __init__(self, J: Bsr2, stream=None):
+    def __init__(self, J: Bsr2, precision: int = FP64, stream=None):
         self.J = J
         self._Jc = J.c()
         self.h = C.c_void_p()
-        _check(lib().ilu0_create(C.byref(self._Jc), C.byref(self.h), _stream(stream)), "ilu0_create")
+        _check(lib().ilu0_create(C.byref(self._Jc), precision, C.byref(self.h), _stream(stream)), "ilu0_create")
 
     def apply(self, b: torch.Tensor, x: torch.Tensor, stream=None):
         _check(lib().ilu0_apply(self.h, _ptr(b), _ptr(x), _stream(stream)), "ilu0_apply")

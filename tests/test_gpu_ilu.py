@@ -148,3 +148,36 @@ def test_cpr_with_ilu0_matches_oracle(R, oracle, inputs, kind, dec):
     assert abs(st.iterations - ito) <= 1
     np.testing.assert_allclose(x.cpu().numpy(), xo, rtol=1e-6, atol=1e-6 * np.abs(xo).max())
     M.close()
+
+
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_ilu0_fp32_solves_close_to_fp64(R, oracle, inputs, case):
+    """FP32 solves (the factors rounded once, FP32 sweeps): within 1e-4 of
+    the oracle's FP64 solve, relative in the 2-norm; FP32 rounding amplified
+    by the triangular factors' conditioning."""
+    p = _grids(inputs)[case]
+    F, J, rp, col = _jacobian(oracle, inputs, p, case)
+    f = R.Ilu0(R.Bsr2.from_host(rp, col, J), R.FP32)
+    b = inputs.rhs_vector(2 * p.ncell, case)
+    x = torch.empty(2 * p.ncell, dtype=torch.float64, device="cuda")
+    f.apply(_dev(b), x)
+    xo = oracle.ilu0_solve(rp, col, oracle.ilu0(rp, col, J), b)
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-4 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_cpr_ilu0_fp32_converges_like_fp64(R, oracle, inputs, kind):
+    p = inputs.config_gravity_2d(40, 1)
+    F, J, rp, col = _jacobian(oracle, inputs, p, 2)
+    Jd = R.Bsr2.from_host(rp, col, J)
+    its = {}
+    for prec in (R.FP32, R.FP64):
+        M = R.Precond(Jd, R.PrecParams(kind=kind, decouple=2, p1=1, amg=R.AmgParams(precision=prec)))
+        x = torch.zeros(2 * p.ncell, dtype=torch.float64, device="cuda")
+        st = R.gmres_solve(Jd, M, _dev(-F), x, R.GmresParams(maxit=600))
+        assert st.status == R.RS_OK
+        res = -F - oracle.bsr2_spmv(rp, col, J, x.cpu().numpy())
+        assert np.linalg.norm(res) <= 1.0001e-8 * np.linalg.norm(F)
+        its[prec] = st.iterations
+        M.close()
+    assert its[R.FP32] <= 1.15 * its[R.FP64] + 2, its
