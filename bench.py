@@ -45,7 +45,7 @@ KINDS = (("amgJ", 0, 0), ("cpr1", 1, 2), ("bf", 3, 0))
 # None where no capture of the current version exists.
 NCU_TRAFFIC = {
     ("k_hgs", "fp64", "lognormal256bf"): (11.759872e6 + 0.0, "profiles/k_hgs_fp64_lognormal256_bf_level0.md"),
-    ("k_hgs", "fp64", "layered128"): (225.427968e6 + 12.004352e6, "profiles/k_hgs_fp64_layered128_level0.md"),
+    ("k_hgs", "fp64", "layered128"): (225.426688e6 + 11.628800e6, "profiles/k_hgs_fp64_layered128_level0.md"),
     ("k_csr_residual", "fp32", "layered128"): (141.960448e6 + 6.054144e6,
                                              "profiles/k_csr_residual_fp32_layered128_level0.md"),
     ("k_hgs", "fp32", "layered128"): (150.325760e6 + 6.161408e6, "profiles/k_hgs_fp32_layered128_level0.md"),
