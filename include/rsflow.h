@@ -117,6 +117,9 @@ typedef struct rs_amg_params {
                               point-block hybrid Gauss-Seidel smoother; 1: scalar AMG */
   int32_t precision;       /* RS_PREC_* of the V-cycle */
   int32_t chunk;           /* rows per chunk of the hybrid smoother (32..512) */
+  int32_t agg_levels;      /* aggressive coarsening (0..8): the first agg_levels coarse grids are
+                              each two coarsening stages, interpolated by the product of the
+                              two stages' P (the intermediate level is dropped); 0: off */
 } rs_amg_params;
 
 typedef struct rs_amg rs_amg;

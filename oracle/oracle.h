@@ -48,6 +48,8 @@ typedef struct {
   int32_t interp;      /* 0 classical, 1 extended+i */
   int32_t num_functions; /* 2: systems (point) AMG, 2 interleaved unknowns per point; else scalar */
   int32_t chunk;       /* rows per block of the hybrid smoother */
+  int32_t agg_levels;  /* aggressive coarsening: the first agg_levels coarse grids are
+                          two coarsening stages each (P = P_l P_{l+1}, level l+1 dropped) */
 } or_amg_params;
 
 typedef struct or_amg or_amg;

@@ -756,6 +756,29 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
     l++;
   }
   H->nlev = l + 1;
+  /* Aggressive coarsening, two-stage form: the coarse grid of level k is the
+   * second of two PMIS stages, C2 within C1, and its interpolation the product
+   * of the two stages' interpolations, P = P_k P_{k+1} (each stage extended+i
+   * or classical on its own Galerkin operator); the intermediate level is
+   * dropped, its operator A_{k+2} = P_{k+1}^T (P_k^T A_k P_k) P_{k+1} kept as
+   * the next level's. A fine point is C when it is C in both stages. Applied
+   * to the first agg_levels coarse grids while two more levels exist. */
+  for (int32_t k = 0; k < prm->agg_levels && k + 2 < H->nlev; k++) {
+    or_csr *P = or_spgemm(H->P[k], H->P[k + 1]);
+    int8_t *cf = xmalloc((size_t)H->A[k]->n + 1);
+    int32_t ic = 0;
+    for (int32_t i = 0; i < H->A[k]->n; i++) cf[i] = H->cf[k][i] == 1 ? H->cf[k + 1][ic++] : (int8_t)-1;
+    or_csr_free(H->P[k]); or_csr_free(H->R[k]); free(H->cf[k]);
+    H->P[k] = P;
+    H->R[k] = or_transpose(P);
+    H->cf[k] = cf;
+    or_csr_free(H->A[k + 1]); or_csr_free(H->P[k + 1]); or_csr_free(H->R[k + 1]); free(H->cf[k + 1]);
+    for (int32_t j = k + 1; j + 1 < H->nlev; j++) {
+      H->A[j] = H->A[j + 1]; H->P[j] = H->P[j + 1]; H->R[j] = H->R[j + 1]; H->cf[j] = H->cf[j + 1];
+    }
+    H->nlev--;
+    H->A[H->nlev] = NULL; H->P[H->nlev] = NULL; H->R[H->nlev] = NULL; H->cf[H->nlev] = NULL;
+  }
   for (int32_t k = 0; k < H->nlev - 1; k++) {
     or_csr *A = H->A[k];
     H->colour[k] = xmalloc(sizeof(int32_t) * ((size_t)A->n + 1));

@@ -15,6 +15,7 @@ static int check_amg_params(const rs_amg_params &a) {
   if (a.nu1 < 0 || a.nu2 < 0 || a.nu1 > 16 || a.nu2 > 16) return fail(RS_EINVAL, "bad sweep counts");
   if (a.interp != RS_INTERP_CLASSICAL && a.interp != RS_INTERP_EXTI) return fail(RS_EINVAL, "bad interpolation");
   if (a.precision != RS_PREC_FP32 && a.precision != RS_PREC_FP64) return fail(RS_EINVAL, "bad precision");
+  if (a.agg_levels < 0 || a.agg_levels > 8) return fail(RS_EINVAL, "agg_levels outside [0, 8]");
   return 0;
 }
 }  // namespace rs

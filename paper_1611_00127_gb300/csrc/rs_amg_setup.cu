@@ -1095,6 +1095,71 @@ static int colour_level(Level &L, const int32_t *seg, const int32_t *dseg_off, c
   return 0;
 }
 
+static void level_free(Level &L, cudaStream_t s);
+
+// fine C/F marks after two coarsening stages: C iff C in both (the first
+// stage's C points, in order, are the second stage's rows)
+__global__ void k_cf_merge(int32_t n, const int8_t *__restrict__ cf0, const int32_t *__restrict__ cidx,
+                           const int8_t *__restrict__ cf1, int8_t *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = cf0[i] == 1 ? cf1[cidx[i]] : (int8_t)-1;
+}
+
+__global__ void k_is_c(int32_t n, const int8_t *__restrict__ cf, int32_t *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = cf[i] == 1;
+}
+
+// Aggressive coarsening, two-stage form: level l's coarse grid becomes the
+// second of two PMIS stages and its interpolation the product of the two
+// stages' interpolations, P = P_l P_{l+1}, R = P^T; level l+1 is dropped and
+// A_{l+2} = P_{l+1}^T (P_l^T A_l P_l) P_{l+1} stays the next operator. Applied
+// to the first prm.agg_levels coarse grids while every system coarsens past
+// the dropped level.
+static int merge_levels(Hier &H, const rs_amg_params &prm, int32_t *f32err, cudaStream_t s) {
+  for (int32_t l = 0; l < prm.agg_levels && l + 2 < (int32_t)H.L.size(); l++) {
+    bool all = true;
+    for (int32_t q = 0; q < H.nseg; q++) all = all && H.last_level[q] >= l + 2;
+    if (!all) break;
+    Level &L = H.L[l];
+    Level &M = H.L[l + 1];
+    DCsr P, R;
+    RS_TRY(spgemm(L.P, M.P, P, s));
+    RS_TRY(transpose(P, R, s));
+    const int32_t n = L.A.n;
+    Scratch sc(s);
+    int32_t *cidx = nullptr;
+    int8_t *cf = nullptr;
+    RS_TRY(sc.get(&cidx, (size_t)n + 1));
+    RS_TRY(dalloc_n(&cf, (size_t)n + 1, s));
+    if (n > 0) {
+      RS_COUNTED k_is_c<<<grid_for(n), kBlock, 0, s>>>(n, L.cf, cidx);
+      int32_t nc = 0;
+      RS_TRY(exclusive_scan(cidx, cidx, n, s, &nc));
+      RS_COUNTED k_cf_merge<<<grid_for(n), kBlock, 0, s>>>(n, L.cf, cidx, M.cf, cf);
+    }
+    if (H.precision == RS_PREC_FP32) {
+      RS_TRY(dalloc_n(&P.valf, (size_t)P.nnz + 1, s));
+      RS_TRY(dalloc_n(&R.valf, (size_t)R.nnz + 1, s));
+      if (P.nnz) RS_COUNTED k_to_f32<<<grid_for(P.nnz), kBlock, 0, s>>>(P.nnz, P.val, P.valf, f32err);
+      if (R.nnz) RS_COUNTED k_to_f32<<<grid_for(R.nnz), kBlock, 0, s>>>(R.nnz, R.val, R.valf, f32err);
+    }
+    RS_CHECK_CUDA(cudaGetLastError());
+    RS_CHECK_CUDA(cudaStreamSynchronize(s));
+    dcsr_free(L.P, s);
+    dcsr_free(L.R, s);
+    dfree(L.cf, s);
+    L.P = P;
+    L.R = R;
+    L.cf = cf;
+    level_free(M, s);
+    H.L.erase(H.L.begin() + l + 1);
+    for (int32_t q = 0; q < H.nseg; q++) H.last_level[q]--;
+    H.nlev = (int32_t)H.L.size();
+  }
+  return 0;
+}
+
 int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg_params &prm, Hier &H,
               cudaStream_t s) {
   H.prm = prm;
@@ -1511,6 +1576,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
   H.nlev = (int32_t)H.L.size();
   for (int32_t q = 0; q < H.nseg; q++)
     if (H.last_level[q] < 0) H.last_level[q] = H.nlev - 1;
+  RS_TRY(merge_levels(H, prm, f32err, s));
   int32_t hrange = 0;
   RS_TRY(sync_copy(&hrange, f32err, sizeof(int32_t), s));
   if (hrange)
@@ -1518,8 +1584,8 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
   return amg_tune_smoother(H, s);
 }
 
-void amg_free(Hier &H, cudaStream_t s) {
-  for (Level &L : H.L) {
+static void level_free(Level &L, cudaStream_t s) {
+  {
     dcsr_free(L.A, s);
     dcsr_free(L.P, s);
     dcsr_free(L.R, s);
@@ -1549,6 +1615,10 @@ void amg_free(Hier &H, cudaStream_t s) {
     dfree(L.r, s);
     dfree(L.t, s);
   }
+}
+
+void amg_free(Hier &H, cudaStream_t s) {
+  for (Level &L : H.L) level_free(L, s);
   H.L.clear();
   H.nlev = 0;
 }
