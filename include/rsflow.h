@@ -120,6 +120,8 @@ typedef struct rs_amg_params {
   int32_t agg_levels;      /* aggressive coarsening (0..8): the first agg_levels coarse grids are
                               each two coarsening stages, interpolated by the product of the
                               two stages' P (the intermediate level is dropped); 0: off */
+  int32_t chunk_coarse;    /* rows per chunk of the hybrid smoother on levels >= 1 (32..512);
+                              0: `chunk` on every level */
 } rs_amg_params;
 
 typedef struct rs_amg rs_amg;

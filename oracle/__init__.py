@@ -66,7 +66,8 @@ class _AmgParams(C.Structure):
     _fields_ = [("theta", C.c_double), ("seed", C.c_uint64), ("max_levels", C.c_int32),
                 ("coarse_n", C.c_int32), ("max_dense", C.c_int32), ("smoother", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("interp", C.c_int32),
-                ("num_functions", C.c_int32), ("chunk", C.c_int32), ("agg_levels", C.c_int32)]
+                ("num_functions", C.c_int32), ("chunk", C.c_int32), ("agg_levels", C.c_int32),
+                ("chunk_coarse", C.c_int32)]
 
 
 class _PrecParams(C.Structure):
@@ -333,11 +334,12 @@ class AmgParams:
     num_functions: int = 1
     chunk: int = 512
     agg_levels: int = 0
+    chunk_coarse: int = 32
 
     def c(self):
         return _AmgParams(self.theta, self.seed, self.max_levels, self.coarse_n,
                           self.max_dense, self.smoother, self.nu1, self.nu2, self.interp,
-                          self.num_functions, self.chunk, self.agg_levels)
+                          self.num_functions, self.chunk, self.agg_levels, self.chunk_coarse)
 
 
 def splitmix64(seed: int, counter: int) -> int:

@@ -50,6 +50,7 @@ typedef struct {
   int32_t chunk;       /* rows per block of the hybrid smoother */
   int32_t agg_levels;  /* aggressive coarsening: the first agg_levels coarse grids are
                           two coarsening stages each (P = P_l P_{l+1}, level l+1 dropped) */
+  int32_t chunk_coarse; /* hybrid-smoother chunk on levels >= 1 (0: `chunk` everywhere) */
 } or_amg_params;
 
 typedef struct or_amg or_amg;

@@ -481,6 +481,12 @@ int32_t or_chunk_rows(const or_csr *A, int32_t chunk) {
   return C;
 }
 
+/* The hybrid smoother's chunk parameter on level l: `chunk` on level 0,
+ * `chunk_coarse` (when set) on the coarser levels. */
+static int32_t level_chunk(const or_amg_params *p, int32_t l) {
+  return (l == 0 || p->chunk_coarse <= 0) ? p->chunk : p->chunk_coarse;
+}
+
 /* Colouring used by the hybrid smoother: rows are cut into chunks of
  * or_chunk_rows(A) consecutive rows; inside each chunk, rows are coloured
  * first-fit in ascending order, each taking the lowest colour not used by an
@@ -783,9 +789,9 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
     or_csr *A = H->A[k];
     H->colour[k] = xmalloc(sizeof(int32_t) * ((size_t)A->n + 1));
     if (H->b > 1) {
-      H->ncol[k] = or_chunk_colour_pt(A, prm->chunk, H->b, H->colour[k]);
+      H->ncol[k] = or_chunk_colour_pt(A, level_chunk(prm, k), H->b, H->colour[k]);
       H->binv[k] = block_inverses2(A);
-    } else if (prm->smoother == 2) H->ncol[k] = or_chunk_colour(A, prm->chunk, H->colour[k]);
+    } else if (prm->smoother == 2) H->ncol[k] = or_chunk_colour(A, level_chunk(prm, k), H->colour[k]);
     else H->ncol[k] = or_jp_colour(A, prm->seed, k, H->colour[k]);
     H->l1[k] = xmalloc(sizeof(double) * ((size_t)A->n + 1));
     for (int32_t i = 0; i < A->n; i++) {
@@ -813,9 +819,9 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
     int32_t k = H->nlev - 1;
     H->colour[k] = xmalloc(sizeof(int32_t) * ((size_t)nc + 1));
     if (H->b > 1) {
-      H->ncol[k] = or_chunk_colour_pt(Ac, prm->chunk, H->b, H->colour[k]);
+      H->ncol[k] = or_chunk_colour_pt(Ac, level_chunk(prm, k), H->b, H->colour[k]);
       H->binv[k] = block_inverses2(Ac);
-    } else if (prm->smoother == 2) H->ncol[k] = or_chunk_colour(Ac, prm->chunk, H->colour[k]);
+    } else if (prm->smoother == 2) H->ncol[k] = or_chunk_colour(Ac, level_chunk(prm, k), H->colour[k]);
     else H->ncol[k] = or_jp_colour(Ac, prm->seed, k, H->colour[k]);
     H->l1[k] = xmalloc(sizeof(double) * ((size_t)nc + 1));
     for (int32_t i = 0; i < nc; i++) {
@@ -881,7 +887,7 @@ void or_amg_smooth(const or_amg *H, int32_t l, const double *b, double *x) {
      * inverse diagonal block times those two numbers */
     double *xo = xmalloc(sizeof(double) * ((size_t)A->n + 1));
     memcpy(xo, x, sizeof(double) * (size_t)A->n);
-    int32_t C = or_chunk_rows(A, H->prm.chunk);
+    int32_t C = or_chunk_rows(A, level_chunk(&H->prm, l));
     for (int32_t c0 = 0; c0 < A->n; c0 += C) {
       int32_t c1 = c0 + C < A->n ? c0 + C : A->n;
       for (int32_t c = 0; c < H->ncol[l]; c++) {
@@ -917,7 +923,7 @@ void or_amg_smooth(const or_amg *H, int32_t l, const double *b, double *x) {
     memcpy(xo, x, sizeof(double) * (size_t)A->n);
     /* chunk size: the `chunk` parameter, halved (not below 32) while
      * chunk * ceil(nnz / n) exceeds 12288 entries */
-    int32_t C = or_chunk_rows(A, H->prm.chunk);
+    int32_t C = or_chunk_rows(A, level_chunk(&H->prm, l));
     for (int32_t c0 = 0; c0 < A->n; c0 += C) {
       int32_t c1 = c0 + C < A->n ? c0 + C : A->n;
       for (int32_t c = 0; c < H->ncol[l]; c++) {

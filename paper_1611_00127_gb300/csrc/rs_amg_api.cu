@@ -16,6 +16,8 @@ static int check_amg_params(const rs_amg_params &a) {
   if (a.interp != RS_INTERP_CLASSICAL && a.interp != RS_INTERP_EXTI) return fail(RS_EINVAL, "bad interpolation");
   if (a.precision != RS_PREC_FP32 && a.precision != RS_PREC_FP64) return fail(RS_EINVAL, "bad precision");
   if (a.agg_levels < 0 || a.agg_levels > 8) return fail(RS_EINVAL, "agg_levels outside [0, 8]");
+  if (a.chunk_coarse != 0 && (a.chunk_coarse < 32 || a.chunk_coarse > 512))
+    return fail(RS_EINVAL, "chunk_coarse outside [32, 512]");
   return 0;
 }
 }  // namespace rs

@@ -1410,8 +1410,9 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     const bool any_smooth = std::any_of(smooth_seg.begin(), smooth_seg.end(), [](uint8_t v) { return v != 0; });
     if (any_smooth && H.prm.smoother == RS_SMOOTH_HYBRID) {
       // chunk k = rows [packed[2k], packed[2k+1]), never spanning two systems;
-      // per system the chunk size is `chunk`, halved (not below 32) while
-      // chunk * ceil(nnz / n) of that system exceeds 12288 entries
+      // per system the chunk size is `chunk` (`chunk_coarse`, when set, on
+      // levels >= 1), halved (not below 32) while chunk * ceil(nnz / n) of
+      // that system exceeds 12288 entries
       std::vector<int32_t> rpb(nseg + 1);
       {
         int32_t *tmp = nullptr;
@@ -1421,12 +1422,15 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       }
       std::vector<int32_t> packed;
       int32_t nsm = 0;
+      const int32_t C0 = (l == 0 || prm.chunk_coarse <= 0) ? prm.chunk : prm.chunk_coarse;
+      Lc.chunk_c = 0;
       for (int32_t q = 0; q < nseg; q++) {
         if (!smooth_seg[q]) continue;
         const int64_t nq = Lc.seg_off[q + 1] - Lc.seg_off[q], zq = rpb[q + 1] - rpb[q];
         const int64_t avg = nq > 0 ? (zq + nq - 1) / nq : 1;
-        int32_t C = prm.chunk;
+        int32_t C = C0;
         while (C > 32 && (int64_t)C * avg > 12288) C /= 2;
+        Lc.chunk_c = std::max(Lc.chunk_c, C);
         for (int32_t r = Lc.seg_off[q]; r < Lc.seg_off[q + 1]; r += C) {
           packed.push_back(r);
           packed.push_back(std::min(r + C, Lc.seg_off[q + 1]));

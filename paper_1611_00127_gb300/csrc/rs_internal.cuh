@@ -170,6 +170,7 @@ struct Level {
   double *cinv = nullptr;            // stacked dense inverses, row-major
   // hybrid smoother: chunks of consecutive rows (never spanning two systems)
   int32_t nchunk = 0;
+  int32_t chunk_c = 0;               // largest chunk (rows) of this level
   int32_t chunk_max_nnz = 0;         // largest number of matrix entries in one chunk
   int32_t hs_chunk_max = 0;          // largest number of packed smoother entries in one chunk
   int32_t *chunk_row0 = nullptr;     // [2 nchunk] (first row, end row) of each chunk

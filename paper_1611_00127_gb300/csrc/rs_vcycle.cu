@@ -686,16 +686,17 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
     // staging area: the level's largest chunk of packed entries (the diagonal
     // is not among them)
     const int32_t stage = std::min(L.hs_chunk_max, kHgsStageEntries);
-    const size_t shm = hgs_smem<T>(H.prm.chunk, stage, L.ncolour);
+    const int32_t cmax = L.chunk_c > 0 ? L.chunk_c : H.prm.chunk;   // the level's largest chunk
+    const size_t shm = hgs_smem<T>(cmax, stage, L.ncolour);
     const double ns = L.nsmooth, nz = L.A.n ? (double)L.A.nnz * ns / L.A.n : 0.0;
     const int hl = L.hgs_lpr > 0 ? L.hgs_lpr : hgs_lpr(L.A.n, L.A.nnz, L.nchunk);
     if (L.nfun == 2) {
-      const size_t shm2 = hgs2_smem<T>(H.prm.chunk, stage, L.ncolour);
+      const size_t shm2 = hgs2_smem<T>(cmax, stage, L.ncolour);
       for (int sw = 0; sw < sweeps; sw++) {
         T *out = (cur == xa) ? xb : xa;
         ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);
         RS_LPR_SWITCH(hl, hgs2_attr<T, L_>(); RS_COUNTED launch_pdl(k_hgs2<T, L_>, dim3(L.nchunk), dim3(kHgsThreads),
-                              shm2, s, L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, H.prm.chunk, stage,
+                              shm2, s, L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, cmax, stage,
                               L.hs_rp, L.hs_mid, L.hs_col, hs_vals<T>(L), binv_of<T>(L), b, (const T *)cur, out));
         cur = out;
       }
@@ -705,7 +706,7 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
       T *out = (cur == xa) ? xb : xa;
       ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);
       RS_LPR_SWITCH(hl, hgs_attr<T, L_>(); RS_COUNTED launch_pdl(k_hgs<T, L_>, dim3(L.nchunk), dim3(kHgsThreads), shm, s,
-                            L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, H.prm.chunk, stage, L.hs_rp,
+                            L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, cmax, stage, L.hs_rp,
                             L.hs_mid, L.hs_col, hs_vals<T>(L), dinv, b, (const T *)cur, out));
       cur = out;
     }

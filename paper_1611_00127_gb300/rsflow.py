@@ -74,7 +74,7 @@ class AmgParamsC(C.Structure):
                 ("coarse_n", C.c_int32), ("max_dense", C.c_int32), ("smoother", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("interp", C.c_int32),
                 ("num_functions", C.c_int32), ("precision", C.c_int32), ("chunk", C.c_int32),
-                ("agg_levels", C.c_int32)]
+                ("agg_levels", C.c_int32), ("chunk_coarse", C.c_int32)]
 
 
 class PrecParamsC(C.Structure):
@@ -255,11 +255,12 @@ class AmgParams:
     precision: int = FP32
     chunk: int = 512
     agg_levels: int = 0
+    chunk_coarse: int = 32
 
     def c(self):
         return AmgParamsC(self.theta, self.seed, self.max_levels, self.coarse_n, self.max_dense,
                           self.smoother, self.nu1, self.nu2, self.interp, self.num_functions,
-                          self.precision, self.chunk, self.agg_levels)
+                          self.precision, self.chunk, self.agg_levels, self.chunk_coarse)
 
 
 @dataclass

@@ -364,3 +364,23 @@ def test_gmres_3d_matches_oracle(R, oracle, inputs, prec):
         kind=1, decouple=2, amg=oracle.AmgParams(theta=0.5))), maxit=500)
     assert sto == 0
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-6
+
+
+@pytest.mark.parametrize("cc", [0, 64, 128])
+def test_coarse_chunk_option_matches_oracle(R, oracle, inputs, cc):
+    """The coarse-level chunk of the hybrid smoother (0: `chunk` on every
+    level): same colourings as the oracle, and the FP64 V-cycle within
+    1e-10, for scalar and point AMG."""
+    p = inputs.config_lognormal_2d(1e3, n=40)
+    u, uo = inputs.front_state(p)
+    Fo, Jo, (rp, col) = oracle.assemble(p, u, uo, inputs.DAY)
+    jrp, jc, jv = oracle.scalar_from_bsr2(rp, col, Jo).arrays()
+    for arp, ac, av, nf in ((*inputs.poisson_2d(50), 1), (jrp, jc, jv, 2)):
+        oh = oracle.Amg(oracle.Csr.from_arrays(arp, ac, av), oracle.AmgParams(num_functions=nf, chunk_coarse=cc))
+        gh = R.Amg.setup(R.Csr(arp, ac, av), R.AmgParams(num_functions=nf, chunk_coarse=cc, precision=R.FP64))
+        _hier_compare(gh, oh)
+        b = inputs.rhs_vector(arp.size - 1, 2)
+        x = torch.empty(arp.size - 1, dtype=torch.float64, device="cuda")
+        gh.apply(_dev(b), x)
+        xo = oh.vcycle(b)
+        np.testing.assert_allclose(x.cpu().numpy(), xo, rtol=1e-10, atol=1e-11 * np.abs(xo).max())

@@ -325,3 +325,43 @@ def test_chunk_colouring_valid_and_first_fit(oracle, inputs, which):
             earlier = set(col[nb[nb < i]])
             assert set(range(col[i])) <= earlier
     assert nc == col.max() + 1
+
+
+def test_coarse_levels_use_the_coarse_chunk(oracle, inputs):
+    """With chunk_coarse set, level 0 keeps `chunk` and every coarser level
+    is coloured and swept in chunks of chunk_coarse rows: its colouring is
+    valid and first fit within those chunks, and after one sweep from zero
+    the last-colour rows of each chunk satisfy their equations with the
+    sweep's values inside the chunk and zero outside."""
+    rp, c, v = inputs.poisson_2d(48)
+    A0 = sp.csr_matrix((v, c, rp))
+    H = oracle.Amg(oracle.Csr.from_scipy(A0), oracle.AmgParams(chunk=512, chunk_coarse=32, coarse_n=20))
+    Href = oracle.Amg(oracle.Csr.from_scipy(A0), oracle.AmgParams(chunk=512, chunk_coarse=0, coarse_n=20))
+    assert H.sizes() == Href.sizes() and H.nlevels >= 3
+    np.testing.assert_array_equal(H.colours(0)[0], Href.colours(0)[0])
+    for l in range(1, H.nlevels - 1):
+        A = H.A(l).scipy().tocsr()
+        col, nc = H.colours(l)
+        n = A.shape[0]
+        S = ((A + A.T) != 0).tocsr()
+        for c0 in range(0, n, 32):
+            c1 = min(c0 + 32, n)
+            for i in range(c0, c1):
+                nb = S.indices[S.indptr[i]:S.indptr[i + 1]]
+                nb = nb[(nb >= c0) & (nb < c1) & (nb != i)]
+                assert not np.any(col[nb] == col[i])
+                assert set(range(col[i])) <= set(col[nb[nb < i]])
+        rng = np.random.default_rng(l)
+        b = rng.standard_normal(n)
+        x = H.smooth(l, b, np.zeros(n))
+        checked = 0
+        for c0 in range(0, n, 32):
+            c1 = min(c0 + 32, n)
+            last = col[c0:c1].max()
+            xin = np.zeros(n)
+            xin[c0:c1] = x[c0:c1]
+            r = b - A @ xin
+            rows = [i for i in range(c0, c1) if col[i] == last]
+            np.testing.assert_allclose(r[rows], 0.0, atol=1e-10 * np.abs(b).max())
+            checked += len(rows)
+        assert checked > 0

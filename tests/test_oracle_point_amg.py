@@ -86,13 +86,13 @@ def test_point_hierarchy_structure(oracle, inputs):
 def test_point_amg_without_cross_coupling_is_scalar_amg_per_function(oracle, inputs):
     """Function 0 = 2D Poisson L, function 1 = 3 L, no coupling between them:
     the point hierarchy coarsens both like scalar AMG on L, and one point
-    V-cycle equals scalar V-cycles on L and on 3 L (chunks of 256 points
-    against scalar chunks of 256 rows)."""
+    V-cycle equals scalar V-cycles on L and on 3 L (chunks of 256 points,
+    32 on the coarse levels, against scalar chunks of as many rows)."""
     L = _poisson(inputs, 40)
     A = _interleave(L, 3.0 * L)
-    Hp = oracle.Amg(oracle.Csr.from_scipy(A), oracle.AmgParams(num_functions=2, chunk=512))
-    H0 = oracle.Amg(oracle.Csr.from_scipy(L), oracle.AmgParams(chunk=256))
-    H1 = oracle.Amg(oracle.Csr.from_scipy(sp.csr_matrix(3.0 * L)), oracle.AmgParams(chunk=256))
+    Hp = oracle.Amg(oracle.Csr.from_scipy(A), oracle.AmgParams(num_functions=2, chunk=512, chunk_coarse=64))
+    H0 = oracle.Amg(oracle.Csr.from_scipy(L), oracle.AmgParams(chunk=256, chunk_coarse=32))
+    H1 = oracle.Amg(oracle.Csr.from_scipy(sp.csr_matrix(3.0 * L)), oracle.AmgParams(chunk=256, chunk_coarse=32))
     assert Hp.sizes() == [2 * s for s in H0.sizes()]
     for l in range(H0.nlevels - 1):
         np.testing.assert_array_equal(Hp.cf(l)[0::2], H0.cf(l))
