@@ -184,6 +184,7 @@ struct Level {
   // diagonal blocks of the points (row-major, FP64 and FP32)
   int32_t nfun = 1;
   int32_t hgs_lpr = 0;               // lanes per row of the hybrid sweep (0: by rule)
+  int8_t xfer_lpr[3] = {0, 0, 0};    // lanes per row of residual, restriction, prolongation (0: by rule)
   double *binv = nullptr;
   float *binvf = nullptr;
   int32_t hs_nnz = 0;

@@ -582,6 +582,16 @@ static int pick_lpr(int32_t n, int32_t nnz) {
     default: { constexpr int L_ = 32; __VA_ARGS__; } break; \
   }
 
+// lanes per row of level L's transfer `which` (0 residual with A, 1
+// restriction with R, 2 prolongation with P): the autotuned choice, else the
+// rule above
+template <typename T>
+static int xfer_lpr(const Level &L, int which) {
+  if (L.xfer_lpr[which] > 0) return L.xfer_lpr[which];
+  const DCsr &M = which == 0 ? L.A : (which == 1 ? L.R : L.P);
+  return pick_lpr<T>(M.n, M.nnz);
+}
+
 template <typename T>
 static const T *vals(const DCsr &A);
 template <>
@@ -750,20 +760,20 @@ static T *cycle(const Hier &H, int32_t l, cudaStream_t s) {
     const Level &N = H.L[l + 1];
     T *r = static_cast<T *>(L.r);
     const double sz = sizeof(T);
-    const int lpr = pick_lpr<T>(L.A.n, L.A.nnz);
+    const int lpr = xfer_lpr<T>(L, 0);
     {
       ProfScope ps(kProfCsr, L.A.nnz * (4.0 + sz) + (L.A.n + 1) * 4.0 + 3.0 * L.A.n * sz, s);
       RS_LPR_SWITCH(lpr, RS_COUNTED launch_pdl(k_csr<T, L_, 1>, dim3(csr_grid(L.A.n, L_)), dim3(kBlock), 0, s,
                              L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), (const T *)cur, static_cast<const T *>(L.b), r));
     }
-    const int lr = pick_lpr<T>(L.R.n, L.R.nnz);
+    const int lr = xfer_lpr<T>(L, 1);
     {
       ProfScope ps(kProfCsr, L.R.nnz * (4.0 + sz) + (L.R.n + 1) * 4.0 + (L.R.n + L.A.n) * sz, s);
       RS_LPR_SWITCH(lr, RS_COUNTED launch_pdl(k_csr<T, L_, 0>, dim3(csr_grid(L.R.n, L_)), dim3(kBlock), 0, s,
                             L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), (const T *)r, (const T *)nullptr, static_cast<T *>(N.b)));
     }
     const T *xc = cycle<T>(H, l + 1, s);
-    const int lp = pick_lpr<T>(L.P.n, L.P.nnz);
+    const int lp = xfer_lpr<T>(L, 2);
     {
       ProfScope ps(kProfCsr, L.P.nnz * (4.0 + sz) + (L.P.n + 1) * 4.0 + (2.0 * L.P.n + L.R.n) * sz, s);
       RS_LPR_SWITCH(lp, RS_COUNTED launch_pdl(k_csr<T, L_, 2>, dim3(csr_grid(L.P.n, L_)), dim3(kBlock), 0, s,
@@ -800,17 +810,17 @@ static double level_xfer(const Hier &H, int32_t l, int which, int reps, cudaStre
   T *x = static_cast<T *>(L.x), *r = static_cast<T *>(L.r);
   for (int k = 0; k < reps; k++) {
     if (which == 0) {
-      const int lpr = pick_lpr<T>(L.A.n, L.A.nnz);
+      const int lpr = xfer_lpr<T>(L, 0);
       RS_LPR_SWITCH(lpr, RS_COUNTED launch_pdl(k_csr<T, L_, 1>, dim3(csr_grid(L.A.n, L_)), dim3(kBlock), 0,
                                                s, L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), (const T *)x,
                                                static_cast<const T *>(L.b), r));
     } else if (which == 1) {
-      const int lr = pick_lpr<T>(L.R.n, L.R.nnz);
+      const int lr = xfer_lpr<T>(L, 1);
       RS_LPR_SWITCH(lr, RS_COUNTED launch_pdl(k_csr<T, L_, 0>, dim3(csr_grid(L.R.n, L_)), dim3(kBlock), 0,
                                               s, L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), (const T *)r,
                                               (const T *)nullptr, static_cast<T *>(N.b)));
     } else {
-      const int lp = pick_lpr<T>(L.P.n, L.P.nnz);
+      const int lp = xfer_lpr<T>(L, 2);
       RS_LPR_SWITCH(lp, RS_COUNTED launch_pdl(k_csr<T, L_, 2>, dim3(csr_grid(L.P.n, L_)), dim3(kBlock), 0,
                                               s, L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P),
                                               (const T *)static_cast<T *>(N.x), (const T *)nullptr, x));
@@ -870,7 +880,69 @@ static int tune_level(const Hier &H, Level &L, cudaStream_t s) {
   return 0;
 }
 
+// Transfers, the same way: each level's residual, restriction and
+// prolongation time every lanes-per-row choice on the level's own vectors;
+// decisions are cached per (precision, transfer, log2 rows, log2 of 4x the
+// mean row length).
+static std::mutex g_xfer_tune_mu;
+static std::map<std::tuple<int, int, int, int>, int> g_xfer_tune;
+
+template <typename T>
+static int tune_xfer(Hier &H, int32_t l, int which, cudaStream_t s) {
+  static const int cand64[] = {1, 2, 4, 8}, cand32[] = {1, 2, 4, 8, 16};
+  const int *cand = sizeof(T) == 8 ? cand64 : cand32;
+  const int ncand = sizeof(T) == 8 ? 4 : 5;
+  Level &L = H.L[l];
+  cudaEvent_t e0, e1;
+  RS_CHECK_CUDA(cudaEventCreate(&e0));
+  RS_CHECK_CUDA(cudaEventCreate(&e1));
+  float best = 0.f;
+  int bestl = 0;
+  for (int k = 0; k < ncand; k++) {
+    L.xfer_lpr[which] = (int8_t)cand[k];
+    level_xfer<T>(H, l, which, 1, s);     // warm-up
+    RS_CHECK_CUDA(cudaEventRecord(e0, s));
+    level_xfer<T>(H, l, which, 4, s);
+    RS_CHECK_CUDA(cudaEventRecord(e1, s));
+    RS_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RS_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (bestl == 0 || ms < best) { best = ms; bestl = cand[k]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  L.xfer_lpr[which] = (int8_t)bestl;
+  return 0;
+}
+
+static int tune_transfers(Hier &H, cudaStream_t s) {
+  for (int32_t l = 0; l + 1 < H.nlev; l++) {
+    Level &L = H.L[l];
+    if (!L.P.rowptr || L.A.n == 0) continue;
+    for (int which = 0; which < 3; which++) {
+      const DCsr &M = which == 0 ? L.A : (which == 1 ? L.R : L.P);
+      if (M.n == 0) continue;
+      const auto key = std::make_tuple(H.precision, which, ilog2((double)M.n),
+                                       ilog2(4.0 * (double)M.nnz / (double)M.n));
+      {
+        std::lock_guard<std::mutex> lock(g_xfer_tune_mu);
+        auto it = g_xfer_tune.find(key);
+        if (it != g_xfer_tune.end()) {
+          L.xfer_lpr[which] = (int8_t)it->second;
+          continue;
+        }
+      }
+      RS_TRY(H.precision == RS_PREC_FP32 ? tune_xfer<float>(H, l, which, s) : tune_xfer<double>(H, l, which, s));
+      std::lock_guard<std::mutex> lock(g_xfer_tune_mu);
+      g_xfer_tune[key] = L.xfer_lpr[which];
+    }
+  }
+  RS_CHECK_CUDA(cudaGetLastError());
+  return 0;
+}
+
 int amg_tune_smoother(Hier &H, cudaStream_t s) {
+  RS_TRY(tune_transfers(H, s));
   if (H.prm.smoother != RS_SMOOTH_HYBRID) return 0;
   for (int32_t l = 0; l < H.nlev; l++) {
     Level &L = H.L[l];
