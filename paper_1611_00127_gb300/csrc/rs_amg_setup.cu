@@ -1585,6 +1585,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
   RS_TRY(sync_copy(&hrange, f32err, sizeof(int32_t), s));
   if (hrange)
     return fail(RS_ESETUP, "hierarchy values lie beyond the FP32 range; use an FP64 hierarchy (RS_PREC_FP64)");
+  RS_TRY(amg_tail_setup(H, s));
   return amg_tune_smoother(H, s);
 }
 
@@ -1625,6 +1626,9 @@ void amg_free(Hier &H, cudaStream_t s) {
   for (Level &L : H.L) level_free(L, s);
   H.L.clear();
   H.nlev = 0;
+  dfree(H.tail_d, s);
+  H.tail_d = nullptr;
+  H.tail_start = -1;
 }
 
 }  // namespace rs

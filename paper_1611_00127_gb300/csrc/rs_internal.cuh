@@ -196,6 +196,26 @@ struct Level {
   void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
 };
 
+// One level of the coarse tail (levels walked by a single cluster launch):
+// device pointers of the level's operators and vectors, both precisions.
+struct TailLevel {
+  int32_t n = 0, nchunk = 0, ncol = 0, nR = 0, nP = 0;
+  const int32_t *rp = nullptr, *col = nullptr;
+  const double *val = nullptr;
+  const float *valf = nullptr;
+  const int32_t *hrp = nullptr, *hmid = nullptr, *hcol = nullptr;
+  const double *hval = nullptr;
+  const float *hvalf = nullptr;
+  const double *dinv = nullptr, *binv = nullptr;
+  const float *dinvf = nullptr, *binvf = nullptr;
+  const int32_t *chunk_row0 = nullptr, *chunk_coff = nullptr, *chunk_rows = nullptr;
+  const int32_t *Rrp = nullptr, *Rcol = nullptr, *Prp = nullptr, *Pcol = nullptr;
+  const double *Rval = nullptr, *Pval = nullptr;
+  const float *Rvalf = nullptr, *Pvalf = nullptr;
+  void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
+  const double *cinv = nullptr;    // coarsest level: dense inverse, row-major
+};
+
 struct Hier {
   rs_amg_params prm;
   int32_t nlev = 0;
@@ -203,6 +223,9 @@ struct Hier {
   std::vector<Level> L;
   std::vector<int32_t> last_level;   // per system
   int precision = RS_PREC_FP32;
+  // coarse tail: levels tail_start.. run as one cluster launch (-1: none)
+  int32_t tail_start = -1;
+  TailLevel *tail_d = nullptr;
 };
 
 int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off, const rs_amg_params &prm,
@@ -216,6 +239,10 @@ int amg_level_xfer(const Hier &H, int32_t l, int which, int reps, double *bytes_
 // smoothed level's own vectors and stores the fastest in Level::hgs_lpr
 // (decisions cached per level shape). Not inside stream capture.
 int amg_tune_smoother(Hier &H, cudaStream_t s);
+// Chooses the coarse tail (the levels below prm.tail_rows rows, from the
+// first such level with a coarser one down to the dense coarsest level) and
+// uploads its descriptors; single-system hybrid-smoother hierarchies only.
+int amg_tail_setup(Hier &H, cudaStream_t s);
 // RS_ETIMEOUT (and clears the flag) if a smoother CTA gave up waiting for its
 // staging copies since the last call; synchronises the stream.
 int vcycle_wait_status(cudaStream_t s);

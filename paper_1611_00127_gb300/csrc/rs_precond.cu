@@ -348,6 +348,7 @@ static int check_params(const rs_amg_params &a) {
   if (a.agg_levels < 0 || a.agg_levels > 8) return fail(RS_EINVAL, "agg_levels outside [0, 8]");
   if (a.chunk_coarse != 0 && (a.chunk_coarse < 32 || a.chunk_coarse > 512))
     return fail(RS_EINVAL, "chunk_coarse outside [32, 512]");
+  if (a.tail_rows < 0) return fail(RS_EINVAL, "negative tail_rows");
   return 0;
 }
 
