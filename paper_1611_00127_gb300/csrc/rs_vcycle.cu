@@ -761,38 +761,66 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
 // phases (hardware barrier; every thread runs the same phase sequence).
 // Each phase computes what the per-level kernels compute:
 //  - sweep: hybrid Gauss-Seidel on the level's packed operator, one warp per
-//    chunk (chunks of at most kTailChunk rows), its start iterate and
-//    right-hand side less the couplings to other chunks staged in the warp's
-//    shared memory, the colours a __syncwarp apart; point mode solves each
-//    point's 2 x 2 block (a singular block keeps its values);
-//  - residual, restriction, prolongation: one thread per row;
+//    chunk (chunks of at most kTailChunk rows): the chunk's packed entries,
+//    start iterate and right-hand side less the couplings to other chunks
+//    staged in the warp's shared memory, the colours a __syncwarp apart;
+//    point mode solves each point's 2 x 2 block (a singular block keeps its
+//    values);
+//  - residual, restriction, prolongation: kTailLanes lanes per row;
 //  - coarsest level: x = A_c^{-1} b with the FP64 dense inverse.
 // Values written earlier in the launch are read with ld.global.cg (L2).
-constexpr int kTailThreads = 512;
+constexpr int kTailThreads = 256;     // 8 warps per CTA
 constexpr int kTailCtas = 8;
-constexpr int kTailChunk = 64;
+constexpr int kTailChunk = 64;        // longest chunk (rows) a warp sweeps
+constexpr int kTailStage = 768;       // packed entries of a chunk staged per warp
 constexpr int kTailMaxLevels = 24;
+constexpr int kTailLanes = 8;         // lanes per row of the tail's row loops
 
 template <typename T> __device__ __forceinline__ const T *tsel(const double *d, const float *f);
 template <> __device__ __forceinline__ const double *tsel<double>(const double *d, const float *) { return d; }
 template <> __device__ __forceinline__ const float *tsel<float>(const double *, const float *f) { return f; }
 
+// shared memory of one warp: staged packed entries (values, columns), the
+// chunk's start iterate and right-hand side, its row starts and split points
+template <typename T>
+__host__ __device__ constexpr size_t tail_warp_smem() {
+  return ((size_t)kTailStage * sizeof(T) + (size_t)kTailStage * sizeof(int32_t) + 2 * (size_t)kTailChunk * sizeof(T) +
+          (2 * (size_t)kTailChunk + 1) * sizeof(int32_t) + 15) & ~size_t(15);   // 16-byte multiple per warp
+}
+
 template <typename T, bool POINT>
 __device__ __forceinline__ void tail_sweep(const TailLevel &L, const T *xold, T *xnew, int gw, int nw, int lane,
-                                           T *sx, T *sr) {
+                                           unsigned char *ws) {
+  T *wv = reinterpret_cast<T *>(ws);
+  T *sx = wv + kTailStage;
+  T *sr = sx + kTailChunk;
+  int32_t *wc = reinterpret_cast<int32_t *>(sr + kTailChunk);
+  int32_t *lrp = wc + kTailStage;
+  int32_t *lmd = lrp + kTailChunk + 1;
   const T *b = static_cast<const T *>(L.b);
   const T *hv = tsel<T>(L.hval, L.hvalf);
   const int32_t ncol = L.ncol;
   for (int32_t k = gw; k < L.nchunk; k += nw) {
     const int32_t r0 = __ldg(L.chunk_row0 + 2 * k), r1 = __ldg(L.chunk_row0 + 2 * k + 1), len = r1 - r0;
-    for (int32_t i = lane; i < len; i += 32) {
-      const int32_t row = r0 + i;
-      sx[i] = xold ? __ldcg(xold + row) : T(0);
-      T acc = __ldcg(b + row);
-      if (xold) {
-        const int32_t e = __ldg(L.hrp + row + 1);
-        for (int32_t q = __ldg(L.hmid + row); q < e; q++) acc -= __ldg(hv + q) * __ldcg(xold + __ldg(L.hcol + q));
+    const int32_t p0 = __ldg(L.hrp + r0), np = __ldg(L.hrp + r1) - p0;
+    const bool staged = np <= kTailStage;
+    if (staged)
+      for (int32_t e = lane; e < np; e += 32) {
+        wv[e] = __ldg(hv + p0 + e);
+        wc[e] = __ldg(L.hcol + p0 + e);
       }
+    for (int32_t i = lane; i <= len; i += 32) lrp[i] = __ldg(L.hrp + r0 + i) - p0;
+    for (int32_t i = lane; i < len; i += 32) {
+      lmd[i] = __ldg(L.hmid + r0 + i) - p0;
+      sx[i] = xold ? __ldcg(xold + r0 + i) : T(0);
+    }
+    __syncwarp();
+    const int32_t *pc = staged ? wc : L.hcol + p0;
+    const T *pv = staged ? wv : hv + p0;
+    for (int32_t i = lane; i < len; i += 32) {
+      T acc = __ldcg(b + r0 + i);
+      if (xold)
+        for (int32_t q = lmd[i]; q < lrp[i + 1]; q++) acc -= pv[q] * __ldcg(xold + pc[q]);
       sr[i] = acc;
     }
     __syncwarp();
@@ -801,21 +829,19 @@ __device__ __forceinline__ void tail_sweep(const TailLevel &L, const T *xold, T 
       const int32_t beg = __ldg(cof + c), end = __ldg(cof + c + 1);
       for (int32_t pos = beg + lane; pos < end; pos += 32) {
         if (!POINT) {
-          const int32_t li = __ldg(L.chunk_rows + r0 + pos), row = r0 + li;
+          const int32_t li = __ldg(L.chunk_rows + r0 + pos);
           T acc = sr[li];
-          const int32_t m = __ldg(L.hmid + row);
-          for (int32_t q = __ldg(L.hrp + row); q < m; q++) acc -= __ldg(hv + q) * sx[__ldg(L.hcol + q)];
-          const T di = __ldg(tsel<T>(L.dinv, L.dinvf) + row);
+          for (int32_t q = lrp[li]; q < lmd[li]; q++) acc -= pv[q] * sx[pc[q]];
+          const T di = __ldg(tsel<T>(L.dinv, L.dinvf) + r0 + li);
           if (di != T(0)) sx[li] = acc * di;
         } else {
           const int32_t li = __ldg(L.chunk_rows + r0 / 2 + pos);
           T acc[2];
 #pragma unroll
           for (int f = 0; f < 2; f++) {
-            const int32_t lr = 2 * li + f, row = r0 + lr;
+            const int32_t lr = 2 * li + f;
             T a = sr[lr];
-            const int32_t m = __ldg(L.hmid + row);
-            for (int32_t q = __ldg(L.hrp + row); q < m; q++) a -= __ldg(hv + q) * sx[__ldg(L.hcol + q)];
+            for (int32_t q = lrp[lr]; q < lmd[lr]; q++) a -= pv[q] * sx[pc[q]];
             acc[f] = a;
           }
           const T *mi = tsel<T>(L.binv, L.binvf) + 4 * ((int64_t)r0 / 2 + li);
@@ -833,17 +859,27 @@ __device__ __forceinline__ void tail_sweep(const TailLevel &L, const T *xold, T 
   }
 }
 
-// y = b - A x (MODE 1), y = A x (MODE 0), y += A x (MODE 2), a thread per row
+// y = b - A x (MODE 1), y = A x (MODE 0), y += A x (MODE 2); kTailLanes lanes
+// per row, rows taken in a loop whose trip count is uniform over each warp
 template <typename T, int MODE>
 __device__ __forceinline__ void tail_csr(int32_t n, const int32_t *rp, const int32_t *col, const T *val, const T *x,
                                          const T *b, T *y, int64_t gt, int64_t nthr) {
-  for (int64_t i = gt; i < n; i += nthr) {
+  const int64_t gid = gt / kTailLanes, ng = nthr / kTailLanes;
+  const int ln = (int)(gt % kTailLanes);
+  for (int64_t base = 0; base < n; base += ng) {
+    const int64_t i = base + gid;
     T s = T(0);
-    const int32_t e = __ldg(rp + i + 1);
-    for (int32_t k = __ldg(rp + i); k < e; k++) s += __ldg(val + k) * __ldcg(x + __ldg(col + k));
-    if (MODE == 0) y[i] = s;
-    else if (MODE == 1) y[i] = __ldcg(b + i) - s;
-    else y[i] = __ldcg(y + i) + s;
+    if (i < n) {
+      const int32_t e = __ldg(rp + i + 1);
+      for (int32_t k = __ldg(rp + i) + ln; k < e; k += kTailLanes) s += __ldg(val + k) * __ldcg(x + __ldg(col + k));
+    }
+#pragma unroll
+    for (int o = kTailLanes / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, kTailLanes);
+    if (i < n && ln == 0) {
+      if (MODE == 0) y[i] = s;
+      else if (MODE == 1) y[i] = __ldcg(b + i) - s;
+      else y[i] = __ldcg(y + i) + s;
+    }
   }
 }
 
@@ -855,8 +891,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel *__res
   const int64_t nthr = (int64_t)cl.num_blocks() * blockDim.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = (int)cl.block_rank() * (blockDim.x >> 5) + warp, nw = (int)cl.num_blocks() * (blockDim.x >> 5);
-  __shared__ T sx[kTailThreads / 32][kTailChunk];
-  __shared__ T sr[kTailThreads / 32][kTailChunk];
+  extern __shared__ __align__(16) unsigned char tsm[];
+  unsigned char *ws = tsm + (size_t)warp * tail_warp_smem<T>();
   T *cur[kTailMaxLevels];
   for (int32_t l = 0; l + 1 < nl; l++) {
     const TailLevel &L = tl[l];
@@ -864,7 +900,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel *__res
     T *c = nullptr;
     for (int32_t sw = 0; sw < nu1; sw++) {
       T *out = (c == xa) ? xb : xa;
-      tail_sweep<T, POINT>(L, c, out, gw, nw, lane, sx[warp], sr[warp]);
+      tail_sweep<T, POINT>(L, c, out, gw, nw, lane, ws);
       cl.sync();
       c = out;
     }
@@ -882,14 +918,22 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel *__res
     cl.sync();
   }
   {
+    // coarsest level: x = A_c^{-1} b, FP64, kTailLanes lanes per row
     const TailLevel &L = tl[nl - 1];
     T *x = static_cast<T *>(L.x);
     const T *b = static_cast<const T *>(L.b);
-    for (int64_t i = gt; i < L.n; i += nthr) {
-      const double *a = L.cinv + i * (int64_t)L.n;
+    const int64_t gid = gt / kTailLanes, ng = nthr / kTailLanes;
+    const int ln = (int)(gt % kTailLanes);
+    for (int64_t base = 0; base < L.n; base += ng) {
+      const int64_t i = base + gid;
       double s = 0.0;
-      for (int32_t j = 0; j < L.n; j++) s = fma(__ldg(a + j), (double)__ldcg(b + j), s);
-      x[i] = (T)s;
+      if (i < L.n) {
+        const double *a = L.cinv + i * (int64_t)L.n;
+        for (int32_t j = ln; j < L.n; j += kTailLanes) s = fma(__ldg(a + j), (double)__ldcg(b + j), s);
+      }
+#pragma unroll
+      for (int o = kTailLanes / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, kTailLanes);
+      if (i < L.n && ln == 0) x[i] = (T)s;
     }
     cl.sync();
     cur[nl - 1] = x;
@@ -902,12 +946,21 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel *__res
     cl.sync();
     for (int32_t sw = 0; sw < nu2; sw++) {
       T *out = (c == xa) ? xb : xa;
-      tail_sweep<T, POINT>(L, c, out, gw, nw, lane, sx[warp], sr[warp]);
+      tail_sweep<T, POINT>(L, c, out, gw, nw, lane, ws);
       cl.sync();
       c = out;
     }
     cur[l] = c;
   }
+}
+
+template <typename T, bool POINT>
+static void tail_attr() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_tail<T, POINT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(tail_warp_smem<T>() * (kTailThreads / 32)));
+  done = true;
 }
 
 // the buffer holding level l's iterate after `sweeps` sweeps from `c`
@@ -922,6 +975,7 @@ static T *tail_cycle(const Hier &H, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kTailCtas, 1, 1);
   cfg.blockDim = dim3(kTailThreads, 1, 1);
+  cfg.dynamicSmemBytes = tail_warp_smem<T>() * (kTailThreads / 32);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -933,10 +987,13 @@ static T *tail_cycle(const Hier &H, cudaStream_t s) {
   count_launch();
   const int32_t nu1 = H.prm.nu1, nu2 = H.prm.nu2;
   ProfScope ps(kProfOther, 0.0, s);
-  if (H.L[t].nfun == 2)
+  if (H.L[t].nfun == 2) {
+    tail_attr<T, true>();
     cudaLaunchKernelEx(&cfg, k_tail<T, true>, (const TailLevel *)H.tail_d, nl, nu1, nu2);
-  else
+  } else {
+    tail_attr<T, false>();
     cudaLaunchKernelEx(&cfg, k_tail<T, false>, (const TailLevel *)H.tail_d, nl, nu1, nu2);
+  }
   // the same buffer sequence as the kernel's: nu1 sweeps from zero (or the
   // zero-filled x), then nu2 more after the prolongation
   const Level &L = H.L[t];
