@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     return ap.parse_args()
 
 
@@ -411,6 +412,69 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def ensemble_bench(maxit):
+    """The 96-member ensemble (2D grids with sides 64..512, each its own
+    log-normal field; one Jacobian each at the front state): CPR-AMG(1)
+    FGMRES to 1e-8, timed (set-up + solve, L2 flushed before each form) as
+    (a) 96 single-system solves with FP64 V-cycles one after another and
+    (b) one batched solve with FP32 V-cycles: one set-up and one FGMRES call
+    over the 96 stacked systems. One untimed run of each form first."""
+    import torch
+    from paper_1611_00127_gb300 import inputs as I
+    from paper_1611_00127_gb300 import rsflow as R
+    probs = I.config_ensemble()
+    states = [I.front_state(p) for p in probs]
+    singles = []
+    for p, (u, uo) in zip(probs, states):
+        dp = R.DeviceProblems(p)
+        J = R.Bsr2.pattern(dp)
+        F = torch.empty(2 * p.ncell, dtype=torch.float64, device="cuda")
+        R.jacobian_assemble(dp, torch.as_tensor(u, device="cuda"), torch.as_tensor(uo, device="cuda"), I.DAY, J, F)
+        singles.append((J, F))
+    dpb = R.DeviceProblems(probs)
+    Jb = R.Bsr2.pattern(dpb)
+    Fb = torch.empty(2 * dpb.ncell, dtype=torch.float64, device="cuda")
+    R.jacobian_assemble(dpb, torch.as_tensor(np.concatenate([s[0] for s in states]), device="cuda"),
+                        torch.as_tensor(np.concatenate([s[1] for s in states]), device="cuda"), I.DAY, Jb, Fb)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    gp = R.GmresParams(maxit=maxit)
+
+    def single_run():
+        conv = 0
+        for J, F in singles:
+            M = R.Precond(J, R.PrecParams(kind=R.CPR1, amg=R.AmgParams(precision=R.FP64)))
+            x = torch.zeros_like(F)
+            st = R.gmres_solve(J, M, -F, x, gp)
+            conv += int(st.converged)
+            M.close()
+        return conv
+
+    def batched_run():
+        M = R.Precond(Jb, R.PrecParams(kind=R.CPR1, amg=R.AmgParams(precision=R.FP32)))
+        x = torch.zeros_like(Fb)
+        st = R.gmres_solve(Jb, M, -Fb, x, gp)
+        M.close()
+        return int(st.converged)
+
+    out = {}
+    for name, fn in (("fp64_single", single_run), ("fp32_batched", batched_run)):
+        fn()
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        conv = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = dict(ms=ms, converged=conv, solves_per_s=conv / (ms * 1e-3) if ms > 0 else None)
+    f64, f32 = out["fp64_single"], out["fp32_batched"]
+    return dict(members=len(probs), cells=int(dpb.ncell), preconditioner="CPR-AMG(1), quasi-IMPES",
+                fp64_single=f64, fp32_batched=f32,
+                speedup=(f32["solves_per_s"] / f64["solves_per_s"]) if f64["solves_per_s"] else None,
+                how="set-up + FGMRES to 1e-8, CUDA events, L2 flushed before each timed form")
+
+
 def reduce_over_ranks(times_ms, converged, dist, device):
     """Whole-job figures of a replicated step: the slowest rank's times (MAX)
     and the converged solves of all ranks (SUM). With dist None (one
@@ -513,6 +577,7 @@ def main():
                 bytes_per_launch=rl["spmv_bytes"])
     kernel_profile = {k: dict(ms=v[0], gbs=(v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else 0.0), launches=v[2])
                       for k, v in prof.items() if v[2] > 0}
+    ensemble = None if args.no_ensemble else ensemble_bench(args.maxit)
     cpu = None if args.no_cpu_baseline else oracle_sample(probs, states, args.maxit)
     warmup_launch_note = "counted over warm-up + timed steps / (warm-up + timed)"
     line = dict(
@@ -533,6 +598,7 @@ def main():
         clocks=clk.summary(),
         roofline=roofline,
         roofline_large=roofline_large,
+        ensemble=ensemble,
         bsr2_spmv=spmv,
         kernel_profile=dict(note="one eager profiled step, CUDA events per launch (includes launch gaps)",
                             classes=kernel_profile,
