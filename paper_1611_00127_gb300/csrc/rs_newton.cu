@@ -41,6 +41,7 @@ extern "C" int newton_step(const rs_problem *probs, int32_t nprob, double *u, co
   rs_bsr2 J{nb, (int32_t)nnzb, rowptr, col, val, nprob, off.data()};
   rs_newton_stats st{};
   int status = RS_NOT_CONVERGED;
+  bool nonfinite = false;   // the residual became NaN or infinite: the step failed
   int k = 0;
   for (;; k++) {
     auto t0 = std::chrono::steady_clock::now();
@@ -51,7 +52,7 @@ extern "C" int newton_step(const rs_problem *probs, int32_t nprob, double *u, co
     st.fnorm = fn;
     if (fn <= params->ftol) { status = RS_OK; break; }
     if (k >= params->max_newton) break;
-    if (!std::isfinite(fn)) { st.newton_its = k; k = -1; break; }
+    if (!std::isfinite(fn)) { nonfinite = true; break; }
     RS_CHECK_CUDA(cudaMemsetAsync(du, 0, sizeof(double) * 2 * (size_t)nb, s));
     t0 = std::chrono::steady_clock::now();
     rs_precond *M = nullptr;
@@ -70,7 +71,7 @@ extern "C" int newton_step(const rs_problem *probs, int32_t nprob, double *u, co
     // u -= du (du solves J du = F)
     RS_TRY(newton_update(probs, nprob, du, -1.0, params->max_ds, u, s));
   }
-  if (k >= 0 && (status == RS_OK || k >= params->max_newton)) st.newton_its = k;
+  if (nonfinite || status == RS_OK || k >= params->max_newton) st.newton_its = k;
   if (stats) *stats = st;
   RS_CHECK_CUDA(cudaStreamSynchronize(s));
   return status;
