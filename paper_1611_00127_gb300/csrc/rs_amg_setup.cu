@@ -1212,7 +1212,8 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     Scratch sc(s);
     int32_t *seg = nullptr, *dseg_off = nullptr;
     RS_TRY(seg_ids(L.seg_off, n, &seg, s));
-    sc.ptrs.push_back(seg);
+    if (nseg > 1) L.row_seg = seg;     // kept for the V-cycle's retired-system test
+    else sc.ptrs.push_back(seg);
     RS_TRY(upload(&dseg_off, L.seg_off, s));
     sc.ptrs.push_back(dseg_off);
     // which systems still coarsen
@@ -1420,7 +1421,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         RS_COUNTED k_gather_offsets<<<grid_for(nseg + 1), kBlock, 0, s>>>(nseg + 1, dseg_off, Lc.A.rowptr, tmp);
         RS_TRY(sync_copy(rpb.data(), tmp, sizeof(int32_t) * (nseg + 1), s));
       }
-      std::vector<int32_t> packed;
+      std::vector<int32_t> packed, csys;
       int32_t nsm = 0;
       const int32_t C0 = (l == 0 || prm.chunk_coarse <= 0) ? prm.chunk : prm.chunk_coarse;
       Lc.chunk_c = 0;
@@ -1433,6 +1434,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         Lc.chunk_c = std::max(Lc.chunk_c, C);
         for (int32_t r = Lc.seg_off[q]; r < Lc.seg_off[q + 1]; r += C) {
           packed.push_back(r);
+          csys.push_back(q);
           packed.push_back(std::min(r + C, Lc.seg_off[q + 1]));
         }
         nsm += (int32_t)nq;
@@ -1440,6 +1442,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       Lc.nchunk = (int32_t)(packed.size() / 2);
       Lc.nsmooth = nsm;
       RS_TRY(upload(&Lc.chunk_row0, packed, s));
+      if (nseg > 1 && !csys.empty()) RS_TRY(upload(&Lc.chunk_sys, csys, s));
       RS_TRY(dalloc_n(&Lc.colour, (size_t)n, s));
       int32_t *cc = nullptr;   // max colour, error flag, largest chunk
       RS_TRY(sc.get(&cc, 3));
@@ -1504,6 +1507,11 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       RS_TRY(upload(&Lc.cinv_off, ioff, s));
       RS_TRY(upload(&Lc.crows, rows, s));
       RS_TRY(upload(&Lc.crow_seg, rowseg, s));
+      if (nseg > 1) {
+        std::vector<int32_t> rsys(rowseg.size());
+        for (size_t t = 0; t < rowseg.size(); t++) rsys[t] = Lc.cseg[rowseg[t]];
+        RS_TRY(upload(&Lc.crow_sys, rsys, s));
+      }
       RS_TRY(dalloc_n(&Lc.cinv, (size_t)inv_tot, s));
       int32_t maxng = 0;
       for (const int4 &in : info) maxng = std::max(maxng, in.y);
@@ -1619,6 +1627,9 @@ static void level_free(Level &L, cudaStream_t s) {
     dfree(L.b, s);
     dfree(L.r, s);
     dfree(L.t, s);
+    dfree(L.row_seg, s);
+    dfree(L.chunk_sys, s);
+    dfree(L.crow_sys, s);
   }
 }
 

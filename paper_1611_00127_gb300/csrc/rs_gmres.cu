@@ -18,6 +18,7 @@
 
 namespace rs {
 int precond_apply_impl(const rs_precond *M, const double *r, double *z, cudaStream_t s);
+int precond_set_active(const rs_precond *M, const uint8_t *active, cudaStream_t s);
 }
 using namespace rs;
 
@@ -405,7 +406,10 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
     if (nch > 0) RS_COUNTED k_scale<<<nch, kRedThreads, 0, s>>>(dch, nrm, V, V, nullptr);
     for (int j = 0; j < m; j++) {
       double *vj = V + (int64_t)j * n, *zj = Z + (int64_t)j * n, *w = V + (int64_t)(j + 1) * n;
-      if (M) rc = precond_apply_impl(M, vj, zj, s);
+      // retired systems (converged or out of iterations in this cycle) are
+      // skipped by the preconditioner's V-cycles
+      if (M && nseg > 1) rc = precond_set_active(M, active, s);
+      if (M && !rc) rc = precond_apply_impl(M, vj, zj, s);
       else RS_CHECK_CUDA(cudaMemcpyAsync(zj, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       if (rc) break;
       rc = launch_bsr2_spmv(*J, zj, w, s);

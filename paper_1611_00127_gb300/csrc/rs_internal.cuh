@@ -185,6 +185,9 @@ struct Level {
   int32_t nfun = 1;
   int32_t hgs_lpr = 0;               // lanes per row of the hybrid sweep (0: by rule)
   int8_t xfer_lpr[3] = {0, 0, 0};    // lanes per row of residual, restriction, prolongation (0: by rule)
+  // batches only (nullptr for one system): the system of every row, of every
+  // smoother chunk and of every row solved directly here
+  int32_t *row_seg = nullptr, *chunk_sys = nullptr, *crow_sys = nullptr;
   double *binv = nullptr;
   float *binvf = nullptr;
   int32_t hs_nnz = 0;
@@ -223,6 +226,10 @@ struct Hier {
   std::vector<Level> L;
   std::vector<int32_t> last_level;   // per system
   int precision = RS_PREC_FP32;
+  // batches: per-system flags (nseg bytes, device; nullptr: every system
+  // live). A V-cycle writes zeros for the rows of a system whose flag is 0
+  // instead of computing them -- FGMRES retires converged systems this way.
+  const uint8_t *active = nullptr;
   // coarse tail: levels tail_start.. run as one cluster launch (-1: none)
   int32_t tail_start = -1;
   TailLevel *tail_d = nullptr;

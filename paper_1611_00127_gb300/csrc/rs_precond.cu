@@ -33,6 +33,7 @@ struct rs_precond {
   double *dinv = nullptr;          // ABF D^{-1} blocks [4 nb]
   double *p1inv = nullptr;         // P1^{-1} blocks [4 nb] (point-block Jacobi)
   rs_ilu0 *ilu = nullptr;          // P1 = ILU(0) of W J
+  uint8_t *act = nullptr;          // batches: per-system live flags read by the V-cycles (1 = live)
   Hier Hp, Hs, Hj;
   bool has_p = false, has_s = false, has_j = false;
   DCsr Aps;                        // BF coupling block
@@ -153,6 +154,11 @@ int build(rs_precond *M, cudaStream_t s) {
   const rs_precond_params &p = M->prm;
   const int kind = p.kind;
   if (nb == 0) return 0;   // empty system: applying M is a no-op
+  const int32_t nseg = (int32_t)M->seg_off.size() - 1;
+  if (nseg > 1) {
+    RS_TRY(dalloc_n(&M->act, (size_t)nseg, s));
+    RS_CHECK_CUDA(cudaMemsetAsync(M->act, 1, (size_t)nseg, s));
+  }
   RS_TRY(dalloc_n(&M->rt, 2 * (size_t)nb, s));
   RS_TRY(dalloc_n(&M->sb, (size_t)nb, s));
   RS_TRY(dalloc_n(&M->ss, (size_t)nb, s));
@@ -169,6 +175,7 @@ int build(rs_precond *M, cudaStream_t s) {
     dcsr_free(A, s);
     if (r) return r;
     M->has_j = true;
+    M->Hj.active = M->act;
     return 0;
   }
   if (kind == RS_PC_CPR1 || kind == RS_PC_CPR2) {
@@ -198,6 +205,7 @@ int build(rs_precond *M, cudaStream_t s) {
     dcsr_free(App, s);
     if (r) return r;
     M->has_p = true;
+    M->Hp.active = M->act;
     if (kind == RS_PC_CPR2) {
       DCsr Ass;
       RS_TRY(bsr2_part(Jt, 1, 1, Ass, s));
@@ -205,6 +213,7 @@ int build(rs_precond *M, cudaStream_t s) {
       dcsr_free(Ass, s);
       if (r) return r;
       M->has_s = true;
+      M->Hs.active = M->act;
     }
     RS_CHECK_CUDA(cudaStreamSynchronize(s));
     return 0;
@@ -217,8 +226,8 @@ int build(rs_precond *M, cudaStream_t s) {
   RS_TRY(bsr2_part(J, 1, 1, Ass, s));
   int r = simple_schur(App, M->Aps, Asp, Ass, S, s);
   if (!r) r = amg_build(Ass, M->seg_off, p.amg, M->Hs, s);
-  if (!r) { M->has_s = true; r = amg_build(S, M->seg_off, p.amg, M->Hp, s); }
-  if (!r) M->has_p = true;
+  if (!r) { M->has_s = true; M->Hs.active = M->act; r = amg_build(S, M->seg_off, p.amg, M->Hp, s); }
+  if (!r) { M->has_p = true; M->Hp.active = M->act; }
   dcsr_free(App, s);
   dcsr_free(Asp, s);
   dcsr_free(Ass, s);
@@ -240,6 +249,7 @@ void destroy(rs_precond *M) {
   dfree(M->qw, s);
   dfree(M->dinv, s);
   dfree(M->p1inv, s);
+  dfree(M->act, s);
   ilu0_free(M->ilu);
   dfree(M->rt, s);
   dfree(M->sb, s);
@@ -290,6 +300,14 @@ static int apply_body(const rs_precond *M, const double *r, double *z, cudaStrea
       return 0;
     }
   }
+}
+
+// Batches: the V-cycles of the next applies skip (write zeros for) the
+// systems whose flag in `active` (nseg bytes, device) is 0.
+int precond_set_active(const rs_precond *M, const uint8_t *active, cudaStream_t s) {
+  if (!M->act || !active) return 0;
+  RS_CHECK_CUDA(cudaMemcpyAsync(M->act, active, M->seg_off.size() - 1, cudaMemcpyDeviceToDevice, s));
+  return 0;
 }
 
 int precond_apply_impl(const rs_precond *Mc, const double *r, double *z, cudaStream_t s) {

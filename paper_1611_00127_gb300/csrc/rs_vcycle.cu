@@ -136,8 +136,14 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs(const int32_t *__restrict__
                                              const int32_t *__restrict__ hmid, const int32_t *__restrict__ hcol,
                                              const T *__restrict__ hval, const T *__restrict__ dinv,
                                              const T *__restrict__ b, const T *__restrict__ xold,
-                                             T *__restrict__ xnew) {
+                                             T *__restrict__ xnew, const uint8_t *__restrict__ act,
+                                             const int32_t *__restrict__ csys) {
   RS_PDL_ENTRY();
+  if (act && !act[csys[blockIdx.x]]) {   // a retired system of a batch: zeros
+    const int32_t q0 = __ldg(cr + 2 * blockIdx.x), q1 = __ldg(cr + 2 * blockIdx.x + 1);
+    for (int32_t t = q0 + threadIdx.x; t < q1; t += blockDim.x) xnew[t] = T(0);
+    return;
+  }
   // entries of the out-of-chunk pass in flight per lane: four for FP32; two
   // for FP64, where every issued FMA costs FP64-pipe time even for lanes
   // past their row's end (rows of 7-point levels have two or three such
@@ -305,8 +311,14 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs2(const int32_t *__restrict_
                                               const int32_t *__restrict__ hmid, const int32_t *__restrict__ hcol,
                                               const T *__restrict__ hval, const T *__restrict__ binv,
                                               const T *__restrict__ b, const T *__restrict__ xold,
-                                              T *__restrict__ xnew) {
+                                              T *__restrict__ xnew, const uint8_t *__restrict__ act,
+                                              const int32_t *__restrict__ csys) {
   RS_PDL_ENTRY();
+  if (act && !act[csys[blockIdx.x]]) {   // a retired system of a batch: zeros
+    const int32_t q0 = __ldg(cr + 2 * blockIdx.x), q1 = __ldg(cr + 2 * blockIdx.x + 1);
+    for (int32_t t = q0 + threadIdx.x; t < q1; t += blockDim.x) xnew[t] = T(0);
+    return;
+  }
   // entries of the out-of-chunk pass in flight per lane: four for FP32; two
   // for FP64, where every issued FMA costs FP64-pipe time even for lanes
   // past their row's end (rows of 7-point levels have two or three such
@@ -497,26 +509,30 @@ __global__ void k_jacobi_update(int32_t nrows, const int32_t *__restrict__ rows,
 // Groups of LPR lanes take rows in a grid-stride loop (the grid is capped at
 // a few CTAs per SM, so large levels do not pay for tens of thousands of
 // short-lived CTAs); the trip count is uniform across each warp.
+// Batches: with `act`, the rows of a system whose flag is 0 get y = 0 (modes
+// 0 and 1) or keep y (mode 2) without their sums being formed.
 template <typename T, int LPR, int MODE>
 __global__ void __launch_bounds__(256) k_csr(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
                                              const T *__restrict__ val, const T *__restrict__ x,
-                                             const T *__restrict__ b, T *__restrict__ y) {
+                                             const T *__restrict__ b, T *__restrict__ y,
+                                             const uint8_t *__restrict__ act, const int32_t *__restrict__ rseg) {
   RS_PDL_ENTRY();
   const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / LPR;
   const int lane = threadIdx.x % LPR;
   for (int64_t base = 0; base < n; base += groups) {
     const int64_t i = base + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
+    const bool live = i < n && (act == nullptr || act[rseg[i]]);
     T s = T(0);
-    if (i < n) {
+    if (live) {
       const int32_t e = __ldg(rp + i + 1);
       for (int32_t k = __ldg(rp + i) + lane; k < e; k += LPR) s += __ldg(val + k) * __ldg(x + __ldg(col + k));
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, LPR);
     if (i < n && lane == 0) {
-      if (MODE == 0) y[i] = s;                 // y = A x
-      else if (MODE == 1) y[i] = b[i] - s;     // y = b - A x
-      else y[i] += s;                          // y += A x
+      if (MODE == 0) y[i] = live ? s : T(0);                 // y = A x
+      else if (MODE == 1) y[i] = live ? b[i] - s : T(0);     // y = b - A x
+      else if (live) y[i] += s;                              // y += A x
     }
   }
 }
@@ -532,12 +548,17 @@ static unsigned csr_grid(int64_t n, int lpr) {
 template <typename T>
 __global__ void k_coarse_solve(int32_t nrows, const int32_t *__restrict__ crows, const int32_t *__restrict__ crow_seg,
                                const int4 *__restrict__ info, const int64_t *__restrict__ inv_off,
-                               const double *__restrict__ inv, const T *__restrict__ b, T *__restrict__ x) {
+                               const double *__restrict__ inv, const T *__restrict__ b, T *__restrict__ x,
+                               const uint8_t *__restrict__ act, const int32_t *__restrict__ crow_sys) {
   RS_PDL_ENTRY();
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= nrows) return;
   const int32_t row = crows[w];
+  if (act && !act[crow_sys[w]]) {   // a retired system of a batch
+    if (lane == 0) x[row] = T(0);
+    return;
+  }
   const int32_t q = crow_seg[w];
   const int4 in = info[q];
   const int32_t r0 = in.x, n = in.y;
@@ -711,7 +732,8 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
         ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);
         RS_LPR_SWITCH(hl, hgs2_attr<T, L_>(); RS_COUNTED launch_pdl(k_hgs2<T, L_>, dim3(L.nchunk), dim3(kHgsThreads),
                               shm2, s, L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, cmax, stage,
-                              L.hs_rp, L.hs_mid, L.hs_col, hs_vals<T>(L), binv_of<T>(L), b, (const T *)cur, out));
+                              L.hs_rp, L.hs_mid, L.hs_col, hs_vals<T>(L), binv_of<T>(L), b, (const T *)cur, out,
+                              H.active, (const int32_t *)L.chunk_sys));
         cur = out;
       }
       return;
@@ -721,7 +743,8 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
       ProfScope ps(kProfHgs, hgs_bytes(ns, nz, sizeof(T), cur != nullptr), s);
       RS_LPR_SWITCH(hl, hgs_attr<T, L_>(); RS_COUNTED launch_pdl(k_hgs<T, L_>, dim3(L.nchunk), dim3(kHgsThreads), shm, s,
                             L.chunk_row0, L.chunk_coff, L.chunk_rows, L.ncolour, cmax, stage, L.hs_rp,
-                            L.hs_mid, L.hs_col, hs_vals<T>(L), dinv, b, (const T *)cur, out));
+                            L.hs_mid, L.hs_col, hs_vals<T>(L), dinv, b, (const T *)cur, out, H.active,
+                            (const int32_t *)L.chunk_sys));
       cur = out;
     }
     return;
@@ -1061,27 +1084,31 @@ static T *cycle(const Hier &H, int32_t l, cudaStream_t s) {
     {
       ProfScope ps(kProfCsr, L.A.nnz * (4.0 + sz) + (L.A.n + 1) * 4.0 + 3.0 * L.A.n * sz, s);
       RS_LPR_SWITCH(lpr, RS_COUNTED launch_pdl(k_csr<T, L_, 1>, dim3(csr_grid(L.A.n, L_)), dim3(kBlock), 0, s,
-                             L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), (const T *)cur, static_cast<const T *>(L.b), r));
+                             L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), (const T *)cur, static_cast<const T *>(L.b), r,
+                             H.active, (const int32_t *)L.row_seg));
     }
     const int lr = xfer_lpr<T>(L, 1);
     {
       ProfScope ps(kProfCsr, L.R.nnz * (4.0 + sz) + (L.R.n + 1) * 4.0 + (L.R.n + L.A.n) * sz, s);
       RS_LPR_SWITCH(lr, RS_COUNTED launch_pdl(k_csr<T, L_, 0>, dim3(csr_grid(L.R.n, L_)), dim3(kBlock), 0, s,
-                            L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), (const T *)r, (const T *)nullptr, static_cast<T *>(N.b)));
+                            L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), (const T *)r, (const T *)nullptr, static_cast<T *>(N.b),
+                            H.active, (const int32_t *)N.row_seg));
     }
     const T *xc = cycle<T>(H, l + 1, s);
     const int lp = xfer_lpr<T>(L, 2);
     {
       ProfScope ps(kProfCsr, L.P.nnz * (4.0 + sz) + (L.P.n + 1) * 4.0 + (2.0 * L.P.n + L.R.n) * sz, s);
       RS_LPR_SWITCH(lp, RS_COUNTED launch_pdl(k_csr<T, L_, 2>, dim3(csr_grid(L.P.n, L_)), dim3(kBlock), 0, s,
-                            L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P), xc, (const T *)nullptr, cur));
+                            L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P), xc, (const T *)nullptr, cur, H.active,
+                            (const int32_t *)L.row_seg));
     }
   }
   smooth<T>(H, L, H.prm.nu2, cur, s);
   if (L.ncoarse_rows > 0) {
     RS_COUNTED launch_pdl(k_coarse_solve<T>, dim3(grid_for((int64_t)L.ncoarse_rows * 32)), dim3(kBlock), 0, s,
         L.ncoarse_rows, (const int32_t *)L.crows, (const int32_t *)L.crow_seg, (const int4 *)L.cinfo,
-        (const int64_t *)L.cinv_off, (const double *)L.cinv, static_cast<const T *>(L.b), cur);
+        (const int64_t *)L.cinv_off, (const double *)L.cinv, static_cast<const T *>(L.b), cur, H.active,
+        (const int32_t *)L.crow_sys);
   }
   return cur;
 }
@@ -1110,17 +1137,19 @@ static double level_xfer(const Hier &H, int32_t l, int which, int reps, cudaStre
       const int lpr = xfer_lpr<T>(L, 0);
       RS_LPR_SWITCH(lpr, RS_COUNTED launch_pdl(k_csr<T, L_, 1>, dim3(csr_grid(L.A.n, L_)), dim3(kBlock), 0,
                                                s, L.A.n, L.A.rowptr, L.A.col, vals<T>(L.A), (const T *)x,
-                                               static_cast<const T *>(L.b), r));
+                                               static_cast<const T *>(L.b), r, H.active, (const int32_t *)L.row_seg));
     } else if (which == 1) {
       const int lr = xfer_lpr<T>(L, 1);
       RS_LPR_SWITCH(lr, RS_COUNTED launch_pdl(k_csr<T, L_, 0>, dim3(csr_grid(L.R.n, L_)), dim3(kBlock), 0,
                                               s, L.R.n, L.R.rowptr, L.R.col, vals<T>(L.R), (const T *)r,
-                                              (const T *)nullptr, static_cast<T *>(N.b)));
+                                              (const T *)nullptr, static_cast<T *>(N.b), H.active,
+                                              (const int32_t *)N.row_seg));
     } else {
       const int lp = xfer_lpr<T>(L, 2);
       RS_LPR_SWITCH(lp, RS_COUNTED launch_pdl(k_csr<T, L_, 2>, dim3(csr_grid(L.P.n, L_)), dim3(kBlock), 0,
                                               s, L.P.n, L.P.rowptr, L.P.col, vals<T>(L.P),
-                                              (const T *)static_cast<T *>(N.x), (const T *)nullptr, x));
+                                              (const T *)static_cast<T *>(N.x), (const T *)nullptr, x, H.active,
+                                              (const int32_t *)L.row_seg));
     }
   }
   if (which == 0) return L.A.nnz * (4.0 + sz) + (L.A.n + 1) * 4.0 + 3.0 * L.A.n * sz;
