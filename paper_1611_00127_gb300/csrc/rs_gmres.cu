@@ -169,11 +169,15 @@ __device__ __forceinline__ void block_sum_tile(double (&v)[kTile], double *sh, d
 // MODE 0: part = V_{0..nvec-1} . w
 // MODE 1: w -= sum_i V_i h[seg][i], then part = V_{0..nvec-1} . w (next CGS pass)
 // MODE 2: w -= sum_i V_i h[seg][i], then part[0] = w . w
+// Chunks of a retired system (active[seg] = 0) do nothing: their partial
+// sums are not read (the reductions mask retired systems).
 template <int MODE>
 __global__ void __launch_bounds__(kRedThreads) k_arnoldi(const Chunk *__restrict__ chunks, const double *__restrict__ V,
                                                          int64_t ldv, int nvec, const double *__restrict__ h, int stride,
-                                                         double *__restrict__ w, double *__restrict__ part) {
+                                                         double *__restrict__ w, double *__restrict__ part,
+                                                         const uint8_t *__restrict__ active) {
   RS_PDL_ENTRY();
+  if (active && !active[chunks[blockIdx.x].seg]) return;
   __shared__ double ws[kChunk];
   __shared__ double sh[(kRedThreads / 32) * kTile];
   const Chunk ch = chunks[blockIdx.x];
@@ -419,7 +423,7 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
       if (nch > 0) {
         ProfScope ps(kProfArnoldi, (nv + 1) * 8.0 * n, s);
         RS_COUNTED launch_pdl(k_arnoldi<0>, dim3(nch), dim3(kRedThreads), 0, s, (const Chunk *)dch, (const double *)V,
-                              (int64_t)n, j + 1, (const double *)nullptr, stride, w, part);
+                              (int64_t)n, j + 1, (const double *)nullptr, stride, w, part, (const uint8_t *)active);
       }
       RS_COUNTED launch_pdl(k_reduce, dim3(grid_for((int64_t)nseg * (j + 1) * 32)), dim3(kBlock), 0, s, nseg,
                             (const int32_t *)dsegc, j + 1, stride, (const double *)part, hbuf, H, ldh, j, 1,
@@ -427,7 +431,7 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
       if (nch > 0) {
         ProfScope ps(kProfArnoldi, (2.0 * nv + 2) * 8.0 * n, s);
         RS_COUNTED launch_pdl(k_arnoldi<1>, dim3(nch), dim3(kRedThreads), 0, s, (const Chunk *)dch, (const double *)V,
-                              (int64_t)n, j + 1, (const double *)hbuf, stride, w, part);
+                              (int64_t)n, j + 1, (const double *)hbuf, stride, w, part, (const uint8_t *)active);
       }
       RS_COUNTED launch_pdl(k_reduce, dim3(grid_for((int64_t)nseg * (j + 1) * 32)), dim3(kBlock), 0, s, nseg,
                             (const int32_t *)dsegc, j + 1, stride, (const double *)part, hbuf, H, ldh, j, 2,
@@ -435,11 +439,11 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
       if (nch > 0) {
         ProfScope ps(kProfArnoldi, (nv + 2) * 8.0 * n, s);
         RS_COUNTED launch_pdl(k_arnoldi<2>, dim3(nch), dim3(kRedThreads), 0, s, (const Chunk *)dch, (const double *)V,
-                              (int64_t)n, j + 1, (const double *)hbuf, stride, w, part);
+                              (int64_t)n, j + 1, (const double *)hbuf, stride, w, part, (const uint8_t *)active);
       }
       RS_COUNTED launch_pdl(k_reduce, dim3(grid_for((int64_t)nseg * 32)), dim3(kBlock), 0, s, nseg,
                             (const int32_t *)dsegc, 1, stride, (const double *)part, nrm, (double *)nullptr, 0, 0, 3,
-                            (const uint8_t *)nullptr);
+                            (const uint8_t *)active);   // retired systems: norm 0, so their next basis vector is 0
       const int slot = j & 1;
       RS_COUNTED launch_pdl(k_scale, dim3(nch), dim3(kRedThreads), 0, s, (const Chunk *)dch, (const double *)nrm,
                             (const double *)w, w, nact + slot);
