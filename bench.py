@@ -44,13 +44,8 @@ KINDS = (("amgJ", 0, 0), ("cpr1", 1, 2), ("bf", 3, 0))
 # capture of the current kernel version (summaries and commands in profiles/);
 # None where no capture of the current version exists.
 NCU_TRAFFIC = {
-    ("k_hgs", "fp64", "lognormal256bf"): (11.759872e6 + 0.0, "profiles/k_hgs_fp64_lognormal256_bf_level0.md"),
-    ("k_hgs", "fp64", "layered128"): (225.426688e6 + 11.628800e6, "profiles/k_hgs_fp64_layered128_level0.md"),
-    ("k_csr_residual", "fp32", "layered128"): (141.960448e6 + 6.054144e6,
-                                             "profiles/k_csr_residual_fp32_layered128_level0.md"),
-    ("k_csr_restrict", "fp32", "layered128"): (60.597760e6 + 0.222976e6,
-                                             "profiles/k_csr_restrict_fp32_layered128_level0.md"),
-    ("k_hgs", "fp32", "layered128"): (150.325760e6 + 6.161408e6, "profiles/k_hgs_fp32_layered128_level0.md"),
+    ("k_hgs", "fp64", "lognormal256bf"): (11.765248e6 + 0.0, "profiles/k_hgs_fp64_lognormal256_bf_level0.md"),
+    ("k_hgs", "fp64", "layered128"): (225.423104e6 + 11.490048e6, "profiles/k_hgs_fp64_layered128_level0.md"),
     ("k_bsr2_spmv", "f64", "layered128"): (608.675840e6 + 30.454272e6, "profiles/k_bsr2_spmv_layered128.md"),
 }
 
