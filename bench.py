@@ -47,6 +47,11 @@ NCU_TRAFFIC = {
     ("k_hgs", "fp64", "lognormal256bf"): (11.765248e6 + 0.0, "profiles/k_hgs_fp64_lognormal256_bf_level0.md"),
     ("k_hgs", "fp64", "layered128"): (225.423104e6 + 11.490048e6, "profiles/k_hgs_fp64_layered128_level0.md"),
     ("k_bsr2_spmv", "f64", "layered128"): (608.675840e6 + 30.454272e6, "profiles/k_bsr2_spmv_layered128.md"),
+    ("k_hgs", "fp32", "layered128"): (150.313472e6 + 6.125056e6, "profiles/k_hgs_fp32_layered128_level0.md"),
+    ("k_csr_residual", "fp32", "layered128"): (142.222336e6 + 4.032768e6,
+                                             "profiles/k_csr_residual_fp32_layered128_level0.md"),
+    ("k_csr_restrict", "fp32", "layered128"): (60.598272e6 + 0.020992e6,
+                                             "profiles/k_csr_restrict_fp32_layered128_level0.md"),
 }
 
 
