@@ -54,3 +54,27 @@ def test_invalid_arguments_rejected_on_host():
     assert L.amg_setup(None, None, ctypes.byref(h), None) == -1
     assert L.gmres_solve(None, None, None, None, None, None, None) == -1
     assert b"invalid" in L.rs_last_error() or b"null" in L.rs_last_error()
+
+
+def test_parameter_validation_on_host():
+    """Out-of-range solver parameters are refused with RS_EINVAL (-1) and a
+    message naming the parameter, before any GPU work (an empty matrix is
+    enough)."""
+    from paper_1611_00127_gb300 import rsflow as R
+    L = R.lib()
+    csr = R.CsrC(0, 0, None, None, None, 0, None)
+    bad = [(dict(agg_levels=9), b"agg_levels"), (dict(chunk_coarse=16), b"chunk_coarse"),
+           (dict(tail_rows=-1), b"tail_rows"), (dict(theta=2.0), b"theta"),
+           (dict(num_functions=3), b"num_functions"), (dict(precision=5), b"precision"),
+           (dict(nu1=17), b"sweep"), (dict(chunk=16), b"chunk")]
+    for kw, word in bad:
+        p = R.AmgParams(**kw).c()
+        h = ctypes.c_void_p()
+        assert L.amg_setup(ctypes.byref(csr), ctypes.byref(p), ctypes.byref(h), None) == -1, kw
+        assert word in L.rs_last_error(), (kw, L.rs_last_error())
+    J = R.Bsr2C(0, 0, None, None, None, 0, None)
+    for kw, word in ((dict(kind=9), b"kind"), (dict(decouple=7), b"decoupling"), (dict(p1=2), b"P1")):
+        pp = R.PrecParams(**kw).c()
+        h = ctypes.c_void_p()
+        assert L.precond_create(ctypes.byref(J), ctypes.byref(pp), ctypes.byref(h), None) == -1, kw
+        assert word in L.rs_last_error(), (kw, L.rs_last_error())
