@@ -57,3 +57,25 @@ def test_oil_water_run_converges_and_moves_water(oracle, inputs):
     gained = (p.phi * V * (0.8 - sn)).sum()
     injected = p.q_in * dt * inputs.OIL_WATER_STEPS
     assert 0.3 * injected < gained <= injected * (1 + 1e-6)
+
+
+def test_simple_schur_approximation_is_weak_here(oracle, inputs):
+    """Why block factorisation struggles on this section: on the first
+    Jacobian of the linear Ex 1 run, even with both block solves exact
+    (single-level hierarchies, dense LU) FGMRES needs tens of iterations,
+    because S~ replaces A_ss by its diagonal while A_ss carries a capillary
+    diffusion several times its storage term; the exact Schur complement
+    would converge in at most two (pinned on a small grid in the solver
+    tests)."""
+    p = inputs.config_oil_water_2d(1, inputs.PC_LINEAR)
+    u = inputs.uniform_state(p)
+    F, J, (rp, col) = oracle.assemble(p, u, u, inputs.OIL_WATER_DT_DAYS * inputs.DAY)
+    exact = oracle.AmgParams(coarse_n=10 ** 6, max_dense=10 ** 6)
+    M = oracle.Precond(rp, col, J, oracle.PrecParams(kind=3, decouple=0, amg=exact))
+    x, st, its, rr = oracle.fgmres(rp, col, J, -F, M, maxit=400)
+    assert st == 0 and its >= 30, its
+    # the capillary diffusion in A_ss outweighs the storage on its diagonal
+    Ass = oracle.bsr2_part(rp, col, J, 1, 1).scipy().tocsr()
+    V = p.hx * p.hy * 1.0
+    storage = V * p.phi * p.rho_n / (inputs.OIL_WATER_DT_DAYS * inputs.DAY)
+    assert np.median(Ass.diagonal()) > 3 * storage
