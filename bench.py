@@ -408,7 +408,10 @@ def reference_arm(args):
     v = float(np.mean(vals))
     line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic", config=dict(workload=WORKLOAD, grid=f"{args.n}x{args.n}"),
+                dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD, grid=f"{args.n}x{args.n}", solves_per_step=12,
+                            gmres="FGMRES(30), rtol 1e-8, maxit %d" % args.maxit, vcycle="FP64",
+                            parallelism="single host core"),
                 cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=samples[-1]),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
