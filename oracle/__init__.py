@@ -67,7 +67,7 @@ class _AmgParams(C.Structure):
                 ("coarse_n", C.c_int32), ("max_dense", C.c_int32), ("smoother", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("interp", C.c_int32),
                 ("num_functions", C.c_int32), ("chunk", C.c_int32), ("agg_levels", C.c_int32),
-                ("chunk_coarse", C.c_int32)]
+                ("chunk_coarse", C.c_int32), ("restriction", C.c_int32)]
 
 
 class _PrecParams(C.Structure):
@@ -113,6 +113,7 @@ def lib():
             "or_interp": (P, [P, P, P]),
             "or_interp_ext": (P, [P, P, P]),
             "or_galerkin": (P, [P, P]),
+            "or_air_restriction": (P, [P, P, i32]),
             "or_jp_colour": (i32, [P, u64, i32, P]),
             "or_chunk_rows": (i32, [P, i32]),
             "or_chunk_colour": (i32, [P, i32, P]),
@@ -335,11 +336,12 @@ class AmgParams:
     chunk: int = 512
     agg_levels: int = 0
     chunk_coarse: int = 32
+    restriction: int = 0
 
     def c(self):
         return _AmgParams(self.theta, self.seed, self.max_levels, self.coarse_n,
                           self.max_dense, self.smoother, self.nu1, self.nu2, self.interp,
-                          self.num_functions, self.chunk, self.agg_levels, self.chunk_coarse)
+                          self.num_functions, self.chunk, self.agg_levels, self.chunk_coarse, self.restriction)
 
 
 def splitmix64(seed: int, counter: int) -> int:
@@ -368,6 +370,11 @@ def interp(A: Csr, strong, cf) -> Csr:
 def interp_ext(A: Csr, strong, cf) -> Csr:
     return Csr(lib().or_interp_ext(A.h, _p(np.ascontiguousarray(strong, dtype=np.uint8)),
                                    _p(np.ascontiguousarray(cf, dtype=np.int8))))
+
+
+def air_restriction(A: Csr, cf, dist: int = 1) -> Csr:
+    """Approximate ideal restriction for the splitting cf (rows: C points)."""
+    return Csr(lib().or_air_restriction(A.h, _p(np.ascontiguousarray(cf, dtype=np.int8)), int(dist)))
 
 
 def galerkin(A: Csr, P: Csr) -> Csr:

@@ -680,6 +680,98 @@ void or_dense_lu_solve(int32_t n, const double *a, const int32_t *piv, const dou
   }
 }
 
+/* Approximate ideal restriction (AIR; Manteuffel, Southworth et al.,
+ * "Nonsymmetric algebraic multigrid based on local approximate ideal
+ * restriction", 2018) for the C/F splitting cf. The ideal restriction makes
+ * (R A)(i, F) = 0 for every coarse point i; AIR imposes it on a small
+ * neighbourhood: row r of R (the r-th C point i, in order) is e_i - z with z
+ * supported on N_i and A(N_i, N_i)^T z = A(i, N_i)^T, so (R A)(i, N_i) = 0.
+ * N_i: the F points coupled to i in row i (dist = 1), and for dist = 2 also
+ * the F points coupled to those in their rows; ascending. The local systems
+ * are solved by dense LU with partial pivoting. */
+or_csr *or_air_restriction(const or_csr *A, const int8_t *cf, int32_t dist) {
+  int32_t n = A->n, nc = 0;
+  for (int32_t i = 0; i < n; i++) nc += cf[i] == 1;
+  int32_t *mark = xmalloc(sizeof(int32_t) * ((size_t)n + 1));
+  int32_t *pos = xmalloc(sizeof(int32_t) * ((size_t)n + 1));
+  for (int32_t j = 0; j < n; j++) { mark[j] = -1; pos[j] = -1; }
+  size_t cap = (size_t)A->nnz + (size_t)nc + 16, used = 0;
+  int32_t *rcol = xmalloc(sizeof(int32_t) * cap);
+  double *rval = xmalloc(sizeof(double) * cap);
+  or_csr *R = or_csr_alloc(nc, n, 0);
+  int32_t ncap = 64, *nb = xmalloc(sizeof(int32_t) * (size_t)ncap);
+  int32_t r = 0;
+  R->rowptr[0] = 0;
+  for (int32_t i = 0; i < n; i++) {
+    if (cf[i] != 1) continue;
+    int32_t m = 0;
+    for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+      int32_t j = A->col[q];
+      if (j == i || cf[j] == 1 || mark[j] == i) continue;
+      if (m == ncap) { ncap *= 2; nb = realloc(nb, sizeof(int32_t) * (size_t)ncap); if (!nb) abort(); }
+      mark[j] = i;
+      nb[m++] = j;
+    }
+    if (dist >= 2) {
+      int32_t m1 = m;
+      for (int32_t a = 0; a < m1; a++)
+        for (int32_t q = A->rowptr[nb[a]]; q < A->rowptr[nb[a] + 1]; q++) {
+          int32_t j = A->col[q];
+          if (j == i || cf[j] == 1 || mark[j] == i) continue;
+          if (m == ncap) { ncap *= 2; nb = realloc(nb, sizeof(int32_t) * (size_t)ncap); if (!nb) abort(); }
+          mark[j] = i;
+          nb[m++] = j;
+        }
+    }
+    qsort(nb, (size_t)m, sizeof(int32_t), cmp_i32_amg);
+    for (int32_t a = 0; a < m; a++) pos[nb[a]] = a;
+    double *M = xmalloc(sizeof(double) * ((size_t)m * m + 1));
+    double *rhs = xmalloc(sizeof(double) * ((size_t)m + 1));
+    double *z = xmalloc(sizeof(double) * ((size_t)m + 1));
+    int32_t *piv = xmalloc(sizeof(int32_t) * ((size_t)m + 1));
+    for (size_t t = 0; t < (size_t)m * m; t++) M[t] = 0.0;
+    for (int32_t a = 0; a < m; a++) rhs[a] = 0.0;
+    /* M = A(N_i, N_i)^T: row b of A(N_i, .) fills column b of M */
+    for (int32_t b = 0; b < m; b++)
+      for (int32_t q = A->rowptr[nb[b]]; q < A->rowptr[nb[b] + 1]; q++) {
+        int32_t a = A->col[q] < n ? pos[A->col[q]] : -1;
+        if (a >= 0) M[(size_t)a * m + b] = A->val[q];
+      }
+    for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
+      int32_t a = pos[A->col[q]];
+      if (a >= 0) rhs[a] = A->val[q];
+    }
+    if (m > 0) {
+      or_dense_lu(m, M, piv);
+      or_dense_lu_solve(m, M, piv, rhs, z);
+    }
+    if (used + (size_t)m + 1 > cap) {
+      cap = 2 * (used + (size_t)m + 1);
+      rcol = realloc(rcol, sizeof(int32_t) * cap);
+      rval = realloc(rval, sizeof(double) * cap);
+      if (!rcol || !rval) abort();
+    }
+    /* the row: -z on N_i and 1 at i, ascending columns */
+    int placed = 0;
+    for (int32_t a = 0; a < m; a++) {
+      if (!placed && i < nb[a]) { rcol[used] = i; rval[used] = 1.0; used++; placed = 1; }
+      rcol[used] = nb[a];
+      rval[used] = -z[a];
+      used++;
+    }
+    if (!placed) { rcol[used] = i; rval[used] = 1.0; used++; }
+    for (int32_t a = 0; a < m; a++) pos[nb[a]] = -1;
+    free(M); free(rhs); free(z); free(piv);
+    R->rowptr[++r] = (int32_t)used;
+  }
+  free(R->col); free(R->val);
+  R->col = rcol;
+  R->val = rval;
+  R->nnz = (int32_t)used;
+  free(mark); free(pos); free(nb);
+  return R;
+}
+
 /* ---------------- hierarchy ---------------- */
 #define OR_MAXLEV 32
 struct or_amg {
@@ -757,8 +849,16 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
       H->P[l] = prm->interp == 1 ? or_interp_ext(A, st, cf) : or_interp(A, st, cf);
       free(st);
     }
-    H->R[l] = or_transpose(H->P[l]);
-    H->A[l + 1] = or_galerkin(A, H->P[l]);
+    if (H->b == 1 && prm->restriction > 0) {
+      /* AIR restriction, Petrov-Galerkin coarse operator R A P */
+      H->R[l] = or_air_restriction(A, H->cf[l], prm->restriction);
+      or_csr *AP = or_spgemm(A, H->P[l]);
+      H->A[l + 1] = or_spgemm(H->R[l], AP);
+      or_csr_free(AP);
+    } else {
+      H->R[l] = or_transpose(H->P[l]);
+      H->A[l + 1] = or_galerkin(A, H->P[l]);
+    }
     l++;
   }
   H->nlev = l + 1;
@@ -774,9 +874,10 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
     int8_t *cf = xmalloc((size_t)H->A[k]->n + 1);
     int32_t ic = 0;
     for (int32_t i = 0; i < H->A[k]->n; i++) cf[i] = H->cf[k][i] == 1 ? H->cf[k + 1][ic++] : (int8_t)-1;
+    or_csr *Rk = (H->b == 1 && prm->restriction > 0) ? or_spgemm(H->R[k + 1], H->R[k]) : or_transpose(P);
     or_csr_free(H->P[k]); or_csr_free(H->R[k]); free(H->cf[k]);
     H->P[k] = P;
-    H->R[k] = or_transpose(P);
+    H->R[k] = Rk;
     H->cf[k] = cf;
     or_csr_free(H->A[k + 1]); or_csr_free(H->P[k + 1]); or_csr_free(H->R[k + 1]); free(H->cf[k + 1]);
     for (int32_t j = k + 1; j + 1 < H->nlev; j++) {
