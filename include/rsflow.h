@@ -125,6 +125,12 @@ typedef struct rs_amg_params {
   int32_t tail_rows;       /* > 0: the levels with at most this many rows (down to the dense
                               coarsest level) run their part of the V-cycle as one launch of a
                               thread-block cluster; 0: one launch per kernel and level */
+  int32_t restriction;     /* scalar AMG (num_functions 1): 0 Galerkin, R = P^T; 1 approximate
+                              ideal restriction (AIR, Manteuffel, Southworth et al. 2018),
+                              distance 1: R's row for C point i is 1 at i and -z on the F
+                              points N_i coupled to i, A(N_i, N_i)^T z = A(i, N_i)^T, so
+                              (R A)(i, N_i) = 0; A_{l+1} = R A P. For non-symmetric levels
+                              such as the block factorisation's S~. Ignored by systems AMG */
 } rs_amg_params;
 
 typedef struct rs_amg rs_amg;

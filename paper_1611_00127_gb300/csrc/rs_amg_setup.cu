@@ -1110,10 +1110,196 @@ __global__ void k_is_c(int32_t n, const int8_t *__restrict__ cf, int32_t *__rest
   if (i < n) out[i] = cf[i] == 1;
 }
 
+// ------------------------------------------------------------------ approximate ideal restriction
+// AIR (Manteuffel, Southworth et al., "Nonsymmetric algebraic multigrid based
+// on local approximate ideal restriction", 2018), distance 1: row r of R, for
+// the r-th C point i, is 1 at i and -z on N_i, the F points coupled to i in
+// row i (ascending, each once), with A(N_i, N_i)^T z = A(i, N_i)^T, so that
+// (R A)(i, N_i) = 0. The local system is solved by LU with partial pivoting
+// (largest magnitude, the first one on ties; a zero pivot leaves its column
+// uneliminated and its solution component zero) in the operation order of a
+// plain sequential elimination, which this unit, compiled without FMA
+// contraction, reproduces bit for bit.
+
+// Per C point: its row length |N_i| + 1 in R, its fine index, and the
+// largest |N_i|.
+__global__ void k_air_count(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const int8_t *__restrict__ cf, const int32_t *__restrict__ cidx,
+                            int32_t *__restrict__ rlen, int32_t *__restrict__ cpt, int32_t *__restrict__ mmax) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || cf[i] != 1) return;
+  int32_t m = 0;
+  for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+    const int32_t j = col[q];
+    if (j == i || cf[j] == 1) continue;
+    bool dup = false;
+    for (int32_t q2 = rp[i]; q2 < q && !dup; q2++) dup = col[q2] == j;
+    if (!dup) m++;
+  }
+  const int32_t r = cidx[i];
+  rlen[r] = m + 1;
+  cpt[r] = i;
+  atomicMax(mmax, m);
+}
+
+// Position of j in the ascending list nb (element a at nb[a * T]), or -1.
+__device__ __forceinline__ int32_t air_find(const int32_t *nb, size_t T, int32_t m, int32_t j) {
+  int32_t lo = 0, hi = m - 1;
+  while (lo <= hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    const int32_t v = nb[(size_t)mid * T];
+    if (v == j) return mid;
+    if (v < j) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+// T threads, each working through rows t, t + T, ... with its own slice of
+// the work arrays, interleaved across threads (element e of thread t at
+// e * T + t): the local matrix (mx^2), the right-hand side / solution (mx),
+// N_i and the pivots (mx each).
+__global__ void __launch_bounds__(128) k_air_fill(int32_t nc, int32_t T, int32_t mx, const int32_t *__restrict__ rp,
+                                                  const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                  const int8_t *__restrict__ cf, const int32_t *__restrict__ cpt,
+                                                  const int32_t *__restrict__ rrp, double *__restrict__ ws,
+                                                  int32_t *__restrict__ wi, int32_t *__restrict__ rcol,
+                                                  double *__restrict__ rval) {
+  const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const size_t S = (size_t)T;
+  double *M = ws + t;
+  double *x = ws + (size_t)mx * mx * S + t;
+  int32_t *nb = wi + t;
+  int32_t *piv = wi + (size_t)mx * S + t;
+  for (int32_t r = t; r < nc; r += T) {
+    const int32_t i = cpt[r];
+    // N_i by insertion into an ascending list
+    int32_t m = 0;
+    for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+      const int32_t j = col[q];
+      if (j == i || cf[j] == 1) continue;
+      int32_t a = m;
+      while (a > 0 && nb[(size_t)(a - 1) * S] > j) a--;
+      if (a > 0 && nb[(size_t)(a - 1) * S] == j) continue;
+      if (m >= mx) break;   // cannot happen: mx is the largest count
+      for (int32_t b = m; b > a; b--) nb[(size_t)b * S] = nb[(size_t)(b - 1) * S];
+      nb[(size_t)a * S] = j;
+      m++;
+    }
+    // M = A(N_i, N_i)^T (row b of A(N_i, .) fills column b), x = A(i, N_i)^T
+    for (int32_t e = 0; e < m * m; e++) M[(size_t)e * S] = 0.0;
+    for (int32_t a = 0; a < m; a++) x[(size_t)a * S] = 0.0;
+    for (int32_t b = 0; b < m; b++) {
+      const int32_t k = nb[(size_t)b * S];
+      for (int32_t q = rp[k]; q < rp[k + 1]; q++) {
+        const int32_t a = air_find(nb, S, m, col[q]);
+        if (a >= 0) M[(size_t)(a * m + b) * S] = val[q];
+      }
+    }
+    for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+      const int32_t a = air_find(nb, S, m, col[q]);
+      if (a >= 0) x[(size_t)a * S] = val[q];
+    }
+    // LU with partial pivoting, in place
+    for (int32_t k = 0; k < m; k++) {
+      int32_t p = k;
+      double big = fabs(M[(size_t)(k * m + k) * S]);
+      for (int32_t a = k + 1; a < m; a++) {
+        const double v = fabs(M[(size_t)(a * m + k) * S]);
+        if (v > big) { big = v; p = a; }
+      }
+      piv[(size_t)k * S] = p;
+      if (p != k)
+        for (int32_t b = 0; b < m; b++) {
+          const double tmp = M[(size_t)(k * m + b) * S];
+          M[(size_t)(k * m + b) * S] = M[(size_t)(p * m + b) * S];
+          M[(size_t)(p * m + b) * S] = tmp;
+        }
+      const double d = M[(size_t)(k * m + k) * S];
+      if (d == 0.0) continue;
+      for (int32_t a = k + 1; a < m; a++) {
+        const double l = M[(size_t)(a * m + k) * S] / d;
+        M[(size_t)(a * m + k) * S] = l;
+        for (int32_t b = k + 1; b < m; b++) M[(size_t)(a * m + b) * S] -= l * M[(size_t)(k * m + b) * S];
+      }
+    }
+    // solve: row interchanges, forward (unit L), backward (U)
+    for (int32_t k = 0; k < m; k++) {
+      const int32_t p = piv[(size_t)k * S];
+      if (p != k) {
+        const double tmp = x[(size_t)k * S];
+        x[(size_t)k * S] = x[(size_t)p * S];
+        x[(size_t)p * S] = tmp;
+      }
+    }
+    for (int32_t a = 0; a < m; a++) {
+      double v = x[(size_t)a * S];
+      for (int32_t b = 0; b < a; b++) v -= M[(size_t)(a * m + b) * S] * x[(size_t)b * S];
+      x[(size_t)a * S] = v;
+    }
+    for (int32_t a = m - 1; a >= 0; a--) {
+      double v = x[(size_t)a * S];
+      for (int32_t b = a + 1; b < m; b++) v -= M[(size_t)(a * m + b) * S] * x[(size_t)b * S];
+      const double d = M[(size_t)(a * m + a) * S];
+      x[(size_t)a * S] = d != 0.0 ? v / d : 0.0;
+    }
+    // the row: 1 at i, -z on N_i, ascending columns
+    int32_t o = rrp[r];
+    bool placed = false;
+    for (int32_t a = 0; a < m; a++) {
+      const int32_t j = nb[(size_t)a * S];
+      if (!placed && i < j) { rcol[o] = i; rval[o] = 1.0; o++; placed = true; }
+      rcol[o] = j;
+      rval[o] = -x[(size_t)a * S];
+      o++;
+    }
+    if (!placed) { rcol[o] = i; rval[o] = 1.0; }
+  }
+}
+
+// R (nc x n) of level matrix A by approximate ideal restriction, for the marks
+// cf (1 C) and the C index cidx of every C point; nc C points in all.
+static int air_restriction(const DCsr &A, const int8_t *cf, const int32_t *cidx, int32_t nc, DCsr &R,
+                           cudaStream_t s) {
+  const int32_t n = A.n;
+  R.n = nc;
+  R.m = n;
+  RS_TRY(dalloc_n(&R.rowptr, (size_t)nc + 1, s));
+  Scratch sc(s);
+  int32_t *cpt = nullptr, *mmax = nullptr;
+  RS_TRY(sc.get(&cpt, (size_t)nc + 1));
+  RS_TRY(sc.get(&mmax, 1));
+  RS_CHECK_CUDA(cudaMemsetAsync(mmax, 0, sizeof(int32_t), s));
+  RS_CHECK_CUDA(cudaMemsetAsync(R.rowptr, 0, sizeof(int32_t) * ((size_t)nc + 1), s));
+  if (n > 0) RS_COUNTED k_air_count<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cf, cidx, R.rowptr, cpt, mmax);
+  int32_t nnz = 0, mx = 0;
+  RS_TRY(exclusive_scan(R.rowptr, R.rowptr, nc, s, &nnz));
+  RS_TRY(sync_copy(&mx, mmax, sizeof(int32_t), s));
+  if (mx > 4096) return fail(RS_ESETUP, "AIR neighbourhood of more than 4096 points");
+  R.nnz = nnz;
+  RS_TRY(dalloc_n(&R.col, (size_t)nnz + 1, s));
+  RS_TRY(dalloc_n(&R.val, (size_t)nnz + 1, s));
+  if (nc == 0) return 0;
+  // threads bounded by a 256 MB work area
+  const size_t per = ((size_t)mx * mx + mx) * sizeof(double) + 2 * (size_t)mx * sizeof(int32_t);
+  size_t T = (size_t)num_sms() * 256;
+  if (per > 0) T = std::min(T, std::max<size_t>(1, ((size_t)256 << 20) / per));
+  T = std::min(T, (size_t)nc);
+  double *ws = nullptr;
+  int32_t *wi = nullptr;
+  RS_TRY(sc.get(&ws, ((size_t)mx * mx + mx) * T + 1));
+  RS_TRY(sc.get(&wi, 2 * (size_t)mx * T + 1));
+  RS_COUNTED k_air_fill<<<(unsigned)((T + 127) / 128), 128, 0, s>>>(nc, (int32_t)T, mx, A.rowptr, A.col, A.val, cf,
+                                                                     cpt, R.rowptr, ws, wi, R.col, R.val);
+  RS_CHECK_CUDA(cudaGetLastError());
+  return 0;
+}
+
 // Aggressive coarsening, two-stage form: level l's coarse grid becomes the
 // second of two PMIS stages and its interpolation the product of the two
-// stages' interpolations, P = P_l P_{l+1}, R = P^T; level l+1 is dropped and
-// A_{l+2} = P_{l+1}^T (P_l^T A_l P_l) P_{l+1} stays the next operator. Applied
+// stages' interpolations, P = P_l P_{l+1}, R = P^T (with AIR the product of
+// the stages' restrictions, R_{l+1} R_l); level l+1 is dropped and
+// A_{l+2} = R_{l+1} (R_l A_l P_l) P_{l+1} stays the next operator. Applied
 // to the first prm.agg_levels coarse grids while every system coarsens past
 // the dropped level.
 static int merge_levels(Hier &H, const rs_amg_params &prm, int32_t *f32err, cudaStream_t s) {
@@ -1125,7 +1311,8 @@ static int merge_levels(Hier &H, const rs_amg_params &prm, int32_t *f32err, cuda
     Level &M = H.L[l + 1];
     DCsr P, R;
     RS_TRY(spgemm(L.P, M.P, P, s));
-    RS_TRY(transpose(P, R, s));
+    if (L.nfun == 1 && prm.restriction > 0) RS_TRY(spgemm(M.R, L.R, R, s));
+    else RS_TRY(transpose(P, R, s));
     const int32_t n = L.A.n;
     Scratch sc(s);
     int32_t *cidx = nullptr;
@@ -1392,7 +1579,8 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           }
           RS_CHECK_CUDA(cudaGetLastError());
         }
-        RS_TRY(transpose(P, L.R, s));
+        if (B == 1 && prm.restriction > 0) RS_TRY(air_restriction(L.A, L.cf, isc, nc, L.R, s));
+        else RS_TRY(transpose(P, L.R, s));
         DCsr AP;
         RS_TRY(spgemm(L.A, P, AP, s));
         Level next;

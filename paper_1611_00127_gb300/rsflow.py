@@ -74,7 +74,8 @@ class AmgParamsC(C.Structure):
                 ("coarse_n", C.c_int32), ("max_dense", C.c_int32), ("smoother", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("interp", C.c_int32),
                 ("num_functions", C.c_int32), ("precision", C.c_int32), ("chunk", C.c_int32),
-                ("agg_levels", C.c_int32), ("chunk_coarse", C.c_int32), ("tail_rows", C.c_int32)]
+                ("agg_levels", C.c_int32), ("chunk_coarse", C.c_int32), ("tail_rows", C.c_int32),
+                ("restriction", C.c_int32)]
 
 
 class PrecParamsC(C.Structure):
@@ -258,11 +259,13 @@ class AmgParams:
     agg_levels: int = 0
     chunk_coarse: int = 32
     tail_rows: int = 0
+    restriction: int = 0
 
     def c(self):
         return AmgParamsC(self.theta, self.seed, self.max_levels, self.coarse_n, self.max_dense,
                           self.smoother, self.nu1, self.nu2, self.interp, self.num_functions,
-                          self.precision, self.chunk, self.agg_levels, self.chunk_coarse, self.tail_rows)
+                          self.precision, self.chunk, self.agg_levels, self.chunk_coarse, self.tail_rows,
+                          self.restriction)
 
 
 @dataclass

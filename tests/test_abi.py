@@ -66,7 +66,7 @@ def test_parameter_validation_on_host():
     bad = [(dict(agg_levels=9), b"agg_levels"), (dict(chunk_coarse=16), b"chunk_coarse"),
            (dict(tail_rows=-1), b"tail_rows"), (dict(theta=2.0), b"theta"),
            (dict(num_functions=3), b"num_functions"), (dict(precision=5), b"precision"),
-           (dict(nu1=17), b"sweep"), (dict(chunk=16), b"chunk")]
+           (dict(nu1=17), b"sweep"), (dict(chunk=16), b"chunk"), (dict(restriction=2), b"restriction")]
     for kw, word in bad:
         p = R.AmgParams(**kw).c()
         h = ctypes.c_void_p()
