@@ -11,9 +11,7 @@ SIMPLE Schur complement): 12 solves per step, each with its own
 preconditioner setup. V-cycles run in FP64 for the headline number (the
 workload's "plain FP64 on GPU"); the same step with FP32 V-cycles is reported
 beside it. A solve counts when its true relative residual is <= 1e-8 within
-`--maxit` Arnoldi steps. `--restriction 1` builds the scalar AMG hierarchies
-(CPR's pressure block, block factorisation's S~ and A_ss) with approximate
-ideal restriction instead of the paper's Galerkin R = P^T, on both arms.
+`--maxit` Arnoldi steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -69,17 +67,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
-    ap.add_argument("--restriction", type=int, default=0, choices=[0, 1],
-                    help="scalar AMG restriction: 0 Galerkin (R = P^T), 1 approximate ideal restriction")
     return ap.parse_args()
-
-
-# scalar AMG restriction of every preconditioner (set from --restriction)
-RESTRICTION = 0
-
-
-def restriction_name():
-    return "AIR, distance 1" if RESTRICTION else "Galerkin (P^T)"
 
 
 def workload(n):
@@ -172,8 +160,7 @@ class GpuStep:
 
     def params(self, kind, dec):
         R = self.R
-        return R.PrecParams(kind=kind, decouple=dec,
-                            amg=R.AmgParams(precision=self.precision, restriction=RESTRICTION))
+        return R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(precision=self.precision))
 
     def run(self, dps=None, us=None, uos=None, per_solve_profile=None):
         """One step; returns per-solve records. With `per_solve_profile` (a
@@ -242,8 +229,7 @@ class GpuBatchStep:
         recs = []
         for q, (name, kind, dec) in enumerate(KINDS):
             self.xout[q].zero_()
-            M = R.Precond(self.J, R.PrecParams(kind=kind, decouple=dec,
-                                               amg=R.AmgParams(precision=self.precision, restriction=RESTRICTION)))
+            M = R.Precond(self.J, R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(precision=self.precision)))
             st = R.gmres_solve(self.J, M, self.b, self.xout[q], R.GmresParams(m=30, maxit=self.maxit, rtol=1e-8))
             M.close()
             for k in range(len(self.probs)):
@@ -390,8 +376,7 @@ def oracle_sample(probs, states, maxit, budget_s=20.0):
     for k, p in enumerate(probs):
         F, J, (rp, col) = O.assemble(p, states[k][0], states[k][1], 86400.0)
         for name, kind, dec in KINDS:
-            M = O.Precond(rp, col, J, O.PrecParams(kind=kind, decouple=dec,
-                                                   amg=O.AmgParams(restriction=RESTRICTION)))
+            M = O.Precond(rp, col, J, O.PrecParams(kind=kind, decouple=dec))
             x, st, its, rr = O.fgmres(rp, col, J, -F, M, m=30, rtol=1e-8, maxit=maxit)
             done += 1
             conv += int(st == 0)
@@ -426,7 +411,7 @@ def reference_arm(args):
                 dtype="f64", data="synthetic",
                 config=dict(workload=WORKLOAD, grid=f"{args.n}x{args.n}", solves_per_step=12,
                             gmres="FGMRES(30), rtol 1e-8, maxit %d" % args.maxit, vcycle="FP64",
-                            restriction=restriction_name(), parallelism="single host core"),
+                            parallelism="single host core"),
                 cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=samples[-1]),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
@@ -462,7 +447,7 @@ def ensemble_bench(maxit):
     def single_run():
         conv = 0
         for J, F in singles:
-            M = R.Precond(J, R.PrecParams(kind=R.CPR1, amg=R.AmgParams(precision=R.FP64, restriction=RESTRICTION)))
+            M = R.Precond(J, R.PrecParams(kind=R.CPR1, amg=R.AmgParams(precision=R.FP64)))
             x = torch.zeros_like(F)
             st = R.gmres_solve(J, M, -F, x, gp)
             conv += int(st.converged)
@@ -470,7 +455,7 @@ def ensemble_bench(maxit):
         return conv
 
     def batched_run():
-        M = R.Precond(Jb, R.PrecParams(kind=R.CPR1, amg=R.AmgParams(precision=R.FP32, restriction=RESTRICTION)))
+        M = R.Precond(Jb, R.PrecParams(kind=R.CPR1, amg=R.AmgParams(precision=R.FP32)))
         x = torch.zeros_like(Fb)
         st = R.gmres_solve(Jb, M, -Fb, x, gp)
         M.close()
@@ -515,9 +500,7 @@ def solves_per_second(converged, steps, total_ms):
 
 
 def main():
-    global RESTRICTION
     args = parse()
-    RESTRICTION = args.restriction
     if args.impl == "reference":
         return reference_arm(args)
     import torch
@@ -609,8 +592,7 @@ def main():
         config=dict(workload=WORKLOAD, grid=f"{args.n}x{args.n}", solves_per_step=12,
                     bsr2_lanes_per_row=step64.lanes,
                     converged_per_step=conv64, gmres="FGMRES(30), rtol 1e-8, maxit %d" % args.maxit,
-                    vcycle="FP64", restriction=restriction_name(),
-                    l2="flushed (256 MB write) before every timed step",
+                    vcycle="FP64", l2="flushed (256 MB write) before every timed step",
                     parallelism="replicas" if world > 1 else "single GPU"),
         solves=recs64,
         fp32_vcycle=dict(value=value32, ms_per_step=ms32 / args.steps, converged_per_step=conv32, solves=recs32),
