@@ -129,8 +129,12 @@ typedef struct rs_amg_params {
                               ideal restriction (AIR, Manteuffel, Southworth et al. 2018),
                               distance 1: R's row for C point i is 1 at i and -z on the F
                               points N_i coupled to i, A(N_i, N_i)^T z = A(i, N_i)^T, so
-                              (R A)(i, N_i) = 0; A_{l+1} = R A P. For non-symmetric levels
-                              such as the block factorisation's S~. Ignored by systems AMG */
+                              (R A)(i, N_i) = 0; A_{l+1} = R A P. 3: the same over the F
+                              points that strongly influence i only (lAIR, Manteuffel,
+                              Muenzenmaier, Ruge, Southworth 2019), which keeps R A P as
+                              sparse as Galerkin's on transport-dominated levels. For
+                              non-symmetric levels such as the block factorisation's S~ and
+                              A_ss. Ignored by systems AMG */
 } rs_amg_params;
 
 typedef struct rs_amg rs_amg;

@@ -113,7 +113,7 @@ def lib():
             "or_interp": (P, [P, P, P]),
             "or_interp_ext": (P, [P, P, P]),
             "or_galerkin": (P, [P, P]),
-            "or_air_restriction": (P, [P, P, i32]),
+            "or_air_restriction": (P, [P, P, i32, P]),
             "or_jp_colour": (i32, [P, u64, i32, P]),
             "or_chunk_rows": (i32, [P, i32]),
             "or_chunk_colour": (i32, [P, i32, P]),
@@ -372,9 +372,12 @@ def interp_ext(A: Csr, strong, cf) -> Csr:
                                    _p(np.ascontiguousarray(cf, dtype=np.int8))))
 
 
-def air_restriction(A: Csr, cf, dist: int = 1) -> Csr:
-    """Approximate ideal restriction for the splitting cf (rows: C points)."""
-    return Csr(lib().or_air_restriction(A.h, _p(np.ascontiguousarray(cf, dtype=np.int8)), int(dist)))
+def air_restriction(A: Csr, cf, dist: int = 1, strong=None) -> Csr:
+    """Approximate ideal restriction for the splitting cf (rows: C points);
+    with `strong` (one flag per entry of A) over strong couplings only."""
+    st = None if strong is None else np.ascontiguousarray(strong, dtype=np.uint8)
+    return Csr(lib().or_air_restriction(A.h, _p(np.ascontiguousarray(cf, dtype=np.int8)), int(dist),
+                                        None if st is None else _p(st)))
 
 
 def galerkin(A: Csr, P: Csr) -> Csr:

@@ -52,7 +52,8 @@ typedef struct {
                           two coarsening stages each (P = P_l P_{l+1}, level l+1 dropped) */
   int32_t chunk_coarse; /* hybrid-smoother chunk on levels >= 1 (0: `chunk` everywhere) */
   int32_t restriction;  /* scalar AMG: 0 R = P^T (Galerkin); 1, 2 approximate ideal restriction
-                           over distance-1 / distance-2 F neighbourhoods (Petrov-Galerkin R A P) */
+                           over distance-1 / distance-2 F neighbourhoods, 3 over the distance-1
+                           strongly coupled F points (lAIR); Petrov-Galerkin R A P */
 } or_amg_params;
 
 typedef struct or_amg or_amg;
@@ -91,7 +92,7 @@ void or_pmis(const or_csr *A, const uint8_t *strong, uint64_t seed, int32_t leve
 or_csr *or_interp(const or_csr *A, const uint8_t *strong, const int8_t *cf);
 or_csr *or_interp_ext(const or_csr *A, const uint8_t *strong, const int8_t *cf);
 or_csr *or_galerkin(const or_csr *A, const or_csr *P);
-or_csr *or_air_restriction(const or_csr *A, const int8_t *cf, int32_t dist);
+or_csr *or_air_restriction(const or_csr *A, const int8_t *cf, int32_t dist, const uint8_t *strong);
 int32_t or_jp_colour(const or_csr *A, uint64_t seed, int32_t level, int32_t *colour);
 int32_t or_chunk_rows(const or_csr *A, int32_t chunk);
 int32_t or_chunk_colour(const or_csr *A, int32_t chunk, int32_t *colour);

@@ -687,9 +687,12 @@ void or_dense_lu_solve(int32_t n, const double *a, const int32_t *piv, const dou
  * neighbourhood: row r of R (the r-th C point i, in order) is e_i - z with z
  * supported on N_i and A(N_i, N_i)^T z = A(i, N_i)^T, so (R A)(i, N_i) = 0.
  * N_i: the F points coupled to i in row i (dist = 1), and for dist = 2 also
- * the F points coupled to those in their rows; ascending. The local systems
- * are solved by dense LU with partial pivoting. */
-or_csr *or_air_restriction(const or_csr *A, const int8_t *cf, int32_t dist) {
+ * the F points coupled to those in their rows; ascending. With `strong`
+ * (one flag per entry of A, NULL: every entry) only strong couplings count,
+ * the neighbourhoods of the localised form lAIR (Manteuffel, Muenzenmaier,
+ * Ruge, Southworth 2019). The local systems are solved by dense LU with
+ * partial pivoting. */
+or_csr *or_air_restriction(const or_csr *A, const int8_t *cf, int32_t dist, const uint8_t *strong) {
   int32_t n = A->n, nc = 0;
   for (int32_t i = 0; i < n; i++) nc += cf[i] == 1;
   int32_t *mark = xmalloc(sizeof(int32_t) * ((size_t)n + 1));
@@ -707,7 +710,7 @@ or_csr *or_air_restriction(const or_csr *A, const int8_t *cf, int32_t dist) {
     int32_t m = 0;
     for (int32_t q = A->rowptr[i]; q < A->rowptr[i + 1]; q++) {
       int32_t j = A->col[q];
-      if (j == i || cf[j] == 1 || mark[j] == i) continue;
+      if (j == i || cf[j] == 1 || mark[j] == i || (strong && !strong[q])) continue;
       if (m == ncap) { ncap *= 2; nb = realloc(nb, sizeof(int32_t) * (size_t)ncap); if (!nb) abort(); }
       mark[j] = i;
       nb[m++] = j;
@@ -717,7 +720,7 @@ or_csr *or_air_restriction(const or_csr *A, const int8_t *cf, int32_t dist) {
       for (int32_t a = 0; a < m1; a++)
         for (int32_t q = A->rowptr[nb[a]]; q < A->rowptr[nb[a] + 1]; q++) {
           int32_t j = A->col[q];
-          if (j == i || cf[j] == 1 || mark[j] == i) continue;
+          if (j == i || cf[j] == 1 || mark[j] == i || (strong && !strong[q])) continue;
           if (m == ncap) { ncap *= 2; nb = realloc(nb, sizeof(int32_t) * (size_t)ncap); if (!nb) abort(); }
           mark[j] = i;
           nb[m++] = j;
@@ -847,11 +850,14 @@ or_amg *or_amg_setup(const or_csr *A0, const or_amg_params *prm) {
       if (nc == 0 || (double)nc > 0.9 * (double)n) { free(st); free(cf); break; }
       H->cf[l] = cf;
       H->P[l] = prm->interp == 1 ? or_interp_ext(A, st, cf) : or_interp(A, st, cf);
+      /* AIR restriction, Petrov-Galerkin coarse operator R A P; restriction 3
+       * takes distance-1 neighbourhoods of strong couplings (lAIR) */
+      if (prm->restriction > 0)
+        H->R[l] = prm->restriction == 3 ? or_air_restriction(A, cf, 1, st)
+                                        : or_air_restriction(A, cf, prm->restriction, NULL);
       free(st);
     }
     if (H->b == 1 && prm->restriction > 0) {
-      /* AIR restriction, Petrov-Galerkin coarse operator R A P */
-      H->R[l] = or_air_restriction(A, H->cf[l], prm->restriction);
       or_csr *AP = or_spgemm(A, H->P[l]);
       H->A[l + 1] = or_spgemm(H->R[l], AP);
       or_csr_free(AP);

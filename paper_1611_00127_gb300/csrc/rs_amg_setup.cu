@@ -1115,7 +1115,10 @@ __global__ void k_is_c(int32_t n, const int8_t *__restrict__ cf, int32_t *__rest
 // on local approximate ideal restriction", 2018), distance 1: row r of R, for
 // the r-th C point i, is 1 at i and -z on N_i, the F points coupled to i in
 // row i (ascending, each once), with A(N_i, N_i)^T z = A(i, N_i)^T, so that
-// (R A)(i, N_i) = 0. The local system is solved by LU with partial pivoting
+// (R A)(i, N_i) = 0. With a strength array (one flag per entry of A) N_i
+// keeps only the strong couplings: the localised form lAIR (Manteuffel,
+// Muenzenmaier, Ruge, Southworth 2019), whose coarse operators stay as
+// sparse as Galerkin's on transport-dominated levels. The local system is solved by LU with partial pivoting
 // (largest magnitude, the first one on ties; a zero pivot leaves its column
 // uneliminated and its solution component zero) in the operation order of a
 // plain sequential elimination, which this unit, compiled without FMA
@@ -1124,16 +1127,17 @@ __global__ void k_is_c(int32_t n, const int8_t *__restrict__ cf, int32_t *__rest
 // Per C point: its row length |N_i| + 1 in R, its fine index, and the
 // largest |N_i|.
 __global__ void k_air_count(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                            const int8_t *__restrict__ cf, const int32_t *__restrict__ cidx,
-                            int32_t *__restrict__ rlen, int32_t *__restrict__ cpt, int32_t *__restrict__ mmax) {
+                            const int8_t *__restrict__ cf, const uint8_t *__restrict__ strong,
+                            const int32_t *__restrict__ cidx, int32_t *__restrict__ rlen,
+                            int32_t *__restrict__ cpt, int32_t *__restrict__ mmax) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || cf[i] != 1) return;
   int32_t m = 0;
   for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
     const int32_t j = col[q];
-    if (j == i || cf[j] == 1) continue;
+    if (j == i || cf[j] == 1 || (strong && !strong[q])) continue;
     bool dup = false;
-    for (int32_t q2 = rp[i]; q2 < q && !dup; q2++) dup = col[q2] == j;
+    for (int32_t q2 = rp[i]; q2 < q && !dup; q2++) dup = col[q2] == j && (!strong || strong[q2]);
     if (!dup) m++;
   }
   const int32_t r = cidx[i];
@@ -1160,7 +1164,8 @@ __device__ __forceinline__ int32_t air_find(const int32_t *nb, size_t T, int32_t
 // N_i and the pivots (mx each).
 __global__ void __launch_bounds__(128) k_air_fill(int32_t nc, int32_t T, int32_t mx, const int32_t *__restrict__ rp,
                                                   const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                  const int8_t *__restrict__ cf, const int32_t *__restrict__ cpt,
+                                                  const int8_t *__restrict__ cf, const uint8_t *__restrict__ strong,
+                                                  const int32_t *__restrict__ cpt,
                                                   const int32_t *__restrict__ rrp, double *__restrict__ ws,
                                                   int32_t *__restrict__ wi, int32_t *__restrict__ rcol,
                                                   double *__restrict__ rval) {
@@ -1177,7 +1182,7 @@ __global__ void __launch_bounds__(128) k_air_fill(int32_t nc, int32_t T, int32_t
     int32_t m = 0;
     for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
       const int32_t j = col[q];
-      if (j == i || cf[j] == 1) continue;
+      if (j == i || cf[j] == 1 || (strong && !strong[q])) continue;
       int32_t a = m;
       while (a > 0 && nb[(size_t)(a - 1) * S] > j) a--;
       if (a > 0 && nb[(size_t)(a - 1) * S] == j) continue;
@@ -1258,9 +1263,10 @@ __global__ void __launch_bounds__(128) k_air_fill(int32_t nc, int32_t T, int32_t
 }
 
 // R (nc x n) of level matrix A by approximate ideal restriction, for the marks
-// cf (1 C) and the C index cidx of every C point; nc C points in all.
-static int air_restriction(const DCsr &A, const int8_t *cf, const int32_t *cidx, int32_t nc, DCsr &R,
-                           cudaStream_t s) {
+// cf (1 C) and the C index cidx of every C point; nc C points in all; strong
+// (nullptr: every coupling) limits the neighbourhoods to strong couplings.
+static int air_restriction(const DCsr &A, const int8_t *cf, const int32_t *cidx, int32_t nc, const uint8_t *strong,
+                           DCsr &R, cudaStream_t s) {
   const int32_t n = A.n;
   R.n = nc;
   R.m = n;
@@ -1271,7 +1277,8 @@ static int air_restriction(const DCsr &A, const int8_t *cf, const int32_t *cidx,
   RS_TRY(sc.get(&mmax, 1));
   RS_CHECK_CUDA(cudaMemsetAsync(mmax, 0, sizeof(int32_t), s));
   RS_CHECK_CUDA(cudaMemsetAsync(R.rowptr, 0, sizeof(int32_t) * ((size_t)nc + 1), s));
-  if (n > 0) RS_COUNTED k_air_count<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cf, cidx, R.rowptr, cpt, mmax);
+  if (n > 0) RS_COUNTED k_air_count<<<grid_for(n), kBlock, 0, s>>>(n, A.rowptr, A.col, cf, strong, cidx, R.rowptr, cpt,
+                                                                mmax);
   int32_t nnz = 0, mx = 0;
   RS_TRY(exclusive_scan(R.rowptr, R.rowptr, nc, s, &nnz));
   RS_TRY(sync_copy(&mx, mmax, sizeof(int32_t), s));
@@ -1290,7 +1297,7 @@ static int air_restriction(const DCsr &A, const int8_t *cf, const int32_t *cidx,
   RS_TRY(sc.get(&ws, ((size_t)mx * mx + mx) * T + 1));
   RS_TRY(sc.get(&wi, 2 * (size_t)mx * T + 1));
   RS_COUNTED k_air_fill<<<(unsigned)((T + 127) / 128), 128, 0, s>>>(nc, (int32_t)T, mx, A.rowptr, A.col, A.val, cf,
-                                                                     cpt, R.rowptr, ws, wi, R.col, R.val);
+                                                                     strong, cpt, R.rowptr, ws, wi, R.col, R.val);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }
@@ -1579,7 +1586,9 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           }
           RS_CHECK_CUDA(cudaGetLastError());
         }
-        if (B == 1 && prm.restriction > 0) RS_TRY(air_restriction(L.A, L.cf, isc, nc, L.R, s));
+        // (strong: the strength of L.A, as left by the interpolation)
+        if (B == 1 && prm.restriction > 0)
+          RS_TRY(air_restriction(L.A, L.cf, isc, nc, prm.restriction == 3 ? strong : nullptr, L.R, s));
         else RS_TRY(transpose(P, L.R, s));
         DCsr AP;
         RS_TRY(spgemm(L.A, P, AP, s));

@@ -367,8 +367,8 @@ static int check_params(const rs_amg_params &a) {
   if (a.chunk_coarse != 0 && (a.chunk_coarse < 32 || a.chunk_coarse > 512))
     return fail(RS_EINVAL, "chunk_coarse outside [32, 512]");
   if (a.tail_rows < 0) return fail(RS_EINVAL, "negative tail_rows");
-  if (a.restriction != 0 && a.restriction != 1)
-    return fail(RS_EINVAL, "restriction must be 0 (Galerkin) or 1 (AIR, distance 1)");
+  if (a.restriction != 0 && a.restriction != 1 && a.restriction != 3)
+    return fail(RS_EINVAL, "restriction must be 0 (Galerkin), 1 (AIR, distance 1) or 3 (lAIR)");
   return 0;
 }
 

@@ -1,13 +1,16 @@
-"""Approximate ideal restriction (AIR, distance 1) in the GPU set-up against
-the oracle's `restriction = 1` option.
+"""Approximate ideal restriction in the GPU set-up against the oracle's
+options: `restriction = 1` (AIR over every F coupling, distance 1) and
+`restriction = 3` (lAIR: over the strong couplings only).
 
 * Hierarchies bit-exact (splittings, interpolation, operators A_{l+1} =
   R A P, which carry every value of R, colourings) on the oil-water section's
-  S~, a log-normal S~, 2D Poisson, with and without an aggressive level; the
-  FP64 V-cycle within 1e-10 of the oracle's.
+  S~, a log-normal S~, 2D Poisson, with and without an aggressive level, and
+  for lAIR the 8-level hierarchy of a transport-dominated A_ss; the FP64
+  V-cycle within 1e-10 of the oracle's.
 * Block factorisation with AIR on the first Jacobians of the oil-water runs
-  (linear P_c): FGMRES iterations within 5 % of the oracle's (Ex 2: 72, half
-  the Galerkin count; Ex 4: 268, where Galerkin does not converge in 400).
+  (linear P_c) and, with lAIR, on the 128^2 log-normal Jacobian at capillary
+  scale 1e5, where the Galerkin hierarchies stall: FGMRES iterations within
+  5 % of the oracle's.
 """
 import numpy as np
 import pytest
@@ -46,16 +49,28 @@ def _matrices(oracle, inputs):
     u, uo = inputs.front_state(q)
     ln = _schur(oracle, q, u, uo, inputs.DAY)
     rp, c, v = inputs.poisson_2d(60)
-    return {"oil_water_schur": ow, "lognormal_schur": ln, "poisson": sp.csr_matrix((v, c, rp))}
+    q = inputs.config_lognormal_2d(0.0, n=48)
+    u, uo = inputs.front_state(q)
+    F, J, (brp, bcol) = oracle.assemble(q, u, uo, inputs.DAY)
+    ass = oracle.bsr2_part(brp, bcol, J, 1, 1).scipy().tocsr()
+    ass.sort_indices()
+    return {"oil_water_schur": ow, "lognormal_schur": ln, "poisson": sp.csr_matrix((v, c, rp)),
+            "transport_ass": ass}
 
 
 @pytest.mark.parametrize("agg", [0, 1])
-@pytest.mark.parametrize("which", ["oil_water_schur", "lognormal_schur", "poisson"])
-def test_air_hierarchy_bit_exact(R, oracle, inputs, which, agg):
+@pytest.mark.parametrize("which,rs", [("oil_water_schur", (1, 3)), ("lognormal_schur", (1, 3)), ("poisson", (1, 3)),
+                                      ("transport_ass", (3,))])
+def test_air_hierarchy_bit_exact(R, oracle, inputs, which, rs, agg):
+    for r in rs:
+        _hierarchy_case(R, oracle, inputs, which, r, agg)
+
+
+def _hierarchy_case(R, oracle, inputs, which, r, agg):
     A = _matrices(oracle, inputs)[which]
     rp, c, v = A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data
-    oh = oracle.Amg(oracle.Csr.from_arrays(rp, c, v), oracle.AmgParams(restriction=1, agg_levels=agg, coarse_n=40))
-    gh = R.Amg.setup(R.Csr(rp, c, v), R.AmgParams(restriction=1, agg_levels=agg, coarse_n=40, precision=R.FP64))
+    oh = oracle.Amg(oracle.Csr.from_arrays(rp, c, v), oracle.AmgParams(restriction=r, agg_levels=agg, coarse_n=40))
+    gh = R.Amg.setup(R.Csr(rp, c, v), R.AmgParams(restriction=r, agg_levels=agg, coarse_n=40, precision=R.FP64))
     assert gh.sizes() == oh.sizes() and oh.nlevels >= 3
     for l in range(oh.nlevels):
         g = gh.level(l)
@@ -76,16 +91,27 @@ def test_air_hierarchy_bit_exact(R, oracle, inputs, which, agg):
     gh.close()
 
 
-def test_air_block_factorisation_matches_oracle(R, oracle, inputs):
+def _bf_cases(inputs):
     for ex in (2, 4):
         p = inputs.config_oil_water_2d(ex, inputs.PC_LINEAR)
         u = inputs.uniform_state(p)
-        F, J, (rp, col) = oracle.assemble(p, u, u, inputs.OIL_WATER_DT_DAYS * inputs.DAY)
-        Mo = oracle.Precond(rp, col, J, oracle.PrecParams(kind=3, decouple=0, amg=oracle.AmgParams(restriction=1)))
+        yield p, u, u, inputs.OIL_WATER_DT_DAYS * inputs.DAY
+    p = inputs.config_lognormal_2d(1e5, n=128)
+    u, uo = inputs.front_state(p)
+    yield p, u, uo, inputs.DAY
+
+
+@pytest.mark.parametrize("r", [1, 3])
+def test_air_block_factorisation_matches_oracle(R, oracle, inputs, r):
+    for ex, (p, u, uo, dt) in enumerate(_bf_cases(inputs)):
+        if r == 1 and ex == 2:
+            continue                  # AIR over every coupling: the oil-water cases only
+        F, J, (rp, col) = oracle.assemble(p, u, uo, dt)
+        Mo = oracle.Precond(rp, col, J, oracle.PrecParams(kind=3, decouple=0, amg=oracle.AmgParams(restriction=r)))
         xo, sto, ito, _ = oracle.fgmres(rp, col, J, -F, Mo, maxit=400)
         assert sto == 0
         Jd = R.Bsr2.from_host(rp, col, J)
-        M = R.Precond(Jd, R.PrecParams(kind=3, decouple=0, amg=R.AmgParams(restriction=1, precision=R.FP64)))
+        M = R.Precond(Jd, R.PrecParams(kind=3, decouple=0, amg=R.AmgParams(restriction=r, precision=R.FP64)))
         x = torch.zeros(2 * p.ncell, dtype=torch.float64, device="cuda")
         st = R.gmres_solve(Jd, M, _dev(-F), x, R.GmresParams(maxit=400))
         # FP64 V-cycles in another summation order: restarted FGMRES over a
