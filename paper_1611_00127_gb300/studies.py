@@ -18,9 +18,10 @@ per preconditioner, the quantities the paper's tables print.
 
     python -m paper_1611_00127_gb300.studies gravity [--meshes 20 40 80 160]
         [--examples 1 2 3] [--kinds AMG CPR1 CPR2 BF] [--pc bc|linear]
-        [--prec fp64|fp32] [--rtol 1e-8] [--json out.json]
+        [--prec fp64|fp32] [--rtol 1e-8] [--restriction 0|1|3] [--json out.json]
     python -m paper_1611_00127_gb300.studies oil-water [--examples 1 2 3 4]
-        [--pc linear bc] [--kinds ...] [--prec ...] [--rtol ...] [--json ...]
+        [--pc linear bc] [--kinds ...] [--prec ...] [--rtol ...] [--restriction ...]
+        [--json ...]
 
 Newton takes full steps except that each cell's S_n change is cut to
 [-0.2, 0.2] per iteration (an Appleyard chop): from the uniform initial state
@@ -56,22 +57,24 @@ MAX_DS = 0.2
 
 
 def newton_params(kind: str, precision: int = R.FP64, rtol: float = 1e-8, max_newton: int = 40,
-                  max_ds: float = MAX_DS) -> R.NewtonParams:
+                  max_ds: float = MAX_DS, restriction: int = 0) -> R.NewtonParams:
     k, dec, p1 = KINDS[kind]
     return R.NewtonParams(max_newton=max_newton, ftol=1e-6, max_ds=max_ds,
                           gmres=R.GmresParams(m=30, maxit=1000, rtol=rtol),
-                          prec=R.PrecParams(kind=k, decouple=dec, p1=p1, amg=R.AmgParams(precision=precision)))
+                          prec=R.PrecParams(kind=k, decouple=dec, p1=p1,
+                                            amg=R.AmgParams(precision=precision, restriction=restriction)))
 
 
 def run_steps(p, dt: float, steps: int, kind: str, precision: int = R.FP64, rtol: float = 1e-8,
-              keep_states: bool = False) -> dict:
+              keep_states: bool = False, restriction: int = 0) -> dict:
     """Time-step grid `p` from the uniform initial state (p_w = 1e5 Pa,
     S_n = 0.8) with Newton + FGMRES preconditioned by `kind`. Returns per-step
     and total NI/LI, whether every step converged (a step that does not ends
     the run), wall time, and optionally the state after each step (host
-    arrays)."""
+    arrays). `restriction` is the scalar hierarchies' restriction (0 Galerkin,
+    the paper's; 1 AIR; 3 lAIR)."""
     dp = R.DeviceProblems(p)
-    prm = newton_params(kind, precision, rtol)
+    prm = newton_params(kind, precision, rtol, restriction=restriction)
     u = torch.as_tensor(I.uniform_state(p), device="cuda")
     out = dict(kind=kind, pc_model=p.pc_model, dt_days=dt / I.DAY, steps=[], converged=True)
     states = []
@@ -97,20 +100,21 @@ def run_steps(p, dt: float, steps: int, kind: str, precision: int = R.FP64, rtol
 
 
 def run_case(n: int, example: int, kind: str, pc_model: int = I.PC_BROOKS_COREY, precision: int = R.FP64,
-             rtol: float = 1e-8, steps: int = I.GRAVITY_STEPS, keep_states: bool = False) -> dict:
+             rtol: float = 1e-8, steps: int = I.GRAVITY_STEPS, keep_states: bool = False,
+             restriction: int = 0) -> dict:
     """One (mesh, example, preconditioner) case of the gravity study."""
     p = I.config_gravity_2d(n, example, pc_model)
-    out = run_steps(p, I.GRAVITY_DT_DAYS[example] * I.DAY, steps, kind, precision, rtol, keep_states)
+    out = run_steps(p, I.GRAVITY_DT_DAYS[example] * I.DAY, steps, kind, precision, rtol, keep_states, restriction)
     out.update(n=n, example=example)
     return out
 
 
 def run_oil_water(example: int, pc_model: int, kind: str, precision: int = R.FP64, rtol: float = 1e-8,
-                  steps: int = I.OIL_WATER_STEPS, keep_states: bool = False) -> dict:
+                  steps: int = I.OIL_WATER_STEPS, keep_states: bool = False, restriction: int = 0) -> dict:
     """One (example, capillary model, preconditioner) case of the oil-water
     study."""
     p = I.config_oil_water_2d(example, pc_model)
-    out = run_steps(p, I.OIL_WATER_DT_DAYS * I.DAY, steps, kind, precision, rtol, keep_states)
+    out = run_steps(p, I.OIL_WATER_DT_DAYS * I.DAY, steps, kind, precision, rtol, keep_states, restriction)
     out.update(example=example)
     return out
 
@@ -155,6 +159,8 @@ def main():
     ap.add_argument("--pc", nargs="+", choices=["bc", "linear"], default=None)
     ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--restriction", type=int, choices=[0, 1, 3], default=0,
+                    help="scalar AMG restriction: 0 Galerkin (the paper's), 1 AIR, 3 lAIR")
     ap.add_argument("--json", default=None, help="write every result to this file")
     a = ap.parse_args()
     prec = R.FP64 if a.prec == "fp64" else R.FP32
@@ -166,7 +172,7 @@ def main():
         for ex in examples:
             for k in a.kinds:
                 for m in a.meshes:
-                    r = run_case(m, ex, k, pcm, prec, a.rtol)
+                    r = run_case(m, ex, k, pcm, prec, a.rtol, restriction=a.restriction)
                     results.append(r)
                     print(json.dumps(r), flush=True)
         for ex in examples:
@@ -177,7 +183,7 @@ def main():
         for ex in examples:
             for m in models:
                 for k in a.kinds:
-                    r = run_oil_water(ex, m, k, prec, a.rtol)
+                    r = run_oil_water(ex, m, k, prec, a.rtol, restriction=a.restriction)
                     results.append(r)
                     print(json.dumps(r), flush=True)
         print(oil_water_table(results, a.kinds, examples, models))

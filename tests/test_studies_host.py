@@ -32,6 +32,9 @@ def test_newton_parameters(S):
     assert p.prec.amg.precision == R.FP32
     c = p.c()                      # the ctypes struct the C-ABI receives
     assert c.max_ds == 0.2 and c.prec.p1 == R.P1_ILU0 and c.gmres.maxit == 1000
+    assert c.prec.amg.restriction == 0
+    b = S.newton_params("BF", restriction=3).c()
+    assert b.prec.kind == R.BF and b.prec.amg.restriction == 3 and b.prec.amg.precision == R.FP64
 
 
 def test_report_tables(S):
