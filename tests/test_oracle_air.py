@@ -11,6 +11,11 @@ operators (restriction = 1, 2: distance-1 / distance-2 neighbourhoods).
   the Galerkin (R = P^T) V-cycle diverges (1.58 per cycle): AIR's V-cycle
   converges (0.31).
 * restriction = 0 leaves the Galerkin hierarchy unchanged.
+* lAIR (restriction = 3, strong couplings only): its defining equations,
+  the fill-in it avoids on a transport block, and block factorisation
+  converging where the Galerkin hierarchies stall.
+* The limit: on the oil-water S~ after one Newton step AIR's V-cycle
+  diverges while Galerkin's still contracts.
 """
 import numpy as np
 import pytest
@@ -167,3 +172,21 @@ def test_strong_air_block_factorisation_converges_where_galerkin_stalls(oracle, 
         x, st, its, rr = oracle.fgmres(rp, col, J, -F, M, maxit=300)
         res[r] = (st, its)
     assert res[0][0] != 0 and res[3][0] == 0 and res[3][1] <= 150, res
+
+
+def test_air_on_schur_breaks_on_the_second_newton_jacobian(oracle, inputs):
+    """The limit of AIR here: after one chopped Newton step of the linear
+    Ex 1 oil-water run, AIR's local systems on S~ are nearly singular and
+    its V-cycle diverges (restriction 1: ~3e5 per cycle, lAIR: ~70), while
+    the Galerkin cycle still contracts (0.975)."""
+    p = inputs.config_oil_water_2d(1, inputs.PC_LINEAR)
+    dt = inputs.OIL_WATER_DT_DAYS * inputs.DAY
+    u0 = inputs.uniform_state(p)
+    u1, st, ni, li, _ = oracle.newton(p, u0, u0, dt, oracle.NewtonParams(
+        max_newton=1, max_ds=0.2, prec=oracle.PrecParams(kind=3, decouple=0)))
+    assert ni == 1
+    F, J, (rp, col) = oracle.assemble(p, u1, u0, dt)
+    S = oracle.simple_schur(*[oracle.bsr2_part(rp, col, J, r, c) for r, c in ((0, 0), (0, 1), (1, 0), (1, 1))])
+    A = S.scipy().tocsr()
+    rates = {r: _rate(oracle.Amg(S, oracle.AmgParams(restriction=r)), A) for r in (0, 1, 3)}
+    assert rates[0] < 1.0 and rates[1] > 1e3 and rates[3] > 10.0, rates
