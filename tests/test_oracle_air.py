@@ -1,6 +1,7 @@
 """Pins of the oracle's approximate ideal restriction (AIR; Manteuffel,
 Southworth et al. 2018), an option of its scalar AMG for non-symmetric
-operators (restriction = 1, 2: distance-1 / distance-2 neighbourhoods).
+operators (restriction = 1, 2: distance-1 / distance-2 neighbourhoods; 3:
+the distance-1 strong couplings only, lAIR).
 
 * Defining equations: (R A)(i, N_i) = 0 for every coarse point i, R(i, i) = 1
   and R(i, j) = 0 for the other C points.
