@@ -4,7 +4,9 @@
 using namespace rs;
 
 namespace rs {
-static int check_amg_params(const rs_amg_params &a) {
+// Host-side check of AMG parameters (RS_EINVAL with a message naming the
+// parameter); shared by amg_setup and precond_create.
+int check_amg_params(const rs_amg_params &a) {
   if (!(a.theta >= 0.0 && a.theta <= 1.0)) return fail(RS_EINVAL, "theta outside [0,1]");
   if (a.max_levels < 1 || a.coarse_n < 1 || a.max_dense < 1 || a.max_dense > 8192)
     return fail(RS_EINVAL, "bad level limits");

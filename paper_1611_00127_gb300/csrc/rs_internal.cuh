@@ -235,6 +235,7 @@ struct Hier {
   TailLevel *tail_d = nullptr;
 };
 
+int check_amg_params(const rs_amg_params &a);
 int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off, const rs_amg_params &prm,
               Hier &H, cudaStream_t s);
 void amg_free(Hier &H, cudaStream_t s);

@@ -352,26 +352,6 @@ int precond_apply_impl(const rs_precond *Mc, const double *r, double *z, cudaStr
 }
 }  // namespace rs
 
-static int check_params(const rs_amg_params &a) {
-  if (!(a.theta >= 0.0 && a.theta <= 1.0)) return fail(RS_EINVAL, "theta outside [0,1]");
-  if (a.max_levels < 1 || a.coarse_n < 1 || a.max_dense < 1 || a.max_dense > 8192)
-    return fail(RS_EINVAL, "bad level limits");
-  if (a.smoother != RS_SMOOTH_MCGS && a.smoother != RS_SMOOTH_L1JACOBI && a.smoother != RS_SMOOTH_HYBRID)
-    return fail(RS_EINVAL, "bad smoother");
-  if (a.smoother == RS_SMOOTH_HYBRID && (a.chunk < 32 || a.chunk > 512)) return fail(RS_EINVAL, "chunk outside [32, 512]");
-  if (a.num_functions < 0 || a.num_functions > 2) return fail(RS_EINVAL, "num_functions must be 1 or 2");
-  if (a.nu1 < 0 || a.nu2 < 0 || a.nu1 > 16 || a.nu2 > 16) return fail(RS_EINVAL, "bad sweep counts");
-  if (a.interp != RS_INTERP_CLASSICAL && a.interp != RS_INTERP_EXTI) return fail(RS_EINVAL, "bad interpolation");
-  if (a.precision != RS_PREC_FP32 && a.precision != RS_PREC_FP64) return fail(RS_EINVAL, "bad precision");
-  if (a.agg_levels < 0 || a.agg_levels > 8) return fail(RS_EINVAL, "agg_levels outside [0, 8]");
-  if (a.chunk_coarse != 0 && (a.chunk_coarse < 32 || a.chunk_coarse > 512))
-    return fail(RS_EINVAL, "chunk_coarse outside [32, 512]");
-  if (a.tail_rows < 0) return fail(RS_EINVAL, "negative tail_rows");
-  if (a.restriction != 0 && a.restriction != 1 && a.restriction != 3)
-    return fail(RS_EINVAL, "restriction must be 0 (Galerkin), 1 (AIR, distance 1) or 3 (lAIR)");
-  return 0;
-}
-
 extern "C" int precond_create(const rs_bsr2 *J, const rs_precond_params *params, rs_precond **out,
                               cudaStream_t stream) {
   if (!out) return fail(RS_EINVAL, "null output handle");
@@ -383,7 +363,7 @@ extern "C" int precond_create(const rs_bsr2 *J, const rs_precond_params *params,
   if (params->decouple < RS_DECOUPLE_NONE || params->decouple > RS_DECOUPLE_QIMPES)
     return fail(RS_EINVAL, "unknown decoupling");
   if (params->p1 != RS_P1_BLOCK_JACOBI && params->p1 != RS_P1_ILU0) return fail(RS_EINVAL, "unknown P1");
-  RS_TRY(check_params(params->amg));
+  RS_TRY(check_amg_params(params->amg));
   rs_precond *M = new rs_precond();
   M->prm = *params;
   M->J = *J;
