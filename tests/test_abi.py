@@ -54,6 +54,17 @@ def test_invalid_arguments_rejected_on_host():
     assert L.amg_setup(None, None, ctypes.byref(h), None) == -1
     assert L.gmres_solve(None, None, None, None, None, None, None) == -1
     assert b"invalid" in L.rs_last_error() or b"null" in L.rs_last_error()
+    assert L.ilu0_create(None, 1, ctypes.byref(h), None) == -1
+    assert L.ilu0_create(None, 1, None, None) == -1
+    J = R.Bsr2C(0, 0, None, None, None, 0, None)
+    assert L.ilu0_create(ctypes.byref(J), 5, ctypes.byref(h), None) == -1
+    assert b"precision" in L.rs_last_error()
+    assert L.ilu0_apply(None, None, None, None) == -1
+    assert L.ilu0_info(None, None, None, None) == -1
+    assert L.ilu0_factors(None, None, None) == -1
+    assert L.ilu0_destroy(None) == 0
+    n = ctypes.c_int32()
+    assert L.amg_tail_level(None, ctypes.byref(n)) == -1
 
 
 def test_parameter_validation_on_host():
