@@ -246,10 +246,13 @@ int jacobian_assemble(const rs_problem *probs, int32_t nprob, const double *u, c
  * the library. Scratch lives in fixed arrays of the library's device image
  * (about 3.2 MB held on every GPU that loads the library, until exit).
  * Limits: at most 65536 cells and 64 grids per call, else RS_EINVAL with a
- * message naming the limit. The first call on a device looks up the arrays'
- * device addresses (cudaGetSymbolAddress); make that first call before any
- * stream capture. All calls share the arrays: calls that overlap on the GPU
- * race. Arguments and outputs as for jacobian_assemble. */
+ * message naming the limit. The grid descriptions reach the device as a
+ * kernel parameter; the call copies nothing from host memory. The first call
+ * on a device looks up the arrays' device addresses (cudaGetSymbolAddress);
+ * make that first call before any stream capture. All calls share the
+ * arrays, which keep the last call's contents (every call overwrites what it
+ * reads): calls that overlap on the GPU race. Arguments and outputs as for
+ * jacobian_assemble. */
 int jacobian_assemble_noalloc(const rs_problem *probs, int32_t nprob, const double *u, const double *u_old,
                               double dt, rs_bsr2 *J, double *F, cudaStream_t stream);
 

@@ -28,6 +28,10 @@
 
 namespace rs {
 
+// Largest total cell count of one call (the block layout indexes rows and
+// neighbours in 32-bit integers).
+constexpr int64_t kMaxCells = 0x3fffffff;
+
 struct DProb {
   int32_t dim, nx, ny, nz;
   double hx, hy, hz;
@@ -256,33 +260,43 @@ __global__ void k_assemble(const DProb *probs, int32_t nprob, int32_t ncell, con
   }
 }
 
+// Checks one grid description and fills its device descriptor. Cell counts
+// are formed in 64-bit integers: a product of dimensions that wraps in 32 bits
+// would otherwise pass the limits and let the kernels index past the arrays.
+static int check_grid(const rs_problem &q, int32_t k, int64_t cell0, DProb *out) {
+  if (q.nx < 1 || q.ny < 1 || q.nz < 1 || (q.dim != 2 && q.dim != 3) || (q.dim == 2 && q.nz != 1))
+    return fail(RS_EINVAL, "bad grid dimensions in problem " + std::to_string(k));
+  const int64_t n = (int64_t)q.nx * (int64_t)q.ny * (int64_t)q.nz;
+  if (n > kMaxCells || cell0 + n > kMaxCells)
+    return fail(RS_EINVAL, "too many cells: problem " + std::to_string(k) + " brings the total to " +
+                               std::to_string(cell0 + n) + ", above " + std::to_string(kMaxCells));
+  if (!q.kx || !q.ky || (q.dim == 3 && !q.kz)) return fail(RS_EINVAL, "missing permeability");
+  if (q.pc_model < 0 || q.pc_model > 2 || !(q.bc_lambda > 0) || !(q.mu_w > 0) || !(q.mu_n > 0))
+    return fail(RS_EINVAL, "bad constitutive parameters");
+  if (q.well_in < -1 || q.well_in >= n || q.well_out < -1 || q.well_out >= n ||
+      (q.well_out >= 0 && q.well_out % q.nx != q.nx - 1))
+    return fail(RS_EINVAL, "bad well cells in problem " + std::to_string(k));
+  DProb &p = *out;
+  p.dim = q.dim; p.nx = q.nx; p.ny = q.ny; p.nz = q.nz;
+  p.hx = q.hx; p.hy = q.hy; p.hz = q.hz;
+  p.kx = q.kx; p.ky = q.ky; p.kz = q.kz ? q.kz : q.kx;
+  p.phi = q.phi; p.mu_w = q.mu_w; p.mu_n = q.mu_n; p.rho_w = q.rho_w; p.rho_n = q.rho_n; p.g = q.g;
+  p.pc_model = q.pc_model; p.pc_p0 = q.pc_p0; p.pc_pd = q.pc_pd; p.bc_lambda = q.bc_lambda;
+  p.s_wr = q.s_wr; p.s_nr = q.s_nr; p.u_in = q.u_in; p.p_out = q.p_out; p.sn_out = q.sn_out;
+  p.q_in = q.q_in; p.well_in = q.well_in; p.well_out = q.well_out;
+  p.cell0 = (int32_t)cell0;
+  p.ncell = (int32_t)n;
+  return 0;
+}
+
 static int upload_probs(const rs_problem *probs, int32_t nprob, DProb **d, int32_t *ncell, cudaStream_t s) {
   if (!probs || nprob < 1) return fail(RS_EINVAL, "no problem descriptions");
   std::vector<DProb> h(nprob);
   int64_t tot = 0;
   for (int32_t k = 0; k < nprob; k++) {
-    const rs_problem &q = probs[k];
-    if (q.nx < 1 || q.ny < 1 || q.nz < 1 || (q.dim != 2 && q.dim != 3) || (q.dim == 2 && q.nz != 1))
-      return fail(RS_EINVAL, "bad grid dimensions in problem " + std::to_string(k));
-    if (!q.kx || !q.ky || (q.dim == 3 && !q.kz)) return fail(RS_EINVAL, "missing permeability");
-    if (q.pc_model < 0 || q.pc_model > 2 || !(q.bc_lambda > 0) || !(q.mu_w > 0) || !(q.mu_n > 0))
-      return fail(RS_EINVAL, "bad constitutive parameters");
-    if (q.well_in < -1 || q.well_in >= q.nx * q.ny * q.nz || q.well_out < -1 ||
-        q.well_out >= q.nx * q.ny * q.nz || (q.well_out >= 0 && q.well_out % q.nx != q.nx - 1))
-      return fail(RS_EINVAL, "bad well cells in problem " + std::to_string(k));
-    DProb &p = h[k];
-    p.dim = q.dim; p.nx = q.nx; p.ny = q.ny; p.nz = q.nz;
-    p.hx = q.hx; p.hy = q.hy; p.hz = q.hz;
-    p.kx = q.kx; p.ky = q.ky; p.kz = q.kz ? q.kz : q.kx;
-    p.phi = q.phi; p.mu_w = q.mu_w; p.mu_n = q.mu_n; p.rho_w = q.rho_w; p.rho_n = q.rho_n; p.g = q.g;
-    p.pc_model = q.pc_model; p.pc_p0 = q.pc_p0; p.pc_pd = q.pc_pd; p.bc_lambda = q.bc_lambda;
-    p.s_wr = q.s_wr; p.s_nr = q.s_nr; p.u_in = q.u_in; p.p_out = q.p_out; p.sn_out = q.sn_out;
-    p.q_in = q.q_in; p.well_in = q.well_in; p.well_out = q.well_out;
-    p.cell0 = (int32_t)tot;
-    p.ncell = q.nx * q.ny * q.nz;
-    tot += (int64_t)p.ncell;
+    RS_TRY(check_grid(probs[k], k, tot, &h[k]));
+    tot += (int64_t)h[k].ncell;
   }
-  if (tot > 0x3fffffff) return fail(RS_EINVAL, "too many cells");
   *ncell = (int32_t)tot;
   RS_TRY(dalloc_n(d, (size_t)nprob, s));
   RS_CHECK_CUDA(cudaMemcpyAsync(*d, h.data(), sizeof(DProb) * nprob, cudaMemcpyHostToDevice, s));
@@ -422,7 +436,9 @@ int newton_update(const rs_problem *probs, int32_t nprob, const double *du, doub
 // processes. For them, jacobian_assemble_noalloc does the same work as
 // jacobian_assemble with its scratch (the per-cell constitutive table and the
 // grid descriptors) held in fixed-size arrays that live in the library's
-// device image, so the call itself allocates nothing on the device.
+// device image, so the call itself allocates nothing on the device. The
+// descriptors reach the device as a kernel parameter, not through a copy
+// from host memory.
 //
 // Limits: at most kNoAllocMaxCells cells and kNoAllocMaxGrids grids per call.
 // The arrays exist once per device for as long as the library is loaded
@@ -438,6 +454,19 @@ constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_props[6 * kNoAllocMaxCells];
 static __device__ __align__(256) DProb g_noalloc_grids[kNoAllocMaxGrids];
+
+// The grid descriptors of one call, passed by value as a kernel parameter
+// (64 descriptors of 208 bytes: within the 32 KB parameter limit).
+struct NoAllocGridPack {
+  DProb g[kNoAllocMaxGrids];
+};
+static_assert(sizeof(NoAllocGridPack) <= 32000, "grid pack exceeds the kernel parameter limit");
+
+// Copies the first n descriptors of the parameter into the fixed array.
+__global__ void k_noalloc_grids(const __grid_constant__ NoAllocGridPack pack, int32_t n) {
+  const int i = threadIdx.x;
+  if (i < n) g_noalloc_grids[i] = pack.g[i];
+}
 
 struct NoAllocPtrs {
   double *props = nullptr;
@@ -481,38 +510,22 @@ extern "C" int jacobian_assemble_noalloc(const rs_problem *probs, int32_t nprob,
   if (nprob > kNoAllocMaxGrids)
     return fail(RS_EINVAL, "jacobian_assemble_noalloc: " + std::to_string(nprob) + " grids exceed the limit of " +
                                std::to_string(kNoAllocMaxGrids));
-  DProb h[kNoAllocMaxGrids];
+  NoAllocGridPack pack;
   int64_t tot = 0;
   for (int32_t k = 0; k < nprob; k++) {
-    const rs_problem &q = probs[k];
-    if (q.nx < 1 || q.ny < 1 || q.nz < 1 || (q.dim != 2 && q.dim != 3) || (q.dim == 2 && q.nz != 1))
-      return fail(RS_EINVAL, "bad grid dimensions in problem " + std::to_string(k));
-    if (!q.kx || !q.ky || (q.dim == 3 && !q.kz)) return fail(RS_EINVAL, "missing permeability");
-    if (q.pc_model < 0 || q.pc_model > 2 || !(q.bc_lambda > 0) || !(q.mu_w > 0) || !(q.mu_n > 0))
-      return fail(RS_EINVAL, "bad constitutive parameters");
-    if (q.well_in < -1 || q.well_in >= q.nx * q.ny * q.nz || q.well_out < -1 ||
-        q.well_out >= q.nx * q.ny * q.nz || (q.well_out >= 0 && q.well_out % q.nx != q.nx - 1))
-      return fail(RS_EINVAL, "bad well cells in problem " + std::to_string(k));
-    DProb &p = h[k];
-    p.dim = q.dim; p.nx = q.nx; p.ny = q.ny; p.nz = q.nz;
-    p.hx = q.hx; p.hy = q.hy; p.hz = q.hz;
-    p.kx = q.kx; p.ky = q.ky; p.kz = q.kz ? q.kz : q.kx;
-    p.phi = q.phi; p.mu_w = q.mu_w; p.mu_n = q.mu_n; p.rho_w = q.rho_w; p.rho_n = q.rho_n; p.g = q.g;
-    p.pc_model = q.pc_model; p.pc_p0 = q.pc_p0; p.pc_pd = q.pc_pd; p.bc_lambda = q.bc_lambda;
-    p.s_wr = q.s_wr; p.s_nr = q.s_nr; p.u_in = q.u_in; p.p_out = q.p_out; p.sn_out = q.sn_out;
-    p.q_in = q.q_in; p.well_in = q.well_in; p.well_out = q.well_out;
-    p.cell0 = (int32_t)tot;
-    p.ncell = q.nx * q.ny * q.nz;
-    tot += (int64_t)p.ncell;
+    RS_TRY(check_grid(probs[k], k, tot, &pack.g[k]));
+    tot += (int64_t)pack.g[k].ncell;
+    if (tot > kNoAllocMaxCells)
+      return fail(RS_EINVAL, "jacobian_assemble_noalloc: " + std::to_string(tot) +
+                                 " cells exceed the limit of " + std::to_string(kNoAllocMaxCells));
   }
-  if (tot > kNoAllocMaxCells)
-    return fail(RS_EINVAL, "jacobian_assemble_noalloc: " + std::to_string(tot) + " cells exceed the limit of " +
-                               std::to_string(kNoAllocMaxCells));
   const int32_t ncell = (int32_t)tot;
   if (J && (J->nb != ncell || !J->row_ptr || !J->val)) return fail(RS_EINVAL, "Jacobian does not match the grids");
   NoAllocPtrs d;
   RS_TRY(noalloc_ptrs(&d));
-  RS_CHECK_CUDA(cudaMemcpyAsync(d.grids, h, sizeof(DProb) * nprob, cudaMemcpyHostToDevice, stream));
+  // The descriptors travel as a kernel parameter (copied at launch), so no
+  // host buffer has to outlive this call.
+  RS_COUNTED k_noalloc_grids<<<1, kNoAllocMaxGrids, 0, stream>>>(pack, nprob);
   RS_COUNTED k_props<<<grid_for(ncell), kBlock, 0, stream>>>(d.grids, nprob, ncell, u, d.props);
   RS_COUNTED k_assemble<<<grid_for(ncell, 128), 128, 0, stream>>>(d.grids, nprob, ncell, u, u_old, dt, d.props,
                                                                  J ? J->row_ptr : nullptr, J ? J->val : nullptr, F);

@@ -89,3 +89,38 @@ def test_parameter_validation_on_host():
         h = ctypes.c_void_p()
         assert L.precond_create(ctypes.byref(J), ctypes.byref(pp), ctypes.byref(h), None) == -1, kw
         assert word in L.rs_last_error(), (kw, L.rs_last_error())
+
+
+def test_grid_sizes_checked_in_64_bit_before_any_launch():
+    """A grid whose cell count wraps in 32-bit arithmetic (65537 x 65536
+    wraps to 65536; 65536 x 65536 x 2 wraps to 0) is refused by every call
+    that takes grid descriptions, before any GPU work, and so is a total
+    beyond the 32-bit block index range. The vectors are host dummies that a
+    refused call never touches."""
+    from paper_1611_00127_gb300 import rsflow as R
+    L = R.lib()
+    buf = (ctypes.c_double * 4)()
+    ibuf = (ctypes.c_int32 * 4)()
+    cases = [(3, 65537, 65536, 1), (3, 65536, 65536, 2), (2, 1 << 30, 1, 1), (3, 1024, 1024, 1024)]
+    for dim, nx, ny, nz in cases:
+        arr = (R.Problem * 1)()
+        arr[0] = R.Problem(dim, nx, ny, nz, 1.0, 1.0, 1.0, 0, 0, 0, 0.2, 1e-3, 5e-3, 1000.0, 700.0, 0.0,
+                           2, 0.0, 5e3, 2.0, 0.0, 0.0, 1e-6, 1e5, 0.1, 0.0, -1, -1)
+        ptr = ctypes.cast(buf, ctypes.c_void_p)
+        assert L.jacobian_assemble(arr, 1, ptr, ptr, 86400.0, None, ptr, None) == -1, (nx, ny, nz)
+        assert b"too many cells" in L.rs_last_error(), L.rs_last_error()
+        assert L.jacobian_assemble_noalloc(arr, 1, ptr, ptr, 86400.0, None, ptr, None) == -1, (nx, ny, nz)
+        assert b"too many cells" in L.rs_last_error(), L.rs_last_error()
+        ip = ctypes.cast(ibuf, ctypes.c_void_p)
+        assert L.rs_bsr2_pattern(arr, 1, ip, ip, None) == -1, (nx, ny, nz)
+        assert b"too many cells" in L.rs_last_error(), L.rs_last_error()
+    # two grids that fit alone but not together (dummy permeability pointers:
+    # the first grid passes its own checks)
+    buf_addr = ctypes.addressof(buf)
+    arr = (R.Problem * 2)()
+    for k in range(2):
+        arr[k] = R.Problem(3, 1024, 1024, 600, 1.0, 1.0, 1.0, buf_addr, buf_addr, buf_addr, 0.2, 1e-3, 5e-3, 1000.0, 700.0, 0.0,
+                           2, 0.0, 5e3, 2.0, 0.0, 0.0, 1e-6, 1e5, 0.1, 0.0, -1, -1)
+    ptr = ctypes.cast(buf, ctypes.c_void_p)
+    assert L.jacobian_assemble(arr, 2, ptr, ptr, 86400.0, None, ptr, None) == -1
+    assert b"too many cells" in L.rs_last_error(), L.rs_last_error()
