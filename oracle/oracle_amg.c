@@ -472,13 +472,13 @@ int32_t or_jp_colour(const or_csr *A, uint64_t seed, int32_t level, int32_t *col
   return ncol;
 }
 
-/* Rows per chunk of the hybrid smoother on a matrix: `chunk`, halved (not
- * below 32) while chunk * ceil(nnz / n) exceeds 12288 entries. */
+/* Rows per chunk of the hybrid smoother: the `chunk` parameter (512 when
+ * unset), a plain method parameter like the number of processes of the
+ * parallel hybrid Gauss-Seidel it stands in for (Sec. 4.1). The matrix does
+ * not enter. */
 int32_t or_chunk_rows(const or_csr *A, int32_t chunk) {
-  int32_t C = chunk > 0 ? chunk : 512;
-  int64_t avg = A->n > 0 ? ((int64_t)A->nnz + A->n - 1) / A->n : 1;
-  while (C > 32 && (int64_t)C * avg > 12288) C /= 2;
-  return C;
+  (void)A;
+  return chunk > 0 ? chunk : 512;
 }
 
 /* The hybrid smoother's chunk parameter on level l: `chunk` on level 0,
@@ -1028,8 +1028,7 @@ void or_amg_smooth(const or_amg *H, int32_t l, const double *b, double *x) {
      * Gauss-Seidel of parallel AMG codes, with a chunk in place of a process). */
     double *xo = xmalloc(sizeof(double) * ((size_t)A->n + 1));
     memcpy(xo, x, sizeof(double) * (size_t)A->n);
-    /* chunk size: the `chunk` parameter, halved (not below 32) while
-     * chunk * ceil(nnz / n) exceeds 12288 entries */
+    /* chunk size: the level's `chunk` parameter */
     int32_t C = or_chunk_rows(A, level_chunk(&H->prm, l));
     for (int32_t c0 = 0; c0 < A->n; c0 += C) {
       int32_t c1 = c0 + C < A->n ? c0 + C : A->n;

@@ -1609,25 +1609,15 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
     if (any_smooth && H.prm.smoother == RS_SMOOTH_HYBRID) {
       // chunk k = rows [packed[2k], packed[2k+1]), never spanning two systems;
       // per system the chunk size is `chunk` (`chunk_coarse`, when set, on
-      // levels >= 1), halved (not below 32) while chunk * ceil(nnz / n) of
-      // that system exceeds 12288 entries
-      std::vector<int32_t> rpb(nseg + 1);
-      {
-        int32_t *tmp = nullptr;
-        RS_TRY(sc.get(&tmp, (size_t)nseg + 1));
-        RS_COUNTED k_gather_offsets<<<grid_for(nseg + 1), kBlock, 0, s>>>(nseg + 1, dseg_off, Lc.A.rowptr, tmp);
-        RS_TRY(sync_copy(rpb.data(), tmp, sizeof(int32_t) * (nseg + 1), s));
-      }
+      // levels >= 1)
       std::vector<int32_t> packed, csys;
       int32_t nsm = 0;
       const int32_t C0 = (l == 0 || prm.chunk_coarse <= 0) ? prm.chunk : prm.chunk_coarse;
       Lc.chunk_c = 0;
       for (int32_t q = 0; q < nseg; q++) {
         if (!smooth_seg[q]) continue;
-        const int64_t nq = Lc.seg_off[q + 1] - Lc.seg_off[q], zq = rpb[q + 1] - rpb[q];
-        const int64_t avg = nq > 0 ? (zq + nq - 1) / nq : 1;
-        int32_t C = C0;
-        while (C > 32 && (int64_t)C * avg > 12288) C /= 2;
+        const int64_t nq = Lc.seg_off[q + 1] - Lc.seg_off[q];
+        const int32_t C = C0;
         Lc.chunk_c = std::max(Lc.chunk_c, C);
         for (int32_t r = Lc.seg_off[q]; r < Lc.seg_off[q + 1]; r += C) {
           packed.push_back(r);

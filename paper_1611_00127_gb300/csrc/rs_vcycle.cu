@@ -72,7 +72,9 @@ __global__ void __launch_bounds__(256) k_gs_colour(int32_t nrows, const int32_t 
 // Chunks with more entries than the staging area read their entries from
 // global memory instead. Result in `xnew`; the order of CTAs does not affect
 // it.
-constexpr int kHgsStageEntries = 12288;
+// 16384 packed entries cover a 512-row chunk of a 25-point (3D Schur
+// complement) level: 210 KB of shared memory in FP64 at the largest.
+constexpr int kHgsStageEntries = 16384;
 constexpr int kHgsMaxColours = 128;
 constexpr int kHgsSpin = 1 << 20;     // bound on the mbarrier wait (iterations)
 constexpr int kHgsThreads = 256;      // threads per chunk CTA
@@ -679,6 +681,9 @@ template <>
 const float *binv_of<float>(const Level &L) { return L.binvf; }
 template <>
 const double *binv_of<double>(const Level &L) { return L.binv; }
+
+static_assert(hgs_smem<double>(512, kHgsStageEntries) + 16 <= 232448, "sweep staging exceeds shared memory");
+static_assert(hgs2_smem<double>(512, kHgsStageEntries) + 16 <= 232448, "sweep staging exceeds shared memory");
 
 template <typename T, int LPR>
 static void hgs2_attr() {

@@ -119,9 +119,6 @@ def test_point_colouring_valid_and_first_fit(oracle, inputs):
     G = sp.csr_matrix((np.ones(Ac.nnz), (Ac.row // 2, Ac.col // 2)), shape=(N, N))
     G = ((G + G.T) != 0).tocsr()
     Crows = 512
-    avg = -(-A.nnz // A.shape[0])
-    while Crows > 32 and Crows * avg > 12288:
-        Crows //= 2
     P = Crows // 2
     for p0 in range(0, N, P):
         p1 = min(p0 + P, N)
@@ -146,8 +143,6 @@ def test_point_smoother_sweep_equations(oracle, inputs):
     col, nc = H.colours(0)
     n = A.shape[0]
     Cr = 512
-    while Cr > 32 and Cr * -(-A.nnz // n) > 12288:
-        Cr //= 2
     checked = 0
     for c0 in range(0, n, Cr):
         c1 = min(c0 + Cr, n)
