@@ -276,7 +276,19 @@ int precond_destroy(rs_precond *M);
 /* z = M^{-1} r (Algorithms 1-3 or the black-box V-cycle), FP64 [2N]. */
 int precond_apply(const rs_precond *M, const double *r, double *z, cudaStream_t stream);
 
-/* Right-preconditioned flexible GMRES(m) (Sec. 3, eq. precon-system) for
+/* Capped device waits. A smoother CTA whose staging copies have not landed
+ * within its wait limit leaves its rows unswept and raises a device flag
+ * (no counterpart in the paper: a guard of this implementation).
+ * gmres_solve and newton_step check the flag before they return and report
+ * RS_ETIMEOUT. After the asynchronous calls (precond_apply, amg_apply,
+ * amg_level_smooth) call rs_wait_status: it synchronises `stream`, returns
+ * RS_ETIMEOUT and clears the flag if it was raised, else RS_OK.
+ * rs_raise_wait_flag sets the flag as a capped wait would, without running a
+ * kernel, so that callers can test their handling of the error. */
+int rs_wait_status(cudaStream_t stream);
+int rs_raise_wait_flag(cudaStream_t stream);
+
+/* Right-preconditioned flexible GMRES(m) (Sec. 3, eq. precon-system) for/* Right-preconditioned flexible GMRES(m) (Sec. 3, eq. precon-system) for
  * J x = b, per system of the batch, with classical Gram-Schmidt applied twice
  * and Givens rotations in FP64. x holds the initial guess on entry. M may be
  * NULL (no preconditioner). Returns RS_OK when every system converged, else

@@ -254,6 +254,8 @@ int amg_tail_setup(Hier &H, cudaStream_t s);
 // RS_ETIMEOUT (and clears the flag) if a smoother CTA gave up waiting for its
 // staging copies since the last call; synchronises the stream.
 int vcycle_wait_status(cudaStream_t s);
+// Sets that flag as a capped wait would (no kernel runs).
+int vcycle_raise_wait_flag(cudaStream_t s);
 // ILU(0) of the point-ordered scalar matrix of J (rs_ilu.cu); the factors
 // keep a reference to J's pattern
 int ilu0_build(const rs_bsr2 &J, int precision, rs_ilu0 **out, cudaStream_t s);

@@ -85,6 +85,28 @@ __device__ int g_hgs_wait_timeout;
 
 __host__ __device__ constexpr size_t hgs_seg(size_t bytes) { return ((bytes + 15) & ~size_t(15)) + 16; }
 
+// Bounded wait of every thread of the CTA on the staging mbarrier (phase 0).
+// Returns true, after a barrier, when the copies have landed. When a wait
+// runs out it raises the timeout flag and waits once more, with the same
+// bound, for the copies still in flight; the CTA then agrees (a barrier
+// with a vote) to leave its rows unswept, so no thread reads shared memory
+// the copies may not have filled and no thread exits while a copy of its
+// CTA can still be writing, unless that second wait ran out as well.
+__device__ __forceinline__ bool hgs_wait_staged(uint32_t ubar) {
+  uint32_t done = 0;
+  for (int it = 0; it < kHgsSpin && !done; it++)
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done) : "r"(ubar) : "memory");
+  const bool first = done != 0;
+  if (!first) {
+    atomicOr(&g_hgs_wait_timeout, 1);
+    for (int it = 0; it < kHgsSpin && !done; it++)
+      asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                   : "=r"(done) : "r"(ubar) : "memory");
+  }
+  return __syncthreads_and(first ? 1 : 0) != 0;
+}
+
 // Dynamic shared memory of a sweep CTA: chunks of up to cmax rows, up to
 // `stage` packed entries staged, ncol colours (the colour offsets come last,
 // so a smaller ncol only trims the end).
@@ -213,19 +235,7 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs(const int32_t *__restrict__
   if (!xold)
     for (int32_t t = threadIdx.x; t < len; t += blockDim.x) xs[t] = T(0);
   // bounded wait for the bulk copies (phase 0 of the barrier)
-  {
-    uint32_t done = 0;
-    for (int it = 0; it < kHgsSpin && !done; it++)
-      asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                   : "=r"(done) : "r"(ubar) : "memory");
-    if (!done) {
-      atomicOr(&g_hgs_wait_timeout, 1);
-      for (int it = 0; it < kHgsSpin && !done; it++)
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(done) : "r"(ubar) : "memory");
-    }
-  }
-  __syncthreads();
+  if (!hgs_wait_staged(ubar)) return;
   const int32_t *lrp = g_rp.dst;       // packed row starts of rows r0..r1
   const int32_t *lmd = g_md.dst;       // packed split points
   T *rhs = g_b.dst;
@@ -387,19 +397,7 @@ __global__ void __launch_bounds__(kHgsThreads) k_hgs2(const int32_t *__restrict_
   T *xs = g_x.dst;
   if (!xold)
     for (int32_t t = threadIdx.x; t < len; t += blockDim.x) xs[t] = T(0);
-  {
-    uint32_t done = 0;
-    for (int it = 0; it < kHgsSpin && !done; it++)
-      asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                   : "=r"(done) : "r"(ubar) : "memory");
-    if (!done) {
-      atomicOr(&g_hgs_wait_timeout, 1);
-      for (int it = 0; it < kHgsSpin && !done; it++)
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(done) : "r"(ubar) : "memory");
-    }
-  }
-  __syncthreads();
+  if (!hgs_wait_staged(ubar)) return;
   const int32_t *lrp = g_rp.dst;
   const int32_t *lmd = g_md.dst;
   T *rhs = g_b.dst;
@@ -1309,6 +1307,13 @@ int vcycle_wait_status(cudaStream_t s) {
   return fail(RS_ETIMEOUT, "smoother: a staging copy did not complete within the wait limit");
 }
 
+int vcycle_raise_wait_flag(cudaStream_t s) {
+  const int one = 1;
+  RS_CHECK_CUDA(cudaMemcpyToSymbolAsync(g_hgs_wait_timeout, &one, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+  RS_CHECK_CUDA(cudaStreamSynchronize(s));
+  return 0;
+}
+
 int amg_level_sweeps(const Hier &H, int32_t l, int sweeps, double *bytes_per_sweep, cudaStream_t s) {
   if (l < 0 || l >= H.nlev) return fail(RS_EINVAL, "level out of range");
   const double by = H.precision == RS_PREC_FP32 ? level_sweeps<float>(H, l, sweeps, s)
@@ -1337,3 +1342,7 @@ int amg_vcycle(const Hier &H, const double *b, double *x, cudaStream_t s) {
 }
 
 }  // namespace rs
+
+extern "C" int rs_wait_status(cudaStream_t stream) { return rs::vcycle_wait_status(stream); }
+
+extern "C" int rs_raise_wait_flag(cudaStream_t stream) { return rs::vcycle_raise_wait_flag(stream); }

@@ -18,6 +18,7 @@ import torch
 from . import build as _build
 
 RS_OK, RS_NOT_CONVERGED = 0, 1
+RS_EINVAL, RS_ECUDA, RS_ETIMEOUT = -1, -2, -3
 AMG_J, CPR1, CPR2, BF, AMG_J_SCALAR = 0, 1, 2, 3, 4
 DECOUPLE_NONE, DECOUPLE_ABF, DECOUPLE_QIMPES = 0, 1, 2
 P1_BLOCK_JACOBI, P1_ILU0 = 0, 1
@@ -135,6 +136,8 @@ def _declare(L):
         "rs_tune_set_bsr2_lpr": (C.c_int, [C.c_int]),
         "rs_autotune_bsr2": (C.c_int, [P, P, P, P, P]),
         "rs_launch_count": (C.c_longlong, []),
+        "rs_wait_status": (C.c_int, [P]),
+        "rs_raise_wait_flag": (C.c_int, [P]),
         "rs_profile_begin": (C.c_int, []),
         "rs_profile_end": (C.c_int, [P, P, P, C.c_int]),
     }
@@ -527,6 +530,20 @@ def profile_end():
     lib().rs_profile_end(ms.ctypes.data_as(C.c_void_p), by.ctypes.data_as(C.c_void_p),
                          n.ctypes.data_as(C.c_void_p), k)
     return {PROFILE_CLASSES[i]: (float(ms[i]), float(by[i]), int(n[i])) for i in range(k)}
+
+
+def wait_status(stream=None) -> int:
+    """RS_OK, or RS_ETIMEOUT (the flag is then cleared) when a smoother CTA
+    gave up waiting for its staging copies since the last check."""
+    rc = lib().rs_wait_status(_stream(stream))
+    if rc < 0 and rc != RS_ETIMEOUT:
+        _check(rc, "rs_wait_status")
+    return rc
+
+
+def raise_wait_flag(stream=None):
+    """Set the capped-wait flag without running a kernel (error-path tests)."""
+    _check(lib().rs_raise_wait_flag(_stream(stream)), "rs_raise_wait_flag")
 
 
 def launch_count() -> int:

@@ -157,3 +157,47 @@ def test_two_cell_fluxes_hand_values(R, two_cell_cases):
             val = J.val.cpu().numpy().reshape(-1, 2, 2)
             np.testing.assert_allclose(val[rp[0], 0, 0], c["J00_pw_pw"], rtol=1e-12, err_msg=c["name"])
             np.testing.assert_allclose(val[rp[0] + 1, 0, 0], c["J01_pw_pw"], rtol=1e-12, err_msg=c["name"])
+
+
+def test_capped_wait_reported_and_cleared(R, inputs):
+    """A smoother CTA that gives up waiting for its staging copies raises a
+    device flag. Here the flag is raised from the host (no kernel is made to
+    time out): gmres_solve reports RS_ETIMEOUT and clears it, so the next
+    solve succeeds; rs_wait_status reports it after the asynchronous
+    precond_apply; newton_step returns the error with its statistics
+    filled in for the iteration that met it."""
+    import ctypes
+    p = inputs.config_small_2d()
+    u, uo = inputs.front_state(p)
+    dp = R.DeviceProblems(p)
+    J = R.Bsr2.pattern(dp)
+    F = torch.empty(2 * p.ncell, dtype=torch.float64, device="cuda")
+    R.jacobian_assemble(dp, _dev(u), _dev(uo), inputs.DAY, J, F)
+    b = -F
+    M = R.Precond(J, R.PrecParams(kind=R.CPR1))
+    assert R.wait_status() == R.RS_OK
+    R.raise_wait_flag()
+    with pytest.raises(R.RsError, match="wait limit"):
+        R.gmres_solve(J, M, b, torch.zeros_like(b), R.GmresParams(rtol=1e-8))
+    x = torch.zeros_like(b)
+    st = R.gmres_solve(J, M, b, x, R.GmresParams(rtol=1e-8))
+    assert st.status == R.RS_OK
+    z = torch.empty_like(b)
+    M.apply(b, z)
+    assert R.wait_status() == R.RS_OK
+    R.raise_wait_flag()
+    M.apply(b, z)
+    assert R.wait_status() == R.RS_ETIMEOUT
+    assert R.wait_status() == R.RS_OK
+    M.close()
+    # newton_step through the C-ABI directly, to read its statistics
+    L = R.lib()
+    prm = R.NewtonParams(prec=R.PrecParams(kind=R.CPR1))
+    stc = R.NewtonStatsC()
+    ud = _dev(u)
+    R.raise_wait_flag()
+    rc = L.newton_step(dp.c, len(dp), R._ptr(ud), R._ptr(_dev(uo)), inputs.DAY, ctypes.byref(prm.c()),
+                       ctypes.byref(stc), R._stream())
+    assert rc == R.RS_ETIMEOUT
+    assert stc.newton_its == 1 and stc.linear_its > 0 and stc.fnorm > 0
+    assert R.wait_status() == R.RS_OK
