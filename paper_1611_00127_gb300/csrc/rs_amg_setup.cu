@@ -302,12 +302,11 @@ constexpr int kIF = 256;
 // kIF): small capacities on the fine levels let many warps share an SM.
 struct IWarp {
   double *num, *fa, *fd;
-  int32_t *cand, *chat, *nset, *fk, *cnt;   // cnt: ncand, m, nf
-  uint8_t *first;
+  int32_t *hkey, *chat, *nset, *fk, *cnt;   // hkey: candidate hash set; cnt: -, m, nf
 };
 
 __host__ __device__ inline size_t iwarp_bytes(int ccap, int hcap, int fcap) {
-  return 8 * (size_t)(hcap + 2 * fcap) + 4 * (size_t)(ccap + 2 * hcap + fcap + 4) + (((size_t)ccap + 7) & ~size_t(7));
+  return 8 * (size_t)(hcap + 2 * fcap) + 4 * (size_t)(ccap + 2 * hcap + fcap + 4);
 }
 
 __device__ inline IWarp iwarp_at(unsigned char *base, int ccap, int hcap, int fcap) {
@@ -315,13 +314,65 @@ __device__ inline IWarp iwarp_at(unsigned char *base, int ccap, int hcap, int fc
   W.num = reinterpret_cast<double *>(base);
   W.fa = W.num + hcap;
   W.fd = W.fa + fcap;
-  W.cand = reinterpret_cast<int32_t *>(W.fd + fcap);
-  W.chat = W.cand + ccap;
+  W.hkey = reinterpret_cast<int32_t *>(W.fd + fcap);
+  W.chat = W.hkey + ccap;
   W.nset = W.chat + hcap;
   W.fk = W.nset + hcap;
   W.cnt = W.fk + fcap;
-  W.first = reinterpret_cast<uint8_t *>(W.cnt + 4);
   return W;
+}
+
+// Inserts key into the warp's open-addressing set of 2^tbits slots (-1 =
+// empty), counting new keys in *distinct; false when the set is full.
+__device__ __forceinline__ bool hset_insert(int32_t *keys, int tbits, int32_t key, int32_t *distinct) {
+  const int size = 1 << tbits;
+  int h = (int)(((uint32_t)key * 2654435761u) >> (32 - tbits));
+  for (int probes = 0; probes < size; probes++) {
+    const int32_t prev = atomicCAS(&keys[h], -1, key);
+    if (prev == -1) {
+      atomicAdd(distinct, 1);
+      return true;
+    }
+    if (prev == key) return true;
+    h = (h + 1) & (size - 1);
+  }
+  return false;
+}
+
+// Sorts a[0..m) ascending, one warp; a has room for the next power of two
+// of m (cap, a power of two). Up to 32 values: bitonic network in registers;
+// more: bitonic network in place over the padded array.
+__device__ void warp_sort_asc(int32_t *a, int32_t m, int32_t cap) {
+  const int lane = threadIdx.x & 31;
+  if (m <= 1) return;
+  if (m <= 32) {
+    int32_t v = lane < m ? a[lane] : INT32_MAX;
+    for (int k = 2; k <= 32; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const int32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+        const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+        v = (lower == up) ? min(v, o) : max(v, o);
+      }
+    __syncwarp();
+    if (lane < m) a[lane] = v;
+    __syncwarp();
+    return;
+  }
+  int32_t P = 64;
+  while (P < m) P <<= 1;
+  if (P > cap) P = cap;   // (m <= cap, and cap is a power of two)
+  for (int32_t t = m + lane; t < P; t += 32) a[t] = INT32_MAX;
+  __syncwarp();
+  for (int32_t k = 2; k <= P; k <<= 1)
+    for (int32_t j = k >> 1; j > 0; j >>= 1) {
+      for (int32_t t = lane; t < P / 2; t += 32) {
+        const int32_t i = (t / j) * 2 * j + (t % j), q = i + j;
+        const bool up = (i & k) == 0;
+        const int32_t x = a[i], y = a[q];
+        if ((x > y) == up) { a[i] = y; a[q] = x; }
+      }
+      __syncwarp();
+    }
 }
 
 // bounds of a level for the interpolation capacities: the largest number of
@@ -374,9 +425,21 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
       continue;
     }
     const int32_t s = rp[i], e = rp[i + 1];
-    if (lane == 0) { W.cnt[0] = 0; W.cnt[2] = 0; }
+    // this row's hash set: a power of two at least twice its number of
+    // candidate entries (with repeats), within the level's capacity
+    int32_t bnd = 0;
+    for (int32_t q = s + lane; q < e; q += 32) {
+      const int32_t j = col[q];
+      if (j != i && strong[q]) bnd += cf[j] == 1 ? 1 : rp[j + 1] - rp[j];
+    }
+    bnd = __reduce_add_sync(0xffffffffu, bnd);
+    int tbits = 5;
+    while ((1 << tbits) < ccap && (1 << tbits) < 2 * bnd) tbits++;
+    for (int h = lane; h < (1 << tbits); h += 32) W.hkey[h] = -1;
+    if (lane == 0) { W.cnt[1] = 0; W.cnt[2] = 0; }
     __syncwarp();
-    // candidates for Chat_i, and the strong F neighbours in row order
+    // candidates for Chat_i (strong C neighbours of i and of its strong F
+    // neighbours) into the set, and the strong F neighbours in row order
     bool ovf = false;
     for (int32_t b0 = s; b0 < e; b0 += 32) {
       const int32_t q = b0 + lane;
@@ -385,17 +448,11 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
       if (q < e) { j = col[q]; st = j != i && strong[q]; }
       const bool isC = st && cf[j] == 1;
       const bool isF = st && cf[j] != 1;
-      if (isC) {
-        const int32_t p = atomicAdd(&W.cnt[0], 1);
-        if (p < ccap) W.cand[p] = j; else ovf = true;
-      }
+      if (isC && !hset_insert(W.hkey, tbits, j, &W.cnt[1])) ovf = true;
       if (isF) {
         for (int32_t t = rp[j]; t < rp[j + 1]; t++) {
           const int32_t l = col[t];
-          if (l != j && strong[t] && cf[l] == 1) {
-            const int32_t p = atomicAdd(&W.cnt[0], 1);
-            if (p < ccap) W.cand[p] = l; else ovf = true;
-          }
+          if (l != j && strong[t] && cf[l] == 1 && !hset_insert(W.hkey, tbits, l, &W.cnt[1])) ovf = true;
         }
       }
       const unsigned fm = __ballot_sync(0xffffffffu, isF);
@@ -409,31 +466,20 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
       if (lane == 0) W.cnt[2] = nf0 + __popc(fm);
       __syncwarp();
     }
-    const int32_t ncand = W.cnt[0], nf = W.cnt[2];
-    ovf = __any_sync(0xffffffffu, ovf) || ncand > ccap || nf > fcap;
-    // sorted distinct candidates -> Chat_i: mark first occurrences, then rank
-    // each first occurrence among the others
-    int32_t mloc = 0;
+    const int32_t m = W.cnt[1], nf = W.cnt[2];
+    ovf = __any_sync(0xffffffffu, ovf) || m > hcap || nf > fcap;
+    // Chat_i: the distinct candidates in ascending order
     if (!ovf) {
-      for (int32_t a = lane; a < ncand; a += 32) {
-        const int32_t v = W.cand[a];
-        uint8_t fst = 1;
-        for (int32_t b = 0; b < a; b++)
-          if (W.cand[b] == v) { fst = 0; break; }
-        W.first[a] = fst;
+      int32_t base = 0;
+      for (int32_t h0 = 0; h0 < (1 << tbits); h0 += 32) {
+        const int32_t v = W.hkey[h0 + lane];
+        const unsigned occ = __ballot_sync(0xffffffffu, v >= 0);
+        if (v >= 0) W.chat[base + __popc(occ & lt)] = v;
+        base += __popc(occ);
       }
       __syncwarp();
-      for (int32_t a = lane; a < ncand; a += 32) {
-        if (!W.first[a]) continue;
-        const int32_t v = W.cand[a];
-        int32_t rank = 0;
-        for (int32_t b = 0; b < ncand; b++) rank += (W.first[b] && W.cand[b] < v);
-        if (rank < hcap) W.chat[rank] = v; else ovf = true;
-        mloc++;
-      }
+      warp_sort_asc(W.chat, m, hcap);
     }
-    const int32_t m = __reduce_add_sync(0xffffffffu, mloc);
-    ovf = __any_sync(0xffffffffu, ovf) || m > hcap;
     __syncwarp();
     if (ovf) {
       if (lane == 0) { atomicExch(err, 1); if (!WRITE) prp[i] = 0; }
@@ -480,37 +526,62 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
       W.num[idx] = nm.v;
       W.nset[idx] = nm.set ? 1 : 0;
     }
-    // dtil: pass A over row i, then the "+i" terms of the k (ascending), lane 0
-    double dt = 0.0;
-    if (lane == 0) {
-      Acc a{0.0, false};
-      int32_t f = 0;
-      for (int32_t q = s; q < e; q++) {
-        const int32_t j = col[q];
-        const double v = val[q];
-        if (j == i) { a.add(v); continue; }
-        if (find_sorted(W.chat, m, j) >= 0) continue;
-        if (strong[q] && cf[j] != 1) {
-          if (W.fd[f] == 0.0) a.add(v);
-          f++;
-          continue;
+    // dtil: pass A over row i, then the "+i" terms of the k (ascending). The
+    // lanes look up the terms of 32 entries at a time; lane 0 adds them in
+    // row order (the order, and so the rounding, of a sequential sum).
+    Acc a{0.0, false};
+    {
+      int32_t fbase = 0;   // strong F entries of row i before this chunk
+      for (int32_t b0 = s; b0 < e; b0 += 32) {
+        const int32_t q = b0 + lane;
+        bool has = false, isF = false;
+        double v = 0.0;
+        if (q < e) {
+          const int32_t j = col[q];
+          v = val[q];
+          if (j == i) has = true;
+          else if (find_sorted(W.chat, m, j) < 0) {
+            isF = strong[q] && cf[j] != 1;
+            has = !isF;
+          }
         }
-        a.add(v);
+        const unsigned fm = __ballot_sync(0xffffffffu, isF);
+        if (isF) has = W.fd[fbase + __popc(fm & lt)] == 0.0;
+        fbase += __popc(fm);
+        const unsigned hm = __ballot_sync(0xffffffffu, has);
+        for (int t = 0; t < 32; t++) {
+          const double vt = __shfl_sync(0xffffffffu, v, t);
+          if (lane == 0 && ((hm >> t) & 1u)) a.add(vt);
+        }
       }
-      for (int32_t g = 0; g < nf; g++) {
-        const double d = W.fd[g];
-        if (d == 0.0) continue;
-        const int32_t k = W.fk[g];
-        const int32_t qk = find_row(col, rp[k], rp[k + 1], i);
-        if (qk < 0) continue;
-        const double sk = diag[k] < 0.0 ? -1.0 : 1.0;
-        const double av = val[qk];
-        if (!(sk * av < 0.0)) continue;
-        const double tq = W.fa[g] / d;
-        a.add(tq * av);
+      for (int32_t g0 = 0; g0 < nf; g0 += 32) {
+        const int32_t g = g0 + lane;
+        bool has = false;
+        double term = 0.0;
+        if (g < nf) {
+          const double d = W.fd[g];
+          if (d != 0.0) {
+            const int32_t k = W.fk[g];
+            const int32_t qk = find_row(col, rp[k], rp[k + 1], i);
+            if (qk >= 0) {
+              const double sk = diag[k] < 0.0 ? -1.0 : 1.0;
+              const double av = val[qk];
+              if (sk * av < 0.0) {
+                const double tq = W.fa[g] / d;
+                term = tq * av;
+                has = true;
+              }
+            }
+          }
+        }
+        const unsigned hm = __ballot_sync(0xffffffffu, has);
+        for (int t = 0; t < 32; t++) {
+          const double vt = __shfl_sync(0xffffffffu, term, t);
+          if (lane == 0 && ((hm >> t) & 1u)) a.add(vt);
+        }
       }
-      dt = a.v;
     }
+    double dt = a.v;
     dt = __shfl_sync(0xffffffffu, dt, 0);
     __syncwarp();
     // output the set entries in Chat order
@@ -1529,6 +1600,12 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
             ishm = wb * iw;
           }
           const unsigned gw = (unsigned)std::min<int64_t>((F.n + iw - 1) / iw, (int64_t)num_sms() * 64);
+          // algorithmic bytes of one pass: the level's rows once (column,
+          // value, strength flag per entry; row start, diagonal, C/F mark
+          // and coarse index per row)
+          const double ibytes = (double)F.nnz * 13.0 + (double)F.n * 17.0;
+          {
+          ProfScope ps(kProfInterp, ibytes, s);
           if (prm.interp == RS_INTERP_CLASSICAL)
             RS_COUNTED k_interp_classical<false><<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong, cfu,
                                                                        isc, Pf.rowptr, nullptr, nullptr, err);
@@ -1536,6 +1613,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
             RS_COUNTED k_interp_ext_w<false><<<gw, 32 * iw, ishm, s>>>(F.n, ccap, hcap, fcap, F.rowptr, F.col, F.val,
                                                                        diag, strong, cfu, isc, Pf.rowptr, nullptr,
                                                                        nullptr, err);
+          }
           int32_t pnnz = 0;
           RS_TRY(exclusive_scan(Pf.rowptr, Pf.rowptr, F.n, s, &pnnz));
           int32_t herr = 0;
@@ -1544,6 +1622,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           Pf.nnz = pnnz;
           RS_TRY(dalloc_n(&Pf.col, (size_t)pnnz + 1, s));
           RS_TRY(dalloc_n(&Pf.val, (size_t)pnnz + 1, s));
+          ProfScope ps(kProfInterp, ibytes + (double)pnnz * 12.0, s);
           if (prm.interp == RS_INTERP_CLASSICAL)
             RS_COUNTED k_interp_classical<true><<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong, cfu,
                                                                       isc, Pf.rowptr, Pf.col, Pf.val, err);

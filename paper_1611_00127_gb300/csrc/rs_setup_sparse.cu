@@ -155,36 +155,113 @@ int block_diag_inverse(const rs_bsr2 &J, double *dinv, cudaStream_t s) {
 // take the (distinct) entries of B's row k, so every C(i,j) receives its
 // terms in ascending k. Pass 1 counts distinct columns, pass 2 accumulates,
 // sorts the row by column and writes it.
-constexpr int kHash = 2048;       // largest per-row table (slots)
+//
+// Rows are binned by the table they need, so that the many short rows run
+// with small tables (many warps per SM) and only the long ones with large
+// tables: pass 1 sizes a row's table from its product count (an upper bound
+// of its distinct columns), pass 2 from twice the exact distinct count that
+// pass 1 found (short probe sequences).
+constexpr int kHashBits = 11;
+constexpr int kHash = 1 << kHashBits;     // largest per-row table (slots)
 constexpr int kGemmThreads = 256;
+constexpr int kGemmBins = kHashBits - 4;  // tables of 32 .. kHash slots
+constexpr int kGemmSmem = 96 * 1024;      // shared memory budget of one CTA
 
 // table slot of a column key (Fibonacci hashing into 2^tbits slots)
 __device__ __forceinline__ int hslot(int32_t key, int tbits) {
   return (int)(((uint32_t)key * 2654435761u) >> (32 - tbits));
 }
 
-// largest number of products of one row of A with B (an upper bound of the
-// row's distinct output columns)
-__global__ void k_spgemm_maxprod(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
-                                 const int32_t *__restrict__ brp, int32_t *mx) {
+// bin of a row that needs `need` slots: the smallest table of 32 << b slots
+// that holds them (the largest bin when none does; the product kernel then
+// reports the overflow)
+__device__ __forceinline__ int gemm_bin(int64_t need) {
+  int b = 0;
+  while (b < kGemmBins - 1 && (int64_t(32) << b) < need) b++;
+  return b;
+}
+
+// pass-1 bins: the number of products of each row of A with B
+__global__ void k_spgemm_bin1(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
+                              const int32_t *__restrict__ brp, uint8_t *bin, int32_t *bincnt) {
   const int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n) return;
-  int32_t np = 0;
+  int64_t np = 0;
   for (int32_t ka = arp[row]; ka < arp[row + 1]; ka++) {
     const int32_t k = acol[ka];
     np += brp[k + 1] - brp[k];
   }
-  atomicMax(mx, np);
+  const int b = gemm_bin(np);
+  bin[row] = (uint8_t)b;
+  atomicAdd(&bincnt[b], 1);
 }
 
-// One warp per row, with a hash table of `tcap` slots per warp in shared
-// memory (tcap sized from the level's largest row, so small rows leave room
-// for many warps per SM); each row uses the smallest power of two >= 2x its
-// product count. Products are accumulated in ascending inner index (the ka
-// loop is sequential, a B row holds each column once), so sums are
-// reproducible.
+// pass-2 bins: twice the distinct count found by pass 1 (crp scanned)
+__global__ void k_spgemm_bin2(int32_t n, const int32_t *__restrict__ crp, uint8_t *bin, int32_t *bincnt) {
+  const int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const int b = gemm_bin(2 * (int64_t)(crp[row + 1] - crp[row]));
+  bin[row] = (uint8_t)b;
+  atomicAdd(&bincnt[b], 1);
+}
+
+// rows listed bin after bin (any order inside a bin)
+__global__ void k_spgemm_binfill(int32_t n, const uint8_t *__restrict__ bin, int32_t *cursor, int32_t *rows) {
+  const int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  rows[atomicAdd(&cursor[bin[row]], 1)] = row;
+}
+
+// Sorts the pairs (key[t], val[t]), t < cnt, by key (keys distinct), one
+// warp; the arrays have room for the next power of two of cnt (<= tsize).
+__device__ void warp_sort_pairs(int32_t *key, double *val, int32_t cnt, int tsize) {
+  const int lane = threadIdx.x & 31;
+  if (cnt <= 1) return;
+  if (cnt <= 32) {
+    int32_t k = lane < cnt ? key[lane] : INT32_MAX;
+    double v = lane < cnt ? val[lane] : 0.0;
+    for (int kk = 2; kk <= 32; kk <<= 1)
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        const int32_t ok = __shfl_xor_sync(0xffffffffu, k, j);
+        const double ov = __shfl_xor_sync(0xffffffffu, v, j);
+        const bool up = (lane & kk) == 0, lower = (lane & j) == 0;
+        const bool take = (lower == up) ? (ok < k) : (ok > k);
+        if (take) { k = ok; v = ov; }
+      }
+    __syncwarp();
+    if (lane < cnt) { key[lane] = k; val[lane] = v; }
+    __syncwarp();
+    return;
+  }
+  int32_t P = 64;
+  while (P < cnt) P <<= 1;
+  if (P > tsize) P = tsize;
+  for (int32_t t = cnt + lane; t < P; t += 32) key[t] = INT32_MAX;
+  __syncwarp();
+  for (int32_t kk = 2; kk <= P; kk <<= 1)
+    for (int32_t j = kk >> 1; j > 0; j >>= 1) {
+      for (int32_t t = lane; t < P / 2; t += 32) {
+        const int32_t a = (t / j) * 2 * j + (t % j), b = a + j;
+        const bool up = (a & kk) == 0;
+        const int32_t x = key[a], y = key[b];
+        if ((x > y) == up) {
+          key[a] = y;
+          key[b] = x;
+          const double w = val[a];
+          val[a] = val[b];
+          val[b] = w;
+        }
+      }
+      __syncwarp();
+    }
+}
+
+// One warp per listed row, tables of 2^tbits slots in shared memory.
+// Products are accumulated in ascending inner index (the ka loop is
+// sequential, a B row holds each column once), so sums are reproducible.
 template <bool NUMERIC>
-__global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t n, int32_t tcap, const int32_t *__restrict__ arp,
+__global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const int32_t *__restrict__ rows, int tbits,
+                                                         const int32_t *__restrict__ arp,
                                                          const int32_t *__restrict__ acol,
                                                          const double *__restrict__ aval,
                                                          const int32_t *__restrict__ brp,
@@ -194,21 +271,13 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t n, int32_t tcap
                                                          double *__restrict__ cval, int32_t *err) {
   extern __shared__ unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  double *vals = reinterpret_cast<double *>(smem) + (int64_t)warp * tcap;
-  int32_t *keys = reinterpret_cast<int32_t *>(smem + sizeof(double) * (size_t)tcap * nwarps) + (int64_t)warp * tcap;
+  const int tsize = 1 << tbits;
+  double *vals = reinterpret_cast<double *>(smem) + (int64_t)warp * tsize;
+  int32_t *keys = reinterpret_cast<int32_t *>(smem + sizeof(double) * (size_t)tsize * nwarps) + (int64_t)warp * tsize;
   __shared__ int32_t cnt_s[kGemmThreads / 32];
-  for (int32_t row = blockIdx.x * nwarps + warp; row < n; row += gridDim.x * nwarps) {
+  for (int32_t r = blockIdx.x * nwarps + warp; r < nrows; r += gridDim.x * nwarps) {
+    const int32_t row = rows[r];
     const int32_t as = arp[row], ae = arp[row + 1];
-    // upper bound of distinct columns: the number of products
-    int32_t np = 0;
-    for (int32_t ka = as + lane; ka < ae; ka += 32) {
-      const int32_t k = acol[ka];
-      np += brp[k + 1] - brp[k];
-    }
-    np = __reduce_add_sync(0xffffffffu, np);
-    int tbits = 5;
-    while ((1 << tbits) < tcap && (1 << tbits) < 2 * np) tbits++;
-    const int tsize = 1 << tbits;
     for (int h = lane; h < tsize; h += 32) keys[h] = -1;
     if (lane == 0) cnt_s[warp] = 0;
     __syncwarp();
@@ -242,10 +311,10 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t n, int32_t tcap
     if (cnt > tsize && lane == 0) atomicExch(err, 1);
     if (!NUMERIC) {
       if (lane == 0) crp[row] = cnt;
-    } else {
+    } else if (cnt <= tsize) {
       // compact the occupied slots to the front of the table (in place: a
       // slot moves only to a lower index, after the whole warp has read its
-      // chunk), then rank each entry by column and scatter to the output row
+      // chunk), sort them by column and write the output row
       int32_t base_c = 0;
       for (int h0 = 0; h0 < tsize; h0 += 32) {
         const int32_t j = keys[h0 + lane];
@@ -260,17 +329,46 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t n, int32_t tcap
         base_c += __popc(occ);
         __syncwarp();
       }
-      const int32_t base = crp[row];
-      for (int32_t a = lane; a < cnt; a += 32) {
-        const int32_t j = keys[a];
-        int32_t rank = 0;
-        for (int32_t g = 0; g < cnt; g++) rank += keys[g] < j;
-        ccol[base + rank] = j;
-        cval[base + rank] = vals[a];
+      warp_sort_pairs(keys, vals, cnt, tsize);
+      const int32_t base = crp[row], room = crp[row + 1] - base;
+      if (room != cnt && lane == 0) atomicExch(err, 1);
+      for (int32_t a = lane; a < cnt && a < room; a += 32) {
+        ccol[base + a] = keys[a];
+        cval[base + a] = vals[a];
       }
     }
     __syncwarp();
   }
+}
+
+// Lists the rows bin by bin (bin counts bincnt_d on the device) and launches
+// the product kernel once per non-empty bin with that bin's table size.
+template <bool NUMERIC>
+static int spgemm_pass(const DCsr &A, const DCsr &B, DCsr &C, const uint8_t *bin, const int32_t *bincnt_d,
+                       int32_t *cursor, int32_t *rows, int32_t *err, cudaStream_t s) {
+  int32_t hcnt[kGemmBins];
+  RS_CHECK_CUDA(cudaMemcpyAsync(hcnt, bincnt_d, sizeof(hcnt), cudaMemcpyDeviceToHost, s));
+  RS_CHECK_CUDA(cudaStreamSynchronize(s));
+  int32_t hoff[kGemmBins + 1];
+  hoff[0] = 0;
+  for (int b = 0; b < kGemmBins; b++) hoff[b + 1] = hoff[b] + hcnt[b];
+  RS_CHECK_CUDA(cudaMemcpyAsync(cursor, hoff, sizeof(int32_t) * kGemmBins, cudaMemcpyHostToDevice, s));
+  RS_COUNTED k_spgemm_binfill<<<grid_for(A.n), kBlock, 0, s>>>(A.n, bin, cursor, rows);
+  // (cudaMemcpyAsync from the pageable stack array hoff stages the data
+  // before it returns)
+  for (int b = 0; b < kGemmBins; b++) {
+    if (hcnt[b] == 0) continue;
+    const int tbits = 5 + b, tsize = 1 << tbits;
+    const int warps =
+        (int)std::max<int64_t>(1, std::min<int64_t>(kGemmThreads / 32, kGemmSmem / (12 * (int64_t)tsize)));
+    const size_t shm = (sizeof(double) + sizeof(int32_t)) * (size_t)tsize * warps;
+    const unsigned grid = (unsigned)std::min<int64_t>((hcnt[b] + warps - 1) / warps, (int64_t)num_sms() * 32);
+    RS_COUNTED k_spgemm<NUMERIC><<<grid, 32 * warps, shm, s>>>(hcnt[b], rows + hoff[b], tbits, A.rowptr, A.col,
+                                                               A.val, B.rowptr, B.col, B.val, C.rowptr, C.col,
+                                                               C.val, err);
+  }
+  RS_CHECK_CUDA(cudaGetLastError());
+  return 0;
 }
 
 int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
@@ -278,34 +376,26 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   C.m = B.m;
   RS_TRY(dalloc_n(&C.rowptr, (size_t)A.n + 1, s));
   Scratch sc(s);
-  int32_t *err = nullptr;
+  int32_t *err = nullptr, *bincnt = nullptr, *cursor = nullptr, *rows = nullptr;
+  uint8_t *bin = nullptr;
   RS_TRY(sc.get(&err, 2));
+  RS_TRY(sc.get(&bincnt, 2 * kGemmBins));
+  RS_TRY(sc.get(&cursor, kGemmBins));
+  RS_TRY(sc.get(&rows, (size_t)A.n + 1));
+  RS_TRY(sc.get(&bin, (size_t)A.n + 1));
   RS_CHECK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), s));
+  RS_CHECK_CUDA(cudaMemsetAsync(bincnt, 0, 2 * kGemmBins * sizeof(int32_t), s));
   static bool attr = false;
   if (!attr) {
-    const int mx = (int)(sizeof(double) + sizeof(int32_t)) * kHash * (kGemmThreads / 32);
-    RS_CHECK_CUDA(cudaFuncSetAttribute(k_spgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    RS_CHECK_CUDA(cudaFuncSetAttribute(k_spgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    RS_CHECK_CUDA(cudaFuncSetAttribute(k_spgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
+    RS_CHECK_CUDA(cudaFuncSetAttribute(k_spgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
     attr = true;
   }
-  // per-warp table: twice the largest row's product count, as a power of two
-  // (32..kHash); rows with more products than kHash / 2 are an error
-  int32_t maxprod = 0;
-  if (A.n > 0) {
-    RS_COUNTED k_spgemm_maxprod<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, B.rowptr, err + 1);
-    RS_CHECK_CUDA(cudaMemcpyAsync(&maxprod, err + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    RS_CHECK_CUDA(cudaStreamSynchronize(s));
-  }
-  int32_t tcap = 32;
-  while (tcap < kHash && tcap < 2 * maxprod) tcap *= 2;
-  // as many warps per CTA as keep a CTA's tables within 48 KB (1..8)
-  int warps = (int)std::min<int64_t>(kGemmThreads / 32, std::max<int64_t>(1, (48 * 1024) / (12 * (int64_t)tcap)));
-  const size_t shm = (sizeof(double) + sizeof(int32_t)) * (size_t)tcap * warps;
-  const unsigned grid = (unsigned)std::min<int64_t>((A.n + warps - 1) / warps, (int64_t)num_sms() * 32);
   ProfScope ps(kProfSpgemm, A.nnz * 12.0 + B.nnz * 12.0, s);
-  if (A.n > 0)
-    RS_COUNTED k_spgemm<false><<<grid, 32 * warps, shm, s>>>(A.n, tcap, A.rowptr, A.col, A.val, B.rowptr, B.col,
-                                                             B.val, C.rowptr, nullptr, nullptr, err);
+  if (A.n > 0) {
+    RS_COUNTED k_spgemm_bin1<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, B.rowptr, bin, bincnt);
+    RS_TRY(spgemm_pass<false>(A, B, C, bin, bincnt, cursor, rows, err, s));
+  }
   int32_t tot = 0;
   RS_TRY(exclusive_scan(C.rowptr, C.rowptr, A.n, s, &tot));
   int32_t herr = 0;
@@ -315,9 +405,13 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   C.nnz = tot;
   RS_TRY(dalloc_n(&C.col, (size_t)tot, s));
   RS_TRY(dalloc_n(&C.val, (size_t)tot, s));
-  if (A.n > 0)
-    RS_COUNTED k_spgemm<true><<<grid, 32 * warps, shm, s>>>(A.n, tcap, A.rowptr, A.col, A.val, B.rowptr, B.col,
-                                                            B.val, C.rowptr, C.col, C.val, err);
+  if (A.n > 0) {
+    RS_COUNTED k_spgemm_bin2<<<grid_for(A.n), kBlock, 0, s>>>(A.n, C.rowptr, bin, bincnt + kGemmBins);
+    RS_TRY(spgemm_pass<true>(A, B, C, bin, bincnt + kGemmBins, cursor, rows, err, s));
+    RS_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RS_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (herr) return fail(RS_ESETUP, "sparse product row exceeds the per-row table");
+  }
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }
