@@ -1,17 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: Jacobian solves per second to a 1e-8 relative residual.
 
-Workload (one "step"): the 256x256-cell 2D log-normal permeability grid
-(sigma 2, correlation length 8 cells, mean ln 1e-12), capillary scale swept over
-{0, 1e3, 1e4, 1e5} Pa; for each scale the exact Newton Jacobian at the
-synthetic front state is assembled on the GPU and solved by right-
-preconditioned FGMRES(30) with each of the three preconditioners (black-box
-AMG on J, CPR-AMG with quasi-IMPES decoupling, block factorisation with the
-SIMPLE Schur complement): 12 solves per step, each with its own
-preconditioner setup. V-cycles run in FP64 for the headline number (the
-workload's "plain FP64 on GPU"); the same step with FP32 V-cycles is reported
-beside it. A solve counts when its true relative residual is <= 1e-8 within
-`--maxit` Arnoldi steps.
+Headline workload (one "step"): the 256^3-cell 3D channelised grid (33.5M
+unknowns; 30 % channel facies from a Gaussian field with correlation lengths
+64/8/4 cells, k = 1e-11 in channels and 1e-15 outside, times a unit log-normal
+noise; Brooks-Corey entry pressure 1e4 Pa) at the first Newton iterate of its
+first one-day backward-Euler step. Each step assembles F and the exact
+Jacobian J on the GPU and solves J dx = -F twice, with CPR-AMG (quasi-IMPES
+decoupling, Alg. 1) and with block factorisation (SIMPLE Schur complement,
+Alg. 3), each from its own preconditioner set-up: right-preconditioned
+FGMRES(30) in FP64 with FP32 V-cycles, to a true relative residual of 1e-8.
+A solve counts when it converges within `--maxit` Arnoldi steps; solves/s is
+converged solves over the wall time of assembly + set-ups + solves.
+
+Beside it, on one GPU: the same step with FP64 V-cycles; the 128^3 layered
+grid with FP32 and FP64 V-cycles; the 256x256 log-normal grid (12 solves:
+4 capillary scales x 3 preconditioners) single-system and batched; the
+96-member ensemble; the level-0 kernels of the 256^3 hierarchy against the
+HBM roofline; the same step end to end from host buffers; and the CPU
+oracle on a bounded window of the same field.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -35,24 +42,21 @@ sys.path.insert(0, ROOT)
 
 import numpy as np
 
-METRIC = "Jacobian solves/s to 1e-8 relative residual (256x256 2D log-normal, 4 capillary scales x 3 preconditioners)"
+METRIC = "Jacobian solves/s to 1e-8 relative residual"
 UNIT = "solves/s"
-WORKLOAD = "2d_256x256_lognormal_sigma2_ell8_pc{0,1e3,1e4,1e5}_x_{amgJ,cpr1_qimpes,bf}"
+WORKLOAD = "3d_256^3_channel_first_newton_jacobian_x_{cpr1_qimpes,bf}_fp32_vcycle"
+WORKLOAD_2D = "2d_256x256_lognormal_sigma2_ell8_pc{0,1e3,1e4,1e5}_x_{amgJ,cpr1_qimpes,bf}"
 PC_SCALES = (0.0, 1e3, 1e4, 1e5)
 KINDS = (("amgJ", 0, 0), ("cpr1", 1, 2), ("bf", 3, 0))
+KINDS_3D = (("cpr1", 1, 2), ("bf", 3, 0))
+THETA_3D = 0.5
+# the CPU oracle's window of the 256^3 field: the corner block of this many
+# cells (1/128 of the grid)
+WINDOW = (64, 64, 32)
 # DRAM bytes (read + write) per launch of the roofline kernels, from one ncu
 # capture of the current kernel version (summaries and commands in profiles/);
-# None where no capture of the current version exists.
-NCU_TRAFFIC = {
-    ("k_hgs", "fp64", "lognormal256bf"): (11.765248e6 + 0.0, "profiles/k_hgs_fp64_lognormal256_bf_level0.md"),
-    ("k_hgs", "fp64", "layered128"): (225.423104e6 + 11.490048e6, "profiles/k_hgs_fp64_layered128_level0.md"),
-    ("k_bsr2_spmv", "f64", "layered128"): (608.675840e6 + 30.454272e6, "profiles/k_bsr2_spmv_layered128.md"),
-    ("k_hgs", "fp32", "layered128"): (150.313472e6 + 6.125056e6, "profiles/k_hgs_fp32_layered128_level0.md"),
-    ("k_csr_residual", "fp32", "layered128"): (142.222336e6 + 4.032768e6,
-                                             "profiles/k_csr_residual_fp32_layered128_level0.md"),
-    ("k_csr_restrict", "fp32", "layered128"): (60.598272e6 + 0.020992e6,
-                                             "profiles/k_csr_restrict_fp32_layered128_level0.md"),
-}
+# absent where no capture of the current version exists.
+NCU_TRAFFIC = {}
 
 
 def parse():
@@ -62,11 +66,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--maxit", type=int, default=300)
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--n3", type=int, default=256, help="cells per side of the 3D channelised headline grid")
+    ap.add_argument("--n", type=int, default=256, help="cells per side of the 2D log-normal grid")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="headline legs only (no 128^3, 2D, ensemble legs)")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--newton", action="store_true",
+                    help="also run the full Newton sequence (5 one-day steps) on the headline grid")
     return ap.parse_args()
 
 
@@ -238,6 +245,76 @@ class GpuBatchStep:
         return recs
 
 
+class Gpu3DStep:
+    """One step of a 3D workload: assemble F and J at the first Newton iterate
+    of the first time step (u = u_old = the initial state), then for each
+    preconditioner kind a set-up and an FGMRES(30) solve of J dx = -F to 1e-8
+    from dx = 0. With `host` (pinned host copies of kx, ky, kz and u), every
+    step first copies the inputs to the device and every solution back."""
+
+    def __init__(self, p, precision, maxit, host=None):
+        import torch
+        from paper_1611_00127_gb300 import inputs as I
+        from paper_1611_00127_gb300 import rsflow as R
+        self.R, self.torch, self.I = R, torch, I
+        self.p = p
+        self.precision = precision
+        self.maxit = maxit
+        self.dp = R.DeviceProblems(p)
+        self.J = R.Bsr2.pattern(self.dp)
+        n = 2 * p.ncell
+        self.F = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.b = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.u = torch.as_tensor(I.initial_state(p), device="cuda")
+        self.xout = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in KINDS_3D]
+        self.host = host
+        if host is not None:
+            # the problem reads its permeability from buffers the copies refill
+            self.dk = torch.empty_like(host["k"], device="cuda")
+            self.dp.c[0].kx, self.dp.c[0].ky, self.dp.c[0].kz = (self.dk[0].data_ptr(), self.dk[1].data_ptr(),
+                                                                 self.dk[2].data_ptr())
+            self.hx = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in KINDS_3D]
+            self.h2d = host["k"].numel() * 8 + host["u"].numel() * 8
+            self.d2h = sum(h.numel() * 8 for h in self.hx)
+
+    def params(self, kind, dec):
+        R = self.R
+        return R.PrecParams(kind=kind, decouple=dec, amg=R.AmgParams(theta=THETA_3D, precision=self.precision))
+
+    def run(self, per_solve_profile=None):
+        R, torch = self.R, self.torch
+        if self.host is not None:
+            self.dk.copy_(self.host["k"], non_blocking=True)
+            self.u.copy_(self.host["u"], non_blocking=True)
+        R.jacobian_assemble(self.dp, self.u, self.u, self.I.DAY, self.J, self.F)
+        torch.neg(self.F, out=self.b)
+        recs = []
+        for q, (name, kind, dec) in enumerate(KINDS_3D):
+            torch.cuda.nvtx.range_push(name)
+            if per_solve_profile is not None:
+                torch.cuda.synchronize()
+                R.profile_begin()
+            self.xout[q].zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record()
+            M = R.Precond(self.J, self.params(kind, dec))
+            ev[1].record()
+            st = R.gmres_solve(self.J, M, self.b, self.xout[q], R.GmresParams(m=30, maxit=self.maxit, rtol=1e-8))
+            ev[2].record()
+            M.close()
+            if per_solve_profile is not None:
+                torch.cuda.synchronize()
+                per_solve_profile[name] = R.profile_end()
+            torch.cuda.nvtx.range_pop()
+            if self.host is not None:
+                self.hx[q].copy_(self.xout[q], non_blocking=True)
+            ev[2].synchronize()
+            recs.append(dict(prec=name, its=int(st.iterations), relres=float(st.relres),
+                             converged=bool(st.converged == 1), setup_ms=round(ev[0].elapsed_time(ev[1]), 3),
+                             solve_ms=round(ev[1].elapsed_time(ev[2]), 3)))
+        return recs
+
+
 def flush_l2(buf):
     buf.add_(1.0)
 
@@ -249,25 +326,6 @@ def hbm_peak():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
-
-
-def sweep_roofline(probs, states, precision, reps=50):
-    """Average device duration of the dominant kernel (one hybrid Gauss-Seidel
-    sweep of level 0 of the largest hierarchy in the workload: the SIMPLE Schur
-    complement of the block-factorisation preconditioner at capillary scale
-    1e3), timed with CUDA events on the launching stream over `reps`
-    back-to-back launches, and the block SpMV timed the same way."""
-    from paper_1611_00127_gb300 import kernel_bench
-    from paper_1611_00127_gb300 import rsflow as R
-    return kernel_bench.lognormal(probs[1].nx, PC_SCALES[1], precision, R.BF, reps)
-
-
-def sweep_roofline_3d(precision, n=128, reps=20):
-    """The same sweep on an HBM-resident case: level 0 (A_pp, 2.1M rows) of the
-    CPR hierarchy of the 128^3 layered workload, L2 flushed before the loop."""
-    from paper_1611_00127_gb300 import kernel_bench
-    from paper_1611_00127_gb300 import rsflow as R
-    return kernel_bench.layered(n, precision, R.CPR1, reps)
 
 
 def shares(prof):
@@ -293,115 +351,108 @@ def profiled_step(step):
 
 
 def time_steps(step, steps, warmup, sync_barrier):
+    """W untimed steps, then K steps each bracketed by an L2 flush, a barrier
+    and a device synchronisation and timed with CUDA events. Returns (total
+    ms, last step's records, launches of the library's kernels in the timed
+    steps)."""
     import torch
+    from paper_1611_00127_gb300 import rsflow as R
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     for _ in range(warmup):
         step.run()
     torch.cuda.synchronize()
     total_ms = 0.0
     recs = None
+    launches = 0
     for _ in range(steps):
         flush_l2(flush)
         torch.cuda.synchronize()
         sync_barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push("step")
+        l0 = R.launch_count()
         e0.record()
         recs = step.run()
         e1.record()
         torch.cuda.synchronize()
+        launches += R.launch_count() - l0
         torch.cuda.nvtx.range_pop()
         total_ms += e0.elapsed_time(e1)
-    return total_ms, recs
+    return total_ms, recs, launches
 
 
-def e2e_steps(probs, states, precision, maxit, steps, warmup):
-    """The same step through the public API starting from pinned host inputs:
-    permeability fields and states copied in, every solution copied out,
-    inside the timed region."""
+def e2e_wall(step, steps, warmup):
+    """Wall-clock time of `steps` steps of a host-buffer step (inputs copied
+    in and solutions copied out inside each step), after `warmup` steps."""
     import torch
-    from paper_1611_00127_gb300 import rsflow as R
-    n = 2 * probs[0].ncell
-    host_k = [torch.from_numpy(np.ascontiguousarray(np.stack([p.kx, p.ky, p.kz]))).pin_memory() for p in probs]
-    host_u = [torch.from_numpy(np.ascontiguousarray(s[0])).pin_memory() for s in states]
-    host_uo = [torch.from_numpy(np.ascontiguousarray(s[1])).pin_memory() for s in states]
-    host_x = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(len(probs) * len(KINDS))]
-    step = GpuStep(probs, states, precision, maxit)
-    dev_k = [torch.empty_like(h, device="cuda") for h in host_k]
-    dev_u = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in probs]
-    dev_uo = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in probs]
-    # problems bound to the device buffers that the copies refill every step
-    dps = []
-    for k, p in enumerate(probs):
-        dp = R.DeviceProblems(p)
-        dp.c[0].kx, dp.c[0].ky, dp.c[0].kz = (dev_k[k][0].data_ptr(), dev_k[k][1].data_ptr(), dev_k[k][2].data_ptr())
-        dps.append(dp)
-    h2d = sum(h.numel() * 8 for h in host_k) + sum(h.numel() * 8 for h in host_u) * 2
-    d2h = sum(h.numel() * 8 for h in host_x)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-
-    def one():
-        for k in range(len(probs)):
-            dev_k[k].copy_(host_k[k], non_blocking=True)
-            dev_u[k].copy_(host_u[k], non_blocking=True)
-            dev_uo[k].copy_(host_uo[k], non_blocking=True)
-        recs = step.run(dps, dev_u, dev_uo)
-        for q, h in enumerate(host_x):
-            h.copy_(step.xout[q], non_blocking=True)
-        return recs
-
     for _ in range(warmup):
-        one()
+        step.run()
     torch.cuda.synchronize()
-    total = 0.0
-    nconv = 0
+    total, nconv = 0.0, 0
     for _ in range(steps):
-        flush.add_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        recs = one()
+        recs = step.run()
         torch.cuda.synchronize()
         total += time.perf_counter() - t0
         nconv += sum(r["converged"] for r in recs)
-    return nconv, total, h2d, d2h
+    return nconv, total
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(probs, states, maxit, budget_s=20.0):
-    """Times the oracle (single-threaded, as it stands) on whole solves of the
-    same workload, in workload order, until ~budget_s of CPU time is used."""
+def oracle_window(p_full, maxit, its_full=None):
+    """The CPU oracle (single-threaded, as it stands) on the corner window of
+    WINDOW cells of the headline field: assembly, then for each
+    preconditioner kind its set-up and FGMRES(30) to 1e-8. Returns the
+    measured times and, extrapolated to the whole grid (every cost scaled by
+    the cell ratio, FGMRES by the full grid's iteration counts `its_full` when
+    given, else the window's), the whole grid's solves/s."""
     import oracle as O
+    from paper_1611_00127_gb300 import inputs as I
+    w = I.window(p_full, *WINDOW)
+    ratio = p_full.ncell / w.ncell
+    u0 = I.initial_state(w)
     t0 = time.perf_counter()
-    done, conv, ran = 0, 0, []
-    for k, p in enumerate(probs):
-        F, J, (rp, col) = O.assemble(p, states[k][0], states[k][1], 86400.0)
-        for name, kind, dec in KINDS:
-            M = O.Precond(rp, col, J, O.PrecParams(kind=kind, decouple=dec))
-            x, st, its, rr = O.fgmres(rp, col, J, -F, M, m=30, rtol=1e-8, maxit=maxit)
-            done += 1
-            conv += int(st == 0)
-            ran.append(f"pc{PC_SCALES[k]:g}/{name}")
-            if time.perf_counter() - t0 > budget_s:
-                break
-        if time.perf_counter() - t0 > budget_s:
-            break
-    el = time.perf_counter() - t0
-    return dict(value=conv / el, unit=UNIT, cores=1, kind="oracle",
-                sample=f"{done} of 12 solves of one step ({', '.join(ran)}), {conv} converged, {el:.1f} s, "
-                       f"assembly + setup + FGMRES per solve")
+    F, J, (rp, col) = O.assemble(w, u0, u0, I.DAY)
+    t_asm = time.perf_counter() - t0
+    parts, total_full, conv = [], t_asm * ratio, 0
+    for name, kind, dec in KINDS_3D:
+        t0 = time.perf_counter()
+        M = O.Precond(rp, col, J, O.PrecParams(kind=kind, decouple=dec, amg=O.AmgParams(theta=THETA_3D)))
+        t1 = time.perf_counter()
+        x, st, its, rr = O.fgmres(rp, col, J, -F, M, m=30, rtol=1e-8, maxit=maxit)
+        t2 = time.perf_counter()
+        conv += int(st == 0)
+        its_f = (its_full or {}).get(name, its)
+        per_it = (t2 - t1) / max(its, 1)
+        total_full += ratio * ((t1 - t0) + per_it * its_f)
+        parts.append(f"{name}: set-up {t1 - t0:.2f} s, {its} iterations {t2 - t1:.2f} s")
+    value = len(KINDS_3D) / total_full if total_full > 0 else 0.0
+    return dict(value=value, unit=UNIT, cores=1, kind="oracle", extrapolated=True,
+                sample=(f"window of {w.nx}x{w.ny}x{w.nz} cells of the {p_full.nx}x{p_full.ny}x{p_full.nz} field "
+                        f"(1/{ratio:g} of the cells), FP64: assembly {t_asm:.2f} s; " + "; ".join(parts) +
+                        f"; {conv} of {len(KINDS_3D)} converged. Extrapolated to the whole grid: every cost x "
+                        f"{ratio:g} (cells), FGMRES at the whole grid's iteration counts "
+                        f"{its_full if its_full else '(the window' + chr(39) + 's)'}"),
+                window_conv=conv)
+
+
+def host_cores():
+    return os.cpu_count() or 1
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    probs, states = workload(args.n)
+    from paper_1611_00127_gb300 import inputs as I
     import oracle as O
     O.build()
+    p = I.config_channel_3d(args.n3)
     vals, samples = [], []
     for w in range(args.warmup + args.steps):
-        # each step: one bounded sample (first solves of the workload, ~10 s)
-        r = oracle_sample(probs, states, args.maxit, budget_s=10.0)
+        # each step: one bounded sample (the oracle on the window, extrapolated)
+        r = oracle_window(p, args.maxit)
         if w >= args.warmup:
             vals.append(r["value"])
             samples.append(r["sample"])
@@ -409,10 +460,11 @@ def reference_arm(args):
     line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic",
-                config=dict(workload=WORKLOAD, grid=f"{args.n}x{args.n}", solves_per_step=12,
+                config=dict(workload=WORKLOAD, grid=f"{args.n3}x{args.n3}x{args.n3}", solves_per_step=len(KINDS_3D),
                             gmres="FGMRES(30), rtol 1e-8, maxit %d" % args.maxit, vcycle="FP64",
-                            parallelism="single host core"),
-                cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=samples[-1]),
+                            parallelism="single host core", host_cores=host_cores()),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=samples[-1],
+                                  extrapolated=True, host_cores=host_cores()),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
 
@@ -499,6 +551,22 @@ def solves_per_second(converged, steps, total_ms):
     return converged * steps / (total_ms / 1e3) if total_ms > 0 else 0.0
 
 
+def class_roofline(prof, peak, peak_kind, classes=None):
+    """Roofline of the kernel class with the most device time in a profiled
+    step: algorithmic bytes of all its launches over their summed device
+    time (= bytes per launch over the average launch duration)."""
+    cand = {k: v for k, v in prof.items() if v[2] > 0 and v[1] > 0 and (classes is None or k in classes)}
+    if not cand:
+        return None
+    k = max(cand, key=lambda c: cand[c][0])
+    ms, by, n = cand[k]
+    achieved = by / (ms * 1e-3) / 1e9
+    tr = NCU_TRAFFIC.get(k)
+    return dict(bound="hbm", kernel=k, achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                traffic=tr[0] / n if tr else None, traffic_source=tr[1] if tr else None, peak_source=peak_kind,
+                launches=n, ms=ms, bytes=by, launch_ms=ms / n, bytes_per_launch=by / n)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -517,102 +585,156 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    from paper_1611_00127_gb300 import inputs as I
+    from paper_1611_00127_gb300 import kernel_bench
     from paper_1611_00127_gb300 import rsflow as R
-    probs, states = workload(args.n)
     R.lib()
-    # headline: FP64 V-cycles
-    step64 = GpuStep(probs, states, R.FP64, args.maxit)
-    l0 = R.launch_count()
+    p = I.config_channel_3d(args.n3)
+    # headline: FP32 V-cycles in FP64 FGMRES
+    step = Gpu3DStep(p, R.FP32, args.maxit)
     with ClockSampler(local) as clk:
-        ms64, recs64 = time_steps(step64, args.steps, args.warmup, barrier)
-    launches = (R.launch_count() - l0)
-    conv64 = sum(r["converged"] for r in recs64)
-    step32 = GpuStep(probs, states, R.FP32, args.maxit)
-    ms32, recs32 = time_steps(step32, args.steps, 1, barrier)
+        ms32, recs32, launches = time_steps(step, args.steps, args.warmup, barrier)
     conv32 = sum(r["converged"] for r in recs32)
-    stepb = GpuBatchStep(probs, states, R.FP32, args.maxit)
-    msb, recsb = time_steps(stepb, args.steps, 1, barrier)
-    convb = sum(r["converged"] for r in recsb)
-    (ms64, ms32, msb), (conv64, conv32, convb) = reduce_over_ranks([ms64, ms32, msb], [conv64, conv32, convb],
-                                                                   dist, "cuda")
-    value = solves_per_second(conv64, args.steps, ms64)
-    value32 = solves_per_second(conv32, args.steps, ms32)
-    valueb = solves_per_second(convb, args.steps, msb)
+    # the same step with FP64 V-cycles
+    k64 = min(args.steps, 3)
+    step64 = Gpu3DStep(p, R.FP64, args.maxit)
+    ms64, recs64, _ = time_steps(step64, k64, 1, barrier)
+    conv64 = sum(r["converged"] for r in recs64)
+    del step64
+    # end to end: the same step from pinned host buffers
     e2e = None
+    te_ms, ce, ke = 0.0, 0, min(args.steps, 5)
     if not args.no_e2e:
-        nconv_e, total_s, h2d, d2h = e2e_steps(probs, states, R.FP64, args.maxit, args.steps, 1)
-        (te_ms,), (ce,) = reduce_over_ranks([total_s * 1e3], [nconv_e], dist, "cuda")
-        e2e = dict(value=solves_per_second(ce, 1, te_ms), unit=UNIT, h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h)
+        host = dict(k=torch.from_numpy(np.ascontiguousarray(np.stack([p.kx, p.ky, p.kz]))).pin_memory(),
+                    u=torch.from_numpy(I.initial_state(p)).pin_memory())
+        stepe = Gpu3DStep(p, R.FP32, args.maxit, host=host)
+        ce, te_s = e2e_wall(stepe, ke, 1)
+        te_ms = te_s * 1e3
+        h2d, d2h = stepe.h2d, stepe.d2h
+        del stepe, host
+    (ms32, ms64, te_ms), (conv32, conv64, ce) = reduce_over_ranks([ms32, ms64, te_ms], [conv32, conv64, ce],
+                                                                  dist, "cuda")
+    # (every step solves the same systems: the last step's converged count holds for each)
+    value = solves_per_second(conv32, args.steps, ms32)
+    value64 = solves_per_second(conv64, k64, ms64)
+    if not args.no_e2e:
+        e2e = dict(value=solves_per_second(ce, 1, te_ms), unit=UNIT, h2d_bytes_per_step=h2d,
+                   d2h_bytes_per_step=d2h, steps=ke,
+                   how="public API, permeability and state copied in from pinned host memory and both "
+                       "solutions copied out inside every step, wall clock")
     if rank != 0:
         return
-    prof, per_solve = profiled_step(step64)
     peak, peak_kind = hbm_peak()
-    rl = sweep_roofline(probs, states, R.FP64)
-    achieved = rl["sweep_bytes"] / (rl["sweep_ms"] * 1e-3) / 1e9
-    roofline = dict(bound="hbm", kernel="k_hgs (hybrid multicolour Gauss-Seidel sweep, FP64)",
-                    achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                    traffic=NCU_TRAFFIC[("k_hgs", "fp64", "lognormal256bf")][0],
-                    traffic_source=NCU_TRAFFIC[("k_hgs", "fp64", "lognormal256bf")][1] + " (caches flushed by ncu)",
-                    peak_source=peak_kind, launch_ms=rl["sweep_ms"], bytes_per_launch=rl["sweep_bytes"],
-                    units=f"level 0 of the Schur-complement hierarchy: {rl['rows']} rows, {rl['nnz']} entries",
-                    note="working set of this 256x256 workload is L2-resident (<129 MB); roofline_large repeats "
-                         "the measurement on an HBM-resident 128^3 level")
-    roofline_large = None
-    if not args.no_large:
-        roofline_large = {}
-        for pname, prec in (("fp64", R.FP64), ("fp32", R.FP32)):
-            big = sweep_roofline_3d(prec)
-            a2 = big["sweep_bytes"] / (big["sweep_ms"] * 1e-3) / 1e9
-            s2 = big["spmv_bytes"] / (big["spmv_ms"] * 1e-3) / 1e9
-            tr, src = NCU_TRAFFIC.get(("k_hgs", pname, "layered128"), (None, None))
-            trs, srcs = NCU_TRAFFIC.get(("k_bsr2_spmv", "f64", "layered128"), (None, None))
-            roofline_large[pname] = dict(
-                bound="hbm", kernel=f"k_hgs {pname.upper()}, level 0 (A_pp) of the 128^3 layered CPR hierarchy",
-                achieved=a2, peak=peak, unit="GB/s", frac=a2 / peak, traffic=tr, traffic_source=src,
-                launch_ms=big["sweep_ms"], bytes_per_launch=big["sweep_bytes"],
-                units=f"{big['rows']} rows, {big['nnz']} entries",
-                bsr2_spmv=dict(achieved=s2, frac=s2 / peak, launch_ms=big["spmv_ms"], traffic=trs,
-                               traffic_source=srcs, bytes_per_launch=big["spmv_bytes"], nnzb=big["nnzb"]),
-                transfer={k: dict(achieved=v["gbs"], frac=v["gbs"] / peak, launch_ms=v["ms"],
-                              bytes_per_launch=v["bytes"],
-                              traffic=NCU_TRAFFIC.get(("k_csr_" + k, pname, "layered128"), (None,))[0])
-                          for k, v in big["transfer"].items()},
-                l2="flushed before the timed launches; working set > L2")
-    spmv = dict(achieved=rl["spmv_bytes"] / (rl["spmv_ms"] * 1e-3) / 1e9, launch_ms=rl["spmv_ms"],
-                bytes_per_launch=rl["spmv_bytes"])
+    # per kernel class, one profiled headline step
+    prof, per_solve = profiled_step(step)
+    roofline = class_roofline(prof, peak, peak_kind)
+    roofline_solve = class_roofline(prof, peak, peak_kind,
+                                    classes=("hybrid_gs_sweep", "csr_resid_restrict_prolong", "bsr2_spmv",
+                                             "gmres_cgs2"))
     kernel_profile = {k: dict(ms=v[0], gbs=(v[1] / (v[0] * 1e-3) / 1e9 if v[0] > 0 else 0.0), launches=v[2])
                       for k, v in prof.items() if v[2] > 0}
-    ensemble = None if args.no_ensemble else ensemble_bench(600)
-    cpu = None if args.no_cpu_baseline else oracle_sample(probs, states, args.maxit)
-    warmup_launch_note = "counted over warm-up + timed steps / (warm-up + timed)"
+    del step
+    torch.cuda.empty_cache()
+    # level-0 kernels of the headline's CPR hierarchy, L2 flushed, both precisions
+    level0 = {}
+    for pname, prec in (("fp32", R.FP32), ("fp64", R.FP64)):
+        k = kernel_bench.channel(args.n3, prec, R.CPR1, reps=20, p=p)
+        sw = k["sweep_bytes"] / (k["sweep_ms"] * 1e-3) / 1e9
+        sp = k["spmv_bytes"] / (k["spmv_ms"] * 1e-3) / 1e9
+        level0[pname] = dict(
+            rows=k["rows"], nnz=k["nnz"],
+            k_hgs=dict(launch_ms=k["sweep_ms"], bytes_per_launch=k["sweep_bytes"], achieved=sw, frac=sw / peak),
+            k_bsr2_spmv=dict(launch_ms=k["spmv_ms"], bytes_per_launch=k["spmv_bytes"], achieved=sp, frac=sp / peak,
+                             nnzb=k["nnzb"]),
+            transfer={t: dict(launch_ms=v["ms"], bytes_per_launch=v["bytes"], achieved=v["gbs"],
+                              frac=v["gbs"] / peak) for t, v in k["transfer"].items()})
+        torch.cuda.empty_cache()
+    side = {}
+    if not args.no_side:
+        # 128^3 layered grid, FP32 and FP64 V-cycles
+        p128 = I.config_layered_3d(128)
+        for pname, prec in (("fp32", R.FP32), ("fp64", R.FP64)):
+            st = Gpu3DStep(p128, prec, args.maxit)
+            m, r, _ = time_steps(st, 3, 1, barrier)
+            side[f"layered128_{pname}"] = dict(value=solves_per_second(sum(x["converged"] for x in r), 3, m),
+                                               ms_per_step=m / 3, solves=r)
+            del st
+        side["layered128_fp32_over_fp64"] = (side["layered128_fp32"]["value"] / side["layered128_fp64"]["value"]
+                                             if side["layered128_fp64"]["value"] else None)
+        torch.cuda.empty_cache()
+        # 256x256 log-normal grid: 12 solves per step
+        probs, states = workload(args.n)
+        for pname, prec, cls in (("fp64", R.FP64, GpuStep), ("fp32", R.FP32, GpuStep),
+                                 ("fp32_batched", R.FP32, GpuBatchStep)):
+            st = cls(probs, states, prec, args.maxit)
+            m, r, _ = time_steps(st, 3, 1, barrier)
+            side[f"lognormal256_{pname}"] = dict(value=solves_per_second(sum(x["converged"] for x in r), 3, m),
+                                                 ms_per_step=m / 3, converged_per_step=sum(x["converged"] for x in r),
+                                                 solves=r)
+            del st
+        side["lognormal256_workload"] = WORKLOAD_2D
+        torch.cuda.empty_cache()
+    ensemble = None if (args.no_ensemble or args.no_side) else ensemble_bench(600)
+    newton = newton_sequence(p, args.maxit) if args.newton else None
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = oracle_window(p, args.maxit, its_full={r["prec"]: r["its"] for r in recs32})
+        cpu["host_cores"] = host_cores()
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
-        ms_per_step=ms64 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+        ms_per_step=ms32 / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64+f32",
         data="synthetic",
-        config=dict(workload=WORKLOAD, grid=f"{args.n}x{args.n}", solves_per_step=12,
-                    bsr2_lanes_per_row=step64.lanes,
-                    converged_per_step=conv64, gmres="FGMRES(30), rtol 1e-8, maxit %d" % args.maxit,
-                    vcycle="FP64", l2="flushed (256 MB write) before every timed step",
+        config=dict(workload=WORKLOAD, grid=f"{args.n3}x{args.n3}x{args.n3}", dof=2 * p.ncell,
+                    preconditioners=["CPR-AMG(1), quasi-IMPES, point-block Jacobi P1",
+                                     "block factorisation, SIMPLE Schur complement"],
+                    solves_per_step=len(KINDS_3D), converged_per_step=conv32 // max(world, 1),
+                    gmres="FP64 FGMRES(30), rtol 1e-8, maxit %d" % args.maxit, vcycle="FP32",
+                    amg="PMIS, ext+i, theta 0.5, hybrid multicolour Gauss-Seidel V(1,1)",
+                    l2="flushed (256 MB write) before every timed step; working set > L2",
                     parallelism="replicas" if world > 1 else "single GPU"),
-        solves=recs64,
-        fp32_vcycle=dict(value=value32, ms_per_step=ms32 / args.steps, converged_per_step=conv32, solves=recs32),
-        batched_fp32=dict(value=valueb, ms_per_step=msb / args.steps, converged_per_step=convb,
-                          speedup_vs_fp64_single=valueb / value if value > 0 else None,
-                          how="4 Jacobians stacked as one batch; one setup + one FGMRES call per preconditioner kind",
-                          solves=recsb),
+        solves=recs32,
+        fp64_vcycle=dict(value=value64, ms_per_step=ms64 / k64, steps=k64, solves=recs64,
+                         fp32_over_fp64=value / value64 if value64 > 0 else None),
         clocks=clk.summary(),
         roofline=roofline,
-        roofline_large=roofline_large,
+        roofline_solve=roofline_solve,
+        level0_kernels=level0,
+        kernel_profile=dict(note="one eager profiled headline step, CUDA events per launch", classes=kernel_profile),
+        side=side,
         ensemble=ensemble,
-        bsr2_spmv=spmv,
-        kernel_profile=dict(note="one eager profiled step, CUDA events per launch (includes launch gaps)",
-                            classes=kernel_profile,
-                            shares_pc10000_cpr1=shares(per_solve.get("pc10000_cpr1", {}))),
-        gpu_launches=int(round(launches / (args.steps + args.warmup))) * args.steps,
+        newton=newton,
+        gpu_launches=int(launches),
         e2e=e2e,
         cpu_baseline=cpu,
     )
     print(json.dumps(line))
+
+
+def newton_sequence(p, maxit, steps=5):
+    """The headline grid's full Newton sequence: `steps` one-day backward-Euler
+    steps from the initial state, with CPR-AMG and with block factorisation
+    (FP32 V-cycles). Each Newton iteration is one Jacobian solve; solves/s is
+    Newton iterations over the wall time of the sequence."""
+    import torch
+    from paper_1611_00127_gb300 import inputs as I
+    from paper_1611_00127_gb300 import rsflow as R
+    dp = R.DeviceProblems(p)
+    out = {}
+    for name, kind, dec in KINDS_3D:
+        prm = R.NewtonParams(prec=R.PrecParams(kind=kind, decouple=dec,
+                                               amg=R.AmgParams(theta=THETA_3D, precision=R.FP32)),
+                             gmres=R.GmresParams(maxit=maxit))
+        u = torch.as_tensor(I.initial_state(p), device="cuda")
+        per, nits, t0 = [], 0, time.perf_counter()
+        for k in range(steps):
+            u_old = u.clone()
+            rc, st = R.newton_step(dp, u, u_old, I.DAY, prm)
+            nits += st["newton_its"]
+            per.append(dict(step=k, rc=rc, **st))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out[name] = dict(steps=per, newton_its=nits, wall_s=wall, solves_per_s=nits / wall if wall > 0 else None)
+    return out
 
 
 if __name__ == "__main__":

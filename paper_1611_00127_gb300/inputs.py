@@ -202,6 +202,21 @@ def config_channel_3d(n: int = 256, pc_scale: float = 1e4) -> Problem:
                    name=f"3d_{n}^3_channel")
 
 
+def window(p: Problem, nx: int, ny: int, nz: int) -> Problem:
+    """The corner block of cells ix < nx, iy < ny, iz < nz of a grid as a
+    grid of its own (same permeability values and constants). Used to time
+    the CPU oracle on a bounded part of a field too large for it."""
+    if not (1 <= nx <= p.nx and 1 <= ny <= p.ny and 1 <= nz <= p.nz):
+        raise ValueError("window larger than the grid")
+
+    def cut(a):
+        return np.ascontiguousarray(a.reshape(p.nz, p.ny, p.nx)[:nz, :ny, :nx]).reshape(-1)
+
+    dim = 3 if nz > 1 or p.dim == 3 else 2
+    return dataclasses.replace(p, dim=dim, nx=nx, ny=ny, nz=nz, kx=cut(p.kx), ky=cut(p.ky), kz=cut(p.kz),
+                               well_in=-1, well_out=-1, name=f"{p.name}_window{nx}x{ny}x{nz}")
+
+
 MILLIDARCY = 9.869233e-16   # m^2
 
 # Capillary-pressure parameter sets "Ex 1".."Ex 4" of Sec. 4 (Table of P_c

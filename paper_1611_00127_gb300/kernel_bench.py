@@ -1,7 +1,7 @@
 """Kernel microbenchmark: the hybrid Gauss-Seidel sweep of AMG level 0 and the
 block SpMV, timed back to back with CUDA events on the launching stream.
 
-    python -m paper_1611_00127_gb300.kernel_bench [--grid layered3d|lognormal2d]
+    python -m paper_1611_00127_gb300.kernel_bench [--grid layered3d|channel3d|lognormal2d]
         [--n N] [--pc PC] [--prec fp64|fp32] [--reps 20] [--kind cpr1|bf] [--ilu]
 
 The case is the exact Newton Jacobian at the synthetic front state of the
@@ -147,6 +147,26 @@ def layered(n: int, precision: int, kind: int = R.CPR1, reps: int = 20, chunk: i
                 spmv_lanes=case.lanes, transfer=xfer)
 
 
+def channel(n: int, precision: int, kind: int = R.CPR1, reps: int = 20, chunk: int = 512, p=None) -> dict:
+    """Sweep, transfer and SpMV timings on the n^3 channelised workload at
+    its first Newton Jacobian (u = u_old = the initial state), L2 flushed."""
+    p = p if p is not None else I.config_channel_3d(n)
+    u0 = I.initial_state(p)
+    case = Level0Case(p, (u0, u0), precision, kind, chunk=chunk)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    ts, bs = case.time_sweeps(reps, flush)
+    tm, bm = case.time_spmv(reps, flush)
+    xfer = {}
+    for which, name in enumerate(("residual", "restrict", "prolong")):
+        t, by = case.time_transfer(which, reps, flush)
+        xfer[name] = dict(ms=t, bytes=by, gbs=by / (t * 1e-3) / 1e9)
+    n0, nnz0 = case.level0()
+    nnzb = case.J.nnzb
+    case.close()
+    return dict(sweep_ms=ts, sweep_bytes=bs, rows=n0, nnz=nnz0, spmv_ms=tm, spmv_bytes=bm, nnzb=nnzb,
+                spmv_lanes=case.lanes, transfer=xfer)
+
+
 def lognormal(n: int, pc: float, precision: int, kind: int = R.BF, reps: int = 50, flush_l2: bool = False,
               chunk: int = 512) -> dict:
     """Sweep and SpMV timings on the n x n log-normal grid with capillary scale
@@ -166,7 +186,7 @@ def lognormal(n: int, pc: float, precision: int, kind: int = R.BF, reps: int = 5
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--grid", choices=["layered3d", "lognormal2d"], default="layered3d")
+    ap.add_argument("--grid", choices=["layered3d", "channel3d", "lognormal2d"], default="layered3d")
     ap.add_argument("--n", type=int, default=None, help="cells per side (128 for 3D, 256 for 2D)")
     ap.add_argument("--pc", type=float, default=1e3, help="capillary scale of the 2D grid")
     ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64")
@@ -189,6 +209,9 @@ def main():
     if a.grid == "layered3d":
         a.n = a.n or 128
         r = layered(a.n, prec, kind, a.reps, a.chunk)
+    elif a.grid == "channel3d":
+        a.n = a.n or 256
+        r = channel(a.n, prec, kind, a.reps, a.chunk)
     else:
         a.n = a.n or 256
         r = lognormal(a.n, a.pc, prec, kind, a.reps, chunk=a.chunk)
