@@ -401,17 +401,34 @@ __device__ __forceinline__ int find_row(const int32_t *col, int32_t s, int32_t e
   return -1;
 }
 
-template <bool WRITE>
+// Moves row i's cnt[i] entries from the scratch rows at toff[i] to the
+// interpolation matrix's rows at prp[i].
+__global__ void k_interp_compact(int32_t n, const int32_t *__restrict__ toff, const int32_t *__restrict__ prp,
+                                 const int32_t *__restrict__ tcol, const double *__restrict__ tval,
+                                 int32_t *__restrict__ pcol, double *__restrict__ pval) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t a = toff[i], b = prp[i], c = prp[i + 1] - b;
+  for (int32_t t = 0; t < c; t++) {
+    pcol[b + t] = tcol[a + t];
+    pval[b + t] = tval[a + t];
+  }
+}
+
+// SIZE = true: prp[i] = the size of Chat_i (1 for a C row), an upper bound
+// of row i's entries. SIZE = false: row i's entries at pcol/pval + prp[i]
+// (offsets of the sizes) and their number in cnt[i].
+template <bool SIZE>
 __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int hcap, int fcap,
                                                      const int32_t *__restrict__ rp,
-                                                                const int32_t *__restrict__ col,
-                                                                const double *__restrict__ val,
-                                                                const double *__restrict__ diag,
-                                                                const uint8_t *__restrict__ strong,
-                                                                const int8_t *__restrict__ cf,
-                                                                const int32_t *__restrict__ cidx, int32_t *prp,
-                                                                int32_t *__restrict__ pcol, double *__restrict__ pval,
-                                                                int32_t *err) {
+                                                     const int32_t *__restrict__ col,
+                                                     const double *__restrict__ val,
+                                                     const double *__restrict__ diag,
+                                                     const uint8_t *__restrict__ strong,
+                                                     const int8_t *__restrict__ cf,
+                                                     const int32_t *__restrict__ cidx, int32_t *prp,
+                                                     int32_t *__restrict__ pcol, double *__restrict__ pval,
+                                                     int32_t *__restrict__ cnt, int32_t *err) {
   extern __shared__ __align__(16) unsigned char iwsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const IWarp W = iwarp_at(iwsm + (size_t)warp * iwarp_bytes(ccap, hcap, fcap), ccap, hcap, fcap);
@@ -419,8 +436,8 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
   for (int32_t i = blockIdx.x * nwarps + warp; i < n; i += gridDim.x * nwarps) {
     if (cf[i] == 1) {
       if (lane == 0) {
-        if (WRITE) { pcol[prp[i]] = cidx[i]; pval[prp[i]] = 1.0; }
-        else prp[i] = 1;
+        if (SIZE) prp[i] = 1;
+        else { pcol[prp[i]] = cidx[i]; pval[prp[i]] = 1.0; cnt[i] = 1; }
       }
       continue;
     }
@@ -468,6 +485,14 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
     }
     const int32_t m = W.cnt[1], nf = W.cnt[2];
     ovf = __any_sync(0xffffffffu, ovf) || m > hcap || nf > fcap;
+    if (SIZE) {
+      if (lane == 0) {
+        if (ovf) atomicExch(err, 1);
+        prp[i] = ovf ? 0 : m;
+      }
+      __syncwarp();
+      continue;
+    }
     // Chat_i: the distinct candidates in ascending order
     if (!ovf) {
       int32_t base = 0;
@@ -482,11 +507,11 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
     }
     __syncwarp();
     if (ovf) {
-      if (lane == 0) { atomicExch(err, 1); if (!WRITE) prp[i] = 0; }
+      if (lane == 0) { atomicExch(err, 1); cnt[i] = 0; }
       continue;
     }
     if (m == 0) {
-      if (!WRITE && lane == 0) prp[i] = 0;
+      if (lane == 0) cnt[i] = 0;
       continue;
     }
     // denominators d_k = sum over row k (ascending) of entries in Chat_i + {i}
@@ -590,14 +615,14 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
       const int32_t idx = b0 + lane;
       const bool on = idx < m && W.nset[idx] && dt != 0.0;
       const unsigned om = __ballot_sync(0xffffffffu, on);
-      if (WRITE && on) {
+      if (on) {
         const int32_t p = prp[i] + base + __popc(om & lt);
         pcol[p] = cidx[W.chat[idx]];
         pval[p] = -(W.num[idx] / dt);
       }
       base += __popc(om);
     }
-    if (!WRITE && lane == 0) prp[i] = base;
+    if (lane == 0) cnt[i] = base;
     __syncwarp();
   }
 }
@@ -1604,32 +1629,63 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           // value, strength flag per entry; row start, diagonal, C/F mark
           // and coarse index per row)
           const double ibytes = (double)F.nnz * 13.0 + (double)F.n * 17.0;
-          {
-          ProfScope ps(kProfInterp, ibytes, s);
-          if (prm.interp == RS_INTERP_CLASSICAL)
-            RS_COUNTED k_interp_classical<false><<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong, cfu,
-                                                                       isc, Pf.rowptr, nullptr, nullptr, err);
-          else
-            RS_COUNTED k_interp_ext_w<false><<<gw, 32 * iw, ishm, s>>>(F.n, ccap, hcap, fcap, F.rowptr, F.col, F.val,
-                                                                       diag, strong, cfu, isc, Pf.rowptr, nullptr,
-                                                                       nullptr, err);
-          }
-          int32_t pnnz = 0;
-          RS_TRY(exclusive_scan(Pf.rowptr, Pf.rowptr, F.n, s, &pnnz));
-          int32_t herr = 0;
-          RS_TRY(sync_copy(&herr, err, sizeof(int32_t), s));
-          if (herr) return fail(RS_ESETUP, "interpolation set too large on level " + std::to_string(l));
-          Pf.nnz = pnnz;
-          RS_TRY(dalloc_n(&Pf.col, (size_t)pnnz + 1, s));
-          RS_TRY(dalloc_n(&Pf.val, (size_t)pnnz + 1, s));
-          ProfScope ps(kProfInterp, ibytes + (double)pnnz * 12.0, s);
-          if (prm.interp == RS_INTERP_CLASSICAL)
+          if (prm.interp == RS_INTERP_CLASSICAL) {
+            {
+              ProfScope ps(kProfInterp, ibytes, s);
+              RS_COUNTED k_interp_classical<false><<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong,
+                                                                         cfu, isc, Pf.rowptr, nullptr, nullptr, err);
+            }
+            int32_t pnnz = 0;
+            RS_TRY(exclusive_scan(Pf.rowptr, Pf.rowptr, F.n, s, &pnnz));
+            int32_t herr = 0;
+            RS_TRY(sync_copy(&herr, err, sizeof(int32_t), s));
+            if (herr) return fail(RS_ESETUP, "interpolation set too large on level " + std::to_string(l));
+            Pf.nnz = pnnz;
+            RS_TRY(dalloc_n(&Pf.col, (size_t)pnnz + 1, s));
+            RS_TRY(dalloc_n(&Pf.val, (size_t)pnnz + 1, s));
+            ProfScope ps(kProfInterp, ibytes + (double)pnnz * 12.0, s);
             RS_COUNTED k_interp_classical<true><<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, strong, cfu,
                                                                       isc, Pf.rowptr, Pf.col, Pf.val, err);
-          else
-            RS_COUNTED k_interp_ext_w<true><<<gw, 32 * iw, ishm, s>>>(F.n, ccap, hcap, fcap, F.rowptr, F.col, F.val,
-                                                                      diag, strong, cfu, isc, Pf.rowptr, Pf.col,
-                                                                      Pf.val, err);
+          } else {
+            // ext+i: the size of every Chat_i (a cheap pass: candidates
+            // only), the weights once into rows of that size, then the rows
+            // moved together
+            Scratch si(s);
+            int32_t *toff = nullptr, *tcnt = nullptr, *tcol = nullptr;
+            double *tval = nullptr;
+            RS_TRY(si.get(&toff, (size_t)F.n + 1));
+            RS_TRY(si.get(&tcnt, (size_t)F.n + 1));
+            {
+              ProfScope ps(kProfInterp, ibytes, s);
+              if (F.n > 0)
+                RS_COUNTED k_interp_ext_w<true><<<gw, 32 * iw, ishm, s>>>(F.n, ccap, hcap, fcap, F.rowptr, F.col,
+                                                                          F.val, diag, strong, cfu, isc, toff,
+                                                                          nullptr, nullptr, nullptr, err);
+            }
+            int32_t tnnz = 0;
+            RS_TRY(exclusive_scan(toff, toff, F.n, s, &tnnz));
+            int32_t herr = 0;
+            RS_TRY(sync_copy(&herr, err, sizeof(int32_t), s));
+            if (herr) return fail(RS_ESETUP, "interpolation set too large on level " + std::to_string(l));
+            RS_TRY(si.get(&tcol, (size_t)tnnz + 1));
+            RS_TRY(si.get(&tval, (size_t)tnnz + 1));
+            {
+              ProfScope ps(kProfInterp, ibytes + (double)tnnz * 12.0, s);
+              if (F.n > 0)
+                RS_COUNTED k_interp_ext_w<false><<<gw, 32 * iw, ishm, s>>>(F.n, ccap, hcap, fcap, F.rowptr, F.col,
+                                                                           F.val, diag, strong, cfu, isc, toff, tcol,
+                                                                           tval, tcnt, err);
+            }
+            int32_t pnnz = 0;
+            RS_TRY(exclusive_scan(tcnt, Pf.rowptr, F.n, s, &pnnz));
+            RS_TRY(sync_copy(&herr, err, sizeof(int32_t), s));
+            if (herr) return fail(RS_ESETUP, "interpolation set too large on level " + std::to_string(l));
+            Pf.nnz = pnnz;
+            RS_TRY(dalloc_n(&Pf.col, (size_t)pnnz + 1, s));
+            RS_TRY(dalloc_n(&Pf.val, (size_t)pnnz + 1, s));
+            if (F.n > 0)
+              RS_COUNTED k_interp_compact<<<gf, kBlock, 0, s>>>(F.n, toff, Pf.rowptr, tcol, tval, Pf.col, Pf.val);
+          }
           RS_CHECK_CUDA(cudaGetLastError());
           return 0;
         };

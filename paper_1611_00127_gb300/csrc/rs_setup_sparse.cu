@@ -181,35 +181,57 @@ __device__ __forceinline__ int gemm_bin(int64_t need) {
   return b;
 }
 
+// Adds one to bin b's counter for every lane of the warp, one atomic per
+// distinct bin of the warp (all 32 lanes call it; `ok` lanes count).
+__device__ __forceinline__ void warp_bin_add(bool ok, int b, int32_t *cnt) {
+  const unsigned act = __ballot_sync(0xffffffffu, ok);
+  if (!ok) return;
+  const unsigned same = __match_any_sync(act, b);
+  if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&cnt[b], __popc(same));
+}
+
 // pass-1 bins: the number of products of each row of A with B
 __global__ void k_spgemm_bin1(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
                               const int32_t *__restrict__ brp, uint8_t *bin, int32_t *bincnt) {
   const int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= n) return;
-  int64_t np = 0;
-  for (int32_t ka = arp[row]; ka < arp[row + 1]; ka++) {
-    const int32_t k = acol[ka];
-    np += brp[k + 1] - brp[k];
+  int b = 0;
+  if (row < n) {
+    int64_t np = 0;
+    for (int32_t ka = arp[row]; ka < arp[row + 1]; ka++) {
+      const int32_t k = acol[ka];
+      np += brp[k + 1] - brp[k];
+    }
+    b = gemm_bin(np);
+    bin[row] = (uint8_t)b;
   }
-  const int b = gemm_bin(np);
-  bin[row] = (uint8_t)b;
-  atomicAdd(&bincnt[b], 1);
+  warp_bin_add(row < n, b, bincnt);
 }
 
 // pass-2 bins: twice the distinct count found by pass 1 (crp scanned)
 __global__ void k_spgemm_bin2(int32_t n, const int32_t *__restrict__ crp, uint8_t *bin, int32_t *bincnt) {
   const int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= n) return;
-  const int b = gemm_bin(2 * (int64_t)(crp[row + 1] - crp[row]));
-  bin[row] = (uint8_t)b;
-  atomicAdd(&bincnt[b], 1);
+  int b = 0;
+  if (row < n) {
+    b = gemm_bin(2 * (int64_t)(crp[row + 1] - crp[row]));
+    bin[row] = (uint8_t)b;
+  }
+  warp_bin_add(row < n, b, bincnt);
 }
 
-// rows listed bin after bin (any order inside a bin)
+// rows listed bin after bin (any order inside a bin); one atomic per
+// distinct bin of a warp
 __global__ void k_spgemm_binfill(int32_t n, const uint8_t *__restrict__ bin, int32_t *cursor, int32_t *rows) {
   const int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= n) return;
-  rows[atomicAdd(&cursor[bin[row]], 1)] = row;
+  const bool ok = row < n;
+  const unsigned act = __ballot_sync(0xffffffffu, ok);
+  if (!ok) return;
+  const int b = bin[row];
+  const unsigned same = __match_any_sync(act, b);
+  const int lane = threadIdx.x & 31, leader = __ffs(same) - 1;
+  int32_t base = 0;
+  if (lane == leader) base = atomicAdd(&cursor[b], __popc(same));
+  base = __shfl_sync(same, base, leader);
+  rows[base + __popc(same & ((1u << lane) - 1u))] = row;
 }
 
 // Sorts the pairs (key[t], val[t]), t < cnt, by key (keys distinct), one
