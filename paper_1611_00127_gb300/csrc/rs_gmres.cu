@@ -343,6 +343,13 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
   RS_TRY(sc.get(&active, (size_t)nseg));
   RS_TRY(sc.get(&bad, (size_t)nseg));
   RS_TRY(sc.get(&st, (size_t)nseg));
+  // batches: the system of every block row, read by the block SpMV to skip
+  // the rows of retired systems
+  int32_t *brseg = nullptr;
+  if (nseg > 1) {
+    RS_TRY(seg_ids(boff, J->nb, &brseg, s));
+    sc.ptrs.push_back(brseg);
+  }
   if (nch > 0) RS_CHECK_CUDA(cudaMemcpyAsync(dch, chunks.data(), sizeof(Chunk) * nch, cudaMemcpyHostToDevice, s));
   RS_CHECK_CUDA(cudaMemcpyAsync(dsegc, seg_chunk.data(), sizeof(int32_t) * (nseg + 1), cudaMemcpyHostToDevice, s));
   RS_CHECK_CUDA(cudaMemsetAsync(its, 0, sizeof(int32_t) * nseg, s));
@@ -416,7 +423,7 @@ extern "C" int gmres_solve(const rs_bsr2 *J, const rs_precond *M, const double *
       if (M && !rc) rc = precond_apply_impl(M, vj, zj, s);
       else RS_CHECK_CUDA(cudaMemcpyAsync(zj, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       if (rc) break;
-      rc = launch_bsr2_spmv(*J, zj, w, s);
+      rc = launch_bsr2_spmv(*J, zj, w, s, brseg ? active : nullptr, brseg);
       if (rc) break;
       // CGS2: dots, reduce, (update + second dots), reduce, (update + norm)
       const double nv = j + 1;

@@ -136,7 +136,10 @@ void dcsr_free(DCsr &A, cudaStream_t s);
 
 // ------------------------------------------------------------------ kernels shared across files
 // y = J x, r = b - J x (bsr2, FP64)
-int launch_bsr2_spmv(const rs_bsr2 &J, const double *x, double *y, cudaStream_t s);
+// y = J x; with act (per-system flags) and rseg (system of each block row),
+// rows of systems whose flag is 0 get y = 0 without being read
+int launch_bsr2_spmv(const rs_bsr2 &J, const double *x, double *y, cudaStream_t s, const uint8_t *act = nullptr,
+                     const int32_t *rseg = nullptr);
 int launch_bsr2_residual(const rs_bsr2 &J, const double *x, const double *b, double *r,
                          cudaStream_t s);
 

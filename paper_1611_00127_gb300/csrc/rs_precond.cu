@@ -34,6 +34,7 @@ struct rs_precond {
   double *p1inv = nullptr;         // P1^{-1} blocks [4 nb] (point-block Jacobi)
   rs_ilu0 *ilu = nullptr;          // P1 = ILU(0) of W J
   uint8_t *act = nullptr;          // batches: per-system live flags read by the V-cycles (1 = live)
+  int32_t *rseg = nullptr;         // batches: the system of every block row (glue kernels)
   Hier Hp, Hs, Hj;
   bool has_p = false, has_s = false, has_j = false;
   DCsr Aps;                        // BF coupling block
@@ -51,11 +52,23 @@ struct rs_precond {
 
 namespace {
 
+// Batches: block row i belongs to a retired system (its flag is 0); the glue
+// kernels then write zeros for it without reading its data, as the V-cycles
+// do (act == nullptr: a single system, never retired).
+__device__ __forceinline__ bool retired(const uint8_t *act, const int32_t *rseg, int64_t i) {
+  return act != nullptr && !act[rseg[i]];
+}
+
 // rt = W r; z = P1^{-1} rt when P1 is point-block Jacobi (p1inv != NULL)
 __global__ void k_cpr_stage1(int32_t nb, int mode, const double *qw, const double *dinv, const double *p1inv,
-                             const double *r, double *rt, double *z) {
+                             const double *r, double *rt, double *z, const uint8_t *act, const int32_t *rseg) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
+  if (retired(act, rseg, i)) {
+    reinterpret_cast<double2 *>(rt)[i] = make_double2(0.0, 0.0);
+    if (p1inv) reinterpret_cast<double2 *>(z)[i] = make_double2(0.0, 0.0);
+    return;
+  }
   const double2 rv = reinterpret_cast<const double2 *>(r)[i];
   double2 t = rv;
   if (mode == RS_DECOUPLE_QIMPES) {
@@ -78,12 +91,14 @@ __global__ void __launch_bounds__(256) k_cpr_resid(int32_t nb, const int32_t *__
                                                    const double *__restrict__ z, const double *__restrict__ rt,
                                                    int mode, const double *__restrict__ qw,
                                                    const double *__restrict__ dinv, double *__restrict__ sb,
-                                                   double *__restrict__ ss) {
+                                                   double *__restrict__ ss, const uint8_t *__restrict__ act,
+                                                   const int32_t *__restrict__ rseg) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t row = tid / LPR;
   const int lane = threadIdx.x % LPR;
   double y0 = 0.0, y1 = 0.0;
-  if (row < nb) {
+  const bool live = row < nb && !retired(act, rseg, row);
+  if (live) {
     const int32_t e = rowptr[row + 1];
     for (int32_t k = rowptr[row] + lane; k < e; k += LPR) {
       const double2 v01 = reinterpret_cast<const double2 *>(val)[2 * (int64_t)k];
@@ -98,7 +113,10 @@ __global__ void __launch_bounds__(256) k_cpr_resid(int32_t nb, const int32_t *__
     y0 += __shfl_down_sync(0xffffffffu, y0, o, LPR);
     y1 += __shfl_down_sync(0xffffffffu, y1, o, LPR);
   }
-  if (row < nb && lane == 0) {
+  if (row < nb && lane == 0 && !live) {
+    sb[row] = 0.0;
+    if (ss) ss[row] = 0.0;
+  } else if (row < nb && lane == 0) {
     double w0 = y0, w1 = y1;
     if (mode == RS_DECOUPLE_QIMPES) {
       w0 = y0 + qw[row] * y1;
@@ -113,33 +131,41 @@ __global__ void __launch_bounds__(256) k_cpr_resid(int32_t nb, const int32_t *__
   }
 }
 
-__global__ void k_cpr_update(int32_t nb, const double *dp, const double *ds, double *z) {
+__global__ void k_cpr_update(int32_t nb, const double *dp, const double *ds, double *z, const uint8_t *act,
+                             const int32_t *rseg) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nb) return;
+  if (i >= nb || retired(act, rseg, i)) return;
   z[2 * (int64_t)i] += dp[i];
   if (ds) z[2 * (int64_t)i + 1] += ds[i];
 }
 
-__global__ void k_take(int32_t nb, const double *r, int comp, double *out) {
+__global__ void k_take(int32_t nb, const double *r, int comp, double *out, const uint8_t *act,
+                       const int32_t *rseg) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nb) out[i] = r[2 * (int64_t)i + comp];
+  if (i < nb) out[i] = retired(act, rseg, i) ? 0.0 : r[2 * (int64_t)i + comp];
 }
 
 // rp_i = r_{2i} - (A_ps s)_i
 // one thread per row (rows of A_ps hold a handful of entries; no FP64
 // shuffle additions)
 __global__ void k_bf_rp(int32_t nb, const int32_t *rp, const int32_t *col, const double *val, const double *s,
-                        const double *r, double *out) {
+                        const double *r, double *out, const uint8_t *act, const int32_t *rseg) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nb) return;
+  if (retired(act, rseg, i)) {
+    out[i] = 0.0;
+    return;
+  }
   double acc = 0.0;
   for (int32_t k = rp[i]; k < rp[i + 1]; k++) acc = fma(val[k], s[col[k]], acc);
   out[i] = r[2 * i] - acc;
 }
 
-__global__ void k_interleave(int32_t nb, const double *p, const double *s, double *z) {
+__global__ void k_interleave(int32_t nb, const double *p, const double *s, double *z, const uint8_t *act,
+                             const int32_t *rseg) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nb) reinterpret_cast<double2 *>(z)[i] = make_double2(p[i], s[i]);
+  if (i < nb)
+    reinterpret_cast<double2 *>(z)[i] = retired(act, rseg, i) ? make_double2(0.0, 0.0) : make_double2(p[i], s[i]);
 }
 
 std::vector<int32_t> dof_offsets(const std::vector<int32_t> &blk) {
@@ -158,6 +184,7 @@ int build(rs_precond *M, cudaStream_t s) {
   if (nseg > 1) {
     RS_TRY(dalloc_n(&M->act, (size_t)nseg, s));
     RS_CHECK_CUDA(cudaMemsetAsync(M->act, 1, (size_t)nseg, s));
+    RS_TRY(seg_ids(M->seg_off, nb, &M->rseg, s));
   }
   RS_TRY(dalloc_n(&M->rt, 2 * (size_t)nb, s));
   RS_TRY(dalloc_n(&M->sb, (size_t)nb, s));
@@ -250,6 +277,7 @@ void destroy(rs_precond *M) {
   dfree(M->dinv, s);
   dfree(M->p1inv, s);
   dfree(M->act, s);
+  dfree(M->rseg, s);
   ilu0_free(M->ilu);
   dfree(M->rt, s);
   dfree(M->sb, s);
@@ -272,30 +300,31 @@ static int apply_body(const rs_precond *M, const double *r, double *z, cudaStrea
     case RS_PC_AMG_J_SCALAR:
       return amg_vcycle(M->Hj, r, z, s);
     case RS_PC_BF: {
-      RS_COUNTED k_take<<<g, kBlock, 0, s>>>(nb, r, 1, M->sb);
+      RS_COUNTED k_take<<<g, kBlock, 0, s>>>(nb, r, 1, M->sb, M->act, M->rseg);
       RS_TRY(amg_vcycle(M->Hs, M->sb, M->sx, s));                 // A_ss s = R_s r
       RS_COUNTED k_bf_rp<<<grid_for((int64_t)nb), kBlock, 0, s>>>(nb, M->Aps.rowptr, M->Aps.col, M->Aps.val, M->sx, r,
-                                                           M->ss);    // r_p = R_p r - A_ps s
+                                                           M->ss, M->act, M->rseg);    // r_p = R_p r - A_ps s
       RS_TRY(amg_vcycle(M->Hp, M->ss, M->sy, s));                 // S~ p = r_p
-      RS_COUNTED k_interleave<<<g, kBlock, 0, s>>>(nb, M->sy, M->sx, z);
+      RS_COUNTED k_interleave<<<g, kBlock, 0, s>>>(nb, M->sy, M->sx, z, M->act, M->rseg);
       RS_CHECK_CUDA(cudaGetLastError());
       return 0;
     }
     default: {
       const int mode = M->prm.decouple;
       const bool two = M->prm.kind == RS_PC_CPR2;
-      RS_COUNTED k_cpr_stage1<<<g, kBlock, 0, s>>>(nb, mode, M->qw, M->dinv, M->p1inv, r, M->rt, z);
+      RS_COUNTED k_cpr_stage1<<<g, kBlock, 0, s>>>(nb, mode, M->qw, M->dinv, M->p1inv, r, M->rt, z, M->act, M->rseg);
       if (M->ilu) RS_TRY(ilu0_solve(M->ilu, M->rt, z, s));
       {
         ProfScope ps(kProfBsr2, M->J.nnzb * 36.0 + (nb + 1) * 4.0 + nb * (16.0 + 16.0 + 16.0), s);
         // one lane per block row: on GB300 every FP64 shuffle addition costs
         // FP64-pipe time, and a row's blocks share cache lines
         RS_COUNTED k_cpr_resid<1><<<grid_for((int64_t)nb), kBlock, 0, s>>>(
-            nb, M->J.row_ptr, M->J.col, M->J.val, z, M->rt, mode, M->qw, M->dinv, M->sb, two ? M->ss : nullptr);
+            nb, M->J.row_ptr, M->J.col, M->J.val, z, M->rt, mode, M->qw, M->dinv, M->sb, two ? M->ss : nullptr, M->act,
+            M->rseg);
       }
       RS_TRY(amg_vcycle(M->Hp, M->sb, M->sx, s));
       if (two) RS_TRY(amg_vcycle(M->Hs, M->ss, M->sy, s));
-      RS_COUNTED k_cpr_update<<<g, kBlock, 0, s>>>(nb, M->sx, two ? M->sy : nullptr, z);
+      RS_COUNTED k_cpr_update<<<g, kBlock, 0, s>>>(nb, M->sx, two ? M->sy : nullptr, z, M->act, M->rseg);
       RS_CHECK_CUDA(cudaGetLastError());
       return 0;
     }

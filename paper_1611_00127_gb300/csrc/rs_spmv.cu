@@ -15,12 +15,17 @@ __global__ void __launch_bounds__(256) k_bsr2_spmv(int32_t nb, const int32_t *__
                                                    const int32_t *__restrict__ col,
                                                    const double *__restrict__ val,
                                                    const double *__restrict__ x,
-                                                   const double *__restrict__ b, double *__restrict__ y) {
+                                                   const double *__restrict__ b, double *__restrict__ y,
+                                                   const uint8_t *__restrict__ act,
+                                                   const int32_t *__restrict__ rseg) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t row = tid / LPR;
   const int lane = threadIdx.x % LPR;
   double y0 = 0.0, y1 = 0.0;
-  if (row < nb) {
+  // a row of a retired system of a batch (act[system] = 0) gets y = 0
+  // without reading its blocks
+  const bool live = row < nb && (act == nullptr || act[rseg[row]]);
+  if (live) {
     const int32_t s = __ldg(rowptr + row), e = __ldg(rowptr + row + 1);
     for (int32_t k = s + lane; k < e; k += LPR) {
       const double2 v01 = __ldg(reinterpret_cast<const double2 *>(val) + 2 * (int64_t)k);
@@ -39,7 +44,9 @@ __global__ void __launch_bounds__(256) k_bsr2_spmv(int32_t nb, const int32_t *__
   }
   if (row < nb && lane == 0) {
     double2 out;
-    if (RESID) {
+    if (!live) {
+      out = make_double2(0.0, 0.0);
+    } else if (RESID) {
       const double2 bv = reinterpret_cast<const double2 *>(b)[row];
       out = make_double2(bv.x - y0, bv.y - y1);
     } else {
@@ -58,23 +65,25 @@ extern "C" int rs_tune_set_bsr2_lpr(int lpr) {
 }
 
 template <bool RESID>
-static int launch(const rs_bsr2 &J, const double *x, const double *b, double *y, cudaStream_t s) {
+static int launch(const rs_bsr2 &J, const double *x, const double *b, double *y, cudaStream_t s,
+                  const uint8_t *act = nullptr, const int32_t *rseg = nullptr) {
   if (J.nb <= 0) return 0;
   const int64_t threads = (int64_t)J.nb * g_bsr2_lpr;
   const unsigned grid = grid_for(threads);
   ProfScope ps(kProfBsr2, J.nnzb * 36.0 + (J.nb + 1) * 4.0 + J.nb * (RESID ? 48.0 : 32.0), s);
   switch (g_bsr2_lpr) {
-    case 1: RS_COUNTED k_bsr2_spmv<1, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
-    case 2: RS_COUNTED k_bsr2_spmv<2, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
-    case 8: RS_COUNTED k_bsr2_spmv<8, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
-    default: RS_COUNTED k_bsr2_spmv<4, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y); break;
+    case 1: RS_COUNTED k_bsr2_spmv<1, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y, act, rseg); break;
+    case 2: RS_COUNTED k_bsr2_spmv<2, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y, act, rseg); break;
+    case 8: RS_COUNTED k_bsr2_spmv<8, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y, act, rseg); break;
+    default: RS_COUNTED k_bsr2_spmv<4, RESID><<<grid, kBlock, 0, s>>>(J.nb, J.row_ptr, J.col, J.val, x, b, y, act, rseg); break;
   }
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }
 
-int launch_bsr2_spmv(const rs_bsr2 &J, const double *x, double *y, cudaStream_t s) {
-  return launch<false>(J, x, nullptr, y, s);
+int launch_bsr2_spmv(const rs_bsr2 &J, const double *x, double *y, cudaStream_t s, const uint8_t *act,
+                     const int32_t *rseg) {
+  return launch<false>(J, x, nullptr, y, s, act, rseg);
 }
 
 int launch_bsr2_residual(const rs_bsr2 &J, const double *x, const double *b, double *r, cudaStream_t s) {
