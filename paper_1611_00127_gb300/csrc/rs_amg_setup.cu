@@ -302,11 +302,11 @@ constexpr int kIF = 256;
 // kIF): small capacities on the fine levels let many warps share an SM.
 struct IWarp {
   double *num, *fa, *fd;
-  int32_t *hkey, *chat, *nset, *fk, *cnt;   // hkey: candidate hash set; cnt: -, m, nf
+  int32_t *hkey, *chat, *nset, *fk, *fb, *fe, *fneg, *cnt;   // hkey: candidate hash set; cnt: -, m, nf
 };
 
 __host__ __device__ inline size_t iwarp_bytes(int ccap, int hcap, int fcap) {
-  return 8 * (size_t)(hcap + 2 * fcap) + 4 * (size_t)(ccap + 2 * hcap + fcap + 4);
+  return 8 * (size_t)(hcap + 2 * fcap) + 4 * (size_t)(ccap + 2 * hcap + 4 * fcap + 4);
 }
 
 __device__ inline IWarp iwarp_at(unsigned char *base, int ccap, int hcap, int fcap) {
@@ -318,9 +318,27 @@ __device__ inline IWarp iwarp_at(unsigned char *base, int ccap, int hcap, int fc
   W.chat = W.hkey + ccap;
   W.nset = W.chat + hcap;
   W.fk = W.nset + hcap;
-  W.cnt = W.fk + fcap;
+  W.fb = W.fk + fcap;
+  W.fe = W.fb + fcap;
+  W.fneg = W.fe + fcap;
+  W.cnt = W.fneg + fcap;
   return W;
 }
+
+// Sign tests on the bit pattern (integer instructions; GB300 issues FP64
+// comparisons on its slow FP64 pipe): v < 0, v > 0 (false for +-0 and NaN),
+// and v == +-0.
+__device__ __forceinline__ bool dneg(double v) {
+  const long long b = __double_as_longlong(v), a = b & 0x7fffffffffffffffLL;
+  return b < 0 && a != 0 && a <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool dpos(double v) {
+  const long long b = __double_as_longlong(v);
+  return b > 0 && b <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool dzero(double v) { return (__double_as_longlong(v) & 0x7fffffffffffffffLL) == 0; }
+// a_kl has the sign opposite to a_kk (a_kk < 0: a_kl > 0; else a_kl < 0)
+__device__ __forceinline__ bool dopposite(int neg_kk, double akl) { return neg_kk ? dpos(akl) : dneg(akl); }
 
 // Inserts key into the warp's open-addressing set of 2^tbits slots (-1 =
 // empty), counting new keys in *distinct; false when the set is full.
@@ -516,18 +534,25 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
     }
     // denominators d_k = sum over row k (ascending) of entries in Chat_i + {i}
     // whose sign is opposite to a_kk; one lane per k
+    // (each k's row bounds and diagonal sign are kept for the passes below,
+    // and fa becomes t_k = a_ik / d_k, divided once per k)
     for (int32_t f = lane; f < nf; f += 32) {
       const int32_t k = W.fk[f];
-      const double sk = diag[k] < 0.0 ? -1.0 : 1.0;
+      const int neg = dneg(diag[k]) ? 1 : 0;
+      const int32_t kb = rp[k], ke = rp[k + 1];
       Acc d{0.0, false};
-      for (int32_t t = rp[k]; t < rp[k + 1]; t++) {
+      for (int32_t t = kb; t < ke; t++) {
         const int32_t l = col[t];
         if (l == k || !(l == i || find_sorted(W.chat, m, l) >= 0)) continue;
         const double av = val[t];
-        if (!(sk * av < 0.0)) continue;
+        if (!dopposite(neg, av)) continue;
         d.add(av);
       }
       W.fd[f] = d.v;
+      W.fa[f] = dzero(d.v) ? 0.0 : W.fa[f] / d.v;
+      W.fb[f] = kb;
+      W.fe[f] = ke;
+      W.fneg[f] = neg;
     }
     __syncwarp();
     // numerators: one lane per target j; a_ij first, then t_k * abar_kj for k ascending
@@ -537,16 +562,12 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
       Acc nm{0.0, false};
       if (qi >= 0) nm.add(val[qi]);
       for (int32_t f = 0; f < nf; f++) {
-        const double d = W.fd[f];
-        if (d == 0.0) continue;
-        const int32_t k = W.fk[f];
-        const int32_t qk = find_row(col, rp[k], rp[k + 1], l);
+        if (dzero(W.fd[f])) continue;
+        const int32_t qk = find_row(col, W.fb[f], W.fe[f], l);
         if (qk < 0) continue;
-        const double sk = diag[k] < 0.0 ? -1.0 : 1.0;
         const double av = val[qk];
-        if (!(sk * av < 0.0)) continue;
-        const double tq = W.fa[f] / d;
-        nm.add(tq * av);
+        if (!dopposite(W.fneg[f], av)) continue;
+        nm.add(W.fa[f] * av);
       }
       W.num[idx] = nm.v;
       W.nset[idx] = nm.set ? 1 : 0;
@@ -571,7 +592,7 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
           }
         }
         const unsigned fm = __ballot_sync(0xffffffffu, isF);
-        if (isF) has = W.fd[fbase + __popc(fm & lt)] == 0.0;
+        if (isF) has = dzero(W.fd[fbase + __popc(fm & lt)]);
         fbase += __popc(fm);
         const unsigned hm = __ballot_sync(0xffffffffu, has);
         for (int t = 0; t < 32; t++) {
@@ -583,19 +604,13 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
         const int32_t g = g0 + lane;
         bool has = false;
         double term = 0.0;
-        if (g < nf) {
-          const double d = W.fd[g];
-          if (d != 0.0) {
-            const int32_t k = W.fk[g];
-            const int32_t qk = find_row(col, rp[k], rp[k + 1], i);
-            if (qk >= 0) {
-              const double sk = diag[k] < 0.0 ? -1.0 : 1.0;
-              const double av = val[qk];
-              if (sk * av < 0.0) {
-                const double tq = W.fa[g] / d;
-                term = tq * av;
-                has = true;
-              }
+        if (g < nf && !dzero(W.fd[g])) {
+          const int32_t qk = find_row(col, W.fb[g], W.fe[g], i);
+          if (qk >= 0) {
+            const double av = val[qk];
+            if (dopposite(W.fneg[g], av)) {
+              term = W.fa[g] * av;
+              has = true;
             }
           }
         }
