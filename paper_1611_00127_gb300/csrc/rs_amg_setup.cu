@@ -446,12 +446,20 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
                                                      const int8_t *__restrict__ cf,
                                                      const int32_t *__restrict__ cidx, int32_t *prp,
                                                      int32_t *__restrict__ pcol, double *__restrict__ pval,
-                                                     int32_t *__restrict__ cnt, int32_t *err) {
+                                                     int32_t *__restrict__ cnt, int32_t *err,
+                                                     const int32_t *__restrict__ rlist, int32_t nlist,
+                                                     uint8_t *__restrict__ big, int32_t *__restrict__ defer) {
   extern __shared__ __align__(16) unsigned char iwsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const IWarp W = iwarp_at(iwsm + (size_t)warp * iwarp_bytes(ccap, hcap, fcap), ccap, hcap, fcap);
   const unsigned lt = (1u << lane) - 1u;
-  for (int32_t i = blockIdx.x * nwarps + warp; i < n; i += gridDim.x * nwarps) {
+  // rows: all n, or the listed ones; the rows a small-workspace size pass
+  // deferred (big[i] = 1) are left to the pass over their list
+  const int32_t nrow = rlist ? nlist : n;
+  const bool skip_big = !SIZE && big != nullptr && rlist == nullptr;
+  for (int32_t idx = blockIdx.x * nwarps + warp; idx < nrow; idx += gridDim.x * nwarps) {
+    const int32_t i = rlist ? rlist[idx] : idx;
+    if (skip_big && big[i]) continue;
     if (cf[i] == 1) {
       if (lane == 0) {
         if (SIZE) prp[i] = 1;
@@ -505,8 +513,14 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
     ovf = __any_sync(0xffffffffu, ovf) || m > hcap || nf > fcap;
     if (SIZE) {
       if (lane == 0) {
-        if (ovf) atomicExch(err, 1);
-        prp[i] = ovf ? 0 : m;
+        if (ovf && defer) {        // too large for this workspace: defer the row
+          big[i] = 1;
+          defer[1 + atomicAdd(&defer[0], 1)] = i;
+          prp[i] = 0;
+        } else {
+          if (ovf) atomicExch(err, 1);
+          prp[i] = ovf ? 0 : m;
+        }
       }
       __syncwarp();
       continue;
@@ -594,10 +608,10 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
         const unsigned fm = __ballot_sync(0xffffffffu, isF);
         if (isF) has = dzero(W.fd[fbase + __popc(fm & lt)]);
         fbase += __popc(fm);
-        const unsigned hm = __ballot_sync(0xffffffffu, has);
-        for (int t = 0; t < 32; t++) {
-          const double vt = __shfl_sync(0xffffffffu, v, t);
-          if (lane == 0 && ((hm >> t) & 1u)) a.add(vt);
+        // (only the lanes holding a term: one FP64 add per term)
+        for (unsigned hm = __ballot_sync(0xffffffffu, has); hm; hm &= hm - 1u) {
+          const double vt = __shfl_sync(0xffffffffu, v, __ffs(hm) - 1);
+          if (lane == 0) a.add(vt);
         }
       }
       for (int32_t g0 = 0; g0 < nf; g0 += 32) {
@@ -614,10 +628,9 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
             }
           }
         }
-        const unsigned hm = __ballot_sync(0xffffffffu, has);
-        for (int t = 0; t < 32; t++) {
-          const double vt = __shfl_sync(0xffffffffu, term, t);
-          if (lane == 0 && ((hm >> t) & 1u)) a.add(vt);
+        for (unsigned hm = __ballot_sync(0xffffffffu, has); hm; hm &= hm - 1u) {
+          const double vt = __shfl_sync(0xffffffffu, term, __ffs(hm) - 1);
+          if (lane == 0) a.add(vt);
         }
       }
     }
@@ -1621,8 +1634,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           RS_TRY(dalloc_n(&Pf.rowptr, (size_t)F.n + 1, s));
           RS_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
           // ext+i work arrays sized for this level (see IWarp)
-          int ccap = kICand, hcap = kICap, fcap = kIF, iw = 2;
-          size_t ishm = 0;
+          int ccap = kICand, hcap = kICap, fcap = kIF;
           if (prm.interp != RS_INTERP_CLASSICAL && F.n > 0) {
             int32_t *bd = nullptr;
             RS_TRY(sc.get(&bd, 2));
@@ -1633,13 +1645,12 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
             ccap = 32;
             while (ccap < kICand && ccap < hb[0]) ccap *= 2;
             hcap = std::min(ccap, kICap);
+            // the candidate set never needs more than twice Chat's capacity
+            // (more distinct candidates than hcap is an error either way)
+            ccap = std::min(ccap, 2 * hcap);
             fcap = 8;
             while (fcap < kIF && fcap < hb[1]) fcap *= 2;
-            const size_t wb = iwarp_bytes(ccap, hcap, fcap);
-            iw = (int)std::min<size_t>(8, std::max<size_t>(1, (48 * 1024) / wb));
-            ishm = wb * iw;
           }
-          const unsigned gw = (unsigned)std::min<int64_t>((F.n + iw - 1) / iw, (int64_t)num_sms() * 64);
           // algorithmic bytes of one pass: the level's rows once (column,
           // value, strength flag per entry; row start, diagonal, C/F mark
           // and coarse index per row)
@@ -1664,18 +1675,48 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           } else {
             // ext+i: the size of every Chat_i (a cheap pass: candidates
             // only), the weights once into rows of that size, then the rows
-            // moved together
+            // moved together. Every row is first taken with a small
+            // workspace (many warps per SM); the rows it cannot hold are
+            // listed and taken again with the level's full workspace.
             Scratch si(s);
-            int32_t *toff = nullptr, *tcnt = nullptr, *tcol = nullptr;
+            int32_t *toff = nullptr, *tcnt = nullptr, *tcol = nullptr, *defer = nullptr;
             double *tval = nullptr;
+            uint8_t *bigf = nullptr;
             RS_TRY(si.get(&toff, (size_t)F.n + 1));
             RS_TRY(si.get(&tcnt, (size_t)F.n + 1));
+            struct Cfg { int c, h, f, iw; size_t shm; };
+            auto cfg_of = [](int c, int h, int f) {
+              const size_t wb = iwarp_bytes(c, h, f);
+              const int w = (int)std::min<size_t>(8, std::max<size_t>(1, (48 * 1024) / wb));
+              return Cfg{c, h, f, w, wb * w};
+            };
+            const Cfg cbig = cfg_of(ccap, hcap, fcap);
+            const Cfg csmall = cfg_of(std::min(ccap, 256), std::min(hcap, 128), std::min(fcap, 64));
+            const bool split = csmall.iw > cbig.iw;
+            auto grid_w = [&](const Cfg &c, int64_t rows) {
+              return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + c.iw - 1) / c.iw, (int64_t)num_sms() * 64));
+            };
+            int32_t nbig = 0;
+            if (split) {
+              RS_TRY(si.get(&bigf, (size_t)F.n + 1));
+              RS_TRY(si.get(&defer, (size_t)F.n + 1));
+              RS_CHECK_CUDA(cudaMemsetAsync(bigf, 0, (size_t)F.n + 1, s));
+              RS_CHECK_CUDA(cudaMemsetAsync(defer, 0, sizeof(int32_t), s));
+            }
             {
               ProfScope ps(kProfInterp, ibytes, s);
+              const Cfg &c = split ? csmall : cbig;
               if (F.n > 0)
-                RS_COUNTED k_interp_ext_w<true><<<gw, 32 * iw, ishm, s>>>(F.n, ccap, hcap, fcap, F.rowptr, F.col,
-                                                                          F.val, diag, strong, cfu, isc, toff,
-                                                                          nullptr, nullptr, nullptr, err);
+                RS_COUNTED k_interp_ext_w<true><<<grid_w(c, F.n), 32 * c.iw, c.shm, s>>>(
+                    F.n, c.c, c.h, c.f, F.rowptr, F.col, F.val, diag, strong, cfu, isc, toff, nullptr, nullptr,
+                    nullptr, err, nullptr, 0, split ? bigf : nullptr, split ? defer : nullptr);
+              if (split) {
+                RS_TRY(sync_copy(&nbig, defer, sizeof(int32_t), s));
+                if (nbig > 0)
+                  RS_COUNTED k_interp_ext_w<true><<<grid_w(cbig, nbig), 32 * cbig.iw, cbig.shm, s>>>(
+                      F.n, cbig.c, cbig.h, cbig.f, F.rowptr, F.col, F.val, diag, strong, cfu, isc, toff, nullptr,
+                      nullptr, nullptr, err, defer + 1, nbig, nullptr, nullptr);
+              }
             }
             int32_t tnnz = 0;
             RS_TRY(exclusive_scan(toff, toff, F.n, s, &tnnz));
@@ -1686,10 +1727,15 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
             RS_TRY(si.get(&tval, (size_t)tnnz + 1));
             {
               ProfScope ps(kProfInterp, ibytes + (double)tnnz * 12.0, s);
+              const Cfg &c = split ? csmall : cbig;
               if (F.n > 0)
-                RS_COUNTED k_interp_ext_w<false><<<gw, 32 * iw, ishm, s>>>(F.n, ccap, hcap, fcap, F.rowptr, F.col,
-                                                                           F.val, diag, strong, cfu, isc, toff, tcol,
-                                                                           tval, tcnt, err);
+                RS_COUNTED k_interp_ext_w<false><<<grid_w(c, F.n), 32 * c.iw, c.shm, s>>>(
+                    F.n, c.c, c.h, c.f, F.rowptr, F.col, F.val, diag, strong, cfu, isc, toff, tcol, tval, tcnt, err,
+                    nullptr, 0, split ? bigf : nullptr, nullptr);
+              if (nbig > 0)
+                RS_COUNTED k_interp_ext_w<false><<<grid_w(cbig, nbig), 32 * cbig.iw, cbig.shm, s>>>(
+                    F.n, cbig.c, cbig.h, cbig.f, F.rowptr, F.col, F.val, diag, strong, cfu, isc, toff, tcol, tval,
+                    tcnt, err, defer + 1, nbig, nullptr, nullptr);
             }
             int32_t pnnz = 0;
             RS_TRY(exclusive_scan(tcnt, Pf.rowptr, F.n, s, &pnnz));

@@ -234,35 +234,36 @@ __global__ void k_spgemm_binfill(int32_t n, const uint8_t *__restrict__ bin, int
   rows[base + __popc(same & ((1u << lane) - 1u))] = row;
 }
 
-// Sorts the pairs (key[t], val[t]), t < cnt, by key (keys distinct), one
-// warp; the arrays have room for the next power of two of cnt (<= tsize).
-__device__ void warp_sort_pairs(int32_t *key, double *val, int32_t cnt, int tsize) {
-  const int lane = threadIdx.x & 31;
-  if (cnt <= 1) return;
-  if (cnt <= 32) {
-    int32_t k = lane < cnt ? key[lane] : INT32_MAX;
-    double v = lane < cnt ? val[lane] : 0.0;
-    for (int kk = 2; kk <= 32; kk <<= 1)
+// Sorts the pairs (key[t], val[t]), t < cnt, by key (keys distinct) with
+// the G lanes of a group (lane gl of the group, mask gmask); the arrays have
+// room for the next power of two of cnt (<= tsize). Up to G pairs: bitonic
+// network in registers; more: bitonic network in place.
+template <int G>
+__device__ void group_sort_pairs(int32_t *key, double *val, int32_t cnt, int tsize, int gl, unsigned gmask) {
+  if (cnt <= G) {
+    int32_t k = gl < cnt ? key[gl] : INT32_MAX;
+    double v = gl < cnt ? val[gl] : 0.0;
+    for (int kk = 2; kk <= G; kk <<= 1)
       for (int j = kk >> 1; j > 0; j >>= 1) {
-        const int32_t ok = __shfl_xor_sync(0xffffffffu, k, j);
-        const double ov = __shfl_xor_sync(0xffffffffu, v, j);
-        const bool up = (lane & kk) == 0, lower = (lane & j) == 0;
+        const int32_t ok = __shfl_xor_sync(gmask, k, j, G);
+        const double ov = __shfl_xor_sync(gmask, v, j, G);
+        const bool up = (gl & kk) == 0, lower = (gl & j) == 0;
         const bool take = (lower == up) ? (ok < k) : (ok > k);
         if (take) { k = ok; v = ov; }
       }
-    __syncwarp();
-    if (lane < cnt) { key[lane] = k; val[lane] = v; }
-    __syncwarp();
+    __syncwarp(gmask);
+    if (gl < cnt) { key[gl] = k; val[gl] = v; }
+    __syncwarp(gmask);
     return;
   }
-  int32_t P = 64;
+  int32_t P = 2 * G;
   while (P < cnt) P <<= 1;
   if (P > tsize) P = tsize;
-  for (int32_t t = cnt + lane; t < P; t += 32) key[t] = INT32_MAX;
-  __syncwarp();
+  for (int32_t t = cnt + gl; t < P; t += G) key[t] = INT32_MAX;
+  __syncwarp(gmask);
   for (int32_t kk = 2; kk <= P; kk <<= 1)
     for (int32_t j = kk >> 1; j > 0; j >>= 1) {
-      for (int32_t t = lane; t < P / 2; t += 32) {
+      for (int32_t t = gl; t < P / 2; t += G) {
         const int32_t a = (t / j) * 2 * j + (t % j), b = a + j;
         const bool up = (a & kk) == 0;
         const int32_t x = key[a], y = key[b];
@@ -274,14 +275,19 @@ __device__ void warp_sort_pairs(int32_t *key, double *val, int32_t cnt, int tsiz
           val[b] = w;
         }
       }
-      __syncwarp();
+      __syncwarp(gmask);
     }
 }
 
-// One warp per listed row, tables of 2^tbits slots in shared memory.
-// Products are accumulated in ascending inner index (the ka loop is
-// sequential, a B row holds each column once), so sums are reproducible.
-template <bool NUMERIC>
+// Groups of G lanes take one listed row each (32 / G rows per warp), each
+// group with its own table of 2^tbits slots in shared memory. The loops over
+// A's row and B's rows run to the warp's longest, so the groups stay in step
+// and every FP64 multiply or add is one instruction for all of the warp's
+// rows (GB300 issues FP64 at a low rate per instruction, whatever the number
+// of active lanes). Products are accumulated in ascending inner index (the
+// A-row loop is sequential, a B row holds each column once), so sums are
+// reproducible.
+template <int G, bool NUMERIC>
 __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const int32_t *__restrict__ rows, int tbits,
                                                          const int32_t *__restrict__ arp,
                                                          const int32_t *__restrict__ acol,
@@ -290,73 +296,101 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const in
                                                          const int32_t *__restrict__ bcol,
                                                          const double *__restrict__ bval,
                                                          int32_t *__restrict__ crp, int32_t *__restrict__ ccol,
-                                                         double *__restrict__ cval, int32_t *err) {
+                                                         double *__restrict__ cval, int32_t *err,
+                                                         int32_t *__restrict__ defer) {
+  constexpr int R = 32 / G;
   extern __shared__ unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int grp = lane / G, gl = lane % G;
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+  const unsigned glow = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
   const int tsize = 1 << tbits;
-  double *vals = reinterpret_cast<double *>(smem) + (int64_t)warp * tsize;
-  int32_t *keys = reinterpret_cast<int32_t *>(smem + sizeof(double) * (size_t)tsize * nwarps) + (int64_t)warp * tsize;
-  __shared__ int32_t cnt_s[kGemmThreads / 32];
-  for (int32_t r = blockIdx.x * nwarps + warp; r < nrows; r += gridDim.x * nwarps) {
-    const int32_t row = rows[r];
-    const int32_t as = arp[row], ae = arp[row + 1];
-    for (int h = lane; h < tsize; h += 32) keys[h] = -1;
-    if (lane == 0) cnt_s[warp] = 0;
+  const int tab = warp * R + grp;
+  double *vals = reinterpret_cast<double *>(smem) + (int64_t)tab * tsize;
+  int32_t *keys =
+      reinterpret_cast<int32_t *>(smem + sizeof(double) * (size_t)tsize * nwarps * R) + (int64_t)tab * tsize;
+  __shared__ int32_t cnt_s[kGemmThreads / 32 * 4];
+  __shared__ int32_t ovf_s[kGemmThreads / 32 * 4];
+  for (int64_t base = ((int64_t)blockIdx.x * nwarps + warp) * R; base < nrows;
+       base += (int64_t)gridDim.x * nwarps * R) {
+    const bool has = base + grp < nrows;
+    const int32_t row = has ? rows[base + grp] : 0;
+    const int32_t as = has ? arp[row] : 0, alen = has ? arp[row + 1] - as : 0;
+    for (int h = gl; h < tsize; h += G) keys[h] = -1;
+    if (gl == 0) { cnt_s[tab] = 0; ovf_s[tab] = 0; }
     __syncwarp();
-    for (int32_t ka = as; ka < ae; ka++) {
-      const int32_t k = acol[ka];
-      const double a = aval[ka];
-      const int32_t bs = brp[k], be = brp[k + 1];
-      for (int32_t kb = bs + lane; kb < be; kb += 32) {
-        const int32_t j = bcol[kb];
-        int h = hslot(j, tbits);
-        int probes = 0;
-        for (;;) {
-          int32_t prev = atomicCAS(&keys[h], -1, j);
-          if (prev == -1) {
-            atomicAdd(&cnt_s[warp], 1);
-            if (NUMERIC) vals[h] = a * bval[kb];
-            break;
+    const int32_t amax = __reduce_max_sync(0xffffffffu, alen);
+    for (int32_t t = 0; t < amax; t++) {
+      const bool on = t < alen;
+      const int32_t k = on ? acol[as + t] : 0;
+      const double a = on ? aval[as + t] : 0.0;
+      const int32_t bs = on ? brp[k] : 0, blen = on ? brp[k + 1] - bs : 0;
+      const int32_t bmax = __reduce_max_sync(0xffffffffu, blen);
+      for (int32_t u0 = 0; u0 < bmax; u0 += G) {
+        const int32_t u = u0 + gl;
+        const bool live = u < blen;
+        const int32_t j = live ? bcol[bs + u] : -1;
+        double prod = 0.0;
+        if (NUMERIC) prod = a * (live ? bval[bs + u] : 0.0);
+        int h = -1;
+        bool fresh = false;
+        if (live) {
+          h = hslot(j, tbits);
+          for (int probes = 0;; probes++) {
+            const int32_t prev = atomicCAS(&keys[h], -1, j);
+            if (prev == -1) { fresh = true; atomicAdd(&cnt_s[tab], 1); break; }
+            if (prev == j) break;
+            h = (h + 1) & (tsize - 1);
+            if (probes + 1 >= tsize) { ovf_s[tab] = 1; h = -1; break; }
           }
-          if (prev == j) {
-            if (NUMERIC) vals[h] = vals[h] + a * bval[kb];
-            break;
-          }
-          h = (h + 1) & (tsize - 1);
-          if (++probes >= tsize) { atomicExch(err, 1); break; }
+        }
+        __syncwarp();
+        if (NUMERIC && h >= 0) vals[h] = fresh ? prod : vals[h] + prod;
+        __syncwarp();
+      }
+    }
+    const int32_t cnt = cnt_s[tab];
+    const bool over = ovf_s[tab] != 0 || cnt > tsize;
+    if (!NUMERIC) {
+      // a row whose distinct columns overflow this table is listed in
+      // `defer` for a pass with the largest table (without a list: error)
+      if (has && gl == 0) {
+        if (over && defer) {
+          defer[1 + atomicAdd(&defer[0], 1)] = row;
+          crp[row] = 0;
+        } else {
+          if (over) atomicExch(err, 1);
+          crp[row] = cnt;
         }
       }
-      __syncwarp();
-    }
-    __syncwarp();
-    const int32_t cnt = cnt_s[warp];
-    if (cnt > tsize && lane == 0) atomicExch(err, 1);
-    if (!NUMERIC) {
-      if (lane == 0) crp[row] = cnt;
-    } else if (cnt <= tsize) {
+    } else {
+      if (has && over && gl == 0) atomicExch(err, 1);
       // compact the occupied slots to the front of the table (in place: a
-      // slot moves only to a lower index, after the whole warp has read its
+      // slot moves only to a lower index, after the whole group has read its
       // chunk), sort them by column and write the output row
       int32_t base_c = 0;
-      for (int h0 = 0; h0 < tsize; h0 += 32) {
-        const int32_t j = keys[h0 + lane];
-        const double v = vals[h0 + lane];
-        const unsigned occ = __ballot_sync(0xffffffffu, j >= 0);
+      for (int h0 = 0; h0 < tsize; h0 += G) {
+        const int32_t j = keys[h0 + gl];
+        const double v = vals[h0 + gl];
+        const unsigned occ = (__ballot_sync(0xffffffffu, j >= 0) >> (grp * G)) & glow;
         __syncwarp();
         if (j >= 0) {
-          const int32_t pos = base_c + __popc(occ & ((1u << lane) - 1u));
+          const int32_t pos = base_c + __popc(occ & ((1u << gl) - 1u));
           keys[pos] = j;
           vals[pos] = v;
         }
         base_c += __popc(occ);
         __syncwarp();
       }
-      warp_sort_pairs(keys, vals, cnt, tsize);
-      const int32_t base = crp[row], room = crp[row + 1] - base;
-      if (room != cnt && lane == 0) atomicExch(err, 1);
-      for (int32_t a = lane; a < cnt && a < room; a += 32) {
-        ccol[base + a] = keys[a];
-        cval[base + a] = vals[a];
+      const int32_t scnt = has && cnt <= tsize ? cnt : 0;
+      group_sort_pairs<G>(keys, vals, scnt, tsize, gl, gmask);
+      if (has && cnt <= tsize) {
+        const int32_t cb = crp[row], room = crp[row + 1] - cb;
+        if (room != cnt && gl == 0) atomicExch(err, 1);
+        for (int32_t a = gl; a < cnt && a < room; a += G) {
+          ccol[cb + a] = keys[a];
+          cval[cb + a] = vals[a];
+        }
       }
     }
     __syncwarp();
@@ -365,29 +399,55 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const in
 
 // Lists the rows bin by bin (bin counts bincnt_d on the device) and launches
 // the product kernel once per non-empty bin with that bin's table size.
+// Lists the rows bin by bin (bin counts bincnt_d on the device) and launches
+// the product kernel once per non-empty bin with that bin's table size. In
+// the first pass (tables sized by the product count, often several times the
+// distinct count) a bin's rows first try a table of at most kGemmTry slots;
+// the rows it cannot hold run again with the largest table.
+constexpr int kGemmTryBits = 8;
 template <bool NUMERIC>
 static int spgemm_pass(const DCsr &A, const DCsr &B, DCsr &C, const uint8_t *bin, const int32_t *bincnt_d,
-                       int32_t *cursor, int32_t *rows, int32_t *err, cudaStream_t s) {
+                       int32_t *cursor, int32_t *rows, int32_t *err, int32_t *defer, cudaStream_t s) {
   int32_t hcnt[kGemmBins];
   RS_CHECK_CUDA(cudaMemcpyAsync(hcnt, bincnt_d, sizeof(hcnt), cudaMemcpyDeviceToHost, s));
   RS_CHECK_CUDA(cudaStreamSynchronize(s));
   int32_t hoff[kGemmBins + 1];
   hoff[0] = 0;
   for (int b = 0; b < kGemmBins; b++) hoff[b + 1] = hoff[b] + hcnt[b];
-  RS_CHECK_CUDA(cudaMemcpyAsync(cursor, hoff, sizeof(int32_t) * kGemmBins, cudaMemcpyHostToDevice, s));
-  RS_COUNTED k_spgemm_binfill<<<grid_for(A.n), kBlock, 0, s>>>(A.n, bin, cursor, rows);
   // (cudaMemcpyAsync from the pageable stack array hoff stages the data
   // before it returns)
+  RS_CHECK_CUDA(cudaMemcpyAsync(cursor, hoff, sizeof(int32_t) * kGemmBins, cudaMemcpyHostToDevice, s));
+  RS_COUNTED k_spgemm_binfill<<<grid_for(A.n), kBlock, 0, s>>>(A.n, bin, cursor, rows);
+  if (!NUMERIC) RS_CHECK_CUDA(cudaMemsetAsync(defer, 0, sizeof(int32_t), s));
+  auto run = [&](int tbits, int32_t nrows, const int32_t *list, int32_t *dfr) {
+    const int tsize = 1 << tbits;
+    // lanes per row: 8 for tables of up to 64 slots, 16 for 128, else 32
+    const int G = tsize <= 64 ? 8 : (tsize <= 128 ? 16 : 32), R = 32 / G;
+    const int warps = (int)std::max<int64_t>(
+        1, std::min<int64_t>(kGemmThreads / 32, kGemmSmem / (12 * (int64_t)tsize * R)));
+    const size_t shm = (sizeof(double) + sizeof(int32_t)) * (size_t)tsize * warps * R;
+    const int64_t per_cta = (int64_t)warps * R;
+    const unsigned grid = (unsigned)std::min<int64_t>((nrows + per_cta - 1) / per_cta, (int64_t)num_sms() * 32);
+    auto kern = G == 8 ? k_spgemm<8, NUMERIC> : (G == 16 ? k_spgemm<16, NUMERIC> : k_spgemm<32, NUMERIC>);
+    RS_COUNTED kern<<<grid, 32 * warps, shm, s>>>(nrows, list, tbits, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val,
+                                                  C.rowptr, C.col, C.val, err, dfr);
+  };
+  bool tried = false;
   for (int b = 0; b < kGemmBins; b++) {
     if (hcnt[b] == 0) continue;
-    const int tbits = 5 + b, tsize = 1 << tbits;
-    const int warps =
-        (int)std::max<int64_t>(1, std::min<int64_t>(kGemmThreads / 32, kGemmSmem / (12 * (int64_t)tsize)));
-    const size_t shm = (sizeof(double) + sizeof(int32_t)) * (size_t)tsize * warps;
-    const unsigned grid = (unsigned)std::min<int64_t>((hcnt[b] + warps - 1) / warps, (int64_t)num_sms() * 32);
-    RS_COUNTED k_spgemm<NUMERIC><<<grid, 32 * warps, shm, s>>>(hcnt[b], rows + hoff[b], tbits, A.rowptr, A.col,
-                                                               A.val, B.rowptr, B.col, B.val, C.rowptr, C.col,
-                                                               C.val, err);
+    const int tbits = 5 + b;
+    if (!NUMERIC && tbits > kGemmTryBits) {
+      run(kGemmTryBits, hcnt[b], rows + hoff[b], defer);
+      tried = true;
+    } else {
+      run(tbits, hcnt[b], rows + hoff[b], nullptr);
+    }
+  }
+  if (tried) {
+    int32_t nd = 0;
+    RS_CHECK_CUDA(cudaMemcpyAsync(&nd, defer, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RS_CHECK_CUDA(cudaStreamSynchronize(s));
+    if (nd > 0) run(kHashBits, nd, defer + 1, nullptr);
   }
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
@@ -398,25 +458,29 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   C.m = B.m;
   RS_TRY(dalloc_n(&C.rowptr, (size_t)A.n + 1, s));
   Scratch sc(s);
-  int32_t *err = nullptr, *bincnt = nullptr, *cursor = nullptr, *rows = nullptr;
+  int32_t *err = nullptr, *bincnt = nullptr, *cursor = nullptr, *rows = nullptr, *defer = nullptr;
   uint8_t *bin = nullptr;
   RS_TRY(sc.get(&err, 2));
   RS_TRY(sc.get(&bincnt, 2 * kGemmBins));
   RS_TRY(sc.get(&cursor, kGemmBins));
   RS_TRY(sc.get(&rows, (size_t)A.n + 1));
   RS_TRY(sc.get(&bin, (size_t)A.n + 1));
+  RS_TRY(sc.get(&defer, (size_t)A.n + 1));
   RS_CHECK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), s));
   RS_CHECK_CUDA(cudaMemsetAsync(bincnt, 0, 2 * kGemmBins * sizeof(int32_t), s));
   static bool attr = false;
   if (!attr) {
-    RS_CHECK_CUDA(cudaFuncSetAttribute(k_spgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
-    RS_CHECK_CUDA(cudaFuncSetAttribute(k_spgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
+    const void *ks[6] = {(const void *)k_spgemm<8, false>, (const void *)k_spgemm<16, false>,
+                         (const void *)k_spgemm<32, false>, (const void *)k_spgemm<8, true>,
+                         (const void *)k_spgemm<16, true>, (const void *)k_spgemm<32, true>};
+    for (const void *k : ks)
+      RS_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem));
     attr = true;
   }
   ProfScope ps(kProfSpgemm, A.nnz * 12.0 + B.nnz * 12.0, s);
   if (A.n > 0) {
     RS_COUNTED k_spgemm_bin1<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, B.rowptr, bin, bincnt);
-    RS_TRY(spgemm_pass<false>(A, B, C, bin, bincnt, cursor, rows, err, s));
+    RS_TRY(spgemm_pass<false>(A, B, C, bin, bincnt, cursor, rows, err, defer, s));
   }
   int32_t tot = 0;
   RS_TRY(exclusive_scan(C.rowptr, C.rowptr, A.n, s, &tot));
@@ -429,7 +493,7 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   RS_TRY(dalloc_n(&C.val, (size_t)tot, s));
   if (A.n > 0) {
     RS_COUNTED k_spgemm_bin2<<<grid_for(A.n), kBlock, 0, s>>>(A.n, C.rowptr, bin, bincnt + kGemmBins);
-    RS_TRY(spgemm_pass<true>(A, B, C, bin, bincnt + kGemmBins, cursor, rows, err, s));
+    RS_TRY(spgemm_pass<true>(A, B, C, bin, bincnt + kGemmBins, cursor, rows, err, nullptr, s));
     RS_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RS_CHECK_CUDA(cudaStreamSynchronize(s));
     if (herr) return fail(RS_ESETUP, "sparse product row exceeds the per-row table");
