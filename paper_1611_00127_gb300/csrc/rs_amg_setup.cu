@@ -303,10 +303,11 @@ constexpr int kIF = 256;
 struct IWarp {
   double *num, *fa, *fd;
   int32_t *hkey, *chat, *nset, *fk, *fb, *fe, *fneg, *cnt;   // hkey: candidate hash set; cnt: -, m, nf
+  int16_t *hidx;   // per hash slot: the key's position in the sorted Chat_i
 };
 
 __host__ __device__ inline size_t iwarp_bytes(int ccap, int hcap, int fcap) {
-  return 8 * (size_t)(hcap + 2 * fcap) + 4 * (size_t)(ccap + 2 * hcap + 4 * fcap + 4);
+  return 8 * (size_t)(hcap + 2 * fcap) + 4 * (size_t)(ccap + 2 * hcap + 4 * fcap + 4) + 2 * (size_t)ccap;
 }
 
 __device__ inline IWarp iwarp_at(unsigned char *base, int ccap, int hcap, int fcap) {
@@ -322,7 +323,22 @@ __device__ inline IWarp iwarp_at(unsigned char *base, int ccap, int hcap, int fc
   W.fe = W.fb + fcap;
   W.fneg = W.fe + fcap;
   W.cnt = W.fneg + fcap;
+  W.hidx = reinterpret_cast<int16_t *>(W.cnt + 4);
   return W;
+}
+
+// Position of `key` in the sorted Chat_i through the row's hash set (-1: not
+// a member).
+__device__ __forceinline__ int32_t hfind(const IWarp &W, int tbits, int32_t key) {
+  const int size = 1 << tbits;
+  int h = (int)(((uint32_t)key * 2654435761u) >> (32 - tbits));
+  for (int p = 0; p < size; p++) {
+    const int32_t k = W.hkey[h];
+    if (k == key) return W.hidx[h];
+    if (k < 0) return -1;
+    h = (h + 1) & (size - 1);
+  }
+  return -1;
 }
 
 // Sign tests on the bit pattern (integer instructions; GB300 issues FP64
@@ -536,6 +552,13 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
       }
       __syncwarp();
       warp_sort_asc(W.chat, m, hcap);
+      // map each hash slot to its key's position in Chat_i
+      for (int32_t idx = lane; idx < m; idx += 32) {
+        const int32_t key = W.chat[idx];
+        int h = (int)(((uint32_t)key * 2654435761u) >> (32 - tbits));
+        while (W.hkey[h] != key) h = (h + 1) & ((1 << tbits) - 1);
+        W.hidx[h] = (int16_t)idx;
+      }
     }
     __syncwarp();
     if (ovf) {
@@ -557,7 +580,7 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
       Acc d{0.0, false};
       for (int32_t t = kb; t < ke; t++) {
         const int32_t l = col[t];
-        if (l == k || !(l == i || find_sorted(W.chat, m, l) >= 0)) continue;
+        if (l == k || !(l == i || hfind(W, tbits, l) >= 0)) continue;
         const double av = val[t];
         if (!dopposite(neg, av)) continue;
         d.add(av);
@@ -569,22 +592,38 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
       W.fneg[f] = neg;
     }
     __syncwarp();
-    // numerators: one lane per target j; a_ij first, then t_k * abar_kj for k ascending
+    // numerators, scattered: a_ij first (from row i), then t_k * abar_kj for
+    // the k in ascending order, each k's row spread over the lanes (a row
+    // holds each target at most once, so no two lanes add to one target in a
+    // pass, and every target's terms arrive in the order of a sequential sum)
     for (int32_t idx = lane; idx < m; idx += 32) {
-      const int32_t l = W.chat[idx];
-      const int32_t qi = find_row(col, s, e, l);
-      Acc nm{0.0, false};
-      if (qi >= 0) nm.add(val[qi]);
-      for (int32_t f = 0; f < nf; f++) {
-        if (dzero(W.fd[f])) continue;
-        const int32_t qk = find_row(col, W.fb[f], W.fe[f], l);
-        if (qk < 0) continue;
-        const double av = val[qk];
-        if (!dopposite(W.fneg[f], av)) continue;
-        nm.add(W.fa[f] * av);
+      W.num[idx] = 0.0;
+      W.nset[idx] = 0;
+    }
+    __syncwarp();
+    for (int32_t q = s + lane; q < e; q += 32) {
+      const int32_t x = hfind(W, tbits, col[q]);
+      if (x >= 0) {
+        W.num[x] = val[q];
+        W.nset[x] = 1;
       }
-      W.num[idx] = nm.v;
-      W.nset[idx] = nm.set ? 1 : 0;
+    }
+    __syncwarp();
+    for (int32_t f = 0; f < nf; f++) {
+      if (dzero(W.fd[f])) continue;
+      const double tq = W.fa[f];
+      const int neg = W.fneg[f];
+      const int32_t ke = W.fe[f];
+      for (int32_t q = W.fb[f] + lane; q < ke; q += 32) {
+        const int32_t x = hfind(W, tbits, col[q]);
+        if (x < 0) continue;
+        const double av = val[q];
+        if (!dopposite(neg, av)) continue;
+        const double t = tq * av;
+        W.num[x] = W.nset[x] ? W.num[x] + t : t;
+        W.nset[x] = 1;
+      }
+      __syncwarp();
     }
     // dtil: pass A over row i, then the "+i" terms of the k (ascending). The
     // lanes look up the terms of 32 entries at a time; lane 0 adds them in
@@ -600,7 +639,7 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
           const int32_t j = col[q];
           v = val[q];
           if (j == i) has = true;
-          else if (find_sorted(W.chat, m, j) < 0) {
+          else if (hfind(W, tbits, j) < 0) {
             isF = strong[q] && cf[j] != 1;
             has = !isF;
           }
@@ -1604,11 +1643,15 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       std::vector<int32_t> hc(nseg);
       RS_TRY(sync_copy(hc.data(), segc, sizeof(int32_t) * nseg, s));
       nact = 0;
+      bool dropped = false;   // a system stopped coarsening after PMIS
       for (int32_t q = 0; q < nseg; q++) {
         if (!act[q]) continue;
         const int32_t ng = pseg_off[q + 1] - pseg_off[q];
-        if (hc[q] == 0 || (double)hc[q] > 0.9 * (double)ng) { act[q] = 0; smooth_seg[q] = 0; H.last_level[q] = l; }
-        else nact++;
+        if (hc[q] == 0 || (double)hc[q] > 0.9 * (double)ng) {
+          act[q] = 0; smooth_seg[q] = 0; H.last_level[q] = l; dropped = true;
+        } else {
+          nact++;
+        }
       }
       RS_CHECK_CUDA(cudaMemcpyAsync(dact, act.data(), nseg, cudaMemcpyHostToDevice, s));
       RS_COUNTED k_seg_revert<<<g, kBlock, 0, s>>>(np, cfp, pseg, dact, isc);
@@ -1626,9 +1669,13 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         // interpolation of one function part F (np rows) under the point splitting
         auto interpolate = [&](const DCsr &F, const int8_t *cfu, DCsr &Pf) -> int {
           const unsigned gf = grid_for(F.n);
-          RS_COUNTED k_diag<<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag);
-          RS_COUNTED k_strength<<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, pseg, dact, prm.theta, 1,
-                                                      strong);
+          // the diagonal and strength of F: those PMIS used when F is the
+          // coarsened matrix itself and no system stopped since, else formed
+          if (B > 1 || dropped) {
+            RS_COUNTED k_diag<<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag);
+            RS_COUNTED k_strength<<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, pseg, dact, prm.theta, 1,
+                                                        strong);
+          }
           Pf.n = F.n;
           Pf.m = nc;
           RS_TRY(dalloc_n(&Pf.rowptr, (size_t)F.n + 1, s));
