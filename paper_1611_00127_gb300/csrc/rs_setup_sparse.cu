@@ -192,9 +192,11 @@ __device__ __forceinline__ void warp_bin_add(bool ok, int b, int32_t *cnt) {
 
 // pass-1 bins: the number of products of each row of A with B
 __global__ void k_spgemm_bin1(int32_t n, const int32_t *__restrict__ arp, const int32_t *__restrict__ acol,
-                              const int32_t *__restrict__ brp, uint8_t *bin, int32_t *bincnt) {
+                              const int32_t *__restrict__ brp, uint8_t *bin, int32_t *bincnt, int32_t *npcap,
+                              unsigned long long *captot) {
   const int32_t row = blockIdx.x * blockDim.x + threadIdx.x;
   int b = 0;
+  int32_t cap = 0;
   if (row < n) {
     int64_t np = 0;
     for (int32_t ka = arp[row]; ka < arp[row + 1]; ka++) {
@@ -203,7 +205,14 @@ __global__ void k_spgemm_bin1(int32_t n, const int32_t *__restrict__ arp, const 
     }
     b = gemm_bin(np);
     bin[row] = (uint8_t)b;
+    // the most entries the row can have (its products, at most a full table)
+    cap = (int32_t)(np < kHash ? np : kHash);
+    npcap[row] = cap;
   }
+  // the reservation's total in 64 bits (one atomic per warp; a warp's sum
+  // is at most 32 * kHash)
+  const unsigned ws = __reduce_add_sync(0xffffffffu, (unsigned)cap);
+  if ((threadIdx.x & 31) == 0 && ws) atomicAdd(captot, (unsigned long long)ws);
   warp_bin_add(row < n, b, bincnt);
 }
 
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const in
                                                          const double *__restrict__ bval,
                                                          int32_t *__restrict__ crp, int32_t *__restrict__ ccol,
                                                          double *__restrict__ cval, int32_t *err,
-                                                         int32_t *__restrict__ defer) {
+                                                         int32_t *__restrict__ defer, int32_t *__restrict__ ccnt) {
   constexpr int R = 32 / G;
   extern __shared__ unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -364,7 +373,14 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const in
         }
       }
     } else {
-      if (has && over && gl == 0) atomicExch(err, 1);
+      // one pass into reserved rows (ccnt given: crp holds each row's
+      // reserved capacity, the count goes to ccnt): a row whose distinct
+      // columns overflow this table is listed in `defer` for a pass with the
+      // largest table (without a list: error)
+      if (has && over && gl == 0) {
+        if (defer) defer[1 + atomicAdd(&defer[0], 1)] = row;
+        else atomicExch(err, 1);
+      }
       // compact the occupied slots to the front of the table (in place: a
       // slot moves only to a lower index, after the whole group has read its
       // chunk), sort them by column and write the output row
@@ -382,11 +398,12 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const in
         base_c += __popc(occ);
         __syncwarp();
       }
-      const int32_t scnt = has && cnt <= tsize ? cnt : 0;
+      const int32_t scnt = has && !over ? cnt : 0;
       group_sort_pairs<G>(keys, vals, scnt, tsize, gl, gmask);
-      if (has && cnt <= tsize) {
+      if (has && !over) {
         const int32_t cb = crp[row], room = crp[row + 1] - cb;
-        if (room != cnt && gl == 0) atomicExch(err, 1);
+        if ((ccnt ? cnt > room : room != cnt) && gl == 0) atomicExch(err, 1);
+        if (ccnt && gl == 0) ccnt[row] = cnt;
         for (int32_t a = gl; a < cnt && a < room; a += G) {
           ccol[cb + a] = keys[a];
           cval[cb + a] = vals[a];
@@ -407,7 +424,11 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const in
 constexpr int kGemmTryBits = 8;
 template <bool NUMERIC>
 static int spgemm_pass(const DCsr &A, const DCsr &B, DCsr &C, const uint8_t *bin, const int32_t *bincnt_d,
-                       int32_t *cursor, int32_t *rows, int32_t *err, int32_t *defer, cudaStream_t s) {
+                       int32_t *cursor, int32_t *rows, int32_t *err, int32_t *defer, cudaStream_t s,
+                       int32_t *ccnt = nullptr, int32_t *ccol = nullptr, double *cval = nullptr) {
+  // output rows: C's, or (ccnt given) rows reserved at C.rowptr's offsets
+  int32_t *ocol = ccol ? ccol : C.col;
+  double *oval = cval ? cval : C.val;
   int32_t hcnt[kGemmBins];
   RS_CHECK_CUDA(cudaMemcpyAsync(hcnt, bincnt_d, sizeof(hcnt), cudaMemcpyDeviceToHost, s));
   RS_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -418,7 +439,7 @@ static int spgemm_pass(const DCsr &A, const DCsr &B, DCsr &C, const uint8_t *bin
   // before it returns)
   RS_CHECK_CUDA(cudaMemcpyAsync(cursor, hoff, sizeof(int32_t) * kGemmBins, cudaMemcpyHostToDevice, s));
   RS_COUNTED k_spgemm_binfill<<<grid_for(A.n), kBlock, 0, s>>>(A.n, bin, cursor, rows);
-  if (!NUMERIC) RS_CHECK_CUDA(cudaMemsetAsync(defer, 0, sizeof(int32_t), s));
+  if (defer) RS_CHECK_CUDA(cudaMemsetAsync(defer, 0, sizeof(int32_t), s));
   auto run = [&](int tbits, int32_t nrows, const int32_t *list, int32_t *dfr) {
     const int tsize = 1 << tbits;
     // lanes per row: 8 for tables of up to 64 slots, 16 for 128, else 32
@@ -430,13 +451,13 @@ static int spgemm_pass(const DCsr &A, const DCsr &B, DCsr &C, const uint8_t *bin
     const unsigned grid = (unsigned)std::min<int64_t>((nrows + per_cta - 1) / per_cta, (int64_t)num_sms() * 32);
     auto kern = G == 8 ? k_spgemm<8, NUMERIC> : (G == 16 ? k_spgemm<16, NUMERIC> : k_spgemm<32, NUMERIC>);
     RS_COUNTED kern<<<grid, 32 * warps, shm, s>>>(nrows, list, tbits, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val,
-                                                  C.rowptr, C.col, C.val, err, dfr);
+                                                  C.rowptr, ocol, oval, err, dfr, ccnt);
   };
   bool tried = false;
   for (int b = 0; b < kGemmBins; b++) {
     if (hcnt[b] == 0) continue;
     const int tbits = 5 + b;
-    if (!NUMERIC && tbits > kGemmTryBits) {
+    if (defer && tbits > kGemmTryBits) {
       run(kGemmTryBits, hcnt[b], rows + hoff[b], defer);
       tried = true;
     } else {
@@ -453,19 +474,41 @@ static int spgemm_pass(const DCsr &A, const DCsr &B, DCsr &C, const uint8_t *bin
   return 0;
 }
 
+// Moves row i's cnt[i] entries from the reserved rows at toff[i] to C's rows
+// at crp[i].
+__global__ void k_rows_compact(int32_t n, const int32_t *__restrict__ toff, const int32_t *__restrict__ crp,
+                               const int32_t *__restrict__ tcol, const double *__restrict__ tval,
+                               int32_t *__restrict__ ccol, double *__restrict__ cval) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t a = toff[i], b = crp[i], c = crp[i + 1] - b;
+  for (int32_t t = 0; t < c; t++) {
+    ccol[b + t] = tcol[a + t];
+    cval[b + t] = tval[a + t];
+  }
+}
+
+// C = A B. When the rows' worst cases (each row's product count, at most a
+// full table) fit in a quarter of the free device memory, one numeric pass
+// writes every row into a reserved row of that size and a compaction moves
+// them into C; otherwise a counting pass sizes C's rows first.
 int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   C.n = A.n;
   C.m = B.m;
   RS_TRY(dalloc_n(&C.rowptr, (size_t)A.n + 1, s));
   Scratch sc(s);
-  int32_t *err = nullptr, *bincnt = nullptr, *cursor = nullptr, *rows = nullptr, *defer = nullptr;
+  int32_t *err = nullptr, *bincnt = nullptr, *cursor = nullptr, *rows = nullptr, *defer = nullptr, *npcap = nullptr;
   uint8_t *bin = nullptr;
+  unsigned long long *captot = nullptr;
   RS_TRY(sc.get(&err, 2));
   RS_TRY(sc.get(&bincnt, 2 * kGemmBins));
   RS_TRY(sc.get(&cursor, kGemmBins));
   RS_TRY(sc.get(&rows, (size_t)A.n + 1));
   RS_TRY(sc.get(&bin, (size_t)A.n + 1));
   RS_TRY(sc.get(&defer, (size_t)A.n + 1));
+  RS_TRY(sc.get(&npcap, (size_t)A.n + 1));
+  RS_TRY(sc.get(&captot, 1));
+  RS_CHECK_CUDA(cudaMemsetAsync(captot, 0, sizeof(unsigned long long), s));
   RS_CHECK_CUDA(cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), s));
   RS_CHECK_CUDA(cudaMemsetAsync(bincnt, 0, 2 * kGemmBins * sizeof(int32_t), s));
   static bool attr = false;
@@ -478,13 +521,48 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     attr = true;
   }
   ProfScope ps(kProfSpgemm, A.nnz * 12.0 + B.nnz * 12.0, s);
+  int32_t herr = 0;
   if (A.n > 0) {
-    RS_COUNTED k_spgemm_bin1<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, B.rowptr, bin, bincnt);
+    RS_COUNTED k_spgemm_bin1<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, B.rowptr, bin, bincnt, npcap,
+                                                              captot);
+    unsigned long long hcap = 0;
+    RS_CHECK_CUDA(cudaMemcpyAsync(&hcap, captot, sizeof(hcap), cudaMemcpyDeviceToHost, s));
+    RS_CHECK_CUDA(cudaStreamSynchronize(s));
+    size_t fr = 0, tot_mem = 0;
+    RS_CHECK_CUDA(cudaMemGetInfo(&fr, &tot_mem));
+    if (hcap < 0x7fffffffULL && hcap * 12 <= fr / 4) {
+      // reserved rows: offsets of the capped product counts
+      int32_t *toff = nullptr;
+      RS_TRY(sc.get(&toff, (size_t)A.n + 1));
+      int32_t reserve = 0;
+      RS_TRY(exclusive_scan(npcap, toff, A.n, s, nullptr));
+      reserve = (int32_t)hcap;
+      Scratch st(s);
+      int32_t *tcol = nullptr, *ccnt = nullptr;
+      double *tval = nullptr;
+      RS_TRY(st.get(&tcol, (size_t)reserve + 1));
+      RS_TRY(st.get(&tval, (size_t)reserve + 1));
+      RS_TRY(st.get(&ccnt, (size_t)A.n + 1));
+      DCsr T;
+      T.n = A.n;
+      T.rowptr = toff;
+      RS_TRY(spgemm_pass<true>(A, B, T, bin, bincnt, cursor, rows, err, defer, s, ccnt, tcol, tval));
+      int32_t tot = 0;
+      RS_TRY(exclusive_scan(ccnt, C.rowptr, A.n, s, &tot));
+      RS_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      RS_CHECK_CUDA(cudaStreamSynchronize(s));
+      if (herr) return fail(RS_ESETUP, "sparse product row exceeds the per-row table");
+      C.nnz = tot;
+      RS_TRY(dalloc_n(&C.col, (size_t)tot, s));
+      RS_TRY(dalloc_n(&C.val, (size_t)tot, s));
+      RS_COUNTED k_rows_compact<<<grid_for(A.n), kBlock, 0, s>>>(A.n, toff, C.rowptr, tcol, tval, C.col, C.val);
+      RS_CHECK_CUDA(cudaGetLastError());
+      return 0;
+    }
     RS_TRY(spgemm_pass<false>(A, B, C, bin, bincnt, cursor, rows, err, defer, s));
   }
   int32_t tot = 0;
   RS_TRY(exclusive_scan(C.rowptr, C.rowptr, A.n, s, &tot));
-  int32_t herr = 0;
   RS_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   RS_CHECK_CUDA(cudaStreamSynchronize(s));
   if (herr) return fail(RS_ESETUP, "sparse product row exceeds the per-row table");
