@@ -435,6 +435,32 @@ __device__ __forceinline__ int find_row(const int32_t *col, int32_t s, int32_t e
   return -1;
 }
 
+// Room for row i of P: 1 for a C row; for an F row its candidate count with
+// repeats (1 per strong C neighbour, the length of each strong F neighbour's
+// row), which bounds |Chat_i|, capped at Chat's capacity hcap. The total is
+// summed in 64 bits (one atomic per warp).
+__global__ void k_interp_cap(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             const uint8_t *__restrict__ strong, const int8_t *__restrict__ cf, int32_t hcap,
+                             int32_t *__restrict__ cap, unsigned long long *captot) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  int32_t c = 0;
+  if (i < n) {
+    if (cf[i] == 1) {
+      c = 1;
+    } else {
+      int64_t b = 0;
+      for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+        const int32_t j = col[q];
+        if (j != i && strong[q]) b += cf[j] == 1 ? 1 : rp[j + 1] - rp[j];
+      }
+      c = (int32_t)(b < hcap ? b : hcap);
+    }
+    cap[i] = c;
+  }
+  const unsigned ws = __reduce_add_sync(0xffffffffu, (unsigned)c);
+  if ((threadIdx.x & 31) == 0 && ws) atomicAdd(captot, (unsigned long long)ws);
+}
+
 // Moves row i's cnt[i] entries from the scratch rows at toff[i] to the
 // interpolation matrix's rows at prp[i].
 __global__ void k_interp_compact(int32_t n, const int32_t *__restrict__ toff, const int32_t *__restrict__ prp,
@@ -562,7 +588,11 @@ __global__ void __launch_bounds__(256) k_interp_ext_w(int32_t n, int ccap, int h
     }
     __syncwarp();
     if (ovf) {
-      if (lane == 0) { atomicExch(err, 1); cnt[i] = 0; }
+      if (lane == 0) {
+        if (defer) defer[1 + atomicAdd(&defer[0], 1)] = i;   // for the full workspace
+        else atomicExch(err, 1);
+        cnt[i] = 0;
+      }
       continue;
     }
     if (m == 0) {
@@ -1743,6 +1773,53 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
             auto grid_w = [&](const Cfg &c, int64_t rows) {
               return (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + c.iw - 1) / c.iw, (int64_t)num_sms() * 64));
             };
+            // one pass when the rows' bounds fit a quarter of the free memory:
+            // rows reserved at their bound, the weights formed once (rows the
+            // small workspace cannot hold again with the full one), then
+            // compacted
+            if (F.n > 0) {
+              unsigned long long *captot = nullptr;
+              RS_TRY(si.get(&captot, 1));
+              RS_CHECK_CUDA(cudaMemsetAsync(captot, 0, sizeof(unsigned long long), s));
+              RS_COUNTED k_interp_cap<<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, strong, cfu, cbig.h, toff, captot);
+              unsigned long long hcapt = 0;
+              RS_TRY(sync_copy(&hcapt, captot, sizeof(hcapt), s));
+              size_t fr = 0, tm = 0;
+              RS_CHECK_CUDA(cudaMemGetInfo(&fr, &tm));
+              if (hcapt < 0x7fffffffULL && hcapt * 12 <= fr / 4) {
+                RS_TRY(exclusive_scan(toff, toff, F.n, s, nullptr));
+                RS_TRY(si.get(&tcol, (size_t)hcapt + 1));
+                RS_TRY(si.get(&tval, (size_t)hcapt + 1));
+                RS_TRY(si.get(&defer, (size_t)F.n + 1));
+                RS_CHECK_CUDA(cudaMemsetAsync(defer, 0, sizeof(int32_t), s));
+                int32_t nd = 0;
+                {
+                  ProfScope ps(kProfInterp, ibytes + (double)hcapt * 12.0, s);
+                  const Cfg &c = split ? csmall : cbig;
+                  RS_COUNTED k_interp_ext_w<false><<<grid_w(c, F.n), 32 * c.iw, c.shm, s>>>(
+                      F.n, c.c, c.h, c.f, F.rowptr, F.col, F.val, diag, strong, cfu, isc, toff, tcol, tval, tcnt, err,
+                      nullptr, 0, nullptr, split ? defer : nullptr);
+                  if (split) {
+                    RS_TRY(sync_copy(&nd, defer, sizeof(int32_t), s));
+                    if (nd > 0)
+                      RS_COUNTED k_interp_ext_w<false><<<grid_w(cbig, nd), 32 * cbig.iw, cbig.shm, s>>>(
+                          F.n, cbig.c, cbig.h, cbig.f, F.rowptr, F.col, F.val, diag, strong, cfu, isc, toff, tcol,
+                          tval, tcnt, err, defer + 1, nd, nullptr, nullptr);
+                  }
+                }
+                int32_t pnnz = 0;
+                RS_TRY(exclusive_scan(tcnt, Pf.rowptr, F.n, s, &pnnz));
+                int32_t herr = 0;
+                RS_TRY(sync_copy(&herr, err, sizeof(int32_t), s));
+                if (herr) return fail(RS_ESETUP, "interpolation set too large on level " + std::to_string(l));
+                Pf.nnz = pnnz;
+                RS_TRY(dalloc_n(&Pf.col, (size_t)pnnz + 1, s));
+                RS_TRY(dalloc_n(&Pf.val, (size_t)pnnz + 1, s));
+                RS_COUNTED k_interp_compact<<<gf, kBlock, 0, s>>>(F.n, toff, Pf.rowptr, tcol, tval, Pf.col, Pf.val);
+                RS_CHECK_CUDA(cudaGetLastError());
+                return 0;
+              }
+            }
             int32_t nbig = 0;
             if (split) {
               RS_TRY(si.get(&bigf, (size_t)F.n + 1));
