@@ -53,10 +53,25 @@ THETA_3D = 0.5
 # the CPU oracle's window of the 256^3 field: the corner block of this many
 # cells (1/128 of the grid)
 WINDOW = (64, 64, 32)
-# DRAM bytes (read + write) per launch of the roofline kernels, from one ncu
-# capture of the current kernel version (summaries and commands in profiles/);
-# absent where no capture of the current version exists.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) of all launches of a kernel class in one headline
+# step, from an ncu capture of the current kernels on the 128^3 grid of the
+# same generator scaled to 256^3 by the cell ratio 8 (summary and command in
+# profiles/dram_setup_channel128_step.md); absent where no capture of the
+# current version exists.
+NCU_TRAFFIC = {
+    "setup_spgemm": ((60.468e9 + 19.953e9) * 8, "profiles/dram_setup_channel128_step.md (128^3 step x 8)"),
+    "setup_interp": ((12.766e9 + 1.246e9) * 8, "profiles/dram_setup_channel128_step.md (128^3 step x 8)"),
+}
+# the kernels behind each class of the library's event profiler
+CLASS_KERNELS = {
+    "setup_spgemm": "k_spgemm_bin1, k_spgemm_binfill, k_spgemm, k_rows_compact (Galerkin and Schur-complement "
+                    "sparse products)",
+    "setup_interp": "k_interp_cap, k_interp_ext_w, k_interp_compact (extended+i interpolation)",
+    "hybrid_gs_sweep": "k_hgs, k_hgs2 (hybrid Gauss-Seidel sweeps)",
+    "csr_resid_restrict_prolong": "k_csr (residual, restriction, prolongation)",
+    "bsr2_spmv": "k_bsr2_spmv, k_cpr_resid (block SpMV)",
+    "gmres_cgs2": "k_arnoldi (CGS2 passes)",
+}
 
 
 def parse():
@@ -618,9 +633,11 @@ def class_roofline(prof, peak, peak_kind, classes=None):
     ms, by, n = cand[k]
     achieved = by / (ms * 1e-3) / 1e9
     tr = NCU_TRAFFIC.get(k)
-    return dict(bound="hbm", kernel=k, achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                traffic=tr[0] / n if tr else None, traffic_source=tr[1] if tr else None, peak_source=peak_kind,
-                launches=n, ms=ms, bytes=by, launch_ms=ms / n, bytes_per_launch=by / n)
+    return dict(bound="hbm", kernel=k, kernels=CLASS_KERNELS.get(k), achieved=achieved, peak=peak, unit="GB/s",
+                frac=achieved / peak, traffic=tr[0] / n if tr else None, traffic_source=tr[1] if tr else None,
+                peak_source=peak_kind, launches=n, ms=ms, bytes=by, launch_ms=ms / n, bytes_per_launch=by / n,
+                how="all launches of the class in one profiled headline step: algorithmic bytes over their "
+                    "summed device time (CUDA events around each call)")
 
 
 def main():
