@@ -122,9 +122,6 @@ typedef struct rs_amg_params {
                               two stages' P (the intermediate level is dropped); 0: off */
   int32_t chunk_coarse;    /* rows per chunk of the hybrid smoother on levels >= 1 (32..512);
                               0: `chunk` on every level */
-  int32_t tail_rows;       /* > 0: the levels with at most this many rows (down to the dense
-                              coarsest level) run their part of the V-cycle as one launch of a
-                              thread-block cluster; 0: one launch per kernel and level */
   int32_t restriction;     /* scalar AMG (num_functions 1): 0 Galerkin, R = P^T; 1 approximate
                               ideal restriction (AIR, Manteuffel, Southworth et al. 2018),
                               distance 1: R's row for C point i is 1 at i and -z on the F
@@ -364,8 +361,6 @@ int amg_level_smooth(const rs_amg *H, int32_t l, int32_t sweeps, double *bytes_p
  * RS_EINVAL for a level without a coarser one or an unknown `which`. */
 int amg_level_transfer(const rs_amg *H, int32_t l, int32_t which, int32_t reps, double *bytes_per_launch,
                        cudaStream_t stream);
-/* First level of the coarse tail (run as one cluster launch), or -1. */
-int amg_tail_level(const rs_amg *H, int32_t *start);
 
 /* Hierarchy inside a preconditioner: which = 0 pressure / Schur / black-box,
  * 1 saturation. NULL if absent. */

@@ -20,7 +20,6 @@ int check_amg_params(const rs_amg_params &a) {
   if (a.agg_levels < 0 || a.agg_levels > 8) return fail(RS_EINVAL, "agg_levels outside [0, 8]");
   if (a.chunk_coarse != 0 && (a.chunk_coarse < 32 || a.chunk_coarse > 512))
     return fail(RS_EINVAL, "chunk_coarse outside [32, 512]");
-  if (a.tail_rows < 0) return fail(RS_EINVAL, "negative tail_rows");
   if (a.restriction != 0 && a.restriction != 1 && a.restriction != 3)
     return fail(RS_EINVAL, "restriction must be 0 (Galerkin), 1 (AIR, distance 1) or 3 (lAIR)");
   return 0;
@@ -52,12 +51,6 @@ extern "C" int amg_setup(const rs_csr *A, const rs_amg_params *params, rs_amg **
     return r;
   }
   *H = h;
-  return RS_OK;
-}
-
-extern "C" int amg_tail_level(const rs_amg *H, int32_t *start) {
-  if (!H || !start) return fail(RS_EINVAL, "null argument");
-  *start = H->H.tail_start;
   return RS_OK;
 }
 

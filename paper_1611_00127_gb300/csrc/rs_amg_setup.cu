@@ -42,47 +42,95 @@ __device__ __forceinline__ bool beats(uint64_t ki, int32_t i, uint64_t kj, int32
   return ki > kj || (ki == kj && i < j);
 }
 
+// Row-wise kernels below take G lanes per row (G = 8, 16 or 32 from the mean
+// row length, row_lanes): consecutive lanes read consecutive entries of the
+// row, so a group's loads are contiguous; the grid covers n * G threads in
+// whole warps.
+static int row_lanes(int64_t n, int64_t nnz) {
+  const double avg = n > 0 ? (double)nnz / (double)n : 1.0;
+  return avg <= 10.0 ? 8 : (avg <= 24.0 ? 16 : 32);
+}
+#define RS_ROWG_SWITCH(g, ...)                                   \
+  switch (g) {                                                   \
+    case 8: { constexpr int G_ = 8; __VA_ARGS__; } break;        \
+    case 16: { constexpr int G_ = 16; __VA_ARGS__; } break;      \
+    default: { constexpr int G_ = 32; __VA_ARGS__; } break;      \
+  }
+
+// this thread's group's bits of a warp ballot
+template <int G>
+__device__ __forceinline__ unsigned group_bits(unsigned ballot) {
+  if constexpr (G == 32) return ballot;
+  else return (ballot >> ((threadIdx.x & 31) & ~(G - 1))) & ((1u << G) - 1u);
+}
+
+template <int G>
 __global__ void k_diag(int32_t n, const int32_t *rp, const int32_t *col, const double *val, double *d) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = gid / G;
+  const int gl = (int)(gid % G);
   double v = 0.0;
-  for (int32_t k = rp[i]; k < rp[i + 1]; k++)
-    if (col[k] == i) { v = val[k]; break; }
-  d[i] = v;
+  bool f = false;
+  if (i < n)
+    for (int32_t k = rp[i] + gl; k < rp[i + 1]; k += G)
+      if (col[k] == i) { v = val[k]; f = true; }
+  // the lane holding the diagonal (columns of a row are distinct)
+  const unsigned m = group_bits<G>(__ballot_sync(0xffffffffu, f));
+  const int base = (threadIdx.x & 31) & ~(G - 1);
+  const double dv = __shfl_sync(0xffffffffu, v, m ? base + __ffs(m) - 1 : base);
+  if (i < n && gl == 0) d[i] = m ? dv : 0.0;
 }
 
 // rows of systems that do not coarsen at this level get no strong entries
+template <int G>
 __global__ void k_strength(int32_t n, const int32_t *rp, const int32_t *col, const double *val, const double *diag,
                            const int32_t *seg, const uint8_t *seg_act, double theta, int32_t nfun,
                            uint8_t *strong) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int32_t s = rp[i], e = rp[i + 1];
-  if (!seg_act[seg[i]]) {
-    for (int32_t k = s; k < e; k++) strong[k] = 0;
-    return;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i64 = gid / G;
+  const int gl = (int)(gid % G);
+  const bool ok = i64 < n;
+  const int32_t i = ok ? (int32_t)i64 : 0;
+  int32_t s = 0, e = 0;
+  bool act = false;
+  double sg = 1.0;
+  if (ok) {
+    s = rp[i];
+    e = rp[i + 1];
+    act = seg_act[seg[i]] != 0;
+    sg = diag[i] < 0.0 ? -1.0 : 1.0;
   }
-  const double sg = diag[i] < 0.0 ? -1.0 : 1.0;
   double mx = 0.0;
-  for (int32_t k = s; k < e; k++) {
-    const int32_t j = col[k];
-    if (j == i || (j % nfun) != (i % nfun)) continue;
-    const double v = -(sg * val[k]);
-    if (v > mx) mx = v;
+  if (act)
+    for (int32_t k = s + gl; k < e; k += G) {
+      const int32_t j = col[k];
+      if (j == i || (j % nfun) != (i % nfun)) continue;
+      const double v = -(sg * val[k]);
+      if (v > mx) mx = v;
+    }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, mx, o, G);
+    if (w > mx) mx = w;
   }
+  if (!ok) return;
   const double thr = theta * mx;
-  for (int32_t k = s; k < e; k++) {
-    const int32_t j = col[k];
+  for (int32_t k = s + gl; k < e; k += G) {
     uint8_t st = 0;
-    if (j != i && (j % nfun) == (i % nfun) && mx > 0.0) st = (-(sg * val[k]) >= thr) ? 1 : 0;
+    if (act) {
+      const int32_t j = col[k];
+      if (j != i && (j % nfun) == (i % nfun) && mx > 0.0) st = (-(sg * val[k]) >= thr) ? 1 : 0;
+    }
     strong[k] = st;
   }
 }
 
+template <int G>
 __global__ void k_lambda(int32_t n, const int32_t *rp, const int32_t *col, const uint8_t *strong, int32_t *lam) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = gid / G;
   if (i >= n) return;
-  for (int32_t k = rp[i]; k < rp[i + 1]; k++)
+  for (int32_t k = rp[i] + (int)(gid % G); k < rp[i + 1]; k += G)
     if (strong[k]) atomicAdd(&lam[col[k]], 1);
 }
 
@@ -99,12 +147,16 @@ __global__ void k_pmis_init(int32_t n, const int32_t *lam, const int32_t *seg, c
 }
 
 // every strong edge between two undecided points marks its loser
+template <int G>
 __global__ void k_pmis_losers(int32_t n, const int32_t *rp, const int32_t *col, const uint8_t *strong,
                               const uint64_t *key, const int8_t *cf, uint8_t *notmax) {
-  int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n || cf[j] != 0) return;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j64 = gid / G;
+  if (j64 >= n) return;
+  const int32_t j = (int32_t)j64;
+  if (cf[j] != 0) return;
   const uint64_t kj = key[j];
-  for (int32_t q = rp[j]; q < rp[j + 1]; q++) {
+  for (int32_t q = rp[j] + (int)(gid % G); q < rp[j + 1]; q += G) {
     if (!strong[q]) continue;
     const int32_t k = col[q];
     if (cf[k] != 0) continue;
@@ -122,16 +174,23 @@ __global__ void k_pmis_select(int32_t n, uint8_t *notmax, int8_t *cf) {
 }
 
 // undecided points strongly depending on a C point become F; count the rest
+// (one atomic per warp)
+template <int G>
 __global__ void k_pmis_fmark(int32_t n, const int32_t *rp, const int32_t *col, const uint8_t *strong, int8_t *cf,
                              int32_t *left) {
-  int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n || cf[j] != 0) return;
-  for (int32_t q = rp[j]; q < rp[j + 1]; q++)
-    if (strong[q] && cf[col[q]] == 1) {
-      cf[j] = -1;
-      return;
-    }
-  atomicAdd(left, 1);
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j64 = gid / G;
+  const int gl = (int)(gid % G);
+  const int32_t j = j64 < n ? (int32_t)j64 : 0;
+  const bool und = j64 < n && cf[j] == 0;
+  bool hit = false;
+  if (und)
+    for (int32_t q = rp[j] + gl; q < rp[j + 1]; q += G)
+      if (strong[q] && cf[col[q]] == 1) { hit = true; break; }
+  const bool anyhit = group_bits<G>(__ballot_sync(0xffffffffu, hit)) != 0;
+  if (und && gl == 0 && anyhit) cf[j] = -1;
+  const unsigned rest = __ballot_sync(0xffffffffu, und && gl == 0 && !anyhit);
+  if ((threadIdx.x & 31) == 0 && rest) atomicAdd(left, __popc(rest));
 }
 
 __global__ void k_seg_count_c(int32_t n, const int8_t *cf, const int32_t *seg, int32_t *cnt) {
@@ -459,20 +518,6 @@ __global__ void k_interp_cap(int32_t n, const int32_t *__restrict__ rp, const in
   }
   const unsigned ws = __reduce_add_sync(0xffffffffu, (unsigned)c);
   if ((threadIdx.x & 31) == 0 && ws) atomicAdd(captot, (unsigned long long)ws);
-}
-
-// Moves row i's cnt[i] entries from the scratch rows at toff[i] to the
-// interpolation matrix's rows at prp[i].
-__global__ void k_interp_compact(int32_t n, const int32_t *__restrict__ toff, const int32_t *__restrict__ prp,
-                                 const int32_t *__restrict__ tcol, const double *__restrict__ tval,
-                                 int32_t *__restrict__ pcol, double *__restrict__ pval) {
-  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int32_t a = toff[i], b = prp[i], c = prp[i + 1] - b;
-  for (int32_t t = 0; t < c; t++) {
-    pcol[b + t] = tcol[a + t];
-    pval[b + t] = tval[a + t];
-  }
 }
 
 // SIZE = true: prp[i] = the size of Chat_i (1 for a C row), an upper bound
@@ -1099,38 +1144,62 @@ __global__ void k_to_f32(int64_t n, const double *a, float *b, int32_t *range_er
 // uses its inverse). hs_mid[i] is where row i's second part begins.
 // With B unknowns per point the whole diagonal block of the row's point is
 // left out (the point-block smoother uses its inverse).
-template <int B>
+// G lanes per row (rows of a chunk in a loop of the CTA; the lanes of a
+// group stay together, groups of one warp may part at a chunk's end).
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  if constexpr (G == 32) return 0xffffffffu;
+  else return ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+}
+
+template <int B, int G>
 __global__ void k_hs_count(const int32_t *cr, const int32_t *rp, const int32_t *col, int32_t *cnt) {
   const int32_t k = blockIdx.x;
   const int32_t r0 = cr[2 * k], r1 = cr[2 * k + 1];
-  for (int32_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+  const int gl = threadIdx.x % G;
+  const unsigned gm = group_mask<G>();
+  for (int32_t i = r0 + (int32_t)(threadIdx.x / G); i < r1; i += blockDim.x / G) {
     int32_t c = 0;
-    for (int32_t q = rp[i]; q < rp[i + 1]; q++) c += col[q] / B != i / B;
-    cnt[i] = c;
+    for (int32_t q = rp[i] + gl; q < rp[i + 1]; q += G) c += col[q] / B != i / B;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) c += __shfl_xor_sync(gm, c, o, G);
+    if (gl == 0) cnt[i] = c;
   }
 }
 
-template <typename T, int B>
+// Each row's in-chunk entries (less its point's own block), then its
+// out-of-chunk entries, each part in the row's order: a group's lanes take G
+// entries at a time and place the kept ones by their rank among the kept.
+template <typename T, int B, int G>
 __global__ void k_hs_fill(const int32_t *cr, const int32_t *rp, const int32_t *col, const double *val,
                           const int32_t *hrp, int32_t *hmid, int32_t *hcol, T *hval) {
   const int32_t k = blockIdx.x;
   const int32_t r0 = cr[2 * k], r1 = cr[2 * k + 1];
-  for (int32_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+  const int gl = threadIdx.x % G;
+  const unsigned gm = group_mask<G>();
+  const unsigned below = (1u << gl) - 1u;
+  for (int32_t i = r0 + (int32_t)(threadIdx.x / G); i < r1; i += blockDim.x / G) {
     int32_t pos = hrp[i];
-    for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
-      const int32_t j = col[q];
-      if (j / B != i / B && j >= r0 && j < r1) {
-        hcol[pos] = j - r0;
-        hval[pos++] = (T)val[q];
+    const int32_t qs = rp[i], qe = rp[i + 1];
+    for (int pass = 0; pass < 2; pass++) {
+      for (int32_t q0 = qs; q0 < qe; q0 += G) {
+        const int32_t q = q0 + gl;
+        int32_t j = 0;
+        bool keep = false;
+        if (q < qe) {
+          j = col[q];
+          const bool inside = j >= r0 && j < r1;
+          keep = pass == 0 ? (inside && j / B != i / B) : !inside;
+        }
+        const unsigned m = group_bits<G>(__ballot_sync(gm, keep));
+        if (keep) {
+          const int32_t p = pos + __popc(m & below);
+          hcol[p] = pass == 0 ? j - r0 : j;
+          hval[p] = (T)val[q];
+        }
+        pos += __popc(m);
       }
-    }
-    hmid[i] = pos;
-    for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
-      const int32_t j = col[q];
-      if (j < r0 || j >= r1) {
-        hcol[pos] = j;
-        hval[pos++] = (T)val[q];
-      }
+      if (pass == 0 && gl == 0) hmid[i] = pos;
     }
   }
 }
@@ -1648,11 +1717,13 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       if (B > 1) RS_TRY(sc.get(&cfp, (size_t)np + 1));
       else cfp = L.cf;
       const unsigned g = grid_for(np);
-      RS_COUNTED k_diag<<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, M.val, diag);
-      RS_COUNTED k_strength<<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, M.val, diag, pseg, dact, prm.theta, 1,
-                                                 strong);
+      const int rg = row_lanes(np, M.nnz);
+      const unsigned gg = grid_for((int64_t)np * rg);
+      RS_ROWG_SWITCH(rg, RS_COUNTED k_diag<G_><<<gg, kBlock, 0, s>>>(np, M.rowptr, M.col, M.val, diag);
+                     RS_COUNTED k_strength<G_><<<gg, kBlock, 0, s>>>(np, M.rowptr, M.col, M.val, diag, pseg, dact,
+                                                                     prm.theta, 1, strong));
       RS_CHECK_CUDA(cudaMemsetAsync(lam, 0, sizeof(int32_t) * np, s));
-      RS_COUNTED k_lambda<<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, lam);
+      RS_ROWG_SWITCH(rg, RS_COUNTED k_lambda<G_><<<gg, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, lam));
       RS_COUNTED k_pmis_init<<<g, kBlock, 0, s>>>(np, lam, pseg, dpseg_off, dact, prm.seed, l, key, cfp);
       RS_CHECK_CUDA(cudaMemsetAsync(notmax, 0, (size_t)np, s));
       int32_t hleft = 1, rounds = 0;
@@ -1661,9 +1732,11 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         // a few rounds between host checks; a round with nothing undecided does nothing
         for (int r = 0; r < 3; r++) {
           RS_CHECK_CUDA(cudaMemsetAsync(left, 0, sizeof(int32_t), s));
-          RS_COUNTED k_pmis_losers<<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, key, cfp, notmax);
+          RS_ROWG_SWITCH(rg, RS_COUNTED k_pmis_losers<G_><<<gg, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, key,
+                                                                                cfp, notmax));
           RS_COUNTED k_pmis_select<<<g, kBlock, 0, s>>>(np, notmax, cfp);
-          RS_COUNTED k_pmis_fmark<<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, cfp, left);
+          RS_ROWG_SWITCH(rg, RS_COUNTED k_pmis_fmark<G_><<<gg, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, cfp,
+                                                                               left));
         }
         RS_TRY(sync_copy(&hleft, left, sizeof(int32_t), s));
       }
@@ -1702,9 +1775,11 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
           // the diagonal and strength of F: those PMIS used when F is the
           // coarsened matrix itself and no system stopped since, else formed
           if (B > 1 || dropped) {
-            RS_COUNTED k_diag<<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag);
-            RS_COUNTED k_strength<<<gf, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, pseg, dact, prm.theta, 1,
-                                                        strong);
+            const int fg = row_lanes(F.n, F.nnz);
+            const unsigned gfg = grid_for((int64_t)F.n * fg);
+            RS_ROWG_SWITCH(fg, RS_COUNTED k_diag<G_><<<gfg, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag);
+                           RS_COUNTED k_strength<G_><<<gfg, kBlock, 0, s>>>(F.n, F.rowptr, F.col, F.val, diag, pseg,
+                                                                            dact, prm.theta, 1, strong));
           }
           Pf.n = F.n;
           Pf.m = nc;
@@ -1815,9 +1890,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
                 Pf.nnz = pnnz;
                 RS_TRY(dalloc_n(&Pf.col, (size_t)pnnz + 1, s));
                 RS_TRY(dalloc_n(&Pf.val, (size_t)pnnz + 1, s));
-                RS_COUNTED k_interp_compact<<<gf, kBlock, 0, s>>>(F.n, toff, Pf.rowptr, tcol, tval, Pf.col, Pf.val);
-                RS_CHECK_CUDA(cudaGetLastError());
-                return 0;
+                return copy_rows(F.n, pnnz, toff, Pf.rowptr, tcol, tval, Pf.col, Pf.val, s);
               }
             }
             int32_t nbig = 0;
@@ -1868,8 +1941,7 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
             Pf.nnz = pnnz;
             RS_TRY(dalloc_n(&Pf.col, (size_t)pnnz + 1, s));
             RS_TRY(dalloc_n(&Pf.val, (size_t)pnnz + 1, s));
-            if (F.n > 0)
-              RS_COUNTED k_interp_compact<<<gf, kBlock, 0, s>>>(F.n, toff, Pf.rowptr, tcol, tval, Pf.col, Pf.val);
+            RS_TRY(copy_rows(F.n, pnnz, toff, Pf.rowptr, tcol, tval, Pf.col, Pf.val, s));
           }
           RS_CHECK_CUDA(cudaGetLastError());
           return 0;
@@ -2056,8 +2128,9 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       RS_TRY(dalloc_n(&Lc.hs_rp, (size_t)n + 1, s));
       RS_TRY(dalloc_n(&Lc.hs_mid, (size_t)n, s));
       RS_CHECK_CUDA(cudaMemsetAsync(Lc.hs_rp, 0, sizeof(int32_t) * ((size_t)n + 1), s));
-      RS_COUNTED (B == 1 ? k_hs_count<1> : k_hs_count<2>)<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr,
-                                                                                   Lc.A.col, Lc.hs_rp);
+      const int hg = row_lanes(n, Lc.A.nnz);
+      RS_ROWG_SWITCH(hg, RS_COUNTED (B == 1 ? k_hs_count<1, G_> : k_hs_count<2, G_>)<<<Lc.nchunk, 256, 0, s>>>(
+                             Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.hs_rp));
       int32_t tot = 0;
       RS_TRY(exclusive_scan(Lc.hs_rp, Lc.hs_rp, n, s, &tot));
       Lc.hs_nnz = tot;
@@ -2071,12 +2144,16 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
       RS_TRY(dalloc_n(&Lc.hs_col, (size_t)tot + 1, s));
       if (H.precision == RS_PREC_FP32) {
         RS_TRY(dalloc_n(&Lc.hs_valf, (size_t)tot + 1, s));
-        RS_COUNTED (B == 1 ? k_hs_fill<float, 1> : k_hs_fill<float, 2>)<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.A.val,
-                                                              Lc.hs_rp, Lc.hs_mid, Lc.hs_col, Lc.hs_valf);
+        RS_ROWG_SWITCH(hg, RS_COUNTED (B == 1 ? k_hs_fill<float, 1, G_> : k_hs_fill<float, 2, G_>)<<<Lc.nchunk, 256,
+                                                                                               0, s>>>(
+                               Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.A.val, Lc.hs_rp, Lc.hs_mid, Lc.hs_col,
+                               Lc.hs_valf));
       } else {
         RS_TRY(dalloc_n(&Lc.hs_val, (size_t)tot + 1, s));
-        RS_COUNTED (B == 1 ? k_hs_fill<double, 1> : k_hs_fill<double, 2>)<<<Lc.nchunk, 256, 0, s>>>(Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.A.val,
-                                                               Lc.hs_rp, Lc.hs_mid, Lc.hs_col, Lc.hs_val);
+        RS_ROWG_SWITCH(hg, RS_COUNTED (B == 1 ? k_hs_fill<double, 1, G_> : k_hs_fill<double, 2, G_>)<<<Lc.nchunk,
+                                                                                                 256, 0, s>>>(
+                               Lc.chunk_row0, Lc.A.rowptr, Lc.A.col, Lc.A.val, Lc.hs_rp, Lc.hs_mid, Lc.hs_col,
+                               Lc.hs_val));
       }
       RS_CHECK_CUDA(cudaGetLastError());
     }
@@ -2100,7 +2177,6 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
   RS_TRY(sync_copy(&hrange, f32err, sizeof(int32_t), s));
   if (hrange)
     return fail(RS_ESETUP, "hierarchy values lie beyond the FP32 range; use an FP64 hierarchy (RS_PREC_FP64)");
-  RS_TRY(amg_tail_setup(H, s));
   return amg_tune_smoother(H, s);
 }
 
@@ -2144,9 +2220,6 @@ void amg_free(Hier &H, cudaStream_t s) {
   for (Level &L : H.L) level_free(L, s);
   H.L.clear();
   H.nlev = 0;
-  dfree(H.tail_d, s);
-  H.tail_d = nullptr;
-  H.tail_start = -1;
 }
 
 }  // namespace rs

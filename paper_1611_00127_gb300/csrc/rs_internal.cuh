@@ -150,6 +150,10 @@ int simple_schur(const DCsr &App, const DCsr &Aps, const DCsr &Asp, const DCsr &
                  cudaStream_t s);
 int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s);
 int transpose(const DCsr &A, DCsr &T, cudaStream_t s);
+// Moves row i's crp[i+1] - crp[i] entries from offset toff[i] of (tcol, tval)
+// to offset crp[i] of (ccol, cval); nnz = crp[n] picks the lanes per row.
+int copy_rows(int32_t n, int64_t nnz, const int32_t *toff, const int32_t *crp, const int32_t *tcol,
+              const double *tval, int32_t *ccol, double *cval, cudaStream_t s);
 
 // ------------------------------------------------------------------ AMG
 struct Level {
@@ -202,26 +206,6 @@ struct Level {
   void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
 };
 
-// One level of the coarse tail (levels walked by a single cluster launch):
-// device pointers of the level's operators and vectors, both precisions.
-struct TailLevel {
-  int32_t n = 0, nchunk = 0, ncol = 0, nR = 0, nP = 0;
-  const int32_t *rp = nullptr, *col = nullptr;
-  const double *val = nullptr;
-  const float *valf = nullptr;
-  const int32_t *hrp = nullptr, *hmid = nullptr, *hcol = nullptr;
-  const double *hval = nullptr;
-  const float *hvalf = nullptr;
-  const double *dinv = nullptr, *binv = nullptr;
-  const float *dinvf = nullptr, *binvf = nullptr;
-  const int32_t *chunk_row0 = nullptr, *chunk_coff = nullptr, *chunk_rows = nullptr;
-  const int32_t *Rrp = nullptr, *Rcol = nullptr, *Prp = nullptr, *Pcol = nullptr;
-  const double *Rval = nullptr, *Pval = nullptr;
-  const float *Rvalf = nullptr, *Pvalf = nullptr;
-  void *x = nullptr, *x2 = nullptr, *b = nullptr, *r = nullptr;
-  const double *cinv = nullptr;    // coarsest level: dense inverse, row-major
-};
-
 struct Hier {
   rs_amg_params prm;
   int32_t nlev = 0;
@@ -233,9 +217,6 @@ struct Hier {
   // live). A V-cycle writes zeros for the rows of a system whose flag is 0
   // instead of computing them -- FGMRES retires converged systems this way.
   const uint8_t *active = nullptr;
-  // coarse tail: levels tail_start.. run as one cluster launch (-1: none)
-  int32_t tail_start = -1;
-  TailLevel *tail_d = nullptr;
 };
 
 int check_amg_params(const rs_amg_params &a);
@@ -250,10 +231,6 @@ int amg_level_xfer(const Hier &H, int32_t l, int which, int reps, double *bytes_
 // smoothed level's own vectors and stores the fastest in Level::hgs_lpr
 // (decisions cached per level shape). Not inside stream capture.
 int amg_tune_smoother(Hier &H, cudaStream_t s);
-// Chooses the coarse tail (the levels below prm.tail_rows rows, from the
-// first such level with a coarser one down to the dense coarsest level) and
-// uploads its descriptors; single-system hybrid-smoother hierarchies only.
-int amg_tail_setup(Hier &H, cudaStream_t s);
 // RS_ETIMEOUT (and clears the flag) if a smoother CTA gave up waiting for its
 // staging copies since the last call; synchronises the stream.
 int vcycle_wait_status(cudaStream_t s);

@@ -6,6 +6,8 @@
 // taken on the results (strength, C/F splitting) are reproduced exactly:
 // sums run in ascending inner index, each product is rounded before it is
 // added, and the first term of a sum is the rounded product itself.
+#include <type_traits>
+
 #include "rs_internal.cuh"
 
 namespace rs {
@@ -474,18 +476,38 @@ static int spgemm_pass(const DCsr &A, const DCsr &B, DCsr &C, const uint8_t *bin
   return 0;
 }
 
-// Moves row i's cnt[i] entries from the reserved rows at toff[i] to C's rows
-// at crp[i].
-__global__ void k_rows_compact(int32_t n, const int32_t *__restrict__ toff, const int32_t *__restrict__ crp,
-                               const int32_t *__restrict__ tcol, const double *__restrict__ tval,
-                               int32_t *__restrict__ ccol, double *__restrict__ cval) {
-  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+// Moves row i's crp[i+1] - crp[i] entries from toff[i] to crp[i], G lanes
+// per row: consecutive lanes take consecutive entries, so each group's loads
+// and stores are contiguous.
+template <int G>
+__global__ void k_copy_rows(int32_t n, const int32_t *__restrict__ toff, const int32_t *__restrict__ crp,
+                            const int32_t *__restrict__ tcol, const double *__restrict__ tval,
+                            int32_t *__restrict__ ccol, double *__restrict__ cval) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = gid / G;
   if (i >= n) return;
-  const int32_t a = toff[i], b = crp[i], c = crp[i + 1] - b;
-  for (int32_t t = 0; t < c; t++) {
-    ccol[b + t] = tcol[a + t];
-    cval[b + t] = tval[a + t];
+  const int gl = (int)(gid % G);
+  const int32_t a = __ldg(toff + i), b = __ldg(crp + i), c = __ldg(crp + i + 1) - b;
+  for (int32_t t = gl; t < c; t += G) {
+    ccol[b + t] = __ldg(tcol + a + t);
+    cval[b + t] = __ldg(tval + a + t);
   }
+}
+
+int copy_rows(int32_t n, int64_t nnz, const int32_t *toff, const int32_t *crp, const int32_t *tcol,
+              const double *tval, int32_t *ccol, double *cval, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const double avg = (double)nnz / n;
+  const int G = avg <= 6.0 ? 4 : (avg <= 16.0 ? 8 : (avg <= 40.0 ? 16 : 32));
+  const unsigned grid = (unsigned)(((int64_t)n * G + kBlock - 1) / kBlock);
+  switch (G) {
+    case 4: RS_COUNTED k_copy_rows<4><<<grid, kBlock, 0, s>>>(n, toff, crp, tcol, tval, ccol, cval); break;
+    case 8: RS_COUNTED k_copy_rows<8><<<grid, kBlock, 0, s>>>(n, toff, crp, tcol, tval, ccol, cval); break;
+    case 16: RS_COUNTED k_copy_rows<16><<<grid, kBlock, 0, s>>>(n, toff, crp, tcol, tval, ccol, cval); break;
+    default: RS_COUNTED k_copy_rows<32><<<grid, kBlock, 0, s>>>(n, toff, crp, tcol, tval, ccol, cval); break;
+  }
+  RS_CHECK_CUDA(cudaGetLastError());
+  return 0;
 }
 
 // C = A B. When the rows' worst cases (each row's product count, at most a
@@ -555,9 +577,7 @@ int spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
       C.nnz = tot;
       RS_TRY(dalloc_n(&C.col, (size_t)tot, s));
       RS_TRY(dalloc_n(&C.val, (size_t)tot, s));
-      RS_COUNTED k_rows_compact<<<grid_for(A.n), kBlock, 0, s>>>(A.n, toff, C.rowptr, tcol, tval, C.col, C.val);
-      RS_CHECK_CUDA(cudaGetLastError());
-      return 0;
+      return copy_rows(A.n, tot, toff, C.rowptr, tcol, tval, C.col, C.val, s);
     }
     RS_TRY(spgemm_pass<false>(A, B, C, bin, bincnt, cursor, rows, err, defer, s));
   }
@@ -597,22 +617,60 @@ __global__ void k_transpose_fill(int32_t n, const int32_t *rp, const int32_t *co
   }
 }
 
-// Sort each row by column (rows of a transpose are short).
-__global__ void k_row_sort(int32_t n, const int32_t *rp, int32_t *col, double *val) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int32_t s = rp[i], e = rp[i + 1];
-  for (int32_t a = s + 1; a < e; a++) {
-    const int32_t c = col[a];
-    const double v = val[a];
-    int32_t b = a - 1;
-    while (b >= s && col[b] > c) {
-      col[b + 1] = col[b];
-      val[b + 1] = val[b];
-      b--;
+// Sorts each row by column (the columns of a row are distinct), a warp per
+// row. A row of up to 32 * kSortE entries is held in registers (kSortE per
+// lane); each entry's rank, the number of smaller columns in the row, is
+// counted against every entry by shuffles, and the entry is stored at its
+// rank. A longer row is insertion-sorted by lane 0.
+constexpr int kSortE = 8;
+__global__ void k_row_sort(int32_t n, const int32_t *__restrict__ rp, int32_t *col, double *val) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;   // whole warps
+  const int32_t s = rp[w], e = rp[w + 1], len = e - s;
+  if (len <= 1) return;
+  if (len > 32 * kSortE) {
+    if (lane != 0) return;
+    for (int32_t a = s + 1; a < e; a++) {
+      const int32_t c = col[a];
+      const double v = val[a];
+      int32_t b = a - 1;
+      while (b >= s && col[b] > c) {
+        col[b + 1] = col[b];
+        val[b + 1] = val[b];
+        b--;
+      }
+      col[b + 1] = c;
+      val[b + 1] = v;
     }
-    col[b + 1] = c;
-    val[b + 1] = v;
+    return;
+  }
+  int32_t key[kSortE], rank[kSortE];
+  double v[kSortE];
+#pragma unroll
+  for (int u = 0; u < kSortE; u++) {
+    const int32_t t = u * 32 + lane;
+    key[u] = t < len ? col[s + t] : INT32_MAX;
+    v[u] = t < len ? val[s + t] : 0.0;
+    rank[u] = 0;
+  }
+#pragma unroll
+  for (int u2 = 0; u2 < kSortE; u2++) {
+    if (u2 * 32 >= len) break;   // warp-uniform
+    for (int src = 0; src < 32; src++) {
+      const int32_t k = __shfl_sync(0xffffffffu, key[u2], src);
+#pragma unroll
+      for (int u = 0; u < kSortE; u++) rank[u] += k < key[u];
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < kSortE; u++) {
+    const int32_t t = u * 32 + lane;
+    if (t < len) {
+      col[s + rank[u]] = key[u];
+      val[s + rank[u]] = v[u];
+    }
   }
 }
 
@@ -631,7 +689,7 @@ int transpose(const DCsr &A, DCsr &T, cudaStream_t s) {
   RS_TRY(exclusive_scan(T.rowptr, T.rowptr, A.m, s, nullptr));
   RS_CHECK_CUDA(cudaMemcpyAsync(fill, T.rowptr, sizeof(int32_t) * ((size_t)A.m + 1), cudaMemcpyDeviceToDevice, s));
   if (A.n > 0) RS_COUNTED k_transpose_fill<<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, fill, T.col, T.val);
-  if (A.m > 0) RS_COUNTED k_row_sort<<<grid_for(A.m), kBlock, 0, s>>>(A.m, T.rowptr, T.col, T.val);
+  if (A.m > 0) RS_COUNTED k_row_sort<<<grid_for((int64_t)A.m * 32), kBlock, 0, s>>>(A.m, T.rowptr, T.col, T.val);
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }
@@ -654,46 +712,102 @@ __global__ void k_scale_cols(int32_t nnz, const int32_t *col, const double *val,
   out[k] = dk != 0.0 ? val[k] / dk : 0.0;
 }
 
+// position of column v in the sorted columns a[0..m), or -1
+__device__ __forceinline__ int32_t find_col(const int32_t *a, int32_t m, int32_t v) {
+  int32_t lo = 0, hi = m - 1;
+  while (lo <= hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    const int32_t x = a[mid];
+    if (x == v) return mid;
+    if (x < v) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
 // C = A - B on the union pattern; an entry missing from A counts as 0.0
-// (so the result is 0.0 - b), one missing from B leaves a.
-template <bool FILL>
+// (so the result is 0.0 - b), one missing from B leaves a. G lanes per row:
+// the count pass looks A's columns up in B's row; the fill writes B's row
+// lane-parallel when A's pattern lies inside it (the union is then B's
+// pattern), else the group's first lane merges the two rows.
+template <bool FILL, int G>
 __global__ void k_sub(int32_t n, const int32_t *arp, const int32_t *acol, const double *aval, const int32_t *brp,
                       const int32_t *bcol, const double *bval, int32_t *crp, int32_t *ccol, double *cval) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int32_t p = arp[i], pe = arp[i + 1], q = brp[i], qe = brp[i + 1], o = FILL ? crp[i] : 0, c = 0;
-  while (p < pe || q < qe) {
-    const int32_t ja = p < pe ? acol[p] : 0x7fffffff, jb = q < qe ? bcol[q] : 0x7fffffff;
-    if (ja == jb) {
-      if (FILL) { ccol[o + c] = ja; cval[o + c] = aval[p] - bval[q]; }
-      p++; q++;
-    } else if (ja < jb) {
-      if (FILL) { ccol[o + c] = ja; cval[o + c] = aval[p]; }
-      p++;
-    } else {
-      if (FILL) { ccol[o + c] = jb; cval[o + c] = 0.0 - bval[q]; }
-      q++;
-    }
-    c++;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = gid / G;
+  const int gl = (int)(gid % G);
+  const bool ok = i < n;
+  const int32_t p = ok ? arp[i] : 0, na = ok ? arp[i + 1] - p : 0;
+  const int32_t q = ok ? brp[i] : 0, nb = ok ? brp[i + 1] - q : 0;
+  if (!FILL) {
+    // the union's size: B's entries and A's entries missing from B
+    int32_t extra = 0;
+    for (int32_t t = gl; t < na; t += G) extra += find_col(bcol + q, nb, acol[p + t]) < 0;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) extra += __shfl_xor_sync(0xffffffffu, extra, o, G);
+    if (ok && gl == 0) crp[i] = nb + extra;
+    return;
   }
-  if (!FILL) crp[i] = c;
+  if (!ok) return;
+  const int32_t o = crp[i], c = crp[i + 1] - o;
+  if (c == nb) {
+    // A's pattern inside B's (the usual case): the union is B's row
+    for (int32_t t = gl; t < nb; t += G) {
+      const int32_t j = bcol[q + t];
+      const int32_t pa = find_col(acol + p, na, j);
+      ccol[o + t] = j;
+      cval[o + t] = (pa >= 0 ? aval[p + pa] : 0.0) - bval[q + t];
+    }
+    return;
+  }
+  if (gl != 0) return;
+  int32_t pp = p, pe = p + na, qq = q, qe = q + nb, k = 0;
+  while (pp < pe || qq < qe) {
+    const int32_t ja = pp < pe ? acol[pp] : 0x7fffffff, jb = qq < qe ? bcol[qq] : 0x7fffffff;
+    if (ja == jb) {
+      ccol[o + k] = ja;
+      cval[o + k] = aval[pp] - bval[qq];
+      pp++;
+      qq++;
+    } else if (ja < jb) {
+      ccol[o + k] = ja;
+      cval[o + k] = aval[pp];
+      pp++;
+    } else {
+      ccol[o + k] = jb;
+      cval[o + k] = 0.0 - bval[qq];
+      qq++;
+    }
+    k++;
+  }
 }
 
 int csr_sub(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
   C.n = A.n;
   C.m = A.m;
   RS_TRY(dalloc_n(&C.rowptr, (size_t)A.n + 1, s));
-  if (A.n > 0)
-    RS_COUNTED k_sub<false><<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
-                                                  nullptr, nullptr);
+  const double avg = A.n > 0 ? (double)B.nnz / A.n : 1.0;
+  const int G = avg <= 12.0 ? 8 : (avg <= 32.0 ? 16 : 32);
+  const unsigned grid = grid_for((int64_t)A.n * G);
+  auto launch = [&](auto fill) {
+    constexpr bool F = decltype(fill)::value;
+    if (G == 8)
+      RS_COUNTED k_sub<F, 8><<<grid, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
+                                                    C.col, C.val);
+    else if (G == 16)
+      RS_COUNTED k_sub<F, 16><<<grid, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
+                                                     C.col, C.val);
+    else
+      RS_COUNTED k_sub<F, 32><<<grid, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
+                                                     C.col, C.val);
+  };
+  if (A.n > 0) launch(std::false_type{});
   int32_t tot = 0;
   RS_TRY(exclusive_scan(C.rowptr, C.rowptr, A.n, s, &tot));
   C.nnz = tot;
   RS_TRY(dalloc_n(&C.col, (size_t)tot, s));
   RS_TRY(dalloc_n(&C.val, (size_t)tot, s));
-  if (A.n > 0)
-    RS_COUNTED k_sub<true><<<grid_for(A.n), kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, B.rowptr, B.col, B.val, C.rowptr,
-                                                 C.col, C.val);
+  if (A.n > 0) launch(std::true_type{});
   RS_CHECK_CUDA(cudaGetLastError());
   return 0;
 }

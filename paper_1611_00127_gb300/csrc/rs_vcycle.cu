@@ -777,301 +777,8 @@ static void smooth(const Hier &H, const Level &L, int sweeps, T *&cur, cudaStrea
 
 // One V-cycle on level l with zero initial guess; returns the buffer that
 // holds x_l.
-// ---------------------------------------------------------------- coarse tail
-// The levels below a few thousand rows cost as much per V-cycle as the fine
-// ones when each of their kernels is its own launch: every sweep and transfer
-// is latency (launch, staging, a __syncthreads per colour), not work. The
-// coarse tail runs them -- pre-sweeps, residual, restriction down to the dense
-// coarsest level, its solve, then prolongation and post-sweeps back up -- as
-// one launch of a single cluster of kTailCtas CTAs, a cluster barrier between
-// phases (hardware barrier; every thread runs the same phase sequence).
-// Each phase computes what the per-level kernels compute:
-//  - sweep: hybrid Gauss-Seidel on the level's packed operator, one warp per
-//    chunk (chunks of at most kTailChunk rows): the chunk's packed entries,
-//    start iterate and right-hand side less the couplings to other chunks
-//    staged in the warp's shared memory, the colours a __syncwarp apart;
-//    point mode solves each point's 2 x 2 block (a singular block keeps its
-//    values);
-//  - residual, restriction, prolongation: kTailLanes lanes per row;
-//  - coarsest level: x = A_c^{-1} b with the FP64 dense inverse.
-// Values written earlier in the launch are read with ld.global.cg (L2).
-constexpr int kTailThreads = 256;     // 8 warps per CTA
-constexpr int kTailCtas = 8;
-constexpr int kTailChunk = 64;        // longest chunk (rows) a warp sweeps
-constexpr int kTailStage = 768;       // packed entries of a chunk staged per warp
-constexpr int kTailMaxLevels = 24;
-constexpr int kTailLanes = 8;         // lanes per row of the tail's row loops
-
-template <typename T> __device__ __forceinline__ const T *tsel(const double *d, const float *f);
-template <> __device__ __forceinline__ const double *tsel<double>(const double *d, const float *) { return d; }
-template <> __device__ __forceinline__ const float *tsel<float>(const double *, const float *f) { return f; }
-
-// shared memory of one warp: staged packed entries (values, columns), the
-// chunk's start iterate and right-hand side, its row starts and split points
-template <typename T>
-__host__ __device__ constexpr size_t tail_warp_smem() {
-  return ((size_t)kTailStage * sizeof(T) + (size_t)kTailStage * sizeof(int32_t) + 2 * (size_t)kTailChunk * sizeof(T) +
-          (2 * (size_t)kTailChunk + 1) * sizeof(int32_t) + 15) & ~size_t(15);   // 16-byte multiple per warp
-}
-
-template <typename T, bool POINT>
-__device__ __forceinline__ void tail_sweep(const TailLevel &L, const T *xold, T *xnew, int gw, int nw, int lane,
-                                           unsigned char *ws) {
-  T *wv = reinterpret_cast<T *>(ws);
-  T *sx = wv + kTailStage;
-  T *sr = sx + kTailChunk;
-  int32_t *wc = reinterpret_cast<int32_t *>(sr + kTailChunk);
-  int32_t *lrp = wc + kTailStage;
-  int32_t *lmd = lrp + kTailChunk + 1;
-  const T *b = static_cast<const T *>(L.b);
-  const T *hv = tsel<T>(L.hval, L.hvalf);
-  const int32_t ncol = L.ncol;
-  for (int32_t k = gw; k < L.nchunk; k += nw) {
-    const int32_t r0 = __ldg(L.chunk_row0 + 2 * k), r1 = __ldg(L.chunk_row0 + 2 * k + 1), len = r1 - r0;
-    const int32_t p0 = __ldg(L.hrp + r0), np = __ldg(L.hrp + r1) - p0;
-    const bool staged = np <= kTailStage;
-    if (staged)
-      for (int32_t e = lane; e < np; e += 32) {
-        wv[e] = __ldg(hv + p0 + e);
-        wc[e] = __ldg(L.hcol + p0 + e);
-      }
-    for (int32_t i = lane; i <= len; i += 32) lrp[i] = __ldg(L.hrp + r0 + i) - p0;
-    for (int32_t i = lane; i < len; i += 32) {
-      lmd[i] = __ldg(L.hmid + r0 + i) - p0;
-      sx[i] = xold ? __ldcg(xold + r0 + i) : T(0);
-    }
-    __syncwarp();
-    const int32_t *pc = staged ? wc : L.hcol + p0;
-    const T *pv = staged ? wv : hv + p0;
-    for (int32_t i = lane; i < len; i += 32) {
-      T acc = __ldcg(b + r0 + i);
-      if (xold)
-        for (int32_t q = lmd[i]; q < lrp[i + 1]; q++) acc -= pv[q] * __ldcg(xold + pc[q]);
-      sr[i] = acc;
-    }
-    __syncwarp();
-    const int32_t *cof = L.chunk_coff + (int64_t)k * (ncol + 1);
-    for (int32_t c = 0; c < ncol; c++) {
-      const int32_t beg = __ldg(cof + c), end = __ldg(cof + c + 1);
-      for (int32_t pos = beg + lane; pos < end; pos += 32) {
-        if (!POINT) {
-          const int32_t li = __ldg(L.chunk_rows + r0 + pos);
-          T acc = sr[li];
-          for (int32_t q = lrp[li]; q < lmd[li]; q++) acc -= pv[q] * sx[pc[q]];
-          const T di = __ldg(tsel<T>(L.dinv, L.dinvf) + r0 + li);
-          if (di != T(0)) sx[li] = acc * di;
-        } else {
-          const int32_t li = __ldg(L.chunk_rows + r0 / 2 + pos);
-          T acc[2];
-#pragma unroll
-          for (int f = 0; f < 2; f++) {
-            const int32_t lr = 2 * li + f;
-            T a = sr[lr];
-            for (int32_t q = lrp[lr]; q < lmd[lr]; q++) a -= pv[q] * sx[pc[q]];
-            acc[f] = a;
-          }
-          const T *mi = tsel<T>(L.binv, L.binvf) + 4 * ((int64_t)r0 / 2 + li);
-          const T m0 = __ldg(mi), m1 = __ldg(mi + 1), m2 = __ldg(mi + 2), m3 = __ldg(mi + 3);
-          if (m0 != T(0) || m1 != T(0) || m2 != T(0) || m3 != T(0)) {
-            sx[2 * li] = m0 * acc[0] + m1 * acc[1];
-            sx[2 * li + 1] = m2 * acc[0] + m3 * acc[1];
-          }
-        }
-      }
-      __syncwarp();
-    }
-    for (int32_t i = lane; i < len; i += 32) xnew[r0 + i] = sx[i];
-    __syncwarp();
-  }
-}
-
-// y = b - A x (MODE 1), y = A x (MODE 0), y += A x (MODE 2); kTailLanes lanes
-// per row, rows taken in a loop whose trip count is uniform over each warp
-template <typename T, int MODE>
-__device__ __forceinline__ void tail_csr(int32_t n, const int32_t *rp, const int32_t *col, const T *val, const T *x,
-                                         const T *b, T *y, int64_t gt, int64_t nthr) {
-  const int64_t gid = gt / kTailLanes, ng = nthr / kTailLanes;
-  const int ln = (int)(gt % kTailLanes);
-  for (int64_t base = 0; base < n; base += ng) {
-    const int64_t i = base + gid;
-    T s = T(0);
-    if (i < n) {
-      const int32_t e = __ldg(rp + i + 1);
-      for (int32_t k = __ldg(rp + i) + ln; k < e; k += kTailLanes) s += __ldg(val + k) * __ldcg(x + __ldg(col + k));
-    }
-#pragma unroll
-    for (int o = kTailLanes / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, kTailLanes);
-    if (i < n && ln == 0) {
-      if (MODE == 0) y[i] = s;
-      else if (MODE == 1) y[i] = __ldcg(b + i) - s;
-      else y[i] = __ldcg(y + i) + s;
-    }
-  }
-}
-
-template <typename T, bool POINT>
-__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel *__restrict__ tl, int32_t nl, int32_t nu1,
-                                                        int32_t nu2) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int64_t gt = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x;
-  const int64_t nthr = (int64_t)cl.num_blocks() * blockDim.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = (int)cl.block_rank() * (blockDim.x >> 5) + warp, nw = (int)cl.num_blocks() * (blockDim.x >> 5);
-  extern __shared__ __align__(16) unsigned char tsm[];
-  unsigned char *ws = tsm + (size_t)warp * tail_warp_smem<T>();
-  T *cur[kTailMaxLevels];
-  for (int32_t l = 0; l + 1 < nl; l++) {
-    const TailLevel &L = tl[l];
-    T *xa = static_cast<T *>(L.x), *xb = static_cast<T *>(L.x2);
-    T *c = nullptr;
-    for (int32_t sw = 0; sw < nu1; sw++) {
-      T *out = (c == xa) ? xb : xa;
-      tail_sweep<T, POINT>(L, c, out, gw, nw, lane, ws);
-      cl.sync();
-      c = out;
-    }
-    if (!c) {
-      for (int64_t i = gt; i < L.n; i += nthr) xa[i] = T(0);
-      cl.sync();
-      c = xa;
-    }
-    cur[l] = c;
-    T *r = static_cast<T *>(L.r);
-    tail_csr<T, 1>(L.n, L.rp, L.col, tsel<T>(L.val, L.valf), c, static_cast<const T *>(L.b), r, gt, nthr);
-    cl.sync();
-    tail_csr<T, 0>(L.nR, L.Rrp, L.Rcol, tsel<T>(L.Rval, L.Rvalf), r, nullptr, static_cast<T *>(tl[l + 1].b), gt,
-                   nthr);
-    cl.sync();
-  }
-  {
-    // coarsest level: x = A_c^{-1} b, FP64, kTailLanes lanes per row
-    const TailLevel &L = tl[nl - 1];
-    T *x = static_cast<T *>(L.x);
-    const T *b = static_cast<const T *>(L.b);
-    const int64_t gid = gt / kTailLanes, ng = nthr / kTailLanes;
-    const int ln = (int)(gt % kTailLanes);
-    for (int64_t base = 0; base < L.n; base += ng) {
-      const int64_t i = base + gid;
-      double s = 0.0;
-      if (i < L.n) {
-        const double *a = L.cinv + i * (int64_t)L.n;
-        for (int32_t j = ln; j < L.n; j += kTailLanes) s = fma(__ldg(a + j), (double)__ldcg(b + j), s);
-      }
-#pragma unroll
-      for (int o = kTailLanes / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, kTailLanes);
-      if (i < L.n && ln == 0) x[i] = (T)s;
-    }
-    cl.sync();
-    cur[nl - 1] = x;
-  }
-  for (int32_t l = nl - 2; l >= 0; l--) {
-    const TailLevel &L = tl[l];
-    T *xa = static_cast<T *>(L.x), *xb = static_cast<T *>(L.x2);
-    T *c = cur[l];
-    tail_csr<T, 2>(L.nP, L.Prp, L.Pcol, tsel<T>(L.Pval, L.Pvalf), cur[l + 1], nullptr, c, gt, nthr);
-    cl.sync();
-    for (int32_t sw = 0; sw < nu2; sw++) {
-      T *out = (c == xa) ? xb : xa;
-      tail_sweep<T, POINT>(L, c, out, gw, nw, lane, ws);
-      cl.sync();
-      c = out;
-    }
-    cur[l] = c;
-  }
-}
-
-template <typename T, bool POINT>
-static void tail_attr() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(k_tail<T, POINT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(tail_warp_smem<T>() * (kTailThreads / 32)));
-  done = true;
-}
-
-// the buffer holding level l's iterate after `sweeps` sweeps from `c`
-static void *after_sweeps(const Level &L, void *c, int sweeps) {
-  for (int sw = 0; sw < sweeps; sw++) c = (c == L.x) ? L.x2 : L.x;
-  return c;
-}
-
-template <typename T>
-static T *tail_cycle(const Hier &H, cudaStream_t s) {
-  const int32_t t = H.tail_start, nl = H.nlev - t;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kTailCtas, 1, 1);
-  cfg.blockDim = dim3(kTailThreads, 1, 1);
-  cfg.dynamicSmemBytes = tail_warp_smem<T>() * (kTailThreads / 32);
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kTailCtas;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  count_launch();
-  const int32_t nu1 = H.prm.nu1, nu2 = H.prm.nu2;
-  ProfScope ps(kProfOther, 0.0, s);
-  if (H.L[t].nfun == 2) {
-    tail_attr<T, true>();
-    cudaLaunchKernelEx(&cfg, k_tail<T, true>, (const TailLevel *)H.tail_d, nl, nu1, nu2);
-  } else {
-    tail_attr<T, false>();
-    cudaLaunchKernelEx(&cfg, k_tail<T, false>, (const TailLevel *)H.tail_d, nl, nu1, nu2);
-  }
-  // the same buffer sequence as the kernel's: nu1 sweeps from zero (or the
-  // zero-filled x), then nu2 more after the prolongation
-  const Level &L = H.L[t];
-  void *c = nu1 > 0 ? after_sweeps(L, nullptr, nu1) : L.x;
-  return static_cast<T *>(after_sweeps(L, c, nu2));
-}
-
-int amg_tail_setup(Hier &H, cudaStream_t s) {
-  H.tail_start = -1;
-  const int32_t lim = H.prm.tail_rows;
-  if (lim <= 0 || H.nseg != 1 || H.prm.smoother != RS_SMOOTH_HYBRID || H.nlev < 2) return 0;
-  const Level &Lc = H.L[H.nlev - 1];
-  if (Lc.ncoarse_rows != Lc.A.n || !Lc.cinv || Lc.A.n > lim) return 0;
-  int32_t t = H.nlev - 1;
-  while (t > 0) {
-    const Level &L = H.L[t - 1];
-    if (L.A.n > lim || !L.P.rowptr || L.nsmooth != L.A.n || L.nchunk == 0 || L.chunk_c > kTailChunk ||
-        L.ncoarse_rows != 0)
-      break;
-    t--;
-  }
-  if (t > H.nlev - 2 || H.nlev - t > kTailMaxLevels) return 0;
-  std::vector<TailLevel> v(H.nlev - t);
-  for (int32_t l = t; l < H.nlev; l++) {
-    const Level &L = H.L[l];
-    TailLevel &d = v[l - t];
-    d.n = L.A.n;
-    d.rp = L.A.rowptr; d.col = L.A.col; d.val = L.A.val; d.valf = L.A.valf;
-    d.x = L.x; d.x2 = L.x2; d.b = L.b; d.r = L.r;
-    if (l + 1 < H.nlev) {
-      d.nchunk = L.nchunk; d.ncol = L.ncolour;
-      d.hrp = L.hs_rp; d.hmid = L.hs_mid; d.hcol = L.hs_col; d.hval = L.hs_val; d.hvalf = L.hs_valf;
-      d.dinv = L.dinv; d.dinvf = L.dinvf; d.binv = L.binv; d.binvf = L.binvf;
-      d.chunk_row0 = L.chunk_row0; d.chunk_coff = L.chunk_coff; d.chunk_rows = L.chunk_rows;
-      d.nR = L.R.n; d.Rrp = L.R.rowptr; d.Rcol = L.R.col; d.Rval = L.R.val; d.Rvalf = L.R.valf;
-      d.nP = L.P.n; d.Prp = L.P.rowptr; d.Pcol = L.P.col; d.Pval = L.P.val; d.Pvalf = L.P.valf;
-    } else {
-      d.cinv = L.cinv;
-    }
-  }
-  dfree(H.tail_d, s);
-  H.tail_d = nullptr;
-  RS_TRY(dalloc_n(&H.tail_d, v.size(), s));
-  RS_CHECK_CUDA(cudaMemcpyAsync(H.tail_d, v.data(), sizeof(TailLevel) * v.size(), cudaMemcpyHostToDevice, s));
-  RS_CHECK_CUDA(cudaStreamSynchronize(s));
-  H.tail_start = t;
-  return 0;
-}
-
 template <typename T>
 static T *cycle(const Hier &H, int32_t l, cudaStream_t s) {
-  if (l == H.tail_start) return tail_cycle<T>(H, s);
   const Level &L = H.L[l];
   T *cur = nullptr;
   smooth<T>(H, L, H.prm.nu1, cur, s);
@@ -1246,7 +953,6 @@ static int tune_xfer(Hier &H, int32_t l, int which, cudaStream_t s) {
 
 static int tune_transfers(Hier &H, cudaStream_t s) {
   for (int32_t l = 0; l + 1 < H.nlev; l++) {
-    if (H.tail_start >= 0 && l >= H.tail_start) break;   // run inside the coarse tail
     Level &L = H.L[l];
     if (!L.P.rowptr || L.A.n == 0) continue;
     for (int which = 0; which < 3; which++) {
@@ -1275,7 +981,6 @@ int amg_tune_smoother(Hier &H, cudaStream_t s) {
   RS_TRY(tune_transfers(H, s));
   if (H.prm.smoother != RS_SMOOTH_HYBRID) return 0;
   for (int32_t l = 0; l < H.nlev; l++) {
-    if (H.tail_start >= 0 && l >= H.tail_start) break;   // run inside the coarse tail
     Level &L = H.L[l];
     if (L.nsmooth == 0 || L.nchunk == 0 || L.A.n == 0) continue;
     const auto key = std::make_tuple(H.precision, (int)L.nfun, ilog2((double)L.nchunk),

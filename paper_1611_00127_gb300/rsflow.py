@@ -75,7 +75,7 @@ class AmgParamsC(C.Structure):
                 ("coarse_n", C.c_int32), ("max_dense", C.c_int32), ("smoother", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("interp", C.c_int32),
                 ("num_functions", C.c_int32), ("precision", C.c_int32), ("chunk", C.c_int32),
-                ("agg_levels", C.c_int32), ("chunk_coarse", C.c_int32), ("tail_rows", C.c_int32),
+                ("agg_levels", C.c_int32), ("chunk_coarse", C.c_int32),
                 ("restriction", C.c_int32)]
 
 
@@ -119,7 +119,6 @@ def _declare(L):
         "amg_level_copy": (C.c_int, [P, i32, P, P, P, P, P, P, P, P, P]),
         "amg_level_smooth": (C.c_int, [P, i32, i32, P, P]),
         "amg_level_transfer": (C.c_int, [P, i32, i32, i32, P, P]),
-        "amg_tail_level": (C.c_int, [P, P]),
         "ilu0_create": (C.c_int, [P, i32, P, P]),
         "ilu0_apply": (C.c_int, [P, P, P, P]),
         "ilu0_info": (C.c_int, [P, P, P, P]),
@@ -261,13 +260,12 @@ class AmgParams:
     chunk: int = 512
     agg_levels: int = 0
     chunk_coarse: int = 32
-    tail_rows: int = 0
     restriction: int = 0
 
     def c(self):
         return AmgParamsC(self.theta, self.seed, self.max_levels, self.coarse_n, self.max_dense,
                           self.smoother, self.nu1, self.nu2, self.interp, self.num_functions,
-                          self.precision, self.chunk, self.agg_levels, self.chunk_coarse, self.tail_rows,
+                          self.precision, self.chunk, self.agg_levels, self.chunk_coarse,
                           self.restriction)
 
 
@@ -383,12 +381,6 @@ class Amg:
         _check(lib().amg_level_info(self.h, l, C.byref(n), C.byref(nnz), C.byref(nnzp), C.byref(nc)),
                "amg_level_info")
         return n.value, nnz.value, nnzp.value, nc.value
-
-    def tail_level(self) -> int:
-        """First level run by the coarse-tail launch (-1: none)."""
-        t = C.c_int32()
-        _check(lib().amg_tail_level(self.h, C.byref(t)), "amg_tail_level")
-        return t.value
 
     def level_smooth(self, l: int, sweeps: int, stream=None) -> float:
         """Run smoother sweeps on level l's own vectors; returns bytes per sweep."""

@@ -63,8 +63,6 @@ def test_invalid_arguments_rejected_on_host():
     assert L.ilu0_info(None, None, None, None) == -1
     assert L.ilu0_factors(None, None, None) == -1
     assert L.ilu0_destroy(None) == 0
-    n = ctypes.c_int32()
-    assert L.amg_tail_level(None, ctypes.byref(n)) == -1
 
 
 def test_parameter_validation_on_host():
@@ -75,7 +73,7 @@ def test_parameter_validation_on_host():
     L = R.lib()
     csr = R.CsrC(0, 0, None, None, None, 0, None)
     bad = [(dict(agg_levels=9), b"agg_levels"), (dict(chunk_coarse=16), b"chunk_coarse"),
-           (dict(tail_rows=-1), b"tail_rows"), (dict(theta=2.0), b"theta"),
+           (dict(theta=2.0), b"theta"),
            (dict(num_functions=3), b"num_functions"), (dict(precision=5), b"precision"),
            (dict(nu1=17), b"sweep"), (dict(chunk=16), b"chunk"), (dict(restriction=2), b"restriction")]
     for kw, word in bad:
