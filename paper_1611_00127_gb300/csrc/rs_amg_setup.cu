@@ -926,7 +926,6 @@ __global__ void __launch_bounds__(256) k_chunk_colour(const int32_t *cr, const i
                                                       int32_t *colour, int32_t *maxc, int32_t *err) {
   __shared__ uint32_t adj[kCCMax * kCCWords];
   __shared__ int32_t cs[kCCMax];
-  __shared__ unsigned long long um[2];   // colours used by the current point's coloured neighbours
   const int32_t k = blockIdx.x;
   const int32_t r0 = cr[2 * k], nrow = cr[2 * k + 1] - r0, len = nrow / B;
   if (len > kCCMax) {
@@ -948,11 +947,12 @@ __global__ void __launch_bounds__(256) k_chunk_colour(const int32_t *cr, const i
   }
   __syncthreads();
   if (threadIdx.x < 32) {
+    // greedy in point order, one warp: lane w gathers the colours of the
+    // earlier neighbours in adjacency word w, the warp ORs them together,
+    // and every lane takes the lowest free colour
     const int lane = threadIdx.x;
     int32_t localmax = 0;
     for (int32_t li = 0; li < len; li++) {
-      if (lane == 0) { um[0] = 0ull; um[1] = 0ull; }
-      __syncwarp();
       unsigned long long u0 = 0ull, u1 = 0ull;
       const int32_t wl = li >> 5;
       if (lane < kCCWords && lane <= wl) {
@@ -965,19 +965,18 @@ __global__ void __launch_bounds__(256) k_chunk_colour(const int32_t *cr, const i
           if (c < 64) u0 |= 1ull << c; else u1 |= 1ull << (c - 64);
         }
       }
-      // only the lanes whose words hold coloured neighbours contribute
-      if (u0) atomicOr(&um[0], u0);
-      if (u1) atomicOr(&um[1], u1);
-      __syncwarp();
-      if (lane == 0) {
-        const unsigned long long m0 = um[0], m1 = um[1];
-        int32_t c;
-        if (~m0) c = __ffsll((long long)~m0) - 1;
-        else if (~m1) c = 64 + __ffsll((long long)~m1) - 1;
-        else { c = 0; atomicExch(err, 2); }
-        cs[li] = c;
-        if (c + 1 > localmax) localmax = c + 1;
-      }
+      const unsigned m0 = __reduce_or_sync(0xffffffffu, (unsigned)u0);
+      const unsigned m1 = __reduce_or_sync(0xffffffffu, (unsigned)(u0 >> 32));
+      const unsigned m2 = __reduce_or_sync(0xffffffffu, (unsigned)u1);
+      const unsigned m3 = __reduce_or_sync(0xffffffffu, (unsigned)(u1 >> 32));
+      int32_t c;
+      if (~m0) c = __ffs(~m0) - 1;
+      else if (~m1) c = 32 + __ffs(~m1) - 1;
+      else if (~m2) c = 64 + __ffs(~m2) - 1;
+      else if (~m3) c = 96 + __ffs(~m3) - 1;
+      else { c = 0; if (lane == 0) atomicExch(err, 2); }
+      if (lane == 0) cs[li] = c;
+      if (c + 1 > localmax) localmax = c + 1;
       __syncwarp();
     }
     if (lane == 0) atomicMax(maxc, localmax);

@@ -168,6 +168,7 @@ constexpr int kHash = 1 << kHashBits;     // largest per-row table (slots)
 constexpr int kGemmThreads = 256;
 constexpr int kGemmBins = kHashBits - 4;  // tables of 32 .. kHash slots
 constexpr int kGemmSmem = 96 * 1024;      // shared memory budget of one CTA
+constexpr int kRankE = 4;                 // entries per lane of the rank placement
 
 // table slot of a column key (Fibonacci hashing into 2^tbits slots)
 __device__ __forceinline__ int hslot(int32_t key, int tbits) {
@@ -317,9 +318,12 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const in
   const unsigned glow = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
   const int tsize = 1 << tbits;
   const int tab = warp * R + grp;
-  double *vals = reinterpret_cast<double *>(smem) + (int64_t)tab * tsize;
+  // tables tsize + G elements apart, so that the groups of a warp reading
+  // the same slot index of their own tables hit different banks
+  const int tstride = tsize + G;
+  double *vals = reinterpret_cast<double *>(smem) + (int64_t)tab * tstride;
   int32_t *keys =
-      reinterpret_cast<int32_t *>(smem + sizeof(double) * (size_t)tsize * nwarps * R) + (int64_t)tab * tsize;
+      reinterpret_cast<int32_t *>(smem + sizeof(double) * (size_t)tstride * nwarps * R) + (int64_t)tab * tstride;
   __shared__ int32_t cnt_s[kGemmThreads / 32 * 4];
   __shared__ int32_t ovf_s[kGemmThreads / 32 * 4];
   for (int64_t base = ((int64_t)blockIdx.x * nwarps + warp) * R; base < nrows;
@@ -401,12 +405,38 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const in
         __syncwarp();
       }
       const int32_t scnt = has && !over ? cnt : 0;
-      group_sort_pairs<G>(keys, vals, scnt, tsize, gl, gmask);
+      const int32_t cb = has ? crp[row] : 0, room = has ? crp[row + 1] - cb : 0;
       if (has && !over) {
-        const int32_t cb = crp[row], room = crp[row + 1] - cb;
         if ((ccnt ? cnt > room : room != cnt) && gl == 0) atomicExch(err, 1);
         if (ccnt && gl == 0) ccnt[row] = cnt;
-        for (int32_t a = gl; a < cnt && a < room; a += G) {
+      }
+      if (scnt <= G * kRankE) {
+        // each entry goes to its rank among the row's columns (distinct):
+        // lane gl holds entries gl + G u and counts the smaller columns
+        // against every entry of the compacted table
+        int32_t kk[kRankE], rk[kRankE];
+#pragma unroll
+        for (int u = 0; u < kRankE; u++) {
+          const int32_t e = gl + G * u;
+          kk[u] = e < scnt ? keys[e] : INT32_MAX;
+          rk[u] = 0;
+        }
+        for (int32_t x = 0; x < scnt; x++) {
+          const int32_t kx = keys[x];
+#pragma unroll
+          for (int u = 0; u < kRankE; u++) rk[u] += kx < kk[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kRankE; u++) {
+          const int32_t e = gl + G * u;
+          if (e < scnt && rk[u] < room) {
+            ccol[cb + rk[u]] = kk[u];
+            cval[cb + rk[u]] = vals[e];
+          }
+        }
+      } else {
+        group_sort_pairs<G>(keys, vals, scnt, tsize, gl, gmask);
+        for (int32_t a = gl; a < scnt && a < room; a += G) {
           ccol[cb + a] = keys[a];
           cval[cb + a] = vals[a];
         }
@@ -447,8 +477,8 @@ static int spgemm_pass(const DCsr &A, const DCsr &B, DCsr &C, const uint8_t *bin
     // lanes per row: 8 for tables of up to 64 slots, 16 for 128, else 32
     const int G = tsize <= 64 ? 8 : (tsize <= 128 ? 16 : 32), R = 32 / G;
     const int warps = (int)std::max<int64_t>(
-        1, std::min<int64_t>(kGemmThreads / 32, kGemmSmem / (12 * (int64_t)tsize * R)));
-    const size_t shm = (sizeof(double) + sizeof(int32_t)) * (size_t)tsize * warps * R;
+        1, std::min<int64_t>(kGemmThreads / 32, kGemmSmem / (12 * (int64_t)(tsize + G) * R)));
+    const size_t shm = (sizeof(double) + sizeof(int32_t)) * (size_t)(tsize + G) * warps * R;
     const int64_t per_cta = (int64_t)warps * R;
     const unsigned grid = (unsigned)std::min<int64_t>((nrows + per_cta - 1) / per_cta, (int64_t)num_sms() * 32);
     auto kern = G == 8 ? k_spgemm<8, NUMERIC> : (G == 16 ? k_spgemm<16, NUMERIC> : k_spgemm<32, NUMERIC>);
