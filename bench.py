@@ -59,14 +59,12 @@ WINDOW = (64, 64, 32)
 # profiles/dram_setup_channel128_step.md); absent where no capture of the
 # current version exists.
 NCU_TRAFFIC = {
-    "setup_spgemm": ((60.468e9 + 19.953e9) * 8, "profiles/dram_setup_channel128_step.md (128^3 step x 8)"),
-    "setup_interp": ((12.766e9 + 1.246e9) * 8, "profiles/dram_setup_channel128_step.md (128^3 step x 8)"),
 }
 # the kernels behind each class of the library's event profiler
 CLASS_KERNELS = {
-    "setup_spgemm": "k_spgemm_bin1, k_spgemm_binfill, k_spgemm, k_rows_compact (Galerkin and Schur-complement "
+    "setup_spgemm": "k_spgemm_bin1, k_spgemm_binfill, k_spgemm, k_copy_rows (Galerkin and Schur-complement "
                     "sparse products)",
-    "setup_interp": "k_interp_cap, k_interp_ext_w, k_interp_compact (extended+i interpolation)",
+    "setup_interp": "k_interp_ext_w (extended+i interpolation weights)",
     "hybrid_gs_sweep": "k_hgs, k_hgs2 (hybrid Gauss-Seidel sweeps)",
     "csr_resid_restrict_prolong": "k_csr (residual, restriction, prolongation)",
     "bsr2_spmv": "k_bsr2_spmv, k_cpr_resid (block SpMV)",
