@@ -4,9 +4,13 @@
  *
  * Arithmetic order (stated so another implementation can reproduce the
  * results bit for bit): every sum runs in ascending column (or inner-index)
- * order, each product is rounded before it is added, and the first term of a
- * sum is taken as the rounded product itself (no 0 + x).
+ * order and the first term of a sum is taken as the rounded product itself
+ * (no 0 + x). In the sparse products (or_spgemm and the product inside
+ * or_simple_schur) every later term is accumulated by a fused multiply-add,
+ * acc = fma(a, b, acc), one rounding per term; elsewhere each product is
+ * rounded before it is added.
  */
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 #include "oracle.h"
@@ -148,8 +152,9 @@ static int cmp_i32(const void *a, const void *b) {
 }
 
 /* C = A B, Gustavson row by row. For each (i, j) the terms a_ik b_kj are
- * added in ascending k; the first term initialises the sum. The pattern is
- * every (i, j) reached by some product, zeros included. */
+ * added in ascending k; the first term (rounded) initialises the sum, every
+ * later one is fused into it (fma). The pattern is every (i, j) reached by
+ * some product, zeros included. */
 or_csr *or_spgemm(const or_csr *A, const or_csr *B) {
   int32_t n = A->n, m = B->m;
   int32_t *mark = xmalloc(sizeof(int32_t) * (size_t)m);
@@ -177,13 +182,12 @@ or_csr *or_spgemm(const or_csr *A, const or_csr *B) {
       double a = A->val[ka];
       for (int32_t kb = B->rowptr[k]; kb < B->rowptr[k + 1]; kb++) {
         int32_t j = B->col[kb];
-        double t = a * B->val[kb];
         if (mark[j] != i) {
           mark[j] = i;
-          acc[j] = t;
+          acc[j] = a * B->val[kb];
           C->col[pos++] = j;
         } else {
-          acc[j] = acc[j] + t;
+          acc[j] = fma(a, B->val[kb], acc[j]);
         }
       }
     }
@@ -217,7 +221,8 @@ or_csr *or_transpose(const or_csr *A) {
 /* SIMPLE-type Schur complement (Sec. 3.4, eq. SIMPLE-Schur), read with A_sp
  * in the last factor:  S~ = A_pp - A_ps diag(A_ss)^{-1} A_sp.
  * Row i: for each k of A_ps(i,:) ascending, t = a_ps(i,k) / d_ss(k); for each
- * j of A_sp(k,:) ascending, acc_j gets t * a_sp(k,j) (first term initialises).
+ * j of A_sp(k,:) ascending, acc_j gets t * a_sp(k,j) (the rounded product
+ * initialises, later terms are fused in: acc_j = fma(t, a_sp(k,j), acc_j)).
  * The pattern is the union of A_pp's and the product's; entry = a_pp - acc
  * with a missing operand read as 0. A zero d_ss(k) skips column k. */
 or_csr *or_simple_schur(const or_csr *App, const or_csr *Aps, const or_csr *Asp, const or_csr *Ass) {
@@ -263,10 +268,9 @@ or_csr *or_simple_schur(const or_csr *App, const or_csr *Aps, const or_csr *Asp,
       double t = Aps->val[ka] / dss[k];
       for (int32_t kb = Asp->rowptr[k]; kb < Asp->rowptr[k + 1]; kb++) {
         int32_t j = Asp->col[kb];
-        double pr = t * Asp->val[kb];
         if (mark[j] != i) { mark[j] = i; has[j] = 0; app[j] = 0.0; cols[cnt++] = j; }
-        if (!has[j]) { acc[j] = pr; has[j] = 1; }
-        else acc[j] = acc[j] + pr;
+        if (!has[j]) { acc[j] = t * Asp->val[kb]; has[j] = 1; }
+        else acc[j] = fma(t, Asp->val[kb], acc[j]);
       }
     }
     qsort(cols, (size_t)cnt, sizeof(int32_t), cmp_i32);

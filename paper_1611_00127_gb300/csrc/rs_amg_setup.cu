@@ -193,9 +193,14 @@ __global__ void k_pmis_fmark(int32_t n, const int32_t *rp, const int32_t *col, c
   if ((threadIdx.x & 31) == 0 && rest) atomicAdd(left, __popc(rest));
 }
 
+// (one atomic per distinct system of a warp)
 __global__ void k_seg_count_c(int32_t n, const int8_t *cf, const int32_t *seg, int32_t *cnt) {
-  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && cf[i] == 1) atomicAdd(&cnt[seg[i]], 1);
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool c = i < n && cf[i] == 1;
+  const unsigned act = __ballot_sync(0xffffffffu, c);
+  if (!c) return;
+  const unsigned same = __match_any_sync(act, seg[i]);
+  if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&cnt[seg[i]], __popc(same));
 }
 
 // systems that stop here lose their C points; C flags for the numbering
@@ -471,16 +476,24 @@ __device__ void warp_sort_asc(int32_t *a, int32_t m, int32_t cap) {
 // bounds of a level for the interpolation capacities: the largest number of
 // entries of a row plus its neighbours' rows (bounds the candidate count),
 // and the largest row
+// (the maxima reduced over the warp first: one atomic per warp)
 __global__ void k_interp_bounds(int32_t n, const int32_t *rp, const int32_t *col, int32_t *mx) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int32_t c = rp[i + 1] - rp[i];
-  for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
-    const int32_t j = col[q];
-    c += rp[j + 1] - rp[j];
+  int32_t c = 0, len = 0;
+  if (i < n) {
+    len = rp[i + 1] - rp[i];
+    c = len;
+    for (int32_t q = rp[i]; q < rp[i + 1]; q++) {
+      const int32_t j = col[q];
+      c += rp[j + 1] - rp[j];
+    }
   }
-  atomicMax(mx, c);
-  atomicMax(mx + 1, rp[i + 1] - rp[i]);
+  c = __reduce_max_sync(0xffffffffu, c);
+  len = __reduce_max_sync(0xffffffffu, len);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(mx, c);
+    atomicMax(mx + 1, len);
+  }
 }
 
 __device__ __forceinline__ int find_row(const int32_t *col, int32_t s, int32_t e, int32_t v) {
@@ -1731,11 +1744,11 @@ int amg_build(const DCsr &A0, const std::vector<int32_t> &seg_off0, const rs_amg
         // a few rounds between host checks; a round with nothing undecided does nothing
         for (int r = 0; r < 3; r++) {
           RS_CHECK_CUDA(cudaMemsetAsync(left, 0, sizeof(int32_t), s));
-          RS_ROWG_SWITCH(rg, RS_COUNTED k_pmis_losers<G_><<<gg, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, key,
-                                                                                cfp, notmax));
+          // (a thread per point: after the first rounds most points are
+          // decided and leave at once)
+          RS_COUNTED k_pmis_losers<1><<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, key, cfp, notmax);
           RS_COUNTED k_pmis_select<<<g, kBlock, 0, s>>>(np, notmax, cfp);
-          RS_ROWG_SWITCH(rg, RS_COUNTED k_pmis_fmark<G_><<<gg, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, cfp,
-                                                                               left));
+          RS_COUNTED k_pmis_fmark<1><<<g, kBlock, 0, s>>>(np, M.rowptr, M.col, strong, cfp, left);
         }
         RS_TRY(sync_copy(&hleft, left, sizeof(int32_t), s));
       }

@@ -4,8 +4,10 @@
 //
 // Arithmetic order, shared with the CPU check so that the integer decisions
 // taken on the results (strength, C/F splitting) are reproduced exactly:
-// sums run in ascending inner index, each product is rounded before it is
-// added, and the first term of a sum is the rounded product itself.
+// sums run in ascending inner index and the first term of a sum is the
+// rounded product itself; in the sparse products every later term is fused
+// into the sum (fma, one rounding), elsewhere each product is rounded before
+// it is added.
 #include <type_traits>
 
 #include "rs_internal.cuh"
@@ -345,8 +347,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const in
         const int32_t u = u0 + gl;
         const bool live = u < blen;
         const int32_t j = live ? bcol[bs + u] : -1;
-        double prod = 0.0;
-        if (NUMERIC) prod = a * (live ? bval[bs + u] : 0.0);
+        const double b = (NUMERIC && live) ? bval[bs + u] : 0.0;
         int h = -1;
         bool fresh = false;
         if (live) {
@@ -360,7 +361,9 @@ __global__ void __launch_bounds__(kGemmThreads) k_spgemm(int32_t nrows, const in
           }
         }
         __syncwarp();
-        if (NUMERIC && h >= 0) vals[h] = fresh ? prod : vals[h] + prod;
+        // a fresh entry takes the rounded product (a b + -0 = a b exactly),
+        // a present one fuses the term into its sum: one FP64 instruction
+        if (NUMERIC && h >= 0) vals[h] = fma(a, b, fresh ? -0.0 : vals[h]);
         __syncwarp();
       }
     }
