@@ -59,6 +59,8 @@ WINDOW = (64, 64, 32)
 # profiles/dram_setup_channel128_step.md); absent where no capture of the
 # current version exists.
 NCU_TRAFFIC = {
+    "setup_spgemm": ((41.395e9 + 12.701e9) * 8, "profiles/dram_setup_channel128_step.md (128^3 step x 8)"),
+    "setup_interp": ((8.074e9 + 0.805e9) * 8, "profiles/dram_setup_channel128_step.md (128^3 step x 8)"),
 }
 # the kernels behind each class of the library's event profiler
 CLASS_KERNELS = {
