@@ -161,6 +161,69 @@ def test_spgemm_and_transpose_match_scipy(oracle):
     np.testing.assert_array_equal(T.toarray(), A.T.toarray())
 
 
+def _fl(x):
+    """Round an exact rational to the nearest double (ties to even)."""
+    return float(x)
+
+
+def test_spgemm_rounding_is_rounded_first_term_then_fused(oracle):
+    """Reading R31 of the sparse products: in ascending inner index, the
+    first term is the rounded product and every later term is fused into the
+    sum (one rounding per term). Checked against exact rational arithmetic on
+    terms chosen so that the fused and the separately rounded sums differ in
+    the last place, for the product and for the SIMPLE Schur complement."""
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(11)
+    # a 1 x 3 times 3 x 1 product: c = a0 b0 + a1 b1 + a2 b2
+    found = 0
+    for _ in range(2000):
+        a = 1.0 + rng.random(3)
+        b = 1.0 + rng.random(3)
+        b[1] = -b[1]
+        acc = _fl(Fr(a[0]) * Fr(b[0]))
+        for k in (1, 2):
+            acc = _fl(Fr(a[k]) * Fr(b[k]) + Fr(acc))
+        sep = a[0] * b[0]
+        for k in (1, 2):
+            sep = sep + a[k] * b[k]
+        if acc == sep:
+            continue
+        found += 1
+        A = oracle.Csr.from_arrays(np.array([0, 3], np.int32), np.array([0, 1, 2], np.int32), a)
+        B = oracle.Csr.from_arrays(np.array([0, 1, 2, 3], np.int32), np.zeros(3, np.int32), b)
+        C = oracle.spgemm(A, B).scipy().toarray()
+        assert C[0, 0] == acc, (a, b, C[0, 0], acc, sep)
+        if found >= 20:
+            break
+    assert found >= 20
+    # S~ = A_pp - A_ps diag(A_ss)^-1 A_sp on 2 x 2 blocks: row 0 of the
+    # product is t0 a_sp(0,0) + t1 a_sp(1,0) with t_k = a_ps(0,k) / d_k
+    found = 0
+    for _ in range(2000):
+        aps = 1.0 + rng.random(2)
+        asp = 1.0 + rng.random(2)
+        asp[1] = -asp[1]
+        d = 1.0 + rng.random(2)
+        app = 3.0 + rng.random()
+        t = aps / d
+        acc = _fl(Fr(t[0]) * Fr(asp[0]))
+        acc = _fl(Fr(t[1]) * Fr(asp[1]) + Fr(acc))
+        sep = t[0] * asp[0] + t[1] * asp[1]
+        if acc == sep:
+            continue
+        found += 1
+        I2 = np.array([0, 1, 2], np.int32)
+        App = oracle.Csr.from_arrays(I2, np.array([0, 1], np.int32), np.array([app, app]))
+        Aps = oracle.Csr.from_arrays(np.array([0, 2, 2], np.int32), np.array([0, 1], np.int32), aps)
+        Asp = oracle.Csr.from_arrays(np.array([0, 1, 2], np.int32), np.array([0, 0], np.int32), asp)
+        Ass = oracle.Csr.from_arrays(I2, np.array([0, 1], np.int32), d)
+        S = oracle.simple_schur(App, Aps, Asp, Ass).scipy().toarray()
+        assert S[0, 0] == app - acc, (S[0, 0], app - acc, app - sep)
+        if found >= 20:
+            break
+    assert found >= 20
+
+
 def test_galerkin_matches_dense_triple_product(oracle, inputs):
     rp, c, v = inputs.poisson_2d(10)
     A = _csr(oracle, rp, c, v)
