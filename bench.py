@@ -62,6 +62,8 @@ NCU_TRAFFIC = {
     "setup_spgemm": ((41.395e9 + 12.701e9) * 8, "profiles/dram_setup_channel128_step.md (128^3 step x 8)"),
     "setup_interp": ((8.074e9 + 0.805e9) * 8, "profiles/dram_setup_channel128_step.md (128^3 step x 8)"),
 }
+# nominal HBM3e bandwidth of a GB300 (the fractions are also given against it)
+NOMINAL_HBM_GBS = 7900.0
 # the kernels behind each class of the library's event profiler
 CLASS_KERNELS = {
     "setup_spgemm": "k_spgemm_bin1, k_spgemm_binfill, k_spgemm, k_copy_rows (Galerkin and Schur-complement "
@@ -634,7 +636,8 @@ def class_roofline(prof, peak, peak_kind, classes=None):
     achieved = by / (ms * 1e-3) / 1e9
     tr = NCU_TRAFFIC.get(k)
     return dict(bound="hbm", kernel=k, kernels=CLASS_KERNELS.get(k), achieved=achieved, peak=peak, unit="GB/s",
-                frac=achieved / peak, traffic=tr[0] / n if tr else None, traffic_source=tr[1] if tr else None,
+                frac=achieved / peak, frac_nominal=achieved / NOMINAL_HBM_GBS,
+                traffic=tr[0] / n if tr else None, traffic_source=tr[1] if tr else None,
                 peak_source=peak_kind, launches=n, ms=ms, bytes=by, launch_ms=ms / n, bytes_per_launch=by / n,
                 how="all launches of the class in one profiled headline step: algorithmic bytes over their "
                     "summed device time (CUDA events around each call)")
@@ -728,11 +731,13 @@ def main():
         sp = k["spmv_bytes"] / (k["spmv_ms"] * 1e-3) / 1e9
         level0[pname] = dict(
             rows=k["rows"], nnz=k["nnz"],
-            k_hgs=dict(launch_ms=k["sweep_ms"], bytes_per_launch=k["sweep_bytes"], achieved=sw, frac=sw / peak),
+            k_hgs=dict(launch_ms=k["sweep_ms"], bytes_per_launch=k["sweep_bytes"], achieved=sw, frac=sw / peak,
+                       frac_nominal=sw / NOMINAL_HBM_GBS),
             k_bsr2_spmv=dict(launch_ms=k["spmv_ms"], bytes_per_launch=k["spmv_bytes"], achieved=sp, frac=sp / peak,
-                             nnzb=k["nnzb"]),
+                             frac_nominal=sp / NOMINAL_HBM_GBS, nnzb=k["nnzb"]),
             transfer={t: dict(launch_ms=v["ms"], bytes_per_launch=v["bytes"], achieved=v["gbs"],
-                              frac=v["gbs"] / peak) for t, v in k["transfer"].items()})
+                              frac=v["gbs"] / peak, frac_nominal=v["gbs"] / NOMINAL_HBM_GBS)
+                      for t, v in k["transfer"].items()})
         torch.cuda.empty_cache()
     side = {}
     if not args.no_side:
