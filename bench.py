@@ -300,6 +300,7 @@ class Gpu3DStep:
         self.u = torch.as_tensor(I.initial_state(p), device="cuda")
         self.xout = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in KINDS_3D]
         self.host = host
+        self.hier = {}   # per preconditioner: its hierarchies (filled by a profiled step)
         if host is not None:
             # the problem reads its permeability from buffers the copies refill
             self.dk = torch.empty_like(host["k"], device="cuda")
@@ -333,6 +334,11 @@ class Gpu3DStep:
             ev[1].record()
             st = R.gmres_solve(self.J, M, self.b, self.xout[q], R.GmresParams(m=30, maxit=self.maxit, rtol=1e-8))
             ev[2].record()
+            if per_solve_profile is not None:
+                try:
+                    self.hier[name] = hierarchy_stats(M)
+                except Exception as e:   # a report field only: never fail the bench on it
+                    self.hier[name] = dict(error=str(e))
             M.close()
             if per_solve_profile is not None:
                 torch.cuda.synchronize()
@@ -363,6 +369,23 @@ def hbm_peak():
 def shares(prof):
     tot = sum(v[0] for v in prof.values()) or 1.0
     return {k: round(v[0] / tot, 4) for k, v in prof.items() if v[2] > 0}
+
+
+def hierarchy_stats(M):
+    """Levels, rows per level and operator complexity (the levels' nonzeros
+    summed over the finest level's) of each AMG hierarchy inside a
+    preconditioner (which 0: pressure block, Schur complement or black-box;
+    1: the saturation block)."""
+    out = {}
+    for which, name in ((0, "hierarchy_0"), (1, "hierarchy_1")):
+        H = M.amg(which)
+        if H is None:
+            continue
+        info = [H.level_info(l) for l in range(H.nlevels)]
+        nnz0 = info[0][1] if info and info[0][1] > 0 else 1
+        out[name] = dict(levels=len(info), rows=[x[0] for x in info],
+                         op_complexity=sum(x[1] for x in info) / nnz0)
+    return out
 
 
 def profiled_step(step):
@@ -715,6 +738,7 @@ def main():
     peak, peak_kind = hbm_peak()
     # per kernel class, one profiled headline step
     prof, per_solve = profiled_step(step)
+    hier = dict(getattr(step, "hier", {}))
     roofline = class_roofline(prof, peak, peak_kind)
     roofline_solve = class_roofline(prof, peak, peak_kind,
                                     classes=("hybrid_gs_sweep", "csr_resid_restrict_prolong", "bsr2_spmv",
@@ -796,6 +820,7 @@ def main():
         roofline_solve=roofline_solve,
         level0_kernels=level0,
         kernel_profile=dict(note="one eager profiled headline step, CUDA events per launch", classes=kernel_profile),
+        hierarchies=hier,
         side=side,
         ensemble=ensemble,
         newton=newton,
